@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: exact Jones-polynomial evaluation of the 64-knot random grid-walk workload.
+
+Workload ("scale"): 64 random grid-walk knots, grid side L=40, seeds 1..64 (rank r of
+N uses seeds 64r+1..64r+64), each redrawn until it has 100..400 crossings, random
+over/under per crossing; every knot is evaluated at q = 2, 3, 5 (t = i, e^{i pi/3},
+(3+sqrt 5)/2).  One step = Z(q) and V_K(t(q)) for all 64 x 3 = 192 (knot, q) pairs,
+all on the GPU through libpk.  `value` is knot evaluations per second (one knot = one
+(knot, q) pair), whole job, inputs resident in HBM; L2 is flushed between steps.
+
+--impl reference times the CPU oracle (complex128 spin elimination in numpy) on the
+host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+QS = (2, 3, 5)
+FP32_CORE_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FP64_TFLOPS = 1.25                                    # GB300 FP64 rate (profiling recipe)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--skip-c128", action="store_true", help="omit the complex128 comparison pass")
+    ap.add_argument("--qs", default="2,3,5")
+    return ap.parse_args()
+
+
+def workload(rank):
+    import knotgen as kg
+    return [kg.random_grid_knot(40, 64 * rank + s, True, 100, 400) for s in range(1, 65)]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, dev):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(dev)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(knots, budget_s, qs):
+    """The oracle as it stands on a bounded sample: (evaluations, seconds, sample text)."""
+    import oracle
+    t0 = time.perf_counter()
+    n = 0
+    done = []
+    for gk in knots:
+        for q in qs:
+            g = oracle.tait_graph(gk.pd, outer=gk.outer)
+            z = oracle.z_complex(g.n_v, g.edges, q)
+            oracle.jones_from_z(z, g, q)
+            n += 1
+            done.append(f"{gk.seed}@q{q}")
+            if time.perf_counter() - t0 > budget_s:
+                el = time.perf_counter() - t0
+                return n, el, f"first {n} (knot, q) evaluations in workload order ({done[0]}..{done[-1]})"
+    el = time.perf_counter() - t0
+    return n, el, f"all {n} (knot, q) evaluations"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    qs = tuple(int(x) for x in args.qs.split(","))
+    knots = workload(0)
+    # each step: a bounded sample (~8 s of oracle work) of the workload
+    for _ in range(args.warmup):
+        cpu_oracle_rate(knots, 1.0, qs)
+    tot_n, tot_t = 0, 0.0
+    sample = ""
+    for _ in range(args.steps):
+        n, t, sample = cpu_oracle_rate(knots, 8.0, qs)
+        tot_n += n
+        tot_t += t
+    v = tot_n / tot_t
+    out = {"impl": "reference", "metric": "knot evaluations per second (exact Z(q), V_K(t(q)))",
+           "value": v, "unit": "knots/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": {"workload": "scale: 64 grid-walk knots L=40, 100-400 crossings, q in {2,3,5}",
+                                           "impl": "CPU oracle, numpy complex128 spin elimination"},
+           "cpu_baseline": {"value": v, "unit": "knots/s", "cores": 1, "kind": "oracle",
+                            "sample": sample + " per step"},
+           "e2e": {"value": v, "unit": "knots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1807_02119_gb300 as pk
+
+    qs = tuple(int(x) for x in args.qs.split(","))
+    knots = workload(rank)
+    ctx = pk.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream.cuda_stream)
+    t0 = time.perf_counter()
+    plans = []
+    for gk in knots:
+        k = pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer)
+        for q in qs:
+            plans.append(pk.Plan(ctx, k, q))
+    plan_s = time.perf_counter() - t0
+    stats = [p.stats() for p in plans]
+    prec = args.precision
+
+    # resident workspaces for the headline precision, one per plan
+    ws = [pk.workspace(p, prec) for p in plans]
+    for p, w in zip(plans, ws):
+        pk.upload(p, prec, w)
+    torch.cuda.synchronize()
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def one_pass():
+        for p, w in zip(plans, ws):
+            pk.launch(p, prec, w)
+
+    def results():
+        return [pk.download(p, prec, w) for p, w in zip(plans, ws)]
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    res_main = results()
+
+    # timed region: K steps, L2 flushed between steps (outside the events)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one_pass()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = sum(times) / len(times)
+    if dist:
+        t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    evals = len(plans)
+    value = world * evals / (step_ms / 1000.0)
+
+    # per-kernel-class profile of one pass (CUDA events around every launch)
+    prof = {}
+    for p, w in zip(plans, ws):
+        for kname, d in pk.profile(p, prec, w).items():
+            acc = prof.setdefault(kname, {"ms": 0.0, "launches": 0.0, "cmacs": 0.0, "bytes": 0.0})
+            for f in acc:
+                acc[f] += d[f]
+
+    # end to end through the public API: host PD-derived recipe -> device -> host result
+    e2e_times = []
+    h2d = sum(len(p.debug_blob(0)) for p in plans)
+    d2h = 32 * len(plans)
+    for i in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for p, w in zip(plans, ws):
+            pk.evaluate(p, prec, w)
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_val = world * evals / (sum(e2e_times[1:]) / max(1, len(e2e_times) - 1))
+
+    # complex128 pass for the error report (shared workspace; uploads inside)
+    c128 = None
+    if not args.skip_c128 and prec != "c128":
+        big = max(p.workspace_bytes("c128") for p in plans)
+        wsd = torch.empty(big, dtype=torch.uint8, device="cuda")
+        for p in plans[:8]:
+            pk.evaluate(p, "c128", wsd)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res128 = []
+        for p in plans:
+            pk.upload(p, "c128", wsd)
+            pk.launch(p, "c128", wsd)
+            res128.append(pk.download(p, "c128", wsd))
+        b.record(stream)
+        b.synchronize()
+        ms128 = a.elapsed_time(b)
+        errs = []
+        for (z1, v1), (z2, v2) in zip(res_main, res128):
+            d = z1.exp2 - z2.exp2
+            m1 = z1.mantissa * (2.0 ** d if d > -1000 else 0.0)
+            errs.append(abs(m1 - z2.mantissa) / abs(z2.mantissa))
+        c128 = {"value": world * evals / (ms128 / 1000.0), "unit": "knots/s", "ms_per_step": ms128,
+                "note": "one timed pass after a partial warm-up; program uploads included",
+                "max_rel_err_vs_c128": max(errs), "median_rel_err_vs_c128": statistics.median(errs)}
+        del wsd
+
+    rk = prof["rows"]
+    pk_ = peaks()
+    elem = 16 if prec == "c128" else 8
+    flops = 8.0 * rk["cmacs"]
+    ai = flops / max(rk["bytes"], 1.0)
+    alu_peak = FP64_TFLOPS if prec == "c128" else FP32_CORE_TFLOPS
+    ridge = alu_peak * 1e12 / (pk_["hbm_gbs"] * 1e9)
+    if ai > ridge:
+        ach = flops / (rk["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": ach / alu_peak, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz" if prec != "c128"
+                else "nominal FP64 rate of GB300"}
+    else:
+        ach = rk["bytes"] / (rk["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk_["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk_["hbm_gbs"], "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    roof.update({"kernel": "k_rows (fused permute-and-contract)", "arith_intensity_flop_per_byte": ai,
+                 "launches_per_pass": rk["launches"], "ms_per_pass": rk["ms"]})
+
+    cpu = None
+    if rank == 0 and world == 1:
+        n, t, sample = cpu_oracle_rate(knots, 15.0, qs)
+        cpu = {"value": n / t, "unit": "knots/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    launches = sum(p.launches(prec) for p in plans) * args.steps
+    tot_cmacs = sum(s["cmacs"] for s in stats)
+    if rank == 0:
+        out = {"metric": "knot evaluations per second (exact Z(q), V_K(t(q))), split-FP32 vs complex128",
+               "value": value, "unit": "knots/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+               "config": {"workload": "scale: 64 random grid-walk knots per GPU, L=40, 100-400 crossings, "
+                                      "random over/under, q in {2,3,5}; 192 (knot, q) evaluations per step",
+                          "order": "auto (min-degree spin elimination chosen for all)",
+                          "l2": "flushed between steps (512 MB write)",
+                          "plan_seconds": plan_s, "complex_macs_per_step": tot_cmacs,
+                          "complex_tflops": 8 * tot_cmacs / (step_ms / 1e3) / 1e12},
+               "roofline": roof, "cpu_baseline": cpu,
+               "e2e": {"value": e2e_val, "unit": "knots/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h},
+               "gpu_launches": launches, "clocks": clk, "kernel_classes": prof,
+               "c128": c128}
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * pk.h -- C ABI of the GB300 library that evaluates the Jones polynomial V_K(t(q))
+ * of a knot by exact contraction of the PACI tensor network (Meichanetzidis &
+ * Kourtis, "Evaluating the Jones polynomial with tensor networks").
+ *
+ * Problem statement (Sec. III, first paragraph): given a knot diagram and an
+ * integer q, compute the partition function Z(q) of the q-state Potts model with
+ * anisotropic complex interactions on the knot's signed Tait graph, and from it
+ * V_K(t(q)) = A(q) Z(q) (Eq. JonesPotts) with t(q) = (q + sqrt(q) sqrt(q-4) - 2)/2
+ * (Eq. potts2jones).
+ *
+ * Conventions for every entry point:
+ *  - Return value is a pk_status; nothing is thrown across the ABI.  On error the
+ *    context's pk_last_error() holds a one-line message.
+ *  - The caller owns every array it passes; inputs are copied, never retained.
+ *  - Handles (pk_ctx, pk_knot, pk_plan) are opaque and freed by their *_destroy.
+ *  - A context is used by one host thread at a time.
+ *  - Device pointers are plain CUDA device addresses on the context's device.
+ *  - Results Z and V are returned as pk_scaled because they leave the double
+ *    range for large knots.
+ */
+#ifndef PK_H
+#define PK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pk_ctx pk_ctx;
+typedef struct pk_knot pk_knot;
+typedef struct pk_plan pk_plan;
+
+/* value = (re + i im) * 2^exp2; max(|re|,|im|) in [0.5, 1) unless the value is 0. */
+typedef struct {
+  double re, im;
+  int64_t exp2;
+} pk_scaled;
+
+typedef enum {
+  PK_OK = 0,
+  PK_EINVAL = 1,     /* bad argument: q < 1, malformed PD code, bad sign, NULL pointer */
+  PK_ENOTKNOT = 2,   /* diagram has more than one component (V undefined here)        */
+  PK_ENOMEM = 3,     /* host allocation failed or workspace too small                  */
+  PK_ETOOWIDE = 4,   /* plan exceeds the slicing limits                                 */
+  PK_ECUDA = 5,      /* a CUDA runtime call failed                                      */
+  PK_ETIMEOUT = 6,   /* a bounded device wait gave up                                   */
+  PK_ENODEVICE = 7   /* operation needs a GPU context (device >= 0)                     */
+} pk_status;
+
+typedef enum {
+  PK_C128 = 0,       /* complex128 storage, FP64 arithmetic                               */
+  PK_C64 = 1,        /* complex64 storage, FP32 arithmetic                                */
+  PK_SPLIT_TF32 = 2  /* complex64 storage; large steps as 3xTF32 tensor-core products     */
+} pk_precision;
+
+typedef enum {
+  PK_ORDER_AUTO = 0,         /* cheapest (by complex multiply-adds) of the orders below     */
+  PK_ORDER_GREEDY_EDGE = 1,  /* Sec. III "greedy": vertex tensors on Tait vertices, indices
+                                on edges; contract the pair whose result has the smallest
+                                degree (graph minors H, cost O(q^Delta_H))                  */
+  PK_ORDER_GREEDY_SPIN = 2,  /* same greedy on the network whose COPY tensors are kept as
+                                shared spin indices (clause matrices only)                  */
+  PK_ORDER_ELIM_SPIN = 3,    /* spin network, order from min-degree spin elimination        */
+  PK_ORDER_PARTITION = 4     /* spin network, recursive-bisection separator order           */
+} pk_order;
+
+typedef struct {
+  int32_t order;             /* pk_order                                                    */
+  int32_t flags;             /* reserved, 0                                                 */
+  double max_log2_elems;     /* slice indices until no tensor exceeds 2^x elements (<= 31;
+                                0 -> 31)                                                     */
+  double max_log2_slices;    /* refuse (PK_ETOOWIDE) plans needing more slices (0 -> 40)    */
+} pk_plan_opts;
+
+typedef struct {
+  double log2_max_elems;     /* largest tensor of one slice, log2 elements                  */
+  double cmacs;              /* complex multiply-adds, all slices                           */
+  double bytes_c64;          /* algorithmic bytes at 8 B/element: sum over steps of
+                                |A| + |B| + |C|, all slices (x2 for complex128)             */
+  int64_t n_slices;
+  int32_t n_steps;           /* pairwise contraction steps per slice                        */
+  int32_t max_rank;          /* Delta_H: largest tensor rank (indices) in one slice         */
+  int32_t order_used;        /* pk_order actually used                                      */
+  int32_t n_tensors;         /* initial tensors                                             */
+  uint64_t workspace_c128;   /* device workspace bytes for PK_C128                          */
+  uint64_t workspace_c64;    /* device workspace bytes for PK_C64 / PK_SPLIT_TF32           */
+} pk_plan_stats;
+
+/* ---- context ------------------------------------------------------------------ */
+
+/* device >= 0: a GPU context on that device; stream (a cudaStream_t, may be NULL for
+ * the legacy default stream) is where every launch goes.  device = -1: a host-only
+ * context for knot input and planning (pk_eval returns PK_ENODEVICE). */
+pk_status pk_ctx_create(int32_t device, void* stream, pk_ctx** out);
+pk_status pk_ctx_set_stream(pk_ctx* ctx, void* stream);
+const char* pk_last_error(const pk_ctx* ctx);
+void pk_ctx_destroy(pk_ctx* ctx);
+
+/* ---- knots (Sec. II) ------------------------------------------------------------ */
+
+/* PD code: n crossings, pd[4*i .. 4*i+3] = (a, b, c, d); arcs labelled 0..2n-1 along
+ * the orientation; a = incoming under-arc, then counter-clockwise; c = a+1 mod 2n.
+ * outer_arc/outer_side (side 0 = left, 1 = right of that arc) name a region that the
+ * Tait graph treats as the unbounded, white region (Sec. II); outer_arc = -1 picks
+ * the colour class of the region right of arc 0 as black.  n = 0 is the unknot.
+ * Errors: PK_EINVAL (labels, orientation or planarity wrong). */
+pk_status pk_knot_from_pd(pk_ctx* ctx, const int32_t* pd, int32_t n, int32_t outer_arc,
+                          int32_t outer_side, pk_knot** out);
+
+/* Signed Tait graph given directly: n_e edges uve[3*e..] = (u, v, eps), eps = +-1,
+ * u, v in [0, n_v); writhe w.  Z is defined for any such graph (general PACI
+ * instance, Sec. III); V uses tau = sum eps and needs 4 | 3w + tau + 2 n_v + 2. */
+pk_status pk_knot_from_signed_graph(pk_ctx* ctx, int32_t n_v, int32_t n_e, const int32_t* uve,
+                                    int32_t writhe, pk_knot** out);
+
+/* Random grid-walk knot (Sec. III.A): permutations x, y of 0..L-1 from SplitMix64(seed)
+ * by Fisher-Yates; redrawn from the same stream until the crossing count lies in
+ * [ncross_min, ncross_max]; random_over_under != 0 draws one over/under bit per
+ * crossing, else vertical strands pass over.  The unbounded region is white. */
+pk_status pk_knot_from_grid_walk(pk_ctx* ctx, int32_t L, uint64_t seed, int32_t random_over_under,
+                                 int32_t ncross_min, int32_t ncross_max, pk_knot** out);
+
+pk_status pk_knot_info(const pk_knot* k, int32_t* n_v, int32_t* n_c, int32_t* writhe,
+                       int32_t* tau, int32_t* components);
+/* Copies the signed Tait graph: uve[3*e..] = (u, v, eps) for each crossing (n_c edges). */
+pk_status pk_knot_edges(const pk_knot* k, int32_t* uve);
+/* Copies the PD code (4*n_c ints); PK_EINVAL for knots built from a signed graph. */
+pk_status pk_knot_pd(const pk_knot* k, int32_t* pd);
+void pk_knot_destroy(pk_knot* k);
+
+/* ---- contraction plan (Sec. III: network G_T, contraction order, slicing) ------ */
+
+/* q >= 1.  opts may be NULL (defaults).  PK_ETOOWIDE if slicing cannot meet the limits. */
+pk_status pk_plan_create(pk_ctx* ctx, const pk_knot* k, int32_t q, const pk_plan_opts* opts,
+                         pk_plan** out);
+pk_status pk_plan_info(const pk_plan* p, pk_plan_stats* out);
+/* Device workspace needed by pk_eval / pk_upload / pk_launch at this precision. */
+pk_status pk_plan_workspace_bytes(const pk_plan* p, int32_t precision, uint64_t* bytes);
+/* Plan introspection for host-side checks: writes n_steps records of 8 int64:
+ * (a, b, c, R, K, N, rank_c, kernel) with a/b/c tensor ids and the GEMM extents
+ * R (batch x free-of-A rows), K, N of one slice. */
+pk_status pk_plan_steps(const pk_plan* p, int64_t* rec);
+void pk_plan_destroy(pk_plan* p);
+
+/* ---- evaluation --------------------------------------------------------------- */
+
+/* Full evaluation on the context's stream; blocks until Z and V are on the host.
+ * d_workspace: device buffer of at least pk_plan_workspace_bytes bytes, owned by the
+ * caller; NULL lets the context allocate (and keep) one.  V is written only for
+ * knots (PK_ENOTKNOT otherwise, Z still valid). */
+pk_status pk_eval(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                  uint64_t workspace_bytes, pk_scaled* Z, pk_scaled* V);
+
+/* The three stages of pk_eval, asynchronous on the context's stream:
+ * pk_upload copies the plan's initial-tensor recipe into the workspace (host->device);
+ * pk_launch enqueues every kernel of every slice (the workspace must hold an uploaded
+ * recipe of the same plan and precision); pk_download waits for the stream, copies
+ * the scaled result back and applies A(q). */
+pk_status pk_upload(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                    uint64_t workspace_bytes);
+pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                    uint64_t workspace_bytes);
+pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const void* d_workspace,
+                      pk_scaled* Z, pk_scaled* V);
+
+/* Internal plan records, for host-side verification of a plan without a GPU.
+ * which = 0: the device program (recipe records then slot records, as uploaded);
+ *         1: the step records; 2: per tensor (arena element offset, elements) int64
+ *         pairs; 3: int64 scalars (q, n_init, n_steps, n_slices, n_sliced,
+ *         final_tensor, off_recipe, off_slots, n_slots, sizeof step record);
+ *         4: three doubles (re, im, exp2) of the constant factor (loops of the graph)
+ *         that multiplies the contracted value.
+ * With dst == NULL only *bytes is set.  The record layouts are those of
+ * csrc/pk_internal.h (Recipe, Slot, Step) and may change between versions. */
+pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_t* bytes);
+
+/* Runs the kernels of pk_launch once (same stream, same workspace, recipe already
+ * uploaded) with a CUDA event pair around every launch, waits, and returns per kernel
+ * class c (0 build, 1 rows, 2 split-K, 3 results): out[c] = milliseconds,
+ * out[4+c] = launches, out[8+c] = algorithmic complex multiply-adds, out[12+c] =
+ * algorithmic bytes (|A| + |B| + |C| at the precision's element size).  16 doubles. */
+pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                     uint64_t workspace_bytes, double* out);
+
+/* Number of kernel launches pk_launch issues for this plan and precision. */
+pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launches);
+
+/* Host-side normalisation only: V = A(q) Z for the knot's (n_v, w, tau) (Eq. JonesPotts). */
+pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_scaled* V);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PK_H */

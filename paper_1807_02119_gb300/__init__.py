@@ -1,0 +1,327 @@
+"""Python binding of libpk (include/pk.h): argument marshalling only.
+
+Every step of the evaluation runs in the library (host planning in C++, contraction
+in CUDA kernels for sm_103a).  PyTorch supplies device memory (the workspace) and
+the stream.  There is no CPU fallback: if libpk.so is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpk.so")
+
+PK_C128, PK_C64, PK_SPLIT_TF32 = 0, 1, 2
+PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split_tf32": PK_SPLIT_TF32}
+ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4}
+STATUS = {0: "PK_OK", 1: "PK_EINVAL", 2: "PK_ENOTKNOT", 3: "PK_ENOMEM", 4: "PK_ETOOWIDE",
+          5: "PK_ECUDA", 6: "PK_ETIMEOUT", 7: "PK_ENODEVICE"}
+
+EXPORTED = [
+    "pk_ctx_create", "pk_ctx_set_stream", "pk_last_error", "pk_ctx_destroy",
+    "pk_knot_from_pd", "pk_knot_from_signed_graph", "pk_knot_from_grid_walk", "pk_knot_info",
+    "pk_knot_edges", "pk_knot_pd", "pk_knot_destroy", "pk_plan_create", "pk_plan_info",
+    "pk_plan_workspace_bytes", "pk_plan_steps", "pk_plan_destroy", "pk_eval", "pk_upload",
+    "pk_launch", "pk_download", "pk_plan_launches", "pk_jones_from_z", "pk_plan_debug_blob",
+    "pk_profile",
+]
+
+
+class PkError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pk_scaled(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double), ("exp2", C.c_int64)]
+
+
+class pk_plan_opts(C.Structure):
+    _fields_ = [("order", C.c_int32), ("flags", C.c_int32), ("max_log2_elems", C.c_double),
+                ("max_log2_slices", C.c_double)]
+
+
+class pk_plan_stats(C.Structure):
+    _fields_ = [("log2_max_elems", C.c_double), ("cmacs", C.c_double),
+                ("bytes_c64", C.c_double), ("n_slices", C.c_int64), ("n_steps", C.c_int32),
+                ("max_rank", C.c_int32), ("order_used", C.c_int32), ("n_tensors", C.c_int32),
+                ("workspace_c128", C.c_uint64), ("workspace_c64", C.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpk.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; "
+                          "g.build()'` (there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    P = C.POINTER
+    sig = {
+        "pk_ctx_create": [i32, vp, P(vp)],
+        "pk_ctx_set_stream": [vp, vp],
+        "pk_ctx_destroy": [vp],
+        "pk_knot_from_pd": [vp, P(i32), i32, i32, i32, P(vp)],
+        "pk_knot_from_signed_graph": [vp, i32, i32, P(i32), i32, P(vp)],
+        "pk_knot_from_grid_walk": [vp, i32, u64, i32, i32, i32, P(vp)],
+        "pk_knot_info": [vp, P(i32), P(i32), P(i32), P(i32), P(i32)],
+        "pk_knot_edges": [vp, P(i32)],
+        "pk_knot_pd": [vp, P(i32)],
+        "pk_knot_destroy": [vp],
+        "pk_plan_create": [vp, vp, i32, P(pk_plan_opts), P(vp)],
+        "pk_plan_info": [vp, P(pk_plan_stats)],
+        "pk_plan_workspace_bytes": [vp, i32, P(u64)],
+        "pk_plan_steps": [vp, P(i64)],
+        "pk_plan_destroy": [vp],
+        "pk_eval": [vp, vp, i32, vp, u64, P(pk_scaled), P(pk_scaled)],
+        "pk_upload": [vp, vp, i32, vp, u64],
+        "pk_launch": [vp, vp, i32, vp, u64],
+        "pk_download": [vp, vp, i32, vp, P(pk_scaled), P(pk_scaled)],
+        "pk_plan_launches": [vp, i32, P(i64)],
+        "pk_jones_from_z": [vp, i32, P(pk_scaled), P(pk_scaled)],
+        "pk_plan_debug_blob": [vp, i32, vp, P(u64)],
+        "pk_profile": [vp, vp, i32, vp, u64, P(C.c_double)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = None if name.endswith("destroy") else C.c_int
+    L.pk_last_error.argtypes = [vp]
+    L.pk_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = lib().pk_last_error(ctx.h if ctx is not None else None)
+        raise PkError(status, msg.decode() if msg else "")
+
+
+@dataclass(frozen=True)
+class Scaled:
+    """value = (re + i im) * 2**exp2"""
+    re: float
+    im: float
+    exp2: int
+
+    @staticmethod
+    def of(s: pk_scaled) -> "Scaled":
+        return Scaled(s.re, s.im, s.exp2)
+
+    @property
+    def mantissa(self) -> complex:
+        return complex(self.re, self.im)
+
+    def to_complex(self) -> complex:
+        import math
+        try:
+            return complex(math.ldexp(self.re, self.exp2), math.ldexp(self.im, self.exp2))
+        except OverflowError:
+            return complex(float("inf"), float("inf"))
+
+
+class Context:
+    """A library context.  device=-1 gives a host-only context (knots and plans)."""
+
+    def __init__(self, device: int = -1, stream: int | None = None):
+        h = C.c_void_p()
+        st = lib().pk_ctx_create(device, C.c_void_p(stream or 0), C.byref(h))
+        if st != 0:
+            raise PkError(st, f"pk_ctx_create(device={device})")
+        self.h = h
+        self.device = device
+
+    def set_stream(self, stream: int):
+        _check(lib().pk_ctx_set_stream(self.h, C.c_void_p(stream)), self)
+
+    def close(self):
+        if self.h:
+            lib().pk_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Knot:
+    def __init__(self, h, ctx):
+        self.h = h
+        self.ctx = ctx
+
+    @staticmethod
+    def from_pd(ctx: Context, pd, outer=None) -> "Knot":
+        flat = [int(v) for X in pd for v in X]
+        arr = (C.c_int32 * max(1, len(flat)))(*flat)
+        oa, os_ = (outer if outer is not None else (-1, 0))
+        h = C.c_void_p()
+        _check(lib().pk_knot_from_pd(ctx.h, arr, len(pd), oa, os_, C.byref(h)), ctx)
+        return Knot(h, ctx)
+
+    @staticmethod
+    def from_signed_graph(ctx: Context, n_v, edges, writhe) -> "Knot":
+        flat = [int(v) for e in edges for v in e]
+        arr = (C.c_int32 * max(1, len(flat)))(*flat)
+        h = C.c_void_p()
+        _check(lib().pk_knot_from_signed_graph(ctx.h, n_v, len(edges), arr, writhe, C.byref(h)), ctx)
+        return Knot(h, ctx)
+
+    @staticmethod
+    def from_grid_walk(ctx: Context, L, seed, random_over_under=True, ncross_min=0,
+                       ncross_max=1 << 30) -> "Knot":
+        h = C.c_void_p()
+        _check(lib().pk_knot_from_grid_walk(ctx.h, L, seed, int(random_over_under), ncross_min,
+                                            ncross_max, C.byref(h)), ctx)
+        return Knot(h, ctx)
+
+    def info(self) -> dict:
+        v = [C.c_int32() for _ in range(5)]
+        _check(lib().pk_knot_info(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(("n_v", "n_c", "writhe", "tau", "components"), (x.value for x in v)))
+
+    def edges(self):
+        n = self.info()["n_c"]
+        arr = (C.c_int32 * max(1, 3 * n))()
+        _check(lib().pk_knot_edges(self.h, arr))
+        return [(arr[3 * e], arr[3 * e + 1], arr[3 * e + 2]) for e in range(n)]
+
+    def pd(self):
+        n = self.info()["n_c"]
+        arr = (C.c_int32 * max(1, 4 * n))()
+        _check(lib().pk_knot_pd(self.h, arr))
+        return [tuple(arr[4 * i:4 * i + 4]) for i in range(n)]
+
+    def jones_from_z(self, q: int, z: Scaled) -> Scaled:
+        zz = pk_scaled(z.re, z.im, z.exp2)
+        vv = pk_scaled()
+        _check(lib().pk_jones_from_z(self.h, q, C.byref(zz), C.byref(vv)))
+        return Scaled.of(vv)
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().pk_knot_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Plan:
+    def __init__(self, ctx: Context, knot: Knot, q: int, order: str = "auto",
+                 max_log2_elems: float = 0.0, max_log2_slices: float = 0.0):
+        o = pk_plan_opts(ORDERS[order], 0, max_log2_elems, max_log2_slices)
+        h = C.c_void_p()
+        _check(lib().pk_plan_create(ctx.h, knot.h, q, C.byref(o), C.byref(h)), ctx)
+        self.h = h
+        self.q = q
+        self.knot = knot
+        self.ctx = ctx
+
+    def stats(self) -> dict:
+        s = pk_plan_stats()
+        _check(lib().pk_plan_info(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def workspace_bytes(self, precision="c128") -> int:
+        b = C.c_uint64()
+        _check(lib().pk_plan_workspace_bytes(self.h, PRECISIONS[precision], C.byref(b)))
+        return b.value
+
+    def launches(self, precision="c128") -> int:
+        n = C.c_int64()
+        _check(lib().pk_plan_launches(self.h, PRECISIONS[precision], C.byref(n)))
+        return n.value
+
+    def steps(self):
+        n = self.stats()["n_steps"]
+        arr = (C.c_int64 * max(1, 8 * n))()
+        _check(lib().pk_plan_steps(self.h, arr))
+        keys = ("a", "b", "c", "R", "K", "N", "rank_c", "kernel")
+        return [dict(zip(keys, arr[8 * i:8 * i + 8])) for i in range(n)]
+
+    def debug_blob(self, which: int) -> bytes:
+        nb = C.c_uint64()
+        _check(lib().pk_plan_debug_blob(self.h, which, None, C.byref(nb)))
+        buf = (C.c_uint8 * max(1, nb.value))()
+        _check(lib().pk_plan_debug_blob(self.h, which, buf, C.byref(nb)))
+        return bytes(buf)[:nb.value]
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().pk_plan_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def _torch_stream(ctx: Context):
+    import torch
+    ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+
+
+def workspace(plan: Plan, precision="c128"):
+    """A device workspace for `plan` from the PyTorch allocator."""
+    import torch
+    return torch.empty(plan.workspace_bytes(precision), dtype=torch.uint8,
+                       device=f"cuda:{plan.ctx.device}")
+
+
+def evaluate(plan: Plan, precision: str = "c128", ws=None):
+    """Z(q) and V_K(t(q)) of the plan's knot on the GPU; returns (Z, V) as Scaled
+    (V is None when the diagram is not a knot)."""
+    ctx = plan.ctx
+    if ctx.device < 0:
+        raise PkError(7, "evaluate needs a GPU context")
+    _torch_stream(ctx)
+    if ws is None:
+        ws = workspace(plan, precision)
+    z, v = pk_scaled(), pk_scaled()
+    st = lib().pk_eval(ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
+                       ws.numel() * ws.element_size(), C.byref(z), C.byref(v))
+    if st == 2:
+        return Scaled.of(z), None
+    _check(st, ctx)
+    return Scaled.of(z), Scaled.of(v)
+
+
+def upload(plan: Plan, precision: str, ws):
+    _check(lib().pk_upload(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
+                           ws.numel()), plan.ctx)
+
+
+def launch(plan: Plan, precision: str, ws):
+    _check(lib().pk_launch(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
+                           ws.numel()), plan.ctx)
+
+
+def download(plan: Plan, precision: str, ws):
+    z, v = pk_scaled(), pk_scaled()
+    st = lib().pk_download(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
+                           C.byref(z), C.byref(v))
+    if st == 2:
+        return Scaled.of(z), None
+    _check(st, plan.ctx)
+    return Scaled.of(z), Scaled.of(v)
+
+
+def profile(plan: Plan, precision: str, ws):
+    """Per kernel class (build, rows, splitk, results): ms, launches, complex MACs, bytes
+    of one pass of the plan's kernels, timed with CUDA events on the context's stream."""
+    out = (C.c_double * 16)()
+    _check(lib().pk_profile(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
+                            ws.numel(), out), plan.ctx)
+    names = ("build", "rows", "splitk", "results")
+    return {n: {"ms": out[i], "launches": out[4 + i], "cmacs": out[8 + i], "bytes": out[12 + i]}
+            for i, n in enumerate(names)}

@@ -1,0 +1,422 @@
+// C ABI (include/pk.h): handles, argument checks, workspace handling and the host-side
+// normalisation V = A(q) Z (Eq. JonesPotts).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pk_internal.h"
+
+namespace pk {
+template <typename R>
+cudaError_t launch_plan(const Plan& p, void* ws, cudaStream_t stream);
+template <typename R>
+cudaError_t profile_plan(const Plan& p, void* ws, cudaStream_t stream, double* out);
+}
+
+struct pk_ctx {
+  int32_t device = -1;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  void* own_ws = nullptr;
+  uint64_t own_ws_bytes = 0;
+  pk::SliceResult* pinned_result = nullptr;
+};
+struct pk_knot {
+  pk::Knot k;
+};
+struct pk_plan {
+  pk::Plan p;
+  uint8_t* pinned_program = nullptr;
+};
+
+namespace {
+
+pk_status fail(pk_ctx* c, pk_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+pk_status cuda_fail(pk_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, PK_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+int elem_bytes(int32_t precision) { return precision == PK_C128 ? 16 : 8; }
+bool valid_precision(int32_t p) { return p == PK_C128 || p == PK_C64 || p == PK_SPLIT_TF32; }
+
+pk_scaled to_abi(const pk::Scaled& s) {
+  pk_scaled r;
+  r.re = s.re;
+  r.im = s.im;
+  r.exp2 = s.e;
+  return r;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+pk_status check_ws(pk_ctx* ctx, const pk_plan* p, int32_t precision, void*& ws, uint64_t& bytes) {
+  uint64_t need = p->p.ws_bytes(elem_bytes(precision));
+  if (ws == nullptr) {
+    if (ctx->own_ws_bytes < need) {
+      if (ctx->own_ws) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->own_ws);
+        ctx->own_ws = nullptr;
+        ctx->own_ws_bytes = 0;
+      }
+      cudaError_t e = cudaMalloc(&ctx->own_ws, need);
+      if (e != cudaSuccess) return fail(ctx, PK_ENOMEM, "workspace cudaMalloc failed");
+      ctx->own_ws_bytes = need;
+    }
+    ws = ctx->own_ws;
+    bytes = ctx->own_ws_bytes;
+  }
+  if (bytes < need) return fail(ctx, PK_ENOMEM, "workspace smaller than pk_plan_workspace_bytes");
+  if (((uintptr_t)ws & 255u) != 0) return fail(ctx, PK_EINVAL, "workspace must be 256-byte aligned");
+  return PK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pk_status pk_ctx_create(int32_t device, void* stream, pk_ctx** out) {
+  if (!out) return PK_EINVAL;
+  *out = nullptr;
+  pk_ctx* c = new (std::nothrow) pk_ctx();
+  if (!c) return PK_ENOMEM;
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  if (device >= 0) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
+      delete c;
+      return PK_ENODEVICE;
+    }
+    DeviceGuard g(device);
+    if (cudaMallocHost((void**)&c->pinned_result, sizeof(pk::SliceResult)) != cudaSuccess) {
+      delete c;
+      return PK_ECUDA;
+    }
+  }
+  *out = c;
+  return PK_OK;
+}
+
+pk_status pk_ctx_set_stream(pk_ctx* ctx, void* stream) {
+  if (!ctx) return PK_EINVAL;
+  ctx->stream = (cudaStream_t)stream;
+  return PK_OK;
+}
+
+const char* pk_last_error(const pk_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void pk_ctx_destroy(pk_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->device >= 0) {
+    DeviceGuard g(ctx->device);
+    if (ctx->own_ws) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->own_ws);
+    }
+    if (ctx->pinned_result) cudaFreeHost(ctx->pinned_result);
+  }
+  delete ctx;
+}
+
+pk_status pk_knot_from_pd(pk_ctx* ctx, const int32_t* pd, int32_t n, int32_t outer_arc,
+                          int32_t outer_side, pk_knot** out) {
+  if (!out) return fail(ctx, PK_EINVAL, "null output");
+  *out = nullptr;
+  pk_knot* k = new (std::nothrow) pk_knot();
+  if (!k) return fail(ctx, PK_ENOMEM, "out of host memory");
+  std::string err;
+  if (!pk::knot_from_pd(pd, n, outer_arc, outer_side, k->k, err)) {
+    delete k;
+    return fail(ctx, PK_EINVAL, err);
+  }
+  *out = k;
+  return PK_OK;
+}
+
+pk_status pk_knot_from_signed_graph(pk_ctx* ctx, int32_t n_v, int32_t n_e, const int32_t* uve,
+                                    int32_t writhe, pk_knot** out) {
+  if (!out) return fail(ctx, PK_EINVAL, "null output");
+  *out = nullptr;
+  pk_knot* k = new (std::nothrow) pk_knot();
+  if (!k) return fail(ctx, PK_ENOMEM, "out of host memory");
+  std::string err;
+  if (!pk::knot_from_graph(n_v, n_e, uve, writhe, k->k, err)) {
+    delete k;
+    return fail(ctx, PK_EINVAL, err);
+  }
+  *out = k;
+  return PK_OK;
+}
+
+pk_status pk_knot_from_grid_walk(pk_ctx* ctx, int32_t L, uint64_t seed, int32_t random_over_under,
+                                 int32_t ncross_min, int32_t ncross_max, pk_knot** out) {
+  if (!out) return fail(ctx, PK_EINVAL, "null output");
+  *out = nullptr;
+  std::vector<std::array<int32_t, 4>> pd;
+  int32_t oa, os;
+  std::string err;
+  if (!pk::grid_walk_pd(L, seed, random_over_under != 0, ncross_min, ncross_max, pd, oa, os, err))
+    return fail(ctx, PK_EINVAL, err);
+  std::vector<int32_t> flat(4 * pd.size());
+  for (size_t i = 0; i < pd.size(); ++i)
+    for (int j = 0; j < 4; ++j) flat[4 * i + j] = pd[i][j];
+  return pk_knot_from_pd(ctx, flat.data(), (int32_t)pd.size(), oa, os, out);
+}
+
+pk_status pk_knot_info(const pk_knot* k, int32_t* n_v, int32_t* n_c, int32_t* writhe,
+                       int32_t* tau, int32_t* components) {
+  if (!k) return PK_EINVAL;
+  if (n_v) *n_v = k->k.n_v;
+  if (n_c) *n_c = k->k.n_c;
+  if (writhe) *writhe = k->k.writhe;
+  if (tau) *tau = k->k.tau;
+  if (components) *components = k->k.components;
+  return PK_OK;
+}
+
+pk_status pk_knot_edges(const pk_knot* k, int32_t* uve) {
+  if (!k || (!uve && k->k.n_c > 0)) return PK_EINVAL;
+  for (size_t e = 0; e < k->k.edges.size(); ++e)
+    for (int j = 0; j < 3; ++j) uve[3 * e + j] = k->k.edges[e][j];
+  return PK_OK;
+}
+
+pk_status pk_knot_pd(const pk_knot* k, int32_t* pd) {
+  if (!k || !k->k.has_pd || (!pd && k->k.n_c > 0)) return PK_EINVAL;
+  for (size_t i = 0; i < k->k.pd.size(); ++i)
+    for (int j = 0; j < 4; ++j) pd[4 * i + j] = k->k.pd[i][j];
+  return PK_OK;
+}
+
+void pk_knot_destroy(pk_knot* k) { delete k; }
+
+pk_status pk_plan_create(pk_ctx* ctx, const pk_knot* k, int32_t q, const pk_plan_opts* opts,
+                         pk_plan** out) {
+  if (!out || !k) return fail(ctx, PK_EINVAL, "null argument");
+  *out = nullptr;
+  if (q < 1) return fail(ctx, PK_EINVAL, "q must be >= 1");
+  pk_plan_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  pk_plan* p = new (std::nothrow) pk_plan();
+  if (!p) return fail(ctx, PK_ENOMEM, "out of host memory");
+  std::string err;
+  if (!pk::make_plan(k->k, q, o, p->p, err)) {
+    delete p;
+    if (err.find("slices") != std::string::npos || err.find("runs") != std::string::npos)
+      return fail(ctx, PK_ETOOWIDE, err);
+    return fail(ctx, PK_EINVAL, err);
+  }
+  *out = p;
+  return PK_OK;
+}
+
+pk_status pk_plan_info(const pk_plan* p, pk_plan_stats* out) {
+  if (!p || !out) return PK_EINVAL;
+  const pk::Plan& P = p->p;
+  out->log2_max_elems = P.log2_max_elems;
+  out->cmacs = P.cmacs;
+  out->bytes_c64 = P.bytes_c64;
+  out->n_slices = P.n_slices;
+  out->n_steps = (int32_t)P.steps.size();
+  out->max_rank = P.max_rank;
+  out->order_used = P.order_used;
+  out->n_tensors = P.n_init;
+  out->workspace_c128 = P.ws_bytes(16);
+  out->workspace_c64 = P.ws_bytes(8);
+  return PK_OK;
+}
+
+pk_status pk_plan_workspace_bytes(const pk_plan* p, int32_t precision, uint64_t* bytes) {
+  if (!p || !bytes || !valid_precision(precision)) return PK_EINVAL;
+  *bytes = p->p.ws_bytes(elem_bytes(precision));
+  return PK_OK;
+}
+
+pk_status pk_plan_steps(const pk_plan* p, int64_t* rec) {
+  if (!p || (!rec && !p->p.steps.empty())) return PK_EINVAL;
+  for (size_t i = 0; i < p->p.steps.size(); ++i) {
+    const pk::Step& s = p->p.steps[i];
+    int64_t* r = rec + 8 * i;
+    r[0] = s.a;
+    r[1] = s.b;
+    r[2] = s.c;
+    r[3] = s.R;
+    r[4] = s.K;
+    r[5] = s.N;
+    r[6] = s.rank_c;
+    r[7] = s.kernel;
+  }
+  return PK_OK;
+}
+
+pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_t* bytes) {
+  if (!p || !bytes) return PK_EINVAL;
+  const pk::Plan& P = p->p;
+  std::vector<uint8_t> buf;
+  if (which == 0) {
+    buf = P.program;
+  } else if (which == 1) {
+    buf.resize(sizeof(pk::Step) * P.steps.size());
+    if (!P.steps.empty()) std::memcpy(buf.data(), P.steps.data(), buf.size());
+  } else if (which == 2) {
+    std::vector<int64_t> v;
+    for (const auto& t : P.tensors) {
+      v.push_back(t.offset);
+      v.push_back(t.elems);
+    }
+    buf.resize(8 * v.size());
+    if (!v.empty()) std::memcpy(buf.data(), v.data(), buf.size());
+  } else if (which == 3) {
+    int64_t v[10] = {P.q, P.n_init, (int64_t)P.steps.size(), P.n_slices, (int64_t)P.sliced.size(),
+                     P.final_tensor, (int64_t)P.off_recipe, (int64_t)P.off_slots,
+                     (int64_t)P.slots.size(), (int64_t)sizeof(pk::Step)};
+    buf.resize(sizeof(v));
+    std::memcpy(buf.data(), v, sizeof(v));
+  } else if (which == 4) {
+    double v[3] = {P.factor.re, P.factor.im, (double)P.factor.e};
+    buf.resize(sizeof(v));
+    std::memcpy(buf.data(), v, sizeof(v));
+  } else {
+    return PK_EINVAL;
+  }
+  if (dst) {
+    if (*bytes < buf.size()) return PK_ENOMEM;
+    if (!buf.empty()) std::memcpy(dst, buf.data(), buf.size());
+  }
+  *bytes = buf.size();
+  return PK_OK;
+}
+
+pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launches) {
+  if (!p || !launches || !valid_precision(precision)) return PK_EINVAL;
+  const pk::Plan& P = p->p;
+  *launches = P.n_slices * ((P.n_init > 0 ? 1 : 0) + (int64_t)P.steps.size() + 1) + 1;
+  return PK_OK;
+}
+
+void pk_plan_destroy(pk_plan* p) {
+  if (!p) return;
+  if (p->pinned_program) cudaFreeHost(p->pinned_program);
+  delete p;
+}
+
+pk_status pk_upload(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                    uint64_t workspace_bytes) {
+  if (!ctx || !p || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  pk_status s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
+  if (s != PK_OK) return s;
+  const pk::Plan& P = p->p;
+  if (P.program.empty()) return PK_OK;
+  pk_plan* mp = const_cast<pk_plan*>(p);
+  if (!mp->pinned_program) {
+    if (cudaMallocHost((void**)&mp->pinned_program, P.program.size()) != cudaSuccess)
+      return fail(ctx, PK_ENOMEM, "pinned host allocation failed");
+    std::memcpy(mp->pinned_program, P.program.data(), P.program.size());
+  }
+  cudaError_t e = cudaMemcpyAsync(d_workspace, mp->pinned_program, P.program.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+  return PK_OK;
+}
+
+pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                    uint64_t workspace_bytes) {
+  if (!ctx || !p || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  pk_status s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
+  if (s != PK_OK) return s;
+  cudaError_t e = precision == PK_C128 ? pk::launch_plan<double>(p->p, d_workspace, ctx->stream)
+                                       : pk::launch_plan<float>(p->p, d_workspace, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
+  return PK_OK;
+}
+
+pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                     uint64_t workspace_bytes, double* out) {
+  if (!ctx || !p || !out || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  pk_status s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
+  if (s != PK_OK) return s;
+  cudaError_t e = precision == PK_C128
+                      ? pk::profile_plan<double>(p->p, d_workspace, ctx->stream, out)
+                      : pk::profile_plan<float>(p->p, d_workspace, ctx->stream, out);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "profile");
+  return PK_OK;
+}
+
+pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_scaled* V) {
+  if (!k || !Z || !V || q < 1) return PK_EINVAL;
+  if (k->k.components != 1) return PK_ENOTKNOT;
+  int64_t num = 3LL * k->k.writhe + k->k.tau + 2LL * k->k.n_v + 2;
+  if (num % 4 != 0) return PK_EINVAL;
+  pk::Scaled z;
+  z.re = Z->re;
+  z.im = Z->im;
+  z.e = Z->exp2;
+  *V = to_abi(pk::s_mul(pk::jones_prefactor(k->k, q), z));
+  return PK_OK;
+}
+
+pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const void* d_workspace,
+                      pk_scaled* Z, pk_scaled* V) {
+  if (!ctx || !p || !Z || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  const void* ws = d_workspace ? d_workspace : ctx->own_ws;
+  if (!ws) return fail(ctx, PK_EINVAL, "no workspace");
+  const pk::Plan& P = p->p;
+  const char* src = (const char*)ws + P.off_result + sizeof(pk::SliceResult) * P.n_slices;
+  cudaError_t e = cudaMemcpyAsync(ctx->pinned_result, src, sizeof(pk::SliceResult),
+                                  cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "download");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  pk::Scaled z;
+  z.re = ctx->pinned_result->re;
+  z.im = ctx->pinned_result->im;
+  z.e = ctx->pinned_result->exp;
+  z.norm();
+  z = pk::s_mul(z, P.factor);
+  *Z = to_abi(z);
+  if (V) {
+    pk_knot kk;
+    kk.k = P.knot;
+    pk_status s = pk_jones_from_z(&kk, P.q, Z, V);
+    if (s == PK_ENOTKNOT) return fail(ctx, s, "not a knot: V undefined");
+    if (s != PK_OK) return fail(ctx, s, "3w + tau + 2 n_v + 2 not divisible by 4");
+  }
+  return PK_OK;
+}
+
+pk_status pk_eval(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                  uint64_t workspace_bytes, pk_scaled* Z, pk_scaled* V) {
+  pk_status s = pk_upload(ctx, p, precision, d_workspace, workspace_bytes);
+  if (s != PK_OK) return s;
+  s = pk_launch(ctx, p, precision, d_workspace, workspace_bytes);
+  if (s != PK_OK) return s;
+  return pk_download(ctx, p, precision, d_workspace, Z, V);
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations shared by the host translation units of libpk.
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pk.h"
+
+namespace pk {
+
+// ------------------------------------------------------------------ knots (Sec. II)
+struct Knot {
+  int32_t n_v = 0;         // Tait vertices (black regions)
+  int32_t n_c = 0;         // crossings = Tait edges
+  int32_t writhe = 0;      // sum of twist signs
+  int32_t tau = 0;         // sum of Tait signs
+  int32_t components = 1;  // link components of the diagram
+  std::vector<std::array<int32_t, 3>> edges;  // (u, v, eps)
+  std::vector<std::array<int32_t, 4>> pd;     // empty for graph input
+  bool has_pd = false;
+};
+
+bool knot_from_pd(const int32_t* pd, int32_t n, int32_t outer_arc, int32_t outer_side, Knot& k,
+                  std::string& err);
+bool knot_from_graph(int32_t n_v, int32_t n_e, const int32_t* uve, int32_t writhe, Knot& k,
+                     std::string& err);
+bool grid_walk_pd(int32_t L, uint64_t seed, bool random_over_under, int32_t nmin, int32_t nmax,
+                  std::vector<std::array<int32_t, 4>>& pd, int32_t& outer_arc,
+                  int32_t& outer_side, std::string& err);
+
+// ------------------------------------------------------------------ scaled scalars
+struct Scaled {
+  double re = 0, im = 0;
+  int64_t e = 0;  // value = (re + i im) 2^e
+  void norm();
+};
+Scaled s_mul(const Scaled& a, const Scaled& b);
+Scaled s_pow(Scaled a, int64_t n);
+Scaled s_from(double re, double im);
+
+// ------------------------------------------------------------------ plans (Sec. III)
+constexpr int kMaxRuns = 12;  // merged stride runs per index class
+
+struct Run {
+  int64_t size;
+  int64_t sa, sb;  // element strides in operand A and operand B (0 when absent)
+};
+
+// One initial tensor: entry(i...) = sum_{s<q} prod_j f_j(s, x_j) where x_j is the value of
+// slot j's index (a digit of the element, or a sliced index's fixed value) and
+// f_j(s, x) = (s == x) ? diag_j : 1 for an absorbed clause matrix, [s == x] for a COPY leg.
+// kind CONST1 is the scalar 1.
+struct Recipe {
+  int32_t kind;            // 0 = vertex sum, 1 = const 1
+  int32_t rank;            // free dims
+  int32_t slot0, nslot;    // into Plan::slots
+  int64_t elems;           // q^rank
+  int64_t offset;          // element offset in the tensor arena
+  int32_t meta;            // meta slot (tensor id)
+};
+
+struct Slot {
+  int32_t dimpos;          // position (stride q^dimpos) in the tensor, or -1 if sliced
+  int32_t slice_ord;       // ordinal among sliced indices (valid when dimpos < 0)
+  int32_t absorbed;        // 1: clause matrix, 0: COPY leg
+  int32_t pad;
+  double dre, dim;         // clause diagonal when absorbed
+};
+
+enum KernelKind : int32_t { KROWS = 0, KSPLITK = 1 };
+
+struct Step {
+  int32_t a, b, c;         // tensor ids (a = larger operand; b = -1: constant 1)
+  int32_t kernel;          // KernelKind
+  int64_t off_a, off_b, off_c;  // element offsets in the tensor arena
+  int64_t R, K, N;         // rows (batch x free-of-a), contracted, free-of-b
+  int32_t nrow, nk, nn;    // runs per class
+  Run row[kMaxRuns];       // inner -> outer; C stride of a row digit is implicit (contiguous)
+  Run kr[kMaxRuns];
+  Run nr[kMaxRuns];        // sa unused, sb = stride in B; C offset = n * R
+  int32_t rank_c;
+  int32_t chunks;          // split-K: K chunks
+};
+
+// Per-tensor device bookkeeping: stored value x means x * 2^exp; maxbits is the bit
+// pattern of max(|re|, |im|) over the stored tensor (IEEE order = integer order for
+// non-negative values, so atomicMax on the bits is a max on the values).
+struct Meta {
+  unsigned long long maxbits;
+  long long exp;
+};
+struct SliceResult {
+  double re, im;
+  long long exp;
+  long long pad;
+};
+
+struct TensorInfo {
+  std::vector<int32_t> dims;  // index ids, outermost first (row-major)
+  int64_t elems = 1;
+  int64_t offset = 0;         // element offset in arena
+  int32_t born = -1, dies = -1;
+};
+
+struct Plan {
+  int32_t q = 0;
+  int32_t order_used = 0;
+  Knot knot;
+  // network
+  int32_t n_idx = 0;
+  std::vector<TensorInfo> tensors;  // initial tensors first, then one per step
+  int32_t n_init = 0;
+  std::vector<Recipe> recipes;
+  std::vector<Slot> slots;
+  std::vector<Step> steps;
+  std::vector<int32_t> sliced;       // sliced index ids
+  int64_t n_slices = 1;
+  Scaled factor;                     // constant factors (loops), applied on the host
+  int32_t final_tensor = -1;
+  // stats
+  int32_t max_rank = 0;
+  double log2_max_elems = 0;
+  double cmacs = 0, bytes_c64 = 0;
+  int64_t arena_elems = 0;
+  int64_t splitk_partials = 0;      // complex scratch entries for split-K steps
+  // device program layout (byte offsets inside the workspace)
+  uint64_t off_recipe = 0, off_slots = 0, off_meta = 0, off_result = 0, off_scratch = 0,
+           off_counter = 0, off_arena = 0;
+  uint64_t ws_bytes(int elem_bytes) const;
+  std::vector<uint8_t> program;      // recipe + slots blob copied by pk_upload
+};
+
+bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std::string& err);
+void clause_diag(int32_t q, int32_t mult, int32_t signsum, double& re, double& im);
+Scaled jones_prefactor(const Knot& k, int32_t q);  // A(q) in its integer-exponent form
+
+}  // namespace pk

@@ -1,0 +1,738 @@
+// Contraction planning (Sec. III): the network G_T, a pairwise contraction order,
+// index slicing, per-step GEMM descriptors and the device arena layout.
+//
+// Two equivalent forms of G_T are built from the signed Tait graph:
+//  * edge network  -- one tensor per Tait vertex: its COPY tensor with the clause
+//    matrices of (merged) incident edges absorbed at the lower-numbered endpoint;
+//    one q-dimensional index per edge.  Contracting two tensors is contracting the
+//    edge(s) between two vertices of a graph minor H; a tensor of rank d has q^d
+//    entries, so the cost is O(q^Delta_H) as in Sec. III.B.
+//  * spin network  -- one tensor per (merged) edge, T[s_u, s_v]; the COPY tensor of a
+//    vertex is kept implicit as a spin index shared by every tensor that touches the
+//    vertex (a hyperindex).  Same Z, usually far smaller intermediates.
+// Parallel edges merge into one clause matrix by the entrywise product (both factors
+// depend on the same two spins); a pair of opposite signs gives the all-ones matrix,
+// which factorises and is dropped.  A loop is the constant factor -t^-eps.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <numeric>
+#include <set>
+
+#include "pk_internal.h"
+
+namespace pk {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ scaled scalars
+void Scaled::norm() {
+  double m = std::max(std::fabs(re), std::fabs(im));
+  if (m == 0.0 || !std::isfinite(m)) {
+    if (m == 0.0) e = 0;
+    return;
+  }
+  int k;
+  std::frexp(m, &k);
+  re = std::ldexp(re, -k);
+  im = std::ldexp(im, -k);
+  e += k;
+}
+Scaled s_from(double re, double im) {
+  Scaled s;
+  s.re = re;
+  s.im = im;
+  s.e = 0;
+  s.norm();
+  return s;
+}
+Scaled s_mul(const Scaled& a, const Scaled& b) {
+  Scaled r;
+  r.re = a.re * b.re - a.im * b.im;
+  r.im = a.re * b.im + a.im * b.re;
+  r.e = a.e + b.e;
+  r.norm();
+  return r;
+}
+Scaled s_pow(Scaled a, int64_t n) {
+  if (n < 0) {  // 1/a
+    double d = a.re * a.re + a.im * a.im;
+    Scaled inv;
+    inv.re = a.re / d;
+    inv.im = -a.im / d;
+    inv.e = -a.e;
+    inv.norm();
+    a = inv;
+    n = -n;
+  }
+  Scaled r = s_from(1, 0);
+  while (n) {
+    if (n & 1) r = s_mul(r, a);
+    a = s_mul(a, a);
+    n >>= 1;
+  }
+  return r;
+}
+
+// t(q) of Eq. potts2jones in a form that is exact at q = 2 and q = 4.
+static cd t_of_q(int32_t q) {
+  double qd = q;
+  if (q < 4) return cd((qd - 2) / 2, std::sqrt(qd * (4 - qd)) / 2);
+  return cd(((qd - 2) + std::sqrt(qd * (qd - 4))) / 2, 0);
+}
+static cd c_pow(cd x, int64_t n) {
+  if (n < 0) {
+    x = 1.0 / x;
+    n = -n;
+  }
+  cd r(1, 0);
+  while (n) {
+    if (n & 1) r *= x;
+    x *= x;
+    n >>= 1;
+  }
+  return r;
+}
+
+// Diagonal of the merged clause matrix of `mult` parallel edges whose Tait signs sum
+// to `signsum`: prod (-t^-eps) = (-1)^mult t^-signsum (Eq. clause).
+void clause_diag(int32_t q, int32_t mult, int32_t signsum, double& re, double& im) {
+  cd v = c_pow(t_of_q(q), -signsum);
+  if (mult & 1) v = -v;
+  re = v.real();
+  im = v.imag();
+}
+
+// A(q) of Eq. JonesPotts.  With s the principal fourth root of t, every fractional
+// power in A is a power of s and A = (-1)^(w+n_v+1) t^k (t+1)^-(n_v+1) with
+// k = (3w + tau + 2 n_v + 2)/4, an integer for knots.
+Scaled jones_prefactor(const Knot& k, int32_t q) {
+  int64_t num = 3LL * k.writhe + k.tau + 2LL * k.n_v + 2;
+  cd t = t_of_q(q);
+  Scaled tt = s_from(t.real(), t.imag());
+  Scaled t1 = s_from(t.real() + 1, t.imag());
+  Scaled r = s_mul(s_pow(tt, num / 4), s_pow(t1, -(int64_t)(k.n_v + 1)));
+  if ((k.writhe + k.n_v + 1) & 1) {
+    r.re = -r.re;
+    r.im = -r.im;
+  }
+  return r;
+}
+
+// ------------------------------------------------------------------ network
+namespace {
+
+struct SlotSpec {
+  int32_t index;     // index id
+  int32_t absorbed;  // 1 = clause matrix, 0 = COPY leg
+  double dre, dim;
+};
+struct NetTensor {
+  std::vector<int32_t> dims;  // index ids (initial layout: sorted ascending, outermost first)
+  std::vector<SlotSpec> slots;
+  int32_t kind = 0;           // 0 vertex sum, 1 const 1
+};
+struct Network {
+  int32_t n_idx = 0;
+  std::vector<NetTensor> t;
+  Scaled factor = s_from(1, 0);
+};
+
+struct Merged {
+  int32_t u, v, mult, signsum;
+};
+
+void merge_edges(const Knot& k, int32_t q, std::vector<Merged>& out, Scaled& factor) {
+  std::map<std::pair<int32_t, int32_t>, std::pair<int32_t, int32_t>> m;
+  for (const auto& e : k.edges) {
+    if (e[0] == e[1]) {  // loop: constant factor T[s,s] = -t^-eps
+      double re, im;
+      clause_diag(q, 1, e[2], re, im);
+      factor = s_mul(factor, s_from(re, im));
+      continue;
+    }
+    auto key = std::make_pair(std::min(e[0], e[1]), std::max(e[0], e[1]));
+    auto& mv = m[key];
+    mv.first += 1;
+    mv.second += e[2];
+  }
+  out.clear();
+  for (const auto& kv : m) {
+    int32_t mult = kv.second.first, ss = kv.second.second;
+    if (mult % 2 == 0 && ss == 0) continue;  // all-ones matrix: factorises, dropped
+    out.push_back({kv.first.first, kv.first.second, mult, ss});
+  }
+}
+
+void spin_network(const Knot& k, int32_t q, Network& net) {
+  std::vector<Merged> me;
+  merge_edges(k, q, me, net.factor);
+  net.n_idx = k.n_v;
+  std::vector<char> covered(k.n_v, 0);
+  for (const auto& e : me) {
+    NetTensor t;
+    t.dims = {e.u, e.v};
+    double re, im;
+    clause_diag(q, e.mult, e.signsum, re, im);
+    t.slots = {{e.u, 0, 0, 0}, {e.v, 1, re, im}};  // T[a,b] = sum_s [s=a] M(s,b)
+    covered[e.u] = covered[e.v] = 1;
+    net.t.push_back(t);
+  }
+  for (int32_t v = 0; v < k.n_v; ++v)
+    if (!covered[v]) net.t.push_back(NetTensor());  // isolated vertex: sum_s 1 = q
+}
+
+void edge_network(const Knot& k, int32_t q, Network& net) {
+  std::vector<Merged> me;
+  merge_edges(k, q, me, net.factor);
+  net.n_idx = (int32_t)me.size();
+  std::vector<NetTensor> vt(k.n_v);
+  for (int32_t i = 0; i < (int32_t)me.size(); ++i) {
+    const auto& e = me[i];
+    double re, im;
+    clause_diag(q, e.mult, e.signsum, re, im);
+    vt[e.u].dims.push_back(i);
+    vt[e.u].slots.push_back({i, 1, re, im});
+    vt[e.v].dims.push_back(i);
+    vt[e.v].slots.push_back({i, 0, 0, 0});
+  }
+  net.t = std::move(vt);
+}
+
+// ------------------------------------------------------------------ orders
+struct Seq {
+  std::vector<std::pair<int32_t, int32_t>> pairs;  // operands of each step (tensor ids)
+  std::vector<std::vector<int32_t>> sets;          // index set of every tensor (sorted)
+  double cost_log = 0;                             // log2 of sum of R*K*N (unsliced)
+  int32_t max_rank = 0;
+};
+
+// Result index set of contracting a and b: an index survives iff some other live
+// tensor still carries it.
+void result_set(const std::vector<int32_t>& a, const std::vector<int32_t>& b,
+                const std::vector<int32_t>& cnt, std::vector<int32_t>& out) {
+  out.clear();
+  size_t i = 0, j = 0;
+  while (i < a.size() || j < b.size()) {
+    int32_t x;
+    int c;
+    if (j >= b.size() || (i < a.size() && a[i] < b[j])) {
+      x = a[i++];
+      c = 1;
+    } else if (i >= a.size() || b[j] < a[i]) {
+      x = b[j++];
+      c = 1;
+    } else {
+      x = a[i];
+      ++i;
+      ++j;
+      c = 2;
+    }
+    if (cnt[x] > c) out.push_back(x);
+  }
+}
+
+size_t union_size(const std::vector<int32_t>& a, const std::vector<int32_t>& b) {
+  size_t i = 0, j = 0, n = 0;
+  while (i < a.size() || j < b.size()) {
+    if (j >= b.size() || (i < a.size() && a[i] < b[j]))
+      ++i;
+    else if (i >= a.size() || b[j] < a[i])
+      ++j;
+    else {
+      ++i;
+      ++j;
+    }
+    ++n;
+  }
+  return n;
+}
+
+// Pairwise greedy (Sec. III "greedy"): always contract the pair of tensors sharing an
+// index whose result has the fewest indices; ties -> fewer indices touched, then ids.
+// `restrict_var` >= 0 limits candidates to tensors holding that index (used by the
+// elimination order).
+struct Greedy {
+  int32_t n_idx;
+  std::vector<std::vector<int32_t>> sets;
+  std::vector<char> live;
+  std::vector<int32_t> cnt;
+  std::vector<std::vector<int32_t>> occ;  // index -> tensors (may hold dead ids)
+  Seq seq;
+
+  void init(const Network& net) {
+    n_idx = net.n_idx;
+    cnt.assign(n_idx, 0);
+    occ.assign(n_idx, {});
+    for (const auto& t : net.t) {
+      std::vector<int32_t> s = t.dims;
+      std::sort(s.begin(), s.end());
+      int32_t id = (int32_t)sets.size();
+      for (int32_t x : s) {
+        cnt[x]++;
+        occ[x].push_back(id);
+      }
+      sets.push_back(s);
+      live.push_back(1);
+    }
+    seq.sets = sets;
+    for (const auto& s : sets) seq.max_rank = std::max<int32_t>(seq.max_rank, (int32_t)s.size());
+  }
+  // b = -1 contracts `a` with the constant 1 (sums out indices only `a` still holds)
+  int32_t contract(int32_t a, int32_t b) {
+    static const std::vector<int32_t> none;
+    const std::vector<int32_t>& sb = b >= 0 ? sets[b] : none;
+    std::vector<int32_t> r;
+    result_set(sets[a], sb, cnt, r);
+    for (int32_t x : sets[a]) cnt[x]--;
+    for (int32_t x : sb) cnt[x]--;
+    live[a] = 0;
+    if (b >= 0) live[b] = 0;
+    int32_t id = (int32_t)sets.size();
+    for (int32_t x : r) {
+      cnt[x]++;
+      occ[x].push_back(id);
+    }
+    sets.push_back(r);
+    live.push_back(1);
+    seq.pairs.push_back({a, b});
+    seq.sets.push_back(r);
+    seq.max_rank = std::max<int32_t>(seq.max_rank, (int32_t)r.size());
+    return id;
+  }
+  bool best_pair(int32_t restrict_var, int32_t& ba, int32_t& bb) {
+    bool found = false;
+    std::array<int64_t, 4> best{};
+    std::vector<int32_t> r;
+    auto consider = [&](int32_t a, int32_t b) {
+      if (a == b || !live[a] || !live[b]) return;
+      if (a > b) std::swap(a, b);
+      result_set(sets[a], sets[b], cnt, r);
+      std::array<int64_t, 4> key{(int64_t)r.size(),
+                                 (int64_t)(sets[a].size() + sets[b].size()), a, b};
+      if (!found || key < best) {
+        best = key;
+        found = true;
+      }
+    };
+    if (restrict_var >= 0) {
+      for (int32_t a : occ[restrict_var])
+        for (int32_t b : occ[restrict_var]) consider(a, b);
+    } else {
+      for (int32_t a = 0; a < (int32_t)sets.size(); ++a) {
+        if (!live[a]) continue;
+        for (int32_t x : sets[a])
+          for (int32_t b : occ[x])
+            if (b > a) consider(a, b);
+      }
+    }
+    if (found) {
+      ba = (int32_t)best[2];
+      bb = (int32_t)best[3];
+    }
+    return found;
+  }
+  // finish: combine disconnected pieces (outer products), smallest first; a lone
+  // tensor that still has indices is summed out against the constant 1.
+  void finish() {
+    for (;;) {
+      std::vector<int32_t> l;
+      for (int32_t i = 0; i < (int32_t)sets.size(); ++i)
+        if (live[i]) l.push_back(i);
+      if (l.empty()) return;
+      if (l.size() == 1) {
+        if (!sets[l[0]].empty()) contract(l[0], -1);
+        return;
+      }
+      std::sort(l.begin(), l.end(), [&](int32_t x, int32_t y) {
+        if (sets[x].size() != sets[y].size()) return sets[x].size() < sets[y].size();
+        return x < y;
+      });
+      contract(l[0], l[1]);
+    }
+  }
+};
+
+// Min-degree spin elimination order (on the spin network only).
+std::vector<int32_t> min_degree_order(const Network& net) {
+  std::vector<std::set<int32_t>> nb(net.n_idx);
+  for (const auto& t : net.t)
+    for (int32_t a : t.dims)
+      for (int32_t b : t.dims)
+        if (a != b) nb[a].insert(b);
+  std::vector<char> done(net.n_idx, 0);
+  std::vector<int32_t> order;
+  for (int32_t it = 0; it < net.n_idx; ++it) {
+    int32_t best = -1;
+    size_t bd = 0;
+    for (int32_t v = 0; v < net.n_idx; ++v)
+      if (!done[v] && (best < 0 || nb[v].size() < bd)) {
+        best = v;
+        bd = nb[v].size();
+      }
+    done[best] = 1;
+    order.push_back(best);
+    std::vector<int32_t> N(nb[best].begin(), nb[best].end());
+    for (int32_t a : N) {
+      nb[a].erase(best);
+      for (int32_t b : N)
+        if (a != b) nb[a].insert(b);
+    }
+    nb[best].clear();
+  }
+  return order;
+}
+
+bool run_order(const Network& net, int32_t order, Greedy& g) {
+  g = Greedy();
+  g.init(net);
+  if (order == PK_ORDER_ELIM_SPIN) {
+    std::vector<int32_t> ord = min_degree_order(net);
+    for (int32_t v : ord) {
+      int32_t a, b;
+      while (g.cnt[v] >= 2 && g.best_pair(v, a, b)) g.contract(a, b);
+    }
+  }
+  int32_t a, b;
+  while (g.best_pair(-1, a, b)) g.contract(a, b);
+  g.finish();
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan assembly
+uint64_t Plan::ws_bytes(int elem_bytes) const {
+  return off_arena + (uint64_t)arena_elems * (uint64_t)elem_bytes;
+}
+
+static uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std::string& err) {
+  p = Plan();
+  if (q < 1 || q > 64) {
+    err = "q out of range";
+    return false;
+  }
+  p.q = q;
+  p.knot = k;
+  const double lq = std::log2((double)q);
+  double max_log2 = opts.max_log2_elems > 0 ? opts.max_log2_elems : 31.0;
+  if (max_log2 > 31.0) max_log2 = 31.0;  // 32-bit row indexing in the kernels
+  double max_log2_slices = opts.max_log2_slices > 0 ? opts.max_log2_slices : 40.0;
+  int32_t rmax = q == 1 ? 1 << 20 : (int32_t)std::floor(max_log2 / lq + 1e-9);
+
+  // candidate orders
+  std::vector<int32_t> cands;
+  if (opts.order == PK_ORDER_AUTO)
+    cands = {PK_ORDER_GREEDY_SPIN, PK_ORDER_ELIM_SPIN, PK_ORDER_GREEDY_EDGE};
+  else if (opts.order >= 1 && opts.order <= 3)
+    cands = {opts.order};
+  else if (opts.order == PK_ORDER_PARTITION)
+    cands = {PK_ORDER_ELIM_SPIN};
+  else {
+    err = "unknown order";
+    return false;
+  }
+  Network best_net;
+  Greedy best_g;
+  double best_cost = std::numeric_limits<double>::infinity();
+  int32_t best_order = -1;
+  for (int32_t o : cands) {
+    Network net;
+    if (o == PK_ORDER_GREEDY_EDGE)
+      edge_network(k, q, net);
+    else
+      spin_network(k, q, net);
+    Greedy g;
+    run_order(net, o, g);
+    // cost in complex MACs at this q
+    double c = 0;
+    for (size_t s = 0; s < g.seq.pairs.size(); ++s) {
+      const auto& s2 = g.seq.pairs[s].second >= 0 ? g.seq.sets[g.seq.pairs[s].second]
+                                                   : std::vector<int32_t>();
+      size_t u = union_size(g.seq.sets[g.seq.pairs[s].first], s2);
+      c += std::pow((double)q, (double)u);
+    }
+    if (c < best_cost) {
+      best_cost = c;
+      best_net = net;
+      best_g = g;
+      best_order = o;
+    }
+  }
+  p.order_used = best_order;
+  Network& net = best_net;
+  Greedy& g = best_g;
+  p.factor = net.factor;
+  p.n_idx = net.n_idx;
+  p.n_init = (int32_t)net.t.size();
+  const int32_t n_tens = (int32_t)g.seq.sets.size();
+  const int32_t n_steps = (int32_t)g.seq.pairs.size();
+  if (n_tens != p.n_init + n_steps) {
+    err = "internal: tensor count mismatch";
+    return false;
+  }
+
+  // ---- slicing: remove indices until every tensor has rank <= rmax
+  std::vector<std::vector<int32_t>> sets = g.seq.sets;
+  std::vector<char> sliced(net.n_idx, 0);
+  for (;;) {
+    int32_t worst = 0;
+    for (const auto& s : sets) worst = std::max<int32_t>(worst, (int32_t)s.size());
+    if (worst <= rmax) break;
+    std::vector<int64_t> hits(net.n_idx, 0);
+    std::vector<double> gain(net.n_idx, 0);
+    for (const auto& s : sets)
+      if ((int32_t)s.size() > rmax)
+        for (int32_t x : s) {
+          hits[x]++;
+          gain[x] += std::pow((double)q, (double)s.size() - rmax);
+        }
+    int32_t bx = -1;
+    for (int32_t x = 0; x < net.n_idx; ++x)
+      if (hits[x] > 0 && (bx < 0 || hits[x] > hits[bx] || (hits[x] == hits[bx] && gain[x] > gain[bx])))
+        bx = x;
+    if (bx < 0) {
+      err = "internal: slicing found no index";
+      return false;
+    }
+    sliced[bx] = 1;
+    p.sliced.push_back(bx);
+    for (auto& s : sets) s.erase(std::remove(s.begin(), s.end(), bx), s.end());
+    if ((double)p.sliced.size() * lq > max_log2_slices) {
+      err = "plan needs more slices than allowed";
+      return false;
+    }
+  }
+  p.n_slices = 1;
+  for (size_t i = 0; i < p.sliced.size(); ++i) p.n_slices *= q;
+  std::vector<int32_t> slice_ord(net.n_idx, -1);
+  for (size_t i = 0; i < p.sliced.size(); ++i) slice_ord[p.sliced[i]] = (int32_t)i;
+
+  // ---- tensors and layouts
+  p.tensors.resize(n_tens);
+  for (int32_t i = 0; i < p.n_init; ++i) {
+    TensorInfo& ti = p.tensors[i];
+    for (int32_t x : net.t[i].dims)
+      if (!sliced[x]) ti.dims.push_back(x);  // initial layout: network order
+  }
+  auto qpow = [&](int64_t e) {
+    int64_t r = 1;
+    for (int64_t i = 0; i < e; ++i) r *= q;
+    return r;
+  };
+  p.steps.resize(n_steps);
+  for (int32_t s = 0; s < n_steps; ++s) {
+    int32_t x = g.seq.pairs[s].first, y = g.seq.pairs[s].second;
+    int32_t cid = p.n_init + s;
+    const auto& cset = sets[cid];
+    // roles: a = operand with more elements
+    int32_t a = x, b = y;
+    if (b >= 0 && p.tensors[b].dims.size() > p.tensors[a].dims.size()) std::swap(a, b);
+    static const std::vector<int32_t> no_dims;
+    const auto& ad = p.tensors[a].dims;
+    const auto& bd = b >= 0 ? p.tensors[b].dims : no_dims;
+    auto pos_in = [](const std::vector<int32_t>& d, int32_t v) -> int32_t {
+      for (size_t i = 0; i < d.size(); ++i)
+        if (d[i] == v) return (int32_t)i;
+      return -1;
+    };
+    auto in_c = [&](int32_t v) { return std::binary_search(cset.begin(), cset.end(), v); };
+    Step st;
+    std::memset(&st, 0, sizeof(st));
+    st.a = a;
+    st.b = b;
+    st.c = cid;
+    const int32_t ra = (int32_t)ad.size(), rb = (int32_t)bd.size();
+    auto stride_a = [&](int32_t v) -> int64_t {
+      int32_t pp = pos_in(ad, v);
+      return pp < 0 ? 0 : qpow(ra - 1 - pp);
+    };
+    auto stride_b = [&](int32_t v) -> int64_t {
+      int32_t pp = pos_in(bd, v);
+      return pp < 0 ? 0 : qpow(rb - 1 - pp);
+    };
+    std::vector<Run> rows, ks, ns;
+    std::vector<int32_t> row_dims, n_dims;
+    auto push = [&](std::vector<Run>& v, int64_t sa, int64_t sb) {
+      if (!v.empty()) {
+        Run& l = v.back();
+        if (sa == l.sa * l.size && sb == l.sb * l.size) {
+          l.size *= q;
+          return;
+        }
+      }
+      v.push_back({(int64_t)q, sa, sb});
+    };
+    for (int32_t i = ra - 1; i >= 0; --i) {  // inner -> outer
+      int32_t v = ad[i];
+      if (in_c(v)) {
+        push(rows, stride_a(v), stride_b(v));
+        row_dims.push_back(v);
+      } else {
+        push(ks, stride_a(v), stride_b(v));
+      }
+    }
+    for (int32_t i = rb - 1; i >= 0; --i) {
+      int32_t v = bd[i];
+      if (pos_in(ad, v) >= 0) continue;
+      if (in_c(v)) {
+        push(ns, 0, stride_b(v));
+        n_dims.push_back(v);
+      } else {
+        push(ks, 0, stride_b(v));
+      }
+    }
+    if ((int)rows.size() > kMaxRuns || (int)ks.size() > kMaxRuns || (int)ns.size() > kMaxRuns) {
+      err = "step has too many stride runs";
+      return false;
+    }
+    st.R = st.K = st.N = 1;
+    st.nrow = (int32_t)rows.size();
+    st.nk = (int32_t)ks.size();
+    st.nn = (int32_t)ns.size();
+    for (int i = 0; i < st.nrow; ++i) {
+      st.row[i] = rows[i];
+      st.R *= rows[i].size;
+    }
+    for (int i = 0; i < st.nk; ++i) {
+      st.kr[i] = ks[i];
+      st.K *= ks[i].size;
+    }
+    for (int i = 0; i < st.nn; ++i) {
+      st.nr[i] = ns[i];
+      st.N *= ns[i].size;
+    }
+    // C layout (outermost first): N dims (B order), then row dims (A order)
+    std::vector<int32_t>& cd_ = p.tensors[cid].dims;
+    for (int32_t i = (int32_t)n_dims.size() - 1; i >= 0; --i) cd_.push_back(n_dims[i]);
+    for (int32_t i = (int32_t)row_dims.size() - 1; i >= 0; --i) cd_.push_back(row_dims[i]);
+    st.rank_c = (int32_t)cd_.size();
+    const int64_t outs = st.R * st.N;
+    st.kernel = (outs <= 4096 && st.K >= 4096) ? KSPLITK : KROWS;
+    st.chunks = st.kernel == KSPLITK ? (int32_t)std::min<int64_t>(64, (st.K + 2047) / 2048) : 0;
+    p.steps[s] = st;
+  }
+  p.final_tensor = n_tens - 1;
+
+  // ---- sizes, lifetimes, stats
+  p.max_rank = 0;
+  for (int32_t i = 0; i < n_tens; ++i) {
+    TensorInfo& ti = p.tensors[i];
+    ti.elems = qpow((int64_t)ti.dims.size());
+    p.max_rank = std::max<int32_t>(p.max_rank, (int32_t)ti.dims.size());
+    ti.born = i < p.n_init ? -1 : i - p.n_init;
+    ti.dies = ti.born;
+  }
+  p.tensors[p.final_tensor].dies = n_steps;
+  double cm = 0, by = 0;
+  int64_t partials = 0;
+  for (int32_t s = 0; s < n_steps; ++s) {
+    const Step& st = p.steps[s];
+    p.tensors[st.a].dies = std::max(p.tensors[st.a].dies, s);
+    if (st.b >= 0) p.tensors[st.b].dies = std::max(p.tensors[st.b].dies, s);
+    cm += (double)st.R * (double)st.K * (double)st.N;
+    by += 8.0 * (double)(p.tensors[st.a].elems + (st.b >= 0 ? p.tensors[st.b].elems : 0) +
+                         p.tensors[st.c].elems);
+    if (st.kernel == KSPLITK) partials = std::max<int64_t>(partials, st.R * st.N * st.chunks);
+  }
+  p.cmacs = cm * (double)p.n_slices;
+  p.bytes_c64 = by * (double)p.n_slices;
+  p.log2_max_elems = p.max_rank * lq;
+  p.splitk_partials = partials;
+
+  // ---- arena: first fit by decreasing size over lifetime intervals
+  std::vector<int32_t> ord(n_tens);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+    if (p.tensors[x].elems != p.tensors[y].elems) return p.tensors[x].elems > p.tensors[y].elems;
+    return x < y;
+  });
+  struct Placed {
+    int64_t off, len;
+    int32_t born, dies;
+  };
+  std::vector<Placed> placed;
+  int64_t top = 0;
+  for (int32_t id : ord) {
+    TensorInfo& ti = p.tensors[id];
+    int64_t len = (ti.elems + 63) / 64 * 64;
+    std::vector<std::pair<int64_t, int64_t>> busy;
+    for (const auto& pl : placed)
+      if (!(pl.dies < ti.born || ti.dies < pl.born)) busy.push_back({pl.off, pl.off + pl.len});
+    std::sort(busy.begin(), busy.end());
+    int64_t off = 0;
+    for (const auto& iv : busy) {
+      if (off + len <= iv.first) break;
+      off = std::max(off, iv.second);
+    }
+    ti.offset = off;
+    placed.push_back({off, len, ti.born, ti.dies});
+    top = std::max(top, off + len);
+  }
+  p.arena_elems = top;
+  for (auto& st : p.steps) {
+    st.off_a = p.tensors[st.a].offset;
+    st.off_b = st.b >= 0 ? p.tensors[st.b].offset : 0;
+    st.off_c = p.tensors[st.c].offset;
+  }
+
+  // ---- recipes
+  p.recipes.clear();
+  p.slots.clear();
+  for (int32_t i = 0; i < p.n_init; ++i) {
+    const NetTensor& nt = net.t[i];
+    const TensorInfo& ti = p.tensors[i];
+    Recipe r;
+    std::memset(&r, 0, sizeof(r));
+    r.kind = nt.kind;
+    r.rank = (int32_t)ti.dims.size();
+    r.slot0 = (int32_t)p.slots.size();
+    r.nslot = (int32_t)nt.slots.size();
+    r.elems = ti.elems;
+    r.offset = ti.offset;
+    r.meta = i;
+    for (const auto& ss : nt.slots) {
+      Slot sl;
+      std::memset(&sl, 0, sizeof(sl));
+      int32_t pp = -1;
+      for (size_t j = 0; j < ti.dims.size(); ++j)
+        if (ti.dims[j] == ss.index) pp = (int32_t)(ti.dims.size() - 1 - j);
+      sl.dimpos = pp;
+      sl.slice_ord = pp < 0 ? slice_ord[ss.index] : -1;
+      sl.absorbed = ss.absorbed;
+      sl.dre = ss.dre;
+      sl.dim = ss.dim;
+      p.slots.push_back(sl);
+    }
+    p.recipes.push_back(r);
+  }
+
+  // ---- workspace layout
+  uint64_t off = 0;
+  p.off_recipe = off;
+  off = align256(off + sizeof(Recipe) * p.recipes.size());
+  p.off_slots = off;
+  off = align256(off + sizeof(Slot) * std::max<size_t>(1, p.slots.size()));
+  p.off_meta = off;
+  off = align256(off + 16ull * n_tens);
+  p.off_counter = off;
+  off = align256(off + 4ull * std::max<int32_t>(1, n_steps));
+  p.off_result = off;
+  off = align256(off + 32ull * (uint64_t)p.n_slices + 32);
+  p.off_scratch = off;
+  off = align256(off + 16ull * (uint64_t)std::max<int64_t>(1, partials));
+  p.off_arena = off;
+  p.program.assign(p.off_meta, 0);
+  if (!p.recipes.empty())
+    std::memcpy(p.program.data() + p.off_recipe, p.recipes.data(), sizeof(Recipe) * p.recipes.size());
+  if (!p.slots.empty())
+    std::memcpy(p.program.data() + p.off_slots, p.slots.data(), sizeof(Slot) * p.slots.size());
+  return true;
+}
+
+}  // namespace pk

@@ -1,0 +1,120 @@
+"""Replays a library plan on the CPU with numpy, following the exact records the
+kernels receive (initial-tensor recipes, step stride runs, arena offsets, scaling).
+
+Test infrastructure only: it checks the host planner's bookkeeping without a GPU.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+
+MAXRUNS = 12
+
+
+class Recipe(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("rank", C.c_int32), ("slot0", C.c_int32),
+                ("nslot", C.c_int32), ("elems", C.c_int64), ("offset", C.c_int64),
+                ("meta", C.c_int32)]
+
+
+class Slot(C.Structure):
+    _fields_ = [("dimpos", C.c_int32), ("slice_ord", C.c_int32), ("absorbed", C.c_int32),
+                ("pad", C.c_int32), ("dre", C.c_double), ("dim", C.c_double)]
+
+
+class Run(C.Structure):
+    _fields_ = [("size", C.c_int64), ("sa", C.c_int64), ("sb", C.c_int64)]
+
+
+class Step(C.Structure):
+    _fields_ = [("a", C.c_int32), ("b", C.c_int32), ("c", C.c_int32), ("kernel", C.c_int32),
+                ("off_a", C.c_int64), ("off_b", C.c_int64), ("off_c", C.c_int64),
+                ("R", C.c_int64), ("K", C.c_int64), ("N", C.c_int64),
+                ("nrow", C.c_int32), ("nk", C.c_int32), ("nn", C.c_int32),
+                ("row", Run * MAXRUNS), ("kr", Run * MAXRUNS), ("nr", Run * MAXRUNS),
+                ("rank_c", C.c_int32), ("chunks", C.c_int32)]
+
+
+def _offsets(n, runs, nruns):
+    """Per linear index x < n: (sum digit*sa, sum digit*sb) over the stride runs."""
+    x = np.arange(n, dtype=np.int64)
+    oa = np.zeros(n, dtype=np.int64)
+    ob = np.zeros(n, dtype=np.int64)
+    for i in range(nruns):
+        sz = runs[i].size
+        d = x % sz
+        x = x // sz
+        oa += d * runs[i].sa
+        ob += d * runs[i].sb
+    return oa, ob
+
+
+def replay(plan):
+    sc = np.frombuffer(plan.debug_blob(3), dtype=np.int64)
+    q, n_init, n_steps, n_slices, n_sliced, final_t, off_rec, off_slots, n_slots, step_sz = \
+        [int(v) for v in sc]
+    assert step_sz == C.sizeof(Step), (step_sz, C.sizeof(Step))
+    prog = plan.debug_blob(0)
+    recs = [Recipe.from_buffer_copy(prog, off_rec + i * C.sizeof(Recipe)) for i in range(n_init)]
+    slots = [Slot.from_buffer_copy(prog, off_slots + i * C.sizeof(Slot)) for i in range(n_slots)]
+    sb = plan.debug_blob(1)
+    steps = [Step.from_buffer_copy(sb, i * C.sizeof(Step)) for i in range(n_steps)]
+    tinfo = np.frombuffer(plan.debug_blob(2), dtype=np.int64).reshape(-1, 2)
+    fre, fim, fexp = np.frombuffer(plan.debug_blob(4), dtype=np.float64)
+    arena_n = int((tinfo[:, 0] + tinfo[:, 1]).max())
+    total = []
+    for sl in range(n_slices):
+        sdig = []
+        s = sl
+        for _ in range(n_sliced):
+            sdig.append(s % q)
+            s //= q
+        arena = np.full(arena_n, np.nan + 0j, dtype=np.complex128)
+        mx = {}
+        ex = {}
+        for r in recs:
+            e = np.arange(r.elems, dtype=np.int64)
+            if r.kind == 1:
+                val = np.ones(r.elems, dtype=np.complex128)
+            else:
+                val = np.zeros(r.elems, dtype=np.complex128)
+                for s in range(q):
+                    prod = np.ones(r.elems, dtype=np.complex128)
+                    for j in range(r.nslot):
+                        sl_ = slots[r.slot0 + j]
+                        x = (e // q ** sl_.dimpos) % q if sl_.dimpos >= 0 else \
+                            np.full(r.elems, sdig[sl_.slice_ord])
+                        if sl_.absorbed:
+                            prod = np.where(x == s, prod * complex(sl_.dre, sl_.dim), prod)
+                        else:
+                            prod = np.where(x == s, prod, 0)
+                    val += prod
+            arena[r.offset:r.offset + r.elems] = val
+            mx[r.meta] = float(np.max(np.maximum(np.abs(val.real), np.abs(val.imag))))
+            ex[r.meta] = 0
+        for st in steps:
+            oa, ob = _offsets(st.R, st.row, st.nrow)
+            ka, kb = _offsets(st.K, st.kr, st.nk)
+            _, nb = _offsets(st.N, st.nr, st.nn)
+            A = arena[st.off_a + oa[:, None] + ka[None, :]]                 # R x K
+            ea = math.frexp(mx[st.a])[1] if mx[st.a] > 0 else 0
+            if st.b >= 0:
+                B = arena[st.off_b + ob[:, None, None] + kb[None, :, None] + nb[None, None, :]]
+                eb = math.frexp(mx[st.b])[1] if mx[st.b] > 0 else 0
+                Cv = np.einsum("rk,rkn->nr", A, B)
+                xb = ex[st.b]
+            else:
+                eb, xb = 0, 0
+                Cv = A.sum(axis=1)[None, :]
+            Cv = Cv * 2.0 ** -(ea + eb)
+            flat = Cv.reshape(-1)   # C[n * R + r]
+            arena[st.off_c:st.off_c + flat.size] = flat
+            assert not np.isnan(flat).any()
+            mx[st.c] = float(np.max(np.maximum(np.abs(flat.real), np.abs(flat.imag))))
+            ex[st.c] = ex[st.a] + xb + ea + eb
+        v = arena[tinfo[final_t, 0]]
+        total.append((complex(v), ex[final_t]))
+    # sum of slices, then the constant factor
+    emax = max((e + math.frexp(abs(v))[1] for v, e in total if v != 0), default=0)
+    z = sum(v * 2.0 ** (e - emax) for v, e in total)
+    return complex(z) * complex(fre, fim), emax + int(fexp)

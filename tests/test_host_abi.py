@@ -1,0 +1,149 @@
+"""Host-side checks of libpk (no GPU): exports, knot input, grid walks, plans.
+
+Plans are replayed on the CPU from the library's own records (tests/plan_replay.py)
+and compared with the oracle, so the planner's index bookkeeping, layouts, stride
+runs, slicing and exponent tracking are checked before any kernel runs.
+"""
+import math
+import re
+
+import pytest
+
+import knotgen as kg
+import oracle
+import paper_1807_02119_gb300 as pk
+from oracle.scaled import SC, rel_err
+from plan_replay import replay
+
+HEADER = __file__.rsplit("/tests/", 1)[0] + "/include/pk.h"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return pk.Context(-1)
+
+
+def test_library_exports_every_declared_symbol():
+    names = set(re.findall(r"\b(pk_[a-z0-9_]+)\s*\(", open(HEADER).read()))
+    assert len(names) >= 20
+    L = pk.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert names <= set(pk.EXPORTED) | {"pk_last_error"}
+
+
+def _pds():
+    out = [kg.braid_closure_pd([1, 1, 1], 2), kg.braid_closure_pd([1, -2, 1, -2], 3), [],
+           kg.kink([], 0, 1), kg.braid_closure_pd(kg.torus_braid(3, 5), 3)]
+    for s in range(25):
+        out.append(kg.random_grid_knot(14, s, bool(s % 2), 1).pd)
+    rng = kg.SplitMix64(9)
+    out.append(kg.randomize(out[5], rng, 5))
+    return out
+
+
+def test_knot_from_pd_matches_oracle(ctx):
+    for pd in _pds():
+        k = pk.Knot.from_pd(ctx, pd)
+        g = oracle.tait_graph(pd, black=0)
+        info = k.info()
+        assert (info["n_v"], info["n_c"], info["writhe"], info["tau"], info["components"]) == \
+            (g.n_v, g.n_crossings, g.writhe, g.tau, g.components)
+        edges = k.edges()
+        for q in (2, 3, 5):
+            assert oracle.z_exact(info["n_v"], edges, q) == oracle.z_exact(g.n_v, g.edges, q)
+
+
+def test_outer_region(ctx):
+    for s in range(8):
+        gk = kg.random_grid_knot(12, 40 + s, True, 2)
+        k = pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer)
+        g = oracle.tait_graph(gk.pd, outer=gk.outer)
+        assert k.info()["n_v"] == g.n_v and k.info()["tau"] == g.tau
+
+
+def test_grid_walk_matches_generator(ctx):
+    for (L, seed, rou, lo, hi) in ((12, 0, True, 16, 16), (14, 3, False, 1, 99), (20, 11, True, 30, 60)):
+        k = pk.Knot.from_grid_walk(ctx, L, seed, rou, lo, hi)
+        g = kg.random_grid_knot(L, seed, rou, lo, hi)
+        assert k.pd() == [tuple(x) for x in g.pd]
+        assert k.info()["n_v"] == oracle.tait_graph(g.pd, outer=g.outer).n_v
+
+
+def test_invalid_inputs(ctx):
+    with pytest.raises(pk.PkError) as e:
+        pk.Knot.from_pd(ctx, [(0, 1, 2, 3)])
+    assert e.value.status == 1
+    with pytest.raises(pk.PkError):
+        pk.Knot.from_pd(ctx, [(0, 2, 1, 3), (2, 0, 3, 1)])  # under-strand not a -> a+1
+    k = pk.Knot.from_pd(ctx, kg.braid_closure_pd([1, 1, 1], 2))
+    with pytest.raises(pk.PkError) as e:
+        pk.Plan(ctx, k, 0)
+    assert e.value.status == 1
+    with pytest.raises(pk.PkError):
+        pk.Knot.from_signed_graph(ctx, 2, [(0, 2, 1)], 0)
+    with pytest.raises(pk.PkError):
+        pk.Knot.from_signed_graph(ctx, 2, [(0, 1, 0)], 0)
+
+
+def test_link_pd_is_rejected(ctx):
+    """Arc labels run consecutively along one component, so a two-component PD code
+    (Hopf link) cannot satisfy the convention and is refused."""
+    with pytest.raises(pk.PkError) as e:
+        pk.Knot.from_pd(ctx, [(0, 3, 1, 2), (2, 1, 3, 0)])
+    assert e.value.status == 1
+
+
+def _z_oracle(pd, q):
+    g = oracle.tait_graph(pd, black=0)
+    return oracle.z_complex(g.n_v, g.edges, q)
+
+
+@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "elim_spin", "auto"])
+def test_plan_replay_matches_oracle(ctx, order):
+    for pd in _pds()[:18]:
+        k = pk.Knot.from_pd(ctx, pd)
+        for q in (1, 2, 3, 5):
+            p = pk.Plan(ctx, k, q, order=order)
+            z, e = replay(p)
+            got = SC.of(z, e)
+            want = _z_oracle(pd, q)
+            assert rel_err(got, want) < 1e-10 or (abs(want.m) == 0 and abs(z) < 1e-12), (pd, q, order)
+
+
+def test_plan_replay_with_slicing(ctx):
+    for s in range(6):
+        pd = kg.random_grid_knot(16, 100 + s, True, 20, 60).pd
+        k = pk.Knot.from_pd(ctx, pd)
+        for order, q, lim in (("greedy_edge", 2, 4.0), ("greedy_spin", 3, 4.8), ("elim_spin", 2, 3.0)):
+            p = pk.Plan(ctx, k, q, order=order, max_log2_elems=lim)
+            st = p.stats()
+            assert st["log2_max_elems"] <= lim + 1e-9
+            assert st["n_slices"] >= 1
+            z, e = replay(p)
+            assert rel_err(SC.of(z, e), _z_oracle(pd, q)) < 1e-10, (s, order)
+
+
+def test_plan_stats_and_steps(ctx):
+    pd = kg.random_grid_knot(20, 5, True, 40, 80).pd
+    k = pk.Knot.from_pd(ctx, pd)
+    p = pk.Plan(ctx, k, 3, order="greedy_spin")
+    st = p.stats()
+    steps = p.steps()
+    assert st["n_steps"] == len(steps)
+    assert abs(st["cmacs"] - sum(s["R"] * s["K"] * s["N"] for s in steps)) < 1e-6 * st["cmacs"]
+    assert st["workspace_c128"] > st["workspace_c64"]
+    assert p.launches() == 1 + st["n_slices"] * (2 + st["n_steps"])
+
+
+def test_jones_normalisation_host(ctx):
+    """pk_jones_from_z applies A(q) (Eq. JonesPotts): with the oracle's Z it must
+    reproduce the oracle's V."""
+    for pd in _pds()[:10]:
+        k = pk.Knot.from_pd(ctx, pd)
+        g = oracle.tait_graph(pd, black=0)
+        for q in (1, 2, 3, 5, 6):
+            z = oracle.z_complex(g.n_v, g.edges, q)
+            v = k.jones_from_z(q, pk.Scaled(z.m.real, z.m.imag, z.e))
+            want = oracle.jones(pd, q, black=0)
+            assert rel_err(SC.of(v.mantissa, v.exp2), want) < 1e-12
