@@ -66,9 +66,14 @@ typedef enum {
   PK_ORDER_PARTITION = 4     /* spin network, recursive-bisection separator order           */
 } pk_order;
 
+/* pk_plan_opts.flags: kernel-choice overrides for testing and tuning (default 0 lets
+ * the planner choose per step by its shape). */
+#define PK_FLAG_FORCE_GEMM 1 /* every two-operand step on the tiled GEMM kernel           */
+#define PK_FLAG_FORCE_ROWS 2 /* every step on the row kernel                               */
+
 typedef struct {
   int32_t order;             /* pk_order                                                    */
-  int32_t flags;             /* reserved, 0                                                 */
+  int32_t flags;             /* PK_FLAG_* bits, 0 by default                                */
   double max_log2_elems;     /* slice indices until no tensor exceeds 2^x elements (<= 31;
                                 0 -> 31)                                                     */
   double max_log2_slices;    /* refuse (PK_ETOOWIDE) plans needing more slices (0 -> 40)    */
@@ -178,9 +183,9 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
 
 /* Runs the kernels of pk_launch once (same stream, same workspace, recipe already
  * uploaded) with a CUDA event pair around every launch, waits, and returns per kernel
- * class c (0 build, 1 rows, 2 split-K, 3 results): out[c] = milliseconds,
- * out[4+c] = launches, out[8+c] = algorithmic complex multiply-adds, out[12+c] =
- * algorithmic bytes (|A| + |B| + |C| at the precision's element size).  16 doubles. */
+ * class c (0 build, 1 rows, 2 split-K, 3 results, 4 GEMM): out[c] = milliseconds,
+ * out[5+c] = launches, out[10+c] = algorithmic complex multiply-adds, out[15+c] =
+ * algorithmic bytes (|A| + |B| + |C| at the precision's element size).  20 doubles. */
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                      uint64_t workspace_bytes, double* out);
 

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpk.so")
 
 PK_C128, PK_C64, PK_SPLIT_TF32 = 0, 1, 2
+FLAG_FORCE_GEMM, FLAG_FORCE_ROWS = 1, 2
 PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split_tf32": PK_SPLIT_TF32}
 ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4}
 STATUS = {0: "PK_OK", 1: "PK_EINVAL", 2: "PK_ENOTKNOT", 3: "PK_ENOMEM", 4: "PK_ETOOWIDE",
@@ -219,8 +220,8 @@ class Knot:
 
 class Plan:
     def __init__(self, ctx: Context, knot: Knot, q: int, order: str = "auto",
-                 max_log2_elems: float = 0.0, max_log2_slices: float = 0.0):
-        o = pk_plan_opts(ORDERS[order], 0, max_log2_elems, max_log2_slices)
+                 max_log2_elems: float = 0.0, max_log2_slices: float = 0.0, flags: int = 0):
+        o = pk_plan_opts(ORDERS[order], flags, max_log2_elems, max_log2_slices)
         h = C.c_void_p()
         _check(lib().pk_plan_create(ctx.h, knot.h, q, C.byref(o), C.byref(h)), ctx)
         self.h = h
@@ -319,9 +320,9 @@ def download(plan: Plan, precision: str, ws):
 def profile(plan: Plan, precision: str, ws):
     """Per kernel class (build, rows, splitk, results): ms, launches, complex MACs, bytes
     of one pass of the plan's kernels, timed with CUDA events on the context's stream."""
-    out = (C.c_double * 16)()
+    out = (C.c_double * 20)()
     _check(lib().pk_profile(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
                             ws.numel(), out), plan.ctx)
-    names = ("build", "rows", "splitk", "results")
-    return {n: {"ms": out[i], "launches": out[4 + i], "cmacs": out[8 + i], "bytes": out[12 + i]}
+    names = ("build", "rows", "splitk", "results", "gemm")
+    return {n: {"ms": out[i], "launches": out[5 + i], "cmacs": out[10 + i], "bytes": out[15 + i]}
             for i, n in enumerate(names)}

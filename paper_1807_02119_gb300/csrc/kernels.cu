@@ -310,6 +310,145 @@ __global__ void __launch_bounds__(256) k_rows_big(const Step s, Cx<R>* arena, Me
   block_max_to_meta(vmax, meta + s.c);
 }
 
+// ------------------------------------------------------------------ GEMM-shaped steps
+// Per batch index b: C_b[m, n] = sum_k A_b[m, k] B_b[k, n] on 64 x 64 output tiles,
+// K in chunks of 16.  Operand tiles are gathered through the stride runs (the index
+// permutation) into shared memory, coalesced along whichever of m/k (A) or k/n (B) is
+// unit-stride in memory; each of the 256 threads accumulates a 4 x 4 block of complex
+// outputs in registers (4 real FMAs per complex multiply-add).
+__device__ __forceinline__ void runs4(long long x, const Run4* r, int n, long long& oa,
+                                      long long& ob, long long& oc) {
+  oa = ob = oc = 0;
+  for (int i = 0; i < n; ++i) {
+    long long sz = r[i].size;
+    long long d = x % sz;
+    x /= sz;
+    oa += d * r[i].sa;
+    ob += d * r[i].sb;
+    oc += d * r[i].sc;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_gemm(const Step s, Cx<R>* arena, Meta* meta) {
+  constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, LDA = BM + 1, LDB = BN + 1;
+  __shared__ Cx<R> As[BK * LDA];
+  __shared__ Cx<R> Bs[BK * LDB];
+  __shared__ long long am[BM], cm[BM], bn[BN], cn[BN], ak[BK], bk[BK];
+  __shared__ long long base[3];
+  const int tid = threadIdx.x;
+  const long long tiles_m = (s.M + BM - 1) / BM, tiles_n = (s.N + BN - 1) / BN;
+  long long t = blockIdx.x;
+  const long long tm = t % tiles_m;
+  t /= tiles_m;
+  const long long tn = t % tiles_n;
+  const long long bb = t / tiles_n;
+  if (tid == 0) runs4(bb, s.gb, s.ngb, base[0], base[1], base[2]);
+  if (tid < BM) {
+    long long m = tm * BM + tid;
+    if (m < s.M) {
+      long long d;
+      runs4(m, s.gm, s.ngm, am[tid], d, cm[tid]);
+    } else {
+      am[tid] = -1;
+      cm[tid] = -1;
+    }
+  } else if (tid < BM + BN) {
+    int j = tid - BM;
+    long long n = tn * BN + j;
+    if (n < s.N) {
+      long long d;
+      runs4(n, s.gn, s.ngn, d, bn[j], cn[j]);
+    } else {
+      bn[j] = -1;
+      cn[j] = -1;
+    }
+  }
+  const R scale = step_scale<R>(s, meta, blockIdx.x == 0 && tid == 0);
+  __syncthreads();
+  const Cx<R>* A = arena + s.off_a + base[0];
+  const Cx<R>* B = arena + s.off_b + base[1];
+  Cx<R> acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = {0, 0};
+  const int tx = tid & 15, ty = tid >> 4;
+  for (long long k0 = 0; k0 < s.K; k0 += BK) {
+    if (tid < BK) {
+      long long k = k0 + tid;
+      if (k < s.K) {
+        long long ka, kb;
+        split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
+        ak[tid] = ka;
+        bk[tid] = kb;
+      } else {
+        ak[tid] = -1;
+        bk[tid] = -1;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < (BM * BK) / 256; ++p) {
+      int idx = tid + p * 256, i, j;
+      if (s.a_kinner) {
+        i = idx / BK;
+        j = idx % BK;
+      } else {
+        i = idx % BM;
+        j = idx / BM;
+      }
+      Cx<R> v{0, 0};
+      if (am[i] >= 0 && ak[j] >= 0) v = ld(A + am[i] + ak[j]);
+      As[j * LDA + i] = v;
+    }
+#pragma unroll
+    for (int p = 0; p < (BN * BK) / 256; ++p) {
+      int idx = tid + p * 256, j, kk;
+      if (s.b_kinner) {
+        j = idx / BK;
+        kk = idx % BK;
+      } else {
+        j = idx % BN;
+        kk = idx / BN;
+      }
+      Cx<R> v{0, 0};
+      if (bn[j] >= 0 && bk[kk] >= 0) v = ld(B + bk[kk] + bn[j]);
+      Bs[kk * LDB + j] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      Cx<R> a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk * LDA + tx * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk * LDB + ty * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cmac(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  Cx<R>* C = arena + s.off_c + base[2];
+  R vmax = 0;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int mi = tx * TM + i;
+    if (cm[mi] < 0) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int nj = ty * TN + j;
+      if (cn[nj] < 0) continue;
+      Cx<R> v{acc[i][j].re * scale, acc[i][j].im * scale};
+      st(C + cm[mi] + cn[nj], v);
+      vmax = fmax(vmax, fmax(fabs(v.re), fabs(v.im)));
+    }
+  }
+  block_max_to_meta(vmax, meta + s.c);
+}
+
 // Few outputs, long K: block (chunk, output) sums its slice of K; the last block to
 // finish (ticket counter) adds the partials of every output in chunk order, so the
 // result does not depend on scheduling.
@@ -492,8 +631,10 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
 
 // Enqueues every kernel of every slice.  With `prof` set, an event pair brackets each
 // launch and per-class milliseconds / counts / algorithmic work are accumulated.
+constexpr int kNumClasses = 5;  // build, rows, split-K, results, GEMM
 struct Prof {
-  double ms[4] = {0, 0, 0, 0}, n[4] = {0, 0, 0, 0}, cmacs[4] = {0, 0, 0, 0}, bytes[4] = {0, 0, 0, 0};
+  double ms[kNumClasses] = {}, n[kNumClasses] = {}, cmacs[kNumClasses] = {},
+         bytes[kNumClasses] = {};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   std::vector<int> cls;
 };
@@ -548,7 +689,13 @@ cudaError_t launch_plan_impl(const Plan& p, void* ws, cudaStream_t stream, Prof*
       const double cm = (double)s.R * (double)s.K * (double)s.N;
       const double by = eb * (double)(p.tensors[s.a].elems + (s.b >= 0 ? p.tensors[s.b].elems : 0) +
                                       p.tensors[s.c].elems);
-      if (s.kernel == KSPLITK) {
+      const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
+      if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
+        mark(4, cm, by, true);
+        k_gemm<R><<<(unsigned)gemm_tiles, 256, 0, stream>>>(s, arena, meta);
+        mark(4, 0, 0, false);
+        e = cudaGetLastError();
+      } else if (s.kernel == KSPLITK) {
         mark(2, cm, by, true);
         k_splitk<R><<<dim3((unsigned)s.chunks, (unsigned)(s.R * s.N)), 256, 0, stream>>>(
             s, arena, meta, partial, counters + i);
@@ -592,11 +739,11 @@ cudaError_t profile_plan(const Plan& p, void* ws, cudaStream_t stream, double* o
     cudaEventDestroy(prof.ev[i].first);
     cudaEventDestroy(prof.ev[i].second);
   }
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < kNumClasses; ++c) {
     out[c] = prof.ms[c];
-    out[4 + c] = prof.n[c];
-    out[8 + c] = prof.cmacs[c];
-    out[12 + c] = prof.bytes[c];
+    out[kNumClasses + c] = prof.n[c];
+    out[2 * kNumClasses + c] = prof.cmacs[c];
+    out[3 * kNumClasses + c] = prof.bytes[c];
   }
   return e;
 }

@@ -69,7 +69,13 @@ struct Slot {
   double dre, dim;         // clause diagonal when absorbed
 };
 
-enum KernelKind : int32_t { KROWS = 0, KSPLITK = 1 };
+enum KernelKind : int32_t { KROWS = 0, KSPLITK = 1, KGEMM = 2 };
+
+// A stride run with its stride in C as well (GEMM view of a step).
+struct Run4 {
+  int64_t size;
+  int64_t sa, sb, sc;
+};
 
 struct Step {
   int32_t a, b, c;         // tensor ids (a = larger operand; b = -1: constant 1)
@@ -82,6 +88,16 @@ struct Step {
   Run nr[kMaxRuns];        // sa unused, sb = stride in B; C offset = n * R
   int32_t rank_c;
   int32_t chunks;          // split-K: K chunks
+  // GEMM view: C[b, m, n] = sum_k A[b, m, k] B[b, k, n] with the rows split into batch
+  // runs (present in both operands) and m runs (A only); every run carries its C stride.
+  int64_t Bsz, M;          // R = Bsz * M
+  int32_t ngb, ngm, ngn;
+  int32_t a_kinner;        // A's unit-stride index is a contracted one
+  int32_t b_kinner;        // B's unit-stride index is a contracted one
+  int32_t pad2;
+  Run4 gb[kMaxRuns];
+  Run4 gm[kMaxRuns];
+  Run4 gn[kMaxRuns];
 };
 
 // Per-tensor device bookkeeping: stored value x means x * 2^exp; maxbits is the bit

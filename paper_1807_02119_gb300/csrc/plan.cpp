@@ -612,8 +612,67 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
     for (int32_t i = (int32_t)n_dims.size() - 1; i >= 0; --i) cd_.push_back(n_dims[i]);
     for (int32_t i = (int32_t)row_dims.size() - 1; i >= 0; --i) cd_.push_back(row_dims[i]);
     st.rank_c = (int32_t)cd_.size();
+    // GEMM view: batch / m / n runs with their C strides (C = [n-part, row-part])
+    {
+      std::vector<Run4> gbv, gmv, gnv;
+      auto push4 = [&](std::vector<Run4>& v, int64_t sa, int64_t sb, int64_t sc) {
+        if (!v.empty()) {
+          Run4& l = v.back();
+          if (sa == l.sa * l.size && sb == l.sb * l.size && sc == l.sc * l.size) {
+            l.size *= q;
+            return;
+          }
+        }
+        v.push_back({(int64_t)q, sa, sb, sc});
+      };
+      int64_t csr = 1;  // C stride of the next row dim (inner -> outer, A order)
+      for (int32_t i = ra - 1; i >= 0; --i) {
+        int32_t v = ad[i];
+        if (!in_c(v)) continue;
+        if (pos_in(bd, v) >= 0)
+          push4(gbv, stride_a(v), stride_b(v), csr);
+        else
+          push4(gmv, stride_a(v), 0, csr);
+        csr *= q;
+      }
+      int64_t csn = st.R;
+      for (int32_t i = rb - 1; i >= 0; --i) {
+        int32_t v = bd[i];
+        if (pos_in(ad, v) >= 0 || !in_c(v)) continue;
+        push4(gnv, 0, stride_b(v), csn);
+        csn *= q;
+      }
+      if ((int)gbv.size() > kMaxRuns || (int)gmv.size() > kMaxRuns || (int)gnv.size() > kMaxRuns) {
+        err = "step has too many stride runs";
+        return false;
+      }
+      st.ngb = (int32_t)gbv.size();
+      st.ngm = (int32_t)gmv.size();
+      st.ngn = (int32_t)gnv.size();
+      st.Bsz = st.M = 1;
+      for (int i = 0; i < st.ngb; ++i) {
+        st.gb[i] = gbv[i];
+        st.Bsz *= gbv[i].size;
+      }
+      for (int i = 0; i < st.ngm; ++i) {
+        st.gm[i] = gmv[i];
+        st.M *= gmv[i].size;
+      }
+      for (int i = 0; i < st.ngn; ++i) st.gn[i] = gnv[i];
+      st.a_kinner = (ra > 0 && !in_c(ad[ra - 1])) ? 1 : 0;
+      st.b_kinner = (rb > 0 && pos_in(ad, bd[rb - 1]) >= 0 && !in_c(bd[rb - 1])) ? 1 : 0;
+    }
     const int64_t outs = st.R * st.N;
-    st.kernel = (outs <= 4096 && st.K >= 4096) ? KSPLITK : KROWS;
+    if (b >= 0 && (opts.flags & PK_FLAG_FORCE_GEMM))
+      st.kernel = KGEMM;
+    else if (opts.flags & PK_FLAG_FORCE_ROWS)
+      st.kernel = KROWS;
+    else if (b >= 0 && st.M >= 64 && st.N >= 32 && st.K >= 16)
+      st.kernel = KGEMM;
+    else if (outs <= 4096 && st.K >= 4096)
+      st.kernel = KSPLITK;
+    else
+      st.kernel = KROWS;
     st.chunks = st.kernel == KSPLITK ? (int32_t)std::min<int64_t>(64, (st.K + 2047) / 2048) : 0;
     p.steps[s] = st;
   }

@@ -26,13 +26,21 @@ class Run(C.Structure):
     _fields_ = [("size", C.c_int64), ("sa", C.c_int64), ("sb", C.c_int64)]
 
 
+class Run4(C.Structure):
+    _fields_ = [("size", C.c_int64), ("sa", C.c_int64), ("sb", C.c_int64), ("sc", C.c_int64)]
+
+
 class Step(C.Structure):
     _fields_ = [("a", C.c_int32), ("b", C.c_int32), ("c", C.c_int32), ("kernel", C.c_int32),
                 ("off_a", C.c_int64), ("off_b", C.c_int64), ("off_c", C.c_int64),
                 ("R", C.c_int64), ("K", C.c_int64), ("N", C.c_int64),
                 ("nrow", C.c_int32), ("nk", C.c_int32), ("nn", C.c_int32),
                 ("row", Run * MAXRUNS), ("kr", Run * MAXRUNS), ("nr", Run * MAXRUNS),
-                ("rank_c", C.c_int32), ("chunks", C.c_int32)]
+                ("rank_c", C.c_int32), ("chunks", C.c_int32),
+                ("Bsz", C.c_int64), ("M", C.c_int64), ("ngb", C.c_int32), ("ngm", C.c_int32),
+                ("ngn", C.c_int32), ("a_kinner", C.c_int32), ("b_kinner", C.c_int32),
+                ("pad2", C.c_int32), ("gb", Run4 * MAXRUNS), ("gm", Run4 * MAXRUNS),
+                ("gn", Run4 * MAXRUNS)]
 
 
 def _offsets(n, runs, nruns):
@@ -47,6 +55,33 @@ def _offsets(n, runs, nruns):
         oa += d * runs[i].sa
         ob += d * runs[i].sb
     return oa, ob
+
+
+def _offsets4(n, runs, nruns):
+    x = np.arange(n, dtype=np.int64)
+    o = [np.zeros(n, dtype=np.int64) for _ in range(3)]
+    for i in range(nruns):
+        sz = runs[i].size
+        d = x % sz
+        x = x // sz
+        o[0] += d * runs[i].sa
+        o[1] += d * runs[i].sb
+        o[2] += d * runs[i].sc
+    return o
+
+
+def _gemm_view(st, arena, scale):
+    """The step through its GEMM-view records (batch / m / n runs with C strides)."""
+    ab, bb, cb = _offsets4(st.Bsz, st.gb, st.ngb)
+    am, _, cm = _offsets4(st.M, st.gm, st.ngm)
+    _, bn, cn = _offsets4(st.N, st.gn, st.ngn)
+    ka, kb = _offsets(st.K, st.kr, st.nk)
+    A = arena[st.off_a + ab[:, None, None] + am[None, :, None] + ka[None, None, :]]
+    B = arena[st.off_b + bb[:, None, None] + kb[None, :, None] + bn[None, None, :]]
+    Cv = np.einsum("bmk,bkn->bmn", A, B) * scale
+    idx = st.off_c + cb[:, None, None] + cm[None, :, None] + cn[None, None, :]
+    assert len(np.unique(idx)) == idx.size == st.R * st.N
+    return idx, Cv
 
 
 def replay(plan):
@@ -108,6 +143,12 @@ def replay(plan):
                 Cv = A.sum(axis=1)[None, :]
             Cv = Cv * 2.0 ** -(ea + eb)
             flat = Cv.reshape(-1)   # C[n * R + r]
+            if st.b >= 0:
+                # the GEMM view of the same step must address the same entries
+                idx, Cg = _gemm_view(st, arena, 2.0 ** -(ea + eb))
+                ref = np.empty_like(flat)
+                ref[idx.reshape(-1) - st.off_c] = Cg.reshape(-1)
+                assert np.allclose(ref, flat, rtol=1e-12, atol=1e-300)
             arena[st.off_c:st.off_c + flat.size] = flat
             assert not np.isnan(flat).any()
             mx[st.c] = float(np.max(np.maximum(np.abs(flat.real), np.abs(flat.imag))))

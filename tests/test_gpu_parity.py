@@ -94,7 +94,10 @@ def test_random_knots_vs_oracle(ctx, order, prec):
 def test_slicing_gpu(ctx):
     for s in range(4):
         gk = kg.random_grid_knot(18, 700 + s, True, 40, 70)
-        for q, lim in ((2, 5.0), (3, 6.4)):
+        k = pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer)
+        for q in (2, 3):
+            full = pk.Plan(ctx, k, q).stats()["log2_max_elems"]
+            lim = full - 1.5 * math.log2(q)      # forces at least one sliced index
             z, v, p = run(ctx, gk.pd, q, "c128", outer=gk.outer, max_log2_elems=lim)
             assert p.stats()["n_slices"] > 1
             zo, _ = oracle_zv(gk.pd, q, outer=gk.outer)
@@ -163,3 +166,32 @@ def test_repeat_calls_same_workspace(ctx):
     z2, _ = pk.evaluate(p, "c128", ws)
     assert (z1.re, z1.im, z1.exp2) == (z2.re, z2.im, z2.exp2)   # deterministic
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", C128_TOL), ("c64", C64_TOL)])
+def test_forced_gemm_kernel(ctx, prec, tol):
+    """Every two-operand step on the tiled GEMM kernel: ragged 64 x 64 edge tiles, tiny
+    extents, batch indices and both unit-stride layouts of each operand."""
+    worst = 0.0
+    for s in range(8):
+        gk = kg.random_grid_knot(16, 1200 + s, True, 20, 45)
+        for order in ("greedy_edge", "greedy_spin", "elim_spin"):
+            for q in (2, 3, 5):
+                z, v, p = run(ctx, gk.pd, q, prec, outer=gk.outer, order=order,
+                              flags=pk.FLAG_FORCE_GEMM)
+                assert any(st["kernel"] == 2 for st in p.steps())
+                zo, vo = oracle_zv(gk.pd, q, outer=gk.outer)
+                e = rel_err(z, zo)
+                worst = max(worst, e)
+                assert e <= tol, (s, order, q, e)
+    print(f"[forced GEMM {prec}] worst relative error {worst:.3e}")
+
+
+def test_forced_rows_kernel(ctx):
+    for s in range(4):
+        gk = kg.random_grid_knot(16, 1300 + s, True, 20, 45)
+        for q in (3, 5):
+            z, _, _ = run(ctx, gk.pd, q, "c128", outer=gk.outer, order="greedy_edge",
+                          flags=pk.FLAG_FORCE_ROWS)
+            zo, _ = oracle_zv(gk.pd, q, outer=gk.outer)
+            assert rel_err(z, zo) <= C128_TOL

@@ -147,3 +147,19 @@ def test_jones_normalisation_host(ctx):
             v = k.jones_from_z(q, pk.Scaled(z.m.real, z.m.imag, z.e))
             want = oracle.jones(pd, q, black=0)
             assert rel_err(SC.of(v.mantissa, v.exp2), want) < 1e-12
+
+
+def test_plan_replay_forced_kernels(ctx):
+    """Forcing every step onto the GEMM (or row) kernel keeps the plan valid: the GEMM
+    view's batch/m/n/k stride runs address the same outputs as the row view."""
+    for s in range(6):
+        pd = kg.random_grid_knot(15, 60 + s, True, 15, 40).pd
+        k = pk.Knot.from_pd(ctx, pd)
+        for flags in (pk.FLAG_FORCE_GEMM, pk.FLAG_FORCE_ROWS):
+            for order in ("greedy_edge", "greedy_spin", "elim_spin"):
+                p = pk.Plan(ctx, k, 3, order=order, flags=flags)
+                kinds = {st["kernel"] for st in p.steps()}
+                if flags == pk.FLAG_FORCE_ROWS:
+                    assert kinds <= {0}
+                z, e = replay(p)
+                assert rel_err(SC.of(z, e), _z_oracle(pd, 3)) < 1e-10
