@@ -192,6 +192,22 @@ pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_w
 /* Number of kernel launches pk_launch issues for this plan and precision. */
 pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launches);
 
+/* Allocation-free evaluation (the paper has no counterpart: this is a deployment aid).
+ * Same result as pk_eval, for callers that cannot allocate device memory -- code embedded
+ * in a host application whose allocator has reserved the GPU's memory, or a service that
+ * forbids allocation once running.  The workspace is a file-scope static device array
+ * of 64 MiB (67108864 bytes) that every GPU loading the library holds until exit; no
+ * cudaMalloc, cudaFree or other allocating routine is called.  Plans whose
+ * pk_plan_workspace_bytes exceeds 64 MiB are refused with PK_ENOMEM and a message in
+ * pk_last_error.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that first call
+ * before any stream capture.  All calls on a device share the array, which keeps the
+ * previous call's contents (each call re-uploads its program and clears its bookkeeping);
+ * calls whose GPU work overlaps -- on different streams or contexts of the same device --
+ * race on it.  Blocks until Z (and V, as in pk_eval) are on the host. */
+pk_status pk_eval_noalloc(pk_ctx* ctx, const pk_plan* p, int32_t precision, pk_scaled* Z,
+                          pk_scaled* V);
+
 /* Host-side normalisation only: V = A(q) Z for the knot's (n_v, w, tau) (Eq. JonesPotts). */
 pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_scaled* V);
 

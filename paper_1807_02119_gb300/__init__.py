@@ -26,7 +26,7 @@ EXPORTED = [
     "pk_knot_edges", "pk_knot_pd", "pk_knot_destroy", "pk_plan_create", "pk_plan_info",
     "pk_plan_workspace_bytes", "pk_plan_steps", "pk_plan_destroy", "pk_eval", "pk_upload",
     "pk_launch", "pk_download", "pk_plan_launches", "pk_jones_from_z", "pk_plan_debug_blob",
-    "pk_profile",
+    "pk_profile", "pk_eval_noalloc",
 ]
 
 
@@ -90,6 +90,7 @@ def lib():
         "pk_jones_from_z": [vp, i32, P(pk_scaled), P(pk_scaled)],
         "pk_plan_debug_blob": [vp, i32, vp, P(u64)],
         "pk_profile": [vp, vp, i32, vp, u64, P(C.c_double)],
+        "pk_eval_noalloc": [vp, vp, i32, P(pk_scaled), P(pk_scaled)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -291,6 +292,20 @@ def evaluate(plan: Plan, precision: str = "c128", ws=None):
     z, v = pk_scaled(), pk_scaled()
     st = lib().pk_eval(ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
                        ws.numel() * ws.element_size(), C.byref(z), C.byref(v))
+    if st == 2:
+        return Scaled.of(z), None
+    _check(st, ctx)
+    return Scaled.of(z), Scaled.of(v)
+
+
+def evaluate_noalloc(plan: Plan, precision: str = "c128"):
+    """pk_eval_noalloc: like evaluate() but allocates nothing; the library's fixed 64 MiB
+    per-device scratch array holds the workspace (see include/pk.h)."""
+    ctx = plan.ctx
+    if ctx.device < 0:
+        raise PkError(7, "evaluate_noalloc needs a GPU context")
+    z, v = pk_scaled(), pk_scaled()
+    st = lib().pk_eval_noalloc(ctx.h, plan.h, PRECISIONS[precision], C.byref(z), C.byref(v))
     if st == 2:
         return Scaled.of(z), None
     _check(st, ctx)

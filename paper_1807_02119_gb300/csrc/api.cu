@@ -16,21 +16,7 @@ template <typename R>
 cudaError_t profile_plan(const Plan& p, void* ws, cudaStream_t stream, double* out);
 }
 
-struct pk_ctx {
-  int32_t device = -1;
-  cudaStream_t stream = nullptr;
-  std::string err;
-  void* own_ws = nullptr;
-  uint64_t own_ws_bytes = 0;
-  pk::SliceResult* pinned_result = nullptr;
-};
-struct pk_knot {
-  pk::Knot k;
-};
-struct pk_plan {
-  pk::Plan p;
-  uint8_t* pinned_program = nullptr;
-};
+#include "handles.h"
 
 namespace {
 

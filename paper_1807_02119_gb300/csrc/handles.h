@@ -1,0 +1,25 @@
+// Definitions of the opaque C-ABI handles (include/pk.h), shared by the translation
+// units that implement entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "pk_internal.h"
+
+struct pk_ctx {
+  int32_t device = -1;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  void* own_ws = nullptr;
+  uint64_t own_ws_bytes = 0;
+  pk::SliceResult* pinned_result = nullptr;
+};
+struct pk_knot {
+  pk::Knot k;
+};
+struct pk_plan {
+  pk::Plan p;
+  uint8_t* pinned_program = nullptr;
+};
