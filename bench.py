@@ -4,9 +4,13 @@
 Workload ("scale"): 64 random grid-walk knots, grid side L=40, seeds 1..64 (rank r of
 N uses seeds 64r+1..64r+64), each redrawn until it has 100..400 crossings, random
 over/under per crossing; every knot is evaluated at q = 2, 3, 5 (t = i, e^{i pi/3},
-(3+sqrt 5)/2).  One step = Z(q) and V_K(t(q)) for all 64 x 3 = 192 (knot, q) pairs,
-all on the GPU through libpk.  `value` is knot evaluations per second (one knot = one
-(knot, q) pair), whole job, inputs resident in HBM; L2 is flushed between steps.
+(3+sqrt 5)/2).  One step = Z(q) and V_K(t(q)) for all 64 x 3 = 192 (knot, q) pairs, all
+on the GPU through libpk.  `value` is knot evaluations per second (one knot = one
+(knot, q) pair), whole job, in the headline precision (split FP32 by default), with
+every plan's program resident in HBM (per-plan state buffers; the plans share one
+tensor arena) and L2 flushed between steps.  The same workload is then run once in
+complex64 and once in complex128; the relative error of every evaluation against
+complex128 is reported.
 
 --impl reference times the CPU oracle (complex128 spin elimination in numpy) on the
 host cores on a bounded sample of the same workload.
@@ -24,24 +28,27 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-QS = (2, 3, 5)
 T0 = time.perf_counter()
+SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
+FP32_CORE_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3   # FMA = 2 flops
+FP32_ISSUE_TOPS = SM_COUNT * FP32_LANES * SM_MAX_GHZ / 1e3         # FP32 instructions
+FF_INSTR_PER_CMAC = 48   # float-float complex multiply-add: 4 x (two-product + TwoSum)
+FP64_TFLOPS = 1.25       # GB300 FP64 rate
 
 
 def log(msg):
     print(f"[bench {time.perf_counter() - T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
-FP32_CORE_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
-FP64_TFLOPS = 1.25                                    # GB300 FP64 rate (profiling recipe)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
-    ap.add_argument("--skip-c128", action="store_true", help="omit the complex128 comparison pass")
+    ap.add_argument("--precision", default="split", choices=["split", "c64", "c128"])
+    ap.add_argument("--skip-compare", action="store_true",
+                    help="omit the complex64 / complex128 comparison passes")
     ap.add_argument("--qs", default="2,3,5")
     ap.add_argument("--knots", type=int, default=64, help="knots per GPU (64 = the workload)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle baseline")
@@ -138,13 +145,12 @@ def run_reference(args):
         return
     qs = tuple(int(x) for x in args.qs.split(","))
     knots = workload(0)
-    # each step: a bounded sample (~8 s of oracle work) of the workload
     for _ in range(args.warmup):
         cpu_oracle_rate(knots, 1.0, qs)
     tot_n, tot_t = 0, 0.0
     sample = ""
     for _ in range(args.steps):
-        n, t, sample = cpu_oracle_rate(knots, 8.0, qs)
+        n, t, sample = cpu_oracle_rate(knots, 8.0, qs)   # each step a bounded sample
         tot_n += n
         tot_t += t
     v = tot_n / tot_t
@@ -152,12 +158,20 @@ def run_reference(args):
            "value": v, "unit": "knots/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-           "data": "synthetic", "config": {"workload": "scale: 64 grid-walk knots L=40, 100-400 crossings, q in {2,3,5}",
-                                           "impl": "CPU oracle, numpy complex128 spin elimination"},
+           "data": "synthetic",
+           "config": {"workload": "scale: 64 grid-walk knots L=40, 100-400 crossings, q in {2,3,5}",
+                      "impl": "CPU oracle, numpy complex128 spin elimination"},
            "cpu_baseline": {"value": v, "unit": "knots/s", "cores": 1, "kind": "oracle",
                             "sample": sample + " per step"},
            "e2e": {"value": v, "unit": "knots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def rel_err(a, b):
+    """|a - b| / |b| for two pk.Scaled values."""
+    d = a.exp2 - b.exp2
+    ma = a.mantissa * (2.0 ** d if d > -1000 else 0.0)
+    return abs(ma - b.mantissa) / abs(b.mantissa) if b.mantissa != 0 else abs(ma)
 
 
 def main():
@@ -193,26 +207,40 @@ def main():
     log(f"planned {len(plans)} evaluations in {plan_s:.2f}s")
     stats = [p.stats() for p in plans]
     prec = args.precision
+    dev = f"cuda:{local}"
 
-    # resident workspaces for the headline precision, one per plan
-    ws = [pk.workspace(p, prec) for p in plans]
-    for p, w in zip(plans, ws):
-        pk.upload(p, prec, w)
+    def buffers(pr):
+        """Per-plan state buffers (resident programs) and one shared tensor arena."""
+        sizes = [p.state_bytes(pr) for p in plans]
+        states = [torch.empty(max(s, 256), dtype=torch.uint8, device=dev) for s, _ in sizes]
+        arena = torch.empty(max(a for _, a in sizes) + 256, dtype=torch.uint8, device=dev)
+        for p, s in zip(plans, states):
+            pk.upload(p, pr, s)
+        return states, arena
+
+    def one_pass(pr, states, arena, subset=None):
+        for i, (p, s) in enumerate(zip(plans, states)):
+            if subset is None or i in subset:
+                pk.launch_arena(p, pr, s, arena)
+
+    def results(pr, states):
+        return [pk.download(p, pr, s) for p, s in zip(plans, states)]
+
+    states, arena = buffers(prec)
     torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-
-    def one_pass():
-        for p, w in zip(plans, ws):
-            pk.launch(p, prec, w)
-
-    def results():
-        return [pk.download(p, prec, w) for p, w in zip(plans, ws)]
-
-    for _ in range(args.warmup):
-        one_pass()
+    # warm-up: W passes, the last one with an event pair around every launch
+    for _ in range(max(0, args.warmup - 1)):
+        one_pass(prec, states, arena)
+    prof = {}
+    for p, s in zip(plans, states):
+        for kname, d in pk.profile(p, prec, s, arena).items():
+            acc = prof.setdefault(kname, {"ms": 0.0, "launches": 0.0, "cmacs": 0.0, "bytes": 0.0})
+            for f in acc:
+                acc[f] += d[f]
     torch.cuda.synchronize()
-    res_main = results()
+    res_main = results(prec, states)
     log("warm-up done")
 
     # timed region: K steps, L2 flushed between steps (outside the events)
@@ -226,7 +254,7 @@ def main():
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        one_pass()
+        one_pass(prec, states, arena)
         b.record(stream)
         b.synchronize()
         times.append(a.elapsed_time(b))
@@ -235,92 +263,98 @@ def main():
     log(f"timed {args.steps} steps")
     step_ms = sum(times) / len(times)
     if dist:
-        t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
+        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t.item())
     evals = len(plans)
     value = world * evals / (step_ms / 1000.0)
 
-    log("profiling pass")
-    # per-kernel-class profile of one pass (CUDA events around every launch)
-    prof = {}
-    for p, w in zip(plans, ws):
-        for kname, d in pk.profile(p, prec, w).items():
-            acc = prof.setdefault(kname, {"ms": 0.0, "launches": 0.0, "cmacs": 0.0, "bytes": 0.0})
-            for f in acc:
-                acc[f] += d[f]
-
-    log("end-to-end passes")
-    # end to end through the public API: host PD-derived recipe -> device -> host result
-    e2e_times = []
+    # end to end through the public API: program host->device (pinned), kernels,
+    # scaled result device->host, for every evaluation
     h2d = sum(len(p.debug_blob(0)) for p in plans)
     d2h = 32 * len(plans)
-    for i in range(max(2, args.steps // 2)):
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        for p, w in zip(plans, ws):
-            pk.evaluate(p, prec, w)
-        e2e_times.append(time.perf_counter() - t1)
-    e2e_val = world * evals / (sum(e2e_times[1:]) / max(1, len(e2e_times) - 1))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for p, s in zip(plans, states):
+        pk.upload(p, prec, s)
+        pk.launch_arena(p, prec, s, arena)
+        pk.download(p, prec, s)
+    e2e_s = time.perf_counter() - t1
+    e2e_val = world * evals / e2e_s
+    log("end-to-end pass")
+    del states, arena
+    torch.cuda.empty_cache()
 
-    log("complex128 pass")
-    # complex128 pass for the error report (shared workspace; uploads inside)
-    c128 = None
-    if not args.skip_c128 and prec != "c128":
-        big = max(p.workspace_bytes("c128") for p in plans)
-        wsd = torch.empty(big, dtype=torch.uint8, device="cuda")
-        for p in plans[:8]:
-            pk.evaluate(p, "c128", wsd)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        res128 = []
-        for p in plans:
-            pk.upload(p, "c128", wsd)
-            pk.launch(p, "c128", wsd)
-            res128.append(pk.download(p, "c128", wsd))
-        b.record(stream)
-        b.synchronize()
-        ms128 = a.elapsed_time(b)
-        errs = []
-        for (z1, v1), (z2, v2) in zip(res_main, res128):
-            d = z1.exp2 - z2.exp2
-            m1 = z1.mantissa * (2.0 ** d if d > -1000 else 0.0)
-            errs.append(abs(m1 - z2.mantissa) / abs(z2.mantissa))
-        c128 = {"value": world * evals / (ms128 / 1000.0), "unit": "knots/s", "ms_per_step": ms128,
-                "note": "one timed pass after a partial warm-up; program uploads included",
-                "max_rel_err_vs_c128": max(errs), "median_rel_err_vs_c128": statistics.median(errs)}
-        del wsd
+    # the same workload once in each other precision; errors against complex128
+    compare = {}
+    res_by = {prec: res_main}
+    if not args.skip_compare:
+        for pr in ("c64", "c128"):
+            if pr == prec:
+                continue
+            st2, ar2 = buffers(pr)
+            one_pass(pr, st2, ar2, subset=set(range(min(6, len(plans)))))   # loads the kernels
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one_pass(pr, st2, ar2)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            res_by[pr] = results(pr, st2)
+            compare[pr] = {"value": world * evals / (ms / 1000.0), "unit": "knots/s",
+                           "ms_per_step": ms, "note": "one timed pass after loading the kernels"}
+            del st2, ar2
+            torch.cuda.empty_cache()
+            log(f"{pr} pass")
+        if "c128" in res_by:
+            for pr, res in res_by.items():
+                if pr == "c128":
+                    continue
+                errs = [max(rel_err(z, zr), rel_err(v, vr))
+                        for (z, v), (zr, vr) in zip(res, res_by["c128"])]
+                entry = compare.setdefault(pr, {})
+                entry.update({"max_rel_err_vs_c128": max(errs),
+                              "median_rel_err_vs_c128": statistics.median(errs),
+                              "evaluations_over_1e-6": sum(e > 1e-6 for e in errs)})
 
-    KNAMES = {"gemm": "k_gemm (tiled strided complex GEMM)",
+    # roofline of the dominant kernel class, from the event-timed warm-up pass
+    knames = {"gemm": "k_gemm (tiled strided complex GEMM)",
               "rows": "k_rows (fused permute-and-contract, thread per output row)",
               "splitk": "k_splitk", "build": "k_build", "results": "k_slice_result/k_sum_slices"}
     dom = max(prof, key=lambda c: prof[c]["ms"])
     rk = prof[dom]
     pk_ = peaks()
-    elem = 16 if prec == "c128" else 8
     flops = 8.0 * rk["cmacs"]
-    ai = flops / max(rk["bytes"], 1.0)
-    alu_peak = FP64_TFLOPS if prec == "c128" else FP32_CORE_TFLOPS
-    ridge = alu_peak * 1e12 / (pk_["hbm_gbs"] * 1e9)
-    if ai > ridge:
-        ach = flops / (rk["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ach / alu_peak, "traffic": None,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz" if prec != "c128"
-                else "nominal FP64 rate of GB300"}
+    sec = rk["ms"] / 1e3
+    ai = flops / max(rk["bytes"], 1.0)           # bytes at the precision's entry size
+    if prec == "split":
+        peak = FP32_ISSUE_TOPS / FF_INSTR_PER_CMAC * 8
+        src = ("derived: 152 SM x 128 FP32 lanes x 2.07 GHz FP32 instructions / 48 instructions "
+               "per float-float complex multiply-add x 8 flops")
+    elif prec == "c64":
+        peak, src = FP32_CORE_TFLOPS, "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"
     else:
-        ach = rk["bytes"] / (rk["ms"] / 1e3) / 1e9
+        peak, src = FP64_TFLOPS, "nominal FP64 rate of GB300"
+    ridge = peak * 1e12 / (pk_["hbm_gbs"] * 1e9)
+    if ai > ridge:
+        ach = flops / sec / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": src}
+    else:
+        ach = rk["bytes"] / sec / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": pk_["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk_["hbm_gbs"], "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-    roof.update({"kernel": KNAMES[dom], "arith_intensity_flop_per_byte": ai,
+                "frac": ach / pk_["hbm_gbs"], "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    roof.update({"kernel": knames[dom], "arith_intensity_flop_per_byte": ai,
                  "launches_per_pass": rk["launches"], "ms_per_pass": rk["ms"],
-                 "share_of_pass": rk["ms"] / sum(v["ms"] for v in prof.values())})
+                 "share_of_pass": rk["ms"] / sum(v["ms"] for v in prof.values()),
+                 "flops_count": "8 real flops per complex multiply-add"})
 
-    log("cpu baseline")
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
+        log("cpu baseline")
         n, t, sample = cpu_oracle_rate(knots, 15.0, qs)
         cpu = {"value": n / t, "unit": "knots/s", "cores": 1, "kind": "oracle", "sample": sample}
 
@@ -333,7 +367,7 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
                "config": {"workload": "scale: 64 random grid-walk knots per GPU, L=40, 100-400 crossings, "
                                       "random over/under, q in {2,3,5}; 192 (knot, q) evaluations per step",
-                          "order": "auto (min-degree spin elimination chosen for all)",
+                          "order": "auto per knot (fewest complex multiply-adds)",
                           "l2": "flushed between steps (512 MB write)",
                           "plan_seconds": plan_s, "complex_macs_per_step": tot_cmacs,
                           "complex_tflops": 8 * tot_cmacs / (step_ms / 1e3) / 1e12},
@@ -341,7 +375,7 @@ def main():
                "e2e": {"value": e2e_val, "unit": "knots/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": clk, "kernel_classes": prof,
-               "c128": c128}
+               "precisions": compare}
         print(json.dumps(out))
     if dist:
         dist.barrier()

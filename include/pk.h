@@ -51,8 +51,12 @@ typedef enum {
 
 typedef enum {
   PK_C128 = 0,       /* complex128 storage, FP64 arithmetic                               */
-  PK_C64 = 1,        /* complex64 storage, FP32 arithmetic                                */
-  PK_SPLIT_TF32 = 2  /* complex64 storage; large steps as 3xTF32 tensor-core products     */
+  PK_C64 = 1,        /* complex64 storage, FP32 arithmetic; with pk_plan_opts.tail_steps
+                        > 0 the final contractions run in complex128                      */
+  PK_SPLIT = 2       /* split FP32: every real number is an unevaluated pair of floats
+                        hi + lo (16 bytes per complex entry); products are split exactly
+                        with an FMA (two-product) and sums carried in float pairs
+                        (TwoSum), i.e. about 48 significant bits on the FP32 units       */
 } pk_precision;
 
 typedef enum {
@@ -77,6 +81,9 @@ typedef struct {
   double max_log2_elems;     /* slice indices until no tensor exceeds 2^x elements (<= 31;
                                 0 -> 31)                                                     */
   double max_log2_slices;    /* refuse (PK_ETOOWIDE) plans needing more slices (0 -> 40)    */
+  int32_t tail_steps;        /* PK_C64: this many final contractions run in complex128
+                                (<= 0: none)                                                 */
+  int32_t reserved;          /* 0                                                           */
 } pk_plan_opts;
 
 typedef struct {
@@ -90,7 +97,8 @@ typedef struct {
   int32_t order_used;        /* pk_order actually used                                      */
   int32_t n_tensors;         /* initial tensors                                             */
   uint64_t workspace_c128;   /* device workspace bytes for PK_C128                          */
-  uint64_t workspace_c64;    /* device workspace bytes for PK_C64 / PK_SPLIT_TF32           */
+  uint64_t workspace_c64;    /* device workspace bytes for PK_C64                           */
+  uint64_t workspace_split;  /* device workspace bytes for PK_SPLIT                         */
 } pk_plan_stats;
 
 /* ---- context ------------------------------------------------------------------ */
@@ -170,24 +178,40 @@ pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_wo
 pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const void* d_workspace,
                       pk_scaled* Z, pk_scaled* V);
 
+/* The workspace of an evaluation is a small per-plan state (initial-tensor program,
+ * per-tensor bookkeeping, slice results, split-K scratch: *state_bytes) followed by the
+ * tensor arena (*arena_bytes); their sum is pk_plan_workspace_bytes.  They may also
+ * live in two separate buffers: pk_upload and pk_download then take the state buffer,
+ * and pk_launch_arena takes both (the profile entry point likewise).  Plans whose
+ * launches are ordered on one stream may share one arena while each keeps its state
+ * (and so its uploaded program) resident. */
+pk_status pk_plan_state_bytes(const pk_plan* p, int32_t precision, uint64_t* state_bytes,
+                              uint64_t* arena_bytes);
+pk_status pk_launch_arena(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_state,
+                          uint64_t state_bytes, void* d_arena, uint64_t arena_bytes);
+
 /* Internal plan records, for host-side verification of a plan without a GPU.
- * which = 0: the device program (recipe records then slot records, as uploaded);
+ * which = 0: the device program (recipe, slot and widening records, as uploaded);
  *         1: the step records; 2: per tensor (arena element offset, elements) int64
  *         pairs; 3: int64 scalars (q, n_init, n_steps, n_slices, n_sliced,
- *         final_tensor, off_recipe, off_slots, n_slots, sizeof step record);
+ *         final_tensor, off_recipe, off_slots, n_slots, sizeof step record,
+ *         tail_first, n_tail, n_widen, off_widen, final tail offset);
  *         4: three doubles (re, im, exp2) of the constant factor (loops of the graph)
- *         that multiplies the contracted value.
+ *         that multiplies the contracted value; 5: the complex128 tail-step records
+ *         of PK_SPLIT.
  * With dst == NULL only *bytes is set.  The record layouts are those of
- * csrc/pk_internal.h (Recipe, Slot, Step) and may change between versions. */
+ * csrc/pk_internal.h (Recipe, Slot, Step, ConvRec, TailStep) and may change between
+ * versions. */
 pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_t* bytes);
 
 /* Runs the kernels of pk_launch once (same stream, same workspace, recipe already
- * uploaded) with a CUDA event pair around every launch, waits, and returns per kernel
+ * uploaded; d_arena NULL = the arena inside the workspace, else as pk_launch_arena)
+ * with a CUDA event pair around every launch, waits, and returns per kernel
  * class c (0 build, 1 rows, 2 split-K, 3 results, 4 GEMM): out[c] = milliseconds,
  * out[5+c] = launches, out[10+c] = algorithmic complex multiply-adds, out[15+c] =
  * algorithmic bytes (|A| + |B| + |C| at the precision's element size).  20 doubles. */
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
-                     uint64_t workspace_bytes, double* out);
+                     uint64_t workspace_bytes, void* d_arena, uint64_t arena_bytes, double* out);
 
 /* Number of kernel launches pk_launch issues for this plan and precision. */
 pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launches);

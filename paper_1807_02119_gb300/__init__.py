@@ -13,9 +13,9 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpk.so")
 
-PK_C128, PK_C64, PK_SPLIT_TF32 = 0, 1, 2
+PK_C128, PK_C64, PK_SPLIT = 0, 1, 2
 FLAG_FORCE_GEMM, FLAG_FORCE_ROWS = 1, 2
-PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split_tf32": PK_SPLIT_TF32}
+PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split": PK_SPLIT}
 ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4}
 STATUS = {0: "PK_OK", 1: "PK_EINVAL", 2: "PK_ENOTKNOT", 3: "PK_ENOMEM", 4: "PK_ETOOWIDE",
           5: "PK_ECUDA", 6: "PK_ETIMEOUT", 7: "PK_ENODEVICE"}
@@ -26,7 +26,7 @@ EXPORTED = [
     "pk_knot_edges", "pk_knot_pd", "pk_knot_destroy", "pk_plan_create", "pk_plan_info",
     "pk_plan_workspace_bytes", "pk_plan_steps", "pk_plan_destroy", "pk_eval", "pk_upload",
     "pk_launch", "pk_download", "pk_plan_launches", "pk_jones_from_z", "pk_plan_debug_blob",
-    "pk_profile", "pk_eval_noalloc",
+    "pk_profile", "pk_eval_noalloc", "pk_plan_state_bytes", "pk_launch_arena",
 ]
 
 
@@ -42,14 +42,16 @@ class pk_scaled(C.Structure):
 
 class pk_plan_opts(C.Structure):
     _fields_ = [("order", C.c_int32), ("flags", C.c_int32), ("max_log2_elems", C.c_double),
-                ("max_log2_slices", C.c_double)]
+                ("max_log2_slices", C.c_double), ("tail_steps", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class pk_plan_stats(C.Structure):
     _fields_ = [("log2_max_elems", C.c_double), ("cmacs", C.c_double),
                 ("bytes_c64", C.c_double), ("n_slices", C.c_int64), ("n_steps", C.c_int32),
                 ("max_rank", C.c_int32), ("order_used", C.c_int32), ("n_tensors", C.c_int32),
-                ("workspace_c128", C.c_uint64), ("workspace_c64", C.c_uint64)]
+                ("workspace_c128", C.c_uint64), ("workspace_c64", C.c_uint64),
+                ("workspace_split", C.c_uint64)]
 
 
 _lib = None
@@ -89,8 +91,10 @@ def lib():
         "pk_plan_launches": [vp, i32, P(i64)],
         "pk_jones_from_z": [vp, i32, P(pk_scaled), P(pk_scaled)],
         "pk_plan_debug_blob": [vp, i32, vp, P(u64)],
-        "pk_profile": [vp, vp, i32, vp, u64, P(C.c_double)],
+        "pk_profile": [vp, vp, i32, vp, u64, vp, u64, P(C.c_double)],
         "pk_eval_noalloc": [vp, vp, i32, P(pk_scaled), P(pk_scaled)],
+        "pk_plan_state_bytes": [vp, i32, P(u64), P(u64)],
+        "pk_launch_arena": [vp, vp, i32, vp, u64, vp, u64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -221,8 +225,9 @@ class Knot:
 
 class Plan:
     def __init__(self, ctx: Context, knot: Knot, q: int, order: str = "auto",
-                 max_log2_elems: float = 0.0, max_log2_slices: float = 0.0, flags: int = 0):
-        o = pk_plan_opts(ORDERS[order], flags, max_log2_elems, max_log2_slices)
+                 max_log2_elems: float = 0.0, max_log2_slices: float = 0.0, flags: int = 0,
+                 tail_steps: int = 0):
+        o = pk_plan_opts(ORDERS[order], flags, max_log2_elems, max_log2_slices, tail_steps, 0)
         h = C.c_void_p()
         _check(lib().pk_plan_create(ctx.h, knot.h, q, C.byref(o), C.byref(h)), ctx)
         self.h = h
@@ -239,6 +244,12 @@ class Plan:
         b = C.c_uint64()
         _check(lib().pk_plan_workspace_bytes(self.h, PRECISIONS[precision], C.byref(b)))
         return b.value
+
+    def state_bytes(self, precision="c128"):
+        """(state bytes, arena bytes) of the workspace split (pk_plan_state_bytes)."""
+        s, a = C.c_uint64(), C.c_uint64()
+        _check(lib().pk_plan_state_bytes(self.h, PRECISIONS[precision], C.byref(s), C.byref(a)))
+        return s.value, a.value
 
     def launches(self, precision="c128") -> int:
         n = C.c_int64()
@@ -322,6 +333,13 @@ def launch(plan: Plan, precision: str, ws):
                            ws.numel()), plan.ctx)
 
 
+def launch_arena(plan: Plan, precision: str, state, arena):
+    """pk_launch_arena: the plan's state buffer and a (possibly shared) tensor arena."""
+    _check(lib().pk_launch_arena(plan.ctx.h, plan.h, PRECISIONS[precision],
+                                 C.c_void_p(state.data_ptr()), state.numel(),
+                                 C.c_void_p(arena.data_ptr()), arena.numel()), plan.ctx)
+
+
 def download(plan: Plan, precision: str, ws):
     z, v = pk_scaled(), pk_scaled()
     st = lib().pk_download(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
@@ -332,12 +350,15 @@ def download(plan: Plan, precision: str, ws):
     return Scaled.of(z), Scaled.of(v)
 
 
-def profile(plan: Plan, precision: str, ws):
-    """Per kernel class (build, rows, splitk, results): ms, launches, complex MACs, bytes
-    of one pass of the plan's kernels, timed with CUDA events on the context's stream."""
+def profile(plan: Plan, precision: str, ws, arena=None):
+    """Per kernel class (build, rows, splitk, results, gemm): ms, launches, complex MACs,
+    bytes of one pass of the plan's kernels, timed with CUDA events on the context's
+    stream.  `arena` (optional) is a separate tensor arena as for launch_arena()."""
     out = (C.c_double * 20)()
+    ap = C.c_void_p(arena.data_ptr()) if arena is not None else None
+    an = arena.numel() if arena is not None else 0
     _check(lib().pk_profile(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
-                            ws.numel(), out), plan.ctx)
+                            ws.numel(), ap, an, out), plan.ctx)
     names = ("build", "rows", "splitk", "results", "gemm")
     return {n: {"ms": out[i], "launches": out[5 + i], "cmacs": out[10 + i], "bytes": out[15 + i]}
             for i, n in enumerate(names)}

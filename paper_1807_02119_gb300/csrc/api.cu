@@ -9,13 +9,6 @@
 
 #include "pk_internal.h"
 
-namespace pk {
-template <typename R>
-cudaError_t launch_plan(const Plan& p, void* ws, cudaStream_t stream);
-template <typename R>
-cudaError_t profile_plan(const Plan& p, void* ws, cudaStream_t stream, double* out);
-}
-
 #include "handles.h"
 
 namespace {
@@ -28,7 +21,7 @@ pk_status cuda_fail(pk_ctx* c, cudaError_t e, const char* where) {
   return fail(c, PK_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 int elem_bytes(int32_t precision) { return precision == PK_C128 ? 16 : 8; }
-bool valid_precision(int32_t p) { return p == PK_C128 || p == PK_C64 || p == PK_SPLIT_TF32; }
+bool valid_precision(int32_t p) { return p == PK_C128 || p == PK_C64 || p == PK_SPLIT; }
 
 pk_scaled to_abi(const pk::Scaled& s) {
   pk_scaled r;
@@ -52,7 +45,7 @@ struct DeviceGuard {
 };
 
 pk_status check_ws(pk_ctx* ctx, const pk_plan* p, int32_t precision, void*& ws, uint64_t& bytes) {
-  uint64_t need = p->p.ws_bytes(elem_bytes(precision));
+  uint64_t need = p->p.ws_bytes(precision);
   if (ws == nullptr) {
     if (ctx->own_ws_bytes < need) {
       if (ctx->own_ws) {
@@ -225,14 +218,15 @@ pk_status pk_plan_info(const pk_plan* p, pk_plan_stats* out) {
   out->max_rank = P.max_rank;
   out->order_used = P.order_used;
   out->n_tensors = P.n_init;
-  out->workspace_c128 = P.ws_bytes(16);
-  out->workspace_c64 = P.ws_bytes(8);
+  out->workspace_c128 = P.ws_bytes(PK_C128);
+  out->workspace_c64 = P.ws_bytes(PK_C64);
+  out->workspace_split = P.ws_bytes(PK_SPLIT);
   return PK_OK;
 }
 
 pk_status pk_plan_workspace_bytes(const pk_plan* p, int32_t precision, uint64_t* bytes) {
   if (!p || !bytes || !valid_precision(precision)) return PK_EINVAL;
-  *bytes = p->p.ws_bytes(elem_bytes(precision));
+  *bytes = p->p.ws_bytes(precision);
   return PK_OK;
 }
 
@@ -271,11 +265,16 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
     buf.resize(8 * v.size());
     if (!v.empty()) std::memcpy(buf.data(), v.data(), buf.size());
   } else if (which == 3) {
-    int64_t v[10] = {P.q, P.n_init, (int64_t)P.steps.size(), P.n_slices, (int64_t)P.sliced.size(),
+    int64_t v[15] = {P.q, P.n_init, (int64_t)P.steps.size(), P.n_slices, (int64_t)P.sliced.size(),
                      P.final_tensor, (int64_t)P.off_recipe, (int64_t)P.off_slots,
-                     (int64_t)P.slots.size(), (int64_t)sizeof(pk::Step)};
+                     (int64_t)P.slots.size(), (int64_t)sizeof(pk::Step), P.tail_first,
+                     (int64_t)P.tail.size(), (int64_t)P.conv.size(), (int64_t)P.off_conv,
+                     P.final_tail_off};
     buf.resize(sizeof(v));
     std::memcpy(buf.data(), v, sizeof(v));
+  } else if (which == 5) {
+    buf.resize(sizeof(pk::TailStep) * P.tail.size());
+    if (!P.tail.empty()) std::memcpy(buf.data(), P.tail.data(), buf.size());
   } else if (which == 4) {
     double v[3] = {P.factor.re, P.factor.im, (double)P.factor.e};
     buf.resize(sizeof(v));
@@ -294,7 +293,8 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
 pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launches) {
   if (!p || !launches || !valid_precision(precision)) return PK_EINVAL;
   const pk::Plan& P = p->p;
-  *launches = P.n_slices * ((P.n_init > 0 ? 1 : 0) + (int64_t)P.steps.size() + 1) + 1;
+  const int64_t widen = (precision == PK_SPLIT && !P.conv.empty()) ? 1 : 0;
+  *launches = P.n_slices * ((P.n_init > 0 ? 1 : 0) + (int64_t)P.steps.size() + 1 + widen) + 1;
   return PK_OK;
 }
 
@@ -309,7 +309,11 @@ pk_status pk_upload(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_wo
   if (!ctx || !p || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
   if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
   DeviceGuard g(ctx->device);
-  pk_status s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
+  pk_status s = PK_OK;
+  if (d_workspace == nullptr)
+    s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
+  else if (workspace_bytes < p->p.off_arena)
+    s = fail(ctx, PK_ENOMEM, "buffer smaller than the plan state (pk_plan_state_bytes)");
   if (s != PK_OK) return s;
   const pk::Plan& P = p->p;
   if (P.program.empty()) return PK_OK;
@@ -332,22 +336,58 @@ pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_wo
   DeviceGuard g(ctx->device);
   pk_status s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
   if (s != PK_OK) return s;
-  cudaError_t e = precision == PK_C128 ? pk::launch_plan<double>(p->p, d_workspace, ctx->stream)
-                                       : pk::launch_plan<float>(p->p, d_workspace, ctx->stream);
+  cudaError_t e = pk::launch_plan(p->p, precision, d_workspace,
+                                  (char*)d_workspace + p->p.off_arena, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
+  return PK_OK;
+}
+
+static pk_status check_split(pk_ctx* ctx, const pk_plan* p, int32_t precision, const void* state,
+                             uint64_t state_bytes, const void* arena, uint64_t arena_bytes) {
+  const uint64_t need_state = p->p.off_arena;
+  const uint64_t need_arena = p->p.ws_bytes(precision) - p->p.off_arena;
+  if (!state || !arena) return fail(ctx, PK_EINVAL, "null state or arena");
+  if (state_bytes < need_state || arena_bytes < need_arena)
+    return fail(ctx, PK_ENOMEM, "state or arena smaller than pk_plan_state_bytes");
+  if ((((uintptr_t)state) & 255u) || (((uintptr_t)arena) & 255u))
+    return fail(ctx, PK_EINVAL, "state and arena must be 256-byte aligned");
+  return PK_OK;
+}
+
+pk_status pk_plan_state_bytes(const pk_plan* p, int32_t precision, uint64_t* state_bytes,
+                              uint64_t* arena_bytes) {
+  if (!p || !state_bytes || !arena_bytes || !valid_precision(precision)) return PK_EINVAL;
+  *state_bytes = p->p.off_arena;
+  *arena_bytes = p->p.ws_bytes(precision) - p->p.off_arena;
+  return PK_OK;
+}
+
+pk_status pk_launch_arena(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_state,
+                          uint64_t state_bytes, void* d_arena, uint64_t arena_bytes) {
+  if (!ctx || !p || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  pk_status s = check_split(ctx, p, precision, d_state, state_bytes, d_arena, arena_bytes);
+  if (s != PK_OK) return s;
+  cudaError_t e = pk::launch_plan(p->p, precision, d_state, d_arena, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
   return PK_OK;
 }
 
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
-                     uint64_t workspace_bytes, double* out) {
+                     uint64_t workspace_bytes, void* d_arena, uint64_t arena_bytes, double* out) {
   if (!ctx || !p || !out || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
   if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
   DeviceGuard g(ctx->device);
-  pk_status s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
+  pk_status s;
+  if (d_arena == nullptr) {
+    s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
+    d_arena = (char*)d_workspace + p->p.off_arena;
+  } else {
+    s = check_split(ctx, p, precision, d_workspace, workspace_bytes, d_arena, arena_bytes);
+  }
   if (s != PK_OK) return s;
-  cudaError_t e = precision == PK_C128
-                      ? pk::profile_plan<double>(p->p, d_workspace, ctx->stream, out)
-                      : pk::profile_plan<float>(p->p, d_workspace, ctx->stream, out);
+  cudaError_t e = pk::profile_plan(p->p, precision, d_workspace, d_arena, ctx->stream, out);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "profile");
   return PK_OK;
 }

@@ -23,3 +23,13 @@ struct pk_plan {
   pk::Plan p;
   uint8_t* pinned_program = nullptr;
 };
+
+namespace pk {
+// Enqueue every kernel of every slice of `p` at `precision` on `stream` (launch.cu);
+// `ws` holds the plan state (bytes [0, off_arena)), `arena` the tensors.
+cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,
+                        cudaStream_t stream);
+// Same, with CUDA-event timing per kernel class; waits for the stream (launch.cu).
+cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,
+                         cudaStream_t stream, double* out);
+}  // namespace pk

@@ -1,5 +1,5 @@
-// Device kernels of the contraction (Sec. III): building the initial tensors of G_T,
-// one pairwise contraction step, and the per-slice / all-slice results.
+// Device kernels of the contraction (Sec. III), included by launch.cu: initial tensors
+// of G_T, one pairwise contraction step, and the per-slice / all-slice results.
 //
 // A step computes C[b, m, n] = sum_k A[b, m, k] B[b, k, n] where b (batch) are indices
 // kept in both operands, m kept only in A, n kept only in B, and k summed.  The
@@ -8,9 +8,15 @@
 // the store (no separate transpose pass).  C is written as [n-part, row-part] with the
 // row part (b and m, in A's order) innermost and contiguous.
 //
+// Storage types R: double (complex128), float (complex64) and ff (complex "split FP32":
+// each real number is an unevaluated float pair hi + lo, |lo| <= ulp(hi)/2, computed
+// with exact FMA two-products and TwoSum additions -- about 48 significant bits on the
+// FP32 units).
+//
 // Scaling: a stored tensor x stands for x * 2^exp.  A step multiplies its products by
 // 2^-(eA+eB), eX being the binary exponent of max|X| (so operands enter at magnitude
 // below 1), and records exp(C) = exp(A) + exp(B) + eA + eB.  Powers of two are exact.
+#pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,49 +27,160 @@
 
 namespace pk {
 
+struct ff {
+  float hi, lo;
+};
+
 template <typename R>
 struct Cx {
   R re, im;
 };
+
+// S: the scalar type of magnitudes and scale factors for a storage type
 template <typename R>
-struct VecOf;
-template <>
-struct VecOf<double> {
-  using T = double2;
+struct Traits {
+  using S = R;
 };
 template <>
-struct VecOf<float> {
-  using T = float2;
+struct Traits<ff> {
+  using S = float;
 };
 
+// ---- float-float arithmetic (Dekker / Knuth error-free transformations)
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ ff ff_norm(float hi, float lo) {
+  float s = __fadd_rn(hi, lo);
+  return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+// a * b for float-float a, b: the exact product of the high parts plus the cross terms
+__device__ __forceinline__ void ff_mul(const ff& a, const ff& b, float& p, float& e) {
+  two_prod(a.hi, b.hi, p, e);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+}
+// (hi, lo) += (p, e)
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float p, float e) {
+  float s, err;
+  two_sum(hi, p, s, err);
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+  hi = s;
+}
+
+// ---- loads, stores, conversions
 template <typename R>
-__device__ __forceinline__ Cx<R> ld(const Cx<R>* p) {
-  typename VecOf<R>::T v = __ldg(reinterpret_cast<const typename VecOf<R>::T*>(p));
+__device__ __forceinline__ Cx<R> ld(const Cx<R>* p);
+template <>
+__device__ __forceinline__ Cx<double> ld(const Cx<double>* p) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(p));
   return {v.x, v.y};
 }
-template <typename R>
-__device__ __forceinline__ void st(Cx<R>* p, Cx<R> x) {
-  typename VecOf<R>::T v;
-  v.x = x.re;
-  v.y = x.im;
-  *reinterpret_cast<typename VecOf<R>::T*>(p) = v;
+template <>
+__device__ __forceinline__ Cx<float> ld(const Cx<float>* p) {
+  float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
 }
+template <>
+__device__ __forceinline__ Cx<ff> ld(const Cx<ff>* p) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ void st(Cx<double>* p, Cx<double> x) {
+  *reinterpret_cast<double2*>(p) = make_double2(x.re, x.im);
+}
+__device__ __forceinline__ void st(Cx<float>* p, Cx<float> x) {
+  *reinterpret_cast<float2*>(p) = make_float2(x.re, x.im);
+}
+__device__ __forceinline__ void st(Cx<ff>* p, Cx<ff> x) {
+  *reinterpret_cast<float4*>(p) = make_float4(x.re.hi, x.re.lo, x.im.hi, x.im.lo);
+}
+
 template <typename R>
-__device__ __forceinline__ void cmac(Cx<R>& acc, const Cx<R>& a, const Cx<R>& b) {
+__device__ __forceinline__ R from_double(double x) {
+  return (R)x;
+}
+template <>
+__device__ __forceinline__ ff from_double<ff>(double x) {
+  float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return (double)x; }
+__device__ __forceinline__ double to_double(ff x) { return (double)x.hi + (double)x.lo; }
+
+template <typename R>
+__device__ __forceinline__ Cx<R> czero() {
+  return {from_double<R>(0.0), from_double<R>(0.0)};
+}
+// max(|re|, |im|) in the scalar type (the high part for float-float)
+__device__ __forceinline__ double mag(const Cx<double>& v) { return fmax(fabs(v.re), fabs(v.im)); }
+__device__ __forceinline__ float mag(const Cx<float>& v) { return fmaxf(fabsf(v.re), fabsf(v.im)); }
+__device__ __forceinline__ float mag(const Cx<ff>& v) { return fmaxf(fabsf(v.re.hi), fabsf(v.im.hi)); }
+
+__device__ __forceinline__ void cmac(Cx<double>& acc, const Cx<double>& a, const Cx<double>& b) {
   acc.re = fma(a.re, b.re, acc.re);
   acc.re = fma(-a.im, b.im, acc.re);
   acc.im = fma(a.re, b.im, acc.im);
   acc.im = fma(a.im, b.re, acc.im);
 }
+__device__ __forceinline__ void cmac(Cx<float>& acc, const Cx<float>& a, const Cx<float>& b) {
+  acc.re = fmaf(a.re, b.re, acc.re);
+  acc.re = fmaf(-a.im, b.im, acc.re);
+  acc.im = fmaf(a.re, b.im, acc.im);
+  acc.im = fmaf(a.im, b.re, acc.im);
+}
 
+// ---- accumulators: plain in the storage precision, or float-float
+template <typename R>
+struct Acc {
+  Cx<R> v{0, 0};
+  __device__ __forceinline__ void mac(const Cx<R>& a, const Cx<R>& b) { cmac(v, a, b); }
+  __device__ __forceinline__ void add(const Cx<R>& a) {
+    v.re += a.re;
+    v.im += a.im;
+  }
+  __device__ __forceinline__ Cx<R> get(R scale) const { return {v.re * scale, v.im * scale}; }
+};
+template <>
+struct Acc<ff> {
+  float rh = 0, rl = 0, ih = 0, il = 0;
+  __device__ __forceinline__ void mac(const Cx<ff>& a, const Cx<ff>& b) {
+    float p, e;
+    ff_mul(a.re, b.re, p, e);
+    ff_acc(rh, rl, p, e);
+    ff_mul(a.im, b.im, p, e);
+    ff_acc(rh, rl, -p, -e);
+    ff_mul(a.re, b.im, p, e);
+    ff_acc(ih, il, p, e);
+    ff_mul(a.im, b.re, p, e);
+    ff_acc(ih, il, p, e);
+  }
+  __device__ __forceinline__ void add(const Cx<ff>& a) {
+    ff_acc(rh, rl, a.re.hi, a.re.lo);
+    ff_acc(ih, il, a.im.hi, a.im.lo);
+  }
+  __device__ __forceinline__ Cx<ff> get(float scale) const {  // scale: a power of two
+    ff r = ff_norm(rh, rl), i = ff_norm(ih, il);
+    return {{r.hi * scale, r.lo * scale}, {i.hi * scale, i.lo * scale}};
+  }
+};
+
+// ---- bookkeeping
 __device__ __forceinline__ unsigned long long max_bits(double m) {
   return (unsigned long long)__double_as_longlong(m);
 }
 __device__ __forceinline__ unsigned long long max_bits(float m) {
   return (unsigned long long)__float_as_uint(m);
 }
-template <typename R>
-__device__ __forceinline__ R bits_to_val(unsigned long long b);
+template <typename S>
+__device__ __forceinline__ S bits_to_val(unsigned long long b);
 template <>
 __device__ __forceinline__ double bits_to_val<double>(unsigned long long b) {
   return __longlong_as_double((long long)b);
@@ -74,37 +191,39 @@ __device__ __forceinline__ float bits_to_val<float>(unsigned long long b) {
 }
 
 // binary exponent e with m * 2^-e in [0.5, 1); 0 for m == 0
-template <typename R>
-__device__ __forceinline__ int bin_exp(R m) {
-  if (!(m > R(0))) return 0;
+template <typename S>
+__device__ __forceinline__ int bin_exp(S m) {
+  if (!(m > S(0))) return 0;
   int e;
   frexp(m, &e);
   return e;
 }
 
-template <typename R>
-__device__ __forceinline__ void block_max_to_meta(R v, Meta* meta) {
-  __shared__ R red[32];
+template <typename S>
+__device__ __forceinline__ void block_max_to_meta(S v, Meta* meta) {
+  __shared__ S red[32];
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) red[w] = v;
   __syncthreads();
   if (w == 0) {
     int nw = (blockDim.x + 31) >> 5;
-    v = lane < nw ? red[lane] : R(0);
+    v = lane < nw ? red[lane] : S(0);
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0 && v > R(0)) atomicMax(&meta->maxbits, max_bits(v));
+    if (lane == 0 && v > S(0)) atomicMax(&meta->maxbits, max_bits(v));
   }
 }
 
 // ------------------------------------------------------------------ initial tensors
-// One grid row (blockIdx.y) per initial tensor; entry = sum_{s<q} prod_j f_j(s, x_j).
+// One grid row (blockIdx.y) per initial tensor; entry = sum_{s<q} prod_j f_j(s, x_j),
+// formed in double and rounded once to the storage type.
 template <typename R>
 __global__ void __launch_bounds__(256) k_build(const Recipe* __restrict__ rec,
                                                const Slot* __restrict__ slots, Cx<R>* arena,
                                                Meta* meta, int q, long long slice, int n_sliced) {
+  using S = typename Traits<R>::S;
   const Recipe r = rec[blockIdx.y];
-  R vmax = 0;
+  S vmax = 0;
   int sdig[64];
   {
     long long s = slice;
@@ -150,9 +269,9 @@ __global__ void __launch_bounds__(256) k_build(const Recipe* __restrict__ rec,
         }
       }
     }
-    Cx<R> v{(R)sre, (R)sim};
+    const Cx<R> v{from_double<R>(sre), from_double<R>(sim)};
     st(arena + r.offset + e, v);
-    vmax = fmax(vmax, fmax(fabs(v.re), fabs(v.im)));
+    vmax = fmax(vmax, mag(v));
   }
   block_max_to_meta(vmax, meta + r.meta);
 }
@@ -185,17 +304,17 @@ __device__ __forceinline__ void split_runs32(unsigned x, const Run* runs, int n,
 }
 
 // scale = 2^-(eA+eB); when write_exp, also records exp(C) = exp(A) + exp(B) + eA + eB
-template <typename R>
-__device__ __forceinline__ R step_scale(const Step& s, Meta* meta, bool write_exp) {
-  int ea = bin_exp(bits_to_val<R>(meta[s.a].maxbits));
+template <typename S>
+__device__ __forceinline__ S step_scale(const Step& s, Meta* meta, bool write_exp) {
+  int ea = bin_exp(bits_to_val<S>(meta[s.a].maxbits));
   int eb = 0;
   long long xb = 0;
   if (s.b >= 0) {
-    eb = bin_exp(bits_to_val<R>(meta[s.b].maxbits));
+    eb = bin_exp(bits_to_val<S>(meta[s.b].maxbits));
     xb = meta[s.b].exp;
   }
   if (write_exp) meta[s.c].exp = meta[s.a].exp + xb + ea + eb;
-  return (R)ldexp(1.0, -(ea + eb));
+  return (S)ldexp(1.0, -(ea + eb));
 }
 
 // Thread per output row r (batch x free-of-A): the K values A[r, :] are loaded once
@@ -203,6 +322,7 @@ __device__ __forceinline__ R step_scale(const Step& s, Meta* meta, bool write_ex
 // (read through the L1/texture path: it is small or shared across the warp).
 template <typename R, int KREG>
 __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* meta) {
+  using S = typename Traits<R>::S;
   extern __shared__ long long sm[];
   long long* kA = sm;
   long long* kB = sm + s.K;
@@ -212,7 +332,7 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
     long long dummy;
     split_runs(n, s.nr, s.nn, dummy, nB[n]);
   }
-  const R scale = step_scale<R>(s, meta, blockIdx.x == 0 && threadIdx.x == 0);
+  const S scale = step_scale<S>(s, meta, blockIdx.x == 0 && threadIdx.x == 0);
   __syncthreads();
   const Cx<R>* A = arena + s.off_a;
   const Cx<R>* B = arena + s.off_b;
@@ -220,7 +340,7 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
   const bool hasB = s.b >= 0;
   const int K = (int)s.K, N = (int)s.N;
   const unsigned R_ = (unsigned)s.R;
-  R vmax = 0;
+  S vmax = 0;
   for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < R_; r += gridDim.x * blockDim.x) {
     long long oa, ob;
     split_runs32(r, s.row, s.nrow, oa, ob);
@@ -230,42 +350,35 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
       for (int k = 0; k < KREG; ++k)
         if (k < K) a[k] = ld(A + oa + kA[k]);
       for (int n = 0; n < N; ++n) {
-        Cx<R> acc{0, 0};
+        Acc<R> acc;
         if (hasB) {
           const Cx<R>* Bn = B + ob + nB[n];
 #pragma unroll
           for (int k = 0; k < KREG; ++k)
-            if (k < K) cmac(acc, a[k], ld(Bn + kB[k]));
+            if (k < K) acc.mac(a[k], ld(Bn + kB[k]));
         } else {
 #pragma unroll
           for (int k = 0; k < KREG; ++k)
-            if (k < K) {
-              acc.re += a[k].re;
-              acc.im += a[k].im;
-            }
+            if (k < K) acc.add(a[k]);
         }
-        acc.re *= scale;
-        acc.im *= scale;
-        st(C + (long long)n * R_ + r, acc);
-        vmax = fmax(vmax, fmax(fabs(acc.re), fabs(acc.im)));
+        const Cx<R> v = acc.get(scale);
+        st(C + (long long)n * R_ + r, v);
+        vmax = fmax(vmax, mag(v));
       }
     } else {
       for (int n = 0; n < N; ++n) {
-        Cx<R> acc{0, 0};
+        Acc<R> acc;
         const Cx<R>* Bn = B + ob + (hasB ? nB[n] : 0);
         for (int k = 0; k < K; ++k) {
           Cx<R> av = ld(A + oa + kA[k]);
           if (hasB)
-            cmac(acc, av, ld(Bn + kB[k]));
-          else {
-            acc.re += av.re;
-            acc.im += av.im;
-          }
+            acc.mac(av, ld(Bn + kB[k]));
+          else
+            acc.add(av);
         }
-        acc.re *= scale;
-        acc.im *= scale;
-        st(C + (long long)n * R_ + r, acc);
-        vmax = fmax(vmax, fmax(fabs(acc.re), fabs(acc.im)));
+        const Cx<R> v = acc.get(scale);
+        st(C + (long long)n * R_ + r, v);
+        vmax = fmax(vmax, mag(v));
       }
     }
   }
@@ -276,35 +389,33 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
 // offset is recomputed from the stride runs.
 template <typename R>
 __global__ void __launch_bounds__(256) k_rows_big(const Step s, Cx<R>* arena, Meta* meta) {
-  const R scale = step_scale<R>(s, meta, blockIdx.x == 0 && threadIdx.x == 0);
+  using S = typename Traits<R>::S;
+  const S scale = step_scale<S>(s, meta, blockIdx.x == 0 && threadIdx.x == 0);
   const Cx<R>* A = arena + s.off_a;
   const Cx<R>* B = arena + s.off_b;
   Cx<R>* C = arena + s.off_c;
   const bool hasB = s.b >= 0;
   const unsigned R_ = (unsigned)s.R;
-  R vmax = 0;
+  S vmax = 0;
   for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < R_; r += gridDim.x * blockDim.x) {
     long long oa, ob;
     split_runs32(r, s.row, s.nrow, oa, ob);
     for (long long n = 0; n < s.N; ++n) {
       long long dummy, nb = 0;
       if (hasB) split_runs((unsigned long long)n, s.nr, s.nn, dummy, nb);
-      Cx<R> acc{0, 0};
+      Acc<R> acc;
       for (long long k = 0; k < s.K; ++k) {
         long long ka, kb;
         split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
         Cx<R> av = ld(A + oa + ka);
-        if (hasB) {
-          cmac(acc, av, ld(B + ob + nb + kb));
-        } else {
-          acc.re += av.re;
-          acc.im += av.im;
-        }
+        if (hasB)
+          acc.mac(av, ld(B + ob + nb + kb));
+        else
+          acc.add(av);
       }
-      acc.re *= scale;
-      acc.im *= scale;
-      st(C + n * (long long)R_ + r, acc);
-      vmax = fmax(vmax, fmax(fabs(acc.re), fabs(acc.im)));
+      const Cx<R> v = acc.get(scale);
+      st(C + n * (long long)R_ + r, v);
+      vmax = fmax(vmax, mag(v));
     }
   }
   block_max_to_meta(vmax, meta + s.c);
@@ -315,7 +426,7 @@ __global__ void __launch_bounds__(256) k_rows_big(const Step s, Cx<R>* arena, Me
 // K in chunks of 16.  Operand tiles are gathered through the stride runs (the index
 // permutation) into shared memory, coalesced along whichever of m/k (A) or k/n (B) is
 // unit-stride in memory; each of the 256 threads accumulates a 4 x 4 block of complex
-// outputs in registers (4 real FMAs per complex multiply-add).
+// outputs in registers.
 __device__ __forceinline__ void runs4(long long x, const Run4* r, int n, long long& oa,
                                       long long& ob, long long& oc) {
   oa = ob = oc = 0;
@@ -331,6 +442,7 @@ __device__ __forceinline__ void runs4(long long x, const Run4* r, int n, long lo
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_gemm(const Step s, Cx<R>* arena, Meta* meta) {
+  using S = typename Traits<R>::S;
   constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, LDA = BM + 1, LDB = BN + 1;
   __shared__ Cx<R> As[BK * LDA];
   __shared__ Cx<R> Bs[BK * LDB];
@@ -364,15 +476,11 @@ __global__ void __launch_bounds__(256) k_gemm(const Step s, Cx<R>* arena, Meta* 
       cn[j] = -1;
     }
   }
-  const R scale = step_scale<R>(s, meta, blockIdx.x == 0 && tid == 0);
+  const S scale = step_scale<S>(s, meta, blockIdx.x == 0 && tid == 0);
   __syncthreads();
   const Cx<R>* A = arena + s.off_a + base[0];
   const Cx<R>* B = arena + s.off_b + base[1];
-  Cx<R> acc[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = {0, 0};
+  Acc<R> acc[TM][TN];
   const int tx = tid & 15, ty = tid >> 4;
   for (long long k0 = 0; k0 < s.K; k0 += BK) {
     if (tid < BK) {
@@ -398,7 +506,7 @@ __global__ void __launch_bounds__(256) k_gemm(const Step s, Cx<R>* arena, Meta* 
         i = idx % BM;
         j = idx / BM;
       }
-      Cx<R> v{0, 0};
+      Cx<R> v = czero<R>();
       if (am[i] >= 0 && ak[j] >= 0) v = ld(A + am[i] + ak[j]);
       As[j * LDA + i] = v;
     }
@@ -412,7 +520,7 @@ __global__ void __launch_bounds__(256) k_gemm(const Step s, Cx<R>* arena, Meta* 
         j = idx % BN;
         kk = idx / BN;
       }
-      Cx<R> v{0, 0};
+      Cx<R> v = czero<R>();
       if (bn[j] >= 0 && bk[kk] >= 0) v = ld(B + bk[kk] + bn[j]);
       Bs[kk * LDB + j] = v;
     }
@@ -427,12 +535,12 @@ __global__ void __launch_bounds__(256) k_gemm(const Step s, Cx<R>* arena, Meta* 
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) cmac(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TN; ++j) acc[i][j].mac(a[i], b[j]);
     }
     __syncthreads();
   }
   Cx<R>* C = arena + s.off_c + base[2];
-  R vmax = 0;
+  S vmax = 0;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int mi = tx * TM + i;
@@ -441,20 +549,21 @@ __global__ void __launch_bounds__(256) k_gemm(const Step s, Cx<R>* arena, Meta* 
     for (int j = 0; j < TN; ++j) {
       const int nj = ty * TN + j;
       if (cn[nj] < 0) continue;
-      Cx<R> v{acc[i][j].re * scale, acc[i][j].im * scale};
+      const Cx<R> v = acc[i][j].get(scale);
       st(C + cm[mi] + cn[nj], v);
-      vmax = fmax(vmax, fmax(fabs(v.re), fabs(v.im)));
+      vmax = fmax(vmax, mag(v));
     }
   }
   block_max_to_meta(vmax, meta + s.c);
 }
 
-// Few outputs, long K: block (chunk, output) sums its slice of K; the last block to
-// finish (ticket counter) adds the partials of every output in chunk order, so the
-// result does not depend on scheduling.
+// Few outputs, long K: block (chunk, output) sums its slice of K in double; the last
+// block to finish (ticket counter) adds the partials of every output in chunk order,
+// so the result does not depend on scheduling.
 template <typename R>
 __global__ void __launch_bounds__(256) k_splitk(const Step s, Cx<R>* arena, Meta* meta,
                                                 Cx<double>* partial, unsigned* counter) {
+  using S = typename Traits<R>::S;
   const int chunks = s.chunks;
   const long long o = blockIdx.y;
   const long long r = o % s.R, n = o / s.R;
@@ -465,29 +574,31 @@ __global__ void __launch_bounds__(256) k_splitk(const Step s, Cx<R>* arena, Meta
   const long long k0 = (long long)blockIdx.x * per, k1 = min((long long)s.K, k0 + per);
   const Cx<R>* A = arena + s.off_a;
   const Cx<R>* B = arena + s.off_b + ob + nb;
-  Cx<double> acc{0, 0};
+  double are = 0, aim = 0;
   for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     long long ka, kb;
     split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
-    Cx<R> av = ld(A + oa + ka);
+    const Cx<R> av = ld(A + oa + ka);
+    const double xr = to_double(av.re), xi = to_double(av.im);
     if (s.b >= 0) {
-      Cx<R> bv = ld(B + kb);
-      acc.re += (double)av.re * bv.re - (double)av.im * bv.im;
-      acc.im += (double)av.re * bv.im + (double)av.im * bv.re;
+      const Cx<R> bv = ld(B + kb);
+      const double yr = to_double(bv.re), yi = to_double(bv.im);
+      are += xr * yr - xi * yi;
+      aim += xr * yi + xi * yr;
     } else {
-      acc.re += av.re;
-      acc.im += av.im;
+      are += xr;
+      aim += xi;
     }
   }
   __shared__ double rr[32], ri[32];
   for (int off = 16; off > 0; off >>= 1) {
-    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
-    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+    are += __shfl_xor_sync(0xffffffffu, are, off);
+    aim += __shfl_xor_sync(0xffffffffu, aim, off);
   }
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
-    rr[w] = acc.re;
-    ri[w] = acc.im;
+    rr[w] = are;
+    ri[w] = aim;
   }
   __syncthreads();
   __shared__ bool last;
@@ -499,16 +610,16 @@ __global__ void __launch_bounds__(256) k_splitk(const Step s, Cx<R>* arena, Meta
     }
     partial[o * chunks + blockIdx.x] = {tre, tim};
     __threadfence();
-    unsigned t = atomicAdd(counter, 1u);
-    last = (t == gridDim.x * gridDim.y - 1);
+    unsigned tk = atomicAdd(counter, 1u);
+    last = (tk == gridDim.x * gridDim.y - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  const R scale = step_scale<R>(s, meta, threadIdx.x == 0);
+  const S scale = step_scale<S>(s, meta, threadIdx.x == 0);
   Cx<R>* C = arena + s.off_c;
   const long long outs = s.R * s.N;
-  R vmax = 0;
+  S vmax = 0;
   for (long long oo = threadIdx.x; oo < outs; oo += blockDim.x) {
     double tre = 0, tim = 0;
     const volatile double* pp = (const volatile double*)partial;
@@ -517,9 +628,9 @@ __global__ void __launch_bounds__(256) k_splitk(const Step s, Cx<R>* arena, Meta
       tim += pp[2 * (oo * chunks + c) + 1];
     }
     // C is laid out [n, r] with r innermost: output o = r + n * R, the same linear index
-    Cx<R> v{(R)(tre * (double)scale), (R)(tim * (double)scale)};
+    const Cx<R> v{from_double<R>(tre * (double)scale), from_double<R>(tim * (double)scale)};
     st(C + oo, v);
-    vmax = fmax(vmax, fmax(fabs(v.re), fabs(v.im)));
+    vmax = fmax(vmax, mag(v));
   }
   block_max_to_meta(vmax, meta + s.c);
   if (threadIdx.x == 0) *counter = 0u;
@@ -530,9 +641,9 @@ template <typename R>
 __global__ void k_slice_result(const Cx<R>* arena, long long off, const Meta* meta, int tensor,
                                SliceResult* out, long long slice) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  Cx<R> v = arena[off];
-  out[slice].re = (double)v.re;
-  out[slice].im = (double)v.im;
+  const Cx<R> v = arena[off];
+  out[slice].re = to_double(v.re);
+  out[slice].im = to_double(v.im);
   out[slice].exp = meta[tensor].exp;
 }
 
@@ -585,172 +696,5 @@ __global__ void k_sum_slices(SliceResult* res, long long n) {
     res[n].exp = emax == LLONG_MIN ? 0 : emax;
   }
 }
-
-// ------------------------------------------------------------------ launchers
-namespace {
-template <typename R>
-size_t rows_smem(const Step& s) {
-  return sizeof(long long) * (size_t)(2 * s.K + s.N);
-}
-
-template <typename R>
-cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st) {
-  size_t sm = rows_smem<R>(s);
-  long long blocks = (s.R + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  if (blocks < 1) blocks = 1;
-  if (sm > 200 * 1024) {
-    k_rows_big<R><<<(unsigned)blocks, 256, 0, st>>>(s, arena, meta);
-    return cudaGetLastError();
-  }
-  int kmax = sizeof(R) == 8 ? 16 : 32;
-  const int K = (int)s.K;
-  void (*fn)(const Step, Cx<R>*, Meta*);
-  if (K <= 1)
-    fn = k_rows<R, 1>;
-  else if (K <= 2)
-    fn = k_rows<R, 2>;
-  else if (K <= 4)
-    fn = k_rows<R, 4>;
-  else if (K <= 8)
-    fn = k_rows<R, 8>;
-  else if (K <= 16)
-    fn = k_rows<R, 16>;
-  else if (K <= kmax)
-    fn = k_rows<R, 32>;
-  else
-    fn = k_rows<R, 0>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  fn<<<(unsigned)blocks, 256, sm, st>>>(s, arena, meta);
-  return cudaGetLastError();
-}
-}  // namespace
-
-// Enqueues every kernel of every slice.  With `prof` set, an event pair brackets each
-// launch and per-class milliseconds / counts / algorithmic work are accumulated.
-constexpr int kNumClasses = 5;  // build, rows, split-K, results, GEMM
-struct Prof {
-  double ms[kNumClasses] = {}, n[kNumClasses] = {}, cmacs[kNumClasses] = {},
-         bytes[kNumClasses] = {};
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-  std::vector<int> cls;
-};
-
-template <typename R>
-cudaError_t launch_plan_impl(const Plan& p, void* ws, cudaStream_t stream, Prof* prof) {
-  char* base = (char*)ws;
-  Cx<R>* arena = (Cx<R>*)(base + p.off_arena);
-  Meta* meta = (Meta*)(base + p.off_meta);
-  const Recipe* rec = (const Recipe*)(base + p.off_recipe);
-  const Slot* slots = (const Slot*)(base + p.off_slots);
-  SliceResult* res = (SliceResult*)(base + p.off_result);
-  Cx<double>* partial = (Cx<double>*)(base + p.off_scratch);
-  unsigned* counters = (unsigned*)(base + p.off_counter);
-  if (p.n_init > 65535) return cudaErrorInvalidValue;
-  int64_t maxel = 1, initel = 0;
-  for (const auto& r : p.recipes) {
-    maxel = std::max<int64_t>(maxel, r.elems);
-    initel += r.elems;
-  }
-  unsigned bx = (unsigned)std::min<int64_t>((maxel + 255) / 256, 64);
-  const double eb = (double)sizeof(Cx<R>);
-  auto mark = [&](int c, double cm, double by, bool begin) -> cudaError_t {
-    if (!prof) return cudaSuccess;
-    if (begin) {
-      cudaEvent_t a, b;
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
-      prof->ev.push_back({a, b});
-      prof->cls.push_back(c);
-      prof->n[c] += 1;
-      prof->cmacs[c] += cm;
-      prof->bytes[c] += by;
-      return cudaEventRecord(a, stream);
-    }
-    return cudaEventRecord(prof->ev.back().second, stream);
-  };
-  cudaError_t e;
-  for (long long sl = 0; sl < p.n_slices; ++sl) {
-    e = cudaMemsetAsync(base + p.off_meta, 0, p.off_result - p.off_meta, stream);
-    if (e != cudaSuccess) return e;
-    if (p.n_init > 0) {
-      mark(0, 0, eb * (double)initel, true);
-      k_build<R><<<dim3(bx, (unsigned)p.n_init), 256, 0, stream>>>(
-          rec, slots, arena, meta, p.q, sl, (int)p.sliced.size());
-      mark(0, 0, 0, false);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    }
-    for (size_t i = 0; i < p.steps.size(); ++i) {
-      const Step& s = p.steps[i];
-      const double cm = (double)s.R * (double)s.K * (double)s.N;
-      const double by = eb * (double)(p.tensors[s.a].elems + (s.b >= 0 ? p.tensors[s.b].elems : 0) +
-                                      p.tensors[s.c].elems);
-      const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
-      if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
-        mark(4, cm, by, true);
-        k_gemm<R><<<(unsigned)gemm_tiles, 256, 0, stream>>>(s, arena, meta);
-        mark(4, 0, 0, false);
-        e = cudaGetLastError();
-      } else if (s.kernel == KSPLITK) {
-        mark(2, cm, by, true);
-        k_splitk<R><<<dim3((unsigned)s.chunks, (unsigned)(s.R * s.N)), 256, 0, stream>>>(
-            s, arena, meta, partial, counters + i);
-        mark(2, 0, 0, false);
-        e = cudaGetLastError();
-      } else {
-        mark(1, cm, by, true);
-        e = launch_rows<R>(s, arena, meta, stream);
-        mark(1, 0, 0, false);
-      }
-      if (e != cudaSuccess) return e;
-    }
-    mark(3, 0, 0, true);
-    k_slice_result<R><<<1, 32, 0, stream>>>(arena, p.tensors[p.final_tensor].offset, meta,
-                                            p.final_tensor, res, sl);
-    mark(3, 0, 0, false);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  mark(3, 0, 0, true);
-  k_sum_slices<<<1, 256, 0, stream>>>(res, p.n_slices);
-  mark(3, 0, 0, false);
-  return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_plan(const Plan& p, void* ws, cudaStream_t stream) {
-  return launch_plan_impl<R>(p, ws, stream, nullptr);
-}
-
-template <typename R>
-cudaError_t profile_plan(const Plan& p, void* ws, cudaStream_t stream, double* out) {
-  Prof prof;
-  cudaError_t e = launch_plan_impl<R>(p, ws, stream, &prof);
-  cudaError_t e2 = cudaStreamSynchronize(stream);
-  if (e == cudaSuccess) e = e2;
-  for (size_t i = 0; i < prof.ev.size(); ++i) {
-    float ms = 0;
-    if (e == cudaSuccess) cudaEventElapsedTime(&ms, prof.ev[i].first, prof.ev[i].second);
-    prof.ms[prof.cls[i]] += ms;
-    cudaEventDestroy(prof.ev[i].first);
-    cudaEventDestroy(prof.ev[i].second);
-  }
-  for (int c = 0; c < kNumClasses; ++c) {
-    out[c] = prof.ms[c];
-    out[kNumClasses + c] = prof.n[c];
-    out[2 * kNumClasses + c] = prof.cmacs[c];
-    out[3 * kNumClasses + c] = prof.bytes[c];
-  }
-  return e;
-}
-template cudaError_t profile_plan<double>(const Plan&, void*, cudaStream_t, double*);
-template cudaError_t profile_plan<float>(const Plan&, void*, cudaStream_t, double*);
-
-template cudaError_t launch_plan<double>(const Plan&, void*, cudaStream_t);
-template cudaError_t launch_plan<float>(const Plan&, void*, cudaStream_t);
 
 }  // namespace pk

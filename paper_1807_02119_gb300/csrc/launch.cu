@@ -1,0 +1,272 @@
+// Enqueueing a plan's kernels (Sec. III contraction sequence) for one precision.
+//
+//  complex128: every kernel in FP64 on complex128 tensors;
+//  complex64 : every kernel in FP32 on complex64 tensors, except (when the plan has a
+//              tail) the last steps, which run in complex128 on a separate tail region
+//              whose complex64 inputs are widened first;
+//  split     : every kernel on float-float ("split FP32") tensors.
+//  The slice scalar and the sum over slices are always formed in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace pk {
+
+namespace {
+
+// Widens the listed complex64 tensors into complex128 copies (one grid row each) and
+// carries their bookkeeping over (the max-abs bits re-encoded as a double).
+__global__ void __launch_bounds__(256) k_widen(const ConvRec* __restrict__ conv,
+                                               const Cx<float>* arena, Cx<double>* tail,
+                                               Meta* meta) {
+  const ConvRec c = conv[blockIdx.y];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < c.elems;
+       e += (long long)gridDim.x * blockDim.x) {
+    Cx<float> v = arena[c.src_off + e];
+    tail[c.dst_off + e] = {(double)v.re, (double)v.im};
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float m = __uint_as_float((unsigned)meta[c.src_meta].maxbits);
+    meta[c.dst_meta].maxbits = (unsigned long long)__double_as_longlong((double)m);
+    meta[c.dst_meta].exp = meta[c.src_meta].exp;
+  }
+}
+
+constexpr int kNumClasses = 5;  // build, rows, split-K, results, GEMM
+
+// Optional per-launch timing: an event pair around every launch, summed per class.
+struct Prof {
+  double ms[kNumClasses] = {}, n[kNumClasses] = {}, cmacs[kNumClasses] = {},
+         bytes[kNumClasses] = {};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  std::vector<int> cls;
+};
+struct Marker {
+  Prof* prof;
+  cudaStream_t st;
+  void begin(int c, double cm, double by) {
+    if (!prof) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    prof->ev.push_back({a, b});
+    prof->cls.push_back(c);
+    prof->n[c] += 1;
+    prof->cmacs[c] += cm;
+    prof->bytes[c] += by;
+    cudaEventRecord(a, st);
+  }
+  void end() {
+    if (prof) cudaEventRecord(prof->ev.back().second, st);
+  }
+};
+
+template <typename R>
+cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st) {
+  const size_t sm = sizeof(long long) * (size_t)(2 * s.K + s.N);
+  long long blocks = (s.R + 255) / 256;
+  blocks = std::max<long long>(1, std::min<long long>(blocks, 152 * 8));
+  if (sm > 200 * 1024) {
+    k_rows_big<R><<<(unsigned)blocks, 256, 0, st>>>(s, arena, meta);
+    return cudaGetLastError();
+  }
+  const int kmax = sizeof(R) == 8 ? 16 : 32;
+  const int K = (int)s.K;
+  void (*fn)(const Step, Cx<R>*, Meta*);
+  if (K <= 1)
+    fn = k_rows<R, 1>;
+  else if (K <= 2)
+    fn = k_rows<R, 2>;
+  else if (K <= 4)
+    fn = k_rows<R, 4>;
+  else if (K <= 8)
+    fn = k_rows<R, 8>;
+  else if (K <= 16)
+    fn = k_rows<R, 16>;
+  else if (K <= kmax)
+    fn = k_rows<R, 32>;
+  else
+    fn = k_rows<R, 0>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  fn<<<(unsigned)blocks, 256, sm, st>>>(s, arena, meta);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_step(const Plan& p, const Step& s, size_t i, Cx<R>* arena, Meta* meta,
+                        Cx<double>* partial, unsigned* counters, cudaStream_t stream, Marker& mk,
+                        double elem_bytes) {
+  const double cm = (double)s.R * (double)s.K * (double)s.N;
+  const double by = elem_bytes * (double)(p.tensors[p.steps[i].a].elems +
+                                          (p.steps[i].b >= 0 ? p.tensors[p.steps[i].b].elems : 0) +
+                                          p.tensors[p.steps[i].c].elems);
+  const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
+  cudaError_t e;
+  if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
+    mk.begin(4, cm, by);
+    k_gemm<R><<<(unsigned)gemm_tiles, 256, 0, stream>>>(s, arena, meta);
+    mk.end();
+    e = cudaGetLastError();
+  } else if (s.kernel == KSPLITK) {
+    mk.begin(2, cm, by);
+    k_splitk<R><<<dim3((unsigned)s.chunks, (unsigned)(s.R * s.N)), 256, 0, stream>>>(
+        s, arena, meta, partial, counters + i);
+    mk.end();
+    e = cudaGetLastError();
+  } else {
+    mk.begin(1, cm, by);
+    e = launch_rows<R>(s, arena, meta, stream);
+    mk.end();
+  }
+  return e;
+}
+
+// Steps [first, last) of the plan, all in storage type R.
+template <typename R>
+cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t first, int32_t last,
+                        cudaStream_t stream,
+                        Marker& mk) {
+  Cx<R>* arena = (Cx<R>*)arena_base;
+  Meta* meta = (Meta*)(base + p.off_meta);
+  Cx<double>* partial = (Cx<double>*)(base + p.off_scratch);
+  unsigned* counters = (unsigned*)(base + p.off_counter);
+  for (int32_t i = first; i < last; ++i) {
+    cudaError_t e = launch_step<R>(p, p.steps[i], (size_t)i, arena, meta, partial, counters,
+                                       stream, mk, (double)sizeof(Cx<R>));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t launch_build(const Plan& p, char* base, char* arena_base, long long sl, cudaStream_t stream,
+                         Marker& mk) {
+  if (p.n_init <= 0) return cudaSuccess;
+  if (p.n_init > 65535) return cudaErrorInvalidValue;
+  int64_t maxel = 1, initel = 0;
+  for (const auto& r : p.recipes) {
+    maxel = std::max<int64_t>(maxel, r.elems);
+    initel += r.elems;
+  }
+  const unsigned bx = (unsigned)std::min<int64_t>((maxel + 255) / 256, 64);
+  mk.begin(0, 0, (double)sizeof(Cx<R>) * (double)initel);
+  k_build<R><<<dim3(bx, (unsigned)p.n_init), 256, 0, stream>>>(
+      (const Recipe*)(base + p.off_recipe), (const Slot*)(base + p.off_slots),
+      (Cx<R>*)arena_base, (Meta*)(base + p.off_meta), p.q, sl, (int)p.sliced.size());
+  mk.end();
+  return cudaGetLastError();
+}
+
+// `ws` holds the plan's state (program, bookkeeping, results, scratch: the bytes before
+// off_arena); `arena` holds its tensors (and the complex128 tail region, if any).
+cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena, cudaStream_t stream,
+                        Prof* prof) {
+  char* base = (char*)ws;
+  char* arena_base = (char*)arena;
+  Marker mk{prof, stream};
+  SliceResult* res = (SliceResult*)(base + p.off_result);
+  const int32_t n_steps = (int32_t)p.steps.size();
+  cudaError_t e;
+  for (long long sl = 0; sl < p.n_slices; ++sl) {
+    e = cudaMemsetAsync(base + p.off_meta, 0, p.off_result - p.off_meta, stream);
+    if (e != cudaSuccess) return e;
+    if (precision == PK_C128) {
+      if ((e = launch_build<double>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
+      if ((e = launch_bulk<double>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
+      mk.begin(3, 0, 0);
+      k_slice_result<double><<<1, 32, 0, stream>>>((Cx<double>*)arena_base,
+                                                   p.tensors[p.final_tensor].offset,
+                                                   (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
+      mk.end();
+    } else if (precision == PK_SPLIT) {
+      if ((e = launch_build<ff>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
+      if ((e = launch_bulk<ff>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
+      mk.begin(3, 0, 0);
+      k_slice_result<ff><<<1, 32, 0, stream>>>((Cx<ff>*)arena_base,
+                                               p.tensors[p.final_tensor].offset,
+                                               (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
+      mk.end();
+    } else if (p.tail.empty() && p.conv.empty()) {  // complex64
+      if ((e = launch_build<float>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
+      if ((e = launch_bulk<float>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
+      mk.begin(3, 0, 0);
+      k_slice_result<float><<<1, 32, 0, stream>>>((Cx<float>*)arena_base,
+                                                  p.tensors[p.final_tensor].offset,
+                                                  (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
+      mk.end();
+    } else {  // complex64 with a complex128 tail
+      if ((e = launch_build<float>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
+      if ((e = launch_bulk<float>(p, base, arena_base, 0, p.tail_first, stream, mk)) != cudaSuccess) return e;
+      Cx<double>* tail = (Cx<double>*)(arena_base + (p.off_tail - p.off_arena));
+      Meta* meta = (Meta*)(base + p.off_meta);
+      if (!p.conv.empty()) {
+        int64_t maxel = 1;
+        for (const auto& c : p.conv) maxel = std::max<int64_t>(maxel, c.elems);
+        const unsigned bx = (unsigned)std::min<int64_t>((maxel + 255) / 256, 256);
+        mk.begin(0, 0, 24.0 * (double)maxel);
+        k_widen<<<dim3(bx, (unsigned)p.conv.size()), 256, 0, stream>>>(
+            (const ConvRec*)(base + p.off_conv), (const Cx<float>*)arena_base, tail, meta);
+        mk.end();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
+      for (const TailStep& ts : p.tail) {
+        Step s = p.steps[ts.step];
+        s.a = ts.meta_a;
+        s.b = ts.meta_b;
+        s.off_a = ts.off_a;
+        s.off_b = ts.off_b;
+        s.off_c = ts.off_c;
+        e = launch_step<double>(p, s, (size_t)ts.step, tail, meta,
+                                (Cx<double>*)(base + p.off_scratch),
+                                (unsigned*)(base + p.off_counter), stream, mk, 16.0);
+        if (e != cudaSuccess) return e;
+      }
+      mk.begin(3, 0, 0);
+      k_slice_result<double><<<1, 32, 0, stream>>>(tail, p.final_tail_off, meta, p.final_tensor,
+                                                   res, sl);
+      mk.end();
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  mk.begin(3, 0, 0);
+  k_sum_slices<<<1, 256, 0, stream>>>(res, p.n_slices);
+  mk.end();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,
+                        cudaStream_t stream) {
+  return launch_impl(p, precision, ws, arena, stream, nullptr);
+}
+
+cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,
+                         cudaStream_t stream, double* out) {
+  Prof prof;
+  cudaError_t e = launch_impl(p, precision, ws, arena, stream, &prof);
+  cudaError_t e2 = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess) e = e2;
+  for (size_t i = 0; i < prof.ev.size(); ++i) {
+    float ms = 0;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, prof.ev[i].first, prof.ev[i].second);
+    prof.ms[prof.cls[i]] += ms;
+    cudaEventDestroy(prof.ev[i].first);
+    cudaEventDestroy(prof.ev[i].second);
+  }
+  for (int c = 0; c < kNumClasses; ++c) {
+    out[c] = prof.ms[c];
+    out[kNumClasses + c] = prof.n[c];
+    out[2 * kNumClasses + c] = prof.cmacs[c];
+    out[3 * kNumClasses + c] = prof.bytes[c];
+  }
+  return e;
+}
+
+}  // namespace pk

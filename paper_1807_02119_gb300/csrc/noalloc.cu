@@ -19,11 +19,6 @@
 #include "handles.h"
 #include "pk_internal.h"
 
-namespace pk {
-template <typename R>
-cudaError_t launch_plan(const Plan& p, void* ws, cudaStream_t stream);
-}
-
 namespace {
 
 constexpr unsigned long long kNoallocScratchBytes = 64ull << 20;  // 64 MiB per device
@@ -58,12 +53,12 @@ pk_status noalloc_fail(pk_ctx* c, pk_status s, const std::string& m) {
 extern "C" pk_status pk_eval_noalloc(pk_ctx* ctx, const pk_plan* p, int32_t precision,
                                      pk_scaled* Z, pk_scaled* V) {
   if (!ctx || !p || !Z) return noalloc_fail(ctx, PK_EINVAL, "null argument");
-  if (precision != PK_C128 && precision != PK_C64 && precision != PK_SPLIT_TF32)
+  if (precision != PK_C128 && precision != PK_C64 && precision != PK_SPLIT)
     return noalloc_fail(ctx, PK_EINVAL, "bad precision");
   if (ctx->device < 0) return noalloc_fail(ctx, PK_ENODEVICE, "host-only context");
   if (ctx->device >= kMaxDevices) return noalloc_fail(ctx, PK_ENODEVICE, "device index too large");
   const pk::Plan& P = p->p;
-  const uint64_t need = P.ws_bytes(precision == PK_C128 ? 16 : 8);
+  const uint64_t need = P.ws_bytes(precision);
   if (need > kNoallocScratchBytes)
     return noalloc_fail(ctx, PK_ENOMEM,
                         "plan needs " + std::to_string(need) +
@@ -79,8 +74,7 @@ extern "C" pk_status pk_eval_noalloc(pk_ctx* ctx, const pk_plan* p, int32_t prec
     e = cudaMemcpyAsync(ws, P.program.data(), P.program.size(), cudaMemcpyHostToDevice,
                         ctx->stream);
   if (e == cudaSuccess)
-    e = precision == PK_C128 ? pk::launch_plan<double>(P, ws, ctx->stream)
-                             : pk::launch_plan<float>(P, ws, ctx->stream);
+    e = pk::launch_plan(P, precision, ws, (char*)ws + P.off_arena, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->pinned_result,
                         (const char*)ws + P.off_result + sizeof(pk::SliceResult) * P.n_slices,

@@ -113,6 +113,21 @@ struct SliceResult {
   long long pad;
 };
 
+// Split precision: a bulk (complex64) tensor read by a complex128 tail step is copied,
+// widened, into the tail region; its copy gets its own bookkeeping slot.
+struct ConvRec {
+  int64_t src_off;   // complex64 elements into the arena
+  int64_t dst_off;   // complex128 elements into the tail region
+  int64_t elems;
+  int32_t src_meta, dst_meta;
+};
+struct TailStep {
+  int32_t step;
+  int32_t meta_a, meta_b;            // bookkeeping slots of the (possibly converted) operands
+  int32_t pad;
+  int64_t off_a, off_b, off_c;       // complex128 elements into the tail region
+};
+
 struct TensorInfo {
   std::vector<int32_t> dims;  // index ids, outermost first (row-major)
   int64_t elems = 1;
@@ -144,8 +159,18 @@ struct Plan {
   // device program layout (byte offsets inside the workspace)
   uint64_t off_recipe = 0, off_slots = 0, off_meta = 0, off_result = 0, off_scratch = 0,
            off_counter = 0, off_arena = 0;
-  uint64_t ws_bytes(int elem_bytes) const;
+  uint64_t ws_bytes(int32_t precision) const;
   std::vector<uint8_t> program;      // recipe + slots blob copied by pk_upload
+  // split precision: steps >= tail_first run in complex128 in a separate tail region;
+  // bulk tensors they read are up-converted there first
+  int32_t tail_first = 0;
+  std::vector<ConvRec> conv;
+  std::vector<TailStep> tail;        // one per step >= tail_first
+  int64_t tail_elems = 0;            // complex128 elements of the tail region
+  int64_t final_tail_off = 0;        // final tensor's offset in the tail region
+  int32_t n_meta = 0;                // tensors + converted copies
+  uint64_t off_tail = 0;             // byte offset of the tail region (split only)
+  uint64_t off_conv = 0;             // byte offset of the ConvRec records (in the program)
 };
 
 bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std::string& err);

@@ -405,8 +405,12 @@ bool run_order(const Network& net, int32_t order, Greedy& g) {
 }  // namespace
 
 // ------------------------------------------------------------------ plan assembly
-uint64_t Plan::ws_bytes(int elem_bytes) const {
-  return off_arena + (uint64_t)arena_elems * (uint64_t)elem_bytes;
+uint64_t Plan::ws_bytes(int32_t precision) const {
+  if (precision == PK_C64) {
+    if (tail.empty()) return off_arena + (uint64_t)arena_elems * 8ull;
+    return off_tail + (uint64_t)tail_elems * 16ull;  // complex128 tail region after the arena
+  }
+  return off_arena + (uint64_t)arena_elems * 16ull;  // complex128 and float-float pairs
 }
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
@@ -771,14 +775,65 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
     p.recipes.push_back(r);
   }
 
+  // ---- split precision: the last `tail` steps in complex128
+  {
+    int32_t T = opts.tail_steps > 0 ? opts.tail_steps : 0;
+    T = std::min<int32_t>(T, n_steps);
+    p.tail_first = n_steps - T;
+    std::vector<int64_t> tail_off(n_tens, -1);
+    std::vector<int32_t> tail_meta(n_tens, -1);
+    int64_t top2 = 0;
+    auto place = [&](int64_t elems) {
+      int64_t o = top2;
+      top2 += (elems + 63) / 64 * 64;
+      return o;
+    };
+    p.conv.clear();
+    p.tail.clear();
+    auto operand = [&](int32_t x) {  // tail offset and meta slot of an operand
+      if (tail_off[x] < 0) {
+        ConvRec cr;
+        cr.src_off = p.tensors[x].offset;
+        cr.dst_off = place(p.tensors[x].elems);
+        cr.elems = p.tensors[x].elems;
+        cr.src_meta = x;
+        cr.dst_meta = n_tens + (int32_t)p.conv.size();
+        p.conv.push_back(cr);
+        tail_off[x] = cr.dst_off;
+        tail_meta[x] = cr.dst_meta;
+      }
+    };
+    for (int32_t s2 = p.tail_first; s2 < n_steps; ++s2) {
+      const Step& st = p.steps[s2];
+      operand(st.a);
+      if (st.b >= 0) operand(st.b);
+      TailStep ts;
+      std::memset(&ts, 0, sizeof(ts));
+      ts.step = s2;
+      ts.meta_a = tail_meta[st.a];
+      ts.meta_b = st.b >= 0 ? tail_meta[st.b] : -1;
+      ts.off_a = tail_off[st.a];
+      ts.off_b = st.b >= 0 ? tail_off[st.b] : 0;
+      ts.off_c = place(p.tensors[st.c].elems);
+      tail_off[st.c] = ts.off_c;
+      tail_meta[st.c] = st.c;
+      p.tail.push_back(ts);
+    }
+    p.tail_elems = top2;
+    p.final_tail_off = tail_off[p.final_tensor];
+    p.n_meta = n_tens + (int32_t)p.conv.size();
+  }
+
   // ---- workspace layout
   uint64_t off = 0;
   p.off_recipe = off;
   off = align256(off + sizeof(Recipe) * p.recipes.size());
   p.off_slots = off;
   off = align256(off + sizeof(Slot) * std::max<size_t>(1, p.slots.size()));
+  p.off_conv = off;
+  off = align256(off + sizeof(ConvRec) * std::max<size_t>(1, p.conv.size()));
   p.off_meta = off;
-  off = align256(off + 16ull * n_tens);
+  off = align256(off + 16ull * p.n_meta);
   p.off_counter = off;
   off = align256(off + 4ull * std::max<int32_t>(1, n_steps));
   p.off_result = off;
@@ -786,11 +841,14 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   p.off_scratch = off;
   off = align256(off + 16ull * (uint64_t)std::max<int64_t>(1, partials));
   p.off_arena = off;
+  p.off_tail = align256(p.off_arena + 8ull * (uint64_t)p.arena_elems);
   p.program.assign(p.off_meta, 0);
   if (!p.recipes.empty())
     std::memcpy(p.program.data() + p.off_recipe, p.recipes.data(), sizeof(Recipe) * p.recipes.size());
   if (!p.slots.empty())
     std::memcpy(p.program.data() + p.off_slots, p.slots.data(), sizeof(Slot) * p.slots.size());
+  if (!p.conv.empty())
+    std::memcpy(p.program.data() + p.off_conv, p.conv.data(), sizeof(ConvRec) * p.conv.size());
   return true;
 }
 

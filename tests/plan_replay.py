@@ -30,6 +30,17 @@ class Run4(C.Structure):
     _fields_ = [("size", C.c_int64), ("sa", C.c_int64), ("sb", C.c_int64), ("sc", C.c_int64)]
 
 
+class ConvRec(C.Structure):
+    _fields_ = [("src_off", C.c_int64), ("dst_off", C.c_int64), ("elems", C.c_int64),
+                ("src_meta", C.c_int32), ("dst_meta", C.c_int32)]
+
+
+class TailStep(C.Structure):
+    _fields_ = [("step", C.c_int32), ("meta_a", C.c_int32), ("meta_b", C.c_int32),
+                ("pad", C.c_int32), ("off_a", C.c_int64), ("off_b", C.c_int64),
+                ("off_c", C.c_int64)]
+
+
 class Step(C.Structure):
     _fields_ = [("a", C.c_int32), ("b", C.c_int32), ("c", C.c_int32), ("kernel", C.c_int32),
                 ("off_a", C.c_int64), ("off_b", C.c_int64), ("off_c", C.c_int64),
@@ -84,10 +95,11 @@ def _gemm_view(st, arena, scale):
     return idx, Cv
 
 
-def replay(plan):
+def replay(plan, split=False):
     sc = np.frombuffer(plan.debug_blob(3), dtype=np.int64)
     q, n_init, n_steps, n_slices, n_sliced, final_t, off_rec, off_slots, n_slots, step_sz = \
-        [int(v) for v in sc]
+        [int(v) for v in sc[:10]]
+    tail_first, n_tail, n_conv, off_conv, final_tail_off = [int(v) for v in sc[10:15]]
     assert step_sz == C.sizeof(Step), (step_sz, C.sizeof(Step))
     prog = plan.debug_blob(0)
     recs = [Recipe.from_buffer_copy(prog, off_rec + i * C.sizeof(Recipe)) for i in range(n_init)]
@@ -97,6 +109,11 @@ def replay(plan):
     tinfo = np.frombuffer(plan.debug_blob(2), dtype=np.int64).reshape(-1, 2)
     fre, fim, fexp = np.frombuffer(plan.debug_blob(4), dtype=np.float64)
     arena_n = int((tinfo[:, 0] + tinfo[:, 1]).max())
+    convs = [ConvRec.from_buffer_copy(prog, off_conv + i * C.sizeof(ConvRec)) for i in range(n_conv)]
+    tb = plan.debug_blob(5)
+    tails = [TailStep.from_buffer_copy(tb, i * C.sizeof(TailStep)) for i in range(n_tail)]
+    tail_n = max([cr.dst_off + cr.elems for cr in convs] +
+                 [ts.off_c + int(tinfo[steps[ts.step].c, 1]) for ts in tails] + [1])
     total = []
     for sl in range(n_slices):
         sdig = []
@@ -127,35 +144,57 @@ def replay(plan):
             arena[r.offset:r.offset + r.elems] = val
             mx[r.meta] = float(np.max(np.maximum(np.abs(val.real), np.abs(val.imag))))
             ex[r.meta] = 0
+        if split and n_tail > 0:
+            # complex128 tail: widen the bulk tensors it reads, run its steps in the
+            # tail region with the tail records' offsets and bookkeeping slots
+            tail_region = np.full(max(1, tail_n), np.nan + 0j, dtype=np.complex128)
+            for st in steps[:tail_first]:
+                _step(st, arena, arena, mx, ex)
+            for cr in convs:
+                tail_region[cr.dst_off:cr.dst_off + cr.elems] = arena[cr.src_off:cr.src_off + cr.elems]
+                mx[cr.dst_meta], ex[cr.dst_meta] = mx[cr.src_meta], ex[cr.src_meta]
+            for ts in tails:
+                st = Step.from_buffer_copy(bytes(steps[ts.step]))
+                st.a, st.b = ts.meta_a, ts.meta_b
+                st.off_a, st.off_b, st.off_c = ts.off_a, ts.off_b, ts.off_c
+                _step(st, tail_region, tail_region, mx, ex)
+            v = tail_region[final_tail_off]
+            total.append((complex(v), ex[final_t]))
+            continue
         for st in steps:
-            oa, ob = _offsets(st.R, st.row, st.nrow)
-            ka, kb = _offsets(st.K, st.kr, st.nk)
-            _, nb = _offsets(st.N, st.nr, st.nn)
-            A = arena[st.off_a + oa[:, None] + ka[None, :]]                 # R x K
-            ea = math.frexp(mx[st.a])[1] if mx[st.a] > 0 else 0
-            if st.b >= 0:
-                B = arena[st.off_b + ob[:, None, None] + kb[None, :, None] + nb[None, None, :]]
-                eb = math.frexp(mx[st.b])[1] if mx[st.b] > 0 else 0
-                Cv = np.einsum("rk,rkn->nr", A, B)
-                xb = ex[st.b]
-            else:
-                eb, xb = 0, 0
-                Cv = A.sum(axis=1)[None, :]
-            Cv = Cv * 2.0 ** -(ea + eb)
-            flat = Cv.reshape(-1)   # C[n * R + r]
-            if st.b >= 0:
-                # the GEMM view of the same step must address the same entries
-                idx, Cg = _gemm_view(st, arena, 2.0 ** -(ea + eb))
-                ref = np.empty_like(flat)
-                ref[idx.reshape(-1) - st.off_c] = Cg.reshape(-1)
-                assert np.allclose(ref, flat, rtol=1e-12, atol=1e-300)
-            arena[st.off_c:st.off_c + flat.size] = flat
-            assert not np.isnan(flat).any()
-            mx[st.c] = float(np.max(np.maximum(np.abs(flat.real), np.abs(flat.imag))))
-            ex[st.c] = ex[st.a] + xb + ea + eb
+            _step(st, arena, arena, mx, ex)
         v = arena[tinfo[final_t, 0]]
         total.append((complex(v), ex[final_t]))
     # sum of slices, then the constant factor
     emax = max((e + math.frexp(abs(v))[1] for v, e in total if v != 0), default=0)
     z = sum(v * 2.0 ** (e - emax) for v, e in total)
     return complex(z) * complex(fre, fim), emax + int(fexp)
+
+
+def _step(st, arena, out, mx, ex):
+    """One step exactly as the kernels address it (operands and output in `arena`)."""
+    oa, ob = _offsets(st.R, st.row, st.nrow)
+    ka, kb = _offsets(st.K, st.kr, st.nk)
+    _, nb = _offsets(st.N, st.nr, st.nn)
+    A = arena[st.off_a + oa[:, None] + ka[None, :]]                 # R x K
+    ea = math.frexp(mx[st.a])[1] if mx[st.a] > 0 else 0
+    if st.b >= 0:
+        B = arena[st.off_b + ob[:, None, None] + kb[None, :, None] + nb[None, None, :]]
+        eb = math.frexp(mx[st.b])[1] if mx[st.b] > 0 else 0
+        Cv = np.einsum("rk,rkn->nr", A, B)
+        xb = ex[st.b]
+    else:
+        eb, xb = 0, 0
+        Cv = A.sum(axis=1)[None, :]
+    Cv = Cv * 2.0 ** -(ea + eb)
+    flat = Cv.reshape(-1)   # C[n * R + r]
+    if st.b >= 0:
+        # the GEMM view of the same step must address the same entries
+        idx, Cg = _gemm_view(st, arena, 2.0 ** -(ea + eb))
+        ref = np.empty_like(flat)
+        ref[idx.reshape(-1) - st.off_c] = Cg.reshape(-1)
+        assert np.allclose(ref, flat, rtol=1e-12, atol=1e-300)
+    out[st.off_c:st.off_c + flat.size] = flat
+    assert not np.isnan(flat).any()
+    mx[st.c] = float(np.max(np.maximum(np.abs(flat.real), np.abs(flat.imag))))
+    ex[st.c] = ex[st.a] + xb + ea + eb

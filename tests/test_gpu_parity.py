@@ -195,3 +195,66 @@ def test_forced_rows_kernel(ctx):
                           flags=pk.FLAG_FORCE_ROWS)
             zo, _ = oracle_zv(gk.pd, q, outer=gk.outer)
             assert rel_err(z, zo) <= C128_TOL
+
+
+SPLIT_TOL = 1e-6   # split FP32 (float-float arithmetic, complex128 tail) target
+
+
+@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "elim_spin"])
+def test_split_precision_vs_oracle(ctx, order):
+    worst = 0.0
+    for s in range(10):
+        gk = kg.random_grid_knot(16, 500 + s, True, 20, 45)
+        for q in (2, 3, 5):
+            z, v, _ = run(ctx, gk.pd, q, "split", outer=gk.outer, order=order)
+            zo, vo = oracle_zv(gk.pd, q, outer=gk.outer)
+            ez, ev = rel_err(z, zo), rel_err(v, vo)
+            worst = max(worst, ez, ev)
+            assert ez <= SPLIT_TOL and ev <= SPLIT_TOL, (s, q, ez, ev)
+    print(f"[{order} split] worst relative error {worst:.3e}")
+
+
+def test_split_forced_gemm(ctx):
+    """Float-float GEMM kernel on every two-operand step."""
+    worst = 0.0
+    for s in range(6):
+        gk = kg.random_grid_knot(16, 1200 + s, True, 20, 45)
+        for q in (3, 5):
+            zo, _ = oracle_zv(gk.pd, q, outer=gk.outer)
+            for order in ("greedy_edge", "elim_spin"):
+                z, _, p = run(ctx, gk.pd, q, "split", outer=gk.outer, order=order,
+                              flags=pk.FLAG_FORCE_GEMM)
+                e = rel_err(z, zo)
+                worst = max(worst, e)
+                assert e <= SPLIT_TOL, (s, q, order, e)
+    print(f"[split forced GEMM] worst relative error {worst:.3e}")
+
+
+def test_c64_with_fp64_tail(ctx):
+    """complex64 bulk with the last 1, 4 or all contractions widened to complex128."""
+    worst = {}
+    for s in range(6):
+        gk = kg.random_grid_knot(16, 1200 + s, True, 20, 45)
+        for q in (3, 5):
+            zo, _ = oracle_zv(gk.pd, q, outer=gk.outer)
+            for tail in (1, 4, 1000):
+                z, _, p = run(ctx, gk.pd, q, "c64", outer=gk.outer, order="greedy_edge",
+                              tail_steps=tail)
+                e = rel_err(z, zo)
+                worst[tail] = max(worst.get(tail, 0.0), e)
+                assert e <= C64_TOL, (s, q, tail, e)
+    print("[c64 + FP64 tail] worst relative error by tail length", worst)
+
+
+def test_split_closed_forms_and_slices(ctx):
+    for pd, poly in ((TREFOIL, {1: 1, 3: 1, 4: -1}), (FIG8, {-2: 1, -1: -1, 0: 1, 1: -1, 2: 1}),
+                     ([], {0: 1})):
+        for q in range(1, 7):
+            _, v, _ = run(ctx, pd, q, "split")
+            assert rel_err(v, exact_to_complex(kg_eval(poly, q), 1, q)) <= SPLIT_TOL
+    gk = kg.random_grid_knot(18, 700, True, 40, 70)
+    k = pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer)
+    full = pk.Plan(ctx, k, 3).stats()["log2_max_elems"]
+    z, _, p = run(ctx, gk.pd, 3, "split", outer=gk.outer, max_log2_elems=full - 3)
+    assert p.stats()["n_slices"] > 1
+    assert rel_err(z, oracle_zv(gk.pd, 3, outer=gk.outer)[0]) <= SPLIT_TOL

@@ -163,3 +163,25 @@ def test_plan_replay_forced_kernels(ctx):
                     assert kinds <= {0}
                 z, e = replay(p)
                 assert rel_err(SC.of(z, e), _z_oracle(pd, 3)) < 1e-10
+
+
+def test_plan_replay_split_tail_layout(ctx):
+    """The complex128 tail of PK_SPLIT (widened inputs, tail-region offsets, separate
+    bookkeeping slots) addresses the same contraction as the plain plan."""
+    for s in range(5):
+        pd = kg.random_grid_knot(15, 80 + s, True, 15, 40).pd
+        k = pk.Knot.from_pd(ctx, pd)
+        for tail in (0, 1, 7, -1, 1000):
+            for order in ("greedy_spin", "elim_spin"):
+                p = pk.Plan(ctx, k, 3, order=order, tail_steps=tail)
+                z, e = replay(p, split=True)
+                assert rel_err(SC.of(z, e), _z_oracle(pd, 3)) < 1e-10, (s, tail, order)
+                st = p.stats()
+                assert st["workspace_split"] > 0
+    # sliced plan with a tail
+    pd = kg.random_grid_knot(16, 101, True, 20, 60).pd
+    k = pk.Knot.from_pd(ctx, pd)
+    p = pk.Plan(ctx, k, 2, order="greedy_edge", max_log2_elems=4.0, tail_steps=3)
+    assert p.stats()["n_slices"] > 1
+    z, e = replay(p, split=True)
+    assert rel_err(SC.of(z, e), _z_oracle(pd, 2)) < 1e-10
