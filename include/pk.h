@@ -213,6 +213,30 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                      uint64_t workspace_bytes, void* d_arena, uint64_t arena_bytes, double* out);
 
+/* ---- batched evaluation (many knots in one launch) ------------------------------- */
+
+/* A batch of n planned knots (plans must outlive pk_batch_create only: their data is
+ * copied) evaluated together at one precision by one persistent kernel: each CTA takes
+ * the next knot from a work counter and performs its whole contraction (Sec. III),
+ * so knots of uneven size balance across the GPU without any CTA waiting for another.
+ * The counter reset and the launch are recorded once into a CUDA graph per workspace
+ * and replayed by every pk_batch_launch. */
+typedef struct pk_batch pk_batch;
+pk_status pk_batch_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, int32_t precision,
+                          pk_batch** out);
+/* Device workspace for the batch; *upload_bytes (may be NULL) is the part pk_batch_upload
+ * copies host->device (knot headers, recipes and steps). */
+pk_status pk_batch_workspace_bytes(const pk_batch* b, uint64_t* bytes, uint64_t* upload_bytes);
+pk_status pk_batch_upload(pk_ctx* ctx, pk_batch* b, void* d_workspace, uint64_t workspace_bytes);
+pk_status pk_batch_launch(pk_ctx* ctx, pk_batch* b, void* d_workspace, uint64_t workspace_bytes);
+/* Waits for the stream; Z[i], V[i] for knot i (V[i] = 0 and PK_ENOTKNOT for non-knots). */
+pk_status pk_batch_download(pk_ctx* ctx, pk_batch* b, const void* d_workspace, pk_scaled* Z,
+                            pk_scaled* V);
+/* create + upload + launch + download + destroy. */
+pk_status pk_eval_batch(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, int32_t precision,
+                        void* d_workspace, uint64_t workspace_bytes, pk_scaled* Z, pk_scaled* V);
+void pk_batch_destroy(pk_batch* b);
+
 /* Number of kernel launches pk_launch issues for this plan and precision. */
 pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launches);
 

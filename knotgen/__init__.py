@@ -63,18 +63,18 @@ class SplitMix64:
 # --------------------------------------------------------------------------- grid walk
 
 def _grid_crossings(xs, ys):
-    """Crossings (i, j) of vertical segment V_i with horizontal segment H_j, sorted."""
-    L = len(xs)
-    out = []
-    for i in range(L):
-        x = xs[i]
-        ylo, yhi = sorted((ys[i], ys[(i + 1) % L]))
-        for j in range(L):
-            yj = ys[(j + 1) % L]
-            xlo, xhi = sorted((xs[j], xs[(j + 1) % L]))
-            if xlo < x < xhi and ylo < yj < yhi:
-                out.append((i, j))
-    return out
+    """Crossings (i, j) of vertical segment V_i with horizontal segment H_j, in
+    lexicographic (i, j) order."""
+    import numpy as np
+    x = np.asarray(xs)
+    y = np.asarray(ys)
+    xn, yn = np.roll(x, -1), np.roll(y, -1)
+    ylo, yhi = np.minimum(y, yn), np.maximum(y, yn)        # V_i spans y_i .. y_{i+1}
+    xlo, xhi = np.minimum(x, xn), np.maximum(x, xn)        # H_j spans x_j .. x_{j+1} at y_{j+1}
+    hit = ((xlo[None, :] < x[:, None]) & (x[:, None] < xhi[None, :]) &
+           (ylo[:, None] < yn[None, :]) & (yn[None, :] < yhi[:, None]))
+    ii, jj = np.nonzero(hit)                                 # row-major: sorted by (i, j)
+    return [(int(i), int(j)) for i, j in zip(ii, jj)]
 
 
 def grid_walk_pd(xs, ys, over_bits=None):
@@ -410,9 +410,11 @@ def knot_suite(name: str):
 
     tiny    : L=12, seed 0, redrawn until exactly 16 crossings, random over/under.
     scale   : L=40, seeds 1..64, each redrawn until 100..400 crossings, random over/under.
-    batch   : L=24, 4096 knots; knot s targets a crossing count drawn uniformly in
-              20..120 from SplitMix64(0xB47C4) and is redrawn from seed s until it
-              has exactly that many crossings, random over/under.
+    batch   : 4096 knots; knot s targets a crossing count t drawn uniformly in 20..120
+              from SplitMix64(0xB47C4), uses the grid side L = round(sqrt(t / 0.1))
+              (inverting the mean crossing count ~0.1 L^2, as Sec. III.B inverts its
+              fit of <n_c>(L)) and is redrawn from seed s until it has t-2..t+2
+              crossings, random over/under.
     grad    : one knot with 300 crossings; L=53 (the grid side whose typical
               crossing count is about 300), seed 7, random over/under.
     large   : 8 knots with 600..1000 crossings at L=86, seeds 1..8, random over/under.
@@ -426,7 +428,8 @@ def knot_suite(name: str):
         out = []
         for s in range(4096):
             target = 20 + tr.below(101)
-            out.append(random_grid_knot(24, s, True, target, target))
+            L = max(6, int(round((target / 0.1) ** 0.5)))
+            out.append(random_grid_knot(L, s, True, target - 2, target + 2))
         return out
     if name == "grad":
         return [random_grid_knot(53, 7, True, 300, 300)]

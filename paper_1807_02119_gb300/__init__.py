@@ -27,6 +27,8 @@ EXPORTED = [
     "pk_plan_workspace_bytes", "pk_plan_steps", "pk_plan_destroy", "pk_eval", "pk_upload",
     "pk_launch", "pk_download", "pk_plan_launches", "pk_jones_from_z", "pk_plan_debug_blob",
     "pk_profile", "pk_eval_noalloc", "pk_plan_state_bytes", "pk_launch_arena",
+    "pk_batch_create", "pk_batch_workspace_bytes", "pk_batch_upload", "pk_batch_launch",
+    "pk_batch_download", "pk_eval_batch", "pk_batch_destroy",
 ]
 
 
@@ -95,6 +97,13 @@ def lib():
         "pk_eval_noalloc": [vp, vp, i32, P(pk_scaled), P(pk_scaled)],
         "pk_plan_state_bytes": [vp, i32, P(u64), P(u64)],
         "pk_launch_arena": [vp, vp, i32, vp, u64, vp, u64],
+        "pk_batch_create": [vp, P(vp), i32, i32, P(vp)],
+        "pk_batch_workspace_bytes": [vp, P(u64), P(u64)],
+        "pk_batch_upload": [vp, vp, vp, u64],
+        "pk_batch_launch": [vp, vp, vp, u64],
+        "pk_batch_download": [vp, vp, vp, P(pk_scaled), P(pk_scaled)],
+        "pk_eval_batch": [vp, P(vp), i32, i32, vp, u64, P(pk_scaled), P(pk_scaled)],
+        "pk_batch_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -362,3 +371,59 @@ def profile(plan: Plan, precision: str, ws, arena=None):
     names = ("build", "rows", "splitk", "results", "gemm")
     return {n: {"ms": out[i], "launches": out[5 + i], "cmacs": out[10 + i], "bytes": out[15 + i]}
             for i, n in enumerate(names)}
+
+
+class Batch:
+    """pk_batch: many planned knots evaluated by one persistent launch (CUDA graph)."""
+
+    def __init__(self, plans, precision="split"):
+        self.plans = list(plans)
+        self.ctx = self.plans[0].ctx
+        self.precision = precision
+        arr = (C.c_void_p * len(self.plans))(*[p.h.value for p in self.plans])
+        h = C.c_void_p()
+        _check(lib().pk_batch_create(self.ctx.h, arr, len(self.plans), PRECISIONS[precision],
+                                     C.byref(h)), self.ctx)
+        self.h = h
+
+    def workspace_bytes(self):
+        b, u = C.c_uint64(), C.c_uint64()
+        _check(lib().pk_batch_workspace_bytes(self.h, C.byref(b), C.byref(u)))
+        return b.value, u.value
+
+    def upload(self, ws):
+        _check(lib().pk_batch_upload(self.ctx.h, self.h, C.c_void_p(ws.data_ptr()), ws.numel()),
+               self.ctx)
+
+    def launch(self, ws):
+        _check(lib().pk_batch_launch(self.ctx.h, self.h, C.c_void_p(ws.data_ptr()), ws.numel()),
+               self.ctx)
+
+    def download(self, ws):
+        n = len(self.plans)
+        z = (pk_scaled * n)()
+        v = (pk_scaled * n)()
+        st = lib().pk_batch_download(self.ctx.h, self.h, C.c_void_p(ws.data_ptr()), z, v)
+        if st not in (0, 2):
+            _check(st, self.ctx)
+        return [Scaled.of(x) for x in z], [Scaled.of(x) for x in v]
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().pk_batch_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def evaluate_batch(plans, precision="split", ws=None):
+    """Z and V of every plan's knot from one persistent launch; returns two lists."""
+    import torch
+    b = Batch(plans, precision)
+    _torch_stream(b.ctx)
+    if ws is None:
+        ws = torch.empty(b.workspace_bytes()[0], dtype=torch.uint8, device=f"cuda:{b.ctx.device}")
+    b.upload(ws)
+    b.launch(ws)
+    return b.download(ws)

@@ -92,6 +92,20 @@ __device__ __forceinline__ Cx<ff> ld(const Cx<ff>* p) {
   float4 v = __ldg(reinterpret_cast<const float4*>(p));
   return {{v.x, v.y}, {v.z, v.w}};
 }
+// Coherent loads (plain ld.global): for data the same kernel wrote earlier, which the
+// read-only path of __ldg does not guarantee to see.
+__device__ __forceinline__ Cx<double> ldc(const Cx<double>* p) {
+  double2 v = *reinterpret_cast<const double2*>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ Cx<float> ldc(const Cx<float>* p) {
+  float2 v = *reinterpret_cast<const float2*>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ Cx<ff> ldc(const Cx<ff>* p) {
+  float4 v = *reinterpret_cast<const float4*>(p);
+  return {{v.x, v.y}, {v.z, v.w}};
+}
 __device__ __forceinline__ void st(Cx<double>* p, Cx<double> x) {
   *reinterpret_cast<double2*>(p) = make_double2(x.re, x.im);
 }
@@ -215,8 +229,50 @@ __device__ __forceinline__ void block_max_to_meta(S v, Meta* meta) {
 }
 
 // ------------------------------------------------------------------ initial tensors
-// One grid row (blockIdx.y) per initial tensor; entry = sum_{s<q} prod_j f_j(s, x_j),
-// formed in double and rounded once to the storage type.
+// Entry e of an initial tensor: sum_{s<q} prod_j f_j(s, x_j) in double (x_j = the
+// digit of e at slot j's position, or the fixed value of a sliced index).
+__device__ __forceinline__ void recipe_value(const Recipe& r, const Slot* slots, long long e, int q,
+                                             const int* sdig, double& sre, double& sim) {
+  sre = 0;
+  sim = 0;
+  if (r.kind == 1) {
+    sre = 1;
+    return;
+  }
+  for (int s = 0; s < q; ++s) {
+    double pre = 1, pim = 0;
+    bool zero = false;
+    for (int j = 0; j < r.nslot; ++j) {
+      const Slot sl = slots[r.slot0 + j];
+      int x;
+      if (sl.dimpos >= 0) {
+        long long t = e;
+        for (int d = 0; d < sl.dimpos; ++d) t /= q;
+        x = (int)(t % q);
+      } else {
+        x = sdig[sl.slice_ord];
+      }
+      if (sl.absorbed) {
+        if (s == x) {
+          double nre = pre * sl.dre - pim * sl.dim;
+          double nim = pre * sl.dim + pim * sl.dre;
+          pre = nre;
+          pim = nim;
+        }
+      } else if (s != x) {
+        zero = true;
+        break;
+      }
+    }
+    if (!zero) {
+      sre += pre;
+      sim += pim;
+    }
+  }
+}
+
+// One grid row (blockIdx.y) per initial tensor, formed in double and rounded once to
+// the storage type.
 template <typename R>
 __global__ void __launch_bounds__(256) k_build(const Recipe* __restrict__ rec,
                                                const Slot* __restrict__ slots, Cx<R>* arena,
@@ -234,41 +290,8 @@ __global__ void __launch_bounds__(256) k_build(const Recipe* __restrict__ rec,
   }
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < r.elems;
        e += (long long)gridDim.x * blockDim.x) {
-    double sre = 0, sim = 0;
-    if (r.kind == 1) {
-      sre = 1;
-    } else {
-      for (int s = 0; s < q; ++s) {
-        double pre = 1, pim = 0;
-        bool zero = false;
-        for (int j = 0; j < r.nslot; ++j) {
-          const Slot sl = slots[r.slot0 + j];
-          int x;
-          if (sl.dimpos >= 0) {
-            long long t = e;
-            for (int d = 0; d < sl.dimpos; ++d) t /= q;
-            x = (int)(t % q);
-          } else {
-            x = sdig[sl.slice_ord];
-          }
-          if (sl.absorbed) {
-            if (s == x) {
-              double nre = pre * sl.dre - pim * sl.dim;
-              double nim = pre * sl.dim + pim * sl.dre;
-              pre = nre;
-              pim = nim;
-            }
-          } else if (s != x) {
-            zero = true;
-            break;
-          }
-        }
-        if (!zero) {
-          sre += pre;
-          sim += pim;
-        }
-      }
-    }
+    double sre, sim;
+    recipe_value(r, slots, e, q, sdig, sre, sim);
     const Cx<R> v{from_double<R>(sre), from_double<R>(sim)};
     st(arena + r.offset + e, v);
     vmax = fmax(vmax, mag(v));
@@ -648,7 +671,7 @@ __global__ void k_slice_result(const Cx<R>* arena, long long off, const Meta* me
 }
 
 // Sum over slices in double with a common exponent; fixed assignment and tree order.
-__global__ void k_sum_slices(SliceResult* res, long long n) {
+static __global__ void k_sum_slices(SliceResult* res, long long n) {
   __shared__ long long emax_s[256];
   __shared__ double sre[256], sim[256];
   long long emax = LLONG_MIN;

@@ -1,0 +1,86 @@
+"""Batched evaluation (one persistent launch for many knots) against single evaluations
+and the CPU oracle."""
+import pytest
+
+import knotgen as kg
+import oracle
+import paper_1807_02119_gb300 as pk
+from oracle.scaled import SC, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "split": 1e-6, "c64": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = pk.Context(0)
+    c.set_stream(torch.cuda.current_stream().cuda_stream)
+    return c
+
+
+def sc(s):
+    return SC.of(s.mantissa, s.exp2)
+
+
+def _plans(ctx, knots, q):
+    return [pk.Plan(ctx, pk.Knot.from_pd(ctx, k.pd, outer=k.outer), q) for k in knots]
+
+
+@pytest.mark.parametrize("prec", ["c128", "split", "c64"])
+def test_batch_matches_single(ctx, prec):
+    knots = kg.knot_suite("batch")[:96]          # 18..122 crossings, uneven
+    plans = _plans(ctx, knots, 3)
+    Z, V = pk.evaluate_batch(plans, prec)
+    worst = 0.0
+    for p, z, v in zip(plans, Z, V):
+        zs, vs = pk.evaluate(p, prec)
+        e = max(rel_err(sc(z), sc(zs)), rel_err(sc(v), sc(vs)))
+        worst = max(worst, e)
+        assert e <= TOL[prec], e
+    print(f"[batch {prec}] worst relative difference to single evaluation {worst:.3e}")
+
+
+def test_batch_vs_oracle(ctx):
+    knots = kg.knot_suite("batch")[:24]
+    plans = _plans(ctx, knots, 3)
+    for prec in ("c128", "split"):
+        Z, V = pk.evaluate_batch(plans, prec)
+        for k, z, v in zip(knots, Z, V):
+            g = oracle.tait_graph(k.pd, outer=k.outer)
+            zo = oracle.z_complex(g.n_v, g.edges, 3)
+            vo = oracle.jones_from_z(zo, g, 3)
+            assert rel_err(sc(z), zo) <= TOL[prec]
+            assert rel_err(sc(v), vo) <= TOL[prec]
+
+
+def test_batch_mixed_q_slices_and_trivial(ctx):
+    """Different q in one batch, sliced plans, the unknot and a kink; relaunch gives
+    bit-identical results (the recorded graph is replayed)."""
+    import torch
+    knots = kg.knot_suite("batch")[100:112]
+    plans = []
+    for i, k in enumerate(knots):
+        kn = pk.Knot.from_pd(ctx, k.pd, outer=k.outer)
+        q = (2, 3, 5)[i % 3]
+        full = pk.Plan(ctx, kn, q).stats()["log2_max_elems"]
+        plans.append(pk.Plan(ctx, kn, q, max_log2_elems=max(1.0, full - 2.5) if i % 2 else 0.0))
+    plans.append(pk.Plan(ctx, pk.Knot.from_pd(ctx, []), 3))
+    plans.append(pk.Plan(ctx, pk.Knot.from_pd(ctx, kg.kink([], 0, 1)), 5))
+    assert any(p.stats()["n_slices"] > 1 for p in plans)
+    b = pk.Batch(plans, "split")
+    ws = torch.empty(b.workspace_bytes()[0], dtype=torch.uint8, device="cuda")
+    b.upload(ws)
+    b.launch(ws)
+    Z1, V1 = b.download(ws)
+    b.launch(ws)
+    Z2, V2 = b.download(ws)
+    assert [(z.re, z.im, z.exp2) for z in Z1] == [(z.re, z.im, z.exp2) for z in Z2]
+    for p, z, v in zip(plans, Z1, V1):
+        zs, vs = pk.evaluate(p, "c128")
+        assert rel_err(sc(z), sc(zs)) <= TOL["split"]
+        assert rel_err(sc(v), sc(vs)) <= TOL["split"]
+    assert abs(V1[-2].to_complex() - 1) < 1e-12 and abs(V1[-1].to_complex() - 1) < 1e-12
