@@ -67,7 +67,10 @@ typedef enum {
   PK_ORDER_GREEDY_SPIN = 2,  /* same greedy on the network whose COPY tensors are kept as
                                 shared spin indices (clause matrices only)                  */
   PK_ORDER_ELIM_SPIN = 3,    /* spin network, order from min-degree spin elimination        */
-  PK_ORDER_PARTITION = 4     /* spin network, recursive-bisection separator order           */
+  PK_ORDER_PARTITION = 4,    /* spin network, recursive-bisection separator order (not yet
+                                built: falls back to PK_ORDER_ELIM_SPIN)                     */
+  PK_ORDER_FILL_SPIN = 5     /* spin network, min-fill elimination with randomised ties,
+                                best of pk_plan_opts.restarts restarts                       */
 } pk_order;
 
 /* pk_plan_opts.flags: kernel-choice overrides for testing and tuning (default 0 lets
@@ -83,7 +86,7 @@ typedef struct {
   double max_log2_slices;    /* refuse (PK_ETOOWIDE) plans needing more slices (0 -> 40)    */
   int32_t tail_steps;        /* PK_C64: this many final contractions run in complex128
                                 (<= 0: none)                                                 */
-  int32_t reserved;          /* 0                                                           */
+  int32_t restarts;          /* min-fill restarts for PK_ORDER_FILL_SPIN / AUTO (0 -> 8)    */
 } pk_plan_opts;
 
 typedef struct {

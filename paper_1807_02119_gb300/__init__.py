@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libpk.so")
 PK_C128, PK_C64, PK_SPLIT = 0, 1, 2
 FLAG_FORCE_GEMM, FLAG_FORCE_ROWS = 1, 2
 PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split": PK_SPLIT}
-ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4}
+ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4,
+          "fill_spin": 5}
 STATUS = {0: "PK_OK", 1: "PK_EINVAL", 2: "PK_ENOTKNOT", 3: "PK_ENOMEM", 4: "PK_ETOOWIDE",
           5: "PK_ECUDA", 6: "PK_ETIMEOUT", 7: "PK_ENODEVICE"}
 
@@ -45,7 +46,7 @@ class pk_scaled(C.Structure):
 class pk_plan_opts(C.Structure):
     _fields_ = [("order", C.c_int32), ("flags", C.c_int32), ("max_log2_elems", C.c_double),
                 ("max_log2_slices", C.c_double), ("tail_steps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("restarts", C.c_int32)]
 
 
 class pk_plan_stats(C.Structure):
@@ -235,8 +236,9 @@ class Knot:
 class Plan:
     def __init__(self, ctx: Context, knot: Knot, q: int, order: str = "auto",
                  max_log2_elems: float = 0.0, max_log2_slices: float = 0.0, flags: int = 0,
-                 tail_steps: int = 0):
-        o = pk_plan_opts(ORDERS[order], flags, max_log2_elems, max_log2_slices, tail_steps, 0)
+                 tail_steps: int = 0, restarts: int = 0):
+        o = pk_plan_opts(ORDERS[order], flags, max_log2_elems, max_log2_slices, tail_steps,
+                         restarts)
         h = C.c_void_p()
         _check(lib().pk_plan_create(ctx.h, knot.h, q, C.byref(o), C.byref(h)), ctx)
         self.h = h

@@ -41,7 +41,7 @@ Scaled s_pow(Scaled a, int64_t n);
 Scaled s_from(double re, double im);
 
 // ------------------------------------------------------------------ plans (Sec. III)
-constexpr int kMaxRuns = 12;  // merged stride runs per index class
+constexpr int kMaxRuns = 20;  // merged stride runs per index class (Step stays < 4 KB)
 
 struct Run {
   int64_t size;

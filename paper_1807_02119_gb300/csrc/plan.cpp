@@ -386,11 +386,82 @@ std::vector<int32_t> min_degree_order(const Network& net) {
   return order;
 }
 
-bool run_order(const Network& net, int32_t order, Greedy& g) {
+// Min-fill spin elimination order: eliminate the spin whose neighbours need the fewest
+// new adjacencies to become a clique (ties: fewer neighbours, then a seeded random
+// key, so different seeds give different orders).  Fill counts are cached and only
+// recomputed for spins whose neighbourhood changed.
+std::vector<int32_t> min_fill_order(const Network& net, uint64_t seed) {
+  const int32_t n = net.n_idx;
+  const int32_t W = (n + 63) / 64;
+  std::vector<uint64_t> bits((size_t)n * W, 0);
+  std::vector<std::vector<int32_t>> nb(n);
+  auto adj = [&](int32_t a, int32_t b) { return (bits[(size_t)a * W + (b >> 6)] >> (b & 63)) & 1; };
+  auto link = [&](int32_t a, int32_t b) {
+    if (a == b || adj(a, b)) return;
+    bits[(size_t)a * W + (b >> 6)] |= 1ull << (b & 63);
+    bits[(size_t)b * W + (a >> 6)] |= 1ull << (a & 63);
+    nb[a].push_back(b);
+    nb[b].push_back(a);
+  };
+  for (const auto& t : net.t)
+    for (int32_t a : t.dims)
+      for (int32_t b : t.dims) link(a, b);
+  uint64_t s = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  std::vector<uint64_t> key(n);
+  for (int32_t v = 0; v < n; ++v) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    key[v] = seed == 0 ? (uint64_t)v : (z ^ (z >> 31));
+  }
+  std::vector<int64_t> fill(n, 0);
+  std::vector<char> dirty(n, 1), done(n, 0);
+  std::vector<int32_t> order;
+  order.reserve(n);
+  for (int32_t it = 0; it < n; ++it) {
+    int32_t best = -1;
+    for (int32_t v = 0; v < n; ++v) {
+      if (done[v]) continue;
+      if (dirty[v]) {
+        int64_t c = 0;
+        const auto& N = nb[v];
+        for (size_t i = 0; i < N.size(); ++i)
+          for (size_t j = i + 1; j < N.size(); ++j)
+            if (!adj(N[i], N[j])) ++c;
+        fill[v] = c;
+        dirty[v] = 0;
+      }
+      if (best < 0 || fill[v] < fill[best] ||
+          (fill[v] == fill[best] && (nb[v].size() < nb[best].size() ||
+                                     (nb[v].size() == nb[best].size() && key[v] < key[best]))))
+        best = v;
+    }
+    done[best] = 1;
+    order.push_back(best);
+    std::vector<int32_t> N = nb[best];
+    for (int32_t a : N) {
+      auto& L = nb[a];
+      L.erase(std::remove(L.begin(), L.end(), best), L.end());
+      bits[(size_t)a * W + (best >> 6)] &= ~(1ull << (best & 63));
+    }
+    for (size_t i = 0; i < N.size(); ++i)
+      for (size_t j = i + 1; j < N.size(); ++j) link(N[i], N[j]);
+    for (int32_t a : N) {
+      dirty[a] = 1;
+      for (int32_t b : nb[a]) dirty[b] = 1;
+    }
+    nb[best].clear();
+  }
+  return order;
+}
+
+bool run_order(const Network& net, int32_t order, Greedy& g, uint64_t seed = 0) {
   g = Greedy();
   g.init(net);
-  if (order == PK_ORDER_ELIM_SPIN) {
-    std::vector<int32_t> ord = min_degree_order(net);
+  if (order == PK_ORDER_ELIM_SPIN || order == PK_ORDER_FILL_SPIN) {
+    std::vector<int32_t> ord =
+        order == PK_ORDER_ELIM_SPIN ? min_degree_order(net) : min_fill_order(net, seed);
     for (int32_t v : ord) {
       int32_t a, b;
       while (g.cnt[v] >= 2 && g.best_pair(v, a, b)) g.contract(a, b);
@@ -429,15 +500,19 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   double max_log2_slices = opts.max_log2_slices > 0 ? opts.max_log2_slices : 40.0;
   int32_t rmax = q == 1 ? 1 << 20 : (int32_t)std::floor(max_log2 / lq + 1e-9);
 
-  // candidate orders
-  std::vector<int32_t> cands;
-  if (opts.order == PK_ORDER_AUTO)
-    cands = {PK_ORDER_GREEDY_SPIN, PK_ORDER_ELIM_SPIN, PK_ORDER_GREEDY_EDGE};
-  else if (opts.order >= 1 && opts.order <= 3)
-    cands = {opts.order};
-  else if (opts.order == PK_ORDER_PARTITION)
-    cands = {PK_ORDER_ELIM_SPIN};
-  else {
+  // candidate orders: (order, seed); min-fill restarts differ by their tie-break seed
+  const int32_t restarts = opts.restarts > 0 ? opts.restarts : 8;
+  std::vector<std::pair<int32_t, uint64_t>> cands;
+  if (opts.order == PK_ORDER_AUTO) {
+    cands = {{PK_ORDER_GREEDY_SPIN, 0}, {PK_ORDER_ELIM_SPIN, 0}, {PK_ORDER_GREEDY_EDGE, 0}};
+    for (int32_t r = 0; r < restarts; ++r) cands.push_back({PK_ORDER_FILL_SPIN, (uint64_t)r});
+  } else if (opts.order >= 1 && opts.order <= 3) {
+    cands = {{opts.order, 0}};
+  } else if (opts.order == PK_ORDER_FILL_SPIN) {
+    for (int32_t r = 0; r < restarts; ++r) cands.push_back({PK_ORDER_FILL_SPIN, (uint64_t)r});
+  } else if (opts.order == PK_ORDER_PARTITION) {
+    cands = {{PK_ORDER_ELIM_SPIN, 0}};
+  } else {
     err = "unknown order";
     return false;
   }
@@ -445,14 +520,15 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   Greedy best_g;
   double best_cost = std::numeric_limits<double>::infinity();
   int32_t best_order = -1;
-  for (int32_t o : cands) {
+  for (const auto& cand : cands) {
+    const int32_t o = cand.first;
     Network net;
     if (o == PK_ORDER_GREEDY_EDGE)
       edge_network(k, q, net);
     else
       spin_network(k, q, net);
     Greedy g;
-    run_order(net, o, g);
+    run_order(net, o, g, cand.second);
     // cost in complex MACs at this q
     double c = 0;
     for (size_t s = 0; s < g.seq.pairs.size(); ++s) {

@@ -8,7 +8,7 @@ import math
 
 import numpy as np
 
-MAXRUNS = 12
+MAXRUNS = 20
 
 
 class Recipe(C.Structure):
