@@ -7,8 +7,9 @@ over/under per crossing; every knot is evaluated at q = 2, 3, 5 (t = i, e^{i pi/
 (3+sqrt 5)/2).  One step = Z(q) and V_K(t(q)) for all 64 x 3 = 192 (knot, q) pairs, all
 on the GPU through libpk.  `value` is knot evaluations per second (one knot = one
 (knot, q) pair), whole job, in the headline precision (split FP32 by default), with
-every plan's program resident in HBM (per-plan state buffers; the plans share one
-tensor arena) and L2 flushed between steps.  The same workload is then run once in
+every plan's program resident in HBM (one workspace per plan) and the 192 plans'
+launch sequences replayed as independent branches of one CUDA graph; L2 is flushed
+between steps.  The same workload is then run once in
 complex64 and once in complex128; the relative error of every evaluation against
 complex128 is reported.
 
@@ -43,7 +44,7 @@ def log(msg):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="split", choices=["split", "c64", "c128"])
@@ -307,41 +308,39 @@ def main():
     prec = args.precision
     dev = f"cuda:{local}"
 
-    def buffers(pr):
-        """Per-plan state buffers (resident programs) and one shared tensor arena."""
-        sizes = [p.state_bytes(pr) for p in plans]
-        states = [torch.empty(max(s, 256), dtype=torch.uint8, device=dev) for s, _ in sizes]
-        arena = torch.empty(max(a for _, a in sizes) + 256, dtype=torch.uint8, device=dev)
-        for p, s in zip(plans, states):
-            pk.upload(p, pr, s)
-        return states, arena
+    def workspaces(pr):
+        """A full workspace per plan (program uploaded, resident in HBM)."""
+        ws = [torch.empty(p.workspace_bytes(pr) + 256, dtype=torch.uint8, device=dev) for p in plans]
+        for p, w in zip(plans, ws):
+            pk.upload(p, pr, w)
+        return ws
 
-    def one_pass(pr, states, arena, subset=None):
-        for i, (p, s) in enumerate(zip(plans, states)):
-            if subset is None or i in subset:
-                pk.launch_arena(p, pr, s, arena)
+    def results(pr, ws):
+        return [pk.download(p, pr, w) for p, w in zip(plans, ws)]
 
-    def results(pr, states):
-        return [pk.download(p, pr, s) for p, s in zip(plans, states)]
-
-    states, arena = buffers(prec)
+    # every plan's kernels recorded as an independent branch of one CUDA graph
+    ws = workspaces(prec)
+    group = pk.Group(plans, prec, ws)
     torch.cuda.synchronize()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    log("workspaces and graph ready")
 
-    # warm-up: W passes, the last one with an event pair around every launch
-    for _ in range(max(0, args.warmup - 1)):
-        one_pass(prec, states, arena)
+    # warm-up: W replays; then one sequential pass with an event pair around every launch
+    for _ in range(args.warmup):
+        group.launch()
+    torch.cuda.synchronize()
     prof = {}
-    for p, s in zip(plans, states):
-        for kname, d in pk.profile(p, prec, s, arena).items():
+    for p, w in zip(plans, ws):
+        for kname, d in pk.profile(p, prec, w).items():
             acc = prof.setdefault(kname, {"ms": 0.0, "launches": 0.0, "cmacs": 0.0, "bytes": 0.0})
             for f in acc:
                 acc[f] += d[f]
+    group.launch()
     torch.cuda.synchronize()
-    res_main = results(prec, states)
+    res_main = results(prec, ws)
     log("warm-up done")
 
-    # timed region: K steps, L2 flushed between steps (outside the events)
+    # timed region: K replays, L2 flushed between steps (outside the events)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -352,7 +351,7 @@ def main():
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        one_pass(prec, states, arena)
+        group.launch()
         b.record(stream)
         b.synchronize()
         times.append(a.elapsed_time(b))
@@ -367,43 +366,45 @@ def main():
     evals = len(plans)
     value = world * evals / (step_ms / 1000.0)
 
-    # end to end through the public API: program host->device (pinned), kernels,
-    # scaled result device->host, for every evaluation
+    # end to end through the public API: every program host->device (pinned), the
+    # kernels, every scaled result device->host
     h2d = sum(len(p.debug_blob(0)) for p in plans)
     d2h = 32 * len(plans)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    for p, s in zip(plans, states):
-        pk.upload(p, prec, s)
-        pk.launch_arena(p, prec, s, arena)
-        pk.download(p, prec, s)
+    for p, w in zip(plans, ws):
+        pk.upload(p, prec, w)
+    group.launch()
+    results(prec, ws)
     e2e_s = time.perf_counter() - t1
     e2e_val = world * evals / e2e_s
     log("end-to-end pass")
-    del states, arena
+    del group, ws
     torch.cuda.empty_cache()
 
-    # the same workload once in each other precision; errors against complex128
+    # the same workload once in each other precision (same concurrent execution);
+    # errors against complex128
     compare = {}
     res_by = {prec: res_main}
     if not args.skip_compare:
         for pr in ("c64", "c128"):
             if pr == prec:
                 continue
-            st2, ar2 = buffers(pr)
-            one_pass(pr, st2, ar2, subset=set(range(min(6, len(plans)))))   # loads the kernels
+            ws2 = workspaces(pr)
+            g2 = pk.Group(plans, pr, ws2)
+            g2.launch()                         # loads the kernels
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            one_pass(pr, st2, ar2)
+            g2.launch()
             b.record(stream)
             b.synchronize()
             ms = a.elapsed_time(b)
-            res_by[pr] = results(pr, st2)
+            res_by[pr] = results(pr, ws2)
             compare[pr] = {"value": world * evals / (ms / 1000.0), "unit": "knots/s",
-                           "ms_per_step": ms, "note": "one timed pass after loading the kernels"}
-            del st2, ar2
+                           "ms_per_step": ms, "note": "one timed replay after a warm-up replay"}
+            del g2, ws2
             torch.cuda.empty_cache()
             log(f"{pr} pass")
         if "c128" in res_by:

@@ -172,8 +172,10 @@ pk_status pk_eval(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_work
 /* The three stages of pk_eval, asynchronous on the context's stream:
  * pk_upload copies the plan's initial-tensor recipe into the workspace (host->device);
  * pk_launch enqueues every kernel of every slice (the workspace must hold an uploaded
- * recipe of the same plan and precision); pk_download waits for the stream, copies
- * the scaled result back and applies A(q). */
+ * recipe of the same plan and precision); the first launch for a given workspace and
+ * precision records the sequence into a CUDA graph (on a private stream of the
+ * context), later launches replay it, so a plan should keep using the same buffers;
+ * pk_download waits for the stream, copies the scaled result back and applies A(q). */
 pk_status pk_upload(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                     uint64_t workspace_bytes);
 pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
@@ -215,6 +217,20 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
  * algorithmic bytes (|A| + |B| + |C| at the precision's element size).  20 doubles. */
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                      uint64_t workspace_bytes, void* d_arena, uint64_t arena_bytes, double* out);
+
+/* ---- groups of plans run concurrently ------------------------------------------- */
+
+/* n plans, each with its own full workspace (already uploaded with pk_upload), whose
+ * launch sequences are recorded as independent branches of one CUDA graph, so the GPU
+ * overlaps the plans' (often small, latency-bound) kernels.  pk_group_launch replays
+ * it on the context's stream; results are read per plan with pk_download.  The
+ * workspaces must stay allocated while the group exists. */
+typedef struct pk_group pk_group;
+pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, int32_t precision,
+                          void* const* d_workspaces, const uint64_t* workspace_bytes,
+                          pk_group** out);
+pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp);
+void pk_group_destroy(pk_group* grp);
 
 /* ---- batched evaluation (many knots in one launch) ------------------------------- */
 

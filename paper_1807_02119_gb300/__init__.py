@@ -29,7 +29,8 @@ EXPORTED = [
     "pk_launch", "pk_download", "pk_plan_launches", "pk_jones_from_z", "pk_plan_debug_blob",
     "pk_profile", "pk_eval_noalloc", "pk_plan_state_bytes", "pk_launch_arena",
     "pk_batch_create", "pk_batch_workspace_bytes", "pk_batch_upload", "pk_batch_launch",
-    "pk_batch_download", "pk_eval_batch", "pk_batch_destroy",
+    "pk_batch_download", "pk_eval_batch", "pk_batch_destroy", "pk_group_create",
+    "pk_group_launch", "pk_group_destroy",
 ]
 
 
@@ -105,6 +106,9 @@ def lib():
         "pk_batch_download": [vp, vp, vp, P(pk_scaled), P(pk_scaled)],
         "pk_eval_batch": [vp, P(vp), i32, i32, vp, u64, P(pk_scaled), P(pk_scaled)],
         "pk_batch_destroy": [vp],
+        "pk_group_create": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
+        "pk_group_launch": [vp, vp],
+        "pk_group_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -429,3 +433,32 @@ def evaluate_batch(plans, precision="split", ws=None):
     b.upload(ws)
     b.launch(ws)
     return b.download(ws)
+
+
+class Group:
+    """pk_group: plans (each with its own uploaded workspace) replayed concurrently as
+    independent branches of one CUDA graph."""
+
+    def __init__(self, plans, precision, workspaces):
+        self.plans = list(plans)
+        self.ctx = self.plans[0].ctx
+        self.ws = list(workspaces)
+        n = len(self.plans)
+        parr = (C.c_void_p * n)(*[p.h.value for p in self.plans])
+        warr = (C.c_void_p * n)(*[w.data_ptr() for w in self.ws])
+        barr = (C.c_uint64 * n)(*[w.numel() for w in self.ws])
+        h = C.c_void_p()
+        _check(lib().pk_group_create(self.ctx.h, parr, n, PRECISIONS[precision], warr, barr,
+                                     C.byref(h)), self.ctx)
+        self.h = h
+
+    def launch(self):
+        _check(lib().pk_group_launch(self.ctx.h, self.h), self.ctx)
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().pk_group_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass

@@ -66,6 +66,50 @@ pk_status check_ws(pk_ctx* ctx, const pk_plan* p, int32_t precision, void*& ws, 
   return PK_OK;
 }
 
+// Enqueues the plan's kernels on the context's stream.  The launch sequence is recorded
+// once into a CUDA graph on the context's private capture stream (for this state
+// buffer, arena and precision) and replayed afterwards; very long sequences (many
+// slices) are launched directly.
+pk_status launch_recorded(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* ws, void* arena) {
+  const pk::Plan& P = p->p;
+  const double nodes = (double)P.n_slices * (double)(P.steps.size() + 4);
+  if (nodes > 20000.0) {
+    cudaError_t e = pk::launch_plan(P, precision, ws, arena, ctx->stream);
+    return e == cudaSuccess ? PK_OK : cuda_fail(ctx, e, "launch");
+  }
+  PlanGraph& g = const_cast<pk_plan*>(p)->graph;
+  if (!(g.exec && g.ws == ws && g.arena == arena && g.precision == precision)) {
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    cudaError_t e = pk::prepare_kernels();
+    if (e == cudaSuccess && !ctx->capture)
+      e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph set-up");
+    e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
+    cudaError_t e1 = pk::launch_plan(P, precision, ws, arena, ctx->capture);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->capture, &graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e1 != cudaSuccess ? e1 : e2, "record launch sequence");
+    }
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g.exec = nullptr;
+      return cuda_fail(ctx, e, "instantiate graph");
+    }
+    g.ws = ws;
+    g.arena = arena;
+    g.precision = precision;
+  }
+  cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
+  return e == cudaSuccess ? PK_OK : cuda_fail(ctx, e, "graph launch");
+}
+
 }  // namespace
 
 extern "C" {
@@ -110,6 +154,7 @@ void pk_ctx_destroy(pk_ctx* ctx) {
       cudaFree(ctx->own_ws);
     }
     if (ctx->pinned_result) cudaFreeHost(ctx->pinned_result);
+    if (ctx->capture) cudaStreamDestroy(ctx->capture);
   }
   delete ctx;
 }
@@ -301,6 +346,7 @@ pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launche
 void pk_plan_destroy(pk_plan* p) {
   if (!p) return;
   if (p->pinned_program) cudaFreeHost(p->pinned_program);
+  if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
   delete p;
 }
 
@@ -336,9 +382,7 @@ pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_wo
   DeviceGuard g(ctx->device);
   pk_status s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
   if (s != PK_OK) return s;
-  cudaError_t e = pk::launch_plan(p->p, precision, d_workspace,
-                                  (char*)d_workspace + p->p.off_arena, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
+  return launch_recorded(ctx, p, precision, d_workspace, (char*)d_workspace + p->p.off_arena);
   return PK_OK;
 }
 
@@ -369,9 +413,7 @@ pk_status pk_launch_arena(pk_ctx* ctx, const pk_plan* p, int32_t precision, void
   DeviceGuard g(ctx->device);
   pk_status s = check_split(ctx, p, precision, d_state, state_bytes, d_arena, arena_bytes);
   if (s != PK_OK) return s;
-  cudaError_t e = pk::launch_plan(p->p, precision, d_state, d_arena, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
-  return PK_OK;
+  return launch_recorded(ctx, p, precision, d_state, d_arena);
 }
 
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
@@ -390,6 +432,76 @@ pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_w
   cudaError_t e = pk::profile_plan(p->p, precision, d_workspace, d_arena, ctx->stream, out);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "profile");
   return PK_OK;
+}
+
+}  // extern "C"
+
+struct pk_group {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t n = 0;
+};
+
+extern "C" {
+
+pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, int32_t precision,
+                          void* const* d_workspaces, const uint64_t* workspace_bytes,
+                          pk_group** out) {
+  if (!ctx || !out || n < 0 || (n > 0 && (!plans || !d_workspaces || !workspace_bytes)) ||
+      !valid_precision(precision))
+    return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  pk_group* grp = new (std::nothrow) pk_group();
+  if (!grp) return fail(ctx, PK_ENOMEM, "out of host memory");
+  grp->n = n;
+  cudaError_t e = pk::prepare_kernels();
+  if (e == cudaSuccess && !ctx->capture) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaGraphCreate(&grp->graph, 0);
+  for (int32_t i = 0; e == cudaSuccess && i < n; ++i) {
+    void* ws = d_workspaces[i];
+    uint64_t bytes = workspace_bytes[i];
+    pk_status s = check_ws(ctx, plans[i], precision, ws, bytes);
+    if (s != PK_OK || ws == nullptr) {
+      pk_group_destroy(grp);
+      return s != PK_OK ? s : fail(ctx, PK_EINVAL, "null workspace");
+    }
+    e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    cudaError_t e1 = pk::launch_plan(plans[i]->p, precision, ws,
+                                     (char*)ws + plans[i]->p.off_arena, ctx->capture);
+    cudaGraph_t child = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->capture, &child);
+    e = e1 != cudaSuccess ? e1 : e2;
+    if (e == cudaSuccess) {
+      cudaGraphNode_t node;
+      e = cudaGraphAddChildGraphNode(&node, grp->graph, nullptr, 0, child);  // no dependencies
+    }
+    if (child) cudaGraphDestroy(child);
+  }
+  if (e == cudaSuccess && n > 0) e = cudaGraphInstantiate(&grp->exec, grp->graph, 0);
+  if (e != cudaSuccess) {
+    pk_group_destroy(grp);
+    return cuda_fail(ctx, e, "group graph");
+  }
+  *out = grp;
+  return PK_OK;
+}
+
+pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp) {
+  if (!ctx || !grp) return fail(ctx, PK_EINVAL, "bad argument");
+  if (grp->n == 0) return PK_OK;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaGraphLaunch(grp->exec, ctx->stream);
+  return e == cudaSuccess ? PK_OK : cuda_fail(ctx, e, "group launch");
+}
+
+void pk_group_destroy(pk_group* grp) {
+  if (!grp) return;
+  if (grp->exec) cudaGraphExecDestroy(grp->exec);
+  if (grp->graph) cudaGraphDestroy(grp->graph);
+  delete grp;
 }
 
 pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_scaled* V) {

@@ -11,6 +11,7 @@
 struct pk_ctx {
   int32_t device = -1;
   cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;  // private stream on which launch sequences are recorded
   std::string err;
   void* own_ws = nullptr;
   uint64_t own_ws_bytes = 0;
@@ -19,9 +20,17 @@ struct pk_ctx {
 struct pk_knot {
   pk::Knot k;
 };
+// A plan's launch sequence recorded as a CUDA graph for one (state, arena, precision).
+struct PlanGraph {
+  void* ws = nullptr;
+  void* arena = nullptr;
+  int32_t precision = -1;
+  cudaGraphExec_t exec = nullptr;
+};
 struct pk_plan {
   pk::Plan p;
   uint8_t* pinned_program = nullptr;
+  PlanGraph graph;
 };
 
 namespace pk {
@@ -32,4 +41,7 @@ cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,
 // Same, with CUDA-event timing per kernel class; waits for the stream (launch.cu).
 cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,
                          cudaStream_t stream, double* out);
+// Sets the kernel attributes launch_plan relies on (shared-memory limits), once per
+// device; call before recording a launch sequence into a graph (launch.cu).
+cudaError_t prepare_kernels();
 }  // namespace pk

@@ -90,11 +90,7 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
     fn = k_rows<R, 32>;
   else
     fn = k_rows<R, 0>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  fn<<<(unsigned)blocks, 256, sm, st>>>(s, arena, meta);
+  fn<<<(unsigned)blocks, 256, sm, st>>>(s, arena, meta);  // limit raised by prepare_kernels
   return cudaGetLastError();
 }
 
@@ -242,13 +238,45 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
 
 }  // namespace
 
+namespace {
+template <typename R>
+cudaError_t raise_rows_smem() {
+  const int lim = 200 * 1024;
+  void (*fns[])(const Step, Cx<R>*, Meta*) = {k_rows<R, 1>,  k_rows<R, 2>,  k_rows<R, 4>,
+                                              k_rows<R, 8>,  k_rows<R, 16>, k_rows<R, 32>,
+                                              k_rows<R, 0>};
+  for (auto f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t prepare_kernels() {
+  static bool done[256] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 256 && done[dev]) return cudaSuccess;
+  if ((e = raise_rows_smem<double>()) != cudaSuccess) return e;
+  if ((e = raise_rows_smem<float>()) != cudaSuccess) return e;
+  if ((e = raise_rows_smem<ff>()) != cudaSuccess) return e;
+  if (dev >= 0 && dev < 256) done[dev] = true;
+  return cudaSuccess;
+}
+
 cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,
                         cudaStream_t stream) {
+  cudaError_t e = prepare_kernels();
+  if (e != cudaSuccess) return e;
   return launch_impl(p, precision, ws, arena, stream, nullptr);
 }
 
 cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,
                          cudaStream_t stream, double* out) {
+  cudaError_t pe = prepare_kernels();
+  if (pe != cudaSuccess) return pe;
   Prof prof;
   cudaError_t e = launch_impl(p, precision, ws, arena, stream, &prof);
   cudaError_t e2 = cudaStreamSynchronize(stream);

@@ -84,3 +84,26 @@ def test_batch_mixed_q_slices_and_trivial(ctx):
         assert rel_err(sc(z), sc(zs)) <= TOL["split"]
         assert rel_err(sc(v), sc(vs)) <= TOL["split"]
     assert abs(V1[-2].to_complex() - 1) < 1e-12 and abs(V1[-1].to_complex() - 1) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["split", "c128"])
+def test_group_concurrent_replay(ctx, prec):
+    """Plans recorded as independent graph branches (run concurrently) give the same
+    results as evaluating them one by one, on two replays."""
+    import torch
+    knots = kg.knot_suite("scale")[:6]
+    plans = []
+    for k in knots:
+        kn = pk.Knot.from_pd(ctx, k.pd, outer=k.outer)
+        plans += [pk.Plan(ctx, kn, q) for q in (2, 3)]
+    ws = [torch.empty(p.workspace_bytes(prec) + 256, dtype=torch.uint8, device="cuda")
+          for p in plans]
+    for p, w in zip(plans, ws):
+        pk.upload(p, prec, w)
+    g = pk.Group(plans, prec, ws)
+    for _ in range(2):
+        g.launch()
+        got = [pk.download(p, prec, w) for p, w in zip(plans, ws)]
+        for p, (z, v) in zip(plans, got):
+            zs, vs = pk.evaluate(p, prec)
+            assert rel_err(sc(z), sc(zs)) <= TOL[prec] and rel_err(sc(v), sc(vs)) <= TOL[prec]
