@@ -46,7 +46,8 @@ typedef enum {
   PK_ETOOWIDE = 4,   /* plan exceeds the slicing limits                                 */
   PK_ECUDA = 5,      /* a CUDA runtime call failed                                      */
   PK_ETIMEOUT = 6,   /* a bounded device wait gave up                                   */
-  PK_ENODEVICE = 7   /* operation needs a GPU context (device >= 0)                     */
+  PK_ENODEVICE = 7,  /* operation needs a GPU context (device >= 0)                     */
+  PK_EZERO = 8       /* Z is zero, so log-derivatives are undefined                     */
 } pk_status;
 
 typedef enum {
@@ -77,6 +78,11 @@ typedef enum {
  * the planner choose per step by its shape). */
 #define PK_FLAG_FORCE_GEMM 1 /* every two-operand step on the tiled GEMM kernel           */
 #define PK_FLAG_FORCE_ROWS 2 /* every step on the row kernel                               */
+#define PK_FLAG_GRAD 4       /* also build the reverse (adjoint) program used by pk_grad.
+                                The network then keeps every edge group as a tensor (a pair
+                                of opposite-sign parallel edges is not dropped, loops become
+                                vectors over their vertex's spin) and only spin-network
+                                orders are used; Z is unchanged                              */
 
 typedef struct {
   int32_t order;             /* pk_order                                                    */
@@ -87,6 +93,18 @@ typedef struct {
   int32_t tail_steps;        /* PK_C64: this many final contractions run in complex128
                                 (<= 0: none)                                                 */
   int32_t restarts;          /* min-fill restarts for PK_ORDER_FILL_SPIN / AUTO (0 -> 8)    */
+  int32_t checkpoint_stride; /* PK_FLAG_GRAD: the reverse pass keeps the forward
+                                intermediates whose tree level (leaves 0, a step's result
+                                1 + its operands' maximum) is a multiple of this and
+                                recomputes the others from them (<= 1: keep all)             */
+  const double* edge_weights;/* NULL for the Jones weights of Eq. clause, or 4 doubles per
+                                Tait edge e (pk_knot_edges order): the clause matrix of e is
+                                diag (w[4e] + i w[4e+1]) and off-diagonal (w[4e+2] + i
+                                w[4e+3]): a general anisotropic complex Potts instance.
+                                Read during pk_plan_create only.  V is then reported with
+                                the A(q) of the standard weights (meaningless unless they
+                                are those weights); such networks are general (see
+                                PK_FLAG_GRAD) and use spin-network orders                   */
 } pk_plan_opts;
 
 typedef struct {
@@ -277,6 +295,54 @@ pk_status pk_eval_noalloc(pk_ctx* ctx, const pk_plan* p, int32_t precision, pk_s
 
 /* Host-side normalisation only: V = A(q) Z for the knot's (n_v, w, tau) (Eq. JonesPotts). */
 pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_scaled* V);
+
+/* ---- reverse pass (adjoint contraction) ------------------------------------------
+ *
+ * Z = sum over spin states of prod_e T_e[s_u, s_v] (Sec. II) is linear in every entry
+ * of every clause matrix T_e, so dZ/dT_e[a, b] is the same sum restricted to
+ * s_u = a, s_v = b with T_e left out: (T_e[a,b] / Z) dZ/dT_e[a,b] is the (complex) joint
+ * distribution of the two spins of edge e ("edge-resolved Potts correlations").  pk_grad
+ * computes every dZ/dT_e in one reverse pass over the plan's contraction tree: for a step
+ * C = sum A B the adjoints are dZ/dA = sum C' B and dZ/dB = sum A C' (C' = dZ/dC; no
+ * complex conjugate: Z is holomorphic in every entry), each again a pairwise contraction
+ * run by the same kernels, with the forward intermediates kept at every
+ * pk_plan_opts.checkpoint_stride-th tree level and the others recomputed.  Parallel
+ * edges share one tensor M = prod T_e (entrywise); dZ/dT_e = dZ/dM * prod_{e' != e} T_e'. */
+
+/* Device workspace of pk_grad for a plan made with PK_FLAG_GRAD. */
+pk_status pk_grad_workspace_bytes(const pk_plan* p, int32_t precision, uint64_t* bytes);
+
+/* Z, V and the reverse pass.  d_workspace: NULL (the context's own buffer) or at least
+ * pk_grad_workspace_bytes, 256-byte aligned.  dlogZ_dT (may be NULL): 2*n_e*q*q
+ * doubles, entry ((e*q + a)*q + b) = re, im of (1/Z) dZ/dT_e[a, b] with a the spin of
+ * edge e's first vertex and b of its second (pk_knot_edges order); for a loop only
+ * a == b is defined, off-diagonal entries are 0.  dlogV_dt (may be NULL): 2 doubles,
+ * (1/V) dV/dt at fixed q: the network's dimension q stays fixed while t moves through
+ * the clause weights -t^-eps and through A = (-1)^(w+n_v+1) t^k (t+1)^-(n_v+1), giving
+ * k/t - (n_v+1)/(t+1) + sum_e eps_e t^(-eps_e-1) sum_a (1/Z) dZ/dT_e[a,a].  It is not the
+ * derivative of the Jones polynomial (which would move q as well); NaN when the plan's
+ * weights are not the standard ones.  Errors: PK_EINVAL (plan without PK_FLAG_GRAD),
+ * PK_EZERO (Z = 0), PK_ENOMEM, PK_ECUDA.  Blocks until the results are on the host. */
+pk_status pk_grad(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                  uint64_t workspace_bytes, pk_scaled* Z, pk_scaled* V, double* dlogZ_dT,
+                  double* dlogV_dt);
+
+/* Host-side last stage of pk_grad, for checking it without a GPU: acc holds, per edge
+ * group g of the plan (pk_grad_stats out[7] groups), 2*q*q doubles of dZ/dM_g scaled by
+ * 2^-acc_exp[g] (row-major over (spin of the group's lower vertex, spin of the higher);
+ * a loop uses the first q entries), and Z.  Writes dlogZ_dT and dlogV_dt as pk_grad. */
+pk_status pk_grad_from_accumulators(const pk_plan* p, const double* acc, const int64_t* acc_exp,
+                                    const pk_scaled* Z, double* dlogZ_dT, double* dlogV_dt);
+
+/* Reverse-program statistics of a PK_FLAG_GRAD plan, 10 doubles: complex multiply-adds
+ * per slice of the forward, recompute and adjoint steps; their step counts; arena
+ * elements; forward intermediates kept as checkpoints; edge groups; slices. */
+pk_status pk_grad_stats(const pk_plan* p, double* out);
+
+/* New clause weights for a plan made with PK_FLAG_GRAD or edge_weights (same layout as
+ * pk_plan_opts.edge_weights; NULL restores the standard weights of t(q)).  The order,
+ * slicing and arena are unchanged; the next pk_upload / pk_eval / pk_grad uses them. */
+pk_status pk_plan_set_weights(pk_plan* p, const double* edge_weights);
 
 #ifdef __cplusplus
 }

@@ -14,12 +14,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpk.so")
 
 PK_C128, PK_C64, PK_SPLIT = 0, 1, 2
-FLAG_FORCE_GEMM, FLAG_FORCE_ROWS = 1, 2
+FLAG_FORCE_GEMM, FLAG_FORCE_ROWS, FLAG_GRAD = 1, 2, 4
 PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split": PK_SPLIT}
 ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4,
           "fill_spin": 5}
 STATUS = {0: "PK_OK", 1: "PK_EINVAL", 2: "PK_ENOTKNOT", 3: "PK_ENOMEM", 4: "PK_ETOOWIDE",
-          5: "PK_ECUDA", 6: "PK_ETIMEOUT", 7: "PK_ENODEVICE"}
+          5: "PK_ECUDA", 6: "PK_ETIMEOUT", 7: "PK_ENODEVICE", 8: "PK_EZERO"}
 
 EXPORTED = [
     "pk_ctx_create", "pk_ctx_set_stream", "pk_last_error", "pk_ctx_destroy",
@@ -30,7 +30,8 @@ EXPORTED = [
     "pk_profile", "pk_eval_noalloc", "pk_plan_state_bytes", "pk_launch_arena",
     "pk_batch_create", "pk_batch_workspace_bytes", "pk_batch_upload", "pk_batch_launch",
     "pk_batch_download", "pk_eval_batch", "pk_batch_destroy", "pk_group_create",
-    "pk_group_launch", "pk_group_destroy",
+    "pk_group_launch", "pk_group_destroy", "pk_grad_workspace_bytes", "pk_grad",
+    "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights",
 ]
 
 
@@ -47,7 +48,8 @@ class pk_scaled(C.Structure):
 class pk_plan_opts(C.Structure):
     _fields_ = [("order", C.c_int32), ("flags", C.c_int32), ("max_log2_elems", C.c_double),
                 ("max_log2_slices", C.c_double), ("tail_steps", C.c_int32),
-                ("restarts", C.c_int32)]
+                ("restarts", C.c_int32), ("checkpoint_stride", C.c_int32),
+                ("edge_weights", C.POINTER(C.c_double))]
 
 
 class pk_plan_stats(C.Structure):
@@ -109,6 +111,13 @@ def lib():
         "pk_group_create": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
         "pk_group_launch": [vp, vp],
         "pk_group_destroy": [vp],
+        "pk_grad_workspace_bytes": [vp, i32, P(u64)],
+        "pk_grad": [vp, vp, i32, vp, u64, P(pk_scaled), P(pk_scaled), P(C.c_double),
+                    P(C.c_double)],
+        "pk_grad_from_accumulators": [vp, P(C.c_double), P(i64), P(pk_scaled), P(C.c_double),
+                                      P(C.c_double)],
+        "pk_grad_stats": [vp, P(C.c_double)],
+        "pk_plan_set_weights": [vp, P(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -237,18 +246,60 @@ class Knot:
             pass
 
 
+def _weights_array(weights, n_e):
+    """4 doubles per Tait edge (diag re, diag im, off re, off im) from an (n_e, 2) array
+    of complex (diagonal, off-diagonal) clause weights."""
+    flat = []
+    for d, o in weights:
+        d, o = complex(d), complex(o)
+        flat += [d.real, d.imag, o.real, o.imag]
+    if len(flat) != 4 * n_e:
+        raise ValueError(f"expected {n_e} (diagonal, off-diagonal) weight pairs")
+    return (C.c_double * max(1, len(flat)))(*flat)
+
+
 class Plan:
+    """A contraction plan.  grad=True also builds the reverse-pass program (pk_grad);
+    weights: None (the Jones weights of Eq. clause) or one (diagonal, off-diagonal) complex
+    pair per Tait edge."""
+
     def __init__(self, ctx: Context, knot: Knot, q: int, order: str = "auto",
                  max_log2_elems: float = 0.0, max_log2_slices: float = 0.0, flags: int = 0,
-                 tail_steps: int = 0, restarts: int = 0):
-        o = pk_plan_opts(ORDERS[order], flags, max_log2_elems, max_log2_slices, tail_steps,
-                         restarts)
+                 tail_steps: int = 0, restarts: int = 0, grad: bool = False,
+                 checkpoint_stride: int = 0, weights=None):
+        w = None
+        if weights is not None:
+            w = _weights_array(weights, knot.info()["n_c"])
+        o = pk_plan_opts(ORDERS[order], flags | (FLAG_GRAD if grad else 0), max_log2_elems,
+                         max_log2_slices, tail_steps, restarts, checkpoint_stride,
+                         C.cast(w, C.POINTER(C.c_double)) if w is not None else None)
         h = C.c_void_p()
         _check(lib().pk_plan_create(ctx.h, knot.h, q, C.byref(o), C.byref(h)), ctx)
         self.h = h
         self.q = q
         self.knot = knot
         self.ctx = ctx
+        self.n_e = knot.info()["n_c"]
+
+    def set_weights(self, weights=None):
+        """pk_plan_set_weights: new (diagonal, off-diagonal) pairs per Tait edge, or the
+        standard weights of t(q) for None."""
+        w = _weights_array(weights, self.n_e) if weights is not None else None
+        _check(lib().pk_plan_set_weights(self.h, C.cast(w, C.POINTER(C.c_double))
+                                         if w is not None else None), self.ctx)
+
+    def grad_workspace_bytes(self, precision="c128") -> int:
+        b = C.c_uint64()
+        _check(lib().pk_grad_workspace_bytes(self.h, PRECISIONS[precision], C.byref(b)))
+        return b.value
+
+    def grad_stats(self) -> dict:
+        out = (C.c_double * 10)()
+        _check(lib().pk_grad_stats(self.h, out))
+        keys = ("cmacs_forward", "cmacs_recompute", "cmacs_adjoint", "steps_forward",
+                "steps_recompute", "steps_adjoint", "arena_elems", "checkpoints", "groups",
+                "slices")
+        return dict(zip(keys, list(out)))
 
     def stats(self) -> dict:
         s = pk_plan_stats()
@@ -462,3 +513,99 @@ class Group:
                 self.h = None
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- reverse pass
+
+def grad(plan: Plan, precision: str = "c128", ws=None):
+    """pk_grad: Z, V, (1/Z) dZ/dT_e[a, b] for every Tait edge e (numpy complex128 array of
+    shape (n_e, q, q)) and (1/V) dV/dt at fixed q.  The plan needs grad=True."""
+    import numpy as np
+    ctx = plan.ctx
+    if ctx.device < 0:
+        raise PkError(7, "grad needs a GPU context")
+    _torch_stream(ctx)
+    if ws is None:
+        import torch
+        ws = torch.empty(plan.grad_workspace_bytes(precision), dtype=torch.uint8,
+                         device=f"cuda:{ctx.device}")
+    q, n_e = plan.q, plan.n_e
+    z, v = pk_scaled(), pk_scaled()
+    dl = (C.c_double * max(1, 2 * n_e * q * q))()
+    dv = (C.c_double * 2)()
+    st = lib().pk_grad(ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
+                       ws.numel() * ws.element_size(), C.byref(z), C.byref(v), dl, dv)
+    knot_ok = st != 2
+    if st == 2:  # not a knot: Z and the derivatives of log Z are still defined
+        st = lib().pk_grad(ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
+                           ws.numel() * ws.element_size(), C.byref(z), None, dl, None)
+    _check(st, ctx)
+    arr = np.frombuffer(dl, dtype=np.float64)[:2 * n_e * q * q].copy()
+    dlogz = (arr[0::2] + 1j * arr[1::2]).reshape(n_e, q, q)
+    return (Scaled.of(z), Scaled.of(v) if knot_ok else None, dlogz,
+            complex(dv[0], dv[1]) if knot_ok else None)
+
+
+def grad_from_accumulators(plan: Plan, acc, acc_exp, z: Scaled):
+    """pk_grad_from_accumulators (host only): the last stage of pk_grad from per-group
+    adjoint accumulators (acc: complex array (groups, q*q); acc_exp: int array)."""
+    import numpy as np
+    q, n_e = plan.q, plan.n_e
+    a = np.ascontiguousarray(np.asarray(acc, dtype=np.complex128).reshape(-1)).view(np.float64)
+    a = np.ascontiguousarray(a)
+    ex = np.ascontiguousarray(np.asarray(acc_exp, dtype=np.int64))
+    zz = pk_scaled(z.re, z.im, z.exp2)
+    dl = (C.c_double * max(1, 2 * n_e * q * q))()
+    dv = (C.c_double * 2)()
+    _check(lib().pk_grad_from_accumulators(
+        plan.h, a.ctypes.data_as(C.POINTER(C.c_double)) if a.size else None,
+        ex.ctypes.data_as(C.POINTER(C.c_int64)) if ex.size else None, C.byref(zz), dl, dv))
+    arr = np.frombuffer(dl, dtype=np.float64)[:2 * n_e * q * q].copy()
+    return (arr[0::2] + 1j * arr[1::2]).reshape(n_e, q, q), complex(dv[0], dv[1])
+
+
+_LOGZ_FN = None
+
+
+def _logz_function():
+    global _LOGZ_FN
+    if _LOGZ_FN is not None:
+        return _LOGZ_FN
+    import math
+
+    import torch
+
+    class LogZ(torch.autograd.Function):
+        """log Z as a function of the clause weights, (n_e, 2) complex128 = (diagonal,
+        off-diagonal) per Tait edge.  The forward runs pk_grad (contraction and reverse
+        pass on the GPU); the backward returns the saved holomorphic derivatives in
+        PyTorch's convention for complex inputs (grad_output times their conjugate)."""
+
+        @staticmethod
+        def forward(ctx, weights, plan, precision):
+            plan.set_weights([(complex(d), complex(o)) for d, o in weights.detach().cpu().tolist()])
+            z, _, dlogz, _ = grad(plan, precision)
+            q = plan.q
+            eye = torch.eye(q, dtype=torch.bool)
+            d = torch.as_tensor(dlogz, dtype=torch.complex128)
+            jd = d[:, eye].sum(dim=1)
+            jo = d[:, ~eye].sum(dim=1)
+            ctx.save_for_backward(torch.stack([jd, jo], dim=1).to(weights.device))
+            logz = complex(math.log(abs(z.mantissa)) + z.exp2 * math.log(2.0),
+                           math.atan2(z.im, z.re))
+            return torch.tensor(logz, dtype=torch.complex128, device=weights.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (jac,) = ctx.saved_tensors
+            return g * jac.conj(), None, None
+
+    _LOGZ_FN = LogZ
+    return LogZ
+
+
+def log_z(plan: Plan, weights, precision: str = "c128"):
+    """torch: log Z(weights) with autograd through the reverse pass (plan made with
+    grad=True).  weights: complex128 tensor (n_e, 2) of (diagonal, off-diagonal) clause
+    weights per Tait edge.  The imaginary part is the principal argument of Z."""
+    return _logz_function().apply(weights, plan, precision)

@@ -2,6 +2,7 @@
 // normalisation V = A(q) Z (Eq. JonesPotts).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -44,8 +45,7 @@ struct DeviceGuard {
   }
 };
 
-pk_status check_ws(pk_ctx* ctx, const pk_plan* p, int32_t precision, void*& ws, uint64_t& bytes) {
-  uint64_t need = p->p.ws_bytes(precision);
+pk_status check_ws_need(pk_ctx* ctx, uint64_t need, void*& ws, uint64_t& bytes) {
   if (ws == nullptr) {
     if (ctx->own_ws_bytes < need) {
       if (ctx->own_ws) {
@@ -61,9 +61,13 @@ pk_status check_ws(pk_ctx* ctx, const pk_plan* p, int32_t precision, void*& ws, 
     ws = ctx->own_ws;
     bytes = ctx->own_ws_bytes;
   }
-  if (bytes < need) return fail(ctx, PK_ENOMEM, "workspace smaller than pk_plan_workspace_bytes");
+  if (bytes < need) return fail(ctx, PK_ENOMEM, "workspace smaller than the plan needs");
   if (((uintptr_t)ws & 255u) != 0) return fail(ctx, PK_EINVAL, "workspace must be 256-byte aligned");
   return PK_OK;
+}
+
+pk_status check_ws(pk_ctx* ctx, const pk_plan* p, int32_t precision, void*& ws, uint64_t& bytes) {
+  return check_ws_need(ctx, p->p.ws_bytes(precision), ws, bytes);
 }
 
 // Enqueues the plan's kernels on the context's stream.  The launch sequence is recorded
@@ -324,6 +328,25 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
     double v[3] = {P.factor.re, P.factor.im, (double)P.factor.e};
     buf.resize(sizeof(v));
     std::memcpy(buf.data(), v, sizeof(v));
+  } else if (which >= 6 && which <= 9 && P.grad.built) {
+    const pk::GradProgram& G = P.grad;
+    if (which == 6) {
+      buf.resize(sizeof(pk::Step) * G.steps.size());
+      if (!G.steps.empty()) std::memcpy(buf.data(), G.steps.data(), buf.size());
+    } else if (which == 7) {
+      int64_t v[16] = {(int64_t)G.steps.size(), G.n_meta, G.arena_elems, G.root_offset,
+                       G.root_meta, (int64_t)G.off_recipe, (int64_t)G.off_slots,
+                       (int64_t)G.off_leaves, (int64_t)G.leaves.size(), P.n_slices,
+                       (int64_t)sizeof(pk::GradLeaf), P.n_init, (int64_t)P.slots.size(), P.q,
+                       (int64_t)P.sliced.size(), (int64_t)sizeof(pk::Slot)};
+      buf.resize(sizeof(v));
+      std::memcpy(buf.data(), v, sizeof(v));
+    } else if (which == 8) {
+      buf = G.program;
+    } else {
+      buf.resize(G.phase.size());
+      if (!G.phase.empty()) std::memcpy(buf.data(), G.phase.data(), buf.size());
+    }
   } else {
     return PK_EINVAL;
   }
@@ -346,6 +369,7 @@ pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launche
 void pk_plan_destroy(pk_plan* p) {
   if (!p) return;
   if (p->pinned_program) cudaFreeHost(p->pinned_program);
+  if (p->pinned_grad) cudaFreeHost(p->pinned_grad);
   if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
   delete p;
 }
@@ -555,6 +579,104 @@ pk_status pk_eval(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_work
   s = pk_launch(ctx, p, precision, d_workspace, workspace_bytes);
   if (s != PK_OK) return s;
   return pk_download(ctx, p, precision, d_workspace, Z, V);
+}
+
+pk_status pk_grad_workspace_bytes(const pk_plan* p, int32_t precision, uint64_t* bytes) {
+  if (!p || !bytes || !valid_precision(precision) || !p->p.grad.built) return PK_EINVAL;
+  *bytes = p->p.grad.ws_bytes(precision);
+  return PK_OK;
+}
+
+pk_status pk_grad_stats(const pk_plan* p, double* out) {
+  if (!p || !out || !p->p.grad.built) return PK_EINVAL;
+  const pk::GradProgram& G = p->p.grad;
+  double n[3] = {0, 0, 0};
+  for (int8_t ph : G.phase) n[ph] += 1;
+  const double v[10] = {G.cmacs[0], G.cmacs[1], G.cmacs[2], n[0], n[1], n[2],
+                        (double)G.arena_elems, (double)G.n_checkpoints,
+                        (double)G.leaves.size(), (double)p->p.n_slices};
+  std::memcpy(out, v, sizeof(v));
+  return PK_OK;
+}
+
+pk_status pk_grad_from_accumulators(const pk_plan* p, const double* acc, const int64_t* acc_exp,
+                                    const pk_scaled* Z, double* dlogZ_dT, double* dlogV_dt) {
+  if (!p || !Z || !p->p.grad.built || (!acc && !p->p.groups.empty()) ||
+      (!acc_exp && !p->p.groups.empty()))
+    return PK_EINVAL;
+  pk::Scaled z;
+  z.re = Z->re;
+  z.im = Z->im;
+  z.e = Z->exp2;
+  return pk::grad_finalize(p->p, acc, acc_exp, z, dlogZ_dT, dlogV_dt) ? PK_OK : PK_EZERO;
+}
+
+pk_status pk_plan_set_weights(pk_plan* p, const double* edge_weights) {
+  if (!p || !p->p.general) return PK_EINVAL;
+  if (!pk::set_weights(p->p, edge_weights)) return PK_EINVAL;
+  if (p->pinned_program) {  // refilled from the new program by the next pk_upload
+    cudaFreeHost(p->pinned_program);
+    p->pinned_program = nullptr;
+  }
+  return PK_OK;
+}
+
+pk_status pk_grad(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                  uint64_t workspace_bytes, pk_scaled* Z, pk_scaled* V, double* dlogZ_dT,
+                  double* dlogV_dt) {
+  if (!ctx || !p || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (!p->p.grad.built) return fail(ctx, PK_EINVAL, "plan made without PK_FLAG_GRAD");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  const pk::Plan& P = p->p;
+  const pk::GradProgram& G = P.grad;
+  pk_status s = check_ws_need(ctx, G.ws_bytes(precision), d_workspace, workspace_bytes);
+  if (s != PK_OK) return s;
+  const uint64_t nl = std::max<size_t>(1, G.leaves.size());
+  const uint64_t acc_bytes = 16ull * (uint64_t)P.q * P.q * nl + 8ull * nl;
+  const uint64_t prog = (G.program.size() + 255) & ~uint64_t(255);
+  pk_plan* mp = const_cast<pk_plan*>(p);
+  if (!mp->pinned_grad &&
+      cudaMallocHost((void**)&mp->pinned_grad, prog + sizeof(pk::SliceResult) + acc_bytes) !=
+          cudaSuccess) {
+    mp->pinned_grad = nullptr;
+    return fail(ctx, PK_ENOMEM, "pinned host allocation failed");
+  }
+  uint8_t* host = mp->pinned_grad;
+  std::memcpy(host, G.program.data(), G.program.size());  // the current weights
+  char* ws = (char*)d_workspace;
+  cudaError_t e = cudaMemcpyAsync(ws, host, G.program.size(), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = pk::launch_grad(P, precision, ws, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host + prog, ws + G.off_result + sizeof(pk::SliceResult) * P.n_slices,
+                        sizeof(pk::SliceResult), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host + prog + sizeof(pk::SliceResult), ws + G.off_acc, acc_bytes,
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reverse pass");
+  const pk::SliceResult* r = (const pk::SliceResult*)(host + prog);
+  pk::Scaled z;
+  z.re = r->re;
+  z.im = r->im;
+  z.e = r->exp;
+  z.norm();
+  z = pk::s_mul(z, P.factor);
+  pk_scaled zs = to_abi(z);
+  if (Z) *Z = zs;
+  if (V) {
+    pk_knot kk;
+    kk.k = P.knot;
+    pk_status sv = pk_jones_from_z(&kk, P.q, &zs, V);
+    if (sv == PK_ENOTKNOT) return fail(ctx, sv, "not a knot: V undefined");
+    if (sv != PK_OK) return fail(ctx, sv, "3w + tau + 2 n_v + 2 not divisible by 4");
+  }
+  const double* acc = (const double*)(host + prog + sizeof(pk::SliceResult));
+  const int64_t* acc_exp = (const int64_t*)(host + prog + sizeof(pk::SliceResult) +
+                                            16ull * (uint64_t)P.q * P.q * nl);
+  if (!pk::grad_finalize(P, acc, acc_exp, z, dlogZ_dT, dlogV_dt))
+    return fail(ctx, PK_EZERO, "Z is zero: log-derivatives undefined");
+  return PK_OK;
 }
 
 }  // extern "C"

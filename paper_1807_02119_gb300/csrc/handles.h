@@ -30,6 +30,7 @@ struct PlanGraph {
 struct pk_plan {
   pk::Plan p;
   uint8_t* pinned_program = nullptr;
+  uint8_t* pinned_grad = nullptr;  // the reverse-pass program and its downloaded results
   PlanGraph graph;
 };
 
@@ -41,6 +42,8 @@ cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,
 // Same, with CUDA-event timing per kernel class; waits for the stream (launch.cu).
 cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,
                          cudaStream_t stream, double* out);
+// The reverse-pass program of a PK_FLAG_GRAD plan on `ws` (layout GradProgram::off_*).
+cudaError_t launch_grad(const Plan& p, int32_t precision, void* ws, cudaStream_t stream);
 // Sets the kernel attributes launch_plan relies on (shared-memory limits), once per
 // device; call before recording a launch sequence into a graph (launch.cu).
 cudaError_t prepare_kernels();

@@ -230,7 +230,8 @@ __device__ __forceinline__ void block_max_to_meta(S v, Meta* meta) {
 
 // ------------------------------------------------------------------ initial tensors
 // Entry e of an initial tensor: sum_{s<q} prod_j f_j(s, x_j) in double (x_j = the
-// digit of e at slot j's position, or the fixed value of a sliced index).
+// digit of e at slot j's position, or the fixed value of a sliced index); an absorbed
+// slot contributes its clause matrix entry M(s, x_j) (diagonal or off-diagonal weight).
 __device__ __forceinline__ void recipe_value(const Recipe& r, const Slot* slots, long long e, int q,
                                              const int* sdig, double& sre, double& sim) {
   sre = 0;
@@ -253,12 +254,11 @@ __device__ __forceinline__ void recipe_value(const Recipe& r, const Slot* slots,
         x = sdig[sl.slice_ord];
       }
       if (sl.absorbed) {
-        if (s == x) {
-          double nre = pre * sl.dre - pim * sl.dim;
-          double nim = pre * sl.dim + pim * sl.dre;
-          pre = nre;
-          pim = nim;
-        }
+        const double fre = s == x ? sl.dre : sl.ore, fim = s == x ? sl.dim : sl.oim;
+        const double nre = pre * fre - pim * fim;
+        const double nim = pre * fim + pim * fre;
+        pre = nre;
+        pim = nim;
       } else if (s != x) {
         zero = true;
         break;
@@ -668,6 +668,73 @@ __global__ void k_slice_result(const Cx<R>* arena, long long off, const Meta* me
   out[slice].re = to_double(v.re);
   out[slice].im = to_double(v.im);
   out[slice].exp = meta[tensor].exp;
+}
+
+// Reverse pass: adds this slice's adjoint of every clause tensor (true value: stored x
+// 2^exp) into its complex128 accumulator (true value: acc x 2^acc_exp), one block per
+// tensor.  Entries whose sliced coordinates differ from this slice's values get nothing
+// from it.  Both terms are brought to the larger of their binary exponents before the
+// sum, so neither can overflow; the block's order of work is fixed (deterministic).
+template <typename R>
+__global__ void __launch_bounds__(256) k_grad_accum(const GradLeaf* __restrict__ leaves,
+                                                    const Cx<R>* arena, const Meta* meta,
+                                                    Cx<double>* acc, long long* acc_exp, int q,
+                                                    long long slice) {
+  const GradLeaf L = leaves[blockIdx.x];
+  int sdig[2] = {0, 0};
+  for (int j = 0; j < 2; ++j)
+    if (L.slice_ord[j] >= 0) {
+      long long s = slice;
+      for (int i = 0; i < L.slice_ord[j]; ++i) s /= q;
+      sdig[j] = (int)(s % q);
+    }
+  const int n = L.rank == 2 ? q * q : (L.rank == 1 ? q : 1);
+  Cx<double>* A = acc + (long long)blockIdx.x * q * q;
+  const long long ev = L.meta >= 0 ? meta[L.meta].exp : 0;
+  auto incoming = [&](int e) -> Cx<double> {
+    const int d[2] = {L.rank == 2 ? e / q : e, L.rank == 2 ? e % q : 0};
+    long long off = 0;
+    for (int j = 0; j < L.rank && j < 2; ++j) {
+      if (L.slice_ord[j] >= 0) {
+        if (d[j] != sdig[j]) return {0.0, 0.0};
+      } else {
+        off += (long long)d[j] * L.stride[j];
+      }
+    }
+    if (L.meta < 0) return {1.0, 0.0};
+    const Cx<R> v = arena[L.offset + off];
+    return {to_double(v.re), to_double(v.im)};
+  };
+  __shared__ double red_i[256], red_a[256];
+  double mi = 0, ma = 0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const Cx<double> v = incoming(e);
+    mi = fmax(mi, fmax(fabs(v.re), fabs(v.im)));
+    ma = fmax(ma, fmax(fabs(A[e].re), fabs(A[e].im)));
+  }
+  red_i[threadIdx.x] = mi;
+  red_a[threadIdx.x] = ma;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red_i[threadIdx.x] = fmax(red_i[threadIdx.x], red_i[threadIdx.x + o]);
+      red_a[threadIdx.x] = fmax(red_a[threadIdx.x], red_a[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  mi = red_i[0];
+  ma = red_a[0];
+  if (!(mi > 0)) return;  // nothing from this slice (uniform across the block)
+  const long long eo = acc_exp[blockIdx.x];
+  long long enew = ev + bin_exp(mi);
+  if (ma > 0) enew = max(enew, eo + (long long)bin_exp(ma));
+  auto pow2 = [](long long d) { return ldexp(1.0, (int)max(-1100LL, min(1000LL, d))); };
+  const double so = ma > 0 ? pow2(eo - enew) : 0.0, si = pow2(ev - enew);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const Cx<double> v = incoming(e);
+    A[e] = {A[e].re * so + v.re * si, A[e].im * so + v.im * si};
+  }
+  if (threadIdx.x == 0) acc_exp[blockIdx.x] = enew;
 }
 
 // Sum over slices in double with a common exponent; fixed assignment and tree order.

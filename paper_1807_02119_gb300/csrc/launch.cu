@@ -94,14 +94,12 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
   return cudaGetLastError();
 }
 
+// One contraction step; `counter` is its split-K ticket, `by` its algorithmic bytes
+// (for the optional timing only).
 template <typename R>
-cudaError_t launch_step(const Plan& p, const Step& s, size_t i, Cx<R>* arena, Meta* meta,
-                        Cx<double>* partial, unsigned* counters, cudaStream_t stream, Marker& mk,
-                        double elem_bytes) {
+cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* partial,
+                        unsigned* counter, cudaStream_t stream, Marker& mk, double by) {
   const double cm = (double)s.R * (double)s.K * (double)s.N;
-  const double by = elem_bytes * (double)(p.tensors[p.steps[i].a].elems +
-                                          (p.steps[i].b >= 0 ? p.tensors[p.steps[i].b].elems : 0) +
-                                          p.tensors[p.steps[i].c].elems);
   const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
   cudaError_t e;
   if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
@@ -112,7 +110,7 @@ cudaError_t launch_step(const Plan& p, const Step& s, size_t i, Cx<R>* arena, Me
   } else if (s.kernel == KSPLITK) {
     mk.begin(2, cm, by);
     k_splitk<R><<<dim3((unsigned)s.chunks, (unsigned)(s.R * s.N)), 256, 0, stream>>>(
-        s, arena, meta, partial, counters + i);
+        s, arena, meta, partial, counter);
     mk.end();
     e = cudaGetLastError();
   } else {
@@ -121,6 +119,11 @@ cudaError_t launch_step(const Plan& p, const Step& s, size_t i, Cx<R>* arena, Me
     mk.end();
   }
   return e;
+}
+
+double step_bytes(const Plan& p, const Step& s, double elem_bytes) {
+  return elem_bytes * (double)(p.tensors[s.a].elems + (s.b >= 0 ? p.tensors[s.b].elems : 0) +
+                               p.tensors[s.c].elems);
 }
 
 // Steps [first, last) of the plan, all in storage type R.
@@ -133,8 +136,8 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
   Cx<double>* partial = (Cx<double>*)(base + p.off_scratch);
   unsigned* counters = (unsigned*)(base + p.off_counter);
   for (int32_t i = first; i < last; ++i) {
-    cudaError_t e = launch_step<R>(p, p.steps[i], (size_t)i, arena, meta, partial, counters,
-                                       stream, mk, (double)sizeof(Cx<R>));
+    cudaError_t e = launch_step<R>(p.steps[i], arena, meta, partial, counters + i, stream, mk,
+                                   step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)));
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -218,9 +221,9 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
         s.off_a = ts.off_a;
         s.off_b = ts.off_b;
         s.off_c = ts.off_c;
-        e = launch_step<double>(p, s, (size_t)ts.step, tail, meta,
-                                (Cx<double>*)(base + p.off_scratch),
-                                (unsigned*)(base + p.off_counter), stream, mk, 16.0);
+        e = launch_step<double>(s, tail, meta, (Cx<double>*)(base + p.off_scratch),
+                                (unsigned*)(base + p.off_counter) + ts.step, stream, mk,
+                                step_bytes(p, p.steps[ts.step], 16.0));
         if (e != cudaSuccess) return e;
       }
       mk.begin(3, 0, 0);
@@ -233,6 +236,50 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
   mk.begin(3, 0, 0);
   k_sum_slices<<<1, 256, 0, stream>>>(res, p.n_slices);
   mk.end();
+  return cudaGetLastError();
+}
+
+// The reverse-pass program of a PK_FLAG_GRAD plan (forward, recompute and adjoint
+// steps on one arena), per slice followed by the slice scalar and the accumulation of
+// the clause tensors' adjoints; then the sum over slices.
+template <typename R>
+cudaError_t launch_grad_impl(const Plan& p, char* base, cudaStream_t stream) {
+  const GradProgram& G = p.grad;
+  Marker mk{nullptr, stream};
+  Cx<R>* arena = (Cx<R>*)(base + G.off_arena);
+  Meta* meta = (Meta*)(base + G.off_meta);
+  SliceResult* res = (SliceResult*)(base + G.off_result);
+  Cx<double>* partial = (Cx<double>*)(base + G.off_scratch);
+  unsigned* counters = (unsigned*)(base + G.off_counter);
+  const uint64_t nl = std::max<size_t>(1, G.leaves.size());
+  Cx<double>* acc = (Cx<double>*)(base + G.off_acc);
+  long long* acc_exp = (long long*)(base + G.off_acc + 16ull * (uint64_t)p.q * p.q * nl);
+  if (p.n_init > 65535) return cudaErrorInvalidValue;
+  int64_t maxel = 1;
+  for (const auto& r : G.recipes) maxel = std::max<int64_t>(maxel, r.elems);
+  const unsigned bx = (unsigned)std::min<int64_t>((maxel + 255) / 256, 64);
+  cudaError_t e = cudaMemsetAsync(base + G.off_acc, 0, G.off_arena - G.off_acc, stream);
+  if (e != cudaSuccess) return e;
+  for (long long sl = 0; sl < p.n_slices; ++sl) {
+    e = cudaMemsetAsync(base + G.off_meta, 0, G.off_result - G.off_meta, stream);
+    if (e != cudaSuccess) return e;
+    if (p.n_init > 0) {
+      k_build<R><<<dim3(bx, (unsigned)p.n_init), 256, 0, stream>>>(
+          (const Recipe*)(base + G.off_recipe), (const Slot*)(base + G.off_slots), arena, meta,
+          p.q, sl, (int)p.sliced.size());
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    for (size_t i = 0; i < G.steps.size(); ++i) {
+      e = launch_step<R>(G.steps[i], arena, meta, partial, counters + i, stream, mk, 0.0);
+      if (e != cudaSuccess) return e;
+    }
+    k_slice_result<R><<<1, 32, 0, stream>>>(arena, G.root_offset, meta, G.root_meta, res, sl);
+    if (!G.leaves.empty())
+      k_grad_accum<R><<<(unsigned)G.leaves.size(), 256, 0, stream>>>(
+          (const GradLeaf*)(base + G.off_leaves), arena, meta, acc, acc_exp, p.q, sl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_sum_slices<<<1, 256, 0, stream>>>(res, p.n_slices);
   return cudaGetLastError();
 }
 
@@ -271,6 +318,15 @@ cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,
   cudaError_t e = prepare_kernels();
   if (e != cudaSuccess) return e;
   return launch_impl(p, precision, ws, arena, stream, nullptr);
+}
+
+cudaError_t launch_grad(const Plan& p, int32_t precision, void* ws, cudaStream_t stream) {
+  cudaError_t e = prepare_kernels();
+  if (e != cudaSuccess) return e;
+  if (!p.grad.built) return cudaErrorInvalidValue;
+  if (precision == PK_C128) return launch_grad_impl<double>(p, (char*)ws, stream);
+  if (precision == PK_SPLIT) return launch_grad_impl<ff>(p, (char*)ws, stream);
+  return launch_grad_impl<float>(p, (char*)ws, stream);
 }
 
 cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,

@@ -50,8 +50,8 @@ struct Run {
 
 // One initial tensor: entry(i...) = sum_{s<q} prod_j f_j(s, x_j) where x_j is the value of
 // slot j's index (a digit of the element, or a sliced index's fixed value) and
-// f_j(s, x) = (s == x) ? diag_j : 1 for an absorbed clause matrix, [s == x] for a COPY leg.
-// kind CONST1 is the scalar 1.
+// f_j(s, x) = (s == x) ? diag_j : off_j for an absorbed clause matrix (off_j = 1 for the
+// standard weights), [s == x] for a COPY leg.  kind CONST1 is the scalar 1.
 struct Recipe {
   int32_t kind;            // 0 = vertex sum, 1 = const 1
   int32_t rank;            // free dims
@@ -67,6 +67,7 @@ struct Slot {
   int32_t absorbed;        // 1: clause matrix, 0: COPY leg
   int32_t pad;
   double dre, dim;         // clause diagonal when absorbed
+  double ore, oim;         // clause off-diagonal when absorbed
 };
 
 enum KernelKind : int32_t { KROWS = 0, KSPLITK = 1, KGEMM = 2 };
@@ -128,6 +129,50 @@ struct TailStep {
   int64_t off_a, off_b, off_c;       // complex128 elements into the tail region
 };
 
+// Reverse pass: one record per clause tensor (merged edge group) of a gradient plan.
+// The adjoint dZ/dM of the group's matrix M (full shape q x q, or q for a loop vector)
+// is read from the arena with the strides below and added into an accumulator.
+struct GradLeaf {
+  int32_t meta;            // bookkeeping slot of the adjoint; -1: the adjoint is the constant 1
+  int32_t rank;            // 2: clause matrix over (u, v); 1: loop vector over u
+  int32_t slice_ord[2];    // >= 0: full dim j is a sliced index with this ordinal
+  int64_t offset;          // adjoint's element offset in the arena
+  int64_t stride[2];       // adjoint's element stride of full dim j (0: broadcast)
+};
+
+// Per merged edge group of a general (weighted or gradient) plan: the clause tensor and
+// the Tait edges whose entrywise product it is.
+struct EdgeGroup {
+  int32_t u, v;            // u < v, or u == v for loops
+  int32_t leaf;            // initial tensor id
+  int32_t slot;            // index of its absorbed slot in Plan::slots
+  std::vector<int32_t> members;
+};
+
+// The program of a gradient plan: forward steps, then per checkpoint region the
+// recomputed intermediates and the adjoint steps, all on one arena.
+struct GradProgram {
+  bool built = false;
+  int32_t stride = 1;                // checkpoint stride in tree levels (<= 1: keep all)
+  std::vector<Step> steps;           // launch order; meta slots in a, b, c
+  std::vector<int8_t> phase;         // per step: 0 forward, 1 recompute, 2 adjoint
+  std::vector<Recipe> recipes;       // initial tensors at their offsets in this arena
+  std::vector<GradLeaf> leaves;      // one per EdgeGroup, same order
+  int32_t n_meta = 0;
+  int32_t n_checkpoints = 0;
+  int64_t arena_elems = 0;
+  int64_t partials = 0;
+  int64_t root_offset = 0;
+  int32_t root_meta = 0;
+  double cmacs[3] = {0, 0, 0};       // per slice, by phase
+  uint64_t off_recipe = 0, off_slots = 0, off_leaves = 0, off_meta = 0, off_counter = 0,
+           off_result = 0, off_scratch = 0, off_acc = 0, off_arena = 0;
+  std::vector<uint8_t> program;      // recipes | slots | leaves, copied by pk_grad
+  uint64_t ws_bytes(int32_t precision) const {
+    return off_arena + (uint64_t)arena_elems * (precision == PK_C64 ? 8ull : 16ull);
+  }
+};
+
 struct TensorInfo {
   std::vector<int32_t> dims;  // index ids, outermost first (row-major)
   int64_t elems = 1;
@@ -171,10 +216,35 @@ struct Plan {
   int32_t n_meta = 0;                // tensors + converted copies
   uint64_t off_tail = 0;             // byte offset of the tail region (split only)
   uint64_t off_conv = 0;             // byte offset of the ConvRec records (in the program)
+  // general networks (PK_FLAG_GRAD or custom weights): every edge group is a tensor
+  bool general = false;
+  bool std_weights = true;           // weights are (-t^-eps, 1) of t(q)
+  std::vector<std::array<double, 4>> weights;  // per Tait edge: diag re, im, off re, im
+  std::vector<EdgeGroup> groups;
+  std::vector<std::vector<int32_t>> leaf_dims;  // initial tensors' dims before slicing
+  GradProgram grad;
 };
 
+// Step descriptor for C = sum over the indices of X and Y that are not in `out` of X Y
+// (Y absent: the constant 1).  `a` is the operand with more indices (ties: X); the
+// result's layout is written to `cdims`.
+bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
+                const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
+                bool& swapped, std::vector<int32_t>& cdims, std::string& err);
 bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std::string& err);
+bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err);
+// Writes the clause values of p.weights into p.slots and both program blobs.
+void apply_weights(Plan& p);
+// New per-edge weights (4 doubles per Tait edge; NULL: the standard weights of t(q)) for a
+// general plan; false if a weight is not finite.
+bool set_weights(Plan& p, const double* w);
+// d log Z / dT_c for every Tait edge from the accumulated adjoints (acc: q*q complex per
+// group, exp: power-of-two exponent per group) and Z; dlogV/dt at the standard weights.
+// Returns false when Z is zero.
+bool grad_finalize(const Plan& p, const double* acc, const int64_t* acc_exp, const Scaled& z,
+                   double* dlogz, double* dlogv_dt);
 void clause_diag(int32_t q, int32_t mult, int32_t signsum, double& re, double& im);
+void t_of_q_value(int32_t q, double& re, double& im);  // t(q) of Eq. potts2jones
 Scaled jones_prefactor(const Knot& k, int32_t q);  // A(q) in its integer-exponent form
 
 }  // namespace pk

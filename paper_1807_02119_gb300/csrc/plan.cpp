@@ -83,6 +83,12 @@ static cd t_of_q(int32_t q) {
   if (q < 4) return cd((qd - 2) / 2, std::sqrt(qd * (4 - qd)) / 2);
   return cd(((qd - 2) + std::sqrt(qd * (qd - 4))) / 2, 0);
 }
+void t_of_q_value(int32_t q, double& re, double& im) {
+  const cd t = t_of_q(q);
+  re = t.real();
+  im = t.imag();
+}
+
 static cd c_pow(cd x, int64_t n) {
   if (n < 0) {
     x = 1.0 / x;
@@ -128,56 +134,107 @@ namespace {
 struct SlotSpec {
   int32_t index;     // index id
   int32_t absorbed;  // 1 = clause matrix, 0 = COPY leg
-  double dre, dim;
+  double dre, dim;   // clause diagonal
+  double ore, oim;   // clause off-diagonal
 };
 struct NetTensor {
   std::vector<int32_t> dims;  // index ids (initial layout: sorted ascending, outermost first)
   std::vector<SlotSpec> slots;
   int32_t kind = 0;           // 0 vertex sum, 1 const 1
+  int32_t group = -1;         // general networks: edge group whose clause tensor this is
 };
+struct Merged {
+  int32_t u, v, mult, signsum;
+  double dre, dim, ore, oim;  // entrywise product of the members' clause matrices
+  std::vector<int32_t> members;
+};
+
 struct Network {
   int32_t n_idx = 0;
   std::vector<NetTensor> t;
   Scaled factor = s_from(1, 0);
+  std::vector<Merged> groups;  // spin networks: the merged edge groups, in tensor order
 };
 
-struct Merged {
-  int32_t u, v, mult, signsum;
-};
+// Standard clause weights of one Tait edge: diagonal -t^-eps, off-diagonal 1 (Eq. clause).
+std::array<double, 4> std_weight(int32_t q, int32_t eps) {
+  double re, im;
+  clause_diag(q, 1, eps, re, im);
+  return {re, im, 1.0, 0.0};
+}
 
-void merge_edges(const Knot& k, int32_t q, std::vector<Merged>& out, Scaled& factor) {
-  std::map<std::pair<int32_t, int32_t>, std::pair<int32_t, int32_t>> m;
-  for (const auto& e : k.edges) {
-    if (e[0] == e[1]) {  // loop: constant factor T[s,s] = -t^-eps
+// Parallel edges (and, in general networks, loops at one vertex) form one group whose
+// clause matrix is the entrywise product of the members'.  Standard networks fold loops
+// into the constant factor and drop groups whose product is the all-ones matrix; general
+// networks keep every group as a tensor so that each edge weight has an adjoint.
+void merge_edges(const Knot& k, int32_t q, bool general, bool std_w,
+                 const std::vector<std::array<double, 4>>& w, std::vector<Merged>& out,
+                 Scaled& factor) {
+  std::map<std::pair<int32_t, int32_t>, Merged> m;
+  for (int32_t c = 0; c < (int32_t)k.edges.size(); ++c) {
+    const auto& e = k.edges[c];
+    if (e[0] == e[1] && !general) {  // loop: constant factor T[s,s] = -t^-eps
       double re, im;
       clause_diag(q, 1, e[2], re, im);
       factor = s_mul(factor, s_from(re, im));
       continue;
     }
     auto key = std::make_pair(std::min(e[0], e[1]), std::max(e[0], e[1]));
-    auto& mv = m[key];
-    mv.first += 1;
-    mv.second += e[2];
+    auto it = m.find(key);
+    if (it == m.end()) {
+      Merged g;
+      g.u = key.first;
+      g.v = key.second;
+      g.mult = 0;
+      g.signsum = 0;
+      g.dre = 1;
+      g.dim = 0;
+      g.ore = 1;
+      g.oim = 0;
+      it = m.emplace(key, g).first;
+    }
+    Merged& g = it->second;
+    g.mult += 1;
+    g.signsum += e[2];
+    g.members.push_back(c);
+    const double dre = g.dre * w[c][0] - g.dim * w[c][1], dim = g.dre * w[c][1] + g.dim * w[c][0];
+    const double ore = g.ore * w[c][2] - g.oim * w[c][3], oim = g.ore * w[c][3] + g.oim * w[c][2];
+    g.dre = dre;
+    g.dim = dim;
+    g.ore = ore;
+    g.oim = oim;
   }
   out.clear();
-  for (const auto& kv : m) {
-    int32_t mult = kv.second.first, ss = kv.second.second;
-    if (mult % 2 == 0 && ss == 0) continue;  // all-ones matrix: factorises, dropped
-    out.push_back({kv.first.first, kv.first.second, mult, ss});
+  for (auto& kv : m) {
+    Merged& g = kv.second;
+    if (std_w) {  // exact form of the product of standard weights
+      clause_diag(q, g.mult, g.signsum, g.dre, g.dim);
+      g.ore = 1;
+      g.oim = 0;
+      if (!general && g.mult % 2 == 0 && g.signsum == 0) continue;  // all-ones: factorises
+    }
+    out.push_back(g);
   }
 }
 
-void spin_network(const Knot& k, int32_t q, Network& net) {
-  std::vector<Merged> me;
-  merge_edges(k, q, me, net.factor);
+// Spin network.  A clause tensor T[a,b] = sum_s [s=a] M(s,b) is a COPY leg on u and an
+// absorbed slot on v; a loop vector L[a] = M(a,a) is a COPY leg and an absorbed slot on
+// the same spin.
+void spin_network(const Knot& k, int32_t q, bool general, bool std_w,
+                  const std::vector<std::array<double, 4>>& w, Network& net) {
+  std::vector<Merged>& me = net.groups;
+  merge_edges(k, q, general, std_w, w, me, net.factor);
   net.n_idx = k.n_v;
   std::vector<char> covered(k.n_v, 0);
-  for (const auto& e : me) {
+  for (int32_t gi = 0; gi < (int32_t)me.size(); ++gi) {
+    const auto& e = me[gi];
     NetTensor t;
-    t.dims = {e.u, e.v};
-    double re, im;
-    clause_diag(q, e.mult, e.signsum, re, im);
-    t.slots = {{e.u, 0, 0, 0}, {e.v, 1, re, im}};  // T[a,b] = sum_s [s=a] M(s,b)
+    if (e.u == e.v)
+      t.dims = {e.u};
+    else
+      t.dims = {e.u, e.v};
+    t.slots = {{e.u, 0, 0, 0, 0, 0}, {e.v, 1, e.dre, e.dim, e.ore, e.oim}};
+    t.group = gi;
     covered[e.u] = covered[e.v] = 1;
     net.t.push_back(t);
   }
@@ -187,17 +244,17 @@ void spin_network(const Knot& k, int32_t q, Network& net) {
 
 void edge_network(const Knot& k, int32_t q, Network& net) {
   std::vector<Merged> me;
-  merge_edges(k, q, me, net.factor);
+  std::vector<std::array<double, 4>> w;
+  for (const auto& e : k.edges) w.push_back(std_weight(q, e[2]));
+  merge_edges(k, q, false, true, w, me, net.factor);
   net.n_idx = (int32_t)me.size();
   std::vector<NetTensor> vt(k.n_v);
   for (int32_t i = 0; i < (int32_t)me.size(); ++i) {
     const auto& e = me[i];
-    double re, im;
-    clause_diag(q, e.mult, e.signsum, re, im);
     vt[e.u].dims.push_back(i);
-    vt[e.u].slots.push_back({i, 1, re, im});
+    vt[e.u].slots.push_back({i, 1, e.dre, e.dim, e.ore, e.oim});
     vt[e.v].dims.push_back(i);
-    vt[e.v].slots.push_back({i, 0, 0, 0});
+    vt[e.v].slots.push_back({i, 0, 0, 0, 0, 0});
   }
   net.t = std::move(vt);
 }
@@ -475,6 +532,163 @@ bool run_order(const Network& net, int32_t order, Greedy& g, uint64_t seed = 0) 
 
 }  // namespace
 
+// ------------------------------------------------------------------ step descriptors
+bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
+                const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
+                bool& swapped, std::vector<int32_t>& cdims, std::string& err) {
+  static const std::vector<int32_t> no_dims;
+  swapped = yd != nullptr && yd->size() > xd.size();
+  const bool hasb = yd != nullptr;
+  const auto& ad = swapped ? *yd : xd;
+  const auto& bd = !hasb ? no_dims : (swapped ? xd : *yd);
+  auto qpow = [&](int64_t e) {
+    int64_t r = 1;
+    for (int64_t i = 0; i < e; ++i) r *= q;
+    return r;
+  };
+  auto pos_in = [](const std::vector<int32_t>& d, int32_t v) -> int32_t {
+    for (size_t i = 0; i < d.size(); ++i)
+      if (d[i] == v) return (int32_t)i;
+    return -1;
+  };
+  auto in_c = [&](int32_t v) { return std::binary_search(out.begin(), out.end(), v); };
+  std::memset(&st, 0, sizeof(st));
+  st.b = hasb ? 0 : -1;
+  const int32_t ra = (int32_t)ad.size(), rb = (int32_t)bd.size();
+  auto stride_a = [&](int32_t v) -> int64_t {
+    int32_t pp = pos_in(ad, v);
+    return pp < 0 ? 0 : qpow(ra - 1 - pp);
+  };
+  auto stride_b = [&](int32_t v) -> int64_t {
+    int32_t pp = pos_in(bd, v);
+    return pp < 0 ? 0 : qpow(rb - 1 - pp);
+  };
+  std::vector<Run> rows, ks, ns;
+  std::vector<int32_t> row_dims, n_dims;
+  auto push = [&](std::vector<Run>& v, int64_t sa, int64_t sb) {
+    if (!v.empty()) {
+      Run& l = v.back();
+      if (sa == l.sa * l.size && sb == l.sb * l.size) {
+        l.size *= q;
+        return;
+      }
+    }
+    v.push_back({(int64_t)q, sa, sb});
+  };
+  for (int32_t i = ra - 1; i >= 0; --i) {  // inner -> outer
+    int32_t v = ad[i];
+    if (in_c(v)) {
+      push(rows, stride_a(v), stride_b(v));
+      row_dims.push_back(v);
+    } else {
+      push(ks, stride_a(v), stride_b(v));
+    }
+  }
+  for (int32_t i = rb - 1; i >= 0; --i) {
+    int32_t v = bd[i];
+    if (pos_in(ad, v) >= 0) continue;
+    if (in_c(v)) {
+      push(ns, 0, stride_b(v));
+      n_dims.push_back(v);
+    } else {
+      push(ks, 0, stride_b(v));
+    }
+  }
+  for (int32_t v : out)
+    if (pos_in(ad, v) < 0 && pos_in(bd, v) < 0) {
+      err = "internal: output index held by neither operand";
+      return false;
+    }
+  if ((int)rows.size() > kMaxRuns || (int)ks.size() > kMaxRuns || (int)ns.size() > kMaxRuns) {
+    err = "step has too many stride runs";
+    return false;
+  }
+  st.R = st.K = st.N = 1;
+  st.nrow = (int32_t)rows.size();
+  st.nk = (int32_t)ks.size();
+  st.nn = (int32_t)ns.size();
+  for (int i = 0; i < st.nrow; ++i) {
+    st.row[i] = rows[i];
+    st.R *= rows[i].size;
+  }
+  for (int i = 0; i < st.nk; ++i) {
+    st.kr[i] = ks[i];
+    st.K *= ks[i].size;
+  }
+  for (int i = 0; i < st.nn; ++i) {
+    st.nr[i] = ns[i];
+    st.N *= ns[i].size;
+  }
+  // C layout (outermost first): N dims (B order), then row dims (A order)
+  cdims.clear();
+  for (int32_t i = (int32_t)n_dims.size() - 1; i >= 0; --i) cdims.push_back(n_dims[i]);
+  for (int32_t i = (int32_t)row_dims.size() - 1; i >= 0; --i) cdims.push_back(row_dims[i]);
+  st.rank_c = (int32_t)cdims.size();
+  // GEMM view: batch / m / n runs with their C strides (C = [n-part, row-part])
+  {
+    std::vector<Run4> gbv, gmv, gnv;
+    auto push4 = [&](std::vector<Run4>& v, int64_t sa, int64_t sb, int64_t sc) {
+      if (!v.empty()) {
+        Run4& l = v.back();
+        if (sa == l.sa * l.size && sb == l.sb * l.size && sc == l.sc * l.size) {
+          l.size *= q;
+          return;
+        }
+      }
+      v.push_back({(int64_t)q, sa, sb, sc});
+    };
+    int64_t csr = 1;  // C stride of the next row dim (inner -> outer, A order)
+    for (int32_t i = ra - 1; i >= 0; --i) {
+      int32_t v = ad[i];
+      if (!in_c(v)) continue;
+      if (pos_in(bd, v) >= 0)
+        push4(gbv, stride_a(v), stride_b(v), csr);
+      else
+        push4(gmv, stride_a(v), 0, csr);
+      csr *= q;
+    }
+    int64_t csn = st.R;
+    for (int32_t i = rb - 1; i >= 0; --i) {
+      int32_t v = bd[i];
+      if (pos_in(ad, v) >= 0 || !in_c(v)) continue;
+      push4(gnv, 0, stride_b(v), csn);
+      csn *= q;
+    }
+    if ((int)gbv.size() > kMaxRuns || (int)gmv.size() > kMaxRuns || (int)gnv.size() > kMaxRuns) {
+      err = "step has too many stride runs";
+      return false;
+    }
+    st.ngb = (int32_t)gbv.size();
+    st.ngm = (int32_t)gmv.size();
+    st.ngn = (int32_t)gnv.size();
+    st.Bsz = st.M = 1;
+    for (int i = 0; i < st.ngb; ++i) {
+      st.gb[i] = gbv[i];
+      st.Bsz *= gbv[i].size;
+    }
+    for (int i = 0; i < st.ngm; ++i) {
+      st.gm[i] = gmv[i];
+      st.M *= gmv[i].size;
+    }
+    for (int i = 0; i < st.ngn; ++i) st.gn[i] = gnv[i];
+    st.a_kinner = (ra > 0 && !in_c(ad[ra - 1])) ? 1 : 0;
+    st.b_kinner = (rb > 0 && pos_in(ad, bd[rb - 1]) >= 0 && !in_c(bd[rb - 1])) ? 1 : 0;
+  }
+  const int64_t outs = st.R * st.N;
+  if (hasb && (flags & PK_FLAG_FORCE_GEMM))
+    st.kernel = KGEMM;
+  else if (flags & PK_FLAG_FORCE_ROWS)
+    st.kernel = KROWS;
+  else if (hasb && st.M >= 64 && st.N >= 32 && st.K >= 16)
+    st.kernel = KGEMM;
+  else if (outs <= 4096 && st.K >= 4096)
+    st.kernel = KSPLITK;
+  else
+    st.kernel = KROWS;
+  st.chunks = st.kernel == KSPLITK ? (int32_t)std::min<int64_t>(64, (st.K + 2047) / 2048) : 0;
+  return true;
+}
+
 // ------------------------------------------------------------------ plan assembly
 uint64_t Plan::ws_bytes(int32_t precision) const {
   if (precision == PK_C64) {
@@ -500,11 +714,35 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   double max_log2_slices = opts.max_log2_slices > 0 ? opts.max_log2_slices : 40.0;
   int32_t rmax = q == 1 ? 1 << 20 : (int32_t)std::floor(max_log2 / lq + 1e-9);
 
+  // clause weights: standard (-t^-eps, 1) or given per Tait edge
+  const bool grad = (opts.flags & PK_FLAG_GRAD) != 0;
+  p.general = grad || opts.edge_weights != nullptr;
+  p.std_weights = opts.edge_weights == nullptr;
+  p.weights.clear();
+  for (int32_t c = 0; c < (int32_t)k.edges.size(); ++c) {
+    if (opts.edge_weights) {
+      const double* w = opts.edge_weights + 4 * c;
+      for (int j = 0; j < 4; ++j)
+        if (!std::isfinite(w[j])) {
+          err = "edge weights must be finite";
+          return false;
+        }
+      p.weights.push_back({w[0], w[1], w[2], w[3]});
+    } else {
+      p.weights.push_back(std_weight(q, k.edges[c][2]));
+    }
+  }
+
   // candidate orders: (order, seed); min-fill restarts differ by their tie-break seed
   const int32_t restarts = opts.restarts > 0 ? opts.restarts : 8;
   std::vector<std::pair<int32_t, uint64_t>> cands;
+  if (p.general && opts.order == PK_ORDER_GREEDY_EDGE) {
+    err = "the edge network is not available for gradient or weighted plans";
+    return false;
+  }
   if (opts.order == PK_ORDER_AUTO) {
-    cands = {{PK_ORDER_GREEDY_SPIN, 0}, {PK_ORDER_ELIM_SPIN, 0}, {PK_ORDER_GREEDY_EDGE, 0}};
+    cands = {{PK_ORDER_GREEDY_SPIN, 0}, {PK_ORDER_ELIM_SPIN, 0}};
+    if (!p.general) cands.push_back({PK_ORDER_GREEDY_EDGE, 0});
     for (int32_t r = 0; r < restarts; ++r) cands.push_back({PK_ORDER_FILL_SPIN, (uint64_t)r});
   } else if (opts.order >= 1 && opts.order <= 3) {
     cands = {{opts.order, 0}};
@@ -526,7 +764,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
     if (o == PK_ORDER_GREEDY_EDGE)
       edge_network(k, q, net);
     else
-      spin_network(k, q, net);
+      spin_network(k, q, p.general, p.std_weights, p.weights, net);
     Greedy g;
     run_order(net, o, g, cand.second);
     // cost in complex MACs at this q
@@ -609,151 +847,14 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   for (int32_t s = 0; s < n_steps; ++s) {
     int32_t x = g.seq.pairs[s].first, y = g.seq.pairs[s].second;
     int32_t cid = p.n_init + s;
-    const auto& cset = sets[cid];
-    // roles: a = operand with more elements
-    int32_t a = x, b = y;
-    if (b >= 0 && p.tensors[b].dims.size() > p.tensors[a].dims.size()) std::swap(a, b);
-    static const std::vector<int32_t> no_dims;
-    const auto& ad = p.tensors[a].dims;
-    const auto& bd = b >= 0 ? p.tensors[b].dims : no_dims;
-    auto pos_in = [](const std::vector<int32_t>& d, int32_t v) -> int32_t {
-      for (size_t i = 0; i < d.size(); ++i)
-        if (d[i] == v) return (int32_t)i;
-      return -1;
-    };
-    auto in_c = [&](int32_t v) { return std::binary_search(cset.begin(), cset.end(), v); };
     Step st;
-    std::memset(&st, 0, sizeof(st));
-    st.a = a;
-    st.b = b;
-    st.c = cid;
-    const int32_t ra = (int32_t)ad.size(), rb = (int32_t)bd.size();
-    auto stride_a = [&](int32_t v) -> int64_t {
-      int32_t pp = pos_in(ad, v);
-      return pp < 0 ? 0 : qpow(ra - 1 - pp);
-    };
-    auto stride_b = [&](int32_t v) -> int64_t {
-      int32_t pp = pos_in(bd, v);
-      return pp < 0 ? 0 : qpow(rb - 1 - pp);
-    };
-    std::vector<Run> rows, ks, ns;
-    std::vector<int32_t> row_dims, n_dims;
-    auto push = [&](std::vector<Run>& v, int64_t sa, int64_t sb) {
-      if (!v.empty()) {
-        Run& l = v.back();
-        if (sa == l.sa * l.size && sb == l.sb * l.size) {
-          l.size *= q;
-          return;
-        }
-      }
-      v.push_back({(int64_t)q, sa, sb});
-    };
-    for (int32_t i = ra - 1; i >= 0; --i) {  // inner -> outer
-      int32_t v = ad[i];
-      if (in_c(v)) {
-        push(rows, stride_a(v), stride_b(v));
-        row_dims.push_back(v);
-      } else {
-        push(ks, stride_a(v), stride_b(v));
-      }
-    }
-    for (int32_t i = rb - 1; i >= 0; --i) {
-      int32_t v = bd[i];
-      if (pos_in(ad, v) >= 0) continue;
-      if (in_c(v)) {
-        push(ns, 0, stride_b(v));
-        n_dims.push_back(v);
-      } else {
-        push(ks, 0, stride_b(v));
-      }
-    }
-    if ((int)rows.size() > kMaxRuns || (int)ks.size() > kMaxRuns || (int)ns.size() > kMaxRuns) {
-      err = "step has too many stride runs";
+    bool sw = false;
+    if (!build_step(p.tensors[x].dims, y >= 0 ? &p.tensors[y].dims : nullptr, sets[cid], q,
+                    opts.flags, st, sw, p.tensors[cid].dims, err))
       return false;
-    }
-    st.R = st.K = st.N = 1;
-    st.nrow = (int32_t)rows.size();
-    st.nk = (int32_t)ks.size();
-    st.nn = (int32_t)ns.size();
-    for (int i = 0; i < st.nrow; ++i) {
-      st.row[i] = rows[i];
-      st.R *= rows[i].size;
-    }
-    for (int i = 0; i < st.nk; ++i) {
-      st.kr[i] = ks[i];
-      st.K *= ks[i].size;
-    }
-    for (int i = 0; i < st.nn; ++i) {
-      st.nr[i] = ns[i];
-      st.N *= ns[i].size;
-    }
-    // C layout (outermost first): N dims (B order), then row dims (A order)
-    std::vector<int32_t>& cd_ = p.tensors[cid].dims;
-    for (int32_t i = (int32_t)n_dims.size() - 1; i >= 0; --i) cd_.push_back(n_dims[i]);
-    for (int32_t i = (int32_t)row_dims.size() - 1; i >= 0; --i) cd_.push_back(row_dims[i]);
-    st.rank_c = (int32_t)cd_.size();
-    // GEMM view: batch / m / n runs with their C strides (C = [n-part, row-part])
-    {
-      std::vector<Run4> gbv, gmv, gnv;
-      auto push4 = [&](std::vector<Run4>& v, int64_t sa, int64_t sb, int64_t sc) {
-        if (!v.empty()) {
-          Run4& l = v.back();
-          if (sa == l.sa * l.size && sb == l.sb * l.size && sc == l.sc * l.size) {
-            l.size *= q;
-            return;
-          }
-        }
-        v.push_back({(int64_t)q, sa, sb, sc});
-      };
-      int64_t csr = 1;  // C stride of the next row dim (inner -> outer, A order)
-      for (int32_t i = ra - 1; i >= 0; --i) {
-        int32_t v = ad[i];
-        if (!in_c(v)) continue;
-        if (pos_in(bd, v) >= 0)
-          push4(gbv, stride_a(v), stride_b(v), csr);
-        else
-          push4(gmv, stride_a(v), 0, csr);
-        csr *= q;
-      }
-      int64_t csn = st.R;
-      for (int32_t i = rb - 1; i >= 0; --i) {
-        int32_t v = bd[i];
-        if (pos_in(ad, v) >= 0 || !in_c(v)) continue;
-        push4(gnv, 0, stride_b(v), csn);
-        csn *= q;
-      }
-      if ((int)gbv.size() > kMaxRuns || (int)gmv.size() > kMaxRuns || (int)gnv.size() > kMaxRuns) {
-        err = "step has too many stride runs";
-        return false;
-      }
-      st.ngb = (int32_t)gbv.size();
-      st.ngm = (int32_t)gmv.size();
-      st.ngn = (int32_t)gnv.size();
-      st.Bsz = st.M = 1;
-      for (int i = 0; i < st.ngb; ++i) {
-        st.gb[i] = gbv[i];
-        st.Bsz *= gbv[i].size;
-      }
-      for (int i = 0; i < st.ngm; ++i) {
-        st.gm[i] = gmv[i];
-        st.M *= gmv[i].size;
-      }
-      for (int i = 0; i < st.ngn; ++i) st.gn[i] = gnv[i];
-      st.a_kinner = (ra > 0 && !in_c(ad[ra - 1])) ? 1 : 0;
-      st.b_kinner = (rb > 0 && pos_in(ad, bd[rb - 1]) >= 0 && !in_c(bd[rb - 1])) ? 1 : 0;
-    }
-    const int64_t outs = st.R * st.N;
-    if (b >= 0 && (opts.flags & PK_FLAG_FORCE_GEMM))
-      st.kernel = KGEMM;
-    else if (opts.flags & PK_FLAG_FORCE_ROWS)
-      st.kernel = KROWS;
-    else if (b >= 0 && st.M >= 64 && st.N >= 32 && st.K >= 16)
-      st.kernel = KGEMM;
-    else if (outs <= 4096 && st.K >= 4096)
-      st.kernel = KSPLITK;
-    else
-      st.kernel = KROWS;
-    st.chunks = st.kernel == KSPLITK ? (int32_t)std::min<int64_t>(64, (st.K + 2047) / 2048) : 0;
+    st.a = sw ? y : x;
+    st.b = sw ? x : y;
+    st.c = cid;
     p.steps[s] = st;
   }
   p.final_tensor = n_tens - 1;
@@ -846,9 +947,30 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
       sl.absorbed = ss.absorbed;
       sl.dre = ss.dre;
       sl.dim = ss.dim;
+      sl.ore = ss.ore;
+      sl.oim = ss.oim;
       p.slots.push_back(sl);
     }
     p.recipes.push_back(r);
+  }
+
+  // ---- edge groups of general networks (for weights and the reverse pass)
+  p.groups.clear();
+  p.leaf_dims.clear();
+  for (int32_t i = 0; i < p.n_init; ++i) p.leaf_dims.push_back(net.t[i].dims);
+  if (p.general) {
+    for (int32_t i = 0; i < p.n_init; ++i) {
+      const NetTensor& nt = net.t[i];
+      if (nt.group < 0) continue;
+      const Merged& mg = net.groups[nt.group];
+      EdgeGroup eg;
+      eg.u = mg.u;
+      eg.v = mg.v;
+      eg.leaf = i;
+      eg.slot = p.recipes[i].slot0 + 1;  // the absorbed slot
+      eg.members = mg.members;
+      p.groups.push_back(eg);
+    }
   }
 
   // ---- split precision: the last `tail` steps in complex128
@@ -925,7 +1047,57 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
     std::memcpy(p.program.data() + p.off_slots, p.slots.data(), sizeof(Slot) * p.slots.size());
   if (!p.conv.empty())
     std::memcpy(p.program.data() + p.off_conv, p.conv.data(), sizeof(ConvRec) * p.conv.size());
+  if (grad && !make_grad_program(p, opts.checkpoint_stride, opts.flags, err)) return false;
   return true;
+}
+
+bool set_weights(Plan& p, const double* w) {
+  std::vector<std::array<double, 4>> nw;
+  for (int32_t c = 0; c < (int32_t)p.knot.edges.size(); ++c) {
+    if (!w) {
+      nw.push_back(std_weight(p.q, p.knot.edges[c][2]));
+      continue;
+    }
+    for (int j = 0; j < 4; ++j)
+      if (!std::isfinite(w[4 * c + j])) return false;
+    nw.push_back({w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]});
+  }
+  p.weights = nw;
+  p.std_weights = w == nullptr;
+  apply_weights(p);
+  return true;
+}
+
+void apply_weights(Plan& p) {
+  for (const EdgeGroup& g : p.groups) {
+    double dre = 1, dim = 0, ore = 1, oim = 0;
+    if (p.std_weights) {
+      int32_t ss = 0;
+      for (int32_t c : g.members) ss += p.knot.edges[c][2];
+      clause_diag(p.q, (int32_t)g.members.size(), ss, dre, dim);
+    } else {
+      for (int32_t c : g.members) {
+        const auto& w = p.weights[c];
+        const double a = dre * w[0] - dim * w[1], b = dre * w[1] + dim * w[0];
+        const double c2 = ore * w[2] - oim * w[3], d = ore * w[3] + oim * w[2];
+        dre = a;
+        dim = b;
+        ore = c2;
+        oim = d;
+      }
+    }
+    Slot& sl = p.slots[g.slot];
+    sl.dre = dre;
+    sl.dim = dim;
+    sl.ore = ore;
+    sl.oim = oim;
+  }
+  if (!p.slots.empty()) {
+    std::memcpy(p.program.data() + p.off_slots, p.slots.data(), sizeof(Slot) * p.slots.size());
+    if (p.grad.built)
+      std::memcpy(p.grad.program.data() + p.grad.off_slots, p.slots.data(),
+                  sizeof(Slot) * p.slots.size());
+  }
 }
 
 }  // namespace pk

@@ -19,7 +19,13 @@ class Recipe(C.Structure):
 
 class Slot(C.Structure):
     _fields_ = [("dimpos", C.c_int32), ("slice_ord", C.c_int32), ("absorbed", C.c_int32),
-                ("pad", C.c_int32), ("dre", C.c_double), ("dim", C.c_double)]
+                ("pad", C.c_int32), ("dre", C.c_double), ("dim", C.c_double),
+                ("ore", C.c_double), ("oim", C.c_double)]
+
+
+class GradLeaf(C.Structure):
+    _fields_ = [("meta", C.c_int32), ("rank", C.c_int32), ("slice_ord", C.c_int32 * 2),
+                ("offset", C.c_int64), ("stride", C.c_int64 * 2)]
 
 
 class Run(C.Structure):
@@ -124,26 +130,7 @@ def replay(plan, split=False):
         arena = np.full(arena_n, np.nan + 0j, dtype=np.complex128)
         mx = {}
         ex = {}
-        for r in recs:
-            e = np.arange(r.elems, dtype=np.int64)
-            if r.kind == 1:
-                val = np.ones(r.elems, dtype=np.complex128)
-            else:
-                val = np.zeros(r.elems, dtype=np.complex128)
-                for s in range(q):
-                    prod = np.ones(r.elems, dtype=np.complex128)
-                    for j in range(r.nslot):
-                        sl_ = slots[r.slot0 + j]
-                        x = (e // q ** sl_.dimpos) % q if sl_.dimpos >= 0 else \
-                            np.full(r.elems, sdig[sl_.slice_ord])
-                        if sl_.absorbed:
-                            prod = np.where(x == s, prod * complex(sl_.dre, sl_.dim), prod)
-                        else:
-                            prod = np.where(x == s, prod, 0)
-                    val += prod
-            arena[r.offset:r.offset + r.elems] = val
-            mx[r.meta] = float(np.max(np.maximum(np.abs(val.real), np.abs(val.imag))))
-            ex[r.meta] = 0
+        _build(recs, slots, q, sdig, arena, mx, ex)
         if split and n_tail > 0:
             # complex128 tail: widen the bulk tensors it reads, run its steps in the
             # tail region with the tail records' offsets and bookkeeping slots
@@ -198,3 +185,87 @@ def _step(st, arena, out, mx, ex):
     assert not np.isnan(flat).any()
     mx[st.c] = float(np.max(np.maximum(np.abs(flat.real), np.abs(flat.imag))))
     ex[st.c] = ex[st.a] + xb + ea + eb
+
+
+def _build(recs, slots, q, sdig, arena, mx, ex):
+    """Initial tensors from their recipes, as k_build forms them."""
+    for r in recs:
+        e = np.arange(r.elems, dtype=np.int64)
+        if r.kind == 1:
+            val = np.ones(r.elems, dtype=np.complex128)
+        else:
+            val = np.zeros(r.elems, dtype=np.complex128)
+            for s in range(q):
+                prod = np.ones(r.elems, dtype=np.complex128)
+                for j in range(r.nslot):
+                    sl_ = slots[r.slot0 + j]
+                    x = (e // q ** sl_.dimpos) % q if sl_.dimpos >= 0 else \
+                        np.full(r.elems, sdig[sl_.slice_ord])
+                    if sl_.absorbed:
+                        prod = np.where(x == s, prod * complex(sl_.dre, sl_.dim),
+                                        prod * complex(sl_.ore, sl_.oim))
+                    else:
+                        prod = np.where(x == s, prod, 0)
+                val += prod
+        arena[r.offset:r.offset + r.elems] = val
+        mx[r.meta] = float(np.max(np.maximum(np.abs(val.real), np.abs(val.imag))))
+        ex[r.meta] = 0
+
+
+def replay_grad(plan):
+    """The reverse-pass program of a grad plan on the CPU: returns (Z as (mantissa,
+    exponent), accumulators (groups, q*q) complex, their exponents), as pk_grad's
+    kernels leave them for the host's last stage."""
+    sc = np.frombuffer(plan.debug_blob(7), dtype=np.int64)
+    (n_steps, n_meta, arena_n, root_off, root_meta, off_rec, off_slots, off_leaves, n_leaves,
+     n_slices, leaf_sz, n_init, n_slots, q, n_sliced, slot_sz) = [int(v) for v in sc[:16]]
+    assert leaf_sz == C.sizeof(GradLeaf) and slot_sz == C.sizeof(Slot)
+    prog = plan.debug_blob(8)
+    recs = [Recipe.from_buffer_copy(prog, off_rec + i * C.sizeof(Recipe)) for i in range(n_init)]
+    slots = [Slot.from_buffer_copy(prog, off_slots + i * C.sizeof(Slot)) for i in range(n_slots)]
+    leaves = [GradLeaf.from_buffer_copy(prog, off_leaves + i * C.sizeof(GradLeaf))
+              for i in range(n_leaves)]
+    sb = plan.debug_blob(6)
+    steps = [Step.from_buffer_copy(sb, i * C.sizeof(Step)) for i in range(n_steps)]
+    acc = np.zeros((max(1, n_leaves), q * q), dtype=np.complex128)
+    acc_exp = np.zeros(max(1, n_leaves), dtype=np.int64)
+    total = []
+    for sl in range(n_slices):
+        sdig = []
+        s = sl
+        for _ in range(n_sliced):
+            sdig.append(s % q)
+            s //= q
+        arena = np.full(max(1, arena_n), np.nan + 0j, dtype=np.complex128)
+        mx, ex = {}, {}
+        _build(recs, slots, q, sdig, arena, mx, ex)
+        for st in steps:
+            _step(st, arena, arena, mx, ex)
+        total.append((complex(arena[root_off]), ex[root_meta]))
+        for g, L in enumerate(leaves):
+            n = q * q if L.rank == 2 else q
+            inc = np.zeros(n, dtype=np.complex128)
+            for e in range(n):
+                d = (e // q, e % q) if L.rank == 2 else (e, 0)
+                off, skip = 0, False
+                for j in range(L.rank):
+                    if L.slice_ord[j] >= 0:
+                        skip |= d[j] != sdig[L.slice_ord[j]]
+                    else:
+                        off += d[j] * L.stride[j]
+                if not skip:
+                    inc[e] = 1.0 if L.meta < 0 else arena[L.offset + off]
+            ev = 0 if L.meta < 0 else ex[L.meta]
+            mi = float(np.max(np.maximum(np.abs(inc.real), np.abs(inc.imag))))
+            ma = float(np.max(np.maximum(np.abs(acc[g, :n].real), np.abs(acc[g, :n].imag))))
+            if mi == 0:
+                continue
+            enew = ev + math.frexp(mi)[1]
+            if ma > 0:
+                enew = max(enew, int(acc_exp[g]) + math.frexp(ma)[1])
+            so = 2.0 ** (int(acc_exp[g]) - enew) if ma > 0 else 0.0
+            acc[g, :n] = acc[g, :n] * so + inc * 2.0 ** (ev - enew)
+            acc_exp[g] = enew
+    emax = max((e + math.frexp(abs(v))[1] for v, e in total if v != 0), default=0)
+    z = sum(v * 2.0 ** (e - emax) for v, e in total)
+    return (complex(z), emax), acc[:n_leaves], acc_exp[:n_leaves]
