@@ -30,6 +30,20 @@ def sc(s):
     return SC.of(s.mantissa, s.exp2)
 
 
+def _sliced_plan(ctx, k, q, **kw):
+    """A plan sliced into a few (3..243) slices: the widest tensor's limit is lowered
+    step by step from the unsliced width until slicing starts."""
+    full = pk.Plan(ctx, k, q, **kw).stats()["log2_max_elems"]
+    lim = full
+    while lim > 1.0:
+        lim -= 0.5
+        p = pk.Plan(ctx, k, q, max_log2_elems=lim, **kw)
+        if p.stats()["n_slices"] > 1:
+            assert p.stats()["n_slices"] <= 243
+            return p
+    raise AssertionError("no sliced plan")
+
+
 def _compare(knot, q, z, d, dv, prec, weights=None):
     info, edges = knot.info(), knot.edges()
     zo, do = og.dlogz(info["n_v"], edges, q, weights)
@@ -75,11 +89,8 @@ def test_grad_sliced_and_forced_kernels(ctx):
     for s in range(3):
         gk = kg.random_grid_knot(16, 400 + s, True, 25, 50)
         k = pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer)
-        full = pk.Plan(ctx, k, 3, grad=True).stats()["log2_max_elems"]
         for flags in (0, pk.FLAG_FORCE_GEMM, pk.FLAG_FORCE_ROWS):
-            p = pk.Plan(ctx, k, 3, grad=True, checkpoint_stride=2, flags=flags,
-                        max_log2_elems=max(1.0, full - 2.5))
-            assert p.stats()["n_slices"] > 1
+            p = _sliced_plan(ctx, k, 3, grad=True, checkpoint_stride=2, flags=flags)
             for prec in ("c128", "split"):
                 z, v, d, dv = pk.grad(p, prec)
                 _compare(k, 3, z, d, dv, prec)

@@ -27,6 +27,20 @@ def _host_grad(plan):
     return z, d, dv
 
 
+def _sliced_plan(ctx, k, q, **kw):
+    """A plan sliced into a few (3..243) slices: the widest tensor's limit is lowered
+    step by step from the unsliced width until slicing starts."""
+    full = pk.Plan(ctx, k, q, **kw).stats()["log2_max_elems"]
+    lim = full
+    while lim > 1.0:
+        lim -= 0.5
+        p = pk.Plan(ctx, k, q, max_log2_elems=lim, **kw)
+        if p.stats()["n_slices"] > 1:
+            assert p.stats()["n_slices"] <= 243
+            return p
+    raise AssertionError("no sliced plan")
+
+
 def _knots():
     out = [kg.braid_closure_pd([1, 1, 1], 2), kg.braid_closure_pd([1, -2, 1, -2], 3),
            kg.kink(kg.braid_closure_pd([1, 1, 1], 2), 0, 1),
@@ -78,10 +92,7 @@ def test_grad_sliced(ctx):
         gk = kg.random_grid_knot(14, 120 + s, True, 15, 35)
         k = pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer)
         for q in (2, 3):
-            full = pk.Plan(ctx, k, q, grad=True).stats()["log2_max_elems"]
-            p = pk.Plan(ctx, k, q, grad=True, checkpoint_stride=s % 3,
-                        max_log2_elems=max(1.0, full - 2))
-            assert p.stats()["n_slices"] > 1
+            p = _sliced_plan(ctx, k, q, grad=True, checkpoint_stride=s % 3)
             _check(p, k, q)
 
 
