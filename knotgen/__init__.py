@@ -418,6 +418,9 @@ def knot_suite(name: str):
     grad    : one knot with 300 crossings; L=53 (the grid side whose typical
               crossing count is about 300), seed 7, random over/under.
     large   : 8 knots with 600..1000 crossings at L=86, seeds 1..8, random over/under.
+    large_moved : a copy of each `large` knot after 16 random Reidemeister I/II moves,
+              a base-point shift and a crossing shuffle (SplitMix64(0x1A7E + i) for knot
+              i); PD codes only (no embedding), returned as GridKnot with outer None.
     """
     if name == "tiny":
         return [random_grid_knot(12, 0, True, 16, 16)]
@@ -435,4 +438,11 @@ def knot_suite(name: str):
         return [random_grid_knot(53, 7, True, 300, 300)]
     if name == "large":
         return [random_grid_knot(86, s, True, 600, 1000) for s in range(1, 9)]
+    if name == "large_moved":
+        out = []
+        for i, k in enumerate(knot_suite("large")):
+            pd = randomize(k.pd, SplitMix64(0x1A7E + i), 16)
+            out.append(GridKnot(k.L, k.seed, k.xs, k.ys, k.over_bits, pd, None, k.draws,
+                                {"moves": 16}))
+        return out
     raise KeyError(name)

@@ -530,6 +530,43 @@ bool run_order(const Network& net, int32_t order, Greedy& g, uint64_t seed = 0) 
   return true;
 }
 
+// Index slicing: remove indices until every tensor holds at most rmax of them.  Each
+// round removes the index held by the most over-size tensors (ties: the one whose
+// removal shrinks them most).  `sets` loses the removed indices.
+bool slice_indices(std::vector<std::vector<int32_t>>& sets, int32_t n_idx, int32_t q,
+                   int32_t rmax, size_t max_count, std::vector<int32_t>& out) {
+  out.clear();
+  for (;;) {
+    int32_t worst = 0;
+    for (const auto& s : sets) worst = std::max<int32_t>(worst, (int32_t)s.size());
+    if (worst <= rmax) return true;
+    std::vector<int64_t> hits(n_idx, 0);
+    std::vector<double> gain(n_idx, 0);
+    for (const auto& s : sets)
+      if ((int32_t)s.size() > rmax)
+        for (int32_t x : s) {
+          hits[x]++;
+          gain[x] += std::pow((double)q, (double)s.size() - rmax);
+        }
+    int32_t bx = -1;
+    for (int32_t x = 0; x < n_idx; ++x)
+      if (hits[x] > 0 && (bx < 0 || hits[x] > hits[bx] || (hits[x] == hits[bx] && gain[x] > gain[bx])))
+        bx = x;
+    if (bx < 0 || out.size() >= max_count) return false;
+    out.push_back(bx);
+    for (auto& s : sets) s.erase(std::remove(s.begin(), s.end(), bx), s.end());
+  }
+}
+
+// Complex multiply-adds of a contraction sequence over index sets `sets` (one slice).
+double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& sets, int32_t q) {
+  static const std::vector<int32_t> none;
+  double c = 0;
+  for (const auto& pr : seq.pairs)
+    c += std::pow((double)q, (double)union_size(sets[pr.first], pr.second >= 0 ? sets[pr.second] : none));
+  return c;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ step descriptors
@@ -713,6 +750,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   if (max_log2 > 31.0) max_log2 = 31.0;  // 32-bit row indexing in the kernels
   double max_log2_slices = opts.max_log2_slices > 0 ? opts.max_log2_slices : 40.0;
   int32_t rmax = q == 1 ? 1 << 20 : (int32_t)std::floor(max_log2 / lq + 1e-9);
+  const size_t max_slice_idx = q == 1 ? 0 : (size_t)std::floor(max_log2_slices / lq + 1e-9);
 
   // clause weights: standard (-t^-eps, 1) or given per Tait edge
   const bool grad = (opts.flags & PK_FLAG_GRAD) != 0;
@@ -767,20 +805,21 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
       spin_network(k, q, p.general, p.std_weights, p.weights, net);
     Greedy g;
     run_order(net, o, g, cand.second);
-    // cost in complex MACs at this q
-    double c = 0;
-    for (size_t s = 0; s < g.seq.pairs.size(); ++s) {
-      const auto& s2 = g.seq.pairs[s].second >= 0 ? g.seq.sets[g.seq.pairs[s].second]
-                                                   : std::vector<int32_t>();
-      size_t u = union_size(g.seq.sets[g.seq.pairs[s].first], s2);
-      c += std::pow((double)q, (double)u);
-    }
+    // cost in complex MACs at this q after slicing: slices x work per slice
+    std::vector<std::vector<int32_t>> ss = g.seq.sets;
+    std::vector<int32_t> sl;
+    if (!slice_indices(ss, net.n_idx, q, rmax, max_slice_idx, sl)) continue;
+    const double c = std::pow((double)q, (double)sl.size()) * sequence_cost(g.seq, ss, q);
     if (c < best_cost) {
       best_cost = c;
       best_net = net;
       best_g = g;
       best_order = o;
     }
+  }
+  if (best_order < 0) {
+    err = "plan needs more slices than allowed";
+    return false;
   }
   p.order_used = best_order;
   Network& net = best_net;
@@ -798,34 +837,11 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   // ---- slicing: remove indices until every tensor has rank <= rmax
   std::vector<std::vector<int32_t>> sets = g.seq.sets;
   std::vector<char> sliced(net.n_idx, 0);
-  for (;;) {
-    int32_t worst = 0;
-    for (const auto& s : sets) worst = std::max<int32_t>(worst, (int32_t)s.size());
-    if (worst <= rmax) break;
-    std::vector<int64_t> hits(net.n_idx, 0);
-    std::vector<double> gain(net.n_idx, 0);
-    for (const auto& s : sets)
-      if ((int32_t)s.size() > rmax)
-        for (int32_t x : s) {
-          hits[x]++;
-          gain[x] += std::pow((double)q, (double)s.size() - rmax);
-        }
-    int32_t bx = -1;
-    for (int32_t x = 0; x < net.n_idx; ++x)
-      if (hits[x] > 0 && (bx < 0 || hits[x] > hits[bx] || (hits[x] == hits[bx] && gain[x] > gain[bx])))
-        bx = x;
-    if (bx < 0) {
-      err = "internal: slicing found no index";
-      return false;
-    }
-    sliced[bx] = 1;
-    p.sliced.push_back(bx);
-    for (auto& s : sets) s.erase(std::remove(s.begin(), s.end(), bx), s.end());
-    if ((double)p.sliced.size() * lq > max_log2_slices) {
-      err = "plan needs more slices than allowed";
-      return false;
-    }
+  if (!slice_indices(sets, net.n_idx, q, rmax, max_slice_idx, p.sliced)) {
+    err = "plan needs more slices than allowed";
+    return false;
   }
+  for (int32_t x : p.sliced) sliced[x] = 1;
   p.n_slices = 1;
   for (size_t i = 0; i < p.sliced.size(); ++i) p.n_slices *= q;
   std::vector<int32_t> slice_ord(net.n_idx, -1);

@@ -281,3 +281,22 @@ def test_scaled_overflow_range():
     got = oracle.z_complex(g.n_v, g.edges, q)
     assert got.log2abs() > 1100
     assert rel_err(got, want) < 1e-10
+
+
+def _is_power_of_3(n):
+    if n < 1:
+        return False
+    while n % 3 == 0:
+        n //= 3
+    return n == 1
+
+
+def test_q3_modulus_is_power_of_three():
+    """At q = 3, t = e^(i pi/3) and V = +- i^c (i sqrt 3)^d for every knot (Lickorish and
+    Millett: d is the Z_3-rank of the homology of the double branched cover), so
+    |V|^2 = a^2 + a b + b^2 (V = a + b t exactly, t + conj(t) = 1) is a power of 3."""
+    for pd in _grid_knots(12, 18, 800) + [TREFOIL, FIG8]:
+        a, b = v_exact_as_ring(pd, 3)
+        assert _is_power_of_3(a * a + a * b + b * b), (a, b)
+    a, b = v_exact_as_ring(TREFOIL, 3)
+    assert a * a + a * b + b * b == 3     # i sqrt 3 (Fig. 1 caption)
