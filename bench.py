@@ -59,9 +59,34 @@ def parse():
     return ap.parse_args()
 
 
-def workload(rank):
+KNOTS_PER_RANK = 64
+
+
+def shard_seeds(rank, n=KNOTS_PER_RANK):
+    """Seeds of rank r's knots: 64r+1 .. 64r+64 (weak scaling: fixed work per GPU, no
+    knot shared between ranks)."""
+    return [KNOTS_PER_RANK * rank + s for s in range(1, n + 1)]
+
+
+def workload(rank, n=KNOTS_PER_RANK):
     import knotgen as kg
-    return [kg.random_grid_knot(40, 64 * rank + s, True, 100, 400) for s in range(1, 65)]
+    return [kg.random_grid_knot(40, s, True, 100, 400) for s in shard_seeds(rank, n)]
+
+
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the step time of the slowest rank); x itself when
+    running alone."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, step_ms):
+    """Whole-job throughput: the units all ranks processed per second of the slowest."""
+    return world * units_per_rank / (step_ms / 1000.0)
 
 
 def peaks():
@@ -358,13 +383,9 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     log(f"timed {args.steps} steps")
-    step_ms = sum(times) / len(times)
-    if dist:
-        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(sum(times) / len(times), dist, dev)
     evals = len(plans)
-    value = world * evals / (step_ms / 1000.0)
+    value = job_rate(world, evals, step_ms)
 
     # end to end through the public API: every program host->device (pinned), the
     # kernels, every scaled result device->host
@@ -376,8 +397,8 @@ def main():
         pk.upload(p, prec, w)
     group.launch()
     results(prec, ws)
-    e2e_s = time.perf_counter() - t1
-    e2e_val = world * evals / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t1, dist, dev)
+    e2e_val = job_rate(world, evals, 1000.0 * e2e_s)
     log("end-to-end pass")
     del group, ws
     torch.cuda.empty_cache()
@@ -400,7 +421,7 @@ def main():
             g2.launch()
             b.record(stream)
             b.synchronize()
-            ms = a.elapsed_time(b)
+            ms = max_over_ranks(a.elapsed_time(b), dist, dev)
             res_by[pr] = results(pr, ws2)
             compare[pr] = {"value": world * evals / (ms / 1000.0), "unit": "knots/s",
                            "ms_per_step": ms, "note": "one timed replay after a warm-up replay"}
