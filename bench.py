@@ -35,6 +35,7 @@ FP32_CORE_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3   # FMA = 2 flop
 FP32_ISSUE_TOPS = SM_COUNT * FP32_LANES * SM_MAX_GHZ / 1e3         # FP32 instructions
 FF_INSTR_PER_CMAC = 48   # float-float complex multiply-add: 4 x (two-product + TwoSum)
 FP64_TFLOPS = 1.25       # GB300 FP64 rate
+TC_PAIRS = 15            # BF16 digit pairs per real multiply-add on the tensor cores (5 digits)
 
 
 def log(msg):
@@ -440,7 +441,8 @@ def main():
                               "evaluations_over_1e-6": sum(e > 1e-6 for e in errs)})
 
     # roofline of the dominant kernel class, from the event-timed warm-up pass
-    knames = {"gemm": "k_gemm (tiled strided complex GEMM)",
+    knames = {"gemm": "k_gemm (tiled strided complex GEMM, CUDA cores)",
+              "gemm_tc": "k_gemm_tc (complex GEMM on tcgen05 tensor cores, BF16 digit split)",
               "rows": "k_rows (fused permute-and-contract, thread per output row)",
               "splitk": "k_splitk", "build": "k_build", "results": "k_slice_result/k_sum_slices"}
     dom = max(prof, key=lambda c: prof[c]["ms"])
@@ -449,7 +451,11 @@ def main():
     flops = 8.0 * rk["cmacs"]
     sec = rk["ms"] / 1e3
     ai = flops / max(rk["bytes"], 1.0)           # bytes at the precision's entry size
-    if prec == "split":
+    if dom == "gemm_tc":
+        peak = pk_["bf16_tflops"] / TC_PAIRS
+        src = (f"measured dense BF16 {pk_['bf16_tflops']} TFLOP/s (MEASURED_PEAKS.json) / "
+               f"{TC_PAIRS} BF16 digit-pair products per real multiply-add")
+    elif prec == "split":
         peak = FP32_ISSUE_TOPS / FF_INSTR_PER_CMAC * 8
         src = ("derived: 152 SM x 128 FP32 lanes x 2.07 GHz FP32 instructions / 48 instructions "
                "per float-float complex multiply-add x 8 flops")
@@ -460,7 +466,8 @@ def main():
     ridge = peak * 1e12 / (pk_["hbm_gbs"] * 1e9)
     if ai > ridge:
         ach = flops / sec / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+        roof = {"bound": "tensor" if dom == "gemm_tc" else "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "peak_source": src}
     else:
         ach = rk["bytes"] / sec / 1e9

@@ -78,6 +78,8 @@ typedef enum {
  * the planner choose per step by its shape). */
 #define PK_FLAG_FORCE_GEMM 1 /* every two-operand step on the tiled GEMM kernel           */
 #define PK_FLAG_FORCE_ROWS 2 /* every step on the row kernel                               */
+#define PK_FLAG_NO_TC 8      /* PK_SPLIT: run GEMM-shaped steps on the CUDA cores (float-float
+                                SIMT kernel) instead of the tensor cores                     */
 #define PK_FLAG_GRAD 4       /* also build the reverse (adjoint) program used by pk_grad.
                                 The network then keeps every edge group as a tensor (a pair
                                 of opposite-sign parallel edges is not dropped, loops become
@@ -230,9 +232,10 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
 /* Runs the kernels of pk_launch once (same stream, same workspace, recipe already
  * uploaded; d_arena NULL = the arena inside the workspace, else as pk_launch_arena)
  * with a CUDA event pair around every launch, waits, and returns per kernel
- * class c (0 build, 1 rows, 2 split-K, 3 results, 4 GEMM): out[c] = milliseconds,
- * out[5+c] = launches, out[10+c] = algorithmic complex multiply-adds, out[15+c] =
- * algorithmic bytes (|A| + |B| + |C| at the precision's element size).  20 doubles. */
+ * class c (0 build, 1 rows, 2 split-K, 3 results, 4 GEMM on CUDA cores, 5 GEMM on the
+ * tensor cores): out[c] = milliseconds, out[6+c] = launches, out[12+c] = algorithmic
+ * complex multiply-adds, out[18+c] = algorithmic bytes (|A| + |B| + |C| at the
+ * precision's element size).  24 doubles. */
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                      uint64_t workspace_bytes, void* d_arena, uint64_t arena_bytes, double* out);
 

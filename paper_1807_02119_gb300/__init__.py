@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpk.so")
 
 PK_C128, PK_C64, PK_SPLIT = 0, 1, 2
-FLAG_FORCE_GEMM, FLAG_FORCE_ROWS, FLAG_GRAD = 1, 2, 4
+FLAG_FORCE_GEMM, FLAG_FORCE_ROWS, FLAG_GRAD, FLAG_NO_TC = 1, 2, 4, 8
 PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split": PK_SPLIT}
 ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4,
           "fill_spin": 5}
@@ -417,16 +417,16 @@ def download(plan: Plan, precision: str, ws):
 
 
 def profile(plan: Plan, precision: str, ws, arena=None):
-    """Per kernel class (build, rows, splitk, results, gemm): ms, launches, complex MACs,
+    """Per kernel class (build, rows, splitk, results, gemm, gemm_tc): ms, launches, complex MACs,
     bytes of one pass of the plan's kernels, timed with CUDA events on the context's
     stream.  `arena` (optional) is a separate tensor arena as for launch_arena()."""
-    out = (C.c_double * 20)()
+    out = (C.c_double * 24)()
     ap = C.c_void_p(arena.data_ptr()) if arena is not None else None
     an = arena.numel() if arena is not None else 0
     _check(lib().pk_profile(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
                             ws.numel(), ap, an, out), plan.ctx)
-    names = ("build", "rows", "splitk", "results", "gemm")
-    return {n: {"ms": out[i], "launches": out[5 + i], "cmacs": out[10 + i], "bytes": out[15 + i]}
+    names = ("build", "rows", "splitk", "results", "gemm", "gemm_tc")
+    return {n: {"ms": out[i], "launches": out[6 + i], "cmacs": out[12 + i], "bytes": out[18 + i]}
             for i, n in enumerate(names)}
 
 

@@ -408,6 +408,48 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
   block_max_to_meta(vmax, meta + s.c);
 }
 
+// Thread per output C[n, r] for steps with too few rows to fill the GPU one thread per
+// row: each thread forms one output's K-term sum, reading the contracted index's offsets
+// from shared memory; consecutive threads write consecutive C entries (C index
+// n * R + r is the thread's linear index).
+template <typename R>
+__global__ void __launch_bounds__(256) k_outs(const Step s, Cx<R>* arena, Meta* meta) {
+  using S = typename Traits<R>::S;
+  extern __shared__ long long sm[];
+  long long* kA = sm;
+  long long* kB = sm + s.K;
+  for (long long k = threadIdx.x; k < s.K; k += blockDim.x) split_runs(k, s.kr, s.nk, kA[k], kB[k]);
+  const S scale = step_scale<S>(s, meta, blockIdx.x == 0 && threadIdx.x == 0);
+  __syncthreads();
+  const Cx<R>* A = arena + s.off_a;
+  const Cx<R>* B = arena + s.off_b;
+  Cx<R>* C = arena + s.off_c;
+  const bool hasB = s.b >= 0;
+  const int K = (int)s.K;
+  const unsigned long long R_ = (unsigned long long)s.R;
+  const unsigned long long total = R_ * (unsigned long long)s.N;
+  S vmax = 0;
+  for (unsigned long long o = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; o < total;
+       o += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long n = o / R_, r = o - n * R_;
+    long long oa, ob, nb, dummy;
+    split_runs(r, s.row, s.nrow, oa, ob);
+    split_runs(n, s.nr, s.nn, dummy, nb);
+    const Cx<R>* Ar = A + oa;
+    const Cx<R>* Bn = B + ob + nb;
+    Acc<R> acc;
+    if (hasB) {
+      for (int k = 0; k < K; ++k) acc.mac(ld(Ar + kA[k]), ld(Bn + kB[k]));
+    } else {
+      for (int k = 0; k < K; ++k) acc.add(ld(Ar + kA[k]));
+    }
+    const Cx<R> v = acc.get(scale);
+    st(C + o, v);
+    vmax = fmax(vmax, mag(v));
+  }
+  block_max_to_meta(vmax, meta + s.c);
+}
+
 // Same contraction without offset tables (K too long for shared memory): every k
 // offset is recomputed from the stride runs.
 template <typename R>

@@ -9,9 +9,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
+#include "gemm_tc.cuh"
 
 namespace pk {
 
@@ -35,7 +37,8 @@ __global__ void __launch_bounds__(256) k_widen(const ConvRec* __restrict__ conv,
   }
 }
 
-constexpr int kNumClasses = 5;  // build, rows, split-K, results, GEMM
+constexpr int kNumClasses = 6;  // build, rows, split-K, results, GEMM, tensor-core GEMM
+constexpr int kTcDigits = 5;    // BF16 digits per float-float operand on the tensor cores
 
 // Optional per-launch timing: an event pair around every launch, summed per class.
 struct Prof {
@@ -64,9 +67,19 @@ struct Marker {
   }
 };
 
+// Rows below which one thread per row leaves the GPU short of threads (152 SMs x 2048
+// resident threads); such steps with several outputs per row run thread per output.
+constexpr long long kFewRows = 152LL * 2048;
+
 template <typename R>
 cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st) {
   const size_t sm = sizeof(long long) * (size_t)(2 * s.K + s.N);
+  if (s.R < kFewRows && s.N > 1 && sizeof(long long) * 2 * (size_t)s.K <= 200 * 1024) {
+    const long long outs = s.R * s.N;
+    const long long blocks = std::max<long long>(1, std::min<long long>((outs + 255) / 256, 152 * 16));
+    k_outs<R><<<(unsigned)blocks, 256, sizeof(long long) * 2 * (size_t)s.K, st>>>(s, arena, meta);
+    return cudaGetLastError();
+  }
   long long blocks = (s.R + 255) / 256;
   blocks = std::max<long long>(1, std::min<long long>(blocks, 152 * 8));
   if (sm > 200 * 1024) {
@@ -103,6 +116,15 @@ cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* par
   const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
   cudaError_t e;
   if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
+    if constexpr (std::is_same<R, ff>::value) {
+      if (s.tc) {
+        mk.begin(5, cm, by);
+        k_gemm_tc<kTcDigits><<<(unsigned)gemm_tiles, tc::kThreads, tc::Cfg<kTcDigits>::kSmem, stream>>>(
+            s, arena, meta);
+        mk.end();
+        return cudaGetLastError();
+      }
+    }
     mk.begin(4, cm, by);
     k_gemm<R><<<(unsigned)gemm_tiles, 256, 0, stream>>>(s, arena, meta);
     mk.end();
@@ -291,7 +313,7 @@ cudaError_t raise_rows_smem() {
   const int lim = 200 * 1024;
   void (*fns[])(const Step, Cx<R>*, Meta*) = {k_rows<R, 1>,  k_rows<R, 2>,  k_rows<R, 4>,
                                               k_rows<R, 8>,  k_rows<R, 16>, k_rows<R, 32>,
-                                              k_rows<R, 0>};
+                                              k_rows<R, 0>,  k_outs<R>};
   for (auto f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
@@ -309,6 +331,9 @@ cudaError_t prepare_kernels() {
   if ((e = raise_rows_smem<double>()) != cudaSuccess) return e;
   if ((e = raise_rows_smem<float>()) != cudaSuccess) return e;
   if ((e = raise_rows_smem<ff>()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_gemm_tc<kTcDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::Cfg<kTcDigits>::kSmem)) != cudaSuccess)
+    return e;
   if (dev >= 0 && dev < 256) done[dev] = true;
   return cudaSuccess;
 }

@@ -95,7 +95,7 @@ struct Step {
   int32_t ngb, ngm, ngn;
   int32_t a_kinner;        // A's unit-stride index is a contracted one
   int32_t b_kinner;        // B's unit-stride index is a contracted one
-  int32_t pad2;
+  int32_t tc;              // GEMM step may run on the tensor cores (split precision)
   Run4 gb[kMaxRuns];
   Run4 gm[kMaxRuns];
   Run4 gn[kMaxRuns];

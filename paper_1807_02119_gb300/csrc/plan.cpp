@@ -718,11 +718,12 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
     st.kernel = KROWS;
   else if (hasb && st.M >= 64 && st.N >= 32 && st.K >= 16)
     st.kernel = KGEMM;
-  else if (outs <= 4096 && st.K >= 4096)
+  else if ((outs <= 4096 && st.K >= 4096) || (outs <= 1024 && st.K >= 256))
     st.kernel = KSPLITK;
   else
     st.kernel = KROWS;
   st.chunks = st.kernel == KSPLITK ? (int32_t)std::min<int64_t>(64, (st.K + 2047) / 2048) : 0;
+  st.tc = (st.kernel == KGEMM && !(flags & PK_FLAG_NO_TC)) ? 1 : 0;
   return true;
 }
 

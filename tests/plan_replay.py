@@ -56,7 +56,7 @@ class Step(C.Structure):
                 ("rank_c", C.c_int32), ("chunks", C.c_int32),
                 ("Bsz", C.c_int64), ("M", C.c_int64), ("ngb", C.c_int32), ("ngm", C.c_int32),
                 ("ngn", C.c_int32), ("a_kinner", C.c_int32), ("b_kinner", C.c_int32),
-                ("pad2", C.c_int32), ("gb", Run4 * MAXRUNS), ("gm", Run4 * MAXRUNS),
+                ("tc", C.c_int32), ("gb", Run4 * MAXRUNS), ("gm", Run4 * MAXRUNS),
                 ("gn", Run4 * MAXRUNS)]
 
 
