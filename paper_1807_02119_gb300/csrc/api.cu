@@ -361,8 +361,9 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
 pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launches) {
   if (!p || !launches || !valid_precision(precision)) return PK_EINVAL;
   const pk::Plan& P = p->p;
-  const int64_t widen = (precision == PK_SPLIT && !P.conv.empty()) ? 1 : 0;
-  *launches = P.n_slices * ((P.n_init > 0 ? 1 : 0) + (int64_t)P.steps.size() + 1 + widen) + 1;
+  const int64_t widen = (precision == PK_C64 && !P.conv.empty()) ? 1 : 0;
+  const int64_t digits = precision == PK_SPLIT ? 2 * (int64_t)P.n_tc : 0;  // per tensor-core step
+  *launches = P.n_slices * ((P.n_init > 0 ? 1 : 0) + (int64_t)P.steps.size() + 1 + widen + digits) + 1;
   return PK_OK;
 }
 

@@ -20,12 +20,21 @@
 // so a CTA tile of 64 complex rows x 64 complex columns is one M=128, N=64 MMA per
 // BF16 K-step of 16 (K' = 2 K).
 //
-// Data movement: the operands are gathered through the step's stride runs (arbitrary
-// index permutations, which a TMA tensor map cannot express), converted to digits by all
-// threads and written to shared memory in the canonical K-major layout without swizzle
-// (8-row x 16-byte core matrices); one thread issues the MMAs and commits them to an
-// mbarrier; every wait is bounded (on expiry the tile is poisoned with NaN and counted
-// in pk_tc_timeouts, so a failure shows up as a wrong result, not a hang).
+// Data movement, three kernels per step:
+//  * k_digits<S, true> / k_digits<S, false>: one CTA per 64-row block of A (64-column
+//    block of B) finds the block's exponents over all of K, then converts it chunk by
+//    chunk (16 complex k) into S digit slices laid out exactly as the MMA reads them from
+//    shared memory (the canonical K-major layout without swizzle: 8-row x 16-byte core
+//    matrices) and stores each chunk contiguously in the workspace.  The operands are
+//    gathered through the step's stride runs (arbitrary index permutations, which a TMA
+//    tensor map cannot express); each element is read and converted once.
+//  * k_gemm_tc: warp 0 streams the chunks of its (batch, row block, column block) into a
+//    3-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion by
+//    mbarrier transaction count); warp 1 issues the S (S+1)/2 digit-pair MMAs per K step
+//    and releases each stage with tcgen05.commit; eight epilogue warps flush the S level
+//    accumulators from TMEM into float-float registers every kFlush chunks and finally
+//    store C.  Every wait is bounded: on expiry the tile is poisoned with NaN and counted
+//    in pk_tc_timeouts, so a failure shows up as a wrong result, not a hang.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -33,23 +42,33 @@
 namespace pk {
 namespace tc {
 
-constexpr int kMc = 64;          // complex rows per tile
-constexpr int kNc = 64;          // complex columns per tile
-constexpr int kKc = 32;          // complex k per chunk
+constexpr int kMc = kTcMc;       // complex rows per tile
+constexpr int kNc = kTcNc;       // complex columns per tile
+constexpr int kKc = kTcKc;       // complex k per chunk
 constexpr int kM = 2 * kMc;      // MMA M (re and im rows interleaved)
 constexpr int kN = kNc;          // MMA N
 constexpr int kKr = 2 * kKc;     // MMA K per chunk (real: re half, im half)
-constexpr int kThreads = 256;
-constexpr int kABytes = kM * kKr * 2;   // one digit slice of the A tile (BF16)
-constexpr int kBBytes = kN * kKr * 2;   // one digit slice of the B tile
+constexpr int kKcores = kKr / 8; // 16-byte K core columns per row
+constexpr int kABytes = kM * kKr * 2;   // one digit slice of an A chunk (BF16): 8 KB
+constexpr int kBBytes = kN * kKr * 2;   // one digit slice of a B chunk: 4 KB
+constexpr int kStages = 3;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);   // producer, MMA issuer, epilogue
+constexpr int kConvThreads = 256;
 
 template <int S>
 struct Cfg {
-  static constexpr int kSmem = S * (kABytes + kBBytes) + 1024;  // + alignment slack
+  static constexpr int kAChunk = S * kABytes;     // one chunk of A digits (all slices)
+  static constexpr int kBChunk = S * kBBytes;
+  static constexpr int kStage = kAChunk + kBChunk;
+  static constexpr int kSmem = kStages * kStage + 1024;           // + alignment slack
+  static constexpr int kConvSmem = kAChunk + 1024;                // conversion staging
+  static_assert(S != kTcDigits || (kAChunk == kTcAChunk && kBChunk == kTcBChunk),
+                "chunk sizes must match the host's scratch layout");
   static constexpr int kCols = S * kN <= 32 ? 32 : S * kN <= 64 ? 64 : S * kN <= 128 ? 128
                                : S * kN <= 256 ? 256 : 512;
   // chunks per flush: S pairs per level x (chunks x kKr) terms x 2^14 < 2^24
-  static constexpr int kFlush = (1 << 10) / (S * kKr) > 0 ? ((1 << 10) - 1) / (S * kKr) : 1;
+  static constexpr int kFlush = ((1 << 10) - 1) / (S * kKr) > 0 ? ((1 << 10) - 1) / (S * kKr) : 1;
 };
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
@@ -156,57 +175,208 @@ __device__ __forceinline__ void digits(float h, float l, int e, __nv_bfloat16* d
 
 }  // namespace tc
 
-// One CTA per (batch, 64-row, 64-column) tile of the step's GEMM view.
-template <int S>
-__global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff>* arena, Meta* meta) {
+
+namespace tc {
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+// Contiguous global -> shared copy by the bulk-copy (TMA) engine; completes on `mbar` as
+// transaction bytes.  Addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+// Gather + digit conversion of one chunk of an operand block: 64 tile rows (complex rows
+// of A, or complex columns of B) x 16 complex k.  For A every complex entry fills rows
+// 2r (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).
+template <int S, bool IS_A>
+__device__ __forceinline__ void convert_chunk(const Step& s, const Cx<ff>* base, const long long* ro,
+                                              const int* ex, const long long* kx,
+                                              unsigned char* stage) {
+  constexpr int kSlice = IS_A ? kABytes : kBBytes;
+  const bool kin = IS_A ? s.a_kinner : s.b_kinner;
+  for (int idx = threadIdx.x; idx < 64 * kKc; idx += blockDim.x) {
+    int r, k;
+    if (kin) {
+      r = idx / kKc;
+      k = idx % kKc;
+    } else {
+      r = idx % 64;
+      k = idx / 64;
+    }
+    Cx<ff> v{{0.f, 0.f}, {0.f, 0.f}};
+    if (ro[r] >= 0 && kx[k] >= 0) v = ld(base + ro[r] + kx[k]);
+    __nv_bfloat16 dr[S], di[S];
+    digits<S>(v.re.hi, v.re.lo, ex[r], dr);
+    digits<S>(v.im.hi, v.im.lo, ex[r], di);
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      unsigned char* sl = stage + i * kSlice;
+      if (IS_A) {
+        *(__nv_bfloat16*)(sl + tile_off(2 * r, k, kKcores)) = dr[i];
+        *(__nv_bfloat16*)(sl + tile_off(2 * r, kKc + k, kKcores)) = __hneg(di[i]);
+        *(__nv_bfloat16*)(sl + tile_off(2 * r + 1, k, kKcores)) = di[i];
+        *(__nv_bfloat16*)(sl + tile_off(2 * r + 1, kKc + k, kKcores)) = dr[i];
+      } else {
+        *(__nv_bfloat16*)(sl + tile_off(r, k, kKcores)) = dr[i];
+        *(__nv_bfloat16*)(sl + tile_off(r, kKc + k, kKcores)) = di[i];
+      }
+    }
+  }
+}
+
+}  // namespace tc
+
+// Digits of the A operand (IS_A) or the B operand of a GEMM step: one CTA per (batch,
+// 64-row block); exponents over all K, then S digit slices per chunk of 16 complex k,
+// staged in shared memory and stored with 16-byte writes.
+template <int S, bool IS_A>
+__global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const Cx<ff>* arena,
+                                                             unsigned char* scratch) {
   using namespace tc;
+  static_assert(S == kTcDigits, "digit scratch laid out for kTcDigits digits");
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ long long am[kMc], cm[kMc], bn[kNc], cn[kNc], ak[kKc], bk[kKc];
-  __shared__ long long base[3];
+  __shared__ long long ro[64], kx[kKc];
+  __shared__ long long base;
+  __shared__ int ex[64];
+  __shared__ float red[kConvThreads];
+  unsigned char* stage = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
+  const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K);
+  const long long tiles = IS_A ? L.tiles_m : L.tiles_n;
+  const long long tile = blockIdx.x % tiles, bb = blockIdx.x / tiles;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    long long a, b, c;
+    runs4(bb, s.gb, s.ngb, a, b, c);
+    base = IS_A ? a : b;
+  }
+  if (tid < 64) {
+    const long long r = tile * 64 + tid;
+    long long a, b, c;
+    if (r < (IS_A ? s.M : s.N)) {
+      if (IS_A)
+        runs4(r, s.gm, s.ngm, a, b, c);
+      else
+        runs4(r, s.gn, s.ngn, a, b, c);
+      ro[tid] = IS_A ? a : b;
+    } else {
+      ro[tid] = -1;
+    }
+  }
+  __syncthreads();
+  const Cx<ff>* src = arena + (IS_A ? s.off_a : s.off_b) + base;
+  // exponents: 4 threads per row, all K
+  float mx = 0;
+  const int r = tid >> 2, sub = tid & 3;
+  for (long long c = 0; c < L.chunks; ++c) {
+    if (tid < kKc) {
+      const long long k = c * kKc + tid;
+      long long ka = -1, kb = -1;
+      if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
+      kx[tid] = IS_A ? ka : kb;
+    }
+    __syncthreads();
+    for (int k = sub; k < kKc; k += 4)
+      if (ro[r] >= 0 && kx[k] >= 0) mx = fmaxf(mx, mag(ld(src + ro[r] + kx[k])));
+    __syncthreads();
+  }
+  red[tid] = mx;
+  __syncthreads();
+  int* ex_out = (int*)(scratch + (IS_A ? L.ea_off : L.eb_off)) + (bb * tiles + tile) * 64;
+  if (sub == 0) {
+    const float v = fmaxf(fmaxf(red[tid], red[tid + 1]), fmaxf(red[tid + 2], red[tid + 3]));
+    ex[r] = bin_exp(v);
+    ex_out[r] = ex[r];
+  }
+  __syncthreads();
+  constexpr int kChunkBytes = IS_A ? Cfg<S>::kAChunk : Cfg<S>::kBChunk;
+  unsigned char* dst0 = scratch + (IS_A ? L.a_off : L.b_off) +
+                        (bb * tiles + tile) * L.chunks * (long long)kChunkBytes;
+  for (long long c = 0; c < L.chunks; ++c) {
+    if (tid < kKc) {
+      const long long k = c * kKc + tid;
+      long long ka = -1, kb = -1;
+      if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
+      kx[tid] = IS_A ? ka : kb;
+    }
+    __syncthreads();
+    convert_chunk<S, IS_A>(s, src, ro, ex, kx, stage);
+    __syncthreads();
+    uint4* d = (uint4*)(dst0 + c * (long long)kChunkBytes);
+    const uint4* sv = (const uint4*)stage;
+    for (int i = tid; i < kChunkBytes / 16; i += kConvThreads) d[i] = sv[i];
+    __syncthreads();
+  }
+}
+
+// C tile (64 complex rows x 64 complex columns of one batch index) from the digit chunks:
+// warp 0 streams chunks into the stage ring, warp 1 issues the MMAs, warps 2..9 flush
+// the level accumulators and store C.
+template <int S>
+__global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff>* arena, Meta* meta,
+                                                             const unsigned char* scratch) {
+  using namespace tc;
+  static_assert(S == kTcDigits, "digit scratch laid out for kTcDigits digits");
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ long long cm[kMc], cn[kNc];
+  __shared__ long long cbase;
   __shared__ int ea[kMc], eb[kNc];
-  __shared__ float red[kThreads];
-  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full, acc_empty;
   __shared__ uint32_t tmem_slot;
   __shared__ int bad;
-
   unsigned char* sm = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
-  unsigned char* As = sm;                     // S slices of kM x kKr
-  unsigned char* Bs = sm + S * kABytes;       // S slices of kN x kKr
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const long long tiles_m = (s.M + kMc - 1) / kMc, tiles_n = (s.N + kNc - 1) / kNc;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K);
   long long t = blockIdx.x;
-  const long long tm = t % tiles_m;
-  t /= tiles_m;
-  const long long tn = t % tiles_n;
-  const long long bb = t / tiles_n;
+  const long long tm = t % L.tiles_m;
+  t /= L.tiles_m;
+  const long long tn = t % L.tiles_n;
+  const long long bb = t / L.tiles_n;
 
   if (tid == 0) {
-    runs4(bb, s.gb, s.ngb, base[0], base[1], base[2]);
+    long long a, b;
+    runs4(bb, s.gb, s.ngb, a, b, cbase);
     bad = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 1);
+    }
+    mbar_init(smem_u32(&acc_full), 1);
+    mbar_init(smem_u32(&acc_empty), kEpiWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (tid < kMc) {
-    const long long m = tm * kMc + tid;
-    long long d;
-    if (m < s.M) {
-      runs4(m, s.gm, s.ngm, am[tid], d, cm[tid]);
-    } else {
-      am[tid] = -1;
-      cm[tid] = -1;
-    }
-  } else if (tid < kMc + kNc) {
-    const int j = tid - kMc;
+  if (tid >= 64 && tid < 64 + kMc) {
+    const int i = tid - 64;
+    const long long m = tm * kMc + i;
+    long long a, b;
+    if (m < s.M)
+      runs4(m, s.gm, s.ngm, a, b, cm[i]);
+    else
+      cm[i] = -1;
+    ea[i] = ((const int*)(scratch + L.ea_off))[(bb * L.tiles_m + tm) * kMc + i];
+  } else if (tid >= 64 + kMc && tid < 64 + kMc + kNc) {
+    const int j = tid - 64 - kMc;
     const long long n = tn * kNc + j;
-    long long d;
-    if (n < s.N) {
-      runs4(n, s.gn, s.ngn, d, bn[j], cn[j]);
-    } else {
-      bn[j] = -1;
+    long long a, b;
+    if (n < s.N)
+      runs4(n, s.gn, s.ngn, a, b, cn[j]);
+    else
       cn[j] = -1;
-    }
+    eb[j] = ((const int*)(scratch + L.eb_off))[(bb * L.tiles_n + tn) * kNc + j];
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
                  "r"(Cfg<S>::kCols)
@@ -218,190 +388,117 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
-  const Cx<ff>* A = arena + s.off_a + base[0];
-  const Cx<ff>* B = arena + s.off_b + base[1];
-  const long long nchunks = (s.K + kKc - 1) / kKc;
+  const long long nchunks = L.chunks;
+  const long long ngroups = (nchunks + Cfg<S>::kFlush - 1) / Cfg<S>::kFlush;
+  const uint32_t sm0 = smem_u32(sm);
 
-  // ---- exponents: largest entry of every tile row of A and column of B over all K
-  {
-    float mx = 0;
-    const int r = tid >> 2, sub = tid & 3;  // 4 threads per row (tid < 256: rows 0..63)
-    for (long long c = 0; c < nchunks; ++c) {
-      if (tid < kKc) {
-        const long long k = c * kKc + tid;
-        long long ka = -1, kb = -1;
-        if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
-        ak[tid] = ka;
-        bk[tid] = kb;
-      }
-      __syncthreads();
-      for (int k = sub; k < kKc; k += 4) {
-        if (ak[k] >= 0 && am[r] >= 0) mx = fmaxf(mx, mag(ld(A + am[r] + ak[k])));
-      }
-      __syncthreads();
-    }
-    red[tid] = mx;
-    __syncthreads();
-    if (sub == 0) {
-      const float v = fmaxf(fmaxf(red[tid], red[tid + 1]), fmaxf(red[tid + 2], red[tid + 3]));
-      ea[r] = bin_exp(v);
-    }
-    __syncthreads();
-    mx = 0;
-    for (long long c = 0; c < nchunks; ++c) {
-      if (tid < kKc) {
-        const long long k = c * kKc + tid;
-        long long ka = -1, kb = -1;
-        if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
-        ak[tid] = ka;
-        bk[tid] = kb;
-      }
-      __syncthreads();
-      for (int k = sub; k < kKc; k += 4) {
-        if (bk[k] >= 0 && bn[r] >= 0) mx = fmaxf(mx, mag(ld(B + bk[k] + bn[r])));
-      }
-      __syncthreads();
-    }
-    red[tid] = mx;
-    __syncthreads();
-    if (sub == 0) {
-      const float v = fmaxf(fmaxf(red[tid], red[tid + 1]), fmaxf(red[tid + 2], red[tid + 3]));
-      eb[r] = bin_exp(v);
-    }
-    __syncthreads();
-  }
-
-  // ---- main loop: digits to shared memory, S(S+1)/2 digit-pair MMAs per K step
-  const int lane_row = tid & 127;             // TMEM lane = row of the interleaved C
-  const int col_half = tid >> 7;              // columns 32 * col_half .. + 31
   float acc_h[32], acc_l[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) acc_h[j] = acc_l[j] = 0.f;
-  uint32_t phase = 0;
-  bool first = true;
-  const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-  for (long long c = 0; c < nchunks; ++c) {
-    if (tid < kKc) {
-      const long long k = c * kKc + tid;
-      long long ka = -1, kb = -1;
-      if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
-      ak[tid] = ka;
-      bk[tid] = kb;
-    }
-    __syncthreads();
-    // A: 64 rows x 32 k complex; (m, k) -> rows 2m (re), 2m+1 (im), columns k and 32+k
-    for (int idx = tid; idx < kMc * kKc; idx += kThreads) {
-      int m, k;
-      if (s.a_kinner) {
-        m = idx / kKc;
-        k = idx % kKc;
-      } else {
-        m = idx % kMc;
-        k = idx / kMc;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      const unsigned char* asrc =
+          scratch + L.a_off + (bb * L.tiles_m + tm) * nchunks * (long long)Cfg<S>::kAChunk;
+      const unsigned char* bsrc =
+          scratch + L.b_off + (bb * L.tiles_n + tn) * nchunks * (long long)Cfg<S>::kBChunk;
+      for (long long c = 0; c < nchunks; ++c) {
+        const int st = (int)(c % kStages);
+        if (c >= kStages && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c / kStages) - 1) & 1))) {
+          bad = 1;
+          atomicAdd(&pk_tc_timeouts, 1);
+          break;
+        }
+        const uint32_t dst = sm0 + st * Cfg<S>::kStage;
+        mbar_expect_tx(smem_u32(&full[st]), Cfg<S>::kStage);
+        bulk_g2s(dst, asrc + c * Cfg<S>::kAChunk, Cfg<S>::kAChunk, smem_u32(&full[st]));
+        bulk_g2s(dst + Cfg<S>::kAChunk, bsrc + c * Cfg<S>::kBChunk, Cfg<S>::kBChunk,
+                 smem_u32(&full[st]));
       }
-      Cx<ff> v{{0.f, 0.f}, {0.f, 0.f}};
-      if (am[m] >= 0 && ak[k] >= 0) v = ld(A + am[m] + ak[k]);
-      __nv_bfloat16 dr[S], di[S];
-      digits<S>(v.re.hi, v.re.lo, ea[m], dr);
-      digits<S>(v.im.hi, v.im.lo, ea[m], di);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      for (long long c = 0; c < nchunks; ++c) {
+        const int st = (int)(c % kStages);
+        const long long g = c / Cfg<S>::kFlush;
+        const bool first = c % Cfg<S>::kFlush == 0;
+        const bool last = (c + 1) % Cfg<S>::kFlush == 0 || c + 1 == nchunks;
+        if ((first && g > 0 && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((g - 1) & 1))) ||
+            !mbar_wait(smem_u32(&full[st]), (uint32_t)((c / kStages) & 1))) {
+          bad = 1;
+          atomicAdd(&pk_tc_timeouts, 1);
+          break;
+        }
+        fence_after();
+        const uint32_t a0 = sm0 + st * Cfg<S>::kStage, b0 = a0 + Cfg<S>::kAChunk;
+#pragma unroll 1
+        for (int lv = 0; lv < S; ++lv)
+          for (int i = 0; i <= lv; ++i)
 #pragma unroll
-      for (int i = 0; i < S; ++i) {
-        unsigned char* sl = As + i * kABytes;
-        *(__nv_bfloat16*)(sl + tile_off(2 * m, k, kKr / 8)) = dr[i];
-        *(__nv_bfloat16*)(sl + tile_off(2 * m, kKc + k, kKr / 8)) = __hneg(di[i]);
-        *(__nv_bfloat16*)(sl + tile_off(2 * m + 1, k, kKr / 8)) = di[i];
-        *(__nv_bfloat16*)(sl + tile_off(2 * m + 1, kKc + k, kKr / 8)) = dr[i];
+            for (int kk = 0; kk < kKr / 16; ++kk) {
+              const uint64_t da = smem_desc(a0 + i * kABytes + kk * 256, 128, kKcores * 128);
+              const uint64_t db = smem_desc(b0 + (lv - i) * kBBytes + kk * 256, 128, kKcores * 128);
+              mma_bf16(tmem + lv * kN, da, db, (first && i == 0 && kk == 0) ? 0u : 1u);
+            }
+        commit(smem_u32(&empty[st]));
+        if (last) commit(smem_u32(&acc_full));
       }
     }
-    // B: 32 k x 64 columns complex; (k, n) -> row n, columns k (re) and 32+k (im)
-    for (int idx = tid; idx < kNc * kKc; idx += kThreads) {
-      int n, k;
-      if (s.b_kinner) {
-        n = idx / kKc;
-        k = idx % kKc;
-      } else {
-        n = idx % kNc;
-        k = idx / kNc;
+  } else {  // epilogue warps: flush the levels every kFlush chunks
+    const int quarter = warp & 3, half = (warp - 2) / 4;
+    for (long long g = 0; g < ngroups; ++g) {
+      if (!mbar_wait(smem_u32(&acc_full), (uint32_t)(g & 1))) {
+        if (lane == 0) {
+          bad = 1;
+          atomicAdd(&pk_tc_timeouts, 1);
+        }
+        break;
       }
-      Cx<ff> v{{0.f, 0.f}, {0.f, 0.f}};
-      if (bn[n] >= 0 && bk[k] >= 0) v = ld(B + bk[k] + bn[n]);
-      __nv_bfloat16 dr[S], di[S];
-      digits<S>(v.re.hi, v.re.lo, eb[n], dr);
-      digits<S>(v.im.hi, v.im.lo, eb[n], di);
-#pragma unroll
-      for (int i = 0; i < S; ++i) {
-        unsigned char* sl = Bs + i * kBBytes;
-        *(__nv_bfloat16*)(sl + tile_off(n, k, kKr / 8)) = dr[i];
-        *(__nv_bfloat16*)(sl + tile_off(n, kKc + k, kKr / 8)) = di[i];
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
       fence_after();
 #pragma unroll 1
-      for (int L = 0; L < S; ++L)
-        for (int i = 0; i <= L; ++i)
-          for (int kk = 0; kk < kKr / 16; ++kk) {
-            const uint64_t da = smem_desc(a0 + i * kABytes + kk * 256, 128, (kKr / 8) * 128);
-            const uint64_t db = smem_desc(b0 + (L - i) * kBBytes + kk * 256, 128, (kKr / 8) * 128);
-            mma_bf16(tmem + L * kN, da, db, (first && i == 0 && kk == 0) ? 0u : 1u);
-          }
-      commit(smem_u32(&mbar));
-    }
-    const bool ok = mbar_wait(smem_u32(&mbar), phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        bad = 1;
-        atomicAdd(&pk_tc_timeouts, 1);
-      }
-      break;
-    }
-    fence_after();
-    first = false;
-    if ((c + 1) % Cfg<S>::kFlush == 0 || c + 1 == nchunks) {
-      // levels -> float-float: sum_L acc_L 2^(-14-8L), each level an exact integer
-#pragma unroll 1
-      for (int L = 0; L < S; ++L) {
+      for (int lv = 0; lv < S; ++lv) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + L * kN + col_half * 32, v);
-        const float w = ldexpf(1.0f, -14 - 8 * L);
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + lv * kN + half * 32, v);
+        const float w = ldexpf(1.0f, -14 - 8 * lv);
 #pragma unroll
         for (int j = 0; j < 32; ++j) ff_acc(acc_h[j], acc_l[j], v[j] * w, 0.f);
       }
       fence_before();
-      first = true;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty));
     }
-    __syncthreads();
   }
+  __syncthreads();
 
-  // ---- epilogue: scale by 2^(e(m) + e(n)) and the step's normalisation, pair re / im
-  const int m = lane_row >> 1, part = lane_row & 1;
-  Cx<ff>* C = arena + s.off_c + base[2];
+  // ---- store: scale by 2^(e(m) + e(n)) and the step's normalisation, pair re / im
   float vmax = 0;
+  if (warp >= 2) {
+    const int quarter = warp & 3, half = (warp - 2) / 4;
+    const int row = quarter * 32 + lane, m = row >> 1, part = row & 1;
+    Cx<ff>* C = arena + s.off_c + cbase;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const int n = col_half * 32 + j;
-    const int e = ea[m] + eb[n];
-    ff mine = ff_norm(acc_h[j], acc_l[j]);
-    mine.hi = ldexpf(mine.hi, e) * scale;
-    mine.lo = ldexpf(mine.lo, e) * scale;
-    if (bad) mine.hi = mine.lo = __int_as_float(0x7fc00000);
-    ff other;
-    other.hi = __shfl_xor_sync(0xffffffffu, mine.hi, 1);
-    other.lo = __shfl_xor_sync(0xffffffffu, mine.lo, 1);
-    if ((j & 1) == part && cm[m] >= 0 && cn[n] >= 0) {
-      const Cx<ff> out = part == 0 ? Cx<ff>{mine, other} : Cx<ff>{other, mine};
-      st(C + cm[m] + cn[n], out);
-      vmax = fmaxf(vmax, mag(out));
+    for (int j = 0; j < 32; ++j) {
+      const int n = half * 32 + j;
+      ff mine = ff_norm(acc_h[j], acc_l[j]);
+      const int e = ea[m] + eb[n];
+      mine.hi = ldexpf(mine.hi, e) * scale;
+      mine.lo = ldexpf(mine.lo, e) * scale;
+      if (bad) mine.hi = mine.lo = __int_as_float(0x7fc00000);
+      ff other;
+      other.hi = __shfl_xor_sync(0xffffffffu, mine.hi, 1);
+      other.lo = __shfl_xor_sync(0xffffffffu, mine.lo, 1);
+      if ((j & 1) == part && cm[m] >= 0 && cn[n] >= 0) {
+        const Cx<ff> out = part == 0 ? Cx<ff>{mine, other} : Cx<ff>{other, mine};
+        st(C + cm[m] + cn[n], out);
+        vmax = fmaxf(vmax, mag(out));
+      }
     }
   }
   block_max_to_meta(vmax, meta + s.c);
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 0)
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(Cfg<S>::kCols)
                  : "memory");

@@ -245,6 +245,7 @@ bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err)
 
   // steps with their offsets
   for (Op& op : ops) {
+    op.st.tc = 0;  // the reverse program keeps its GEMM steps on the CUDA cores
     op.st.off_a = inst[op.in_a].off;
     op.st.off_b = op.in_b >= 0 ? inst[op.in_b].off : 0;
     op.st.off_c = inst[op.out].off;

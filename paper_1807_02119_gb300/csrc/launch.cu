@@ -38,7 +38,6 @@ __global__ void __launch_bounds__(256) k_widen(const ConvRec* __restrict__ conv,
 }
 
 constexpr int kNumClasses = 6;  // build, rows, split-K, results, GEMM, tensor-core GEMM
-constexpr int kTcDigits = 5;    // BF16 digits per float-float operand on the tensor cores
 
 // Optional per-launch timing: an event pair around every launch, summed per class.
 struct Prof {
@@ -109,18 +108,26 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
 
 // One contraction step; `counter` is its split-K ticket, `by` its algorithmic bytes
 // (for the optional timing only).
+TcScratch tc_scratch_layout(const Step& s) { return tc_scratch(s.Bsz, s.M, s.N, s.K); }
+
 template <typename R>
 cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* partial,
-                        unsigned* counter, cudaStream_t stream, Marker& mk, double by) {
+                        unsigned* counter, cudaStream_t stream, Marker& mk, double by,
+                        unsigned char* tc_scratch = nullptr) {
   const double cm = (double)s.R * (double)s.K * (double)s.N;
   const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
   cudaError_t e;
   if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
     if constexpr (std::is_same<R, ff>::value) {
-      if (s.tc) {
+      if (s.tc && tc_scratch) {  // digits of A and B, then the tensor-core GEMM
+        const TcScratch L = tc_scratch_layout(s);
         mk.begin(5, cm, by);
+        k_digits<kTcDigits, true><<<(unsigned)(s.Bsz * L.tiles_m), tc::kConvThreads,
+                                    tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
+        k_digits<kTcDigits, false><<<(unsigned)(s.Bsz * L.tiles_n), tc::kConvThreads,
+                                     tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
         k_gemm_tc<kTcDigits><<<(unsigned)gemm_tiles, tc::kThreads, tc::Cfg<kTcDigits>::kSmem, stream>>>(
-            s, arena, meta);
+            s, arena, meta, tc_scratch);
         mk.end();
         return cudaGetLastError();
       }
@@ -157,9 +164,11 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
   Meta* meta = (Meta*)(base + p.off_meta);
   Cx<double>* partial = (Cx<double>*)(base + p.off_scratch);
   unsigned* counters = (unsigned*)(base + p.off_counter);
+  unsigned char* tcs = (std::is_same<R, ff>::value && p.tc_bytes > 0)
+                           ? (unsigned char*)arena_base + p.tc_offset() : nullptr;
   for (int32_t i = first; i < last; ++i) {
     cudaError_t e = launch_step<R>(p.steps[i], arena, meta, partial, counters + i, stream, mk,
-                                   step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)));
+                                   step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)), tcs);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -333,6 +342,12 @@ cudaError_t prepare_kernels() {
   if ((e = raise_rows_smem<ff>()) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_gemm_tc<kTcDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::Cfg<kTcDigits>::kSmem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_digits<kTcDigits, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::Cfg<kTcDigits>::kConvSmem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_digits<kTcDigits, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::Cfg<kTcDigits>::kConvSmem)) != cudaSuccess)
     return e;
   if (dev >= 0 && dev < 256) done[dev] = true;
   return cudaSuccess;

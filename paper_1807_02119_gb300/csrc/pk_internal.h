@@ -129,6 +129,36 @@ struct TailStep {
   int64_t off_a, off_b, off_c;       // complex128 elements into the tail region
 };
 
+#ifdef __CUDACC__
+#define PK_HD __host__ __device__
+#else
+#define PK_HD
+#endif
+
+// GEMM steps of the split precision on the tensor cores: each operand element becomes
+// kTcDigits BF16 digits (exact 8-bit pieces), stored per 64-row block and 16-complex-k
+// chunk in the workspace after the arena, followed by the blocks' exponents.
+constexpr int kTcDigits = 5;
+constexpr int kTcMc = 64, kTcNc = 64, kTcKc = 16;
+constexpr long long kTcAChunk = (long long)kTcDigits * (2 * kTcMc) * (2 * kTcKc) * 2;
+constexpr long long kTcBChunk = (long long)kTcDigits * kTcNc * (2 * kTcKc) * 2;
+struct TcScratch {
+  long long tiles_m, tiles_n, chunks;
+  long long a_off, b_off, ea_off, eb_off, bytes;
+};
+PK_HD inline TcScratch tc_scratch(long long Bsz, long long M, long long N, long long K) {
+  TcScratch x;
+  x.tiles_m = (M + kTcMc - 1) / kTcMc;
+  x.tiles_n = (N + kTcNc - 1) / kTcNc;
+  x.chunks = (K + kTcKc - 1) / kTcKc;
+  x.a_off = 0;
+  x.b_off = x.a_off + Bsz * x.tiles_m * x.chunks * kTcAChunk;
+  x.ea_off = x.b_off + Bsz * x.tiles_n * x.chunks * kTcBChunk;
+  x.eb_off = x.ea_off + ((Bsz * x.tiles_m * kTcMc * 4 + 255) & ~255LL);
+  x.bytes = x.eb_off + ((Bsz * x.tiles_n * kTcNc * 4 + 255) & ~255LL);
+  return x;
+}
+
 // Reverse pass: one record per clause tensor (merged edge group) of a gradient plan.
 // The adjoint dZ/dM of the group's matrix M (full shape q x q, or q for a loop vector)
 // is read from the arena with the strides below and added into an accumulator.
@@ -205,6 +235,8 @@ struct Plan {
   uint64_t off_recipe = 0, off_slots = 0, off_meta = 0, off_result = 0, off_scratch = 0,
            off_counter = 0, off_arena = 0;
   uint64_t ws_bytes(int32_t precision) const;
+  // byte offset of the split precision's digit scratch from the arena's start
+  uint64_t tc_offset() const { return ((uint64_t)arena_elems * 16ull + 255) & ~uint64_t(255); }
   std::vector<uint8_t> program;      // recipe + slots blob copied by pk_upload
   // split precision: steps >= tail_first run in complex128 in a separate tail region;
   // bulk tensors they read are up-converted there first
@@ -215,6 +247,9 @@ struct Plan {
   int64_t final_tail_off = 0;        // final tensor's offset in the tail region
   int32_t n_meta = 0;                // tensors + converted copies
   uint64_t off_tail = 0;             // byte offset of the tail region (split only)
+  int64_t tc_bytes = 0;              // split precision: digit scratch of the largest
+                                     // tensor-core step (after the arena)
+  int32_t n_tc = 0;                  // tensor-core steps per slice
   uint64_t off_conv = 0;             // byte offset of the ConvRec records (in the program)
   // general networks (PK_FLAG_GRAD or custom weights): every edge group is a tensor
   bool general = false;

@@ -733,6 +733,8 @@ uint64_t Plan::ws_bytes(int32_t precision) const {
     if (tail.empty()) return off_arena + (uint64_t)arena_elems * 8ull;
     return off_tail + (uint64_t)tail_elems * 16ull;  // complex128 tail region after the arena
   }
+  if (precision == PK_SPLIT && tc_bytes > 0)   // float-float pairs, then the digit scratch
+    return off_arena + tc_offset() + (uint64_t)tc_bytes;
   return off_arena + (uint64_t)arena_elems * 16ull;  // complex128 and float-float pairs
 }
 
@@ -875,6 +877,13 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
     p.steps[s] = st;
   }
   p.final_tensor = n_tens - 1;
+  p.tc_bytes = 0;
+  p.n_tc = 0;
+  for (const Step& st : p.steps)
+    if (st.kernel == KGEMM && st.tc) {
+      p.n_tc++;
+      p.tc_bytes = std::max<int64_t>(p.tc_bytes, tc_scratch(st.Bsz, st.M, st.N, st.K).bytes);
+    }
 
   // ---- sizes, lifetimes, stats
   p.max_rank = 0;
