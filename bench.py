@@ -325,7 +325,7 @@ def run_large(args):
             plans = []
             for kk in ks:
                 try:
-                    plans.append(pk.Plan(ctx, kk, q, restarts=512 if q > 2 else 8))
+                    plans.append(pk.Plan(ctx, kk, q, restarts=512 if q == 3 else 8))
                 except pk.PkError as e:
                     plans.append(None)
             cms = [p.stats()["cmacs"] if p else float("inf") for p in plans]
