@@ -6,13 +6,13 @@
 // "Error-free transformations of matrix multiplication", Numer. Algorithms 2012):
 // with e(m) the binary exponent of row m's largest entry (over all of K),
 //     x 2^-e(m) = sum_i d_i 2^(-7-8i) + r,   d_i integers, |d_i| <= 128,  |r| <= 2^(-8S-7),
-// and likewise for the columns of B.  Slice i holds d_i 2^(-8i), exact in BF16; digit
-// products are exact; the S (S+1)/2 pairs with i + j < S are accumulated in three FP32
-// TMEM accumulators: level 0 (i = j = 0) and level 1 (i + j = 1), both exact while below
-// 2^24 units, and all levels >= 2 together, whose FP32 rounding lies near 2^-40 of the
-// leading term.  The accumulators are flushed to float-float registers every kFlush
-// chunks; the result is
-//     C(m, n) = 2^(e(m) + e(n) - 14) (acc_0 + acc_1 + acc_rest).
+// and likewise for the columns of B.  A digit is exact in BF16 (8 significant bits), a
+// digit product (|d_a d_b| <= 2^14) is exact, and a sum of such products stays exact in
+// FP32 while it stays below 2^24: the S digit pairs (i, j) of one level L = i + j are
+// accumulated together, and every level is flushed to float-float registers before
+// (L + 1) K' 2^14 can reach 2^24.  Levels L >= S are dropped (their weight is at most
+// 2^(-8S) of the leading term); the result is
+//     C(m, n) = 2^(e(m) + e(n)) sum_{L < S} acc_L(m, n) 2^(-14-8L).
 //
 // Complex arithmetic as one real product: with the rows of C interleaved (re, im),
 //     [re row m] = [Re A(m,:), -Im A(m,:)] . [Re B; Im B],
@@ -28,15 +28,13 @@
 //    matrices) and stores each chunk contiguously in the workspace.  The operands are
 //    gathered through the step's stride runs (arbitrary index permutations, which a TMA
 //    tensor map cannot express); each element is read and converted once.
-//  * k_gemm_tc: persistent, one CTA per SM walking the output tiles (batch, 64-row block,
-//    64-column block).  Warp 0 streams every tile's digit chunks into a 3-stage shared-
-//    memory ring with bulk asynchronous copies (cp.async.bulk, completion by mbarrier
-//    transaction count); warp 1 issues the S (S+1)/2 digit-pair MMAs per K step, releases
-//    each stage with tcgen05.commit and alternates between two TMEM accumulator buffers
-//    per flush group; eight epilogue warps drain a full buffer into float-float registers
-//    while the MMAs fill the other, and store C at the end of each tile.  Every wait is
-//    bounded: on expiry the CTA's remaining tiles are written as NaN and the expiry is
-//    counted in pk_tc_timeouts, so a failure shows up as a wrong result, not a hang.
+//  * k_gemm_tc: warp 0 streams the chunks of its (batch, row block, column block) into a
+//    3-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion by
+//    mbarrier transaction count); warp 1 issues the S (S+1)/2 digit-pair MMAs per K step
+//    and releases each stage with tcgen05.commit; eight epilogue warps flush the S level
+//    accumulators from TMEM into float-float registers every kFlush chunks and finally
+//    store C.  Every wait is bounded: on expiry the tile is poisoned with NaN and counted
+//    in pk_tc_timeouts, so a failure shows up as a wrong result, not a hang.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -67,15 +65,10 @@ struct Cfg {
   static constexpr int kConvSmem = kAChunk + 1024;                // conversion staging
   static_assert(S != kTcDigits || (kAChunk == kTcAChunk && kBChunk == kTcBChunk),
                 "chunk sizes must match the host's scratch layout");
-  // TMEM: accumulators for level 0, level 1 and all levels >= 2, two buffers of 3 x kN
-  // columns (the MMAs fill one while the epilogue drains the other)
-  static constexpr int kAcc = 3;
-  static constexpr int kBufCols = 256;
-  static constexpr int kCols = 512;
-  static_assert(kAcc * kN <= kBufCols, "one buffer of accumulators must fit 256 columns");
-  // chunks per flush: the level-1 accumulator (2 digit pairs, |d_i d_j| <= 2^14 in its
-  // units) must stay exact: 2 x chunks x kKr x 2^14 < 2^24
-  static constexpr int kFlush = ((1 << 10) - 1) / (2 * kKr);
+  static constexpr int kCols = S * kN <= 32 ? 32 : S * kN <= 64 ? 64 : S * kN <= 128 ? 128
+                               : S * kN <= 256 ? 256 : 512;
+  // chunks per flush: S pairs per level x (chunks x kKr) terms x 2^14 < 2^24
+  static constexpr int kFlush = ((1 << 10) - 1) / (S * kKr) > 0 ? ((1 << 10) - 1) / (S * kKr) : 1;
 };
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
@@ -166,15 +159,13 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k, int kcores) {
 
 // S digits of the float-float value (h + l) 2^-e (|value| <= 1): d_i = nearest integer of
 // the running remainder times 2^(7+8i); the remainder is carried exactly as a float pair.
-// Slice i stores d_i 2^(-8i) (exact in BF16), so a digit pair (i, j) lands at its level's
-// weight 2^(-8(i+j)) without further scaling.
 template <int S>
 __device__ __forceinline__ void digits(float h, float l, int e, __nv_bfloat16* d) {
   float yh = ldexpf(h, 7 - e), yl = ldexpf(l, 7 - e);
 #pragma unroll
   for (int i = 0; i < S; ++i) {
     const float di = rintf(yh);
-    d[i] = __float2bfloat16_rn(ldexpf(di, -8 * i));  // slice i carries its weight 2^(-8i)
+    d[i] = __float2bfloat16_rn(di);
     float s, err;
     two_sum(__fsub_rn(yh, di), yl, s, err);
     yh = s * 256.0f;
@@ -330,36 +321,60 @@ __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const
   }
 }
 
-// Persistent GEMM over the step's output tiles (64 complex rows x 64 complex columns of one
-// batch index): warp 0 produces digit chunks, warp 1 issues MMAs, warps 2..9 drain the
-// accumulators and store C.
+// C tile (64 complex rows x 64 complex columns of one batch index) from the digit chunks:
+// warp 0 streams chunks into the stage ring, warp 1 issues the MMAs, warps 2..9 flush
+// the level accumulators and store C.
 template <int S>
 __global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff>* arena, Meta* meta,
                                                              const unsigned char* scratch) {
   using namespace tc;
   static_assert(S == kTcDigits, "digit scratch laid out for kTcDigits digits");
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2];
+  __shared__ long long cm[kMc], cn[kNc];
+  __shared__ long long cbase;
+  __shared__ int ea[kMc], eb[kNc];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full, acc_empty;
   __shared__ uint32_t tmem_slot;
-  __shared__ volatile int bad;
+  __shared__ int bad;
   unsigned char* sm = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K);
-  const long long n_tiles = L.tiles_m * L.tiles_n * s.Bsz;
-  const long long nchunks = L.chunks;
-  const long long groups_per_tile = (nchunks + Cfg<S>::kFlush - 1) / Cfg<S>::kFlush;
+  long long t = blockIdx.x;
+  const long long tm = t % L.tiles_m;
+  t /= L.tiles_m;
+  const long long tn = t % L.tiles_n;
+  const long long bb = t / L.tiles_n;
 
   if (tid == 0) {
+    long long a, b;
+    runs4(bb, s.gb, s.ngb, a, b, cbase);
     bad = 0;
     for (int i = 0; i < kStages; ++i) {
       mbar_init(smem_u32(&full[i]), 1);
       mbar_init(smem_u32(&empty[i]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&acc_full[b]), 1);
-      mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
-    }
+    mbar_init(smem_u32(&acc_full), 1);
+    mbar_init(smem_u32(&acc_empty), kEpiWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid >= 64 && tid < 64 + kMc) {
+    const int i = tid - 64;
+    const long long m = tm * kMc + i;
+    long long a, b;
+    if (m < s.M)
+      runs4(m, s.gm, s.ngm, a, b, cm[i]);
+    else
+      cm[i] = -1;
+    ea[i] = ((const int*)(scratch + L.ea_off))[(bb * L.tiles_m + tm) * kMc + i];
+  } else if (tid >= 64 + kMc && tid < 64 + kMc + kNc) {
+    const int j = tid - 64 - kMc;
+    const long long n = tn * kNc + j;
+    long long a, b;
+    if (n < s.N)
+      runs4(n, s.gn, s.ngn, a, b, cn[j]);
+    else
+      cn[j] = -1;
+    eb[j] = ((const int*)(scratch + L.eb_off))[(bb * L.tiles_n + tn) * kNc + j];
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -373,141 +388,112 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
+  const long long nchunks = L.chunks;
+  const long long ngroups = (nchunks + Cfg<S>::kFlush - 1) / Cfg<S>::kFlush;
   const uint32_t sm0 = smem_u32(sm);
-  auto tile_coords = [&](long long t, long long& tm, long long& tn, long long& bb) {
-    tm = t % L.tiles_m;
-    t /= L.tiles_m;
-    tn = t % L.tiles_n;
-    bb = t / L.tiles_n;
-  };
-  float vmax = 0;
+
+  float acc_h[32], acc_l[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc_h[j] = acc_l[j] = 0.f;
 
   if (warp == 0) {
-    if (lane == 0) {  // producer: every chunk of every tile of this CTA, in order
-      long long gc = 0;
-      for (long long t = blockIdx.x; t < n_tiles && !bad; t += gridDim.x) {
-        long long tm, tn, bb;
-        tile_coords(t, tm, tn, bb);
-        const unsigned char* asrc =
-            scratch + L.a_off + (bb * L.tiles_m + tm) * nchunks * (long long)Cfg<S>::kAChunk;
-        const unsigned char* bsrc =
-            scratch + L.b_off + (bb * L.tiles_n + tn) * nchunks * (long long)Cfg<S>::kBChunk;
-        for (long long c = 0; c < nchunks; ++c, ++gc) {
-          const int st = (int)(gc % kStages);
-          if (gc >= kStages && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((gc / kStages) - 1) & 1))) {
-            bad = 1;
-            atomicAdd(&pk_tc_timeouts, 1);
-            break;
-          }
-          const uint32_t dst = sm0 + st * Cfg<S>::kStage;
-          mbar_expect_tx(smem_u32(&full[st]), Cfg<S>::kStage);
-          bulk_g2s(dst, asrc + c * Cfg<S>::kAChunk, Cfg<S>::kAChunk, smem_u32(&full[st]));
-          bulk_g2s(dst + Cfg<S>::kAChunk, bsrc + c * Cfg<S>::kBChunk, Cfg<S>::kBChunk,
-                   smem_u32(&full[st]));
+    if (lane == 0) {  // producer
+      const unsigned char* asrc =
+          scratch + L.a_off + (bb * L.tiles_m + tm) * nchunks * (long long)Cfg<S>::kAChunk;
+      const unsigned char* bsrc =
+          scratch + L.b_off + (bb * L.tiles_n + tn) * nchunks * (long long)Cfg<S>::kBChunk;
+      for (long long c = 0; c < nchunks; ++c) {
+        const int st = (int)(c % kStages);
+        if (c >= kStages && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c / kStages) - 1) & 1))) {
+          bad = 1;
+          atomicAdd(&pk_tc_timeouts, 1);
+          break;
         }
+        const uint32_t dst = sm0 + st * Cfg<S>::kStage;
+        mbar_expect_tx(smem_u32(&full[st]), Cfg<S>::kStage);
+        bulk_g2s(dst, asrc + c * Cfg<S>::kAChunk, Cfg<S>::kAChunk, smem_u32(&full[st]));
+        bulk_g2s(dst + Cfg<S>::kAChunk, bsrc + c * Cfg<S>::kBChunk, Cfg<S>::kBChunk,
+                 smem_u32(&full[st]));
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      long long gc = 0, gg = 0;
-      for (long long t = blockIdx.x; t < n_tiles && !bad; t += gridDim.x) {
-        for (long long c = 0; c < nchunks; ++c, ++gc) {
-          const int st = (int)(gc % kStages);
-          const bool first = c % Cfg<S>::kFlush == 0;
-          const bool last = (c + 1) % Cfg<S>::kFlush == 0 || c + 1 == nchunks;
-          const int buf = (int)(gg & 1);
-          if ((first && gg >= 2 &&
-               !mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)(((gg >> 1) - 1) & 1))) ||
-              !mbar_wait(smem_u32(&full[st]), (uint32_t)((gc / kStages) & 1))) {
-            bad = 1;
-            atomicAdd(&pk_tc_timeouts, 1);
-            break;
-          }
-          fence_after();
-          const uint32_t a0 = sm0 + st * Cfg<S>::kStage, b0 = a0 + Cfg<S>::kAChunk;
-          const uint32_t d0 = tmem + buf * Cfg<S>::kBufCols;
-#pragma unroll 1
-          for (int lv = 0; lv < S; ++lv)
-            for (int i = 0; i <= lv; ++i)
-#pragma unroll
-              for (int kk = 0; kk < kKr / 16; ++kk) {
-                const int acc = lv < 2 ? lv : 2;
-                const uint64_t da = smem_desc(a0 + i * kABytes + kk * 256, 128, kKcores * 128);
-                const uint64_t db = smem_desc(b0 + (lv - i) * kBBytes + kk * 256, 128, kKcores * 128);
-                const bool init = first && kk == 0 && i == 0 && lv <= 2;  // first term of each accumulator
-                mma_bf16(d0 + acc * kN, da, db, init ? 0u : 1u);
-              }
-          commit(smem_u32(&empty[st]));
-          if (last) {
-            commit(smem_u32(&acc_full[buf]));
-            ++gg;
-          }
-        }
-        if (bad) break;
-      }
-    }
-  } else {  // epilogue warps
-    const int quarter = warp & 3, half = (warp - 2) / 4;
-    const int row = quarter * 32 + lane, m = row >> 1, part = row & 1;
-    long long gg = 0;
-    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-      long long tm, tn, bb;
-      tile_coords(t, tm, tn, bb);
-      float acc_h[32], acc_l[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc_h[j] = acc_l[j] = 0.f;
-      for (long long g = 0; g < groups_per_tile && !bad; ++g, ++gg) {
-        const int buf = (int)(gg & 1);
-        if (!mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)((gg >> 1) & 1))) {
-          if (lane == 0) {
-            bad = 1;
-            atomicAdd(&pk_tc_timeouts, 1);
-          }
+      for (long long c = 0; c < nchunks; ++c) {
+        const int st = (int)(c % kStages);
+        const long long g = c / Cfg<S>::kFlush;
+        const bool first = c % Cfg<S>::kFlush == 0;
+        const bool last = (c + 1) % Cfg<S>::kFlush == 0 || c + 1 == nchunks;
+        if ((first && g > 0 && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((g - 1) & 1))) ||
+            !mbar_wait(smem_u32(&full[st]), (uint32_t)((c / kStages) & 1))) {
+          bad = 1;
+          atomicAdd(&pk_tc_timeouts, 1);
           break;
         }
         fence_after();
+        const uint32_t a0 = sm0 + st * Cfg<S>::kStage, b0 = a0 + Cfg<S>::kAChunk;
 #pragma unroll 1
-        for (int a = 0; a < 3; ++a) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * Cfg<S>::kBufCols + a * kN + half * 32, v);
+        for (int lv = 0; lv < S; ++lv)
+          for (int i = 0; i <= lv; ++i)
 #pragma unroll
-          for (int j = 0; j < 32; ++j) ff_acc(acc_h[j], acc_l[j], v[j], 0.f);
-        }
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+            for (int kk = 0; kk < kKr / 16; ++kk) {
+              const uint64_t da = smem_desc(a0 + i * kABytes + kk * 256, 128, kKcores * 128);
+              const uint64_t db = smem_desc(b0 + (lv - i) * kBBytes + kk * 256, 128, kKcores * 128);
+              mma_bf16(tmem + lv * kN, da, db, (first && i == 0 && kk == 0) ? 0u : 1u);
+            }
+        commit(smem_u32(&empty[st]));
+        if (last) commit(smem_u32(&acc_full));
       }
-      // store this tile: scale by 2^(e(m) + e(n) - 14) and the step's normalisation
-      long long cbase, d1, d2, cm = -1;
-      runs4(bb, s.gb, s.ngb, d1, d2, cbase);
-      const long long mg = tm * kMc + m;
-      if (mg < s.M) runs4(mg, s.gm, s.ngm, d1, d2, cm);
-      const int em = ((const int*)(scratch + L.ea_off))[(bb * L.tiles_m + tm) * kMc + m];
-      const int* ebp = (const int*)(scratch + L.eb_off) + (bb * L.tiles_n + tn) * kNc;
-      Cx<ff>* C = arena + s.off_c + cbase;
+    }
+  } else {  // epilogue warps: flush the levels every kFlush chunks
+    const int quarter = warp & 3, half = (warp - 2) / 4;
+    for (long long g = 0; g < ngroups; ++g) {
+      if (!mbar_wait(smem_u32(&acc_full), (uint32_t)(g & 1))) {
+        if (lane == 0) {
+          bad = 1;
+          atomicAdd(&pk_tc_timeouts, 1);
+        }
+        break;
+      }
+      fence_after();
+#pragma unroll 1
+      for (int lv = 0; lv < S; ++lv) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + lv * kN + half * 32, v);
+        const float w = ldexpf(1.0f, -14 - 8 * lv);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = half * 32 + j;
-        const long long ng = tn * kNc + n;
-        ff mine = ff_norm(acc_h[j], acc_l[j]);
-        const int e = em + ebp[n] - 14;
-        mine.hi = ldexpf(mine.hi, e) * scale;
-        mine.lo = ldexpf(mine.lo, e) * scale;
-        if (bad) mine.hi = mine.lo = __int_as_float(0x7fc00000);
-        ff other;
-        other.hi = __shfl_xor_sync(0xffffffffu, mine.hi, 1);
-        other.lo = __shfl_xor_sync(0xffffffffu, mine.lo, 1);
-        if ((j & 1) == part && cm >= 0 && ng < s.N) {
-          long long cn, e1, e2;
-          runs4(ng, s.gn, s.ngn, e1, e2, cn);
-          const Cx<ff> out = part == 0 ? Cx<ff>{mine, other} : Cx<ff>{other, mine};
-          st(C + cm + cn, out);
-          vmax = fmaxf(vmax, mag(out));
-        }
+        for (int j = 0; j < 32; ++j) ff_acc(acc_h[j], acc_l[j], v[j] * w, 0.f);
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty));
     }
   }
   __syncthreads();
+
+  // ---- store: scale by 2^(e(m) + e(n)) and the step's normalisation, pair re / im
+  float vmax = 0;
+  if (warp >= 2) {
+    const int quarter = warp & 3, half = (warp - 2) / 4;
+    const int row = quarter * 32 + lane, m = row >> 1, part = row & 1;
+    Cx<ff>* C = arena + s.off_c + cbase;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int n = half * 32 + j;
+      ff mine = ff_norm(acc_h[j], acc_l[j]);
+      const int e = ea[m] + eb[n];
+      mine.hi = ldexpf(mine.hi, e) * scale;
+      mine.lo = ldexpf(mine.lo, e) * scale;
+      if (bad) mine.hi = mine.lo = __int_as_float(0x7fc00000);
+      ff other;
+      other.hi = __shfl_xor_sync(0xffffffffu, mine.hi, 1);
+      other.lo = __shfl_xor_sync(0xffffffffu, mine.lo, 1);
+      if ((j & 1) == part && cm[m] >= 0 && cn[n] >= 0) {
+        const Cx<ff> out = part == 0 ? Cx<ff>{mine, other} : Cx<ff>{other, mine};
+        st(C + cm[m] + cn[n], out);
+        vmax = fmaxf(vmax, mag(out));
+      }
+    }
+  }
   block_max_to_meta(vmax, meta + s.c);
   fence_before();
   __syncthreads();

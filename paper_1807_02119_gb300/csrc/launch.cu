@@ -110,19 +110,6 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
 // (for the optional timing only).
 TcScratch tc_scratch_layout(const Step& s) { return tc_scratch(s.Bsz, s.M, s.N, s.K); }
 
-// Streaming multiprocessors of the current device (persistent grids), cached per device.
-int sm_count() {
-  static int cache[256] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 152;
-  if (cache[dev] == 0) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-    cache[dev] = n;
-  }
-  return cache[dev];
-}
-
 template <typename R>
 cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* partial,
                         unsigned* counter, cudaStream_t stream, Marker& mk, double by,
@@ -139,8 +126,7 @@ cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* par
                                     tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
         k_digits<kTcDigits, false><<<(unsigned)(s.Bsz * L.tiles_n), tc::kConvThreads,
                                      tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
-        const long long grid = std::min<long long>(gemm_tiles, sm_count());  // persistent
-        k_gemm_tc<kTcDigits><<<(unsigned)grid, tc::kThreads, tc::Cfg<kTcDigits>::kSmem, stream>>>(
+        k_gemm_tc<kTcDigits><<<(unsigned)gemm_tiles, tc::kThreads, tc::Cfg<kTcDigits>::kSmem, stream>>>(
             s, arena, meta, tc_scratch);
         mk.end();
         return cudaGetLastError();
