@@ -17,7 +17,7 @@
 // Complex arithmetic as one real product: with the rows of C interleaved (re, im),
 //     [re row m] = [Re A(m,:), -Im A(m,:)] . [Re B; Im B],
 //     [im row m] = [Im A(m,:),  Re A(m,:)] . [Re B; Im B],
-// so a CTA tile of 64 complex rows x 64 complex columns is one M=128, N=64 MMA per
+// so a CTA tile of 64 complex rows x 48 complex columns is one M=128, N=48 MMA per
 // BF16 K-step of 16 (K' = 2 K).
 //
 // Data movement, three kernels per step:
@@ -51,7 +51,7 @@ constexpr int kKr = 2 * kKc;     // MMA K per chunk (real: re half, im half)
 constexpr int kKcores = kKr / 8; // 16-byte K core columns per row
 constexpr int kABytes = kM * kKr * 2;   // one digit slice of an A chunk (BF16): 8 KB
 constexpr int kBBytes = kN * kKr * 2;   // one digit slice of a B chunk: 4 KB
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);   // producer, MMA issuer, epilogue
 constexpr int kConvThreads = 256;
@@ -61,8 +61,8 @@ struct Cfg {
   static constexpr int kAChunk = S * kABytes;     // one chunk of A digits (all slices)
   static constexpr int kBChunk = S * kBBytes;
   static constexpr int kStage = kAChunk + kBChunk;
-  static constexpr int kSmem = kStages * kStage + 1024;           // + alignment slack
-  static constexpr int kConvSmem = kAChunk + 1024;                // conversion staging
+  static constexpr int kSmem = kStages * kStage;   // two CTAs per SM (16-byte alignment suffices)
+  static constexpr int kConvSmem = kAChunk + 1024;                // conversion staging (+ alignment)
   static_assert(S != kTcDigits || (kAChunk == kTcAChunk && kBChunk == kTcBChunk),
                 "chunk sizes must match the host's scratch layout");
   static constexpr int kCols = S * kN <= 32 ? 32 : S * kN <= 64 ? 64 : S * kN <= 128 ? 128
@@ -151,6 +151,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 and 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Byte offset of element (row, k) in a K-major, unswizzled tile with `kcores` 8-element
 // K core columns: 8-row groups of kcores x 128 bytes, core matrices of 8 rows x 16 bytes.
 __device__ __forceinline__ uint32_t tile_off(int row, int k, int kcores) {
@@ -207,14 +233,15 @@ __device__ __forceinline__ void convert_chunk(const Step& s, const Cx<ff>* base,
                                               unsigned char* stage) {
   constexpr int kSlice = IS_A ? kABytes : kBBytes;
   const bool kin = IS_A ? s.a_kinner : s.b_kinner;
-  for (int idx = threadIdx.x; idx < 64 * kKc; idx += blockDim.x) {
+  constexpr int kRows = IS_A ? kMc : kNc;
+  for (int idx = threadIdx.x; idx < kRows * kKc; idx += blockDim.x) {
     int r, k;
     if (kin) {
       r = idx / kKc;
       k = idx % kKc;
     } else {
-      r = idx % 64;
-      k = idx / 64;
+      r = idx % kRows;
+      k = idx / kRows;
     }
     Cx<ff> v{{0.f, 0.f}, {0.f, 0.f}};
     if (ro[r] >= 0 && kx[k] >= 0) v = ld(base + ro[r] + kx[k]);
@@ -262,10 +289,11 @@ __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const
     runs4(bb, s.gb, s.ngb, a, b, c);
     base = IS_A ? a : b;
   }
+  constexpr int kRows = IS_A ? kMc : kNc;
   if (tid < 64) {
-    const long long r = tile * 64 + tid;
+    const long long r = tile * kRows + tid;
     long long a, b, c;
-    if (r < (IS_A ? s.M : s.N)) {
+    if (tid < kRows && r < (IS_A ? s.M : s.N)) {
       if (IS_A)
         runs4(r, s.gm, s.ngm, a, b, c);
       else
@@ -294,8 +322,8 @@ __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const
   }
   red[tid] = mx;
   __syncthreads();
-  int* ex_out = (int*)(scratch + (IS_A ? L.ea_off : L.eb_off)) + (bb * tiles + tile) * 64;
-  if (sub == 0) {
+  int* ex_out = (int*)(scratch + (IS_A ? L.ea_off : L.eb_off)) + (bb * tiles + tile) * kRows;
+  if (sub == 0 && r < kRows) {
     const float v = fmaxf(fmaxf(red[tid], red[tid + 1]), fmaxf(red[tid + 2], red[tid + 3]));
     ex[r] = bin_exp(v);
     ex_out[r] = ex[r];
@@ -325,18 +353,18 @@ __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const
 // warp 0 streams chunks into the stage ring, warp 1 issues the MMAs, warps 2..9 flush
 // the level accumulators and store C.
 template <int S>
-__global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff>* arena, Meta* meta,
+__global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff>* arena, Meta* meta,
                                                              const unsigned char* scratch) {
   using namespace tc;
   static_assert(S == kTcDigits, "digit scratch laid out for kTcDigits digits");
-  extern __shared__ __align__(1024) unsigned char dsm[];
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ long long cm[kMc], cn[kNc];
   __shared__ long long cbase;
   __shared__ int ea[kMc], eb[kNc];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full, acc_empty;
   __shared__ uint32_t tmem_slot;
   __shared__ int bad;
-  unsigned char* sm = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
+  unsigned char* sm = dsm;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K);
   long long t = blockIdx.x;
@@ -392,9 +420,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff
   const long long ngroups = (nchunks + Cfg<S>::kFlush - 1) / Cfg<S>::kFlush;
   const uint32_t sm0 = smem_u32(sm);
 
-  float acc_h[32], acc_l[32];
+  constexpr int kCw = kN / 2;  // columns per epilogue thread (two warps per lane quarter)
+  float acc_h[kCw], acc_l[kCw];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc_h[j] = acc_l[j] = 0.f;
+  for (int j = 0; j < kCw; ++j) acc_h[j] = acc_l[j] = 0.f;
 
   if (warp == 0) {
     if (lane == 0) {  // producer
@@ -457,11 +486,13 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff
       fence_after();
 #pragma unroll 1
       for (int lv = 0; lv < S; ++lv) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + lv * kN + half * 32, v);
+        float v[kCw];
+        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + lv * kN + half * kCw;
+        tmem_ld16(ta, v);
+        tmem_ld8(ta + 16, v + 16);
         const float w = ldexpf(1.0f, -14 - 8 * lv);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) ff_acc(acc_h[j], acc_l[j], v[j] * w, 0.f);
+        for (int j = 0; j < kCw; ++j) ff_acc(acc_h[j], acc_l[j], v[j] * w, 0.f);
       }
       fence_before();
       __syncwarp();
@@ -477,8 +508,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_gemm_tc(const Step s, Cx<ff
     const int row = quarter * 32 + lane, m = row >> 1, part = row & 1;
     Cx<ff>* C = arena + s.off_c + cbase;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int n = half * 32 + j;
+    for (int j = 0; j < kCw; ++j) {
+      const int n = half * kCw + j;
       ff mine = ff_norm(acc_h[j], acc_l[j]);
       const int e = ea[m] + eb[n];
       mine.hi = ldexpf(mine.hi, e) * scale;

@@ -126,7 +126,8 @@ cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* par
                                     tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
         k_digits<kTcDigits, false><<<(unsigned)(s.Bsz * L.tiles_n), tc::kConvThreads,
                                      tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
-        k_gemm_tc<kTcDigits><<<(unsigned)gemm_tiles, tc::kThreads, tc::Cfg<kTcDigits>::kSmem, stream>>>(
+        const long long tc_tiles = L.tiles_m * L.tiles_n * s.Bsz;
+        k_gemm_tc<kTcDigits><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<kTcDigits>::kSmem, stream>>>(
             s, arena, meta, tc_scratch);
         mk.end();
         return cudaGetLastError();
@@ -342,6 +343,9 @@ cudaError_t prepare_kernels() {
   if ((e = raise_rows_smem<ff>()) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_gemm_tc<kTcDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::Cfg<kTcDigits>::kSmem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_gemm_tc<kTcDigits>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_digits<kTcDigits, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::Cfg<kTcDigits>::kConvSmem)) != cudaSuccess)
