@@ -227,38 +227,48 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 // Gather + digit conversion of one chunk of an operand block: 64 tile rows (complex rows
 // of A, or complex columns of B) x 16 complex k.  For A every complex entry fills rows
 // 2r (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).
+__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c,
+                                       __nv_bfloat16 d) {
+  uint2 u;
+  u.x = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+  u.y = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
+  return u;
+}
+
+// Gather + digit conversion of one chunk of an operand block: kRows tile rows (complex
+// rows of A, or complex columns of B) x 16 complex k, one thread per (row, 4 consecutive
+// k), written as 8-byte groups of four BF16 digits.  For A every complex entry fills rows
+// 2r (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).
 template <int S, bool IS_A>
 __device__ __forceinline__ void convert_chunk(const Step& s, const Cx<ff>* base, const long long* ro,
                                               const int* ex, const long long* kx,
                                               unsigned char* stage) {
   constexpr int kSlice = IS_A ? kABytes : kBBytes;
-  const bool kin = IS_A ? s.a_kinner : s.b_kinner;
   constexpr int kRows = IS_A ? kMc : kNc;
-  for (int idx = threadIdx.x; idx < kRows * kKc; idx += blockDim.x) {
-    int r, k;
-    if (kin) {
-      r = idx / kKc;
-      k = idx % kKc;
-    } else {
-      r = idx % kRows;
-      k = idx / kRows;
+  for (int idx = threadIdx.x; idx < kRows * (kKc / 4); idx += blockDim.x) {
+    const int r = idx % kRows, k0 = 4 * (idx / kRows);
+    __nv_bfloat16 dr[4][S], di[4][S];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      Cx<ff> v{{0.f, 0.f}, {0.f, 0.f}};
+      if (ro[r] >= 0 && kx[k0 + u] >= 0) v = ld(base + ro[r] + kx[k0 + u]);
+      digits<S>(v.re.hi, v.re.lo, ex[r], dr[u]);
+      digits<S>(v.im.hi, v.im.lo, ex[r], di[u]);
     }
-    Cx<ff> v{{0.f, 0.f}, {0.f, 0.f}};
-    if (ro[r] >= 0 && kx[k] >= 0) v = ld(base + ro[r] + kx[k]);
-    __nv_bfloat16 dr[S], di[S];
-    digits<S>(v.re.hi, v.re.lo, ex[r], dr);
-    digits<S>(v.im.hi, v.im.lo, ex[r], di);
 #pragma unroll
     for (int i = 0; i < S; ++i) {
       unsigned char* sl = stage + i * kSlice;
+      const uint2 re = pack4(dr[0][i], dr[1][i], dr[2][i], dr[3][i]);
+      const uint2 im = pack4(di[0][i], di[1][i], di[2][i], di[3][i]);
       if (IS_A) {
-        *(__nv_bfloat16*)(sl + tile_off(2 * r, k, kKcores)) = dr[i];
-        *(__nv_bfloat16*)(sl + tile_off(2 * r, kKc + k, kKcores)) = __hneg(di[i]);
-        *(__nv_bfloat16*)(sl + tile_off(2 * r + 1, k, kKcores)) = di[i];
-        *(__nv_bfloat16*)(sl + tile_off(2 * r + 1, kKc + k, kKcores)) = dr[i];
+        const uint2 mim = pack4(__hneg(di[0][i]), __hneg(di[1][i]), __hneg(di[2][i]), __hneg(di[3][i]));
+        *(uint2*)(sl + tile_off(2 * r, k0, kKcores)) = re;
+        *(uint2*)(sl + tile_off(2 * r, kKc + k0, kKcores)) = mim;
+        *(uint2*)(sl + tile_off(2 * r + 1, k0, kKcores)) = im;
+        *(uint2*)(sl + tile_off(2 * r + 1, kKc + k0, kKcores)) = re;
       } else {
-        *(__nv_bfloat16*)(sl + tile_off(r, k, kKcores)) = dr[i];
-        *(__nv_bfloat16*)(sl + tile_off(r, kKc + k, kKcores)) = di[i];
+        *(uint2*)(sl + tile_off(r, k0, kKcores)) = re;
+        *(uint2*)(sl + tile_off(r, kKc + k0, kKcores)) = im;
       }
     }
   }
