@@ -122,6 +122,9 @@ typedef struct {
   uint64_t workspace_c128;   /* device workspace bytes for PK_C128                          */
   uint64_t workspace_c64;    /* device workspace bytes for PK_C64                           */
   uint64_t workspace_split;  /* device workspace bytes for PK_SPLIT                         */
+  int32_t n_segments;        /* runs of consecutive small steps launched as one sequence
+                                kernel (one CTA, a block barrier between steps)              */
+  int32_t n_segment_steps;   /* steps inside those runs                                     */
 } pk_plan_stats;
 
 /* ---- context ------------------------------------------------------------------ */

@@ -57,7 +57,8 @@ class pk_plan_stats(C.Structure):
                 ("bytes_c64", C.c_double), ("n_slices", C.c_int64), ("n_steps", C.c_int32),
                 ("max_rank", C.c_int32), ("order_used", C.c_int32), ("n_tensors", C.c_int32),
                 ("workspace_c128", C.c_uint64), ("workspace_c64", C.c_uint64),
-                ("workspace_split", C.c_uint64)]
+                ("workspace_split", C.c_uint64), ("n_segments", C.c_int32),
+                ("n_segment_steps", C.c_int32)]
 
 
 _lib = None

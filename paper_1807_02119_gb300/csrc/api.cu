@@ -270,6 +270,10 @@ pk_status pk_plan_info(const pk_plan* p, pk_plan_stats* out) {
   out->workspace_c128 = P.ws_bytes(PK_C128);
   out->workspace_c64 = P.ws_bytes(PK_C64);
   out->workspace_split = P.ws_bytes(PK_SPLIT);
+  int32_t seg_steps = 0;
+  for (const pk::Segment& g : P.segments) seg_steps += g.count;
+  out->n_segments = (int32_t)P.segments.size();
+  out->n_segment_steps = seg_steps;
   return PK_OK;
 }
 
@@ -363,7 +367,11 @@ pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launche
   const pk::Plan& P = p->p;
   const int64_t widen = (precision == PK_C64 && !P.conv.empty()) ? 1 : 0;
   const int64_t digits = precision == PK_SPLIT ? 2 * (int64_t)P.n_tc : 0;  // per tensor-core step
-  *launches = P.n_slices * ((P.n_init > 0 ? 1 : 0) + (int64_t)P.steps.size() + 1 + widen + digits) + 1;
+  int64_t fused = 0;  // steps saved by sequence launches (runs of small steps)
+  for (const pk::Segment& g : P.segments)
+    if (precision != PK_C64 || g.first + g.count <= P.tail_first) fused += g.count - 1;
+  *launches = P.n_slices * ((P.n_init > 0 ? 1 : 0) + (int64_t)P.steps.size() - fused + 1 + widen +
+                            digits) + 1;
   return PK_OK;
 }
 

@@ -450,6 +450,59 @@ __global__ void __launch_bounds__(256) k_outs(const Step s, Cx<R>* arena, Meta* 
   block_max_to_meta(vmax, meta + s.c);
 }
 
+// Consecutive small steps of one plan in one CTA: each step's outputs spread over the
+// threads, a block barrier between steps, its max-abs formed by a block reduction.
+// Operands written by earlier steps of the same launch are read with coherent loads
+// (the writes are visible to the CTA after the barrier).
+template <typename R>
+__global__ void __launch_bounds__(256) k_seg(const TinyStep* __restrict__ steps, int n,
+                                             Cx<R>* arena, Meta* meta) {
+  using S = typename Traits<R>::S;
+  __shared__ long long kA[kTinyK], kB[kTinyK];
+  __shared__ S red[32];
+  for (int i = 0; i < n; ++i) {
+    const TinyStep& s = steps[i];
+    const int ea = bin_exp(bits_to_val<S>(meta[s.a].maxbits));
+    const bool hasB = s.b >= 0;
+    const int eb = hasB ? bin_exp(bits_to_val<S>(meta[s.b].maxbits)) : 0;
+    const long long exp_c = meta[s.a].exp + (hasB ? meta[s.b].exp : 0) + ea + eb;
+    const S scale = (S)ldexp(1.0, -(ea + eb));
+    for (long long k = threadIdx.x; k < s.K; k += blockDim.x) split_runs(k, s.kr, s.nk, kA[k], kB[k]);
+    __syncthreads();
+    const Cx<R>* A = arena + s.off_a;
+    const Cx<R>* B = arena + s.off_b;
+    Cx<R>* C = arena + s.off_c;
+    const long long outs = s.R * s.N;
+    const int K = (int)s.K;
+    S vmax = 0;
+    for (long long o = threadIdx.x; o < outs; o += blockDim.x) {
+      const long long r = o % s.R, nn = o / s.R;
+      long long oa, ob, d, nb = 0;
+      split_runs((unsigned long long)r, s.row, s.nrow, oa, ob);
+      if (hasB) split_runs((unsigned long long)nn, s.nr, s.nn, d, nb);
+      Acc<R> acc;
+      if (hasB) {
+        for (int k = 0; k < K; ++k) acc.mac(ldc(A + oa + kA[k]), ldc(B + ob + nb + kB[k]));
+      } else {
+        for (int k = 0; k < K; ++k) acc.add(ldc(A + oa + kA[k]));
+      }
+      const Cx<R> v = acc.get(scale);
+      st(C + o, v);
+      vmax = fmax(vmax, mag(v));
+    }
+    for (int off = 16; off > 0; off >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      S m = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+      meta[s.c].maxbits = m > S(0) ? max_bits(m) : 0ull;
+      meta[s.c].exp = exp_c;
+    }
+    __syncthreads();
+  }
+}
+
 // Same contraction without offset tables (K too long for shared memory): every k
 // offset is recomputed from the stride runs.
 template <typename R>

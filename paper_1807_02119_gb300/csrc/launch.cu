@@ -167,10 +167,30 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
   unsigned* counters = (unsigned*)(base + p.off_counter);
   unsigned char* tcs = (std::is_same<R, ff>::value && p.tc_bytes > 0)
                            ? (unsigned char*)arena_base + p.tc_offset() : nullptr;
-  for (int32_t i = first; i < last; ++i) {
+  const TinyStep* tiny = (const TinyStep*)(base + p.off_tiny);
+  size_t sg = 0;
+  for (int32_t i = first; i < last;) {
+    while (sg < p.segments.size() && p.segments[sg].first < i) ++sg;
+    if (sg < p.segments.size() && p.segments[sg].first == i &&
+        i + p.segments[sg].count <= last) {  // a run of small steps: one sequence launch
+      const Segment& g = p.segments[sg];
+      double cm = 0, by = 0;
+      for (int32_t j = i; j < i + g.count; ++j) {
+        cm += (double)p.steps[j].R * (double)p.steps[j].K * (double)p.steps[j].N;
+        by += step_bytes(p, p.steps[j], (double)sizeof(Cx<R>));
+      }
+      mk.begin(1, cm, by);
+      k_seg<R><<<1, 256, 0, stream>>>(tiny + g.tiny0, g.count, arena, meta);
+      mk.end();
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      i += g.count;
+      continue;
+    }
     cudaError_t e = launch_step<R>(p.steps[i], arena, meta, partial, counters + i, stream, mk,
                                    step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)), tcs);
     if (e != cudaSuccess) return e;
+    ++i;
   }
   return cudaSuccess;
 }

@@ -122,6 +122,26 @@ struct ConvRec {
   int64_t elems;
   int32_t src_meta, dst_meta;
 };
+// A small step run inside a sequence kernel (one CTA runs consecutive small steps with a
+// block barrier between them): the step's row, contraction and column runs only.
+struct TinyStep {
+  int32_t a, b, c;         // bookkeeping slots (b = -1: constant 1)
+  int32_t nrow, nk, nn;
+  int64_t off_a, off_b, off_c;
+  int64_t R, K, N;
+  Run row[kMaxRuns];
+  Run kr[kMaxRuns];
+  Run nr[kMaxRuns];
+};
+// Consecutive small steps [first, first + count) run as one launch.
+struct Segment {
+  int32_t first, count;
+  int32_t tiny0;           // index of the first step's TinyStep record
+};
+constexpr int64_t kTinyOuts = 4096;       // outputs per step at most
+constexpr int64_t kTinyWork = 1 << 15;    // complex multiply-adds per step at most
+constexpr int64_t kTinyK = 2048;          // contracted extent (offset table in shared memory)
+
 struct TailStep {
   int32_t step;
   int32_t meta_a, meta_b;            // bookkeeping slots of the (possibly converted) operands
@@ -242,6 +262,9 @@ struct Plan {
   // bulk tensors they read are up-converted there first
   int32_t tail_first = 0;
   std::vector<ConvRec> conv;
+  std::vector<Segment> segments;     // runs of small steps launched as one sequence kernel
+  std::vector<TinyStep> tiny;        // their records (in the program at off_tiny)
+  uint64_t off_tiny = 0;
   std::vector<TailStep> tail;        // one per step >= tail_first
   int64_t tail_elems = 0;            // complex128 elements of the tail region
   int64_t final_tail_off = 0;        // final tensor's offset in the tail region

@@ -1048,6 +1048,54 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
     p.n_meta = n_tens + (int32_t)p.conv.size();
   }
 
+  // ---- segments: maximal runs (>= 2) of consecutive small row-kernel steps
+  p.segments.clear();
+  p.tiny.clear();
+  {
+    auto small = [&](const Step& st) {
+      return st.kernel == KROWS && st.R * st.N <= kTinyOuts && st.K <= kTinyK &&
+             st.R * st.N * st.K <= kTinyWork;
+    };
+    int32_t s0 = 0;
+    while (s0 < n_steps) {
+      if (!small(p.steps[s0])) {
+        ++s0;
+        continue;
+      }
+      int32_t s1 = s0;
+      while (s1 < n_steps && small(p.steps[s1])) ++s1;
+      if (s1 - s0 >= 2) {
+        Segment sg;
+        sg.first = s0;
+        sg.count = s1 - s0;
+        sg.tiny0 = (int32_t)p.tiny.size();
+        for (int32_t i = s0; i < s1; ++i) {
+          const Step& st = p.steps[i];
+          TinyStep ts;
+          std::memset(&ts, 0, sizeof(ts));
+          ts.a = st.a;
+          ts.b = st.b;
+          ts.c = st.c;
+          ts.nrow = st.nrow;
+          ts.nk = st.nk;
+          ts.nn = st.nn;
+          ts.off_a = st.off_a;
+          ts.off_b = st.off_b;
+          ts.off_c = st.off_c;
+          ts.R = st.R;
+          ts.K = st.K;
+          ts.N = st.N;
+          std::memcpy(ts.row, st.row, sizeof(ts.row));
+          std::memcpy(ts.kr, st.kr, sizeof(ts.kr));
+          std::memcpy(ts.nr, st.nr, sizeof(ts.nr));
+          p.tiny.push_back(ts);
+        }
+        p.segments.push_back(sg);
+      }
+      s0 = s1;
+    }
+  }
+
   // ---- workspace layout
   uint64_t off = 0;
   p.off_recipe = off;
@@ -1056,6 +1104,8 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   off = align256(off + sizeof(Slot) * std::max<size_t>(1, p.slots.size()));
   p.off_conv = off;
   off = align256(off + sizeof(ConvRec) * std::max<size_t>(1, p.conv.size()));
+  p.off_tiny = off;
+  off = align256(off + sizeof(TinyStep) * p.tiny.size());
   p.off_meta = off;
   off = align256(off + 16ull * p.n_meta);
   p.off_counter = off;
@@ -1073,6 +1123,8 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
     std::memcpy(p.program.data() + p.off_slots, p.slots.data(), sizeof(Slot) * p.slots.size());
   if (!p.conv.empty())
     std::memcpy(p.program.data() + p.off_conv, p.conv.data(), sizeof(ConvRec) * p.conv.size());
+  if (!p.tiny.empty())
+    std::memcpy(p.program.data() + p.off_tiny, p.tiny.data(), sizeof(TinyStep) * p.tiny.size());
   if (grad && !make_grad_program(p, opts.checkpoint_stride, opts.flags, err)) return false;
   return true;
 }

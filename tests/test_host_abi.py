@@ -133,7 +133,9 @@ def test_plan_stats_and_steps(ctx):
     assert st["n_steps"] == len(steps)
     assert abs(st["cmacs"] - sum(s["R"] * s["K"] * s["N"] for s in steps)) < 1e-6 * st["cmacs"]
     assert st["workspace_c128"] > st["workspace_c64"]
-    assert p.launches() == 1 + st["n_slices"] * (2 + st["n_steps"])
+    fused = st["n_segment_steps"] - st["n_segments"]      # runs of small steps: one launch
+    assert st["n_segments"] > 0
+    assert p.launches() == 1 + st["n_slices"] * (2 + st["n_steps"] - fused)
 
 
 def test_jones_normalisation_host(ctx):
