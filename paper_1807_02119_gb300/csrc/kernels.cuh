@@ -426,15 +426,15 @@ __global__ void __launch_bounds__(256) k_outs(const Step s, Cx<R>* arena, Meta* 
   Cx<R>* C = arena + s.off_c;
   const bool hasB = s.b >= 0;
   const int K = (int)s.K;
-  const unsigned long long R_ = (unsigned long long)s.R;
-  const unsigned long long total = R_ * (unsigned long long)s.N;
+  // R N <= 2^31 (the tensor size limit): 32-bit index arithmetic
+  const unsigned R_ = (unsigned)s.R;
+  const unsigned total = (unsigned)(s.R * s.N);
   S vmax = 0;
-  for (unsigned long long o = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; o < total;
-       o += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long n = o / R_, r = o - n * R_;
+  for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < total; o += gridDim.x * blockDim.x) {
+    const unsigned n = o / R_, r = o - n * R_;
     long long oa, ob, nb, dummy;
-    split_runs(r, s.row, s.nrow, oa, ob);
-    split_runs(n, s.nr, s.nn, dummy, nb);
+    split_runs32(r, s.row, s.nrow, oa, ob);
+    split_runs32(n, s.nr, s.nn, dummy, nb);
     const Cx<R>* Ar = A + oa;
     const Cx<R>* Bn = B + ob + nb;
     Acc<R> acc;
@@ -472,14 +472,14 @@ __global__ void __launch_bounds__(256) k_seg(const TinyStep* __restrict__ steps,
     const Cx<R>* A = arena + s.off_a;
     const Cx<R>* B = arena + s.off_b;
     Cx<R>* C = arena + s.off_c;
-    const long long outs = s.R * s.N;
+    const unsigned outs = (unsigned)(s.R * s.N), R_ = (unsigned)s.R;
     const int K = (int)s.K;
     S vmax = 0;
-    for (long long o = threadIdx.x; o < outs; o += blockDim.x) {
-      const long long r = o % s.R, nn = o / s.R;
+    for (unsigned o = threadIdx.x; o < outs; o += blockDim.x) {
+      const unsigned nn = o / R_, r = o - nn * R_;
       long long oa, ob, d, nb = 0;
-      split_runs((unsigned long long)r, s.row, s.nrow, oa, ob);
-      if (hasB) split_runs((unsigned long long)nn, s.nr, s.nn, d, nb);
+      split_runs32(r, s.row, s.nrow, oa, ob);
+      if (hasB) split_runs32(nn, s.nr, s.nn, d, nb);
       Acc<R> acc;
       if (hasB) {
         for (int k = 0; k < K; ++k) acc.mac(ldc(A + oa + kA[k]), ldc(B + ob + nb + kB[k]));
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(256) k_splitk(const Step s, Cx<R>* arena, Meta
   double are = 0, aim = 0;
   for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     long long ka, kb;
-    split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
+    split_runs32((unsigned)k, s.kr, s.nk, ka, kb);  // K <= 2^31: 32-bit digits
     const Cx<R> av = ld(A + oa + ka);
     const double xr = to_double(av.re), xi = to_double(av.im);
     if (s.b >= 0) {
