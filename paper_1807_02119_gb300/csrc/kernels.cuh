@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 #include "pk_internal.h"
 
@@ -693,19 +694,37 @@ __global__ void __launch_bounds__(256) k_splitk(const Step s, Cx<R>* arena, Meta
   const Cx<R>* A = arena + s.off_a;
   const Cx<R>* B = arena + s.off_b + ob + nb;
   double are = 0, aim = 0;
-  for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    long long ka, kb;
-    split_runs32((unsigned)k, s.kr, s.nk, ka, kb);  // K <= 2^31: 32-bit digits
-    const Cx<R> av = ld(A + oa + ka);
-    const double xr = to_double(av.re), xi = to_double(av.im);
-    if (s.b >= 0) {
-      const Cx<R> bv = ld(B + kb);
-      const double yr = to_double(bv.re), yi = to_double(bv.im);
-      are += xr * yr - xi * yi;
-      aim += xr * yi + xi * yr;
-    } else {
-      are += xr;
-      aim += xi;
+  if constexpr (std::is_same<R, ff>::value) {
+    // float-float products and sums on the FP32 units (FP64 runs at a small fraction of
+    // their rate on this GPU); each thread's partial goes to double for the reduction
+    Acc<ff> acc;
+    for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      long long ka, kb;
+      split_runs32((unsigned)k, s.kr, s.nk, ka, kb);  // K <= 2^31: 32-bit digits
+      const Cx<ff> av = ld(A + oa + ka);
+      if (s.b >= 0)
+        acc.mac(av, ld(B + kb));
+      else
+        acc.add(av);
+    }
+    const Cx<ff> t = acc.get(1.0f);
+    are = to_double(t.re);
+    aim = to_double(t.im);
+  } else {
+    for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      long long ka, kb;
+      split_runs32((unsigned)k, s.kr, s.nk, ka, kb);  // K <= 2^31: 32-bit digits
+      const Cx<R> av = ld(A + oa + ka);
+      const double xr = to_double(av.re), xi = to_double(av.im);
+      if (s.b >= 0) {
+        const Cx<R> bv = ld(B + kb);
+        const double yr = to_double(bv.re), yi = to_double(bv.im);
+        are += xr * yr - xi * yi;
+        aim += xr * yi + xi * yr;
+      } else {
+        are += xr;
+        aim += xi;
+      }
     }
   }
   __shared__ double rr[32], ri[32];
