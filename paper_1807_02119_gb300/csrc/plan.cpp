@@ -558,12 +558,45 @@ bool slice_indices(std::vector<std::vector<int32_t>>& sets, int32_t n_idx, int32
   }
 }
 
-// Complex multiply-adds of a contraction sequence over index sets `sets` (one slice).
+// Estimated cost of a contraction sequence over index sets `sets` (one slice), in units of
+// complex multiply-adds on the CUDA cores: a step shaped for the GEMM kernels (M >= 64,
+// N >= 32, K >= 16 in its GEMM view) is weighted kGemmWeight (the tensor-core GEMM of the
+// split precision does a multiply-add for a fraction of a row kernel's cost), and every
+// output costs kOutWeight multiply-adds (its store and normalisation).
+constexpr double kGemmWeight = 0.15, kOutWeight = 4.0;
 double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& sets, int32_t q) {
   static const std::vector<int32_t> none;
+  const size_t n_init = sets.size() - seq.pairs.size();
   double c = 0;
-  for (const auto& pr : seq.pairs)
-    c += std::pow((double)q, (double)union_size(sets[pr.first], pr.second >= 0 ? sets[pr.second] : none));
+  for (size_t i = 0; i < seq.pairs.size(); ++i) {
+    const auto& pr = seq.pairs[i];
+    const auto& sa0 = sets[pr.first];
+    const auto& sb0 = pr.second >= 0 ? sets[pr.second] : none;
+    const auto& sc = sets[n_init + i];
+    const bool swap = sb0.size() > sa0.size();
+    const auto& sa = swap ? sb0 : sa0;
+    const auto& sb = swap ? sa0 : sb0;
+    auto has = [](const std::vector<int32_t>& v, int32_t x) { return std::binary_search(v.begin(), v.end(), x); };
+    int m = 0, n = 0, k = 0;
+    for (int32_t x : sa) {
+      if (has(sc, x)) {
+        if (!has(sb, x)) ++m;
+      } else {
+        ++k;
+      }
+    }
+    for (int32_t x : sb)
+      if (!has(sa, x)) {
+        if (has(sc, x))
+          ++n;
+        else
+          ++k;
+      }
+    const double macs = std::pow((double)q, (double)union_size(sa, sb));
+    const bool gemm = pr.second >= 0 && std::pow((double)q, m) >= 64 && std::pow((double)q, n) >= 32 &&
+                      std::pow((double)q, k) >= 16;
+    c += macs * (gemm ? kGemmWeight : 1.0) + kOutWeight * std::pow((double)q, (double)sc.size());
+  }
   return c;
 }
 
