@@ -185,18 +185,30 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k, int kcores) {
 
 // S digits of the float-float value (h + l) 2^-e (|value| <= 1): d_i = nearest integer of
 // the running remainder times 2^(7+8i); the remainder is carried exactly as a float pair.
+// sc1 sc2 = 2^(7 - e), the row's scale as two exact powers of two (so that any exponent
+// the stored values can have is covered).  The remainder r = yh - d_i is exact and a
+// multiple of ulp(yh), while |yl| <= ulp(yh) / 2, so |r| >= |yl| unless r = 0 and the fast
+// two-sum (Dekker) is exact; it keeps (yh, yl) normalised for the next digit.
 template <int S>
-__device__ __forceinline__ void digits(float h, float l, int e, __nv_bfloat16* d) {
-  float yh = ldexpf(h, 7 - e), yl = ldexpf(l, 7 - e);
+__device__ __forceinline__ void digits(float h, float l, float sc1, float sc2, __nv_bfloat16* d) {
+  float yh = (h * sc1) * sc2, yl = (l * sc1) * sc2;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
     const float di = rintf(yh);
     d[i] = __float2bfloat16_rn(di);
-    float s, err;
-    two_sum(__fsub_rn(yh, di), yl, s, err);
-    yh = s * 256.0f;
+    const float r = __fsub_rn(yh, di);
+    const float sum = __fadd_rn(r, yl);
+    const float err = __fsub_rn(yl, __fsub_rn(sum, r));
+    yh = sum * 256.0f;
     yl = err * 256.0f;
   }
+}
+
+// 2^(7 - e) as a product of two exact floats (each exponent within [-126, 127]).
+__device__ __forceinline__ void digit_scale(int e, float& sc1, float& sc2) {
+  const int x = 7 - e, x1 = x / 2, x2 = x - x1;
+  sc1 = __int_as_float((max(-126, min(127, x1)) + 127) << 23);
+  sc2 = __int_as_float((max(-126, min(127, x2)) + 127) << 23);
 }
 
 }  // namespace tc
@@ -247,13 +259,15 @@ __device__ __forceinline__ void convert_chunk(const Step& s, const Cx<ff>* base,
   constexpr int kRows = IS_A ? kMc : kNc;
   for (int idx = threadIdx.x; idx < kRows * (kKc / 4); idx += blockDim.x) {
     const int r = idx % kRows, k0 = 4 * (idx / kRows);
+    float sc1, sc2;
+    digit_scale(ex[r], sc1, sc2);
     __nv_bfloat16 dr[4][S], di[4][S];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       Cx<ff> v{{0.f, 0.f}, {0.f, 0.f}};
       if (ro[r] >= 0 && kx[k0 + u] >= 0) v = ld(base + ro[r] + kx[k0 + u]);
-      digits<S>(v.re.hi, v.re.lo, ex[r], dr[u]);
-      digits<S>(v.im.hi, v.im.lo, ex[r], di[u]);
+      digits<S>(v.re.hi, v.re.lo, sc1, sc2, dr[u]);
+      digits<S>(v.im.hi, v.im.lo, sc1, sc2, di[u]);
     }
 #pragma unroll
     for (int i = 0; i < S; ++i) {

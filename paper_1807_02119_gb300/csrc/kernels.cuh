@@ -351,10 +351,10 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
   long long* kA = sm;
   long long* kB = sm + s.K;
   long long* nB = sm + 2 * s.K;
-  for (long long k = threadIdx.x; k < s.K; k += blockDim.x) split_runs(k, s.kr, s.nk, kA[k], kB[k]);
+  for (long long k = threadIdx.x; k < s.K; k += blockDim.x) split_runs32((unsigned)k, s.kr, s.nk, kA[k], kB[k]);
   for (long long n = threadIdx.x; n < s.N; n += blockDim.x) {
     long long dummy;
-    split_runs(n, s.nr, s.nn, dummy, nB[n]);
+    split_runs32((unsigned)n, s.nr, s.nn, dummy, nB[n]);
   }
   const S scale = step_scale<S>(s, meta, blockIdx.x == 0 && threadIdx.x == 0);
   __syncthreads();
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(256) k_outs(const Step s, Cx<R>* arena, Meta* 
   extern __shared__ long long sm[];
   long long* kA = sm;
   long long* kB = sm + s.K;
-  for (long long k = threadIdx.x; k < s.K; k += blockDim.x) split_runs(k, s.kr, s.nk, kA[k], kB[k]);
+  for (long long k = threadIdx.x; k < s.K; k += blockDim.x) split_runs32((unsigned)k, s.kr, s.nk, kA[k], kB[k]);
   const S scale = step_scale<S>(s, meta, blockIdx.x == 0 && threadIdx.x == 0);
   __syncthreads();
   const Cx<R>* A = arena + s.off_a;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(256) k_seg(const TinyStep* __restrict__ steps,
     const int eb = hasB ? bin_exp(bits_to_val<S>(meta[s.b].maxbits)) : 0;
     const long long exp_c = meta[s.a].exp + (hasB ? meta[s.b].exp : 0) + ea + eb;
     const S scale = (S)ldexp(1.0, -(ea + eb));
-    for (long long k = threadIdx.x; k < s.K; k += blockDim.x) split_runs(k, s.kr, s.nk, kA[k], kB[k]);
+    for (long long k = threadIdx.x; k < s.K; k += blockDim.x) split_runs32((unsigned)k, s.kr, s.nk, kA[k], kB[k]);
     __syncthreads();
     const Cx<R>* A = arena + s.off_a;
     const Cx<R>* B = arena + s.off_b;
