@@ -571,6 +571,19 @@ def main():
                  "share_of_pass": rk["ms"] / sum(v["ms"] for v in prof.values()),
                  "flops_count": "8 real flops per complex multiply-add"})
 
+    roof_tc = None
+    if prof.get("gemm_tc", {}).get("ms", 0) > 0:  # the tensor-core GEMM class on its own roofline
+        t = prof["gemm_tc"]
+        ach_tc = 8.0 * t["cmacs"] / (t["ms"] / 1e3) / 1e12
+        peak_tc = pk_["bf16_tflops"] / TC_PAIRS
+        roof_tc = {"bound": "tensor", "achieved": ach_tc, "peak": peak_tc, "unit": "TFLOP/s",
+                   "frac": ach_tc / peak_tc, "traffic": None,
+                   "peak_source": (f"measured dense BF16 {pk_['bf16_tflops']} TFLOP/s "
+                                   f"(MEASURED_PEAKS.json) / {TC_PAIRS} digit-pair products"),
+                   "kernel": knames["gemm_tc"] + ", digit conversion included",
+                   "launches_per_pass": t["launches"], "ms_per_pass": t["ms"],
+                   "share_of_pass": t["ms"] / sum(v["ms"] for v in prof.values())}
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         log("cpu baseline")
@@ -590,7 +603,7 @@ def main():
                           "l2": "flushed between steps (512 MB write)",
                           "plan_seconds": plan_s, "complex_macs_per_step": tot_cmacs,
                           "complex_tflops": 8 * tot_cmacs / (step_ms / 1e3) / 1e12},
-               "roofline": roof, "cpu_baseline": cpu,
+               "roofline": roof, "roofline_tc": roof_tc, "cpu_baseline": cpu,
                "e2e": {"value": e2e_val, "unit": "knots/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": clk, "kernel_classes": prof,
