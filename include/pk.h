@@ -68,8 +68,13 @@ typedef enum {
   PK_ORDER_GREEDY_SPIN = 2,  /* same greedy on the network whose COPY tensors are kept as
                                 shared spin indices (clause matrices only)                  */
   PK_ORDER_ELIM_SPIN = 3,    /* spin network, order from min-degree spin elimination        */
-  PK_ORDER_PARTITION = 4,    /* spin network, recursive-bisection separator order (not yet
-                                built: falls back to PK_ORDER_ELIM_SPIN)                     */
+  PK_ORDER_PARTITION = 4,    /* spin network, nested dissection: the tensors are bisected
+                                recursively (level-structure split of a breadth-first order
+                                from a pseudo-peripheral tensor, then single moves that
+                                shrink the separator); each half's spins are eliminated
+                                before the separator's; best of pk_plan_opts.restarts seeds.
+                                Not among AUTO's candidates (min-fill is far cheaper on
+                                grid-walk knots)                                             */
   PK_ORDER_FILL_SPIN = 5     /* spin network, min-fill elimination with randomised ties,
                                 best of pk_plan_opts.restarts restarts                       */
 } pk_order;

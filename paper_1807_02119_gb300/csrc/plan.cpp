@@ -513,12 +513,181 @@ std::vector<int32_t> min_fill_order(const Network& net, uint64_t seed) {
   return order;
 }
 
+// Separator order (Sec. III "partition" orders): recursive bisection of the network's
+// tensors.  A group is split in two halves that share few indices (spins): a half grown
+// breadth-first over shared indices from a seeded start, then single moves that lower the
+// number of indices held on both sides while each side keeps at least 40% of the group
+// (Kernighan-Lin style).  The bisections give a nested-dissection elimination order of the
+// spins, contracted by the same machinery as the other elimination orders.
+struct Bisection {
+  const std::vector<std::vector<int32_t>>& sets;  // initial tensors' index sets
+  std::vector<std::vector<int32_t>> occ;          // index -> initial tensors holding it
+  uint64_t state;
+  std::vector<int32_t> mark, side;
+  std::vector<int32_t> c0, c1;                    // per index: holders on side 0 / 1
+  Bisection(const std::vector<std::vector<int32_t>>& s, int32_t n_idx, uint64_t seed)
+      : sets(s), occ(n_idx), state(seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull),
+        mark(s.size(), -1), side(s.size(), 0), c0(n_idx, 0), c1(n_idx, 0) {
+    for (int32_t t = 0; t < (int32_t)s.size(); ++t)
+      for (int32_t x : s[t]) occ[x].push_back(t);
+  }
+  uint64_t next() {  // SplitMix64 step
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  void split(const std::vector<int32_t>& group, int32_t stamp, std::vector<int32_t>& g0,
+             std::vector<int32_t>& g1) {
+    const int32_t n = (int32_t)group.size();
+    for (int32_t t : group) {
+      mark[t] = stamp;
+      side[t] = 0;
+    }
+    // breadth-first order over shared indices from a pseudo-peripheral tensor (the last
+    // one reached by a search from a random start; further starts if a component runs
+    // out), then the prefix of that order with the fewest shared indices among the
+    // prefixes holding 40..60% of the group becomes side 1
+    auto bfs = [&](int32_t start, std::vector<int32_t>& out) {
+      std::vector<char> seen(sets.size(), 0);
+      out.clear();
+      int32_t st = start;
+      while ((int32_t)out.size() < n) {
+        if (seen[st]) {
+          for (int32_t t : group)
+            if (!seen[t]) {
+              st = t;
+              break;
+            }
+        }
+        seen[st] = 1;
+        size_t h = out.size();
+        out.push_back(st);
+        for (; h < out.size(); ++h)
+          for (int32_t x : sets[out[h]])
+            for (int32_t u : occ[x])
+              if (mark[u] == stamp && !seen[u]) {
+                seen[u] = 1;
+                out.push_back(u);
+              }
+      }
+    };
+    std::vector<int32_t> order0, order1;
+    bfs(group[next() % n], order0);
+    bfs(order0.back(), order1);
+    for (int32_t t : group)
+      for (int32_t x : sets[t]) c1[x]++;  // c1: holders in the group
+    int32_t cut = 0, best = -1, best_cut = 0;
+    const int32_t lo = std::max<int32_t>(1, (n * 2) / 5), hi = std::max<int32_t>(lo, (n * 3) / 5);
+    for (int32_t i = 0; i < n; ++i) {
+      for (int32_t x : sets[order1[i]]) {
+        const bool was = c0[x] > 0 && c0[x] < c1[x];
+        c0[x]++;
+        const bool now = c0[x] < c1[x];
+        cut += (now ? 1 : 0) - (was ? 1 : 0);
+      }
+      if (i + 1 >= lo && i + 1 <= hi && (best < 0 || cut < best_cut)) {
+        best = i + 1;
+        best_cut = cut;
+      }
+    }
+    for (int32_t t : group)
+      for (int32_t x : sets[t]) c0[x] = c1[x] = 0;
+    int32_t taken = best;
+    for (int32_t i = 0; i < n; ++i) side[order1[i]] = i < best ? 1 : 0;
+    // refinement: move single tensors while that shrinks the number of shared indices
+    for (int32_t t : group)
+      for (int32_t x : sets[t]) (side[t] ? c1 : c0)[x]++;
+    int32_t size1 = taken;
+    const int32_t min_side = std::max<int32_t>(1, (n * 2) / 5);
+    std::vector<int32_t> ord(group);
+    for (int pass = 0; pass < 8; ++pass) {
+      for (int32_t i = n - 1; i > 0; --i) std::swap(ord[i], ord[next() % (i + 1)]);
+      bool moved = false;
+      for (int32_t t : ord) {
+        const int32_t sd = side[t];
+        if ((sd ? size1 : n - size1) - 1 < min_side) continue;
+        int32_t gain = 0;
+        for (int32_t x : sets[t]) {
+          const int32_t cs = sd ? c1[x] : c0[x], co = sd ? c0[x] : c1[x];
+          gain += (co > 0 ? 1 : 0) - (cs > 1 ? 1 : 0);
+        }
+        if (gain <= 0) continue;
+        for (int32_t x : sets[t]) {
+          (sd ? c1 : c0)[x]--;
+          (sd ? c0 : c1)[x]++;
+        }
+        side[t] = 1 - sd;
+        size1 += sd ? -1 : 1;
+        moved = true;
+      }
+      if (!moved) break;
+    }
+    for (int32_t t : group)
+      for (int32_t x : sets[t]) (side[t] ? c1 : c0)[x] = 0;
+    g0.clear();
+    g1.clear();
+    for (int32_t t : group) (side[t] ? g1 : g0).push_back(t);
+    if (g0.empty() || g1.empty()) {  // degenerate: halve by position
+      g0.assign(group.begin(), group.begin() + n / 2);
+      g1.assign(group.begin() + n / 2, group.end());
+    }
+  }
+};
+
+// Nested dissection: the spins of a group are eliminated as those held only by the first
+// half (recursively), then those held only by the second half (recursively), then the
+// separator (spins held by both halves) last; spins held by tensors outside the group
+// belong to an enclosing separator and are ordered there.
+void dissect(Bisection& bi, const std::vector<int32_t>& group, const std::vector<int32_t>& spins,
+             int32_t& stamp, std::vector<char>& side_of, std::vector<int32_t>& order) {
+  if (group.size() <= 2 || spins.size() <= 2) {
+    order.insert(order.end(), spins.begin(), spins.end());
+    return;
+  }
+  std::vector<int32_t> g0, g1;
+  bi.split(group, stamp++, g0, g1);
+  for (int32_t x : spins) side_of[x] = 0;
+  for (int32_t t : g0)
+    for (int32_t x : bi.sets[t]) side_of[x] |= 1;
+  for (int32_t t : g1)
+    for (int32_t x : bi.sets[t]) side_of[x] |= 2;
+  std::vector<int32_t> s0, s1, sep;
+  for (int32_t x : spins) (side_of[x] == 1 ? s0 : side_of[x] == 2 ? s1 : sep).push_back(x);
+  dissect(bi, g0, s0, stamp, side_of, order);
+  dissect(bi, g1, s1, stamp, side_of, order);
+  order.insert(order.end(), sep.begin(), sep.end());
+}
+
+std::vector<int32_t> dissection_order(const Network& net, uint64_t seed) {
+  std::vector<std::vector<int32_t>> sets;
+  for (const auto& t : net.t) {
+    std::vector<int32_t> d = t.dims;
+    std::sort(d.begin(), d.end());
+    d.erase(std::unique(d.begin(), d.end()), d.end());
+    sets.push_back(d);
+  }
+  Bisection bi(sets, net.n_idx, seed);
+  std::vector<int32_t> all(sets.size()), spins;
+  std::iota(all.begin(), all.end(), 0);
+  std::vector<char> held(net.n_idx, 0), side_of(net.n_idx, 0);
+  for (const auto& d : sets)
+    for (int32_t x : d) held[x] = 1;
+  for (int32_t x = 0; x < net.n_idx; ++x)
+    if (held[x]) spins.push_back(x);
+  std::vector<int32_t> order;
+  int32_t stamp = 0;
+  dissect(bi, all, spins, stamp, side_of, order);
+  return order;
+}
+
 bool run_order(const Network& net, int32_t order, Greedy& g, uint64_t seed = 0) {
   g = Greedy();
   g.init(net);
-  if (order == PK_ORDER_ELIM_SPIN || order == PK_ORDER_FILL_SPIN) {
-    std::vector<int32_t> ord =
-        order == PK_ORDER_ELIM_SPIN ? min_degree_order(net) : min_fill_order(net, seed);
+  if (order == PK_ORDER_ELIM_SPIN || order == PK_ORDER_FILL_SPIN || order == PK_ORDER_PARTITION) {
+    std::vector<int32_t> ord = order == PK_ORDER_ELIM_SPIN ? min_degree_order(net)
+                               : order == PK_ORDER_FILL_SPIN ? min_fill_order(net, seed)
+                                                             : dissection_order(net, seed);
     for (int32_t v : ord) {
       int32_t a, b;
       while (g.cnt[v] >= 2 && g.best_pair(v, a, b)) g.contract(a, b);
@@ -823,7 +992,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   } else if (opts.order == PK_ORDER_FILL_SPIN) {
     for (int32_t r = 0; r < restarts; ++r) cands.push_back({PK_ORDER_FILL_SPIN, (uint64_t)r});
   } else if (opts.order == PK_ORDER_PARTITION) {
-    cands = {{PK_ORDER_ELIM_SPIN, 0}};
+    for (int32_t r = 0; r < restarts; ++r) cands.push_back({PK_ORDER_PARTITION, (uint64_t)r});
   } else {
     err = "unknown order";
     return false;

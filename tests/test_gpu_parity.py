@@ -76,7 +76,7 @@ def kg_eval(poly, q):
     return Zt(q).eval_laurent(poly)
 
 
-@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "elim_spin"])
+@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "elim_spin", "fill_spin", "partition"])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_random_knots_vs_oracle(ctx, order, prec):
     worst = 0.0
@@ -200,7 +200,7 @@ def test_forced_rows_kernel(ctx):
 SPLIT_TOL = 1e-6   # split FP32 (float-float arithmetic, complex128 tail) target
 
 
-@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "elim_spin"])
+@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "elim_spin", "fill_spin", "partition"])
 def test_split_precision_vs_oracle(ctx, order):
     worst = 0.0
     for s in range(10):

@@ -99,7 +99,8 @@ def _z_oracle(pd, q):
     return oracle.z_complex(g.n_v, g.edges, q)
 
 
-@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "elim_spin", "auto"])
+@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "elim_spin", "fill_spin", "partition",
+                                   "auto"])
 def test_plan_replay_matches_oracle(ctx, order):
     for pd in _pds()[:18]:
         k = pk.Knot.from_pd(ctx, pd)
