@@ -138,8 +138,8 @@ struct Segment {
   int32_t first, count;
   int32_t tiny0;           // index of the first step's TinyStep record
 };
-constexpr int64_t kTinyOuts = 4096;       // outputs per step at most
-constexpr int64_t kTinyWork = 1 << 15;    // complex multiply-adds per step at most
+constexpr int64_t kTinyOuts = 2048;       // outputs per step at most
+constexpr int64_t kTinyWork = 1 << 12;    // complex multiply-adds per step at most
 constexpr int64_t kTinyK = 2048;          // contracted extent (offset table in shared memory)
 
 struct TailStep {
