@@ -23,13 +23,13 @@
 // Data movement, three kernels per step:
 //  * k_digits<S, true> / k_digits<S, false>: one CTA per 64-row block of A (64-column
 //    block of B) finds the block's exponents over all of K, then converts it chunk by
-//    chunk (kKc = 8 complex k) into S digit slices laid out exactly as the MMA reads them from
+//    chunk (16 complex k) into S digit slices laid out exactly as the MMA reads them from
 //    shared memory (the canonical K-major layout without swizzle: 8-row x 16-byte core
 //    matrices) and stores each chunk contiguously in the workspace.  The operands are
 //    gathered through the step's stride runs (arbitrary index permutations, which a TMA
 //    tensor map cannot express); each element is read and converted once.
 //  * k_gemm_tc: warp 0 streams the chunks of its (batch, row block, column block) into a
-//    4-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion by
+//    3-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion by
 //    mbarrier transaction count); warp 1 issues the S (S+1)/2 digit-pair MMAs per K step
 //    and releases each stage with tcgen05.commit; eight epilogue warps flush the S level
 //    accumulators from TMEM into float-float registers every kFlush chunks and finally
@@ -51,7 +51,7 @@ constexpr int kKr = 2 * kKc;     // MMA K per chunk (real: re half, im half)
 constexpr int kKcores = kKr / 8; // 16-byte K core columns per row
 constexpr int kABytes = kM * kKr * 2;   // one digit slice of an A chunk (BF16): 8 KB
 constexpr int kBBytes = kN * kKr * 2;   // one digit slice of a B chunk: 4 KB
-constexpr int kStages = 4;
+constexpr int kStages = 2;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);   // producer, MMA issuer, epilogue
 constexpr int kConvThreads = 256;
@@ -237,7 +237,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 // Gather + digit conversion of one chunk of an operand block: 64 tile rows (complex rows
-// of A, or complex columns of B) x kKc complex k.  For A every complex entry fills rows
+// of A, or complex columns of B) x 16 complex k.  For A every complex entry fills rows
 // 2r (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).
 __device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c,
                                        __nv_bfloat16 d) {
@@ -248,7 +248,7 @@ __device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bf
 }
 
 // Gather + digit conversion of one chunk of an operand block: kRows tile rows (complex
-// rows of A, or complex columns of B) x kKc complex k, one thread per (row, 4 consecutive
+// rows of A, or complex columns of B) x 16 complex k, one thread per (row, 4 consecutive
 // k), written as 8-byte groups of four BF16 digits.  For A every complex entry fills rows
 // 2r (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).
 template <int S, bool IS_A>
@@ -291,7 +291,7 @@ __device__ __forceinline__ void convert_chunk(const Step& s, const Cx<ff>* base,
 }  // namespace tc
 
 // Digits of the A operand (IS_A) or the B operand of a GEMM step: one CTA per (batch,
-// 64-row block); exponents over all K, then S digit slices per chunk of kKc complex k,
+// 64-row block); exponents over all K, then S digit slices per chunk of 16 complex k,
 // staged in shared memory and stored with 16-byte writes.
 template <int S, bool IS_A>
 __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const Cx<ff>* arena,

@@ -156,10 +156,10 @@ struct TailStep {
 #endif
 
 // GEMM steps of the split precision on the tensor cores: each operand element becomes
-// kTcDigits BF16 digits (exact 8-bit pieces), stored per 64-row block and 8-complex-k
+// kTcDigits BF16 digits (exact 8-bit pieces), stored per 64-row block and 16-complex-k
 // chunk in the workspace after the arena, followed by the blocks' exponents.
 constexpr int kTcDigits = 5;
-constexpr int kTcMc = 64, kTcNc = 48, kTcKc = 8;
+constexpr int kTcMc = 64, kTcNc = 48, kTcKc = 16;
 constexpr long long kTcAChunk = (long long)kTcDigits * (2 * kTcMc) * (2 * kTcKc) * 2;
 constexpr long long kTcBChunk = (long long)kTcDigits * kTcNc * (2 * kTcKc) * 2;
 struct TcScratch {
