@@ -391,11 +391,12 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
   unsigned char* sm = dsm;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K);
+  // column blocks fastest: the CTAs resident at one time share their A row blocks in L2
   long long t = blockIdx.x;
-  const long long tm = t % L.tiles_m;
-  t /= L.tiles_m;
   const long long tn = t % L.tiles_n;
-  const long long bb = t / L.tiles_n;
+  t /= L.tiles_n;
+  const long long tm = t % L.tiles_m;
+  const long long bb = t / L.tiles_m;
 
   if (tid == 0) {
     long long a, b;
@@ -483,16 +484,21 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
           break;
         }
         fence_after();
+        // descriptors of the stage's first A and B slices; a slice or K-step offset is
+        // added to the start-address field (shared addresses < 256 KB: no carry out of it)
         const uint32_t a0 = sm0 + st * Cfg<S>::kStage, b0 = a0 + Cfg<S>::kAChunk;
-#pragma unroll 1
+        const uint64_t da0 = smem_desc(a0, 128, kKcores * 128);
+        const uint64_t db0 = smem_desc(b0, 128, kKcores * 128);
+        const uint32_t acc0 = first ? 0u : 1u;
+#pragma unroll
         for (int lv = 0; lv < S; ++lv)
+#pragma unroll
           for (int i = 0; i <= lv; ++i)
 #pragma unroll
-            for (int kk = 0; kk < kKr / 16; ++kk) {
-              const uint64_t da = smem_desc(a0 + i * kABytes + kk * 256, 128, kKcores * 128);
-              const uint64_t db = smem_desc(b0 + (lv - i) * kBBytes + kk * 256, 128, kKcores * 128);
-              mma_bf16(tmem + lv * kN, da, db, (first && i == 0 && kk == 0) ? 0u : 1u);
-            }
+            for (int kk = 0; kk < kKr / 16; ++kk)
+              mma_bf16(tmem + lv * kN, da0 + (uint64_t)((i * kABytes + kk * 256) >> 4),
+                       db0 + (uint64_t)(((lv - i) * kBBytes + kk * 256) >> 4),
+                       (i == 0 && kk == 0) ? acc0 : 1u);
         commit(smem_u32(&empty[st]));
         if (last) commit(smem_u32(&acc_full));
       }
