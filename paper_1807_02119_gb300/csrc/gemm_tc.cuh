@@ -29,9 +29,11 @@
 //    gathered through the step's stride runs (arbitrary index permutations, which a TMA
 //    tensor map cannot express); each element is read and converted once.
 //  * k_gemm_tc: warp 0 streams the chunks of its (batch, row block, column block) into a
-//    3-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion by
-//    mbarrier transaction count); warp 1 issues the S (S+1)/2 digit-pair MMAs per K step
-//    and releases each stage with tcgen05.commit; eight epilogue warps flush the S level
+//    2-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion by
+//    mbarrier transaction count); warp 1 issues the S (S+1)/2 digit-pair products of a K
+//    step as S MMAs (A digit i against B digits 0 .. S-1-i stacked along N: one issuing
+//    thread cannot keep the tensor pipe busy with N = 48 MMAs) and releases each stage
+//    with tcgen05.commit; eight epilogue warps flush the S level
 //    accumulators from TMEM into float-float registers every kFlush chunks and finally
 //    store C.  Every wait is bounded: on expiry the tile is poisoned with NaN and counted
 //    in pk_tc_timeouts, so a failure shows up as a wrong result, not a hang.
@@ -50,7 +52,7 @@ constexpr int kN = kNc;          // MMA N
 constexpr int kKr = 2 * kKc;     // MMA K per chunk (real: re half, im half)
 constexpr int kKcores = kKr / 8; // 16-byte K core columns per row
 constexpr int kABytes = kM * kKr * 2;   // one digit slice of an A chunk (BF16): 8 KB
-constexpr int kBBytes = kN * kKr * 2;   // one digit slice of a B chunk: 4 KB
+constexpr int kBBytes = kN * kKr * 2;   // one digit slice of a B chunk: 3 KB
 constexpr int kStages = 2;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);   // producer, MMA issuer, epilogue
@@ -63,6 +65,8 @@ struct Cfg {
   static constexpr int kStage = kAChunk + kBChunk;
   static constexpr int kSmem = kStages * kStage;   // two CTAs per SM (16-byte alignment suffices)
   static constexpr int kConvSmem = kAChunk + 1024;                // conversion staging (+ alignment)
+  // one MMA spans the stacked B digits: M = 128 allows N in multiples of 16 up to 256
+  static_assert(kN % 16 == 0 && S * kN <= 256, "stacked B digits exceed one MMA");
   static_assert(S != kTcDigits || (kAChunk == kTcAChunk && kBChunk == kTcBChunk),
                 "chunk sizes must match the host's scratch layout");
   static constexpr int kCols = S * kN <= 32 ? 32 : S * kN <= 64 ? 64 : S * kN <= 128 ? 128
@@ -74,8 +78,10 @@ struct Cfg {
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
 // A and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
 // M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(kM >> 4) << 24);
+constexpr uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kM >> 4) << 24);
+}
 
 // Shared-memory matrix descriptor, K-major without swizzle: start address >> 4 (bits
 // 0-13), leading byte offset >> 4 (bits 16-29: between the two 8-element K core columns
@@ -97,11 +103,12 @@ __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void commit(uint32_t mbar) {
@@ -490,15 +497,17 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
         const uint64_t da0 = smem_desc(a0, 128, kKcores * 128);
         const uint64_t db0 = smem_desc(b0, 128, kKcores * 128);
         const uint32_t acc0 = first ? 0u : 1u;
+        // A digit i meets B digits 0 .. S-1-i in ONE MMA: the B digit slices lie one after
+        // another in shared memory (the same 8-row-group stride), so together they are a
+        // (S - i) N column operand, and its products land on the level accumulators
+        // i .. S-1, which lie one after another in TMEM from column i N.
 #pragma unroll
-        for (int lv = 0; lv < S; ++lv)
+        for (int kk = 0; kk < kKr / 16; ++kk)
 #pragma unroll
-          for (int i = 0; i <= lv; ++i)
-#pragma unroll
-            for (int kk = 0; kk < kKr / 16; ++kk)
-              mma_bf16(tmem + lv * kN, da0 + (uint64_t)((i * kABytes + kk * 256) >> 4),
-                       db0 + (uint64_t)(((lv - i) * kBBytes + kk * 256) >> 4),
-                       (i == 0 && kk == 0) ? acc0 : 1u);
+          for (int i = 0; i < S; ++i)
+            mma_bf16(tmem + i * kN, da0 + (uint64_t)((i * kABytes + kk * 256) >> 4),
+                     db0 + (uint64_t)((kk * 256) >> 4), idesc((S - i) * kN),
+                     (i == 0 && kk == 0) ? acc0 : 1u);
         commit(smem_u32(&empty[st]));
         if (last) commit(smem_u32(&acc_full));
       }
