@@ -21,7 +21,7 @@
 // BF16 K-step of 16 (K' = 2 K).
 //
 // Data movement, three kernels per step:
-//  * k_digits<S, true> / k_digits<S, false>: one CTA per 64-row block of A (64-column
+//  * k_digits<S, true> / k_digits<S, false>: one CTA per 64-row block of A (48-column
 //    block of B) finds the block's exponents over all of K, then converts it chunk by
 //    chunk (16 complex k) into S digit slices laid out exactly as the MMA reads them from
 //    shared memory (the canonical K-major layout without swizzle: 8-row x 16-byte core
@@ -64,7 +64,7 @@ struct Cfg {
   static constexpr int kBChunk = S * kBBytes;
   static constexpr int kStage = kAChunk + kBChunk;
   static constexpr int kSmem = kStages * kStage;   // two CTAs per SM (16-byte alignment suffices)
-  static constexpr int kConvSmem = kAChunk + 1024;                // conversion staging (+ alignment)
+  static constexpr int kConvSmem = 0;   // the digit kernels use static shared memory only
   // one MMA spans the stacked B digits: M = 128 allows N in multiples of 16 up to 256
   static_assert(kN % 16 == 0 && S * kN <= 256, "stacked B digits exceed one MMA");
   static_assert(S != kTcDigits || (kAChunk == kTcAChunk && kBChunk == kTcBChunk),
@@ -243,9 +243,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       : "memory");
 }
 
-// Gather + digit conversion of one chunk of an operand block: 64 tile rows (complex rows
-// of A, or complex columns of B) x 16 complex k.  For A every complex entry fills rows
-// 2r (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).
+// Four BF16 digits as one 8-byte group (k order within a core-matrix row).
 __device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c,
                                        __nv_bfloat16 d) {
   uint2 u;
@@ -254,43 +252,35 @@ __device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bf
   return u;
 }
 
-// Gather + digit conversion of one chunk of an operand block: kRows tile rows (complex
-// rows of A, or complex columns of B) x 16 complex k, one thread per (row, 4 consecutive
-// k), written as 8-byte groups of four BF16 digits.  For A every complex entry fills rows
-// 2r (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).
+// Digit conversion of one item of an operand block: tile row r (a complex row of A, or a
+// complex column of B) x 4 consecutive complex k, written straight into the chunk's digit
+// slices as 8-byte groups of four BF16 digits.  For A every complex entry fills rows 2r
+// (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).  `kl` is the
+// item's first k within its chunk (a multiple of 4).
 template <int S, bool IS_A>
-__device__ __forceinline__ void convert_chunk(const Step& s, const Cx<ff>* base, const long long* ro,
-                                              const int* ex, const long long* kx,
-                                              unsigned char* stage) {
+__device__ __forceinline__ void convert_item(const Cx<ff>* v, int r, int kl, float sc1, float sc2,
+                                             unsigned char* chunk) {
   constexpr int kSlice = IS_A ? kABytes : kBBytes;
-  constexpr int kRows = IS_A ? kMc : kNc;
-  for (int idx = threadIdx.x; idx < kRows * (kKc / 4); idx += blockDim.x) {
-    const int r = idx % kRows, k0 = 4 * (idx / kRows);
-    float sc1, sc2;
-    digit_scale(ex[r], sc1, sc2);
-    __nv_bfloat16 dr[4][S], di[4][S];
+  __nv_bfloat16 dr[4][S], di[4][S];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      Cx<ff> v{{0.f, 0.f}, {0.f, 0.f}};
-      if (ro[r] >= 0 && kx[k0 + u] >= 0) v = ld(base + ro[r] + kx[k0 + u]);
-      digits<S>(v.re.hi, v.re.lo, sc1, sc2, dr[u]);
-      digits<S>(v.im.hi, v.im.lo, sc1, sc2, di[u]);
-    }
+  for (int u = 0; u < 4; ++u) {
+    digits<S>(v[u].re.hi, v[u].re.lo, sc1, sc2, dr[u]);
+    digits<S>(v[u].im.hi, v[u].im.lo, sc1, sc2, di[u]);
+  }
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-      unsigned char* sl = stage + i * kSlice;
-      const uint2 re = pack4(dr[0][i], dr[1][i], dr[2][i], dr[3][i]);
-      const uint2 im = pack4(di[0][i], di[1][i], di[2][i], di[3][i]);
-      if (IS_A) {
-        const uint2 mim = pack4(__hneg(di[0][i]), __hneg(di[1][i]), __hneg(di[2][i]), __hneg(di[3][i]));
-        *(uint2*)(sl + tile_off(2 * r, k0, kKcores)) = re;
-        *(uint2*)(sl + tile_off(2 * r, kKc + k0, kKcores)) = mim;
-        *(uint2*)(sl + tile_off(2 * r + 1, k0, kKcores)) = im;
-        *(uint2*)(sl + tile_off(2 * r + 1, kKc + k0, kKcores)) = re;
-      } else {
-        *(uint2*)(sl + tile_off(r, k0, kKcores)) = re;
-        *(uint2*)(sl + tile_off(r, kKc + k0, kKcores)) = im;
-      }
+  for (int i = 0; i < S; ++i) {
+    unsigned char* sl = chunk + i * kSlice;
+    const uint2 re = pack4(dr[0][i], dr[1][i], dr[2][i], dr[3][i]);
+    const uint2 im = pack4(di[0][i], di[1][i], di[2][i], di[3][i]);
+    if (IS_A) {
+      const uint2 mim = pack4(__hneg(di[0][i]), __hneg(di[1][i]), __hneg(di[2][i]), __hneg(di[3][i]));
+      *(uint2*)(sl + tile_off(2 * r, kl, kKcores)) = re;
+      *(uint2*)(sl + tile_off(2 * r, kKc + kl, kKcores)) = mim;
+      *(uint2*)(sl + tile_off(2 * r + 1, kl, kKcores)) = im;
+      *(uint2*)(sl + tile_off(2 * r + 1, kKc + kl, kKcores)) = re;
+    } else {
+      *(uint2*)(sl + tile_off(r, kl, kKcores)) = re;
+      *(uint2*)(sl + tile_off(r, kKc + kl, kKcores)) = im;
     }
   }
 }
@@ -298,29 +288,34 @@ __device__ __forceinline__ void convert_chunk(const Step& s, const Cx<ff>* base,
 }  // namespace tc
 
 // Digits of the A operand (IS_A) or the B operand of a GEMM step: one CTA per (batch,
-// 64-row block); exponents over all K, then S digit slices per chunk of 16 complex k,
-// staged in shared memory and stored with 16-byte writes.
+// 64-row block).  K is walked in blocks of kConvThreads indices (one index-table entry per
+// thread, one barrier per block): first the rows' exponents over all of K, then the S
+// digit slices of every chunk, stored directly in the workspace.  The thread mapping
+// follows the operand's unit stride: along K (a warp reads 32 x 4 consecutive k of one
+// row) or along the rows (a warp reads 32 consecutive rows).
 template <int S, bool IS_A>
 __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const Cx<ff>* arena,
                                                              unsigned char* scratch) {
   using namespace tc;
   static_assert(S == kTcDigits, "digit scratch laid out for kTcDigits digits");
-  extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ long long ro[64], kx[kKc];
+  constexpr int kRows = IS_A ? kMc : kNc;
+  constexpr int kBlk = kConvThreads;              // k indices per block
+  constexpr int kQuads = kBlk / 4;                // 4-k items per row per block
+  static_assert(kBlk % kKc == 0 && kRows <= 64, "block geometry");
+  __shared__ long long ro[64], kt[kBlk];
   __shared__ long long base;
   __shared__ int ex[64];
   __shared__ float red[kConvThreads];
-  unsigned char* stage = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K);
   const long long tiles = IS_A ? L.tiles_m : L.tiles_n;
   const long long tile = blockIdx.x % tiles, bb = blockIdx.x / tiles;
   const int tid = threadIdx.x;
+  const bool kin = IS_A ? s.a_kinner != 0 : s.b_kinner != 0;
   if (tid == 0) {
     long long a, b, c;
     runs4(bb, s.gb, s.ngb, a, b, c);
     base = IS_A ? a : b;
   }
-  constexpr int kRows = IS_A ? kMc : kNc;
   if (tid < 64) {
     const long long r = tile * kRows + tid;
     long long a, b, c;
@@ -336,47 +331,65 @@ __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const
   }
   __syncthreads();
   const Cx<ff>* src = arena + (IS_A ? s.off_a : s.off_b) + base;
-  // exponents: 4 threads per row, all K
-  float mx = 0;
-  const int r = tid >> 2, sub = tid & 3;
-  for (long long c = 0; c < L.chunks; ++c) {
-    if (tid < kKc) {
-      const long long k = c * kKc + tid;
-      long long ka = -1, kb = -1;
-      if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
-      kx[tid] = IS_A ? ka : kb;
+  const long long kpad = L.chunks * kKc;   // K rounded up to whole chunks
+  auto fill_table = [&](long long kb) {
+    const long long k = kb + tid;
+    long long ka = -1, kb2 = -1;
+    if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb2);
+    kt[tid] = IS_A ? ka : kb2;
+  };
+
+  // ---- exponents: 4 threads per row (rows on consecutive lanes when they are the unit
+  // stride, else the 4 threads of a row on consecutive lanes over consecutive k)
+  const int er = kin ? (tid >> 2) : (tid & 63), es = kin ? (tid & 3) : (tid >> 6);
+  float mx = 0.f;
+  for (long long kb = 0; kb < s.K; kb += kBlk) {
+    __syncthreads();
+    fill_table(kb);
+    __syncthreads();
+    if (er < kRows && ro[er] >= 0) {
+      const long long o = ro[er];
+      const int kn = (int)min((long long)kBlk, s.K - kb);
+#pragma unroll 8
+      for (int k = es; k < kn; k += 4) mx = fmaxf(mx, mag(ld(src + o + kt[k])));
     }
-    __syncthreads();
-    for (int k = sub; k < kKc; k += 4)
-      if (ro[r] >= 0 && kx[k] >= 0) mx = fmaxf(mx, mag(ld(src + ro[r] + kx[k])));
-    __syncthreads();
   }
   red[tid] = mx;
   __syncthreads();
   int* ex_out = (int*)(scratch + (IS_A ? L.ea_off : L.eb_off)) + (bb * tiles + tile) * kRows;
-  if (sub == 0 && r < kRows) {
-    const float v = fmaxf(fmaxf(red[tid], red[tid + 1]), fmaxf(red[tid + 2], red[tid + 3]));
-    ex[r] = bin_exp(v);
-    ex_out[r] = ex[r];
+  if (tid < kRows) {
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v = fmaxf(v, red[kin ? 4 * tid + j : tid + 64 * j]);
+    ex[tid] = bin_exp(v);
+    ex_out[tid] = ex[tid];
   }
-  __syncthreads();
+
+  // ---- digits: items (row, 4 consecutive k), kRows x kQuads per block
   constexpr int kChunkBytes = IS_A ? Cfg<S>::kAChunk : Cfg<S>::kBChunk;
   unsigned char* dst0 = scratch + (IS_A ? L.a_off : L.b_off) +
                         (bb * tiles + tile) * L.chunks * (long long)kChunkBytes;
-  for (long long c = 0; c < L.chunks; ++c) {
-    if (tid < kKc) {
-      const long long k = c * kKc + tid;
-      long long ka = -1, kb = -1;
-      if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
-      kx[tid] = IS_A ? ka : kb;
+  for (long long kb = 0; kb < kpad; kb += kBlk) {
+    __syncthreads();
+    fill_table(kb);
+    __syncthreads();
+    for (int idx = tid; idx < kRows * kQuads; idx += kConvThreads) {
+      const int r = kin ? idx / kQuads : idx % kRows;
+      const int q = kin ? idx % kQuads : idx / kRows;
+      const long long k0 = kb + 4 * q;
+      if (k0 >= kpad) continue;
+      Cx<ff> v[4];
+      const long long o = ro[r];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u] = Cx<ff>{{0.f, 0.f}, {0.f, 0.f}};
+        if (o >= 0 && kt[4 * q + u] >= 0) v[u] = ld(src + o + kt[4 * q + u]);
+      }
+      float sc1, sc2;
+      digit_scale(ex[r], sc1, sc2);
+      convert_item<S, IS_A>(v, r, (int)(k0 % kKc), sc1, sc2,
+                            dst0 + (k0 / kKc) * (long long)kChunkBytes);
     }
-    __syncthreads();
-    convert_chunk<S, IS_A>(s, src, ro, ex, kx, stage);
-    __syncthreads();
-    uint4* d = (uint4*)(dst0 + c * (long long)kChunkBytes);
-    const uint4* sv = (const uint4*)stage;
-    for (int i = tid; i < kChunkBytes / 16; i += kConvThreads) d[i] = sv[i];
-    __syncthreads();
   }
 }
 
