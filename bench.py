@@ -53,6 +53,8 @@ def parse():
                     help="omit the complex64 / complex128 comparison passes")
     ap.add_argument("--qs", default="2,3,5")
     ap.add_argument("--knots", type=int, default=64, help="knots per GPU (64 = the workload)")
+    ap.add_argument("--first", type=int, default=0,
+                    help="index of the first knot taken from the rank's workload (profiling subsets)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle baseline")
     ap.add_argument("--restarts", type=int, default=128,
                     help="min-fill restarts per plan (planning effort; plans are built once, "
@@ -410,7 +412,7 @@ def main():
     import paper_1807_02119_gb300 as pk
 
     qs = tuple(int(x) for x in args.qs.split(","))
-    knots = workload(rank)[:args.knots]
+    knots = workload(rank)[args.first:args.first + args.knots]
     ctx = pk.Context(local)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
@@ -599,7 +601,7 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
                "config": {"workload": "scale: 64 random grid-walk knots per GPU, L=40, 100-400 crossings, "
                                       "random over/under, q in {2,3,5}; 192 (knot, q) evaluations per step",
-                          "order": f"auto per knot (fewest complex multiply-adds, {args.restarts} min-fill restarts)",
+                          "order": f"auto per knot (lowest estimated cost after slicing, {args.restarts} min-fill restarts)",
                           "l2": "flushed between steps (512 MB write)",
                           "plan_seconds": plan_s, "complex_macs_per_step": tot_cmacs,
                           "complex_tflops": 8 * tot_cmacs / (step_ms / 1e3) / 1e12},
