@@ -41,7 +41,7 @@ typedef struct {
 typedef enum {
   PK_OK = 0,
   PK_EINVAL = 1,     /* bad argument: q < 1, malformed PD code, bad sign, NULL pointer */
-  PK_ENOTKNOT = 2,   /* diagram has more than one component (V undefined here)        */
+  PK_ENOTKNOT = 2,   /* kept for compatibility: no longer returned (links get V too)  */
   PK_ENOMEM = 3,     /* host allocation failed or workspace too small                  */
   PK_ETOOWIDE = 4,   /* plan exceeds the slicing limits                                 */
   PK_ECUDA = 5,      /* a CUDA runtime call failed                                      */
@@ -153,6 +153,19 @@ void pk_ctx_destroy(pk_ctx* ctx);
 pk_status pk_knot_from_pd(pk_ctx* ctx, const int32_t* pd, int32_t n, int32_t outer_arc,
                           int32_t outer_side, pk_knot** out);
 
+/* A link diagram (one or more components; Sec. "Conclusions and outlook": Tait graphs,
+ * and so the method, extend to links):
+ * PD code as above but with any labels 0..2n-1 (each occurring twice; c is the arc
+ * leaving through the under-strand, not necessarily a+1), and signs[i] = +1 or -1, the
+ * twist sign of crossing i by the right-hand rule (+1: the over-strand leaves through
+ * arm b, -1: through arm d), which fixes every component's orientation.  The diagram
+ * must be connected (a split diagram has no Tait graph here).  V of a link lies in
+ * Z[t^(1/2)]: it is evaluated with s = exp(Log t / 4), the principal fourth root of the
+ * Potts t(q), in A(q) = (-1)^(w+n_v+1) s^(3w+tau+2n_v+2) (t+1)^-(n_v+1).
+ * Errors: PK_EINVAL (labels, signs, orientation or planarity wrong). */
+pk_status pk_link_from_pd(pk_ctx* ctx, const int32_t* pd, const int32_t* signs, int32_t n,
+                          int32_t outer_arc, int32_t outer_side, pk_knot** out);
+
 /* Signed Tait graph given directly: n_e edges uve[3*e..] = (u, v, eps), eps = +-1,
  * u, v in [0, n_v); writhe w.  Z is defined for any such graph (general PACI
  * instance, Sec. III); V uses tau = sum eps and needs 4 | 3w + tau + 2 n_v + 2. */
@@ -192,8 +205,10 @@ void pk_plan_destroy(pk_plan* p);
 
 /* Full evaluation on the context's stream; blocks until Z and V are on the host.
  * d_workspace: device buffer of at least pk_plan_workspace_bytes bytes, owned by the
- * caller; NULL lets the context allocate (and keep) one.  V is written only for
- * knots (PK_ENOTKNOT otherwise, Z still valid). */
+ * caller; NULL lets the context allocate (and keep) one.  V: the Jones value for knots
+ * and links (see pk_link_from_pd for the branch); PK_EINVAL with Z still valid if the
+ * exponent 3w + tau + 2 n_v + 2 is not a multiple of 4 (knot) or 2 (link), which a
+ * signed graph given by pk_knot_from_signed_graph can violate. */
 pk_status pk_eval(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                   uint64_t workspace_bytes, pk_scaled* Z, pk_scaled* V);
 
@@ -277,7 +292,8 @@ pk_status pk_batch_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
 pk_status pk_batch_workspace_bytes(const pk_batch* b, uint64_t* bytes, uint64_t* upload_bytes);
 pk_status pk_batch_upload(pk_ctx* ctx, pk_batch* b, void* d_workspace, uint64_t workspace_bytes);
 pk_status pk_batch_launch(pk_ctx* ctx, pk_batch* b, void* d_workspace, uint64_t workspace_bytes);
-/* Waits for the stream; Z[i], V[i] for knot i (V[i] = 0 and PK_ENOTKNOT for non-knots). */
+/* Waits for the stream; Z[i], V[i] for knot or link i (V[i] = 0 and PK_EINVAL where the
+ * A(q) exponent condition fails). */
 pk_status pk_batch_download(pk_ctx* ctx, pk_batch* b, const void* d_workspace, pk_scaled* Z,
                             pk_scaled* V);
 /* create + upload + launch + download + destroy. */

@@ -10,6 +10,9 @@ PD convention (used everywhere in this repository): arcs are labelled
 (k+1) mod 2n.  A crossing is a 4-tuple (a, b, c, d): a is the incoming
 under-arc, then b, c, d follow counter-clockwise around the crossing; c is the
 outgoing under-arc (c = a+1 mod 2n) and the over-strand runs between b and d.
+A link (several components) cannot be labelled along one strand; `braid_closure_link`
+labels it component by component and returns the twist sign of every crossing
+(+1: the over-strand leaves through b), which fixes the orientation instead.
 
 Random knots follow the random grid walk of Sec. III.A: two random permutations
 x, y of 0..L-1 give the closed walk (x_i, y_i) -> (x_i, y_{i+1}) -> (x_{i+1}, y_{i+1});
@@ -26,6 +29,7 @@ MASK64 = (1 << 64) - 1
 
 __all__ = [
     "SplitMix64", "GridKnot", "grid_walk_pd", "random_grid_knot", "braid_closure_pd",
+    "braid_closure_link",
     "over_out_is_b", "kink", "poke", "mirror", "connected_sum", "randomize",
     "rotate_labels", "torus_braid", "knot_suite",
 ]
@@ -244,6 +248,70 @@ def braid_closure_pd(word, n_strands: int):
     if len(label) != len(arcs):
         raise ValueError("braid closure is a link, not a knot")
     return [tuple(label[u] for u in x) for x in raw]
+
+
+def braid_closure_link(word, n_strands: int):
+    """Closure of a braid word as a possibly multi-component diagram: (pd, signs,
+    components).  Arcs are labelled component by component along the orientation
+    (strands running upward); signs[i] = +1 when crossing i is sigma_j (over-strand
+    leaving through arm b), -1 for sigma_j^-1.  Every generator sigma_1 ..
+    sigma_{n_strands-1} must occur, so that the diagram is connected."""
+    if not word:
+        raise ValueError("a link diagram needs crossings")
+    if sorted({abs(g) for g in word}) != list(range(1, n_strands)):
+        raise ValueError("every generator must occur (a split diagram has no Tait graph)")
+    parent = {}
+
+    def find(u):
+        while parent[u] != u:
+            parent[u] = parent[parent[u]]
+            u = parent[u]
+        return u
+
+    ids = [0]
+
+    def new():
+        k = ids[0]
+        ids[0] += 1
+        parent[k] = k
+        return k
+
+    cur = [new() for _ in range(n_strands)]
+    start = list(cur)
+    raw = []
+    for g in word:
+        i = abs(g) - 1
+        in_l, in_r = cur[i], cur[i + 1]
+        o1, o2 = new(), new()   # o1: left strand, now at i+1; o2: right strand, now at i
+        raw.append((in_r, o1, o2, in_l) if g > 0 else (in_l, in_r, o1, o2))
+        cur[i], cur[i + 1] = o2, o1
+    for p in range(n_strands):
+        ra, rb = find(cur[p]), find(start[p])
+        if ra != rb:
+            parent[ra] = rb
+    raw = [tuple(find(u) for u in x) for x in raw]
+    signs = [1 if g > 0 else -1 for g in word]
+    nxt = {}
+    for (a, b, c, d), sg in zip(raw, signs):
+        nxt[a] = c
+        if sg > 0:
+            nxt[d] = b
+        else:
+            nxt[b] = d
+    label = {}
+    comps = 0
+    for x in raw:             # a component may pass only over: start from every arc
+        for a in x:
+            if a in label:
+                continue
+            comps += 1
+            u = a
+            while u not in label:
+                label[u] = len(label)
+                u = nxt[u]
+    if len(label) != len(nxt):
+        raise ValueError("inconsistent braid closure")
+    return [tuple(label[u] for u in x) for x in raw], signs, comps
 
 
 def torus_braid(p: int, r: int):

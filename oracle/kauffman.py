@@ -11,11 +11,14 @@ textbook state-sum definition of it.)
   joins arc ends a-b and c-d.  The B-smoothing joins a-d and b-c.
 * <K> = sum_S A^{#A(S) - #B(S)} d^{|S| - 1},  d = -A^2 - A^-2, |S| = loops of S.
 * V(t) = (-A^3)^{-w} <K> with t = A^-4 (w = writhe, right-hand rule).
-Returned as {power of t: integer coefficient}.
+Returned as {power of t: integer coefficient}; for a link the powers are multiples of
+1/2 (Fraction keys).  The bracket needs no orientation; the writhe does: a knot's PD
+labels give it, a link passes the twist signs of its crossings.
 """
 from __future__ import annotations
 
 from collections import Counter, defaultdict
+from fractions import Fraction
 
 
 def _writhe(pd):
@@ -76,15 +79,20 @@ def bracket(pd):
     return {k: v for k, v in out.items() if v}
 
 
-def jones_poly(pd):
-    """V_K(t) as {power of t: coefficient} from the bracket."""
-    w = _writhe(pd)
+def jones_poly(pd, signs=None):
+    """V(t) as {power of t: coefficient} from the bracket (integer powers for a knot,
+    multiples of 1/2 as Fractions for a link given with its crossing signs)."""
+    w = _writhe(pd) if signs is None else sum(signs)
     br = bracket(pd)
     sign = -1 if w % 2 else 1
     out = {}
     for e, c in br.items():
         ea = e - 3 * w             # (-A^3)^-w = (-1)^w A^-3w
-        if ea % 4:
+        if signs is None and ea % 4:
             raise ValueError("not a knot: A-exponent not divisible by 4")
-        out[-ea // 4] = out.get(-ea // 4, 0) + sign * c
+        if ea % 2:
+            raise ValueError("A-exponent of a link bracket must be even")
+        p = Fraction(-ea, 4)
+        key = int(p) if p.denominator == 1 else p
+        out[key] = out.get(key, 0) + sign * c
     return {k: v for k, v in out.items() if v}

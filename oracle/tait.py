@@ -20,6 +20,12 @@ carries no unbounded region, so the caller either names a side of an arc that
 borders it (`outer = (arc, side)`, side 0 = left, 1 = right, as the grid-walk
 generator reports) or the colour class is chosen by `black` (0: the class of the
 region right of arc 0 is black, 1: the other).  Both classes give the same V.
+
+Orientation.  A knot's PD code labels its arcs 0..2n-1 along the orientation, so the
+under-strand runs a -> a+1 and the over-strand's direction follows from its labels.  A
+link (several components) cannot be labelled that way; it is given with `signs`, the
+twist sign of every crossing (+1: the over-strand leaves through arm b, -1: through arm
+d, which is the right-hand rule of step 1), and any labels occurring twice each.
 """
 from __future__ import annotations
 
@@ -52,7 +58,7 @@ def _over_leaves_via_b(pd):
     return out
 
 
-def tait_graph(pd, outer=None, black=None) -> TaitGraph:
+def tait_graph(pd, outer=None, black=None, signs=None) -> TaitGraph:
     n = len(pd)
     if n == 0:
         # a crossingless circle: one black region inside, white outside
@@ -61,10 +67,15 @@ def tait_graph(pd, outer=None, black=None) -> TaitGraph:
     labels = sorted(y for X in pd for y in X)
     if labels != sorted(list(range(two_n)) * 2):
         raise ValueError("each arc label 0..2n-1 must occur exactly twice")
-    for (a, b, c, d) in pd:
-        if c != (a + 1) % two_n:
-            raise ValueError("under-strand must run a -> a+1")
-    via_b = _over_leaves_via_b(pd)
+    if signs is None:
+        for (a, b, c, d) in pd:
+            if c != (a + 1) % two_n:
+                raise ValueError("under-strand must run a -> a+1")
+        via_b = _over_leaves_via_b(pd)
+    else:
+        if len(signs) != n or any(x not in (1, -1) for x in signs):
+            raise ValueError("one twist sign +-1 per crossing")
+        via_b = [x > 0 for x in signs]
 
     # components: follow arc -> next arc through each crossing
     nxt = {}
@@ -74,7 +85,7 @@ def tait_graph(pd, outer=None, black=None) -> TaitGraph:
             nxt[d] = b
         else:
             nxt[b] = d
-    if len(nxt) != two_n:
+    if len(nxt) != two_n or sorted(nxt.values()) != list(range(two_n)):
         raise ValueError("inconsistent over-strand orientation")
     seen = set()
     comps = 0

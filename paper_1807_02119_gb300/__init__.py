@@ -23,7 +23,7 @@ STATUS = {0: "PK_OK", 1: "PK_EINVAL", 2: "PK_ENOTKNOT", 3: "PK_ENOMEM", 4: "PK_E
 
 EXPORTED = [
     "pk_ctx_create", "pk_ctx_set_stream", "pk_last_error", "pk_ctx_destroy",
-    "pk_knot_from_pd", "pk_knot_from_signed_graph", "pk_knot_from_grid_walk", "pk_knot_info",
+    "pk_knot_from_pd", "pk_link_from_pd", "pk_knot_from_signed_graph", "pk_knot_from_grid_walk", "pk_knot_info",
     "pk_knot_edges", "pk_knot_pd", "pk_knot_destroy", "pk_plan_create", "pk_plan_info",
     "pk_plan_workspace_bytes", "pk_plan_steps", "pk_plan_destroy", "pk_eval", "pk_upload",
     "pk_launch", "pk_download", "pk_plan_launches", "pk_jones_from_z", "pk_plan_debug_blob",
@@ -80,6 +80,7 @@ def lib():
         "pk_ctx_set_stream": [vp, vp],
         "pk_ctx_destroy": [vp],
         "pk_knot_from_pd": [vp, P(i32), i32, i32, i32, P(vp)],
+        "pk_link_from_pd": [vp, P(i32), P(i32), i32, i32, i32, P(vp)],
         "pk_knot_from_signed_graph": [vp, i32, i32, P(i32), i32, P(vp)],
         "pk_knot_from_grid_walk": [vp, i32, u64, i32, i32, i32, P(vp)],
         "pk_knot_info": [vp, P(i32), P(i32), P(i32), P(i32), P(i32)],
@@ -197,6 +198,18 @@ class Knot:
         oa, os_ = (outer if outer is not None else (-1, 0))
         h = C.c_void_p()
         _check(lib().pk_knot_from_pd(ctx.h, arr, len(pd), oa, os_, C.byref(h)), ctx)
+        return Knot(h, ctx)
+
+    @staticmethod
+    def from_link_pd(ctx: Context, pd, signs, outer=None) -> "Knot":
+        """pk_link_from_pd: a link (or knot) diagram with the twist sign of every crossing
+        (+1: over-strand leaves through arm b); V is then evaluated for links too."""
+        flat = [int(v) for X in pd for v in X]
+        arr = (C.c_int32 * max(1, len(flat)))(*flat)
+        sg = (C.c_int32 * max(1, len(signs)))(*[int(x) for x in signs])
+        oa, os_ = (outer if outer is not None else (-1, 0))
+        h = C.c_void_p()
+        _check(lib().pk_link_from_pd(ctx.h, arr, sg, len(pd), oa, os_, C.byref(h)), ctx)
         return Knot(h, ctx)
 
     @staticmethod

@@ -178,6 +178,22 @@ pk_status pk_knot_from_pd(pk_ctx* ctx, const int32_t* pd, int32_t n, int32_t out
   return PK_OK;
 }
 
+pk_status pk_link_from_pd(pk_ctx* ctx, const int32_t* pd, const int32_t* signs, int32_t n,
+                          int32_t outer_arc, int32_t outer_side, pk_knot** out) {
+  if (!out) return fail(ctx, PK_EINVAL, "null output");
+  *out = nullptr;
+  if (n > 0 && !signs) return fail(ctx, PK_EINVAL, "null twist signs");
+  pk_knot* k = new (std::nothrow) pk_knot();
+  if (!k) return fail(ctx, PK_ENOMEM, "out of host memory");
+  std::string err;
+  if (!pk::knot_from_pd(pd, n, outer_arc, outer_side, k->k, err, signs)) {
+    delete k;
+    return fail(ctx, PK_EINVAL, err);
+  }
+  *out = k;
+  return PK_OK;
+}
+
 pk_status pk_knot_from_signed_graph(pk_ctx* ctx, int32_t n_v, int32_t n_e, const int32_t* uve,
                                     int32_t writhe, pk_knot** out) {
   if (!out) return fail(ctx, PK_EINVAL, "null output");
@@ -539,9 +555,7 @@ void pk_group_destroy(pk_group* grp) {
 
 pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_scaled* V) {
   if (!k || !Z || !V || q < 1) return PK_EINVAL;
-  if (k->k.components != 1) return PK_ENOTKNOT;
-  int64_t num = 3LL * k->k.writhe + k->k.tau + 2LL * k->k.n_v + 2;
-  if (num % 4 != 0) return PK_EINVAL;
+  if (!pk::jones_defined(k->k)) return PK_EINVAL;
   pk::Scaled z;
   z.re = Z->re;
   z.im = Z->im;
@@ -575,8 +589,7 @@ pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const vo
     pk_knot kk;
     kk.k = P.knot;
     pk_status s = pk_jones_from_z(&kk, P.q, Z, V);
-    if (s == PK_ENOTKNOT) return fail(ctx, s, "not a knot: V undefined");
-    if (s != PK_OK) return fail(ctx, s, "3w + tau + 2 n_v + 2 not divisible by 4");
+    if (s != PK_OK) return fail(ctx, s, "3w + tau + 2 n_v + 2 not divisible by 4 (knot) or 2 (link)");
   }
   return PK_OK;
 }
@@ -677,8 +690,7 @@ pk_status pk_grad(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_work
     pk_knot kk;
     kk.k = P.knot;
     pk_status sv = pk_jones_from_z(&kk, P.q, &zs, V);
-    if (sv == PK_ENOTKNOT) return fail(ctx, sv, "not a knot: V undefined");
-    if (sv != PK_OK) return fail(ctx, sv, "3w + tau + 2 n_v + 2 not divisible by 4");
+    if (sv != PK_OK) return fail(ctx, sv, "3w + tau + 2 n_v + 2 not divisible by 4 (knot) or 2 (link)");
   }
   const double* acc = (const double*)(host + prog + sizeof(pk::SliceResult));
   const int64_t* acc_exp = (const int64_t*)(host + prog + sizeof(pk::SliceResult) +

@@ -429,11 +429,10 @@ pk_status pk_batch_download(pk_ctx* ctx, pk_batch* b, const void* d_ws, pk_scale
     Z[i].exp2 = z.e;
     if (V) {
       const pk::Knot& k = b->kinfo[i];
-      const int64_t num = 3LL * k.writhe + k.tau + 2LL * k.n_v + 2;
-      if (k.components != 1 || num % 4 != 0) {
+      if (!pk::jones_defined(k)) {
         V[i].re = V[i].im = 0;
         V[i].exp2 = 0;
-        status = PK_ENOTKNOT;
+        status = PK_EINVAL;
         continue;
       }
       pk::Scaled v = pk::s_mul(pk::jones_prefactor(k, b->qs[i]), z);
@@ -442,7 +441,7 @@ pk_status pk_batch_download(pk_ctx* ctx, pk_batch* b, const void* d_ws, pk_scale
       V[i].exp2 = v.e;
     }
   }
-  if (status != PK_OK) ctx->err = "some batch entries are not knots: V left 0";
+  if (status != PK_OK) ctx->err = "some batch entries violate the A(q) exponent condition: V left 0";
   return status;
 }
 

@@ -361,8 +361,10 @@ bool grad_finalize(const Plan& p, const double* acc, const int64_t* acc_exp, con
       t_of_q_value(q, tre, tim);
       const cd t(tre, tim);
       const Knot& k = p.knot;
-      const int64_t kk = (3LL * k.writhe + k.tau + 2LL * k.n_v + 2) / 4;
-      cd r = (double)kk / t - (double)(k.n_v + 1) / (t + 1.0);
+      // d/dt log of s^num (s^4 = t) is (num / 4) / t: an integer k for a knot, a multiple
+      // of 1/2 for a link
+      const double kk = (double)(3LL * k.writhe + k.tau + 2LL * k.n_v + 2) / 4.0;
+      cd r = kk / t - (double)(k.n_v + 1) / (t + 1.0);
       for (size_t c = 0; c < n_e; ++c) {
         cd s(0, 0);
         for (int32_t a = 0; a < q; ++a) s += dl[((size_t)c * q + a) * q + a];

@@ -22,8 +22,11 @@ bool over_leaves_b(const std::array<int32_t, 4>& x, int32_t two_n) {
 
 }  // namespace
 
+// `signs` (NULL for a knot labelled along its orientation): the twist sign of every
+// crossing, +1 when the over-strand leaves through arm b; it fixes the orientation of a
+// link, whose labels cannot run 0..2n-1 along one strand.
 bool knot_from_pd(const int32_t* pd, int32_t n, int32_t outer_arc, int32_t outer_side, Knot& k,
-                  std::string& err) {
+                  std::string& err, const int32_t* signs) {
   k = Knot();
   k.has_pd = true;
   if (n < 0 || (n > 0 && pd == nullptr)) {
@@ -47,8 +50,12 @@ bool knot_from_pd(const int32_t* pd, int32_t n, int32_t outer_arc, int32_t outer
       k.pd[i][j] = a;
       seen[a]++;
     }
-    if (k.pd[i][2] != (k.pd[i][0] + 1) % two_n) {
+    if (!signs && k.pd[i][2] != (k.pd[i][0] + 1) % two_n) {
       err = "under-strand must run a -> a+1";
+      return false;
+    }
+    if (signs && signs[i] != 1 && signs[i] != -1) {
+      err = "twist signs must be +-1";
       return false;
     }
   }
@@ -62,7 +69,7 @@ bool knot_from_pd(const int32_t* pd, int32_t n, int32_t outer_arc, int32_t outer
   std::vector<std::array<int32_t, 2>> ends(two_n, {-1, -1});  // encoded 4*X+arm
   std::vector<int32_t> tail_end(two_n, -1), head_end(two_n, -1);
   for (int32_t x = 0; x < n; ++x) {
-    ob[x] = over_leaves_b(k.pd[x], two_n) ? 1 : 0;
+    ob[x] = signs ? (signs[x] > 0 ? 1 : 0) : (over_leaves_b(k.pd[x], two_n) ? 1 : 0);
     for (int arm = 0; arm < 4; ++arm) {
       int32_t a = k.pd[x][arm];
       bool out = (arm == 2) || (arm == 1 && ob[x]) || (arm == 3 && !ob[x]);

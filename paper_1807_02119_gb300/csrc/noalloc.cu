@@ -93,11 +93,8 @@ extern "C" pk_status pk_eval_noalloc(pk_ctx* ctx, const pk_plan* p, int32_t prec
     Z->im = z.im;
     Z->exp2 = z.e;
     if (V) {
-      const int64_t num = 3LL * P.knot.writhe + P.knot.tau + 2LL * P.knot.n_v + 2;
-      if (P.knot.components != 1) {
-        status = noalloc_fail(ctx, PK_ENOTKNOT, "not a knot: V undefined");
-      } else if (num % 4 != 0) {
-        status = noalloc_fail(ctx, PK_EINVAL, "3w + tau + 2 n_v + 2 not divisible by 4");
+      if (!pk::jones_defined(P.knot)) {
+        status = noalloc_fail(ctx, PK_EINVAL, "3w + tau + 2 n_v + 2 not divisible by 4 (knot) or 2 (link)");
       } else {
         pk::Scaled v = pk::s_mul(pk::jones_prefactor(P.knot, P.q), z);
         V->re = v.re;

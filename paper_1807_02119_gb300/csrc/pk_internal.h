@@ -23,7 +23,7 @@ struct Knot {
 };
 
 bool knot_from_pd(const int32_t* pd, int32_t n, int32_t outer_arc, int32_t outer_side, Knot& k,
-                  std::string& err);
+                  std::string& err, const int32_t* signs = nullptr);
 bool knot_from_graph(int32_t n_v, int32_t n_e, const int32_t* uve, int32_t writhe, Knot& k,
                      std::string& err);
 bool grid_walk_pd(int32_t L, uint64_t seed, bool random_over_under, int32_t nmin, int32_t nmax,
@@ -303,6 +303,7 @@ bool grad_finalize(const Plan& p, const double* acc, const int64_t* acc_exp, con
                    double* dlogz, double* dlogv_dt);
 void clause_diag(int32_t q, int32_t mult, int32_t signsum, double& re, double& im);
 void t_of_q_value(int32_t q, double& re, double& im);  // t(q) of Eq. potts2jones
+bool jones_defined(const Knot& k);  // A(q)'s exponent condition (knots: 4 | num, links: 2 | num)
 Scaled jones_prefactor(const Knot& k, int32_t q);  // A(q) in its integer-exponent form
 
 }  // namespace pk

@@ -113,14 +113,25 @@ void clause_diag(int32_t q, int32_t mult, int32_t signsum, double& re, double& i
 }
 
 // A(q) of Eq. JonesPotts.  With s the principal fourth root of t, every fractional
-// power in A is a power of s and A = (-1)^(w+n_v+1) t^k (t+1)^-(n_v+1) with
-// k = (3w + tau + 2 n_v + 2)/4, an integer for knots.
+// power in A is a power of s and A = (-1)^(w+n_v+1) s^num (t+1)^-(n_v+1) with
+// num = 3w + tau + 2 n_v + 2: a multiple of 4 for a knot (A is then branch-free, a power
+// of t), even for a link (V in Z[t^(1/2)], evaluated with the principal s).
+bool jones_defined(const Knot& k) {
+  const int64_t num = 3LL * k.writhe + k.tau + 2LL * k.n_v + 2;
+  return k.components == 1 ? num % 4 == 0 : num % 2 == 0;
+}
 Scaled jones_prefactor(const Knot& k, int32_t q) {
   int64_t num = 3LL * k.writhe + k.tau + 2LL * k.n_v + 2;
   cd t = t_of_q(q);
-  Scaled tt = s_from(t.real(), t.imag());
   Scaled t1 = s_from(t.real() + 1, t.imag());
-  Scaled r = s_mul(s_pow(tt, num / 4), s_pow(t1, -(int64_t)(k.n_v + 1)));
+  Scaled pw;
+  if (num % 4 == 0) {
+    pw = s_pow(s_from(t.real(), t.imag()), num / 4);
+  } else {
+    const cd s4 = std::exp(std::log(t) / 4.0);   // principal fourth root of t
+    pw = s_pow(s_from(s4.real(), s4.imag()), num);
+  }
+  Scaled r = s_mul(pw, s_pow(t1, -(int64_t)(k.n_v + 1)));
   if ((k.writhe + k.n_v + 1) & 1) {
     r.re = -r.re;
     r.im = -r.im;
