@@ -323,6 +323,44 @@ pk_status pk_eval_noalloc(pk_ctx* ctx, const pk_plan* p, int32_t precision, pk_s
 /* Host-side normalisation only: V = A(q) Z for the knot's (n_v, w, tau) (Eq. JonesPotts). */
 pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_scaled* V);
 
+/* ---- exact evaluation and the Jones polynomial (Sec. "Conclusions and outlook") ---- */
+
+/* Z(q) exactly, modulo each of n_primes primes q < p < 2^31 (checked): at integer q the
+ * Potts t is a root of t^2 - (q-2) t + 1, the standard clause entries are integer
+ * polynomials in t, and the plan's contraction is run on the GPU in
+ * F_p[t]/(t^2 - (q-2) t + 1).  zab[2i], zab[2i+1] = (a, b) with Z = a + b t mod primes[i]
+ * (constant factors included).  d_workspace: at least pk_plan_workspace_bytes(PK_C64)
+ * (NULL: the context's own); the program is uploaded into it.  Blocks until done.
+ * Errors: PK_EINVAL (general weights, a complex128 tail, bad moduli), PK_ETOOWIDE (more
+ * than 10^6 slices: each slice is a launch sequence), PK_ENOMEM. */
+pk_status pk_eval_exact(pk_ctx* ctx, const pk_plan* p, const uint32_t* primes, int32_t n_primes,
+                        void* d_workspace, uint64_t workspace_bytes, uint32_t* zab);
+
+/* All coefficients of V_K(t) for a knot given by its PD code, by interpolation between
+ * exact values at integer q = 1, 2, ...: the exponent window comes from the all-A and
+ * all-B smoothings (span <= crossings); each q adds two linear equations (the t^0 and t^1
+ * parts of V(t(q)) in Z[t]/(t^2 - (q-2) t + 1)), solved modulo four primes near 2^31
+ * (Z(q) mod p from pk_eval_exact) and lifted to signed 64-bit integers by the Chinese
+ * remainder theorem with the fourth prime as a check.  On return V = sum_j coef[j]
+ * t^(lowest + j), j < count (count <= capacity, else PK_ENOMEM with count set).  Plans
+ * for q up to about crossings/2 + 3 are built and evaluated: feasible while those fit.
+ * Errors: PK_EINVAL (no PD code, a link, a singular or inconsistent system, coefficients
+ * beyond 64 bits), PK_ETOOWIDE (a plan too wide). */
+pk_status pk_jones_coefficients(pk_ctx* ctx, const pk_knot* k, int32_t capacity, int32_t* lowest,
+                                int32_t* count, int64_t* coef);
+
+/* The two host stages of pk_jones_coefficients (no GPU needed).  pk_jones_plan: the
+ * values of q (n_q of them, 1 .. n_q, into qs if not NULL) and the four moduli (into
+ * primes if not NULL) the knot's exponent window needs.  pk_jones_solve: the coefficients
+ * from zab[2 (iq n_primes + ip) + {0, 1}] = (a, b), Z(qs[iq]) = a + b t mod primes[ip]
+ * (as pk_eval_exact gives them); the last modulus checks the reconstruction.  Errors:
+ * PK_EINVAL (no PD code, a link, bad moduli, a singular or inconsistent system,
+ * coefficients beyond 64 bits), PK_ENOMEM (capacity; count set). */
+pk_status pk_jones_plan(const pk_knot* k, int32_t* n_q, int32_t* qs, int32_t* n_primes, uint32_t* primes);
+pk_status pk_jones_solve(const pk_knot* k, int32_t n_q, const int32_t* qs, int32_t n_primes,
+                         const uint32_t* primes, const uint32_t* zab, int32_t capacity, int32_t* lowest,
+                         int32_t* count, int64_t* coef);
+
 /* ---- reverse pass (adjoint contraction) ------------------------------------------
  *
  * Z = sum over spin states of prod_e T_e[s_u, s_v] (Sec. II) is linear in every entry

@@ -31,7 +31,8 @@ EXPORTED = [
     "pk_batch_create", "pk_batch_workspace_bytes", "pk_batch_upload", "pk_batch_launch",
     "pk_batch_download", "pk_eval_batch", "pk_batch_destroy", "pk_group_create",
     "pk_group_launch", "pk_group_destroy", "pk_grad_workspace_bytes", "pk_grad",
-    "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights",
+    "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights", "pk_eval_exact",
+    "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve",
 ]
 
 
@@ -81,6 +82,11 @@ def lib():
         "pk_ctx_destroy": [vp],
         "pk_knot_from_pd": [vp, P(i32), i32, i32, i32, P(vp)],
         "pk_link_from_pd": [vp, P(i32), P(i32), i32, i32, i32, P(vp)],
+        "pk_eval_exact": [vp, vp, P(C.c_uint32), i32, vp, u64, P(C.c_uint32)],
+        "pk_jones_coefficients": [vp, vp, i32, P(i32), P(i32), P(i64)],
+        "pk_jones_plan": [vp, P(i32), P(i32), P(i32), P(C.c_uint32)],
+        "pk_jones_solve": [vp, i32, P(i32), i32, P(C.c_uint32), P(C.c_uint32), i32, P(i32), P(i32),
+                           P(i64)],
         "pk_knot_from_signed_graph": [vp, i32, i32, P(i32), i32, P(vp)],
         "pk_knot_from_grid_walk": [vp, i32, u64, i32, i32, i32, P(vp)],
         "pk_knot_info": [vp, P(i32), P(i32), P(i32), P(i32), P(i32)],
@@ -387,6 +393,61 @@ def evaluate(plan: Plan, precision: str = "c128", ws=None):
         return Scaled.of(z), None
     _check(st, ctx)
     return Scaled.of(z), Scaled.of(v)
+
+
+def evaluate_exact(plan: Plan, primes, ws=None):
+    """pk_eval_exact: Z(q) modulo each prime as (a, b) with Z = a + b t (t the Potts t(q)),
+    computed on the GPU without rounding."""
+    ctx = plan.ctx
+    if ctx.device < 0:
+        raise PkError(7, "evaluate_exact needs a GPU context")
+    _torch_stream(ctx)
+    n = len(primes)
+    pr = (C.c_uint32 * n)(*[int(x) for x in primes])
+    out = (C.c_uint32 * (2 * n))()
+    if ws is None:
+        ws = workspace(plan, "c64")
+    _check(lib().pk_eval_exact(ctx.h, plan.h, pr, n, C.c_void_p(ws.data_ptr()),
+                               ws.numel() * ws.element_size(), out), ctx)
+    return [(out[2 * i], out[2 * i + 1]) for i in range(n)]
+
+
+def jones_polynomial(ctx: Context, knot: Knot) -> dict:
+    """pk_jones_coefficients: V_K(t) as {power of t: integer coefficient}."""
+    if ctx.device < 0:
+        raise PkError(7, "jones_polynomial needs a GPU context")
+    _torch_stream(ctx)
+    cap = 2 * knot.info()["n_c"] + 8
+    coef = (C.c_int64 * cap)()
+    lo, cnt = C.c_int32(), C.c_int32()
+    _check(lib().pk_jones_coefficients(ctx.h, knot.h, cap, C.byref(lo), C.byref(cnt), coef), ctx)
+    return {lo.value + j: coef[j] for j in range(cnt.value) if coef[j]}
+
+
+def jones_plan(knot: Knot):
+    """pk_jones_plan: (the q values, the moduli) the coefficient solve needs."""
+    nq, npr = C.c_int32(), C.c_int32()
+    _check(lib().pk_jones_plan(knot.h, C.byref(nq), None, C.byref(npr), None))
+    qs = (C.c_int32 * nq.value)()
+    pr = (C.c_uint32 * npr.value)()
+    _check(lib().pk_jones_plan(knot.h, C.byref(nq), qs, C.byref(npr), pr))
+    return list(qs), list(pr)
+
+
+def jones_solve(knot: Knot, qs, primes, zab) -> dict:
+    """pk_jones_solve (host only): V's coefficients from zab[iq][ip] = (a, b), Z(qs[iq]) =
+    a + b t mod primes[ip]."""
+    nq, npr = len(qs), len(primes)
+    q_arr = (C.c_int32 * nq)(*qs)
+    p_arr = (C.c_uint32 * npr)(*primes)
+    flat = [int(v) for row in zab for pair in row for v in pair]
+    z_arr = (C.c_uint32 * len(flat))(*flat)
+    cap = 2 * knot.info()["n_c"] + 8
+    coef = (C.c_int64 * cap)()
+    lo, cnt = C.c_int32(), C.c_int32()
+    _check(lib().pk_jones_solve(knot.h, nq, q_arr, npr, p_arr, z_arr, cap, C.byref(lo), C.byref(cnt),
+                                coef))
+    return {lo.value + j: coef[j] for j in range(cnt.value) if coef[j]}
 
 
 def evaluate_noalloc(plan: Plan, precision: str = "c128"):

@@ -10,6 +10,7 @@
 
 #include "pk_internal.h"
 
+#include "exact_ring.h"
 #include "handles.h"
 
 namespace {
@@ -697,6 +698,163 @@ pk_status pk_grad(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_work
                                             16ull * (uint64_t)P.q * P.q * nl);
   if (!pk::grad_finalize(P, acc, acc_exp, z, dlogZ_dT, dlogV_dt))
     return fail(ctx, PK_EZERO, "Z is zero: log-derivatives undefined");
+  return PK_OK;
+}
+
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ exact evaluation
+namespace {
+
+constexpr int64_t kExactMaxSlices = 1000000;
+
+bool is_prime32(uint32_t p) {
+  if (p < 2) return false;
+  for (uint32_t d = 2; (uint64_t)d * d <= p; ++d)
+    if (p % d == 0) return false;
+  return true;
+}
+
+// Z(q) mod each prime (loop factor included) for an uploaded plan.
+pk_status exact_residues(pk_ctx* ctx, const pk_plan* p, const uint32_t* primes, int32_t n_primes,
+                         void* ws, uint32_t* zab) {
+  const pk::Plan& P = p->p;
+  for (int32_t i = 0; i < n_primes; ++i) {
+    void* sum = (char*)ws + P.off_result;
+    cudaError_t e = pk::launch_exact(P, primes[i], ws, (char*)ws + P.off_arena, sum, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->pinned_result, sum, sizeof(pk::exact::E), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "exact evaluation");
+    pk::exact::E z;
+    std::memcpy(&z, ctx->pinned_result, sizeof(z));
+    const pk::exact::Ring r = pk::exact::make_ring(primes[i], P.q);
+    pk::exact::E f = pk::exact::epow_t(-(long long)P.loop_signsum, r);  // folded loops
+    if (P.loop_count & 1) f = pk::exact::eneg(f, r);
+    z = pk::exact::emul(z, f, r);
+    zab[2 * i] = z.a;
+    zab[2 * i + 1] = z.b;
+  }
+  return PK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pk_status pk_eval_exact(pk_ctx* ctx, const pk_plan* p, const uint32_t* primes, int32_t n_primes,
+                        void* d_workspace, uint64_t workspace_bytes, uint32_t* zab) {
+  if (!ctx || !p || !primes || n_primes < 1 || !zab) return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  const pk::Plan& P = p->p;
+  if (P.general || !P.std_weights || !P.tail.empty())
+    return fail(ctx, PK_EINVAL, "exact evaluation needs the standard weights and no complex128 tail");
+  for (int32_t i = 0; i < n_primes; ++i)
+    if (primes[i] <= (uint32_t)P.q || primes[i] >= (1u << 31) || !is_prime32(primes[i]))
+      return fail(ctx, PK_EINVAL, "moduli must be primes between q and 2^31");
+  if (P.n_slices > kExactMaxSlices)   // every slice is a launch sequence of its own
+    return fail(ctx, PK_ETOOWIDE, "too many slices for the exact path");
+  DeviceGuard g(ctx->device);
+  void* ws = d_workspace;
+  uint64_t bytes = workspace_bytes;
+  pk_status s = check_ws(ctx, p, PK_C64, ws, bytes);
+  if (s != PK_OK) return s;
+  if ((s = pk_upload(ctx, p, PK_C64, ws, bytes)) != PK_OK) return s;
+  return exact_residues(ctx, p, primes, n_primes, ws, zab);
+}
+
+pk_status pk_jones_plan(const pk_knot* k, int32_t* n_q, int32_t* qs_out, int32_t* n_primes,
+                        uint32_t* primes_out) {
+  if (!k || !n_q || !n_primes) return PK_EINVAL;
+  int32_t lo = 0, hi = 0;
+  if (!pk::jones_window(k->k, lo, hi)) return PK_EINVAL;
+  const int32_t m = hi - lo + 1;
+  // q = 1, 2, ... until two equations per q exceed the unknowns by four
+  int32_t nq = 0;
+  while (2 * nq < m + 4) ++nq;
+  if (qs_out)
+    for (int32_t i = 0; i < nq; ++i) qs_out[i] = i + 1;
+  *n_q = nq;
+  // moduli: the four largest primes below 2^31 (the last one checks the reconstruction)
+  int32_t np = 0;
+  for (uint32_t c = (1u << 31) - 1; np < 4; c -= 2)
+    if (is_prime32(c)) {
+      if (primes_out) primes_out[np] = c;
+      ++np;
+    }
+  *n_primes = np;
+  return PK_OK;
+}
+
+pk_status pk_jones_solve(const pk_knot* k, int32_t n_q, const int32_t* qs, int32_t n_primes,
+                         const uint32_t* primes, const uint32_t* zab, int32_t capacity, int32_t* lowest,
+                         int32_t* count, int64_t* coef) {
+  if (!k || n_q < 1 || !qs || n_primes < 2 || !primes || !zab || !lowest || !count || (capacity > 0 && !coef))
+    return PK_EINVAL;
+  int32_t lo = 0, hi = 0;
+  if (!pk::jones_window(k->k, lo, hi)) return PK_EINVAL;
+  const int32_t m = hi - lo + 1;
+  std::vector<int32_t> q(qs, qs + n_q);
+  std::vector<uint32_t> pr(primes, primes + n_primes);
+  for (int32_t i = 0; i < n_q; ++i)
+    for (int32_t j = 0; j < n_primes; ++j)
+      if (q[i] < 1 || pr[j] <= (uint32_t)q[i] || pr[j] >= (1u << 31) || !is_prime32(pr[j])) return PK_EINVAL;
+  std::vector<std::vector<uint32_t>> res(n_primes);
+  for (int32_t ip = 0; ip < n_primes; ++ip) {
+    std::vector<uint32_t> vals(2 * (size_t)n_q);
+    for (int32_t iq = 0; iq < n_q; ++iq) {
+      const uint32_t* z = zab + 2 * ((size_t)iq * n_primes + ip);
+      pk::jones_value_mod(k->k, q[iq], pr[ip], z[0] % pr[ip], z[1] % pr[ip], vals[2 * iq], vals[2 * iq + 1]);
+    }
+    if (!pk::solve_coefficients_mod(q, vals, lo, m, pr[ip], res[ip])) return PK_EINVAL;
+  }
+  std::vector<int64_t> c;
+  if (!pk::crt_signed(pr, res, c)) return PK_EINVAL;
+  int32_t first = 0, last = m - 1;
+  while (first <= last && c[first] == 0) ++first;
+  while (last >= first && c[last] == 0) --last;
+  *lowest = first <= last ? lo + first : 0;
+  *count = first <= last ? last - first + 1 : 0;
+  if (*count > capacity) return PK_ENOMEM;
+  for (int32_t j = 0; j < *count; ++j) coef[j] = c[first + j];
+  return PK_OK;
+}
+
+pk_status pk_jones_coefficients(pk_ctx* ctx, const pk_knot* k, int32_t capacity, int32_t* lowest,
+                                int32_t* count, int64_t* coef) {
+  if (!ctx || !k || !lowest || !count || (capacity > 0 && !coef)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  int32_t nq = 0, np = 0;
+  if (pk_jones_plan(k, &nq, nullptr, &np, nullptr) != PK_OK)
+    return fail(ctx, PK_EINVAL, "coefficients need a knot given by its PD code");
+  std::vector<int32_t> qs(nq);
+  std::vector<uint32_t> primes(np);
+  pk_jones_plan(k, &nq, qs.data(), &np, primes.data());
+  std::vector<uint32_t> zab(2 * (size_t)nq * np);
+  DeviceGuard g(ctx->device);
+  for (int32_t iq = 0; iq < nq; ++iq) {
+    pk_plan* p = nullptr;
+    pk_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    pk_status s = pk_plan_create(ctx, k, qs[iq], &o, &p);
+    if (s != PK_OK) return s;
+    if (p->p.n_slices > kExactMaxSlices) {
+      pk_plan_destroy(p);
+      return fail(ctx, PK_ETOOWIDE, "too many slices for the exact path");
+    }
+    void* ws = nullptr;
+    uint64_t bytes = 0;
+    s = check_ws(ctx, p, PK_C64, ws, bytes);
+    if (s == PK_OK) s = pk_upload(ctx, p, PK_C64, ws, bytes);
+    if (s == PK_OK) s = exact_residues(ctx, p, primes.data(), np, ws, zab.data() + 2 * (size_t)iq * np);
+    pk_plan_destroy(p);
+    if (s != PK_OK) return s;
+  }
+  const pk_status s = pk_jones_solve(k, nq, qs.data(), np, primes.data(), zab.data(), capacity, lowest,
+                                     count, coef);
+  if (s == PK_ENOMEM) return fail(ctx, s, "coefficient buffer too small");
+  if (s != PK_OK) return fail(ctx, s, "coefficient system singular or inconsistent, or beyond 64 bits");
   return PK_OK;
 }
 

@@ -35,6 +35,10 @@ struct pk_plan {
 };
 
 namespace pk {
+// Z(q) of `p` modulo `prime` into the 8 bytes at d_sum (exact.cu); program uploaded in
+// `ws`, tensors in `arena` (complex64 layout).
+cudaError_t launch_exact(const Plan& p, uint32_t prime, void* ws, void* arena, void* d_sum,
+                         cudaStream_t stream);
 // Enqueue every kernel of every slice of `p` at `precision` on `stream` (launch.cu);
 // `ws` holds the plan state (bytes [0, off_arena)), `arena` the tensors.
 cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,

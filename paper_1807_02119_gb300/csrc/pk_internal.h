@@ -65,10 +65,23 @@ struct Slot {
   int32_t dimpos;          // position (stride q^dimpos) in the tensor, or -1 if sliced
   int32_t slice_ord;       // ordinal among sliced indices (valid when dimpos < 0)
   int32_t absorbed;        // 1: clause matrix, 0: COPY leg
-  int32_t pad;
+  int32_t pad;             // absorbed, standard weights: slot_exact_pack(mult, signsum)
   double dre, dim;         // clause diagonal when absorbed
   double ore, oim;         // clause off-diagonal when absorbed
 };
+
+// Exact form of an absorbed clause diagonal under the standard weights: the product of
+// `mult` Tait-edge diagonals -t^-eps with sum of signs `signsum` is (-1)^mult t^-signsum.
+inline int32_t slot_exact_pack(int32_t mult, int32_t signsum) {
+  return (int32_t)(((uint32_t)(signsum & 0xFFFF) << 16) | (uint32_t)(mult & 0xFFFF));
+}
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline void slot_exact_unpack(int32_t pad, int32_t& mult, int32_t& signsum) {
+  mult = pad & 0xFFFF;
+  signsum = (int32_t)(int16_t)((uint32_t)pad >> 16);
+}
 
 enum KernelKind : int32_t { KROWS = 0, KSPLITK = 1, KGEMM = 2 };
 
@@ -244,6 +257,7 @@ struct Plan {
   std::vector<int32_t> sliced;       // sliced index ids
   int64_t n_slices = 1;
   Scaled factor;                     // constant factors (loops), applied on the host
+  int32_t loop_count = 0, loop_signsum = 0;  // the same factor exactly: prod of -t^-eps
   int32_t final_tensor = -1;
   // stats
   int32_t max_rank = 0;
@@ -305,5 +319,16 @@ void clause_diag(int32_t q, int32_t mult, int32_t signsum, double& re, double& i
 void t_of_q_value(int32_t q, double& re, double& im);  // t(q) of Eq. potts2jones
 bool jones_defined(const Knot& k);  // A(q)'s exponent condition (knots: 4 | num, links: 2 | num)
 Scaled jones_prefactor(const Knot& k, int32_t q);  // A(q) in its integer-exponent form
+
+// Exact coefficients of V (jones_exact.cpp): the exponent window of a knot's V from its PD
+// code; V(t(q)) mod p from Z(q) mod p; the coefficients mod p from values at several q;
+// the signed integers from residues (the last prime checks).
+bool jones_window(const Knot& k, int32_t& lo, int32_t& hi);
+void jones_value_mod(const Knot& k, int32_t q, uint32_t p, uint32_t za, uint32_t zb, uint32_t& va,
+                     uint32_t& vb);
+bool solve_coefficients_mod(const std::vector<int32_t>& qs, const std::vector<uint32_t>& vals, int32_t lo,
+                            int32_t m, uint32_t p, std::vector<uint32_t>& c);
+bool crt_signed(const std::vector<uint32_t>& primes, const std::vector<std::vector<uint32_t>>& res,
+                std::vector<int64_t>& out);
 
 }  // namespace pk

@@ -147,6 +147,7 @@ struct SlotSpec {
   int32_t absorbed;  // 1 = clause matrix, 0 = COPY leg
   double dre, dim;   // clause diagonal
   double ore, oim;   // clause off-diagonal
+  int32_t mult = 0, signsum = 0;  // standard weights: diagonal (-1)^mult t^-signsum exactly
 };
 struct NetTensor {
   std::vector<int32_t> dims;  // index ids (initial layout: sorted ascending, outermost first)
@@ -164,6 +165,7 @@ struct Network {
   int32_t n_idx = 0;
   std::vector<NetTensor> t;
   Scaled factor = s_from(1, 0);
+  std::array<int32_t, 2> loops{0, 0};  // folded loops: count, sum of their Tait signs
   std::vector<Merged> groups;  // spin networks: the merged edge groups, in tensor order
 };
 
@@ -180,7 +182,7 @@ std::array<double, 4> std_weight(int32_t q, int32_t eps) {
 // networks keep every group as a tensor so that each edge weight has an adjoint.
 void merge_edges(const Knot& k, int32_t q, bool general, bool std_w,
                  const std::vector<std::array<double, 4>>& w, std::vector<Merged>& out,
-                 Scaled& factor) {
+                 Scaled& factor, std::array<int32_t, 2>* loops = nullptr) {
   std::map<std::pair<int32_t, int32_t>, Merged> m;
   for (int32_t c = 0; c < (int32_t)k.edges.size(); ++c) {
     const auto& e = k.edges[c];
@@ -188,6 +190,10 @@ void merge_edges(const Knot& k, int32_t q, bool general, bool std_w,
       double re, im;
       clause_diag(q, 1, e[2], re, im);
       factor = s_mul(factor, s_from(re, im));
+      if (loops) {
+        (*loops)[0] += 1;
+        (*loops)[1] += e[2];
+      }
       continue;
     }
     auto key = std::make_pair(std::min(e[0], e[1]), std::max(e[0], e[1]));
@@ -234,7 +240,7 @@ void merge_edges(const Knot& k, int32_t q, bool general, bool std_w,
 void spin_network(const Knot& k, int32_t q, bool general, bool std_w,
                   const std::vector<std::array<double, 4>>& w, Network& net) {
   std::vector<Merged>& me = net.groups;
-  merge_edges(k, q, general, std_w, w, me, net.factor);
+  merge_edges(k, q, general, std_w, w, me, net.factor, &net.loops);
   net.n_idx = k.n_v;
   std::vector<char> covered(k.n_v, 0);
   for (int32_t gi = 0; gi < (int32_t)me.size(); ++gi) {
@@ -244,7 +250,7 @@ void spin_network(const Knot& k, int32_t q, bool general, bool std_w,
       t.dims = {e.u};
     else
       t.dims = {e.u, e.v};
-    t.slots = {{e.u, 0, 0, 0, 0, 0}, {e.v, 1, e.dre, e.dim, e.ore, e.oim}};
+    t.slots = {{e.u, 0, 0, 0, 0, 0}, {e.v, 1, e.dre, e.dim, e.ore, e.oim, e.mult, e.signsum}};
     t.group = gi;
     covered[e.u] = covered[e.v] = 1;
     net.t.push_back(t);
@@ -257,13 +263,13 @@ void edge_network(const Knot& k, int32_t q, Network& net) {
   std::vector<Merged> me;
   std::vector<std::array<double, 4>> w;
   for (const auto& e : k.edges) w.push_back(std_weight(q, e[2]));
-  merge_edges(k, q, false, true, w, me, net.factor);
+  merge_edges(k, q, false, true, w, me, net.factor, &net.loops);
   net.n_idx = (int32_t)me.size();
   std::vector<NetTensor> vt(k.n_v);
   for (int32_t i = 0; i < (int32_t)me.size(); ++i) {
     const auto& e = me[i];
     vt[e.u].dims.push_back(i);
-    vt[e.u].slots.push_back({i, 1, e.dre, e.dim, e.ore, e.oim});
+    vt[e.u].slots.push_back({i, 1, e.dre, e.dim, e.ore, e.oim, e.mult, e.signsum});
     vt[e.v].dims.push_back(i);
     vt[e.v].slots.push_back({i, 0, 0, 0, 0, 0});
   }
@@ -1041,6 +1047,8 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   Network& net = best_net;
   Greedy& g = best_g;
   p.factor = net.factor;
+  p.loop_count = net.loops[0];
+  p.loop_signsum = net.loops[1];
   p.n_idx = net.n_idx;
   p.n_init = (int32_t)net.t.size();
   const int32_t n_tens = (int32_t)g.seq.sets.size();
@@ -1188,6 +1196,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
       sl.dim = ss.dim;
       sl.ore = ss.ore;
       sl.oim = ss.oim;
+      if (ss.absorbed) sl.pad = slot_exact_pack(ss.mult, ss.signsum);
       p.slots.push_back(sl);
     }
     p.recipes.push_back(r);

@@ -1,0 +1,75 @@
+"""The Jones polynomial's coefficients by interpolation between exact values at integer q
+(the conclusions' extension), host stages on the CPU: pk_jones_plan / pk_jones_solve fed
+with the oracle's exact Z(q) in Z[t] reduced modulo the library's primes must give the
+Kauffman bracket's polynomial; bad data must be refused, not rounded."""
+import pytest
+
+import knotgen as kg
+import oracle
+import paper_1807_02119_gb300 as pk
+from oracle.kauffman import jones_poly
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return pk.Context(-1)
+
+
+def _residues(pd, outer, qs, primes):
+    g = oracle.tait_graph(pd, outer=outer)
+    rows = []
+    for q in qs:
+        a, b = oracle.z_exact(g.n_v, g.edges, q)      # Z(q) = a + b t exactly
+        rows.append([(a % p, b % p) for p in primes])
+    return rows
+
+
+def _cases():
+    out = [(kg.braid_closure_pd(w, n), None) for w, n in
+           (([1, 1, 1], 2), ([-1, -1, -1], 2), ([1, -2, 1, -2], 3), ([1] * 5, 2), ([1] * 7, 2),
+            ([1, 2] * 4, 3), ([1, 2, 3] * 5, 4))]
+    out.append((kg.kink(kg.braid_closure_pd([1, 1, 1], 2), 0, 1), None))
+    for s in range(6):
+        gk = kg.random_grid_knot(10, 100 + s, True, 8, 16)
+        out.append((gk.pd, gk.outer))
+    return out
+
+
+@pytest.mark.parametrize("i", range(14))
+def test_solve_matches_bracket(ctx, i):
+    pd, outer = _cases()[i]
+    k = pk.Knot.from_pd(ctx, pd, outer=outer)
+    qs, primes = pk.jones_plan(k)
+    assert qs == list(range(1, len(qs) + 1)) and len(primes) == 4
+    assert 2 * len(qs) <= k.info()["n_c"] + 1 + 5      # span <= crossings
+    got = pk.jones_solve(k, qs, primes, _residues(pd, outer, qs, primes))
+    assert got == jones_poly(pd)
+
+
+def test_unknot_and_kinks(ctx):
+    for pd in ([], kg.kink([], 0, 0), kg.kink(kg.kink([], 0, 0), 1, 2)):
+        k = pk.Knot.from_pd(ctx, pd)
+        qs, primes = pk.jones_plan(k)
+        assert pk.jones_solve(k, qs, primes, _residues(pd, None, qs, primes)) == {0: 1}
+
+
+def test_inconsistent_data_is_refused(ctx):
+    pd = kg.braid_closure_pd([1] * 5, 2)
+    k = pk.Knot.from_pd(ctx, pd)
+    qs, primes = pk.jones_plan(k)
+    rows = _residues(pd, None, qs, primes)
+    rows[-1][0] = ((rows[-1][0][0] + 1) % primes[0], rows[-1][0][1])   # one wrong residue
+    with pytest.raises(pk.PkError):
+        pk.jones_solve(k, qs, primes, rows)
+    rows = _residues(pd, None, qs, primes)
+    rows[0][3] = ((rows[0][3][0] + 7) % primes[3], rows[0][3][1])      # the check prime disagrees
+    with pytest.raises(pk.PkError):
+        pk.jones_solve(k, qs, primes, rows)
+
+
+def test_links_and_graphs_are_refused(ctx):
+    pd, signs, _ = kg.braid_closure_link([1, 1], 2)
+    with pytest.raises(pk.PkError):
+        pk.jones_plan(pk.Knot.from_link_pd(ctx, pd, signs))
+    with pytest.raises(pk.PkError):
+        pk.jones_plan(pk.Knot.from_signed_graph(ctx, 2, [(0, 1, 1), (0, 1, 1), (0, 1, 1)], 3))
