@@ -243,7 +243,8 @@ pk_status pk_launch_arena(pk_ctx* ctx, const pk_plan* p, int32_t precision, void
  *         1: the step records; 2: per tensor (arena element offset, elements) int64
  *         pairs; 3: int64 scalars (q, n_init, n_steps, n_slices, n_sliced,
  *         final_tensor, off_recipe, off_slots, n_slots, sizeof step record,
- *         tail_first, n_tail, n_widen, off_widen, final tail offset);
+ *         tail_first, n_tail, n_widen, off_widen, final tail offset, folded loops,
+ *         their sum of Tait signs);
  *         4: three doubles (re, im, exp2) of the constant factor (loops of the graph)
  *         that multiplies the contracted value; 5: the complex128 tail-step records
  *         of PK_SPLIT.

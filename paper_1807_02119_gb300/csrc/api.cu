@@ -335,11 +335,11 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
     buf.resize(8 * v.size());
     if (!v.empty()) std::memcpy(buf.data(), v.data(), buf.size());
   } else if (which == 3) {
-    int64_t v[15] = {P.q, P.n_init, (int64_t)P.steps.size(), P.n_slices, (int64_t)P.sliced.size(),
+    int64_t v[17] = {P.q, P.n_init, (int64_t)P.steps.size(), P.n_slices, (int64_t)P.sliced.size(),
                      P.final_tensor, (int64_t)P.off_recipe, (int64_t)P.off_slots,
                      (int64_t)P.slots.size(), (int64_t)sizeof(pk::Step), P.tail_first,
                      (int64_t)P.tail.size(), (int64_t)P.conv.size(), (int64_t)P.off_conv,
-                     P.final_tail_off};
+                     P.final_tail_off, P.loop_count, P.loop_signsum};
     buf.resize(sizeof(v));
     std::memcpy(buf.data(), v, sizeof(v));
   } else if (which == 5) {

@@ -269,3 +269,101 @@ def replay_grad(plan):
     emax = max((e + math.frexp(abs(v))[1] for v, e in total if v != 0), default=0)
     z = sum(v * 2.0 ** (e - emax) for v, e in total)
     return (complex(z), emax), acc[:n_leaves], acc_exp[:n_leaves]
+
+
+def _ring_mul(x, y, p, qm2):
+    """(a + b t)(c + d t) in F_p[t]/(t^2 - (q-2) t + 1), elementwise on int64 arrays."""
+    a, b = x
+    c, d = y
+    ac, bd = (a * c) % p, (b * d) % p
+    cross = ((a * d) % p + (b * c) % p) % p
+    return (ac - bd) % p, (cross + (qm2 * bd) % p) % p
+
+
+def _tpow(n, p, qm2):
+    """t^n as a pair of ints (t^-1 = (q-2) - t)."""
+    base = (0, 1) if n >= 0 else (qm2, p - 1)
+    res = (1, 0)
+    m = abs(n)
+    while m:
+        if m & 1:
+            res = tuple(int(v) for v in _ring_mul(res, base, p, qm2))
+        base = tuple(int(v) for v in _ring_mul(base, base, p, qm2))
+        m >>= 1
+    return res
+
+
+def replay_exact(plan, p):
+    """Z(q) mod p as (a, b), Z = a + b t, following the records the exact kernels read:
+    recipes with the packed exact clause data (Slot.pad: mult, signsum), every step
+    through its stride runs, the slices, then the folded loops' factor."""
+    sc = np.frombuffer(plan.debug_blob(3), dtype=np.int64)
+    q, n_init, n_steps, n_slices, n_sliced, final_t, off_rec, off_slots, n_slots, step_sz = \
+        [int(v) for v in sc[:10]]
+    loop_count, loop_sign = int(sc[15]), int(sc[16])
+    prog = plan.debug_blob(0)
+    recs = [Recipe.from_buffer_copy(prog, off_rec + i * C.sizeof(Recipe)) for i in range(n_init)]
+    slots = [Slot.from_buffer_copy(prog, off_slots + i * C.sizeof(Slot)) for i in range(n_slots)]
+    sb = plan.debug_blob(1)
+    steps = [Step.from_buffer_copy(sb, i * C.sizeof(Step)) for i in range(n_steps)]
+    tinfo = np.frombuffer(plan.debug_blob(2), dtype=np.int64).reshape(-1, 2)
+    arena_n = int((tinfo[:, 0] + tinfo[:, 1]).max())
+    qm2 = (q - 2) % p
+    total = (0, 0)
+    for sl in range(n_slices):
+        sdig, s = [], sl
+        for _ in range(n_sliced):
+            sdig.append(s % q)
+            s //= q
+        A_ = np.zeros(arena_n, dtype=np.int64)
+        B_ = np.zeros(arena_n, dtype=np.int64)
+        for r in recs:
+            e = np.arange(r.elems, dtype=np.int64)
+            if r.kind == 1:
+                va, vb = np.ones(r.elems, dtype=np.int64), np.zeros(r.elems, dtype=np.int64)
+            else:
+                va, vb = np.zeros(r.elems, dtype=np.int64), np.zeros(r.elems, dtype=np.int64)
+                for spin in range(q):
+                    pa, pb = np.ones(r.elems, dtype=np.int64), np.zeros(r.elems, dtype=np.int64)
+                    for j in range(r.nslot):
+                        sl_ = slots[r.slot0 + j]
+                        x = (e // q ** sl_.dimpos) % q if sl_.dimpos >= 0 else \
+                            np.full(r.elems, sdig[sl_.slice_ord])
+                        if sl_.absorbed:
+                            mult = sl_.pad & 0xFFFF
+                            sign = ((sl_.pad >> 16) & 0xFFFF)
+                            sign = sign - 0x10000 if sign >= 0x8000 else sign
+                            dg = _tpow(-sign, p, qm2)
+                            if mult & 1:
+                                dg = ((-dg[0]) % p, (-dg[1]) % p)
+                            na, nb = _ring_mul((pa, pb), (np.int64(dg[0]), np.int64(dg[1])), p, qm2)
+                            pa, pb = np.where(x == spin, na, pa), np.where(x == spin, nb, pb)
+                        else:
+                            pa, pb = np.where(x == spin, pa, 0), np.where(x == spin, pb, 0)
+                    va, vb = (va + pa) % p, (vb + pb) % p
+            A_[r.offset:r.offset + r.elems] = va
+            B_[r.offset:r.offset + r.elems] = vb
+        for st in steps:
+            oa, ob = _offsets(st.R, st.row, st.nrow)
+            ka, kb = _offsets(st.K, st.kr, st.nk)
+            _, nb = _offsets(st.N, st.nr, st.nn)
+            ca = np.zeros((st.N, st.R), dtype=np.int64)
+            cb = np.zeros((st.N, st.R), dtype=np.int64)
+            for k in range(st.K):
+                ia = st.off_a + oa + ka[k]
+                xa, xb = A_[ia][None, :], B_[ia][None, :]
+                if st.b >= 0:
+                    ib = st.off_b + ob[None, :] + kb[k] + nb[:, None]
+                    pa, pb = _ring_mul((xa, xb), (A_[ib], B_[ib]), p, qm2)
+                else:
+                    pa, pb = xa, xb
+                ca, cb = (ca + pa) % p, (cb + pb) % p
+            A_[st.off_c:st.off_c + st.N * st.R] = ca.reshape(-1)
+            B_[st.off_c:st.off_c + st.N * st.R] = cb.reshape(-1)
+        off = int(tinfo[final_t, 0])
+        total = ((total[0] + int(A_[off])) % p, (total[1] + int(B_[off])) % p)
+    f = _tpow(-loop_sign, p, qm2)
+    if loop_count & 1:
+        f = ((-f[0]) % p, (-f[1]) % p)
+    z = _ring_mul((np.int64(total[0]), np.int64(total[1])), (np.int64(f[0]), np.int64(f[1])), p, qm2)
+    return int(z[0]), int(z[1])

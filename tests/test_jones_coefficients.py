@@ -73,3 +73,41 @@ def test_links_and_graphs_are_refused(ctx):
         pk.jones_plan(pk.Knot.from_link_pd(ctx, pd, signs))
     with pytest.raises(pk.PkError):
         pk.jones_plan(pk.Knot.from_signed_graph(ctx, 2, [(0, 1, 1), (0, 1, 1), (0, 1, 1)], 3))
+
+
+def _sliced(ctx, k, q):
+    lim = pk.Plan(ctx, k, q).stats()["log2_max_elems"]
+    while lim > 1.0:
+        lim -= 0.5
+        p = pk.Plan(ctx, k, q, max_log2_elems=lim)
+        if p.stats()["n_slices"] > 1:
+            return p if p.stats()["n_slices"] <= 243 else None
+    return None
+
+
+def test_exact_records_replay_matches_oracle(ctx):
+    """The records the exact kernels read (recipes with the packed clause data, steps,
+    slices, the folded loops' factor), replayed modulo p, give the oracle's exact Z(q) for
+    every q the interpolation uses (1 .. n_q, including q = 1 and 4), every order, and
+    sliced plans."""
+    from plan_replay import replay_exact
+    p = 2147483629
+    cases = [(kg.braid_closure_pd([1, 1, 1], 2), None),
+             (kg.kink(kg.braid_closure_pd([1, -2, 1, -2], 3), 0, 1), None)]
+    for s in range(2):
+        gk = kg.random_grid_knot(10, 300 + s, True, 10, 18)
+        cases.append((gk.pd, gk.outer))
+    for pd, outer in cases:
+        k = pk.Knot.from_pd(ctx, pd, outer=outer)
+        g = oracle.tait_graph(pd, outer=outer)
+        qs, _ = pk.jones_plan(k)
+        for q in qs:
+            a, b = oracle.z_exact(g.n_v, g.edges, q)
+            want = (a % p, b % p)
+            plans = [pk.Plan(ctx, k, q, order=o) for o in ("auto", "greedy_edge", "elim_spin")]
+            if q in (3, 5):
+                sp = _sliced(ctx, k, q)
+                if sp is not None:
+                    plans.append(sp)
+            for pl in plans:
+                assert replay_exact(pl, p) == want, (len(pd), q)
