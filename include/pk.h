@@ -337,30 +337,32 @@ pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_sc
 pk_status pk_eval_exact(pk_ctx* ctx, const pk_plan* p, const uint32_t* primes, int32_t n_primes,
                         void* d_workspace, uint64_t workspace_bytes, uint32_t* zab);
 
-/* All coefficients of V_K(t) for a knot given by its PD code, by interpolation between
- * exact values at integer q = 1, 2, ...: the exponent window comes from the all-A and
- * all-B smoothings (span <= crossings); each q adds two linear equations (the t^0 and t^1
- * parts of V(t(q)) in Z[t]/(t^2 - (q-2) t + 1)), solved modulo four primes near 2^31
- * (Z(q) mod p from pk_eval_exact) and lifted to signed 64-bit integers by the Chinese
- * remainder theorem with the fourth prime as a check.  On return V = sum_j coef[j]
- * t^(lowest + j), j < count (count <= capacity, else PK_ENOMEM with count set).  Plans
- * for q up to about crossings/2 + 3 are built and evaluated: feasible while those fit.
- * Errors: PK_EINVAL (no PD code, a link, a singular or inconsistent system, coefficients
- * beyond 64 bits), PK_ETOOWIDE (a plan too wide). */
+/* All coefficients of V(t) for a knot or link given by its PD code (pk_knot_from_pd or
+ * pk_link_from_pd), by interpolation between exact values at integer q = 1, 2, ...: the
+ * exponent window comes from the all-A and all-B smoothings (span <= crossings); each q
+ * adds two linear equations (the t^0 and t^1 parts of V(t(q)) in
+ * Z[t]/(t^2 - (q-2) t + 1)), solved modulo four primes near 2^31 (Z(q) mod p from
+ * pk_eval_exact) and lifted to signed 64-bit integers by the Chinese remainder theorem
+ * with the fourth prime as a check.  On return V = sum_j coef[j] t^(lowest + j + half/2),
+ * j < count (count <= capacity, else PK_ENOMEM with count set); *half = 1 when V has
+ * half-integer powers (links with an even number of components; the system is then
+ * solved for V t^(-1/2)).  Plans for q up to about crossings/2 + 3 are built and
+ * evaluated: feasible while those fit.  Errors: PK_EINVAL (no PD code, a singular or
+ * inconsistent system, coefficients beyond 64 bits), PK_ETOOWIDE (a plan too wide). */
 pk_status pk_jones_coefficients(pk_ctx* ctx, const pk_knot* k, int32_t capacity, int32_t* lowest,
-                                int32_t* count, int64_t* coef);
+                                int32_t* count, int64_t* coef, int32_t* half);
 
 /* The two host stages of pk_jones_coefficients (no GPU needed).  pk_jones_plan: the
  * values of q (n_q of them, 1 .. n_q, into qs if not NULL) and the four moduli (into
  * primes if not NULL) the knot's exponent window needs.  pk_jones_solve: the coefficients
  * from zab[2 (iq n_primes + ip) + {0, 1}] = (a, b), Z(qs[iq]) = a + b t mod primes[ip]
  * (as pk_eval_exact gives them); the last modulus checks the reconstruction.  Errors:
- * PK_EINVAL (no PD code, a link, bad moduli, a singular or inconsistent system,
- * coefficients beyond 64 bits), PK_ENOMEM (capacity; count set). */
+ * PK_EINVAL (no PD code, bad moduli, a singular or inconsistent system, coefficients
+ * beyond 64 bits), PK_ENOMEM (capacity; count set). */
 pk_status pk_jones_plan(const pk_knot* k, int32_t* n_q, int32_t* qs, int32_t* n_primes, uint32_t* primes);
 pk_status pk_jones_solve(const pk_knot* k, int32_t n_q, const int32_t* qs, int32_t n_primes,
                          const uint32_t* primes, const uint32_t* zab, int32_t capacity, int32_t* lowest,
-                         int32_t* count, int64_t* coef);
+                         int32_t* count, int64_t* coef, int32_t* half);
 
 /* ---- reverse pass (adjoint contraction) ------------------------------------------
  *

@@ -83,10 +83,10 @@ def lib():
         "pk_knot_from_pd": [vp, P(i32), i32, i32, i32, P(vp)],
         "pk_link_from_pd": [vp, P(i32), P(i32), i32, i32, i32, P(vp)],
         "pk_eval_exact": [vp, vp, P(C.c_uint32), i32, vp, u64, P(C.c_uint32)],
-        "pk_jones_coefficients": [vp, vp, i32, P(i32), P(i32), P(i64)],
+        "pk_jones_coefficients": [vp, vp, i32, P(i32), P(i32), P(i64), P(i32)],
         "pk_jones_plan": [vp, P(i32), P(i32), P(i32), P(C.c_uint32)],
         "pk_jones_solve": [vp, i32, P(i32), i32, P(C.c_uint32), P(C.c_uint32), i32, P(i32), P(i32),
-                           P(i64)],
+                           P(i64), P(i32)],
         "pk_knot_from_signed_graph": [vp, i32, i32, P(i32), i32, P(vp)],
         "pk_knot_from_grid_walk": [vp, i32, u64, i32, i32, i32, P(vp)],
         "pk_knot_info": [vp, P(i32), P(i32), P(i32), P(i32), P(i32)],
@@ -413,15 +413,27 @@ def evaluate_exact(plan: Plan, primes, ws=None):
 
 
 def jones_polynomial(ctx: Context, knot: Knot) -> dict:
-    """pk_jones_coefficients: V_K(t) as {power of t: integer coefficient}."""
+    """pk_jones_coefficients: V(t) as {power of t: integer coefficient} (a link's half-integer
+    powers as Fractions)."""
     if ctx.device < 0:
         raise PkError(7, "jones_polynomial needs a GPU context")
     _torch_stream(ctx)
     cap = 2 * knot.info()["n_c"] + 8
     coef = (C.c_int64 * cap)()
-    lo, cnt = C.c_int32(), C.c_int32()
-    _check(lib().pk_jones_coefficients(ctx.h, knot.h, cap, C.byref(lo), C.byref(cnt), coef), ctx)
-    return {lo.value + j: coef[j] for j in range(cnt.value) if coef[j]}
+    lo, cnt, half = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().pk_jones_coefficients(ctx.h, knot.h, cap, C.byref(lo), C.byref(cnt), coef,
+                                       C.byref(half)), ctx)
+    return _poly(lo.value, cnt.value, coef, half.value)
+
+
+def _poly(lo, cnt, coef, half):
+    """{power of t: coefficient}; powers lowest + j + half/2 (Fractions when half)."""
+    from fractions import Fraction
+    out = {}
+    for j in range(cnt):
+        if coef[j]:
+            out[lo + j + Fraction(1, 2) if half else lo + j] = coef[j]
+    return out
 
 
 def jones_plan(knot: Knot):
@@ -444,10 +456,10 @@ def jones_solve(knot: Knot, qs, primes, zab) -> dict:
     z_arr = (C.c_uint32 * len(flat))(*flat)
     cap = 2 * knot.info()["n_c"] + 8
     coef = (C.c_int64 * cap)()
-    lo, cnt = C.c_int32(), C.c_int32()
+    lo, cnt, half = C.c_int32(), C.c_int32(), C.c_int32()
     _check(lib().pk_jones_solve(knot.h, nq, q_arr, npr, p_arr, z_arr, cap, C.byref(lo), C.byref(cnt),
-                                coef))
-    return {lo.value + j: coef[j] for j in range(cnt.value) if coef[j]}
+                                coef, C.byref(half)))
+    return _poly(lo.value, cnt.value, coef, half.value)
 
 
 def evaluate_noalloc(plan: Plan, precision: str = "c128"):

@@ -789,9 +789,11 @@ pk_status pk_jones_plan(const pk_knot* k, int32_t* n_q, int32_t* qs_out, int32_t
 
 pk_status pk_jones_solve(const pk_knot* k, int32_t n_q, const int32_t* qs, int32_t n_primes,
                          const uint32_t* primes, const uint32_t* zab, int32_t capacity, int32_t* lowest,
-                         int32_t* count, int64_t* coef) {
-  if (!k || n_q < 1 || !qs || n_primes < 2 || !primes || !zab || !lowest || !count || (capacity > 0 && !coef))
+                         int32_t* count, int64_t* coef, int32_t* half) {
+  if (!k || n_q < 1 || !qs || n_primes < 2 || !primes || !zab || !lowest || !count || !half ||
+      (capacity > 0 && !coef))
     return PK_EINVAL;
+  *half = pk::jones_half(k->k);
   int32_t lo = 0, hi = 0;
   if (!pk::jones_window(k->k, lo, hi)) return PK_EINVAL;
   const int32_t m = hi - lo + 1;
@@ -822,12 +824,13 @@ pk_status pk_jones_solve(const pk_knot* k, int32_t n_q, const int32_t* qs, int32
 }
 
 pk_status pk_jones_coefficients(pk_ctx* ctx, const pk_knot* k, int32_t capacity, int32_t* lowest,
-                                int32_t* count, int64_t* coef) {
-  if (!ctx || !k || !lowest || !count || (capacity > 0 && !coef)) return fail(ctx, PK_EINVAL, "bad argument");
+                                int32_t* count, int64_t* coef, int32_t* half) {
+  if (!ctx || !k || !lowest || !count || !half || (capacity > 0 && !coef))
+    return fail(ctx, PK_EINVAL, "bad argument");
   if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
   int32_t nq = 0, np = 0;
   if (pk_jones_plan(k, &nq, nullptr, &np, nullptr) != PK_OK)
-    return fail(ctx, PK_EINVAL, "coefficients need a knot given by its PD code");
+    return fail(ctx, PK_EINVAL, "coefficients need a knot or link given by its PD code");
   std::vector<int32_t> qs(nq);
   std::vector<uint32_t> primes(np);
   pk_jones_plan(k, &nq, qs.data(), &np, primes.data());
@@ -852,7 +855,7 @@ pk_status pk_jones_coefficients(pk_ctx* ctx, const pk_knot* k, int32_t capacity,
     if (s != PK_OK) return s;
   }
   const pk_status s = pk_jones_solve(k, nq, qs.data(), np, primes.data(), zab.data(), capacity, lowest,
-                                     count, coef);
+                                     count, coef, half);
   if (s == PK_ENOMEM) return fail(ctx, s, "coefficient buffer too small");
   if (s != PK_OK) return fail(ctx, s, "coefficient system singular or inconsistent, or beyond 64 bits");
   return PK_OK;

@@ -13,6 +13,9 @@
 //   * enough q give a square-or-taller system, solved by Gaussian elimination mod p;
 //   * the c_j mod several primes give the integers c_j by the Chinese remainder theorem
 //     (Garner's mixed-radix form in 128-bit arithmetic), checked against one more prime.
+// A link's V lies in t^(1/2) Z[t^(+-1)] when its A(q) exponent num = 3w + tau + 2 n_v + 2 is
+// 2 mod 4 (h = 1 below); then W = V t^(-1/2) = (-1)^(w+n_v+1) t^((num-2)/4) Z (t+1)^-(n_v+1)
+// has integer powers and is found the same way, and V's powers are W's plus 1/2.
 // The exponent window [lo, hi] follows from the Kauffman bracket's extreme states: with
 // |s_A|, |s_B| the loop counts of the all-A and all-B smoothings of the n crossings, the
 // bracket's A-degrees lie in [-n - 2(|s_B| - 1), n + 2(|s_A| - 1)], and t = A^-4 with the
@@ -74,8 +77,13 @@ uint32_t inv_mod(uint32_t x, uint32_t p) {  // p prime, x != 0
 
 }  // namespace
 
+int32_t jones_half(const Knot& k) {
+  const long long num = 3LL * k.writhe + k.tau + 2LL * k.n_v + 2;
+  return (int32_t)(((num % 4) + 4) % 4 == 2 ? 1 : 0);
+}
+
 bool jones_window(const Knot& k, int32_t& lo, int32_t& hi) {
-  if (!k.has_pd || k.components != 1) return false;
+  if (!k.has_pd || !jones_defined(k)) return false;
   const long long n = (long long)k.pd.size();
   if (n == 0) {
     lo = hi = 0;
@@ -83,9 +91,12 @@ bool jones_window(const Knot& k, int32_t& lo, int32_t& hi) {
   }
   const long long max_a = n + 2LL * (state_loops(k, true) - 1);
   const long long min_a = -n - 2LL * (state_loops(k, false) - 1);
-  // t-exponent of A-degree a after the writhe factor: e = -(a - 3w) / 4
-  lo = (int32_t)-floor_div(max_a - 3LL * k.writhe, 4);
-  hi = (int32_t)floor_div(-(min_a - 3LL * k.writhe), 4);
+  // t-exponent of A-degree a after the writhe factor: e = -(a - 3w) / 4, a multiple of 1/2
+  // for a link; W = V t^(-h/2) (h = jones_half) has integer exponents e - h/2:
+  // 4 (e - h/2) = 3w - a - 2h
+  const long long h2 = 2LL * jones_half(k);
+  lo = (int32_t)-floor_div(max_a - 3LL * k.writhe + h2, 4);
+  hi = (int32_t)floor_div(3LL * k.writhe - min_a - h2, 4);
   return lo <= hi;
 }
 
@@ -93,7 +104,8 @@ void jones_value_mod(const Knot& k, int32_t q, uint32_t p, uint32_t za, uint32_t
                      uint32_t& vb) {
   using namespace exact;
   const Ring r = make_ring(p, q);
-  const long long kk = (3LL * k.writhe + k.tau + 2LL * k.n_v + 2) / 4;
+  // V t^(-h/2) = (-1)^(w+n_v+1) t^((num - 2h)/4) Z (t+1)^-(n_v+1): an integer power of t
+  const long long kk = (3LL * k.writhe + k.tau + 2LL * k.n_v + 2 - 2LL * jones_half(k)) / 4;
   E v = emul(E{za, zb}, epow_t(kk, r), r);
   // (t + 1)^-(n_v+1) = ((q - 1 - t) / q)^(n_v+1)
   const uint32_t qinv = inv_mod((uint32_t)(q % p), p);

@@ -323,6 +323,7 @@ Scaled jones_prefactor(const Knot& k, int32_t q);  // A(q) in its integer-expone
 // Exact coefficients of V (jones_exact.cpp): the exponent window of a knot's V from its PD
 // code; V(t(q)) mod p from Z(q) mod p; the coefficients mod p from values at several q;
 // the signed integers from residues (the last prime checks).
+int32_t jones_half(const Knot& k);  // 1: V has half-integer powers (the window is of V t^-1/2)
 bool jones_window(const Knot& k, int32_t& lo, int32_t& hi);
 void jones_value_mod(const Knot& k, int32_t q, uint32_t p, uint32_t za, uint32_t zb, uint32_t& va,
                      uint32_t& vb);

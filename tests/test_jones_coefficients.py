@@ -1,7 +1,8 @@
 """The Jones polynomial's coefficients by interpolation between exact values at integer q
 (the conclusions' extension), host stages on the CPU: pk_jones_plan / pk_jones_solve fed
 with the oracle's exact Z(q) in Z[t] reduced modulo the library's primes must give the
-Kauffman bracket's polynomial; bad data must be refused, not rounded."""
+Kauffman bracket's polynomial, for knots and links; bad data must be refused, not
+rounded."""
 import pytest
 
 import knotgen as kg
@@ -67,10 +68,23 @@ def test_inconsistent_data_is_refused(ctx):
         pk.jones_solve(k, qs, primes, rows)
 
 
-def test_links_and_graphs_are_refused(ctx):
-    pd, signs, _ = kg.braid_closure_link([1, 1], 2)
-    with pytest.raises(pk.PkError):
-        pk.jones_plan(pk.Knot.from_link_pd(ctx, pd, signs))
+@pytest.mark.parametrize("word,ns", [([1, -1], 2), ([1, 1], 2), ([-1, -1], 2), ([1, 1, 1, 1], 2),
+                                     ([1] * 6, 2), ([1, 2] * 3, 3), ([1, -2, 1, 2, 2, -1, 2], 3),
+                                     ([1, 2, 3, 1, 2, 3, -2, 1], 4)])
+def test_solve_links_match_bracket(ctx, word, ns):
+    """Links: half-integer powers (an even number of components) through W = V t^(-1/2)."""
+    pd, signs, comps = kg.braid_closure_link(word, ns)
+    k = pk.Knot.from_link_pd(ctx, pd, signs)
+    g = oracle.tait_graph(pd, signs=signs)
+    qs, primes = pk.jones_plan(k)
+    rows = []
+    for q in qs:
+        a, b = oracle.z_exact(g.n_v, g.edges, q)
+        rows.append([(a % p, b % p) for p in primes])
+    assert pk.jones_solve(k, qs, primes, rows) == jones_poly(pd, signs)
+
+
+def test_graphs_are_refused(ctx):
     with pytest.raises(pk.PkError):
         pk.jones_plan(pk.Knot.from_signed_graph(ctx, 2, [(0, 1, 1), (0, 1, 1), (0, 1, 1)], 3))
 
