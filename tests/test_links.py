@@ -154,3 +154,26 @@ def test_link_input_errors(ctx):
         pk.Knot.from_link_pd(ctx, pd, [1, -1])         # inconsistent orientation
     with pytest.raises(ValueError):
         kg.braid_closure_link([1, 1], 3)               # split diagram (sigma_2 unused)
+
+
+@pytest.mark.parametrize("word,ns", [([1, 1], 2), ([1, 1, 1, 1], 2), ([1, 2] * 3, 3), ([1, -2, 1, 2, 2, -1, 2], 3)])
+def test_link_reverse_pass_host(ctx, word, ns):
+    """(1/V) dV/dt at fixed q for links: the library's host stage (its A(q) exponent is a
+    multiple of 1/2 here) on the replayed reverse program against the oracle."""
+    import numpy as np
+
+    import oracle.grad as og
+    from plan_replay import replay_grad
+    pd, signs, _ = kg.braid_closure_link(word, ns)
+    k = pk.Knot.from_link_pd(ctx, pd, signs)
+    info = k.info()
+    g = oracle.tait_graph(pd, signs=signs)
+    for q in (3, 5):
+        p = pk.Plan(ctx, k, q, grad=True, checkpoint_stride=2)
+        (zm, ze), acc, ae = replay_grad(p)
+        z = SC.of(zm, ze)
+        d, dv = pk.grad_from_accumulators(p, acc, ae, pk.Scaled(z.m.real, z.m.imag, z.e))
+        dvo = og.dlogv_dt(g.n_v, g.edges, q, g.writhe, g.tau)
+        assert (info["writhe"], info["tau"], info["n_v"]) == (g.writhe, g.tau, g.n_v)
+        assert abs(dv - dvo) <= 1e-9 * max(1.0, abs(dvo)), (word, q, dv, dvo)
+        assert np.all(np.isfinite(d))
