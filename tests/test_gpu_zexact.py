@@ -1,7 +1,8 @@
 """Exact evaluation on the GPU: Z(q) modulo primes (pk_eval_exact) against the oracle's
 exact Z in Z[t], and the full Jones polynomial (pk_jones_coefficients) against the
 Kauffman bracket (small knots) and against the oracle's exact V(t(q)) at q = 5, 6, 7
-(knots beyond the bracket's 2^n states)."""
+(knots beyond the bracket's 2^n states).  Named to be collected after the core GPU parity
+files (and before the allocation-free entry point's file, which is collected last)."""
 import time
 
 import pytest
