@@ -40,8 +40,11 @@ def _expand(arr, vars_, U):
     return a.reshape([a.shape[present.index(u)] if u in vars_ else 1 for u in U])
 
 
-def _eliminate(n_v, factors, multiply, sum_axis, normalise, max_width=None, order=None):
-    """Generic bucket elimination; `factors` is a list of (vars tuple, payload)."""
+def _eliminate(n_v, factors, multiply, sum_axis, normalise, max_width=None, order=None,
+               bucket=None):
+    """Generic bucket elimination; `factors` is a list of (vars tuple, payload).  With
+    `bucket` (a callable taking the bucket's [(payload, vars)] and the kept spins) the
+    product of the bucket's factors and the sum over the eliminated spin are one call."""
     scopes = [tuple(v) for v, _ in factors]
     payloads = [p for _, p in factors]
     alive, var_facs = _index_scopes(n_v, scopes)
@@ -67,13 +70,16 @@ def _eliminate(n_v, factors, multiply, sum_axis, normalise, max_width=None, orde
         width = max(width, len(U))
         if max_width is not None and len(U) > max_width:
             raise MemoryError(f"elimination width {len(U)} exceeds {max_width}")
-        prod = None
-        for i in idx:
-            term = (payloads[i], list(scopes[i]), U)
-            prod = multiply(prod, term)
-        newp = sum_axis(prod, U.index(v))
-        newp = normalise(newp)
         newscope = tuple(u for u in U if u != v)
+        if bucket is not None and idx:
+            newp = bucket([(payloads[i], list(scopes[i])) for i in idx], list(newscope))
+        else:
+            prod = None
+            for i in idx:
+                term = (payloads[i], list(scopes[i]), U)
+                prod = multiply(prod, term)
+            newp = sum_axis(prod, U.index(v))
+        newp = normalise(newp)
         for i in idx:
             for u in alive[i]:
                 var_facs[u].discard(i)
@@ -92,8 +98,14 @@ def _eliminate(n_v, factors, multiply, sum_axis, normalise, max_width=None, orde
     return result, width
 
 
-def z_complex(n_v, edges, q, max_width=None, order=None, return_width=False):
-    """Z(q) in complex128 with per-factor power-of-two exponents -> SC."""
+def z_complex(n_v, edges, q, max_width=None, order=None, return_width=False, sum_inside=False):
+    """Z(q) in complex128 with per-factor power-of-two exponents -> SC.
+
+    sum_inside=True forms each bucket's new factor sum_{sigma_v} prod_i f_i with one
+    numpy einsum call (a library contraction routine) instead of materialising the
+    product over all the bucket's spins first: the same sum, with arrays q times smaller,
+    so that knots of a few hundred crossings (with an order from `order.min_fill_order`)
+    stay within the host's memory."""
     diag = {+1: clause_diag(q, +1), -1: clause_diag(q, -1)}
     factors = []
     for (u, v, eps) in edges:
@@ -126,7 +138,20 @@ def z_complex(n_v, edges, q, max_width=None, order=None, return_width=False):
         _, k = math.frexp(m)
         return (arr * (2.0 ** -k), e + k)
 
-    res, width = _eliminate(n_v, factors, multiply, sum_axis, normalise, max_width, order)
+    def bucket(terms, keep):
+        label = {}   # einsum labels are small integers: number the bucket's spins
+        for _, vars_ in terms:
+            for u in vars_:
+                label.setdefault(u, len(label))
+        ops = []
+        for (arr, _), vars_ in terms:
+            ops += [arr, [label[u] for u in vars_]]
+        e = sum(ex for (_, ex), _ in terms)
+        out = np.einsum(*ops, [label[u] for u in keep], optimize="greedy")
+        return (np.asarray(out, dtype=np.complex128), e)
+
+    res, width = _eliminate(n_v, factors, multiply, sum_axis, normalise, max_width, order,
+                            bucket if sum_inside else None)
     arr, e = res
     z = SC.of(complex(np.asarray(arr).reshape(())), e)
     return (z, width) if return_width else z

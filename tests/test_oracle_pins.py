@@ -300,3 +300,45 @@ def test_q3_modulus_is_power_of_three():
         assert _is_power_of_3(a * a + a * b + b * b), (a, b)
     a, b = v_exact_as_ring(TREFOIL, 3)
     assert a * a + a * b + b * b == 3     # i sqrt 3 (Fig. 1 caption)
+
+
+# ----------------------------------------------------------------------------- min-fill orders and one-call buckets
+
+@pytest.mark.parametrize("q", [2, 3, 5])
+def test_sum_inside_matches_bruteforce(q):
+    """The one-einsum bucket step (product and sum over the eliminated spin in one
+    library call) against the literal spin sum, on random graphs with loops and parallel
+    edges, under the default order and under min-fill orders."""
+    from oracle.order import min_fill_order
+    rng = random.Random(2000 + q)
+    for trial in range(12):
+        n_v = rng.randint(1, 6 if q <= 3 else 5)
+        edges = _random_signed_graph(rng, n_v, rng.randint(0, 9))
+        zb = z_bruteforce(n_v, edges, q)
+        order, _ = min_fill_order(n_v, edges, q, seed=trial, restarts=3)
+        for o in (None, order):
+            zc = oracle.z_complex(n_v, edges, q, order=o, sum_inside=True)
+            assert rel_err(zc, SC.of(zb)) < 1e-12 or abs(zb) < 1e-12
+
+
+def test_min_fill_order_is_a_narrow_permutation():
+    """min_fill_order returns every spin once; summing in that order gives the exact Z
+    (Z[t], the default elimination) and the torus-knot closed form; and its largest
+    factor is never wider than the default min-degree order's."""
+    from oracle.order import min_fill_order
+    for pd in _grid_knots(6, 22, 700):
+        g = oracle.tait_graph(pd)
+        order, w = min_fill_order(g.n_v, g.edges, 3, seed=1, restarts=4)
+        assert sorted(order) == list(range(g.n_v))
+        _, wd = oracle.z_complex(g.n_v, g.edges, 3, return_width=True)
+        _, wm = oracle.z_complex(g.n_v, g.edges, 3, order=order, return_width=True, sum_inside=True)
+        assert wm == w and w <= wd
+        for q in (2, 3, 5):
+            ze = exact_to_complex(oracle.z_exact(g.n_v, g.edges, q), 1, q)
+            assert rel_err(oracle.z_complex(g.n_v, g.edges, q, order=order, sum_inside=True), ze) < 1e-10
+    pd = kg.braid_closure_pd(kg.torus_braid(2, 9), 2)
+    g = oracle.tait_graph(pd)
+    order, _ = min_fill_order(g.n_v, g.edges, 5)
+    v = oracle.jones_from_z(oracle.z_complex(g.n_v, g.edges, 5, order=order, sum_inside=True), g, 5)
+    want = exact_to_complex(exact_value(torus_jones(2, 9), 5), 1, 5)
+    assert rel_err(v, want) < 1e-9
