@@ -45,7 +45,10 @@ typedef enum {
   PK_ENOMEM = 3,     /* host allocation failed or workspace too small                  */
   PK_ETOOWIDE = 4,   /* plan exceeds the slicing limits                                 */
   PK_ECUDA = 5,      /* a CUDA runtime call failed                                      */
-  PK_ETIMEOUT = 6,   /* a bounded device wait gave up                                   */
+  PK_ETIMEOUT = 6,   /* a bounded device wait gave up (the tensor-core GEMM's pipeline
+                        waits); the result is invalid.  Reported by pk_download, pk_eval and
+                        pk_eval_noalloc from the evaluation's own error word, which every
+                        launch sequence clears again: later evaluations are unaffected     */
   PK_ENODEVICE = 7,  /* operation needs a GPU context (device >= 0)                     */
   PK_EZERO = 8       /* Z is zero, so log-derivatives are undefined                     */
 } pk_status;
@@ -226,6 +229,14 @@ pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_wo
 pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const void* d_workspace,
                       pk_scaled* Z, pk_scaled* V);
 
+/* Host-side last stage of pk_download, for checking it without a GPU: `record` is the
+ * 32-byte total record an evaluation leaves in its workspace (double re, double im,
+ * int64 exp2 of the contracted value, uint64 status word).  Writes Z (the value times the
+ * plan's constant factor) and V = A(q) Z (if V is not NULL).  Errors: PK_ETIMEOUT when the
+ * status word is nonzero (a bounded device wait gave up; Z is then meaningless),
+ * PK_EINVAL as pk_eval for V. */
+pk_status pk_decode_result(const pk_plan* p, const void* record, pk_scaled* Z, pk_scaled* V);
+
 /* The workspace of an evaluation is a small per-plan state (initial-tensor program,
  * per-tensor bookkeeping, slice results, split-K scratch: *state_bytes) followed by the
  * tensor arena (*arena_bytes); their sum is pk_plan_workspace_bytes.  They may also
@@ -256,10 +267,12 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
 /* Runs the kernels of pk_launch once (same stream, same workspace, recipe already
  * uploaded; d_arena NULL = the arena inside the workspace, else as pk_launch_arena)
  * with a CUDA event pair around every launch, waits, and returns per kernel
- * class c (0 build, 1 rows, 2 split-K, 3 results, 4 GEMM on CUDA cores, 5 GEMM on the
- * tensor cores): out[c] = milliseconds, out[6+c] = launches, out[12+c] = algorithmic
- * complex multiply-adds, out[18+c] = algorithmic bytes (|A| + |B| + |C| at the
- * precision's element size).  24 doubles. */
+ * class c (0 build, 1 rows: row, thread-per-output and sequence kernels, 2 split-K,
+ * 3 results, 4 GEMM on CUDA cores, 5 GEMM on the tensor cores, 6 digit conversion for
+ * the tensor-core GEMM): out[c] = milliseconds, out[7+c] = launches, out[14+c] =
+ * algorithmic complex multiply-adds, out[21+c] = algorithmic bytes (|A| + |B| + |C| at
+ * the precision's element size; for class 6 the operands it reads, |A| + |B|).
+ * 28 doubles. */
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                      uint64_t workspace_bytes, void* d_arena, uint64_t arena_bytes, double* out);
 
@@ -276,6 +289,18 @@ pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
                           pk_group** out);
 pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp);
 void pk_group_destroy(pk_group* grp);
+/* As pk_group_create, but inside the graph every kernel launch of every plan is
+ * bracketed by two CUDA event-record nodes, so one pk_group_launch measures the duration
+ * of each launch as it runs among the other plans' launches (the concurrent step, not a
+ * serialised pass).  The extra nodes cost a little time per launch: use a separate
+ * profiled group for measurement and a plain one for timing. */
+pk_status pk_group_create_profiled(pk_ctx* ctx, const pk_plan* const* plans, int32_t n,
+                                   int32_t precision, void* const* d_workspaces,
+                                   const uint64_t* workspace_bytes, pk_group** out);
+/* Waits for the context's stream, then reads the events of the last replay of a
+ * profiled group: per kernel class as pk_profile (28 doubles), the milliseconds being the
+ * sum over launches of each launch's in-replay duration.  PK_EINVAL for a plain group. */
+pk_status pk_group_profile(pk_ctx* ctx, const pk_group* grp, double* out);
 
 /* ---- batched evaluation (many knots in one launch) ------------------------------- */
 

@@ -32,7 +32,8 @@ EXPORTED = [
     "pk_batch_download", "pk_eval_batch", "pk_batch_destroy", "pk_group_create",
     "pk_group_launch", "pk_group_destroy", "pk_grad_workspace_bytes", "pk_grad",
     "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights", "pk_eval_exact",
-    "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve",
+    "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve", "pk_decode_result",
+    "pk_group_create_profiled", "pk_group_profile",
 ]
 
 
@@ -102,6 +103,7 @@ def lib():
         "pk_upload": [vp, vp, i32, vp, u64],
         "pk_launch": [vp, vp, i32, vp, u64],
         "pk_download": [vp, vp, i32, vp, P(pk_scaled), P(pk_scaled)],
+        "pk_decode_result": [vp, vp, P(pk_scaled), P(pk_scaled)],
         "pk_plan_launches": [vp, i32, P(i64)],
         "pk_jones_from_z": [vp, i32, P(pk_scaled), P(pk_scaled)],
         "pk_plan_debug_blob": [vp, i32, vp, P(u64)],
@@ -118,6 +120,8 @@ def lib():
         "pk_batch_destroy": [vp],
         "pk_group_create": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
         "pk_group_launch": [vp, vp],
+        "pk_group_create_profiled": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
+        "pk_group_profile": [vp, vp, P(C.c_double)],
         "pk_group_destroy": [vp],
         "pk_grad_workspace_bytes": [vp, i32, P(u64)],
         "pk_grad": [vp, vp, i32, vp, u64, P(pk_scaled), P(pk_scaled), P(C.c_double),
@@ -503,18 +507,35 @@ def download(plan: Plan, precision: str, ws):
     return Scaled.of(z), Scaled.of(v)
 
 
+def decode_result(plan: Plan, re: float, im: float, exp2: int, status: int = 0):
+    """pk_decode_result (host only): (status code, Z, V) from a total record as the device
+    leaves it (value (re + i im) 2^exp2 and the evaluation's error word)."""
+    import struct
+    rec = C.create_string_buffer(struct.pack("<ddqQ", re, im, exp2, status), 32)
+    z, v = pk_scaled(), pk_scaled()
+    st = lib().pk_decode_result(plan.h, rec, C.byref(z), C.byref(v))
+    return st, Scaled.of(z), Scaled.of(v)
+
+
 def profile(plan: Plan, precision: str, ws, arena=None):
     """Per kernel class (build, rows, splitk, results, gemm, gemm_tc): ms, launches, complex MACs,
     bytes of one pass of the plan's kernels, timed with CUDA events on the context's
     stream.  `arena` (optional) is a separate tensor arena as for launch_arena()."""
-    out = (C.c_double * 24)()
+    out = (C.c_double * 28)()
     ap = C.c_void_p(arena.data_ptr()) if arena is not None else None
     an = arena.numel() if arena is not None else 0
     _check(lib().pk_profile(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
                             ws.numel(), ap, an, out), plan.ctx)
-    names = ("build", "rows", "splitk", "results", "gemm", "gemm_tc")
-    return {n: {"ms": out[i], "launches": out[6 + i], "cmacs": out[12 + i], "bytes": out[18 + i]}
-            for i, n in enumerate(names)}
+    return _classes(out)
+
+
+CLASSES = ("build", "rows", "splitk", "results", "gemm", "gemm_tc", "digits")
+
+
+def _classes(out):
+    n = len(CLASSES)
+    return {c: {"ms": out[i], "launches": out[n + i], "cmacs": out[2 * n + i],
+                "bytes": out[3 * n + i]} for i, c in enumerate(CLASSES)}
 
 
 class Batch:
@@ -575,9 +596,10 @@ def evaluate_batch(plans, precision="split", ws=None):
 
 class Group:
     """pk_group: plans (each with its own uploaded workspace) replayed concurrently as
-    independent branches of one CUDA graph."""
+    independent branches of one CUDA graph.  profiled=True brackets every launch with
+    event-record nodes (pk_group_create_profiled); profile() then reads the last replay."""
 
-    def __init__(self, plans, precision, workspaces):
+    def __init__(self, plans, precision, workspaces, profiled=False):
         self.plans = list(plans)
         self.ctx = self.plans[0].ctx
         self.ws = list(workspaces)
@@ -586,12 +608,19 @@ class Group:
         warr = (C.c_void_p * n)(*[w.data_ptr() for w in self.ws])
         barr = (C.c_uint64 * n)(*[w.numel() for w in self.ws])
         h = C.c_void_p()
-        _check(lib().pk_group_create(self.ctx.h, parr, n, PRECISIONS[precision], warr, barr,
-                                     C.byref(h)), self.ctx)
+        fn = lib().pk_group_create_profiled if profiled else lib().pk_group_create
+        _check(fn(self.ctx.h, parr, n, PRECISIONS[precision], warr, barr, C.byref(h)), self.ctx)
         self.h = h
 
     def launch(self):
         _check(lib().pk_group_launch(self.ctx.h, self.h), self.ctx)
+
+    def profile(self):
+        """Per kernel class: summed in-replay launch durations (ms), launches, complex
+        multiply-adds, algorithmic bytes of the last replay."""
+        out = (C.c_double * 28)()
+        _check(lib().pk_group_profile(self.ctx.h, self.h, out), self.ctx)
+        return _classes(out)
 
     def __del__(self):
         try:

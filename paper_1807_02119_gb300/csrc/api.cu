@@ -117,6 +117,34 @@ pk_status launch_recorded(pk_ctx* ctx, const pk_plan* p, int32_t precision, void
 
 }  // namespace
 
+namespace pk {
+
+pk_status decode_total(const Plan& P, const SliceResult& r, pk_scaled* Z, pk_scaled* V,
+                       std::string& err) {
+  Scaled z;
+  z.re = r.re;
+  z.im = r.im;
+  z.e = r.exp;
+  z.norm();
+  z = s_mul(z, P.factor);
+  *Z = to_abi(z);
+  if (r.status != 0) {
+    err = "a bounded wait of the tensor-core GEMM gave up: the result is invalid (status " +
+          std::to_string(r.status) + ")";
+    return PK_ETIMEOUT;
+  }
+  if (V) {
+    if (!jones_defined(P.knot)) {
+      err = "3w + tau + 2 n_v + 2 not divisible by 4 (knot) or 2 (link)";
+      return PK_EINVAL;
+    }
+    *V = to_abi(s_mul(jones_prefactor(P.knot, P.q), z));
+  }
+  return PK_OK;
+}
+
+}  // namespace pk
+
 extern "C" {
 
 pk_status pk_ctx_create(int32_t device, void* stream, pk_ctx** out) {
@@ -490,13 +518,14 @@ struct pk_group {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int32_t n = 0;
+  std::vector<pk::Prof*> profs;   // profiled groups: the per-launch events of every branch
 };
 
-extern "C" {
+namespace {
 
-pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, int32_t precision,
-                          void* const* d_workspaces, const uint64_t* workspace_bytes,
-                          pk_group** out) {
+pk_status group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, int32_t precision,
+                       void* const* d_workspaces, const uint64_t* workspace_bytes, bool profiled,
+                       pk_group** out) {
   if (!ctx || !out || n < 0 || (n > 0 && (!plans || !d_workspaces || !workspace_bytes)) ||
       !valid_precision(precision))
     return fail(ctx, PK_EINVAL, "bad argument");
@@ -517,10 +546,17 @@ pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
       pk_group_destroy(grp);
       return s != PK_OK ? s : fail(ctx, PK_EINVAL, "null workspace");
     }
+    pk::Prof* prof = nullptr;
+    if (profiled) {
+      prof = pk::prof_new();
+      grp->profs.push_back(prof);
+    }
     e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
-    cudaError_t e1 = pk::launch_plan(plans[i]->p, precision, ws,
-                                     (char*)ws + plans[i]->p.off_arena, ctx->capture);
+    cudaError_t e1 = profiled ? pk::launch_plan_prof(plans[i]->p, precision, ws,
+                                                     (char*)ws + plans[i]->p.off_arena, ctx->capture, prof)
+                              : pk::launch_plan(plans[i]->p, precision, ws,
+                                                (char*)ws + plans[i]->p.off_arena, ctx->capture);
     cudaGraph_t child = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(ctx->capture, &child);
     e = e1 != cudaSuccess ? e1 : e2;
@@ -539,6 +575,31 @@ pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
   return PK_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, int32_t precision,
+                          void* const* d_workspaces, const uint64_t* workspace_bytes,
+                          pk_group** out) {
+  return group_create(ctx, plans, n, precision, d_workspaces, workspace_bytes, false, out);
+}
+
+pk_status pk_group_create_profiled(pk_ctx* ctx, const pk_plan* const* plans, int32_t n,
+                                   int32_t precision, void* const* d_workspaces,
+                                   const uint64_t* workspace_bytes, pk_group** out) {
+  return group_create(ctx, plans, n, precision, d_workspaces, workspace_bytes, true, out);
+}
+
+pk_status pk_group_profile(pk_ctx* ctx, const pk_group* grp, double* out) {
+  if (!ctx || !grp || !out) return fail(ctx, PK_EINVAL, "bad argument");
+  if (grp->profs.empty() && grp->n > 0) return fail(ctx, PK_EINVAL, "group was not created profiled");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = pk::prof_read(grp->profs.data(), (int)grp->profs.size(), out);
+  return e == cudaSuccess ? PK_OK : cuda_fail(ctx, e, "group profile");
+}
+
 pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp) {
   if (!ctx || !grp) return fail(ctx, PK_EINVAL, "bad argument");
   if (grp->n == 0) return PK_OK;
@@ -551,6 +612,7 @@ void pk_group_destroy(pk_group* grp) {
   if (!grp) return;
   if (grp->exec) cudaGraphExecDestroy(grp->exec);
   if (grp->graph) cudaGraphDestroy(grp->graph);
+  for (pk::Prof* p : grp->profs) pk::prof_free(p);
   delete grp;
 }
 
@@ -563,6 +625,14 @@ pk_status pk_jones_from_z(const pk_knot* k, int32_t q, const pk_scaled* Z, pk_sc
   z.e = Z->exp2;
   *V = to_abi(pk::s_mul(pk::jones_prefactor(k->k, q), z));
   return PK_OK;
+}
+
+pk_status pk_decode_result(const pk_plan* p, const void* record, pk_scaled* Z, pk_scaled* V) {
+  if (!p || !record || !Z) return PK_EINVAL;
+  pk::SliceResult r;
+  std::memcpy(&r, record, sizeof(r));
+  std::string err;
+  return pk::decode_total(p->p, r, Z, V, err);
 }
 
 pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const void* d_workspace,
@@ -579,20 +649,9 @@ pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const vo
   if (e != cudaSuccess) return cuda_fail(ctx, e, "download");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
-  pk::Scaled z;
-  z.re = ctx->pinned_result->re;
-  z.im = ctx->pinned_result->im;
-  z.e = ctx->pinned_result->exp;
-  z.norm();
-  z = pk::s_mul(z, P.factor);
-  *Z = to_abi(z);
-  if (V) {
-    pk_knot kk;
-    kk.k = P.knot;
-    pk_status s = pk_jones_from_z(&kk, P.q, Z, V);
-    if (s != PK_OK) return fail(ctx, s, "3w + tau + 2 n_v + 2 not divisible by 4 (knot) or 2 (link)");
-  }
-  return PK_OK;
+  std::string err;
+  const pk_status s = pk::decode_total(P, *ctx->pinned_result, Z, V, err);
+  return s == PK_OK ? PK_OK : fail(ctx, s, err);
 }
 
 pk_status pk_eval(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,

@@ -35,8 +35,11 @@
 //    thread cannot keep the tensor pipe busy with N = 48 MMAs) and releases each stage
 //    with tcgen05.commit; eight epilogue warps flush the S level
 //    accumulators from TMEM into float-float registers every kFlush chunks and finally
-//    store C.  Every wait is bounded: on expiry the tile is poisoned with NaN and counted
-//    in pk_tc_timeouts, so a failure shows up as a wrong result, not a hang.
+//    store C.  Every wait is bounded: on expiry the CTA sets the evaluation's error word
+//    (the status of its total result record, which the host turns into PK_ETIMEOUT),
+//    waits -- again bounded -- for its own bulk copies and MMAs still in flight, writes
+//    its tile as NaN, frees its tensor memory and exits; the other CTAs of the same
+//    evaluation see the error word and give up at once, so a failure is reported, not hung.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -117,17 +120,14 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
                : "memory");
 }
 
-}  // namespace tc
-
-__device__ int pk_tc_timeouts;  // bounded waits that expired (poisoned tiles)
-
-namespace tc {
-
-// Bounded wait for an mbarrier phase; false if it did not complete, or if another CTA
-// has already given up (then every later wait returns at once).
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+// Bounded wait for an mbarrier phase; false if it did not complete within 2^20 polls.
+// `err` is the evaluation's error word: when it is given and another role or CTA of the
+// same evaluation has already given up (err != 0), the wait returns false at once.  The
+// drain waits of the give-up path pass nullptr: they run out their own bound only.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase,
+                                          const unsigned long long* err) {
   for (int i = 0; i < (1 << 20); ++i) {
-    if ((i & 1023) == 1023 && *(volatile int*)&pk_tc_timeouts != 0) return false;
+    if (err && (i & 1023) == 1023 && *(const volatile unsigned long long*)err != 0ull) return false;
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -398,14 +398,16 @@ __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const
 // the level accumulators and store C.
 template <int S>
 __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff>* arena, Meta* meta,
-                                                             const unsigned char* scratch) {
+                                                             const unsigned char* scratch,
+                                                             unsigned long long* err) {
   using namespace tc;
   static_assert(S == kTcDigits, "digit scratch laid out for kTcDigits digits");
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ long long cm[kMc], cn[kNc];
   __shared__ long long cbase;
   __shared__ int ea[kMc], eb[kNc];
-  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full, acc_empty;
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full, acc_empty,
+      drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int bad;
   unsigned char* sm = dsm;
@@ -428,6 +430,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
     }
     mbar_init(smem_u32(&acc_full), 1);
     mbar_init(smem_u32(&acc_empty), kEpiWarps);
+    mbar_init(smem_u32(&drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid >= 64 && tid < 64 + kMc) {
@@ -469,6 +472,8 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
   float acc_h[kCw], acc_l[kCw];
 #pragma unroll
   for (int j = 0; j < kCw; ++j) acc_h[j] = acc_l[j] = 0.f;
+  long long issued = 0;   // producer: chunks whose bulk copies were started
+  long long mmas = 0;     // MMA issuer: chunks whose MMAs were issued
 
   if (warp == 0) {
     if (lane == 0) {  // producer
@@ -478,9 +483,10 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
           scratch + L.b_off + (bb * L.tiles_n + tn) * nchunks * (long long)Cfg<S>::kBChunk;
       for (long long c = 0; c < nchunks; ++c) {
         const int st = (int)(c % kStages);
-        if (c >= kStages && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c / kStages) - 1) & 1))) {
+        if (c >= kStages &&
+            !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c / kStages) - 1) & 1), err)) {
           bad = 1;
-          atomicAdd(&pk_tc_timeouts, 1);
+          atomicOr(err, 1ull);
           break;
         }
         const uint32_t dst = sm0 + st * Cfg<S>::kStage;
@@ -488,6 +494,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
         bulk_g2s(dst, asrc + c * Cfg<S>::kAChunk, Cfg<S>::kAChunk, smem_u32(&full[st]));
         bulk_g2s(dst + Cfg<S>::kAChunk, bsrc + c * Cfg<S>::kBChunk, Cfg<S>::kBChunk,
                  smem_u32(&full[st]));
+        issued = c + 1;
       }
     }
   } else if (warp == 1) {
@@ -497,10 +504,10 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
         const long long g = c / Cfg<S>::kFlush;
         const bool first = c % Cfg<S>::kFlush == 0;
         const bool last = (c + 1) % Cfg<S>::kFlush == 0 || c + 1 == nchunks;
-        if ((first && g > 0 && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((g - 1) & 1))) ||
-            !mbar_wait(smem_u32(&full[st]), (uint32_t)((c / kStages) & 1))) {
+        if ((first && g > 0 && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((g - 1) & 1), err)) ||
+            !mbar_wait(smem_u32(&full[st]), (uint32_t)((c / kStages) & 1), err)) {
           bad = 1;
-          atomicAdd(&pk_tc_timeouts, 1);
+          atomicOr(err, 1ull);
           break;
         }
         fence_after();
@@ -523,15 +530,16 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
                      (i == 0 && kk == 0) ? acc0 : 1u);
         commit(smem_u32(&empty[st]));
         if (last) commit(smem_u32(&acc_full));
+        mmas = c + 1;
       }
     }
   } else {  // epilogue warps: flush the levels every kFlush chunks
     const int quarter = warp & 3, half = (warp - 2) / 4;
     for (long long g = 0; g < ngroups; ++g) {
-      if (!mbar_wait(smem_u32(&acc_full), (uint32_t)(g & 1))) {
+      if (!mbar_wait(smem_u32(&acc_full), (uint32_t)(g & 1), err)) {
         if (lane == 0) {
           bad = 1;
-          atomicAdd(&pk_tc_timeouts, 1);
+          atomicOr(err, 1ull);
         }
         break;
       }
@@ -552,6 +560,23 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
     }
   }
   __syncthreads();
+
+  // ---- give-up path: before the tile is written and the tensor memory freed, wait (with
+  // the same bound, ignoring the error word) for this CTA's asynchronous work in flight:
+  // the bulk copies of the last chunk issued on each stage, and every MMA issued (one more
+  // commit tracks all of them).  If even these waits run out, the CTA exits regardless.
+  if (bad) {
+    if (warp == 0 && lane == 0)
+      for (long long c = issued > kStages ? issued - kStages : 0; c < issued; ++c)
+        mbar_wait(smem_u32(&full[c % kStages]), (uint32_t)((c / kStages) & 1), nullptr);
+    if (warp == 1 && lane == 0 && mmas > 0) {
+      commit(smem_u32(&drain));
+      mbar_wait(smem_u32(&drain), 0u, nullptr);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
 
   // ---- store: scale by 2^(e(m) + e(n)) and the step's normalisation, pair re / im
   float vmax = 0;

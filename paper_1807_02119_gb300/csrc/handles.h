@@ -35,6 +35,22 @@ struct pk_plan {
 };
 
 namespace pk {
+// Kernel classes of the launch-sequence timing: build, rows (row / thread-per-output /
+// sequence kernels), split-K, results, GEMM on the CUDA cores, tensor-core GEMM, digit
+// conversion for the tensor-core GEMM.
+constexpr int kNumClasses = 7;
+// Per-launch CUDA events of one recorded launch sequence (launch.cu).
+struct Prof;
+Prof* prof_new();
+void prof_free(Prof* p);
+// Per class c: out[c] summed milliseconds, out[7+c] launches, out[14+c] complex
+// multiply-adds, out[21+c] algorithmic bytes, over n recorded sequences whose events
+// have completed.
+cudaError_t prof_read(Prof* const* profs, int n, double* out);
+// launch_plan with an event pair around every launch, recorded into `prof` (which must
+// outlive any graph the launches are captured into).
+cudaError_t launch_plan_prof(const Plan& p, int32_t precision, void* ws, void* arena,
+                             cudaStream_t stream, Prof* prof);
 // Z(q) of `p` modulo `prime` into the 8 bytes at d_sum (exact.cu); program uploaded in
 // `ws`, tensors in `arena` (complex64 layout).
 cudaError_t launch_exact(const Plan& p, uint32_t prime, void* ws, void* arena, void* d_sum,

@@ -12,6 +12,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "handles.h"
 #include "kernels.cuh"
 #include "gemm_tc.cuh"
 
@@ -37,15 +38,26 @@ __global__ void __launch_bounds__(256) k_widen(const ConvRec* __restrict__ conv,
   }
 }
 
-constexpr int kNumClasses = 6;  // build, rows, split-K, results, GEMM, tensor-core GEMM
+}  // namespace
 
-// Optional per-launch timing: an event pair around every launch, summed per class.
+// Optional per-launch timing: an event pair around every launch, summed per class.  When
+// the launches are recorded into a graph, the events become event-record nodes and each
+// replay re-records them.
 struct Prof {
   double ms[kNumClasses] = {}, n[kNumClasses] = {}, cmacs[kNumClasses] = {},
          bytes[kNumClasses] = {};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   std::vector<int> cls;
+  ~Prof() {
+    for (auto& e : ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  }
 };
+
+namespace {
+
 struct Marker {
   Prof* prof;
   cudaStream_t st;
@@ -113,22 +125,25 @@ TcScratch tc_scratch_layout(const Step& s) { return tc_scratch(s.Bsz, s.M, s.N, 
 template <typename R>
 cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* partial,
                         unsigned* counter, cudaStream_t stream, Marker& mk, double by,
-                        unsigned char* tc_scratch = nullptr) {
+                        unsigned char* tc_scratch = nullptr, unsigned long long* err = nullptr) {
   const double cm = (double)s.R * (double)s.K * (double)s.N;
   const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
   cudaError_t e;
   if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
     if constexpr (std::is_same<R, ff>::value) {
-      if (s.tc && tc_scratch) {  // digits of A and B, then the tensor-core GEMM
+      if (s.tc && tc_scratch && err) {  // digits of A and B, then the tensor-core GEMM
         const TcScratch L = tc_scratch_layout(s);
-        mk.begin(5, cm, by);
+        // class 6 (digit conversion): its bytes are the operands it reads, |A| + |B|
+        mk.begin(6, 0.0, (double)sizeof(Cx<R>) * (double)(s.R * s.K + s.Bsz * s.K * s.N));
         k_digits<kTcDigits, true><<<(unsigned)(s.Bsz * L.tiles_m), tc::kConvThreads,
                                     tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
         k_digits<kTcDigits, false><<<(unsigned)(s.Bsz * L.tiles_n), tc::kConvThreads,
                                      tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
+        mk.end();
         const long long tc_tiles = L.tiles_m * L.tiles_n * s.Bsz;
+        mk.begin(5, cm, by);
         k_gemm_tc<kTcDigits><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<kTcDigits>::kSmem, stream>>>(
-            s, arena, meta, tc_scratch);
+            s, arena, meta, tc_scratch, err);
         mk.end();
         return cudaGetLastError();
       }
@@ -168,6 +183,7 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
   unsigned char* tcs = (std::is_same<R, ff>::value && p.tc_bytes > 0)
                            ? (unsigned char*)arena_base + p.tc_offset() : nullptr;
   const TinyStep* tiny = (const TinyStep*)(base + p.off_tiny);
+  unsigned long long* err = &((SliceResult*)(base + p.off_result))[p.n_slices].status;
   size_t sg = 0;
   for (int32_t i = first; i < last;) {
     while (sg < p.segments.size() && p.segments[sg].first < i) ++sg;
@@ -188,7 +204,7 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
       continue;
     }
     cudaError_t e = launch_step<R>(p.steps[i], arena, meta, partial, counters + i, stream, mk,
-                                   step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)), tcs);
+                                   step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)), tcs, err);
     if (e != cudaSuccess) return e;
     ++i;
   }
@@ -225,7 +241,11 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
   const int32_t n_steps = (int32_t)p.steps.size();
   cudaError_t e;
   for (long long sl = 0; sl < p.n_slices; ++sl) {
-    e = cudaMemsetAsync(base + p.off_meta, 0, p.off_result - p.off_meta, stream);
+    // bookkeeping and split-K tickets; the first slice also clears the slice results and
+    // the total record (its status word is the evaluation's error word)
+    const uint64_t clear = sl == 0 ? p.off_result - p.off_meta + sizeof(SliceResult) * (p.n_slices + 1)
+                                   : p.off_result - p.off_meta;
+    e = cudaMemsetAsync(base + p.off_meta, 0, clear, stream);
     if (e != cudaSuccess) return e;
     if (precision == PK_C128) {
       if ((e = launch_build<double>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
@@ -393,6 +413,44 @@ cudaError_t launch_grad(const Plan& p, int32_t precision, void* ws, cudaStream_t
   return launch_grad_impl<float>(p, (char*)ws, stream);
 }
 
+cudaError_t launch_plan_prof(const Plan& p, int32_t precision, void* ws, void* arena,
+                             cudaStream_t stream, Prof* prof) {
+  cudaError_t e = prepare_kernels();
+  if (e != cudaSuccess) return e;
+  return launch_impl(p, precision, ws, arena, stream, prof);
+}
+
+Prof* prof_new() { return new Prof(); }
+void prof_free(Prof* p) { delete p; }
+
+// Per class: summed event durations of the recorded launches (after they completed),
+// launches, complex multiply-adds, algorithmic bytes.
+cudaError_t prof_read(Prof* const* profs, int n, double* out) {
+  double ms[kNumClasses] = {}, cnt[kNumClasses] = {}, cm[kNumClasses] = {}, by[kNumClasses] = {};
+  cudaError_t err = cudaSuccess;
+  for (int j = 0; j < n; ++j) {
+    const Prof& prof = *profs[j];
+    for (size_t i = 0; i < prof.ev.size(); ++i) {
+      float t = 0;
+      cudaError_t e = cudaEventElapsedTime(&t, prof.ev[i].first, prof.ev[i].second);
+      if (e != cudaSuccess && err == cudaSuccess) err = e;
+      ms[prof.cls[i]] += t;
+    }
+    for (int c = 0; c < kNumClasses; ++c) {
+      cnt[c] += prof.n[c];
+      cm[c] += prof.cmacs[c];
+      by[c] += prof.bytes[c];
+    }
+  }
+  for (int c = 0; c < kNumClasses; ++c) {
+    out[c] = ms[c];
+    out[kNumClasses + c] = cnt[c];
+    out[2 * kNumClasses + c] = cm[c];
+    out[3 * kNumClasses + c] = by[c];
+  }
+  return err;
+}
+
 cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,
                          cudaStream_t stream, double* out) {
   cudaError_t pe = prepare_kernels();
@@ -401,20 +459,9 @@ cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena
   cudaError_t e = launch_impl(p, precision, ws, arena, stream, &prof);
   cudaError_t e2 = cudaStreamSynchronize(stream);
   if (e == cudaSuccess) e = e2;
-  for (size_t i = 0; i < prof.ev.size(); ++i) {
-    float ms = 0;
-    if (e == cudaSuccess) cudaEventElapsedTime(&ms, prof.ev[i].first, prof.ev[i].second);
-    prof.ms[prof.cls[i]] += ms;
-    cudaEventDestroy(prof.ev[i].first);
-    cudaEventDestroy(prof.ev[i].second);
-  }
-  for (int c = 0; c < kNumClasses; ++c) {
-    out[c] = prof.ms[c];
-    out[kNumClasses + c] = prof.n[c];
-    out[2 * kNumClasses + c] = prof.cmacs[c];
-    out[3 * kNumClasses + c] = prof.bytes[c];
-  }
-  return e;
+  if (e != cudaSuccess) return e;
+  Prof* one = &prof;
+  return prof_read(&one, 1, out);
 }
 
 }  // namespace pk

@@ -65,11 +65,15 @@ extern "C" pk_status pk_eval_noalloc(pk_ctx* ctx, const pk_plan* p, int32_t prec
                             " workspace bytes; pk_eval_noalloc's static scratch holds " +
                             std::to_string(kNoallocScratchBytes) + " (use pk_eval)");
   int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != ctx->device) cudaSetDevice(ctx->device);
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e == cudaSuccess && prev != ctx->device) e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess)   // the symbol lookup below must run with ctx->device current
+    return noalloc_fail(ctx, PK_ECUDA, std::string("pk_eval_noalloc: cannot make device ") +
+                                           std::to_string(ctx->device) + " current: " +
+                                           cudaGetErrorString(e));
   pk_status status = PK_OK;
   void* ws = nullptr;
-  cudaError_t e = scratch_address(ctx->device, &ws);
+  e = scratch_address(ctx->device, &ws);
   if (e == cudaSuccess && !P.program.empty())
     e = cudaMemcpyAsync(ws, P.program.data(), P.program.size(), cudaMemcpyHostToDevice,
                         ctx->stream);
@@ -83,25 +87,9 @@ extern "C" pk_status pk_eval_noalloc(pk_ctx* ctx, const pk_plan* p, int32_t prec
   if (e != cudaSuccess) {
     status = noalloc_fail(ctx, PK_ECUDA, std::string("pk_eval_noalloc: ") + cudaGetErrorString(e));
   } else {
-    pk::Scaled z;
-    z.re = ctx->pinned_result->re;
-    z.im = ctx->pinned_result->im;
-    z.e = ctx->pinned_result->exp;
-    z.norm();
-    z = pk::s_mul(z, P.factor);
-    Z->re = z.re;
-    Z->im = z.im;
-    Z->exp2 = z.e;
-    if (V) {
-      if (!pk::jones_defined(P.knot)) {
-        status = noalloc_fail(ctx, PK_EINVAL, "3w + tau + 2 n_v + 2 not divisible by 4 (knot) or 2 (link)");
-      } else {
-        pk::Scaled v = pk::s_mul(pk::jones_prefactor(P.knot, P.q), z);
-        V->re = v.re;
-        V->im = v.im;
-        V->exp2 = v.e;
-      }
-    }
+    std::string err;
+    status = pk::decode_total(P, *ctx->pinned_result, Z, V, err);
+    if (status != PK_OK) noalloc_fail(ctx, status, "pk_eval_noalloc: " + err);
   }
   if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
   return status;

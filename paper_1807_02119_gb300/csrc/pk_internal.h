@@ -124,7 +124,10 @@ struct Meta {
 struct SliceResult {
   double re, im;
   long long exp;
-  long long pad;
+  // In the total record (index n_slices) only: nonzero when a bounded device wait of this
+  // evaluation gave up (the tensor-core GEMM's pipeline waits); the value is then invalid.
+  // Cleared by the first slice's bookkeeping reset of every launch sequence.
+  unsigned long long status;
 };
 
 // Split precision: a bulk (complex64) tensor read by a complex128 tail step is copied,
@@ -296,6 +299,12 @@ struct Plan {
   std::vector<std::vector<int32_t>> leaf_dims;  // initial tensors' dims before slicing
   GradProgram grad;
 };
+
+// Host side of reading a result back: Z from the total record (normalised, times the
+// plan's constant factor) and V = A(q) Z when V is not null.  PK_ETIMEOUT (with `err` set)
+// when the record's status word is nonzero, PK_EINVAL when A(q)'s exponent condition fails.
+pk_status decode_total(const Plan& P, const SliceResult& r, pk_scaled* Z, pk_scaled* V,
+                       std::string& err);
 
 // Step descriptor for C = sum over the indices of X and Y that are not in `out` of X Y
 // (Y absent: the constant 1).  `a` is the operand with more indices (ties: X); the

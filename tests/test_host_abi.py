@@ -188,3 +188,24 @@ def test_plan_replay_split_tail_layout(ctx):
     assert p.stats()["n_slices"] > 1
     z, e = replay(p, split=True)
     assert rel_err(SC.of(z, e), _z_oracle(pd, 2)) < 1e-10
+
+
+def test_decode_result_status_word(ctx):
+    """The host side of reading a result: the total record's status word (set on the GPU
+    when a bounded wait of the tensor-core GEMM gives up) becomes PK_ETIMEOUT; a zero word
+    gives Z = value x the plan's loop factor and V = A(q) Z (Eq. JonesPotts), as
+    pk_jones_from_z computes it."""
+    k = pk.Knot.from_pd(ctx, kg.kink(kg.braid_closure_pd([1, 1, 1], 2), 0, 1))  # a loop factor
+    for q in (2, 3, 5):
+        p = pk.Plan(ctx, k, q)
+        fre, fim, fexp = __import__("struct").unpack("<3d", p.debug_blob(4))
+        st, z, v = pk.decode_result(p, 0.75, -0.25, 40, 0)
+        assert st == 0
+        want = SC.of(complex(0.75, -0.25), 40) * SC.of(complex(fre, fim), int(fexp))
+        assert rel_err(SC.of(z.mantissa, z.exp2), want) < 1e-15
+        assert v == k.jones_from_z(q, z)
+        for word in (1, 2, 1 << 40):
+            st, z2, _ = pk.decode_result(p, 0.75, -0.25, 40, word)
+            assert st == 6          # PK_ETIMEOUT: the value is not to be used
+    # the record layout the device writes: 32 bytes, status in the last 8
+    assert pk.STATUS[6] == "PK_ETIMEOUT"
