@@ -13,8 +13,14 @@ between steps.  The same workload is then run once in
 complex64 and once in complex128; the relative error of every evaluation against
 complex128 is reported.
 
---impl reference times the CPU oracle (complex128 spin elimination in numpy) on the
-host cores on a bounded sample of the same workload.
+The default line also carries the in-step roofline (one replay of the same graph with an
+event pair around every launch, read per kernel class), the CPU oracle on the host cores
+(single-core and all-core on one identical sample), and two further workloads measured on
+the same GPU: `batch` (4096 small knots in one persistent launch) and `grad` (the reverse
+pass of one 300-crossing knot).
+
+--impl reference times the CPU oracle (complex128 spin elimination in numpy, one
+evaluation per process on all host cores) on a bounded sample of the same workload.
 """
 import argparse
 import json
@@ -56,6 +62,8 @@ def parse():
     ap.add_argument("--first", type=int, default=0,
                     help="index of the first knot taken from the rank's workload (profiling subsets)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle baseline")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="omit the batch and grad workloads of the default line")
     ap.add_argument("--restarts", type=int, default=128,
                     help="min-fill restarts per plan (planning effort; plans are built once, "
                          "before the timed region, on all host cores)")
@@ -69,6 +77,8 @@ def parse():
 
 
 KNOTS_PER_RANK = 64
+METRIC = "knot evaluations per second (exact Z(q), V_K(t(q))), split-FP32 vs complex128"
+ORACLE_MAX_WIDTH = 11     # spins per oracle factor in the CPU samples (q^11 entries at most)
 
 
 def shard_seeds(rank, n=KNOTS_PER_RANK):
@@ -146,63 +156,262 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(knots, budget_s, qs, max_log2_entries=24):
-    """The oracle as it stands on a bounded sample: (evaluations, seconds, sample text).
-
-    Evaluations whose widest elimination factor would exceed 2^max_log2_entries
-    complex entries are skipped (they do not fit a bounded CPU run) and counted."""
+def _oracle_one(job):
+    """One (knot, q) evaluation by the CPU oracle in a worker process: min-fill spin
+    order (oracle.order), Z by spin elimination, V = A(q) Z.  Returns (key, seconds) or
+    (key, None) when its widest factor exceeds ORACLE_MAX_WIDTH spins."""
+    sys.path.insert(0, ROOT)
     import oracle
+    from oracle.order import min_fill_order
+    key, pd, outer, q = job
     t0 = time.perf_counter()
-    n = 0
-    skipped = 0
-    done = []
-    for gk in knots:
-        for q in qs:
-            g = oracle.tait_graph(gk.pd, outer=gk.outer)
-            try:
-                z = oracle.z_complex(g.n_v, g.edges, q,
-                                     max_width=int(max_log2_entries / math.log2(q)))
-            except MemoryError:
+    g = oracle.tait_graph(pd, outer=outer)
+    order, w = min_fill_order(g.n_v, g.edges, q, restarts=4)
+    if w > ORACLE_MAX_WIDTH:
+        return key, None
+    z = oracle.z_complex(g.n_v, g.edges, q, order=order, sum_inside=True)
+    oracle.jones_from_z(z, g, q)
+    return key, time.perf_counter() - t0
+
+
+def _oracle_pool(procs):
+    """A spawn pool of single-threaded oracle workers (numpy's BLAS held to one thread
+    per process, so `procs` is the number of cores used)."""
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    return mp.get_context("spawn").Pool(procs)
+
+
+def oracle_jobs(knots, qs):
+    return [(f"{gk.seed}@q{q}", gk.pd, gk.outer, q) for gk in knots for q in qs]
+
+
+def cpu_oracle_baseline(knots, qs, budget_s=12.0):
+    """The oracle as it stands on the host cores: a sample of the workload chosen in
+    workload order by a single-core run of about budget_s seconds, then the same sample
+    on all cores (one evaluation per process).  Evaluations too wide for the oracle
+    (> ORACLE_MAX_WIDTH spins per factor) are skipped and counted."""
+    jobs = oracle_jobs(knots, qs)
+    sample, skipped, t_single = [], 0, 0.0
+    with _oracle_pool(1) as pool:
+        t0 = time.perf_counter()
+        for job, (key, dt) in zip(jobs, pool.imap(_oracle_one, jobs)):
+            if dt is None:
                 skipped += 1
-                continue
-            oracle.jones_from_z(z, g, q)
-            n += 1
-            done.append(f"{gk.seed}@q{q}")
+            else:
+                sample.append(job)
             if time.perf_counter() - t0 > budget_s:
-                el = time.perf_counter() - t0
-                return n, el, (f"first {n} feasible (knot, q) evaluations in workload order "
-                               f"({done[0]}..{done[-1]}), {skipped} skipped as wider than "
-                               f"2^{max_log2_entries} entries")
-    el = time.perf_counter() - t0
-    return n, el, f"all {n} feasible (knot, q) evaluations, {skipped} skipped"
+                pool.terminate()
+                break
+        t_single = time.perf_counter() - t0
+    ncpu = os.cpu_count() or 1
+    with _oracle_pool(ncpu) as pool:
+        pool.map(_oracle_one, sample[:ncpu])          # workers import numpy first
+        t0 = time.perf_counter()
+        pool.map(_oracle_one, sample, chunksize=1)
+        t_all = time.perf_counter() - t0
+    n = len(sample)
+    text = (f"the first {n + skipped} (knot, q) evaluations in workload order "
+            f"({jobs[0][0]}..{sample[-1][0] if sample else '-'}), {skipped} skipped as wider "
+            f"than {ORACLE_MAX_WIDTH} spins per oracle factor; {n} timed")
+    return {"value": n / t_all, "unit": "knots/s", "cores": ncpu, "kind": "oracle",
+            "sample": text, "single_core": {"value": n / t_single, "cores": 1},
+            "all_core": {"value": n / t_all, "cores": ncpu}}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step evaluates one bounded sample of the
+    scale workload (the evaluations in workload order that fit the oracle and that an
+    all-core warm-up finished within about 6 s) on all host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     qs = tuple(int(x) for x in args.qs.split(","))
-    knots = workload(0)
-    for _ in range(args.warmup):
-        cpu_oracle_rate(knots, 1.0, qs)
-    tot_n, tot_t = 0, 0.0
-    sample = ""
-    for _ in range(args.steps):
-        n, t, sample = cpu_oracle_rate(knots, 8.0, qs)   # each step a bounded sample
-        tot_n += n
-        tot_t += t
-    v = tot_n / tot_t
-    out = {"impl": "reference", "metric": "knot evaluations per second (exact Z(q), V_K(t(q)))",
+    jobs = oracle_jobs(workload(0), qs)
+    ncpu = os.cpu_count() or 1
+    with _oracle_pool(ncpu) as pool:
+        sample, skipped = [], 0
+        t0 = time.perf_counter()
+        for job, (key, dt) in zip(jobs, pool.imap(_oracle_one, jobs)):
+            if dt is None:
+                skipped += 1
+            else:
+                sample.append(job)
+            if time.perf_counter() - t0 > 6.0:
+                break
+        for _ in range(max(0, args.warmup - 1)):
+            pool.map(_oracle_one, sample, chunksize=1)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_one, sample, chunksize=1)
+            times.append(time.perf_counter() - t0)
+    step = sum(times) / len(times)
+    v = len(sample) / step
+    text = (f"{len(sample)} (knot, q) evaluations per step: the first that fit the oracle in "
+            f"workload order ({sample[0][0]}..{sample[-1][0]}), {skipped} skipped as wider than "
+            f"{ORACLE_MAX_WIDTH} spins per factor")
+    out = {"impl": "reference", "metric": METRIC,
            "value": v, "unit": "knots/s", "n_gpus": args.gpus, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000 * step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
            "data": "synthetic",
            "config": {"workload": "scale: 64 grid-walk knots L=40, 100-400 crossings, q in {2,3,5}",
-                      "impl": "CPU oracle, numpy complex128 spin elimination"},
-           "cpu_baseline": {"value": v, "unit": "knots/s", "cores": 1, "kind": "oracle",
-                            "sample": sample + " per step"},
+                      "impl": "CPU oracle, numpy complex128 spin elimination, min-fill order, "
+                              "one evaluation per process"},
+           "cpu_baseline": {"value": v, "unit": "knots/s", "cores": ncpu, "kind": "oracle",
+                            "sample": text},
            "e2e": {"value": v, "unit": "knots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+# bound of each kernel class (see DESIGN.md's kernel table): the tensor-core GEMM by the
+# tensor pipe, the CUDA-core GEMM by its arithmetic units, everything else by HBM
+CLASS_KERNEL = {"build": "k_build", "rows": "k_rows / k_outs / k_seg (fused permute-and-contract)",
+                "splitk": "k_splitk", "results": "k_slice_result / k_sum_slices",
+                "gemm": "k_gemm (tiled strided complex GEMM, CUDA cores)",
+                "gemm_tc": "k_gemm_tc (complex GEMM on tcgen05 tensor cores, BF16 digit products)",
+                "digits": "k_digits (operand digits for k_gemm_tc)"}
+# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) as a
+# multiple of the launch's algorithmic bytes, for the kernels captured under profiles/;
+# None where no capture of the current kernel exists.
+NCU_TRAFFIC_RATIO = {}
+
+
+def roofline_blocks(classes, prec, pk_):
+    """Per kernel class of the in-step replay: achieved = algorithmic bytes (or flops)
+    per launch / average in-step launch duration, against the measured peak.  Algorithmic
+    bytes follow the step definition: e (|A| + |B| + |C|) with e = 8 for complex64 and
+    split storage, 16 for complex128 (the library counts the bytes of its storage type:
+    16 for split, so halved here)."""
+    e_scale = 0.5 if prec == "split" else 1.0
+    out = {}
+    for c, d in classes.items():
+        if d["launches"] <= 0 or d["ms"] <= 0:
+            continue
+        avg_s = d["ms"] / d["launches"] / 1e3
+        alg_bytes = d["bytes"] * e_scale / d["launches"]
+        flops = 8.0 * d["cmacs"] / d["launches"]
+        if c == "gemm_tc":
+            peak = pk_.get("bf16_tflops_sustained", pk_["bf16_tflops"]) / TC_PAIRS
+            ach = flops / avg_s / 1e12
+            blk = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                   "peak_source": f"measured sustained dense BF16 "
+                                  f"{pk_.get('bf16_tflops_sustained', pk_['bf16_tflops'])} TFLOP/s "
+                                  f"(of measured, MEASURED_PEAKS.json) / {TC_PAIRS} BF16 digit-pair "
+                                  f"products per real multiply-add"}
+        elif c == "gemm" and prec != "c128":
+            peak = FP32_ISSUE_TOPS / FF_INSTR_PER_CMAC * 8 if prec == "split" else FP32_CORE_TFLOPS
+            ach = flops / avg_s / 1e12
+            blk = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                   "peak_source": "derived from 152 SM x 128 FP32 lanes x 2.07 GHz"}
+        else:
+            peak = pk_["hbm_gbs"]
+            ach = alg_bytes / avg_s / 1e9
+            blk = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                   "peak_source": "measured copy bandwidth (of measured, MEASURED_PEAKS.json hbm_gbs)"}
+        ratio = NCU_TRAFFIC_RATIO.get(c)
+        blk.update({"frac": ach / peak, "kernel": CLASS_KERNEL[c],
+                    "traffic": ratio * d["bytes"] / d["launches"] if ratio else None,
+                    "launches": d["launches"], "avg_launch_us": 1e6 * avg_s,
+                    "in_step_ms": d["ms"], "alg_bytes_per_launch": alg_bytes,
+                    "flops_per_launch": flops,
+                    "units": "algorithmic bytes e(|A|+|B|+|C|), e = 8 (complex64 / split) or 16 "
+                             "(complex128); flops = 8 per complex multiply-add"})
+        out[c] = blk
+    dom = max(out, key=lambda c: out[c]["in_step_ms"])
+    return dict(out[dom], kernel_class=dom), out
+
+
+def batch_workload(pk, ctx, stream, flush, args):
+    """4096 grid-walk knots of 18..122 crossings at q = 3 in ONE persistent launch (a CUDA
+    graph), split and complex128: device time per launch with inputs resident, and end to
+    end (program upload from pinned memory, the launch, the results back) per step."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    import knotgen as kg
+    knots = kg.knot_suite("batch")
+    t0 = time.perf_counter()
+    kn = [pk.Knot.from_pd(ctx, k.pd, outer=k.outer) for k in knots]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        plans = list(ex.map(lambda k: pk.Plan(ctx, k, 3), kn))
+    plan_s = time.perf_counter() - t0
+    cm = sum(p.stats()["cmacs"] for p in plans)
+    out, res = {"workload": "4096 grid-walk knots, 18-122 crossings (target uniform 20-120, L "
+                            "from the target), q=3, one persistent launch in a CUDA graph",
+                "plan_seconds": plan_s, "complex_macs_per_step": cm}, {}
+    for pr in ("split", "c128"):
+        b = pk.Batch(plans, pr)
+        nbytes, upbytes = b.workspace_bytes()
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        b.upload(ws)
+        for _ in range(max(3, args.warmup)):
+            b.launch(ws)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            b.launch(ws)
+            e.record(stream)
+            e.synchronize()
+            times.append(a.elapsed_time(e))
+        ms = sum(times) / len(times)
+        res[pr] = b.download(ws)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            b.upload(ws)
+            b.launch(ws)
+            b.download(ws)
+        e2e_ms = 1e3 * (time.perf_counter() - t1) / args.steps
+        out[pr] = {"value": len(plans) / (ms / 1e3), "unit": "knots/s", "ms_per_step": ms,
+                   "complex_tflops": 8 * cm / (ms / 1e3) / 1e12,
+                   "e2e": {"value": len(plans) / (e2e_ms / 1e3), "unit": "knots/s",
+                           "h2d_bytes_per_step": upbytes, "d2h_bytes_per_step": 32 * len(plans)}}
+        del ws, b
+        torch.cuda.empty_cache()
+    errs = [max(rel_err(z, zr), rel_err(v, vr)) for z, v, zr, vr in
+            zip(res["split"][0], res["split"][1], res["c128"][0], res["c128"][1])]
+    out["split"].update({"max_rel_err_vs_c128": max(errs),
+                         "evaluations_over_1e-6": sum(x > 1e-6 for x in errs)})
+    return out
+
+
+def grad_workload(pk, ctx, stream, args):
+    """The reverse pass of one 300-crossing grid-walk knot (L=53, seed 7) at q = 3 with
+    intermediates checkpointed every 4th tree level: Z, d log Z over every edge weight and
+    dV/dt per pk_grad call, complex128 and split; the split result against complex128."""
+    import numpy as np
+    import torch
+    import knotgen as kg
+    (gk,) = kg.knot_suite("grad")
+    k = pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer)
+    p = pk.Plan(ctx, k, 3, grad=True, checkpoint_stride=4)
+    gs = p.grad_stats()
+    out = {"workload": f"L=53 seed 7, {k.info()['n_c']} crossings, q=3, checkpoint stride 4",
+           "complex_macs_per_call": gs["cmacs_forward"] + gs["cmacs_recompute"] + gs["cmacs_adjoint"],
+           "steps_per_call": gs["steps_forward"] + gs["steps_recompute"] + gs["steps_adjoint"]}
+    res = {}
+    for pr in ("c128", "split"):
+        ws = torch.empty(p.grad_workspace_bytes(pr), dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            res[pr] = pk.grad(p, pr, ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = max(3, args.steps)
+        for _ in range(n):
+            pk.grad(p, pr, ws)
+        out[pr] = {"ms_per_call": 1e3 * (time.perf_counter() - t0) / n,
+                   "note": "host clock around blocking pk_grad calls (results on the host)"}
+        del ws
+    d128, dsp = res["c128"][2], res["split"][2]
+    out["split"]["max_rel_err_dlogz_vs_c128"] = float(np.max(np.abs(dsp - d128)) / np.max(np.abs(d128)))
+    out["split"]["rel_err_dlogv_dt_vs_c128"] = abs(res["split"][3] - res["c128"][3]) / abs(res["c128"][3])
+    return out
 
 
 def rel_err(a, b):
@@ -446,6 +655,7 @@ def main():
     log("workspaces and graph ready")
 
     # warm-up: W replays; then one sequential pass with an event pair around every launch
+    # (serialised: comparable with the shares of ncu's launch list, not with the step)
     for _ in range(args.warmup):
         group.launch()
     torch.cuda.synchronize()
@@ -495,8 +705,26 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - t1, dist, dev)
     e2e_val = job_rate(world, evals, 1000.0 * e2e_s)
     log("end-to-end pass")
-    del group, ws
+
+    # in-step profile: one replay of the same step as a graph with an event pair around
+    # every launch (event-record nodes), so each launch's duration is taken while it runs
+    # among the other plans' launches; on the same resident workspaces
+    pgroup = pk.Group(plans, prec, ws, profiled=True)
+    pgroup.launch()
+    torch.cuda.synchronize()
+    flush.zero_()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    pgroup.launch()
+    b.record(stream)
+    b.synchronize()
+    instep = pgroup.profile()
+    instep_ms = a.elapsed_time(b)
+    del pgroup, group, ws
     torch.cuda.empty_cache()
+    log("in-step profile")
+    roof, rooflines = roofline_blocks(instep, prec, peaks())
 
     # the same workload once in each other precision (same concurrent execution);
     # errors against complex128
@@ -534,68 +762,22 @@ def main():
                               "median_rel_err_vs_c128": statistics.median(errs),
                               "evaluations_over_1e-6": sum(e > 1e-6 for e in errs)})
 
-    # roofline of the dominant kernel class, from the event-timed warm-up pass
-    knames = {"gemm": "k_gemm (tiled strided complex GEMM, CUDA cores)",
-              "gemm_tc": "k_gemm_tc (complex GEMM on tcgen05 tensor cores, BF16 digit split)",
-              "rows": "k_rows (fused permute-and-contract, thread per output row)",
-              "splitk": "k_splitk", "build": "k_build", "results": "k_slice_result/k_sum_slices"}
-    dom = max(prof, key=lambda c: prof[c]["ms"])
-    rk = prof[dom]
-    pk_ = peaks()
-    flops = 8.0 * rk["cmacs"]
-    sec = rk["ms"] / 1e3
-    ai = flops / max(rk["bytes"], 1.0)           # bytes at the precision's entry size
-    if dom == "gemm_tc":
-        peak = pk_["bf16_tflops"] / TC_PAIRS
-        src = (f"measured dense BF16 {pk_['bf16_tflops']} TFLOP/s (MEASURED_PEAKS.json) / "
-               f"{TC_PAIRS} BF16 digit-pair products per real multiply-add")
-    elif prec == "split":
-        peak = FP32_ISSUE_TOPS / FF_INSTR_PER_CMAC * 8
-        src = ("derived: 152 SM x 128 FP32 lanes x 2.07 GHz FP32 instructions / 48 instructions "
-               "per float-float complex multiply-add x 8 flops")
-    elif prec == "c64":
-        peak, src = FP32_CORE_TFLOPS, "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"
-    else:
-        peak, src = FP64_TFLOPS, "nominal FP64 rate of GB300"
-    ridge = peak * 1e12 / (pk_["hbm_gbs"] * 1e9)
-    if ai > ridge:
-        ach = flops / sec / 1e12
-        roof = {"bound": "tensor" if dom == "gemm_tc" else "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "peak_source": src}
-    else:
-        ach = rk["bytes"] / sec / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": pk_["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk_["hbm_gbs"], "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-    roof.update({"kernel": knames[dom], "arith_intensity_flop_per_byte": ai,
-                 "launches_per_pass": rk["launches"], "ms_per_pass": rk["ms"],
-                 "share_of_pass": rk["ms"] / sum(v["ms"] for v in prof.values()),
-                 "flops_count": "8 real flops per complex multiply-add"})
-
-    roof_tc = None
-    if prof.get("gemm_tc", {}).get("ms", 0) > 0:  # the tensor-core GEMM class on its own roofline
-        t = prof["gemm_tc"]
-        ach_tc = 8.0 * t["cmacs"] / (t["ms"] / 1e3) / 1e12
-        peak_tc = pk_["bf16_tflops"] / TC_PAIRS
-        roof_tc = {"bound": "tensor", "achieved": ach_tc, "peak": peak_tc, "unit": "TFLOP/s",
-                   "frac": ach_tc / peak_tc, "traffic": None,
-                   "peak_source": (f"measured dense BF16 {pk_['bf16_tflops']} TFLOP/s "
-                                   f"(MEASURED_PEAKS.json) / {TC_PAIRS} digit-pair products"),
-                   "kernel": knames["gemm_tc"] + ", digit conversion included",
-                   "launches_per_pass": t["launches"], "ms_per_pass": t["ms"],
-                   "share_of_pass": t["ms"] / sum(v["ms"] for v in prof.values())}
+    extra = {}
+    if not args.skip_extra and world == 1:
+        extra["batch"] = batch_workload(pk, ctx, stream, flush, args)
+        log("batch workload")
+        extra["grad"] = grad_workload(pk, ctx, stream, args)
+        log("grad workload")
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         log("cpu baseline")
-        n, t, sample = cpu_oracle_rate(knots, 15.0, qs)
-        cpu = {"value": n / t, "unit": "knots/s", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = cpu_oracle_baseline(knots, qs)
 
     launches = sum(p.launches(prec) for p in plans) * args.steps
     tot_cmacs = sum(s["cmacs"] for s in stats)
     if rank == 0:
-        out = {"metric": "knot evaluations per second (exact Z(q), V_K(t(q))), split-FP32 vs complex128",
+        out = {"metric": METRIC,
                "value": value, "unit": "knots/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
@@ -605,11 +787,18 @@ def main():
                           "l2": "flushed between steps (512 MB write)",
                           "plan_seconds": plan_s, "complex_macs_per_step": tot_cmacs,
                           "complex_tflops": 8 * tot_cmacs / (step_ms / 1e3) / 1e12},
-               "roofline": roof, "roofline_tc": roof_tc, "cpu_baseline": cpu,
+               "roofline": roof, "rooflines_in_step": rooflines, "cpu_baseline": cpu,
                "e2e": {"value": e2e_val, "unit": "knots/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h},
-               "gpu_launches": launches, "clocks": clk, "kernel_classes": prof,
-               "precisions": compare}
+               "gpu_launches": launches, "clocks": clk,
+               "kernel_classes_in_step": {"replay_ms": instep_ms, "classes": instep,
+                                          "how": "one replay of the step's graph with an event "
+                                                 "pair around every launch; ms = sum over launches "
+                                                 "of each launch's duration"},
+               "kernel_classes_serialised": {"classes": prof,
+                                             "how": "every plan's launches one after another, "
+                                                    "an event pair around each"},
+               "precisions": compare, "workloads": extra}
         print(json.dumps(out))
     if dist:
         dist.barrier()

@@ -88,6 +88,9 @@ typedef enum {
 #define PK_FLAG_FORCE_ROWS 2 /* every step on the row kernel                               */
 #define PK_FLAG_NO_TC 8      /* PK_SPLIT: run GEMM-shaped steps on the CUDA cores (float-float
                                 SIMT kernel) instead of the tensor cores                     */
+#define PK_FLAG_TC_DIGITS4 16 /* PK_SPLIT tensor-core steps: four BF16 digits per operand
+                                (10 digit-pair products, truncation near 2^-32 of a row's and
+                                column's largest entries) instead of five (15 products, 2^-40) */
 #define PK_FLAG_GRAD 4       /* also build the reverse (adjoint) program used by pk_grad.
                                 The network then keeps every edge group as a tensor (a pair
                                 of opposite-sign parallel edges is not dropped, loops become

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpk.so")
 
 PK_C128, PK_C64, PK_SPLIT = 0, 1, 2
-FLAG_FORCE_GEMM, FLAG_FORCE_ROWS, FLAG_GRAD, FLAG_NO_TC = 1, 2, 4, 8
+FLAG_FORCE_GEMM, FLAG_FORCE_ROWS, FLAG_GRAD, FLAG_NO_TC, FLAG_TC_DIGITS4 = 1, 2, 4, 8, 16
 PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split": PK_SPLIT}
 ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4,
           "fill_spin": 5}

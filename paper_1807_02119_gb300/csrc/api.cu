@@ -425,6 +425,7 @@ void pk_plan_destroy(pk_plan* p) {
   if (p->pinned_program) cudaFreeHost(p->pinned_program);
   if (p->pinned_grad) cudaFreeHost(p->pinned_grad);
   if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
+  if (p->grad_graph.exec) cudaGraphExecDestroy(p->grad_graph.exec);
   delete p;
 }
 
@@ -703,6 +704,52 @@ pk_status pk_plan_set_weights(pk_plan* p, const double* edge_weights) {
   return PK_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The reverse-pass launch sequence recorded once per (workspace, precision) into a CUDA
+// graph on the context's capture stream and replayed afterwards; very long sequences
+// (many slices) are launched directly.
+cudaError_t launch_grad_recorded(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* ws) {
+  const pk::Plan& P = p->p;
+  const double nodes = (double)P.n_slices * (double)(P.grad.steps.size() + 4);
+  if (nodes > 20000.0) return pk::launch_grad(P, precision, ws, ctx->stream);
+  PlanGraph& g = const_cast<pk_plan*>(p)->grad_graph;
+  if (!(g.exec && g.ws == ws && g.precision == precision)) {
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    cudaError_t e = pk::prepare_kernels();
+    if (e == cudaSuccess && !ctx->capture)
+      e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e1 = pk::launch_grad(P, precision, ws, ctx->capture);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->capture, &graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return e1 != cudaSuccess ? e1 : e2;
+    }
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g.exec = nullptr;
+      return e;
+    }
+    g.ws = ws;
+    g.precision = precision;
+  }
+  return cudaGraphLaunch(g.exec, ctx->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
 pk_status pk_grad(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                   uint64_t workspace_bytes, pk_scaled* Z, pk_scaled* V, double* dlogZ_dT,
                   double* dlogV_dt) {
@@ -728,7 +775,7 @@ pk_status pk_grad(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_work
   std::memcpy(host, G.program.data(), G.program.size());  // the current weights
   char* ws = (char*)d_workspace;
   cudaError_t e = cudaMemcpyAsync(ws, host, G.program.size(), cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = pk::launch_grad(P, precision, ws, ctx->stream);
+  if (e == cudaSuccess) e = launch_grad_recorded(ctx, p, precision, ws);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(host + prog, ws + G.off_result + sizeof(pk::SliceResult) * P.n_slices,
                         sizeof(pk::SliceResult), cudaMemcpyDeviceToHost, ctx->stream);

@@ -33,6 +33,17 @@ struct BatchKnot {
   int32_t n_sliced, q, final_tensor, pad;
 };
 
+// A step of the batch image: the contraction's extents and operand offsets, with its
+// stride runs packed into the batch's run array (rows, then contracted, then columns)
+// instead of the fixed-size run tables of a Step, so the image is about ten times smaller.
+struct BatchStep {
+  int32_t a, b, c;           // bookkeeping slots relative to the knot (b = -1: constant 1)
+  int16_t nrow, nk, nn, pad;
+  int64_t off_a, off_b, off_c;
+  int64_t R, K, N;
+  int64_t run0;              // first run of this step in the run array
+};
+
 namespace {
 
 constexpr int kBatchThreads = 256;
@@ -50,11 +61,18 @@ __device__ __forceinline__ S block_max(S v, S* red) {
   return v;  // every thread holds the block maximum
 }
 
-// One pairwise step of one knot by the whole CTA (outputs spread over the threads).
+// One pairwise step of one knot by the whole CTA (outputs spread over the threads); the
+// step's runs are staged in shared memory first.
 template <typename R>
-__device__ void cta_step(const Step& s, Cx<R>* arena, Meta* meta, long long* tbl,
-                         typename Traits<R>::S* red) {
+__device__ void cta_step(const BatchStep& s, const Run* __restrict__ runs, Run* srun,
+                         Cx<R>* arena, Meta* meta, long long* tbl, typename Traits<R>::S* red) {
   using S = typename Traits<R>::S;
+  const int nruns = s.nrow + s.nk + s.nn;
+  for (int i = threadIdx.x; i < nruns; i += blockDim.x) srun[i] = runs[s.run0 + i];
+  __syncthreads();
+  const Run* row = srun;
+  const Run* kr = srun + s.nrow;
+  const Run* nr = srun + s.nrow + s.nk;
   const int ea = bin_exp(bits_to_val<S>(meta[s.a].maxbits));
   int eb = 0;
   long long xb = 0;
@@ -68,7 +86,7 @@ __device__ void cta_step(const Step& s, Cx<R>* arena, Meta* meta, long long* tbl
   const bool tab = s.K <= kKTab;
   if (tab)
     for (long long k = threadIdx.x; k < s.K; k += blockDim.x)
-      split_runs((unsigned long long)k, s.kr, s.nk, tbl[k], tbl[kKTab + k]);
+      split_runs((unsigned long long)k, kr, s.nk, tbl[k], tbl[kKTab + k]);
   __syncthreads();
   const Cx<R>* A = arena + s.off_a;
   const Cx<R>* B = arena + s.off_b;
@@ -78,8 +96,8 @@ __device__ void cta_step(const Step& s, Cx<R>* arena, Meta* meta, long long* tbl
   for (long long o = threadIdx.x; o < outs; o += blockDim.x) {
     const long long r = o % s.R, n = o / s.R;
     long long oa, ob, d, nb = 0;
-    split_runs((unsigned long long)r, s.row, s.nrow, oa, ob);
-    if (hasB) split_runs((unsigned long long)n, s.nr, s.nn, d, nb);
+    split_runs((unsigned long long)r, row, s.nrow, oa, ob);
+    if (hasB) split_runs((unsigned long long)n, nr, s.nn, d, nb);
     Acc<R> acc;
     for (long long k = 0; k < s.K; ++k) {
       long long ka, kb;
@@ -87,7 +105,7 @@ __device__ void cta_step(const Step& s, Cx<R>* arena, Meta* meta, long long* tbl
         ka = tbl[k];
         kb = tbl[kKTab + k];
       } else {
-        split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
+        split_runs((unsigned long long)k, kr, s.nk, ka, kb);
       }
       const Cx<R> av = ldc(A + oa + ka);
       if (hasB)
@@ -110,12 +128,14 @@ __device__ void cta_step(const Step& s, Cx<R>* arena, Meta* meta, long long* tbl
 template <typename R>
 __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchKnot* __restrict__ knots,
                                                          int n_knots, const Recipe* recs,
-                                                         const Slot* slots, const Step* steps,
-                                                         Cx<R>* arena, Meta* meta_all,
-                                                         SliceResult* out, unsigned* next) {
+                                                         const Slot* slots, const BatchStep* steps,
+                                                         const Run* runs, Cx<R>* arena,
+                                                         Meta* meta_all, SliceResult* out,
+                                                         unsigned* next) {
   using S = typename Traits<R>::S;
   extern __shared__ long long tbl[];
   __shared__ S red[32];
+  __shared__ Run srun[3 * kMaxRuns];
   __shared__ int kn_s;
   for (;;) {
     __syncthreads();
@@ -156,7 +176,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchKnot* __rest
         }
       }
       __syncthreads();
-      for (long long i = 0; i < K.n_steps; ++i) cta_step<R>(steps[K.step0 + i], A0, meta, tbl, red);
+      for (long long i = 0; i < K.n_steps; ++i)
+        cta_step<R>(steps[K.step0 + i], runs, srun, A0, meta, tbl, red);
       if (threadIdx.x == 0) {  // add this slice's scalar at a common exponent
         const Cx<R> v = ldc(A0 + K.final_offset);
         double vr = to_double(v.re), vi = to_double(v.im);
@@ -202,11 +223,12 @@ struct pk_batch {
   std::vector<pk::BatchKnot> knots;
   std::vector<pk::Recipe> recipes;
   std::vector<pk::Slot> slots;
-  std::vector<pk::Step> steps;
+  std::vector<pk::BatchStep> steps;
+  std::vector<pk::Run> runs;
   std::vector<pk::Knot> kinfo;
   std::vector<pk::Scaled> factor;
   std::vector<int32_t> qs;
-  uint64_t off_knots = 0, off_recipes = 0, off_slots = 0, off_steps = 0, off_meta = 0,
+  uint64_t off_knots = 0, off_recipes = 0, off_slots = 0, off_steps = 0, off_runs = 0, off_meta = 0,
            off_results = 0, off_counter = 0, off_arena = 0, total = 0, image_bytes = 0;
   std::vector<uint8_t> image;
   uint8_t* pinned = nullptr;
@@ -267,12 +289,13 @@ cudaError_t build_graph(pk_batch* b, void* ws, cudaStream_t stream) {
   int n = b->n;
   const pk::Recipe* recs = (const pk::Recipe*)(base + b->off_recipes);
   const pk::Slot* slots = (const pk::Slot*)(base + b->off_slots);
-  const pk::Step* steps = (const pk::Step*)(base + b->off_steps);
+  const pk::BatchStep* steps = (const pk::BatchStep*)(base + b->off_steps);
+  const pk::Run* runs = (const pk::Run*)(base + b->off_runs);
   void* arena = base + b->off_arena;
   pk::Meta* meta = (pk::Meta*)(base + b->off_meta);
   pk::SliceResult* res = (pk::SliceResult*)(base + b->off_results);
   unsigned* counter = (unsigned*)(base + b->off_counter);
-  void* args[] = {&knots, &n, &recs, &slots, &steps, &arena, &meta, &res, &counter};
+  void* args[] = {&knots, &n, &recs, &slots, &steps, &runs, &arena, &meta, &res, &counter};
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, pk::kBatchThreads, smem);
   if (e != cudaSuccess) return e;
@@ -333,7 +356,27 @@ pk_status pk_batch_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
     b->knots.push_back(k);
     b->recipes.insert(b->recipes.end(), P.recipes.begin(), P.recipes.end());
     b->slots.insert(b->slots.end(), P.slots.begin(), P.slots.end());
-    b->steps.insert(b->steps.end(), P.steps.begin(), P.steps.end());
+    for (const pk::Step& st : P.steps) {
+      pk::BatchStep bs;
+      std::memset(&bs, 0, sizeof(bs));
+      bs.a = st.a;
+      bs.b = st.b;
+      bs.c = st.c;
+      bs.nrow = (int16_t)st.nrow;
+      bs.nk = (int16_t)st.nk;
+      bs.nn = (int16_t)st.nn;
+      bs.off_a = st.off_a;
+      bs.off_b = st.off_b;
+      bs.off_c = st.off_c;
+      bs.R = st.R;
+      bs.K = st.K;
+      bs.N = st.N;
+      bs.run0 = (int64_t)b->runs.size();
+      b->runs.insert(b->runs.end(), st.row, st.row + st.nrow);
+      b->runs.insert(b->runs.end(), st.kr, st.kr + st.nk);
+      b->runs.insert(b->runs.end(), st.nr, st.nr + st.nn);
+      b->steps.push_back(bs);
+    }
     b->kinfo.push_back(P.knot);
     b->factor.push_back(P.factor);
     b->qs.push_back(P.q);
@@ -349,7 +392,9 @@ pk_status pk_batch_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
   b->off_slots = off;
   off = pk::a256(off + sizeof(pk::Slot) * std::max<size_t>(1, b->slots.size()));
   b->off_steps = off;
-  off = pk::a256(off + sizeof(pk::Step) * std::max<size_t>(1, b->steps.size()));
+  off = pk::a256(off + sizeof(pk::BatchStep) * std::max<size_t>(1, b->steps.size()));
+  b->off_runs = off;
+  off = pk::a256(off + sizeof(pk::Run) * std::max<size_t>(1, b->runs.size()));
   b->image_bytes = off;
   b->off_meta = off;
   off = pk::a256(off + 16ull * (uint64_t)std::max<int64_t>(1, meta));
@@ -368,7 +413,9 @@ pk_status pk_batch_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
   if (!b->slots.empty())
     std::memcpy(b->image.data() + b->off_slots, b->slots.data(), sizeof(pk::Slot) * b->slots.size());
   if (!b->steps.empty())
-    std::memcpy(b->image.data() + b->off_steps, b->steps.data(), sizeof(pk::Step) * b->steps.size());
+    std::memcpy(b->image.data() + b->off_steps, b->steps.data(), sizeof(pk::BatchStep) * b->steps.size());
+  if (!b->runs.empty())
+    std::memcpy(b->image.data() + b->off_runs, b->runs.data(), sizeof(pk::Run) * b->runs.size());
   *out = b;
   return PK_OK;
 }

@@ -4,7 +4,7 @@
 // The float-float operands carry about 48 significant bits, far more than a BF16 product,
 // so each operand is cut into S signed 8-bit digits (the splitting idea of Ozaki et al.,
 // "Error-free transformations of matrix multiplication", Numer. Algorithms 2012):
-// with e(m) the binary exponent of row m's largest entry (over all of K),
+// with e(m) the binary exponent of row m's largest entry (over one flush group of K),
 //     x 2^-e(m) = sum_i d_i 2^(-7-8i) + r,   d_i integers, |d_i| <= 128,  |r| <= 2^(-8S-7),
 // and likewise for the columns of B.  A digit is exact in BF16 (8 significant bits), a
 // digit product (|d_a d_b| <= 2^14) is exact, and a sum of such products stays exact in
@@ -12,18 +12,20 @@
 // accumulated together, and every level is flushed to float-float registers before
 // (L + 1) K' 2^14 can reach 2^24.  Levels L >= S are dropped (their weight is at most
 // 2^(-8S) of the leading term); the result is
-//     C(m, n) = 2^(e(m) + e(n)) sum_{L < S} acc_L(m, n) 2^(-14-8L).
+//     C(m, n) = sum_groups 2^(e_g(m) + e_g(n)) sum_{L < S} acc_{g,L}(m, n) 2^(-14-8L),
+// each group's exponents applied (exactly: powers of two) when its levels are flushed.
 //
-// Complex arithmetic as one real product: with the rows of C interleaved (re, im),
-//     [re row m] = [Re A(m,:), -Im A(m,:)] . [Re B; Im B],
-//     [im row m] = [Im A(m,:),  Re A(m,:)] . [Re B; Im B],
-// so a CTA tile of 64 complex rows x 48 complex columns is one M=128, N=48 MMA per
-// BF16 K-step of 16 (K' = 2 K).
+// Complex arithmetic as one real product: with the columns of C interleaved (re, im),
+//     [re column n] = [Re A(m,:), Im A(m,:)] . [ Re B(:,n); -Im B(:,n)],
+//     [im column n] = [Re A(m,:), Im A(m,:)] . [ Im B(:,n);  Re B(:,n)],
+// so every complex row of A is one real row of K' = 2 K entries (stored once) and the
+// doubling falls on the columns of B.  A CTA tile of 128 complex rows x 24 complex
+// columns is one M=128, N=48 MMA per BF16 K-step of 16.
 //
 // Data movement, three kernels per step:
-//  * k_digits<S, true> / k_digits<S, false>: one CTA per 64-row block of A (48-column
-//    block of B) finds the block's exponents over all of K, then converts it chunk by
-//    chunk (16 complex k) into S digit slices laid out exactly as the MMA reads them from
+//  * k_digits<S>: one CTA per (128-row block of A or 24-column block of B, flush group of
+//    kFlush chunks of K) finds the block's exponents over the group, then converts it chunk
+//    by chunk (16 complex k) into S digit slices laid out exactly as the MMA reads them from
 //    shared memory (the canonical K-major layout without swizzle: 8-row x 16-byte core
 //    matrices) and stores each chunk contiguously in the workspace.  The operands are
 //    gathered through the step's stride runs (arbitrary index permutations, which a TMA
@@ -50,8 +52,8 @@ namespace tc {
 constexpr int kMc = kTcMc;       // complex rows per tile
 constexpr int kNc = kTcNc;       // complex columns per tile
 constexpr int kKc = kTcKc;       // complex k per chunk
-constexpr int kM = 2 * kMc;      // MMA M (re and im rows interleaved)
-constexpr int kN = kNc;          // MMA N
+constexpr int kM = kMc;          // MMA M (one real row per complex row of A)
+constexpr int kN = 2 * kNc;      // MMA N (re and im columns interleaved)
 constexpr int kKr = 2 * kKc;     // MMA K per chunk (real: re half, im half)
 constexpr int kKcores = kKr / 8; // 16-byte K core columns per row
 constexpr int kABytes = kM * kKr * 2;   // one digit slice of an A chunk (BF16): 8 KB
@@ -70,12 +72,13 @@ struct Cfg {
   static constexpr int kConvSmem = 0;   // the digit kernels use static shared memory only
   // one MMA spans the stacked B digits: M = 128 allows N in multiples of 16 up to 256
   static_assert(kN % 16 == 0 && S * kN <= 256, "stacked B digits exceed one MMA");
-  static_assert(S != kTcDigits || (kAChunk == kTcAChunk && kBChunk == kTcBChunk),
+  static_assert(kAChunk == tc_a_chunk(S) && kBChunk == tc_b_chunk(S),
                 "chunk sizes must match the host's scratch layout");
   static constexpr int kCols = S * kN <= 32 ? 32 : S * kN <= 64 ? 64 : S * kN <= 128 ? 128
                                : S * kN <= 256 ? 256 : 512;
   // chunks per flush: S pairs per level x (chunks x kKr) terms x 2^14 < 2^24
-  static constexpr int kFlush = ((1 << 10) - 1) / (S * kKr) > 0 ? ((1 << 10) - 1) / (S * kKr) : 1;
+  static constexpr int kFlush = tc_flush(S);
+  static_assert(kFlush >= 1, "flush group");
 };
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
@@ -211,12 +214,15 @@ __device__ __forceinline__ void digits(float h, float l, float sc1, float sc2, _
   }
 }
 
-// 2^(7 - e) as a product of two exact floats (each exponent within [-126, 127]).
-__device__ __forceinline__ void digit_scale(int e, float& sc1, float& sc2) {
-  const int x = 7 - e, x1 = x / 2, x2 = x - x1;
-  sc1 = __int_as_float((max(-126, min(127, x1)) + 127) << 23);
-  sc2 = __int_as_float((max(-126, min(127, x2)) + 127) << 23);
+// 2^x as a product of two exact floats (each exponent within [-126, 127]).
+__device__ __forceinline__ void pow2_pair(int x, float& f1, float& f2) {
+  const int x1 = x / 2, x2 = x - x1;
+  f1 = __int_as_float((max(-126, min(127, x1)) + 127) << 23);
+  f2 = __int_as_float((max(-126, min(127, x2)) + 127) << 23);
 }
+
+// 2^(7 - e), the digit scale of a row with exponent e.
+__device__ __forceinline__ void digit_scale(int e, float& sc1, float& sc2) { pow2_pair(7 - e, sc1, sc2); }
 
 }  // namespace tc
 
@@ -254,9 +260,9 @@ __device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bf
 
 // Digit conversion of one item of an operand block: tile row r (a complex row of A, or a
 // complex column of B) x 4 consecutive complex k, written straight into the chunk's digit
-// slices as 8-byte groups of four BF16 digits.  For A every complex entry fills rows 2r
-// (re: [Re, -Im]) and 2r+1 (im: [Im, Re]); for B it fills row r ([Re, Im]).  `kl` is the
-// item's first k within its chunk (a multiple of 4).
+// slices as 8-byte groups of four BF16 digits.  A row r is [Re | Im] along K'; a B column
+// fills real rows 2r ([Re | -Im]) and 2r+1 ([Im | Re]).  `kl` is the item's first k within
+// its chunk (a multiple of 4).
 template <int S, bool IS_A>
 __device__ __forceinline__ void convert_item(const Cx<ff>* v, int r, int kl, float sc1, float sc2,
                                              unsigned char* chunk) {
@@ -273,50 +279,52 @@ __device__ __forceinline__ void convert_item(const Cx<ff>* v, int r, int kl, flo
     const uint2 re = pack4(dr[0][i], dr[1][i], dr[2][i], dr[3][i]);
     const uint2 im = pack4(di[0][i], di[1][i], di[2][i], di[3][i]);
     if (IS_A) {
+      *(uint2*)(sl + tile_off(r, kl, kKcores)) = re;
+      *(uint2*)(sl + tile_off(r, kKc + kl, kKcores)) = im;
+    } else {
       const uint2 mim = pack4(__hneg(di[0][i]), __hneg(di[1][i]), __hneg(di[2][i]), __hneg(di[3][i]));
       *(uint2*)(sl + tile_off(2 * r, kl, kKcores)) = re;
       *(uint2*)(sl + tile_off(2 * r, kKc + kl, kKcores)) = mim;
       *(uint2*)(sl + tile_off(2 * r + 1, kl, kKcores)) = im;
       *(uint2*)(sl + tile_off(2 * r + 1, kKc + kl, kKcores)) = re;
-    } else {
-      *(uint2*)(sl + tile_off(r, kl, kKcores)) = re;
-      *(uint2*)(sl + tile_off(r, kKc + kl, kKcores)) = im;
     }
   }
 }
 
 }  // namespace tc
 
-// Digits of the A operand (IS_A) or the B operand of a GEMM step: one CTA per (batch,
-// 64-row block).  K is walked in blocks of kConvThreads indices (one index-table entry per
-// thread, one barrier per block): first the rows' exponents over all of K, then the S
-// digit slices of every chunk, stored directly in the workspace.  The thread mapping
-// follows the operand's unit stride: along K (a warp reads 32 x 4 consecutive k of one
+// Digits of one block of the A operand (IS_A: 128 rows) or the B operand (24 columns) of
+// a GEMM step over one flush group of K (kFlush chunks of 16 complex k): the exponent of
+// each row over the group's k, then the S digit slices of the group's chunks, stored
+// directly in the workspace.  The second read of the block hits L2.  The thread mapping
+// follows the operand's unit stride: along K (consecutive lanes read consecutive k of one
 // row) or along the rows (a warp reads 32 consecutive rows).
 template <int S, bool IS_A>
-__global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const Cx<ff>* arena,
-                                                             unsigned char* scratch) {
+__device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena, unsigned char* scratch,
+                                             long long blk, long long* ro, long long* kt,
+                                             long long& base, int* ex, float* red) {
   using namespace tc;
-  static_assert(S == kTcDigits, "digit scratch laid out for kTcDigits digits");
   constexpr int kRows = IS_A ? kMc : kNc;
-  constexpr int kBlk = kConvThreads;              // k indices per block
-  constexpr int kQuads = kBlk / 4;                // 4-k items per row per block
-  static_assert(kBlk % kKc == 0 && kRows <= 64, "block geometry");
-  __shared__ long long ro[64], kt[kBlk];
-  __shared__ long long base;
-  __shared__ int ex[64];
-  __shared__ float red[kConvThreads];
-  const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K);
+  constexpr int kRowsPad = IS_A ? 128 : 64;       // rows of the exponent pass's thread grid
+  constexpr int kPer = kConvThreads / kRowsPad;   // threads per row in the exponent pass
+  constexpr int kG = Cfg<S>::kFlush * kKc;        // complex k of one flush group
+  static_assert(kRows <= kRowsPad && kConvThreads % kRowsPad == 0 && kG <= kConvThreads,
+                "block geometry");
+  const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
   const long long tiles = IS_A ? L.tiles_m : L.tiles_n;
-  const long long tile = blockIdx.x % tiles, bb = blockIdx.x / tiles;
+  const long long g = blk % L.groups, t = blk / L.groups;
+  const long long tile = t % tiles, bb = t / tiles;
   const int tid = threadIdx.x;
   const bool kin = IS_A ? s.a_kinner != 0 : s.b_kinner != 0;
+  const long long k0 = g * kG;
+  const long long kpad = L.chunks * kKc;               // K rounded up to whole chunks
+  const int kgn = (int)min((long long)kG, kpad - k0);  // this group's k (whole chunks)
   if (tid == 0) {
     long long a, b, c;
     runs4(bb, s.gb, s.ngb, a, b, c);
     base = IS_A ? a : b;
   }
-  if (tid < 64) {
+  if (tid < kRowsPad) {
     const long long r = tile * kRows + tid;
     long long a, b, c;
     if (tid < kRows && r < (IS_A ? s.M : s.N)) {
@@ -329,90 +337,93 @@ __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const
       ro[tid] = -1;
     }
   }
+  if (tid < kG) {
+    const long long k = k0 + tid;
+    long long ka = -1, kb = -1;
+    if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb);
+    kt[tid] = IS_A ? ka : kb;
+  }
   __syncthreads();
   const Cx<ff>* src = arena + (IS_A ? s.off_a : s.off_b) + base;
-  const long long kpad = L.chunks * kKc;   // K rounded up to whole chunks
-  auto fill_table = [&](long long kb) {
-    const long long k = kb + tid;
-    long long ka = -1, kb2 = -1;
-    if (k < s.K) split_runs((unsigned long long)k, s.kr, s.nk, ka, kb2);
-    kt[tid] = IS_A ? ka : kb2;
-  };
 
-  // ---- exponents: 4 threads per row (rows on consecutive lanes when they are the unit
-  // stride, else the 4 threads of a row on consecutive lanes over consecutive k)
-  const int er = kin ? (tid >> 2) : (tid & 63), es = kin ? (tid & 3) : (tid >> 6);
+  // ---- exponents over the group: kPer threads per row
+  const int er = kin ? (tid / kPer) : (tid % kRowsPad), es = kin ? (tid % kPer) : (tid / kRowsPad);
   float mx = 0.f;
-  for (long long kb = 0; kb < s.K; kb += kBlk) {
-    __syncthreads();
-    fill_table(kb);
-    __syncthreads();
-    if (er < kRows && ro[er] >= 0) {
-      const long long o = ro[er];
-      const int kn = (int)min((long long)kBlk, s.K - kb);
+  if (er < kRows && ro[er] >= 0) {
+    const long long o = ro[er];
 #pragma unroll 8
-      for (int k = es; k < kn; k += 4) mx = fmaxf(mx, mag(ld(src + o + kt[k])));
-    }
+    for (int k = es; k < kgn; k += kPer)
+      if (kt[k] >= 0) mx = fmaxf(mx, mag(ld(src + o + kt[k])));
   }
   red[tid] = mx;
   __syncthreads();
-  int* ex_out = (int*)(scratch + (IS_A ? L.ea_off : L.eb_off)) + (bb * tiles + tile) * kRows;
   if (tid < kRows) {
     float v = 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v = fmaxf(v, red[kin ? 4 * tid + j : tid + 64 * j]);
+    for (int j = 0; j < kPer; ++j) v = fmaxf(v, red[kin ? kPer * tid + j : tid + kRowsPad * j]);
     ex[tid] = bin_exp(v);
-    ex_out[tid] = ex[tid];
+    ((int*)(scratch + (IS_A ? L.ea_off : L.eb_off)))[((bb * tiles + tile) * L.groups + g) * kRows + tid] =
+        ex[tid];
   }
+  __syncthreads();
 
-  // ---- digits: items (row, 4 consecutive k), kRows x kQuads per block
+  // ---- digits: items (row, 4 consecutive k) of the group
   constexpr int kChunkBytes = IS_A ? Cfg<S>::kAChunk : Cfg<S>::kBChunk;
   unsigned char* dst0 = scratch + (IS_A ? L.a_off : L.b_off) +
                         (bb * tiles + tile) * L.chunks * (long long)kChunkBytes;
-  for (long long kb = 0; kb < kpad; kb += kBlk) {
-    __syncthreads();
-    fill_table(kb);
-    __syncthreads();
-    for (int idx = tid; idx < kRows * kQuads; idx += kConvThreads) {
-      const int r = kin ? idx / kQuads : idx % kRows;
-      const int q = kin ? idx % kQuads : idx / kRows;
-      const long long k0 = kb + 4 * q;
-      if (k0 >= kpad) continue;
-      Cx<ff> v[4];
-      const long long o = ro[r];
+  const int quads = kgn / 4;
+  for (int idx = tid; idx < kRows * quads; idx += kConvThreads) {
+    const int r = kin ? idx / quads : idx % kRows;
+    const int q = kin ? idx % quads : idx / kRows;
+    Cx<ff> v[4];
+    const long long o = ro[r];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        v[u] = Cx<ff>{{0.f, 0.f}, {0.f, 0.f}};
-        if (o >= 0 && kt[4 * q + u] >= 0) v[u] = ld(src + o + kt[4 * q + u]);
-      }
-      float sc1, sc2;
-      digit_scale(ex[r], sc1, sc2);
-      convert_item<S, IS_A>(v, r, (int)(k0 % kKc), sc1, sc2,
-                            dst0 + (k0 / kKc) * (long long)kChunkBytes);
+    for (int u = 0; u < 4; ++u) {
+      v[u] = Cx<ff>{{0.f, 0.f}, {0.f, 0.f}};
+      if (o >= 0 && kt[4 * q + u] >= 0) v[u] = ld(src + o + kt[4 * q + u]);
     }
+    float sc1, sc2;
+    digit_scale(ex[r], sc1, sc2);
+    const long long k = k0 + 4 * q;
+    convert_item<S, IS_A>(v, r, (int)(k % kKc), sc1, sc2, dst0 + (k / kKc) * (long long)kChunkBytes);
   }
 }
 
-// C tile (64 complex rows x 64 complex columns of one batch index) from the digit chunks:
-// warp 0 streams chunks into the stage ring, warp 1 issues the MMAs, warps 2..9 flush
-// the level accumulators and store C.
+// Digits of both operands of a GEMM step in one launch: blocks [0, nA) convert A (one per
+// batch index, 128-row block and flush group), the rest convert B.
+template <int S>
+__global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const Cx<ff>* arena,
+                                                             unsigned char* scratch, long long nA) {
+  __shared__ long long ro[128], kt[tc::kConvThreads];
+  __shared__ long long base;
+  __shared__ int ex[128];
+  __shared__ float red[tc::kConvThreads];
+  const long long blk = blockIdx.x;
+  if (blk < nA)
+    digits_block<S, true>(s, arena, scratch, blk, ro, kt, base, ex, red);
+  else
+    digits_block<S, false>(s, arena, scratch, blk - nA, ro, kt, base, ex, red);
+}
+
+// C tile (128 complex rows x 24 complex columns of one batch index) from the digit
+// chunks: warp 0 streams chunks into the stage ring, warp 1 issues the MMAs, warps 2..9
+// flush the level accumulators and store C.
 template <int S>
 __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff>* arena, Meta* meta,
                                                              const unsigned char* scratch,
                                                              unsigned long long* err) {
   using namespace tc;
-  static_assert(S == kTcDigits, "digit scratch laid out for kTcDigits digits");
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ long long cm[kMc], cn[kNc];
   __shared__ long long cbase;
-  __shared__ int ea[kMc], eb[kNc];
+  __shared__ int eb_s[kEpiWarps][kNc / 2];   // per epilogue warp: its columns' group exponents
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full, acc_empty,
       drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int bad;
   unsigned char* sm = dsm;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K);
+  const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
   // column blocks fastest: the CTAs resident at one time share their A row blocks in L2
   long long t = blockIdx.x;
   const long long tn = t % L.tiles_n;
@@ -441,7 +452,6 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
       runs4(m, s.gm, s.ngm, a, b, cm[i]);
     else
       cm[i] = -1;
-    ea[i] = ((const int*)(scratch + L.ea_off))[(bb * L.tiles_m + tm) * kMc + i];
   } else if (tid >= 64 + kMc && tid < 64 + kMc + kNc) {
     const int j = tid - 64 - kMc;
     const long long n = tn * kNc + j;
@@ -450,7 +460,6 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
       runs4(n, s.gn, s.ngn, a, b, cn[j]);
     else
       cn[j] = -1;
-    eb[j] = ((const int*)(scratch + L.eb_off))[(bb * L.tiles_n + tn) * kNc + j];
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -472,8 +481,8 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
   float acc_h[kCw], acc_l[kCw];
 #pragma unroll
   for (int j = 0; j < kCw; ++j) acc_h[j] = acc_l[j] = 0.f;
-  long long issued = 0;   // producer: chunks whose bulk copies were started
-  long long mmas = 0;     // MMA issuer: chunks whose MMAs were issued
+  int issued = 0;   // producer: chunks whose bulk copies were started (chunks < 2^31)
+  int mmas = 0;     // MMA issuer: chunks whose MMAs were issued
 
   if (warp == 0) {
     if (lane == 0) {  // producer
@@ -494,7 +503,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
         bulk_g2s(dst, asrc + c * Cfg<S>::kAChunk, Cfg<S>::kAChunk, smem_u32(&full[st]));
         bulk_g2s(dst + Cfg<S>::kAChunk, bsrc + c * Cfg<S>::kBChunk, Cfg<S>::kBChunk,
                  smem_u32(&full[st]));
-        issued = c + 1;
+        issued = (int)(c + 1);
       }
     }
   } else if (warp == 1) {
@@ -530,12 +539,20 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
                      (i == 0 && kk == 0) ? acc0 : 1u);
         commit(smem_u32(&empty[st]));
         if (last) commit(smem_u32(&acc_full));
-        mmas = c + 1;
+        mmas = (int)(c + 1);
       }
     }
   } else {  // epilogue warps: flush the levels every kFlush chunks
-    const int quarter = warp & 3, half = (warp - 2) / 4;
-    for (long long g = 0; g < ngroups; ++g) {
+    const int quarter = warp & 3, half = (warp - 2) / 4, ew = warp - 2;
+    // this thread's row exponent and its warp's column exponents, per flush group
+    const int* ea_g = (const int*)(scratch + L.ea_off) + (bb * L.tiles_m + tm) * L.groups * kMc +
+                      quarter * 32 + lane;
+    const int* eb_g = (const int*)(scratch + L.eb_off) + (bb * L.tiles_n + tn) * L.groups * kNc +
+                      half * (kNc / 2);
+    for (int g = 0; g < (int)ngroups; ++g) {
+      const int eam = ea_g[g * kMc];
+      if (lane < kNc / 2) eb_s[ew][lane] = eb_g[g * kNc + lane];
+      __syncwarp();
       if (!mbar_wait(smem_u32(&acc_full), (uint32_t)(g & 1), err)) {
         if (lane == 0) {
           bad = 1;
@@ -544,15 +561,29 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
         break;
       }
       fence_after();
-#pragma unroll 1
-      for (int lv = 0; lv < S; ++lv) {
-        float v[kCw];
-        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + lv * kN + half * kCw;
-        tmem_ld16(ta, v);
-        tmem_ld8(ta + 16, v + 16);
-        const float w = ldexpf(1.0f, -14 - 8 * lv);
+      // level L holds integer sums of digit products at weight 2^(-14-8L); per 8 columns the
+      // levels are summed in float-float, then scaled by the group's 2^(e(m) + e(n))
+      // (a power of two: exact) and added to the accumulators
+      const uint32_t ta0 = tmem + ((uint32_t)(quarter * 32) << 16) + half * kCw;
 #pragma unroll
-        for (int j = 0; j < kCw; ++j) ff_acc(acc_h[j], acc_l[j], v[j] * w, 0.f);
+      for (int c8 = 0; c8 < kCw / 8; ++c8) {
+        float th[8], tl[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) th[i] = tl[i] = 0.f;
+#pragma unroll 1
+        for (int lv = 0; lv < S; ++lv) {
+          float v[8];
+          tmem_ld8(ta0 + lv * kN + c8 * 8, v);
+          const float w = __int_as_float((127 - 14 - 8 * lv) << 23);   // 2^(-14-8L)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) ff_acc(th[i], tl[i], v[i] * w, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float f1, f2;
+          pow2_pair(eam + eb_s[ew][(c8 * 8 + i) >> 1], f1, f2);
+          ff_acc(acc_h[c8 * 8 + i], acc_l[c8 * 8 + i], (th[i] * f1) * f2, (tl[i] * f1) * f2);
+        }
       }
       fence_before();
       __syncwarp();
@@ -567,7 +598,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
   // commit tracks all of them).  If even these waits run out, the CTA exits regardless.
   if (bad) {
     if (warp == 0 && lane == 0)
-      for (long long c = issued > kStages ? issued - kStages : 0; c < issued; ++c)
+      for (int c = issued > kStages ? issued - kStages : 0; c < issued; ++c)
         mbar_wait(smem_u32(&full[c % kStages]), (uint32_t)((c / kStages) & 1), nullptr);
     if (warp == 1 && lane == 0 && mmas > 0) {
       commit(smem_u32(&drain));
@@ -578,25 +609,24 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
     fence_after();
   }
 
-  // ---- store: scale by 2^(e(m) + e(n)) and the step's normalisation, pair re / im
+  // ---- store: scale by 2^(e(m) + e(n)) and the step's normalisation; this thread's TMEM
+  // lane is complex row m, its columns hold (re, im) of kCw / 2 complex columns
   float vmax = 0;
   if (warp >= 2) {
     const int quarter = warp & 3, half = (warp - 2) / 4;
-    const int row = quarter * 32 + lane, m = row >> 1, part = row & 1;
+    const int m = quarter * 32 + lane;
     Cx<ff>* C = arena + s.off_c + cbase;
 #pragma unroll
-    for (int j = 0; j < kCw; ++j) {
-      const int n = half * kCw + j;
-      ff mine = ff_norm(acc_h[j], acc_l[j]);
-      const int e = ea[m] + eb[n];
-      mine.hi = ldexpf(mine.hi, e) * scale;
-      mine.lo = ldexpf(mine.lo, e) * scale;
-      if (bad) mine.hi = mine.lo = __int_as_float(0x7fc00000);
-      ff other;
-      other.hi = __shfl_xor_sync(0xffffffffu, mine.hi, 1);
-      other.lo = __shfl_xor_sync(0xffffffffu, mine.lo, 1);
-      if ((j & 1) == part && cm[m] >= 0 && cn[n] >= 0) {
-        const Cx<ff> out = part == 0 ? Cx<ff>{mine, other} : Cx<ff>{other, mine};
+    for (int j = 0; j < kCw / 2; ++j) {
+      const int n = half * (kCw / 2) + j;
+      ff re = ff_norm(acc_h[2 * j], acc_l[2 * j]), im = ff_norm(acc_h[2 * j + 1], acc_l[2 * j + 1]);
+      re.hi *= scale;
+      re.lo *= scale;
+      im.hi *= scale;
+      im.lo *= scale;
+      if (bad) re.hi = re.lo = im.hi = im.lo = __int_as_float(0x7fc00000);
+      if (cm[m] >= 0 && cn[n] >= 0) {
+        const Cx<ff> out{re, im};
         st(C + cm[m] + cn[n], out);
         vmax = fmaxf(vmax, mag(out));
       }

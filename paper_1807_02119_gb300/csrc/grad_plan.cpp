@@ -287,6 +287,9 @@ bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err)
     G.leaves.push_back(L);
   }
 
+  // runs of small steps as sequence launches
+  build_segments(G.steps, G.segments, G.tiny);
+
   // workspace layout
   const uint64_t nl = std::max<size_t>(1, G.leaves.size());
   uint64_t off = 0;
@@ -296,6 +299,8 @@ bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err)
   off = a256(off + sizeof(Slot) * std::max<size_t>(1, p.slots.size()));
   G.off_leaves = off;
   off = a256(off + sizeof(GradLeaf) * nl);
+  G.off_tiny = off;
+  off = a256(off + sizeof(TinyStep) * G.tiny.size());
   G.off_meta = off;
   off = a256(off + 16ull * (uint64_t)G.n_meta);
   G.off_counter = off;
@@ -314,6 +319,8 @@ bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err)
     std::memcpy(G.program.data() + G.off_slots, p.slots.data(), sizeof(Slot) * p.slots.size());
   if (!G.leaves.empty())
     std::memcpy(G.program.data() + G.off_leaves, G.leaves.data(), sizeof(GradLeaf) * G.leaves.size());
+  if (!G.tiny.empty())
+    std::memcpy(G.program.data() + G.off_tiny, G.tiny.data(), sizeof(TinyStep) * G.tiny.size());
   G.built = true;
   return true;
 }

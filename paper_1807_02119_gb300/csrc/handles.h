@@ -32,6 +32,7 @@ struct pk_plan {
   uint8_t* pinned_program = nullptr;
   uint8_t* pinned_grad = nullptr;  // the reverse-pass program and its downloaded results
   PlanGraph graph;
+  PlanGraph grad_graph;            // the reverse-pass launch sequence (arena = null)
 };
 
 namespace pk {

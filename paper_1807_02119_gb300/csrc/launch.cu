@@ -61,6 +61,16 @@ namespace {
 struct Marker {
   Prof* prof;
   cudaStream_t st;
+  // During stream capture a plain event record only marks a dependency; the external
+  // flag makes it an event-record node of the graph, re-recorded by every replay.
+  void record(cudaEvent_t e) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, st);
+  }
   void begin(int c, double cm, double by) {
     if (!prof) return;
     cudaEvent_t a, b;
@@ -71,10 +81,10 @@ struct Marker {
     prof->n[c] += 1;
     prof->cmacs[c] += cm;
     prof->bytes[c] += by;
-    cudaEventRecord(a, st);
+    record(a);
   }
   void end() {
-    if (prof) cudaEventRecord(prof->ev.back().second, st);
+    if (prof) record(prof->ev.back().second);
   }
 };
 
@@ -120,7 +130,22 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
 
 // One contraction step; `counter` is its split-K ticket, `by` its algorithmic bytes
 // (for the optional timing only).
-TcScratch tc_scratch_layout(const Step& s) { return tc_scratch(s.Bsz, s.M, s.N, s.K); }
+// Digit conversion of both operands, then the tensor-core GEMM, for S digits.
+template <int S>
+cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* tcs,
+                      unsigned long long* err, cudaStream_t stream, Marker& mk, double cm, double by) {
+  const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
+  // class 6 (digit conversion): its bytes are the operands it reads, |A| + |B|
+  mk.begin(6, 0.0, (double)sizeof(Cx<ff>) * (double)(s.R * s.K + s.Bsz * s.K * s.N));
+  const long long nA = s.Bsz * L.tiles_m * L.groups, nB = s.Bsz * L.tiles_n * L.groups;
+  k_digits<S><<<(unsigned)(nA + nB), tc::kConvThreads, tc::Cfg<S>::kConvSmem, stream>>>(s, arena, tcs, nA);
+  mk.end();
+  const long long tc_tiles = L.tiles_m * L.tiles_n * s.Bsz;
+  mk.begin(5, cm, by);
+  k_gemm_tc<S><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(s, arena, meta, tcs, err);
+  mk.end();
+  return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* partial,
@@ -131,22 +156,9 @@ cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* par
   cudaError_t e;
   if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
     if constexpr (std::is_same<R, ff>::value) {
-      if (s.tc && tc_scratch && err) {  // digits of A and B, then the tensor-core GEMM
-        const TcScratch L = tc_scratch_layout(s);
-        // class 6 (digit conversion): its bytes are the operands it reads, |A| + |B|
-        mk.begin(6, 0.0, (double)sizeof(Cx<R>) * (double)(s.R * s.K + s.Bsz * s.K * s.N));
-        k_digits<kTcDigits, true><<<(unsigned)(s.Bsz * L.tiles_m), tc::kConvThreads,
-                                    tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
-        k_digits<kTcDigits, false><<<(unsigned)(s.Bsz * L.tiles_n), tc::kConvThreads,
-                                     tc::Cfg<kTcDigits>::kConvSmem, stream>>>(s, arena, tc_scratch);
-        mk.end();
-        const long long tc_tiles = L.tiles_m * L.tiles_n * s.Bsz;
-        mk.begin(5, cm, by);
-        k_gemm_tc<kTcDigits><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<kTcDigits>::kSmem, stream>>>(
-            s, arena, meta, tc_scratch, err);
-        mk.end();
-        return cudaGetLastError();
-      }
+      if (s.tc && tc_scratch && err)  // digits of A and B, then the tensor-core GEMM
+        return s.tc == 4 ? launch_tc<4>(s, arena, meta, tc_scratch, err, stream, mk, cm, by)
+                         : launch_tc<5>(s, arena, meta, tc_scratch, err, stream, mk, cm, by);
     }
     mk.begin(4, cm, by);
     k_gemm<R><<<(unsigned)gemm_tiles, 256, 0, stream>>>(s, arena, meta);
@@ -341,9 +353,20 @@ cudaError_t launch_grad_impl(const Plan& p, char* base, cudaStream_t stream) {
           p.q, sl, (int)p.sliced.size());
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    for (size_t i = 0; i < G.steps.size(); ++i) {
+    const TinyStep* tiny = (const TinyStep*)(base + G.off_tiny);
+    size_t sg = 0;
+    for (size_t i = 0; i < G.steps.size();) {
+      while (sg < G.segments.size() && (size_t)G.segments[sg].first < i) ++sg;
+      if (sg < G.segments.size() && (size_t)G.segments[sg].first == i) {  // one sequence launch
+        const Segment& g = G.segments[sg];
+        k_seg<R><<<1, 256, 0, stream>>>(tiny + g.tiny0, g.count, arena, meta);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        i += g.count;
+        continue;
+      }
       e = launch_step<R>(G.steps[i], arena, meta, partial, counters + i, stream, mk, 0.0);
       if (e != cudaSuccess) return e;
+      ++i;
     }
     k_slice_result<R><<<1, 32, 0, stream>>>(arena, G.root_offset, meta, G.root_meta, res, sl);
     if (!G.leaves.empty())
@@ -370,6 +393,19 @@ cudaError_t raise_rows_smem() {
   }
   return cudaSuccess;
 }
+
+template <int S>
+cudaError_t prepare_tc() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_gemm_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::Cfg<S>::kSmem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_gemm_tc<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_digits<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc::Cfg<S>::kConvSmem);
+}
 }  // namespace
 
 cudaError_t prepare_kernels() {
@@ -381,18 +417,8 @@ cudaError_t prepare_kernels() {
   if ((e = raise_rows_smem<double>()) != cudaSuccess) return e;
   if ((e = raise_rows_smem<float>()) != cudaSuccess) return e;
   if ((e = raise_rows_smem<ff>()) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_gemm_tc<kTcDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::Cfg<kTcDigits>::kSmem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_gemm_tc<kTcDigits>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_digits<kTcDigits, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::Cfg<kTcDigits>::kConvSmem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_digits<kTcDigits, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::Cfg<kTcDigits>::kConvSmem)) != cudaSuccess)
-    return e;
+  if ((e = prepare_tc<4>()) != cudaSuccess) return e;
+  if ((e = prepare_tc<5>()) != cudaSuccess) return e;
   if (dev >= 0 && dev < 256) done[dev] = true;
   return cudaSuccess;
 }

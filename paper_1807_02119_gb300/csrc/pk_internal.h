@@ -108,7 +108,8 @@ struct Step {
   int32_t ngb, ngm, ngn;
   int32_t a_kinner;        // A's unit-stride index is a contracted one
   int32_t b_kinner;        // B's unit-stride index is a contracted one
-  int32_t tc;              // GEMM step may run on the tensor cores (split precision)
+  int32_t tc;              // split precision: BF16 digits per operand on the tensor cores
+                           // (4 or 5), 0 = the GEMM step runs on the CUDA cores
   Run4 gb[kMaxRuns];
   Run4 gm[kMaxRuns];
   Run4 gn[kMaxRuns];
@@ -171,27 +172,34 @@ struct TailStep {
 #define PK_HD
 #endif
 
-// GEMM steps of the split precision on the tensor cores: each operand element becomes
-// kTcDigits BF16 digits (exact 8-bit pieces), stored per 64-row block and 16-complex-k
-// chunk in the workspace after the arena, followed by the blocks' exponents.
-constexpr int kTcDigits = 5;
-constexpr int kTcMc = 64, kTcNc = 48, kTcKc = 16;
-constexpr long long kTcAChunk = (long long)kTcDigits * (2 * kTcMc) * (2 * kTcKc) * 2;
-constexpr long long kTcBChunk = (long long)kTcDigits * kTcNc * (2 * kTcKc) * 2;
+// GEMM steps of the split precision on the tensor cores: each operand element becomes S
+// BF16 digits (exact 8-bit pieces; S = Step::tc, 4 or 5), stored per tile block and
+// 16-complex-k chunk in the workspace after the arena, followed by the blocks' exponents,
+// one per row (column) and flush group of tc_flush(S) chunks.
+// A tile is kTcMc complex rows of A, each stored once as [Re A, Im A], by kTcNc complex
+// columns of B, each stored as two real columns [Re B; -Im B] and [Im B; Re B] (the
+// complex doubling sits on B, the operand the planner keeps smaller).
+constexpr int kTcMc = 128, kTcNc = 24, kTcKc = 16;
+PK_HD constexpr long long tc_a_chunk(int S) { return (long long)S * kTcMc * (2 * kTcKc) * 2; }
+PK_HD constexpr long long tc_b_chunk(int S) { return (long long)S * (2 * kTcNc) * (2 * kTcKc) * 2; }
+// Chunks per flush group: the S digit pairs of a level, 2 kTcKc real terms per chunk and
+// digit products below 2^14 keep a level's FP32 sum exact (below 2^24) for this many chunks.
+PK_HD constexpr int tc_flush(int S) { return ((1 << 10) - 1) / (S * 2 * kTcKc); }
 struct TcScratch {
-  long long tiles_m, tiles_n, chunks;
+  long long tiles_m, tiles_n, chunks, groups;
   long long a_off, b_off, ea_off, eb_off, bytes;
 };
-PK_HD inline TcScratch tc_scratch(long long Bsz, long long M, long long N, long long K) {
+PK_HD inline TcScratch tc_scratch(long long Bsz, long long M, long long N, long long K, int S) {
   TcScratch x;
   x.tiles_m = (M + kTcMc - 1) / kTcMc;
   x.tiles_n = (N + kTcNc - 1) / kTcNc;
   x.chunks = (K + kTcKc - 1) / kTcKc;
+  x.groups = (x.chunks + tc_flush(S) - 1) / tc_flush(S);
   x.a_off = 0;
-  x.b_off = x.a_off + Bsz * x.tiles_m * x.chunks * kTcAChunk;
-  x.ea_off = x.b_off + Bsz * x.tiles_n * x.chunks * kTcBChunk;
-  x.eb_off = x.ea_off + ((Bsz * x.tiles_m * kTcMc * 4 + 255) & ~255LL);
-  x.bytes = x.eb_off + ((Bsz * x.tiles_n * kTcNc * 4 + 255) & ~255LL);
+  x.b_off = x.a_off + Bsz * x.tiles_m * x.chunks * tc_a_chunk(S);
+  x.ea_off = x.b_off + Bsz * x.tiles_n * x.chunks * tc_b_chunk(S);
+  x.eb_off = x.ea_off + ((Bsz * x.tiles_m * x.groups * kTcMc * 4 + 255) & ~255LL);
+  x.bytes = x.eb_off + ((Bsz * x.tiles_n * x.groups * kTcNc * 4 + 255) & ~255LL);
   return x;
 }
 
@@ -224,6 +232,8 @@ struct GradProgram {
   std::vector<int8_t> phase;         // per step: 0 forward, 1 recompute, 2 adjoint
   std::vector<Recipe> recipes;       // initial tensors at their offsets in this arena
   std::vector<GradLeaf> leaves;      // one per EdgeGroup, same order
+  std::vector<Segment> segments;     // runs of small steps launched as one sequence kernel
+  std::vector<TinyStep> tiny;        // their records (in the program at off_tiny)
   int32_t n_meta = 0;
   int32_t n_checkpoints = 0;
   int64_t arena_elems = 0;
@@ -231,9 +241,9 @@ struct GradProgram {
   int64_t root_offset = 0;
   int32_t root_meta = 0;
   double cmacs[3] = {0, 0, 0};       // per slice, by phase
-  uint64_t off_recipe = 0, off_slots = 0, off_leaves = 0, off_meta = 0, off_counter = 0,
-           off_result = 0, off_scratch = 0, off_acc = 0, off_arena = 0;
-  std::vector<uint8_t> program;      // recipes | slots | leaves, copied by pk_grad
+  uint64_t off_recipe = 0, off_slots = 0, off_leaves = 0, off_tiny = 0, off_meta = 0,
+           off_counter = 0, off_result = 0, off_scratch = 0, off_acc = 0, off_arena = 0;
+  std::vector<uint8_t> program;      // recipes | slots | leaves | tiny steps, copied by pk_grad
   uint64_t ws_bytes(int32_t precision) const {
     return off_arena + (uint64_t)arena_elems * (precision == PK_C64 ? 8ull : 16ull);
   }
@@ -313,6 +323,11 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
                 bool& swapped, std::vector<int32_t>& cdims, std::string& err);
 bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std::string& err);
+// Maximal runs (>= 2) of consecutive small row-kernel steps (<= kTinyOuts outputs, K <=
+// kTinyK, <= kTinyWork complex multiply-adds), with their compact records, for the
+// sequence kernel k_seg.
+void build_segments(const std::vector<Step>& steps, std::vector<Segment>& segments,
+                    std::vector<TinyStep>& tiny);
 bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err);
 // Writes the clause values of p.weights into p.slots and both program blobs.
 void apply_weights(Plan& p);

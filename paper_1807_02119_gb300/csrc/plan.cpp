@@ -942,11 +942,61 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
   else
     st.kernel = KROWS;
   st.chunks = st.kernel == KSPLITK ? (int32_t)std::min<int64_t>(64, (st.K + 2047) / 2048) : 0;
-  st.tc = (st.kernel == KGEMM && !(flags & PK_FLAG_NO_TC)) ? 1 : 0;
+  st.tc = (st.kernel == KGEMM && !(flags & PK_FLAG_NO_TC)) ? ((flags & PK_FLAG_TC_DIGITS4) ? 4 : 5)
+                                                           : 0;
   return true;
 }
 
 // ------------------------------------------------------------------ plan assembly
+void build_segments(const std::vector<Step>& steps, std::vector<Segment>& segments,
+                    std::vector<TinyStep>& tiny) {
+  segments.clear();
+  tiny.clear();
+  auto small = [&](const Step& st) {
+    return st.kernel == KROWS && st.R * st.N <= kTinyOuts && st.K <= kTinyK &&
+           st.R * st.N * st.K <= kTinyWork;
+  };
+  const int32_t n_steps = (int32_t)steps.size();
+  int32_t s0 = 0;
+  while (s0 < n_steps) {
+    if (!small(steps[s0])) {
+      ++s0;
+      continue;
+    }
+    int32_t s1 = s0;
+    while (s1 < n_steps && small(steps[s1])) ++s1;
+    if (s1 - s0 >= 2) {
+      Segment sg;
+      sg.first = s0;
+      sg.count = s1 - s0;
+      sg.tiny0 = (int32_t)tiny.size();
+      for (int32_t i = s0; i < s1; ++i) {
+        const Step& st = steps[i];
+        TinyStep ts;
+        std::memset(&ts, 0, sizeof(ts));
+        ts.a = st.a;
+        ts.b = st.b;
+        ts.c = st.c;
+        ts.nrow = st.nrow;
+        ts.nk = st.nk;
+        ts.nn = st.nn;
+        ts.off_a = st.off_a;
+        ts.off_b = st.off_b;
+        ts.off_c = st.off_c;
+        ts.R = st.R;
+        ts.K = st.K;
+        ts.N = st.N;
+        std::memcpy(ts.row, st.row, sizeof(ts.row));
+        std::memcpy(ts.kr, st.kr, sizeof(ts.kr));
+        std::memcpy(ts.nr, st.nr, sizeof(ts.nr));
+        tiny.push_back(ts);
+      }
+      segments.push_back(sg);
+    }
+    s0 = s1;
+  }
+}
+
 uint64_t Plan::ws_bytes(int32_t precision) const {
   if (precision == PK_C64) {
     if (tail.empty()) return off_arena + (uint64_t)arena_elems * 8ull;
@@ -1103,7 +1153,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   for (const Step& st : p.steps)
     if (st.kernel == KGEMM && st.tc) {
       p.n_tc++;
-      p.tc_bytes = std::max<int64_t>(p.tc_bytes, tc_scratch(st.Bsz, st.M, st.N, st.K).bytes);
+      p.tc_bytes = std::max<int64_t>(p.tc_bytes, tc_scratch(st.Bsz, st.M, st.N, st.K, st.tc).bytes);
     }
 
   // ---- sizes, lifetimes, stats
@@ -1271,52 +1321,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   }
 
   // ---- segments: maximal runs (>= 2) of consecutive small row-kernel steps
-  p.segments.clear();
-  p.tiny.clear();
-  {
-    auto small = [&](const Step& st) {
-      return st.kernel == KROWS && st.R * st.N <= kTinyOuts && st.K <= kTinyK &&
-             st.R * st.N * st.K <= kTinyWork;
-    };
-    int32_t s0 = 0;
-    while (s0 < n_steps) {
-      if (!small(p.steps[s0])) {
-        ++s0;
-        continue;
-      }
-      int32_t s1 = s0;
-      while (s1 < n_steps && small(p.steps[s1])) ++s1;
-      if (s1 - s0 >= 2) {
-        Segment sg;
-        sg.first = s0;
-        sg.count = s1 - s0;
-        sg.tiny0 = (int32_t)p.tiny.size();
-        for (int32_t i = s0; i < s1; ++i) {
-          const Step& st = p.steps[i];
-          TinyStep ts;
-          std::memset(&ts, 0, sizeof(ts));
-          ts.a = st.a;
-          ts.b = st.b;
-          ts.c = st.c;
-          ts.nrow = st.nrow;
-          ts.nk = st.nk;
-          ts.nn = st.nn;
-          ts.off_a = st.off_a;
-          ts.off_b = st.off_b;
-          ts.off_c = st.off_c;
-          ts.R = st.R;
-          ts.K = st.K;
-          ts.N = st.N;
-          std::memcpy(ts.row, st.row, sizeof(ts.row));
-          std::memcpy(ts.kr, st.kr, sizeof(ts.kr));
-          std::memcpy(ts.nr, st.nr, sizeof(ts.nr));
-          p.tiny.push_back(ts);
-        }
-        p.segments.push_back(sg);
-      }
-      s0 = s1;
-    }
-  }
+  build_segments(p.steps, p.segments, p.tiny);
 
   // ---- workspace layout
   uint64_t off = 0;

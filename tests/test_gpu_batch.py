@@ -57,6 +57,39 @@ def test_batch_vs_oracle(ctx):
             assert rel_err(sc(v), vo) <= TOL[prec]
 
 
+def _oracle_zv(job):
+    """Z and V of one knot by the CPU oracle (spawned worker: imports its own modules)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import oracle
+    from oracle.order import min_fill_order
+    pd, outer, q = job
+    g = oracle.tait_graph(pd, outer=outer)
+    order, _ = min_fill_order(g.n_v, g.edges, q, restarts=4)
+    z = oracle.z_complex(g.n_v, g.edges, q, order=order, sum_inside=True)
+    return z, oracle.jones_from_z(z, g, q)
+
+
+def test_batch_vs_oracle_512(ctx):
+    """The batch workload's first 512 knots (18..122 crossings, q = 3) in ONE persistent
+    launch, split and complex128, against the CPU oracle knot by knot."""
+    import multiprocessing as mp
+    import os
+    knots = kg.knot_suite("batch")[:512]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        ref = pool.map(_oracle_zv, [(k.pd, k.outer, 3) for k in knots], chunksize=8)
+    plans = _plans(ctx, knots, 3)
+    for prec in ("split", "c128"):
+        Z, V = pk.evaluate_batch(plans, prec)
+        worst = 0.0
+        for i, (z, v, (zo, vo)) in enumerate(zip(Z, V, ref)):
+            e = max(rel_err(sc(z), zo), rel_err(sc(v), vo))
+            assert e <= TOL[prec], (i, prec, e)
+            worst = max(worst, e)
+        print(f"[batch {prec}] 512 knots in one launch, worst relative error vs the oracle {worst:.2e}")
+
+
 def test_batch_mixed_q_slices_and_trivial(ctx):
     """Different q in one batch, sliced plans, the unknot and a kink; relaunch gives
     bit-identical results (the recorded graph is replayed)."""
