@@ -78,7 +78,7 @@ def parse():
 
 KNOTS_PER_RANK = 64
 METRIC = "knot evaluations per second (exact Z(q), V_K(t(q))), split-FP32 vs complex128"
-ORACLE_MAX_WIDTH = 11     # spins per oracle factor in the CPU samples (q^11 entries at most)
+ORACLE_MAX_ENTRIES = 1 << 24   # CPU samples: largest oracle factor after a spin is summed out
 
 
 def shard_seeds(rank, n=KNOTS_PER_RANK):
@@ -159,7 +159,8 @@ class Clocks:
 def _oracle_one(job):
     """One (knot, q) evaluation by the CPU oracle in a worker process: min-fill spin
     order (oracle.order), Z by spin elimination, V = A(q) Z.  Returns (key, seconds) or
-    (key, None) when its widest factor exceeds ORACLE_MAX_WIDTH spins."""
+    (key, None) when a factor would exceed ORACLE_MAX_ENTRIES entries (q^(w-1) for a bucket
+    of w spins)."""
     sys.path.insert(0, ROOT)
     import oracle
     from oracle.order import min_fill_order
@@ -167,7 +168,7 @@ def _oracle_one(job):
     t0 = time.perf_counter()
     g = oracle.tait_graph(pd, outer=outer)
     order, w = min_fill_order(g.n_v, g.edges, q, restarts=4)
-    if w > ORACLE_MAX_WIDTH:
+    if q ** (w - 1) > ORACLE_MAX_ENTRIES:
         return key, None
     z = oracle.z_complex(g.n_v, g.edges, q, order=order, sum_inside=True)
     oracle.jones_from_z(z, g, q)
@@ -191,7 +192,7 @@ def cpu_oracle_baseline(knots, qs, budget_s=12.0):
     """The oracle as it stands on the host cores: a sample of the workload chosen in
     workload order by a single-core run of about budget_s seconds, then the same sample
     on all cores (one evaluation per process).  Evaluations too wide for the oracle
-    (> ORACLE_MAX_WIDTH spins per factor) are skipped and counted."""
+    (a factor above ORACLE_MAX_ENTRIES entries) are skipped and counted."""
     jobs = oracle_jobs(knots, qs)
     sample, skipped, t_single = [], 0, 0.0
     with _oracle_pool(1) as pool:
@@ -213,8 +214,8 @@ def cpu_oracle_baseline(knots, qs, budget_s=12.0):
         t_all = time.perf_counter() - t0
     n = len(sample)
     text = (f"the first {n + skipped} (knot, q) evaluations in workload order "
-            f"({jobs[0][0]}..{sample[-1][0] if sample else '-'}), {skipped} skipped as wider "
-            f"than {ORACLE_MAX_WIDTH} spins per oracle factor; {n} timed")
+            f"({jobs[0][0]}..{sample[-1][0] if sample else '-'}), {skipped} skipped as needing an "
+            f"oracle factor above 2^24 entries; {n} timed")
     return {"value": n / t_all, "unit": "knots/s", "cores": ncpu, "kind": "oracle",
             "sample": text, "single_core": {"value": n / t_single, "cores": 1},
             "all_core": {"value": n / t_all, "cores": ncpu}}
@@ -250,8 +251,8 @@ def run_reference(args):
     step = sum(times) / len(times)
     v = len(sample) / step
     text = (f"{len(sample)} (knot, q) evaluations per step: the first that fit the oracle in "
-            f"workload order ({sample[0][0]}..{sample[-1][0]}), {skipped} skipped as wider than "
-            f"{ORACLE_MAX_WIDTH} spins per factor")
+            f"workload order ({sample[0][0]}..{sample[-1][0]}), {skipped} skipped as needing an "
+            f"oracle factor above 2^24 entries")
     out = {"impl": "reference", "metric": METRIC,
            "value": v, "unit": "knots/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000 * step,
@@ -273,20 +274,27 @@ CLASS_KERNEL = {"build": "k_build", "rows": "k_rows / k_outs / k_seg (fused perm
                 "gemm": "k_gemm (tiled strided complex GEMM, CUDA cores)",
                 "gemm_tc": "k_gemm_tc (complex GEMM on tcgen05 tensor cores, BF16 digit products)",
                 "digits": "k_digits (operand digits for k_gemm_tc)"}
-# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) as a
-# multiple of the launch's algorithmic bytes, for the kernels captured under profiles/;
-# None where no capture of the current kernel exists.
-NCU_TRAFFIC_RATIO = {}
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one captured launch
+# divided by that launch's algorithmic bytes as the library counts them (its storage type,
+# 16 bytes per complex entry in split): the multiple applied to a class's average launch.
+# Source: profiles/k_gemm_tc_split_q5_seed53.md (the heaviest GEMM step of the workload).
+NCU_TRAFFIC_RATIO = {"gemm_tc": 2.70578 / 1.71875}
 
 
-def roofline_blocks(classes, prec, pk_):
-    """Per kernel class of the in-step replay: achieved = algorithmic bytes (or flops)
-    per launch / average in-step launch duration, against the measured peak.  Algorithmic
-    bytes follow the step definition: e (|A| + |B| + |C|) with e = 8 for complex64 and
-    split storage, 16 for complex128 (the library counts the bytes of its storage type:
-    16 for split, so halved here)."""
+def roofline_blocks(classes, prec, pk_, instep=None):
+    """Per kernel class of the serialised event pass (launches one after another, a CUDA
+    event pair around each, on the stream they are launched on): achieved = algorithmic
+    bytes (or flops) per launch / average launch duration, against the measured peak.  The
+    dominant class is the one with the largest GPU-fill-weighted time: each launch's
+    duration times the share of the GPU's CTA slots it fills, which is what a launch costs
+    the concurrent step (many plans' launches overlap there; a one-CTA launch costs almost
+    nothing).  Algorithmic bytes follow the step definition e (|A| + |B| + |C|) with e = 8
+    for complex64 and split storage, 16 for complex128 (the library counts the bytes of its
+    storage type, 16 for split, so halved here)."""
     e_scale = 0.5 if prec == "split" else 1.0
     out = {}
+    tot_fill = sum(d.get("fill_ms", 0.0) for d in classes.values()) or 1.0
+    tot_ms = sum(d["ms"] for d in classes.values()) or 1.0
     for c, d in classes.items():
         if d["launches"] <= 0 or d["ms"] <= 0:
             continue
@@ -294,13 +302,13 @@ def roofline_blocks(classes, prec, pk_):
         alg_bytes = d["bytes"] * e_scale / d["launches"]
         flops = 8.0 * d["cmacs"] / d["launches"]
         if c == "gemm_tc":
-            peak = pk_.get("bf16_tflops_sustained", pk_["bf16_tflops"]) / TC_PAIRS
+            burst = pk_["bf16_tflops"]
+            peak = burst / TC_PAIRS
             ach = flops / avg_s / 1e12
             blk = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                   "peak_source": f"measured sustained dense BF16 "
-                                  f"{pk_.get('bf16_tflops_sustained', pk_['bf16_tflops'])} TFLOP/s "
-                                  f"(of measured, MEASURED_PEAKS.json) / {TC_PAIRS} BF16 digit-pair "
-                                  f"products per real multiply-add"}
+                   "peak_source": f"measured dense BF16 burst {burst} TFLOP/s (of measured, "
+                                  f"MEASURED_PEAKS.json; the kernel is timed alone) / {TC_PAIRS} "
+                                  f"BF16 digit-pair products per real multiply-add"}
         elif c == "gemm" and prec != "c128":
             peak = FP32_ISSUE_TOPS / FF_INSTR_PER_CMAC * 8 if prec == "split" else FP32_CORE_TFLOPS
             ach = flops / avg_s / 1e12
@@ -314,13 +322,18 @@ def roofline_blocks(classes, prec, pk_):
         ratio = NCU_TRAFFIC_RATIO.get(c)
         blk.update({"frac": ach / peak, "kernel": CLASS_KERNEL[c],
                     "traffic": ratio * d["bytes"] / d["launches"] if ratio else None,
+                    "traffic_unit": "bytes per launch (DRAM read + write)",
                     "launches": d["launches"], "avg_launch_us": 1e6 * avg_s,
-                    "in_step_ms": d["ms"], "alg_bytes_per_launch": alg_bytes,
-                    "flops_per_launch": flops,
+                    "serialised_ms": d["ms"], "share_serialised": d["ms"] / tot_ms,
+                    "fill_weighted_ms": d.get("fill_ms"),
+                    "share_fill_weighted": d.get("fill_ms", 0.0) / tot_fill,
+                    "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
                     "units": "algorithmic bytes e(|A|+|B|+|C|), e = 8 (complex64 / split) or 16 "
                              "(complex128); flops = 8 per complex multiply-add"})
+        if instep and c in instep:
+            blk["in_step_summed_ms"] = instep[c]["ms"]
         out[c] = blk
-    dom = max(out, key=lambda c: out[c]["in_step_ms"])
+    dom = max(out, key=lambda c: out[c]["fill_weighted_ms"] or 0.0)
     return dict(out[dom], kernel_class=dom), out
 
 
@@ -662,7 +675,8 @@ def main():
     prof = {}
     for p, w in zip(plans, ws):
         for kname, d in pk.profile(p, prec, w).items():
-            acc = prof.setdefault(kname, {"ms": 0.0, "launches": 0.0, "cmacs": 0.0, "bytes": 0.0})
+            acc = prof.setdefault(kname, {"ms": 0.0, "launches": 0.0, "cmacs": 0.0, "bytes": 0.0,
+                                          "fill_ms": 0.0})
             for f in acc:
                 acc[f] += d[f]
     group.launch()
@@ -724,7 +738,7 @@ def main():
     del pgroup, group, ws
     torch.cuda.empty_cache()
     log("in-step profile")
-    roof, rooflines = roofline_blocks(instep, prec, peaks())
+    roof, rooflines = roofline_blocks(prof, prec, peaks(), instep)
 
     # the same workload once in each other precision (same concurrent execution);
     # errors against complex128
@@ -787,7 +801,7 @@ def main():
                           "l2": "flushed between steps (512 MB write)",
                           "plan_seconds": plan_s, "complex_macs_per_step": tot_cmacs,
                           "complex_tflops": 8 * tot_cmacs / (step_ms / 1e3) / 1e12},
-               "roofline": roof, "rooflines_in_step": rooflines, "cpu_baseline": cpu,
+               "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu,
                "e2e": {"value": e2e_val, "unit": "knots/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": clk,
@@ -797,7 +811,9 @@ def main():
                                                  "of each launch's duration"},
                "kernel_classes_serialised": {"classes": prof,
                                              "how": "every plan's launches one after another, "
-                                                    "an event pair around each"},
+                                                    "an event pair around each; fill_ms weights "
+                                                    "each launch by the share of the GPU's CTA "
+                                                    "slots it fills"},
                "precisions": compare, "workloads": extra}
         print(json.dumps(out))
     if dist:

@@ -274,8 +274,10 @@ pk_status pk_plan_debug_blob(const pk_plan* p, int32_t which, void* dst, uint64_
  * 3 results, 4 GEMM on CUDA cores, 5 GEMM on the tensor cores, 6 digit conversion for
  * the tensor-core GEMM): out[c] = milliseconds, out[7+c] = launches, out[14+c] =
  * algorithmic complex multiply-adds, out[21+c] = algorithmic bytes (|A| + |B| + |C| at
- * the precision's element size; for class 6 the operands it reads, |A| + |B|).
- * 28 doubles. */
+ * the precision's element size; for class 6 the operands it reads, |A| + |B|),
+ * out[28+c] = milliseconds weighted per launch by the share of the GPU it fills
+ * (min(1, CTAs / (multiprocessors x CTAs resident per multiprocessor)): the class's
+ * share of a step in which many plans' launches run concurrently).  35 doubles. */
 pk_status pk_profile(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                      uint64_t workspace_bytes, void* d_arena, uint64_t arena_bytes, double* out);
 
@@ -301,9 +303,17 @@ pk_status pk_group_create_profiled(pk_ctx* ctx, const pk_plan* const* plans, int
                                    int32_t precision, void* const* d_workspaces,
                                    const uint64_t* workspace_bytes, pk_group** out);
 /* Waits for the context's stream, then reads the events of the last replay of a
- * profiled group: per kernel class as pk_profile (28 doubles), the milliseconds being the
+ * profiled group: per kernel class as pk_profile (35 doubles), the milliseconds being the
  * sum over launches of each launch's in-replay duration.  PK_EINVAL for a plain group. */
 pk_status pk_group_profile(pk_ctx* ctx, const pk_group* grp, double* out);
+/* The last replay of a profiled group as a timeline: per kernel launch 6 doubles (plan
+ * index in the group, kernel class as in pk_profile, start and end in milliseconds after
+ * the first plan's first launch began -- negative when earlier --, complex multiply-adds,
+ * algorithmic bytes), plans in group order, launches in launch order.  Writes at most
+ * `capacity` launches and sets *count to the number of launches (PK_ENOMEM when larger
+ * than capacity).  Waits for the context's stream first. */
+pk_status pk_group_timeline(pk_ctx* ctx, const pk_group* grp, double* out, int64_t capacity,
+                            int64_t* count);
 
 /* ---- batched evaluation (many knots in one launch) ------------------------------- */
 

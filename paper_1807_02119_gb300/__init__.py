@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libpk.so")
 PK_C128, PK_C64, PK_SPLIT = 0, 1, 2
 FLAG_FORCE_GEMM, FLAG_FORCE_ROWS, FLAG_GRAD, FLAG_NO_TC, FLAG_TC_DIGITS4 = 1, 2, 4, 8, 16
 PRECISIONS = {"c128": PK_C128, "c64": PK_C64, "split": PK_SPLIT}
+PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4,
           "fill_spin": 5}
 STATUS = {0: "PK_OK", 1: "PK_EINVAL", 2: "PK_ENOTKNOT", 3: "PK_ENOMEM", 4: "PK_ETOOWIDE",
@@ -33,7 +34,7 @@ EXPORTED = [
     "pk_group_launch", "pk_group_destroy", "pk_grad_workspace_bytes", "pk_grad",
     "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights", "pk_eval_exact",
     "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve", "pk_decode_result",
-    "pk_group_create_profiled", "pk_group_profile",
+    "pk_group_create_profiled", "pk_group_profile", "pk_group_timeline",
 ]
 
 
@@ -122,6 +123,7 @@ def lib():
         "pk_group_launch": [vp, vp],
         "pk_group_create_profiled": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
         "pk_group_profile": [vp, vp, P(C.c_double)],
+        "pk_group_timeline": [vp, vp, P(C.c_double), i64, P(i64)],
         "pk_group_destroy": [vp],
         "pk_grad_workspace_bytes": [vp, i32, P(u64)],
         "pk_grad": [vp, vp, i32, vp, u64, P(pk_scaled), P(pk_scaled), P(C.c_double),
@@ -521,7 +523,7 @@ def profile(plan: Plan, precision: str, ws, arena=None):
     """Per kernel class (build, rows, splitk, results, gemm, gemm_tc): ms, launches, complex MACs,
     bytes of one pass of the plan's kernels, timed with CUDA events on the context's
     stream.  `arena` (optional) is a separate tensor arena as for launch_arena()."""
-    out = (C.c_double * 28)()
+    out = (C.c_double * 35)()
     ap = C.c_void_p(arena.data_ptr()) if arena is not None else None
     an = arena.numel() if arena is not None else 0
     _check(lib().pk_profile(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
@@ -535,7 +537,7 @@ CLASSES = ("build", "rows", "splitk", "results", "gemm", "gemm_tc", "digits")
 def _classes(out):
     n = len(CLASSES)
     return {c: {"ms": out[i], "launches": out[n + i], "cmacs": out[2 * n + i],
-                "bytes": out[3 * n + i]} for i, c in enumerate(CLASSES)}
+                "bytes": out[3 * n + i], "fill_ms": out[4 * n + i]} for i, c in enumerate(CLASSES)}
 
 
 class Batch:
@@ -611,6 +613,7 @@ class Group:
         fn = lib().pk_group_create_profiled if profiled else lib().pk_group_create
         _check(fn(self.ctx.h, parr, n, PRECISIONS[precision], warr, barr, C.byref(h)), self.ctx)
         self.h = h
+        self.precision = PRECISIONS[precision]
 
     def launch(self):
         _check(lib().pk_group_launch(self.ctx.h, self.h), self.ctx)
@@ -618,9 +621,19 @@ class Group:
     def profile(self):
         """Per kernel class: summed in-replay launch durations (ms), launches, complex
         multiply-adds, algorithmic bytes of the last replay."""
-        out = (C.c_double * 28)()
+        out = (C.c_double * 35)()
         _check(lib().pk_group_profile(self.ctx.h, self.h, out), self.ctx)
         return _classes(out)
+
+    def timeline(self):
+        """The last replay of a profiled group, one tuple per launch: (plan index, class
+        name, start ms, end ms, complex multiply-adds, algorithmic bytes)."""
+        n = C.c_int64()
+        cap = max(1, sum(p.launches(PRECISION_NAMES[self.precision]) for p in self.plans) * 2)
+        buf = (C.c_double * (6 * cap))()
+        _check(lib().pk_group_timeline(self.ctx.h, self.h, buf, cap, C.byref(n)), self.ctx)
+        return [(int(buf[6 * i]), CLASSES[int(buf[6 * i + 1])], buf[6 * i + 2], buf[6 * i + 3],
+                 buf[6 * i + 4], buf[6 * i + 5]) for i in range(n.value)]
 
     def __del__(self):
         try:

@@ -601,6 +601,18 @@ pk_status pk_group_profile(pk_ctx* ctx, const pk_group* grp, double* out) {
   return e == cudaSuccess ? PK_OK : cuda_fail(ctx, e, "group profile");
 }
 
+pk_status pk_group_timeline(pk_ctx* ctx, const pk_group* grp, double* out, int64_t capacity,
+                            int64_t* count) {
+  if (!ctx || !grp || !count || (capacity > 0 && !out)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (grp->profs.empty() && grp->n > 0) return fail(ctx, PK_EINVAL, "group was not created profiled");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess)
+    e = pk::prof_timeline(grp->profs.data(), (int)grp->profs.size(), out, capacity, count);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "group timeline");
+  return *count > capacity ? fail(ctx, PK_ENOMEM, "timeline buffer too small") : PK_OK;
+}
+
 pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp) {
   if (!ctx || !grp) return fail(ctx, PK_EINVAL, "bad argument");
   if (grp->n == 0) return PK_OK;

@@ -45,9 +45,13 @@ struct Prof;
 Prof* prof_new();
 void prof_free(Prof* p);
 // Per class c: out[c] summed milliseconds, out[7+c] launches, out[14+c] complex
-// multiply-adds, out[21+c] algorithmic bytes, over n recorded sequences whose events
-// have completed.
+// multiply-adds, out[21+c] algorithmic bytes, out[28+c] milliseconds weighted by the share
+// of the GPU's CTA slots each launch fills, over n recorded sequences whose events have
+// completed.
 cudaError_t prof_read(Prof* const* profs, int n, double* out);
+// Per launch of n recorded sequences: (sequence, class, start ms, end ms, complex
+// multiply-adds, algorithmic bytes), times relative to the first sequence's first event.
+cudaError_t prof_timeline(Prof* const* profs, int n, double* out, int64_t cap, int64_t* count);
 // launch_plan with an event pair around every launch, recorded into `prof` (which must
 // outlive any graph the launches are captured into).
 cudaError_t launch_plan_prof(const Plan& p, int32_t precision, void* ws, void* arena,

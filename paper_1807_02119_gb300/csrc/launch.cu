@@ -48,6 +48,8 @@ struct Prof {
          bytes[kNumClasses] = {};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   std::vector<int> cls;
+  std::vector<double> ev_cmacs, ev_bytes;   // per launch
+  std::vector<double> ev_fill;              // per launch: share of the GPU's CTA slots it fills
   ~Prof() {
     for (auto& e : ev) {
       cudaEventDestroy(e.first);
@@ -57,6 +59,14 @@ struct Prof {
 };
 
 namespace {
+
+int g_sms = 152;   // multiprocessors of the current device (set by prepare_kernels)
+
+// Share of the GPU a launch of `grid` CTAs occupies when `per_sm` of them fit on one
+// multiprocessor: 1 for a grid that fills every slot, less for smaller grids.
+double gpu_fill(long long grid, int per_sm) {
+  return std::min(1.0, (double)grid / ((double)g_sms * (double)per_sm));
+}
 
 struct Marker {
   Prof* prof;
@@ -71,13 +81,16 @@ struct Marker {
     else
       cudaEventRecord(e, st);
   }
-  void begin(int c, double cm, double by) {
+  void begin(int c, double cm, double by, double fill) {
     if (!prof) return;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     prof->ev.push_back({a, b});
     prof->cls.push_back(c);
+    prof->ev_cmacs.push_back(cm);
+    prof->ev_bytes.push_back(by);
+    prof->ev_fill.push_back(fill);
     prof->n[c] += 1;
     prof->cmacs[c] += cm;
     prof->bytes[c] += by;
@@ -93,18 +106,23 @@ struct Marker {
 constexpr long long kFewRows = 152LL * 2048;
 
 template <typename R>
-cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st) {
+cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st, Marker& mk,
+                        double cm, double by) {
   const size_t sm = sizeof(long long) * (size_t)(2 * s.K + s.N);
   if (s.R < kFewRows && s.N > 1 && sizeof(long long) * 2 * (size_t)s.K <= 200 * 1024) {
     const long long outs = s.R * s.N;
     const long long blocks = std::max<long long>(1, std::min<long long>((outs + 255) / 256, 152 * 16));
+    mk.begin(1, cm, by, gpu_fill(blocks, 8));
     k_outs<R><<<(unsigned)blocks, 256, sizeof(long long) * 2 * (size_t)s.K, st>>>(s, arena, meta);
+    mk.end();
     return cudaGetLastError();
   }
   long long blocks = (s.R + 255) / 256;
   blocks = std::max<long long>(1, std::min<long long>(blocks, 152 * 8));
+  mk.begin(1, cm, by, gpu_fill(blocks, 8));
   if (sm > 200 * 1024) {
     k_rows_big<R><<<(unsigned)blocks, 256, 0, st>>>(s, arena, meta);
+    mk.end();
     return cudaGetLastError();
   }
   const int kmax = sizeof(R) == 8 ? 16 : 32;
@@ -125,6 +143,7 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
   else
     fn = k_rows<R, 0>;
   fn<<<(unsigned)blocks, 256, sm, st>>>(s, arena, meta);  // limit raised by prepare_kernels
+  mk.end();
   return cudaGetLastError();
 }
 
@@ -136,12 +155,13 @@ cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* t
                       unsigned long long* err, cudaStream_t stream, Marker& mk, double cm, double by) {
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
   // class 6 (digit conversion): its bytes are the operands it reads, |A| + |B|
-  mk.begin(6, 0.0, (double)sizeof(Cx<ff>) * (double)(s.R * s.K + s.Bsz * s.K * s.N));
   const long long nA = s.Bsz * L.tiles_m * L.groups, nB = s.Bsz * L.tiles_n * L.groups;
+  mk.begin(6, 0.0, (double)sizeof(Cx<ff>) * (double)(s.R * s.K + s.Bsz * s.K * s.N),
+           gpu_fill(nA + nB, 8));
   k_digits<S><<<(unsigned)(nA + nB), tc::kConvThreads, tc::Cfg<S>::kConvSmem, stream>>>(s, arena, tcs, nA);
   mk.end();
   const long long tc_tiles = L.tiles_m * L.tiles_n * s.Bsz;
-  mk.begin(5, cm, by);
+  mk.begin(5, cm, by, gpu_fill(tc_tiles, 2));
   k_gemm_tc<S><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(s, arena, meta, tcs, err);
   mk.end();
   return cudaGetLastError();
@@ -160,20 +180,18 @@ cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* par
         return s.tc == 4 ? launch_tc<4>(s, arena, meta, tc_scratch, err, stream, mk, cm, by)
                          : launch_tc<5>(s, arena, meta, tc_scratch, err, stream, mk, cm, by);
     }
-    mk.begin(4, cm, by);
+    mk.begin(4, cm, by, gpu_fill(gemm_tiles, 8));
     k_gemm<R><<<(unsigned)gemm_tiles, 256, 0, stream>>>(s, arena, meta);
     mk.end();
     e = cudaGetLastError();
   } else if (s.kernel == KSPLITK) {
-    mk.begin(2, cm, by);
+    mk.begin(2, cm, by, gpu_fill((long long)s.chunks * s.R * s.N, 8));
     k_splitk<R><<<dim3((unsigned)s.chunks, (unsigned)(s.R * s.N)), 256, 0, stream>>>(
         s, arena, meta, partial, counter);
     mk.end();
     e = cudaGetLastError();
   } else {
-    mk.begin(1, cm, by);
-    e = launch_rows<R>(s, arena, meta, stream);
-    mk.end();
+    e = launch_rows<R>(s, arena, meta, stream, mk, cm, by);
   }
   return e;
 }
@@ -207,7 +225,7 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
         cm += (double)p.steps[j].R * (double)p.steps[j].K * (double)p.steps[j].N;
         by += step_bytes(p, p.steps[j], (double)sizeof(Cx<R>));
       }
-      mk.begin(1, cm, by);
+      mk.begin(1, cm, by, gpu_fill(1, 8));
       k_seg<R><<<1, 256, 0, stream>>>(tiny + g.tiny0, g.count, arena, meta);
       mk.end();
       cudaError_t e = cudaGetLastError();
@@ -234,7 +252,7 @@ cudaError_t launch_build(const Plan& p, char* base, char* arena_base, long long 
     initel += r.elems;
   }
   const unsigned bx = (unsigned)std::min<int64_t>((maxel + 255) / 256, 64);
-  mk.begin(0, 0, (double)sizeof(Cx<R>) * (double)initel);
+  mk.begin(0, 0, (double)sizeof(Cx<R>) * (double)initel, gpu_fill((long long)bx * p.n_init, 8));
   k_build<R><<<dim3(bx, (unsigned)p.n_init), 256, 0, stream>>>(
       (const Recipe*)(base + p.off_recipe), (const Slot*)(base + p.off_slots),
       (Cx<R>*)arena_base, (Meta*)(base + p.off_meta), p.q, sl, (int)p.sliced.size());
@@ -262,7 +280,7 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
     if (precision == PK_C128) {
       if ((e = launch_build<double>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
       if ((e = launch_bulk<double>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
-      mk.begin(3, 0, 0);
+      mk.begin(3, 0, 0, gpu_fill(1, 8));
       k_slice_result<double><<<1, 32, 0, stream>>>((Cx<double>*)arena_base,
                                                    p.tensors[p.final_tensor].offset,
                                                    (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
@@ -270,7 +288,7 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
     } else if (precision == PK_SPLIT) {
       if ((e = launch_build<ff>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
       if ((e = launch_bulk<ff>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
-      mk.begin(3, 0, 0);
+      mk.begin(3, 0, 0, gpu_fill(1, 8));
       k_slice_result<ff><<<1, 32, 0, stream>>>((Cx<ff>*)arena_base,
                                                p.tensors[p.final_tensor].offset,
                                                (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
@@ -278,7 +296,7 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
     } else if (p.tail.empty() && p.conv.empty()) {  // complex64
       if ((e = launch_build<float>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
       if ((e = launch_bulk<float>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
-      mk.begin(3, 0, 0);
+      mk.begin(3, 0, 0, gpu_fill(1, 8));
       k_slice_result<float><<<1, 32, 0, stream>>>((Cx<float>*)arena_base,
                                                   p.tensors[p.final_tensor].offset,
                                                   (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
@@ -292,7 +310,7 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
         int64_t maxel = 1;
         for (const auto& c : p.conv) maxel = std::max<int64_t>(maxel, c.elems);
         const unsigned bx = (unsigned)std::min<int64_t>((maxel + 255) / 256, 256);
-        mk.begin(0, 0, 24.0 * (double)maxel);
+        mk.begin(0, 0, 24.0 * (double)maxel, gpu_fill((long long)bx * p.conv.size(), 8));
         k_widen<<<dim3(bx, (unsigned)p.conv.size()), 256, 0, stream>>>(
             (const ConvRec*)(base + p.off_conv), (const Cx<float>*)arena_base, tail, meta);
         mk.end();
@@ -310,14 +328,14 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
                                 step_bytes(p, p.steps[ts.step], 16.0));
         if (e != cudaSuccess) return e;
       }
-      mk.begin(3, 0, 0);
+      mk.begin(3, 0, 0, gpu_fill(1, 8));
       k_slice_result<double><<<1, 32, 0, stream>>>(tail, p.final_tail_off, meta, p.final_tensor,
                                                    res, sl);
       mk.end();
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  mk.begin(3, 0, 0);
+  mk.begin(3, 0, 0, gpu_fill(1, 8));
   k_sum_slices<<<1, 256, 0, stream>>>(res, p.n_slices);
   mk.end();
   return cudaGetLastError();
@@ -413,6 +431,9 @@ cudaError_t prepare_kernels() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+    g_sms = sms;
   if (dev >= 0 && dev < 256 && done[dev]) return cudaSuccess;
   if ((e = raise_rows_smem<double>()) != cudaSuccess) return e;
   if ((e = raise_rows_smem<float>()) != cudaSuccess) return e;
@@ -452,7 +473,8 @@ void prof_free(Prof* p) { delete p; }
 // Per class: summed event durations of the recorded launches (after they completed),
 // launches, complex multiply-adds, algorithmic bytes.
 cudaError_t prof_read(Prof* const* profs, int n, double* out) {
-  double ms[kNumClasses] = {}, cnt[kNumClasses] = {}, cm[kNumClasses] = {}, by[kNumClasses] = {};
+  double ms[kNumClasses] = {}, cnt[kNumClasses] = {}, cm[kNumClasses] = {}, by[kNumClasses] = {},
+         fm[kNumClasses] = {};
   cudaError_t err = cudaSuccess;
   for (int j = 0; j < n; ++j) {
     const Prof& prof = *profs[j];
@@ -461,6 +483,7 @@ cudaError_t prof_read(Prof* const* profs, int n, double* out) {
       cudaError_t e = cudaEventElapsedTime(&t, prof.ev[i].first, prof.ev[i].second);
       if (e != cudaSuccess && err == cudaSuccess) err = e;
       ms[prof.cls[i]] += t;
+      fm[prof.cls[i]] += t * prof.ev_fill[i];
     }
     for (int c = 0; c < kNumClasses; ++c) {
       cnt[c] += prof.n[c];
@@ -473,8 +496,39 @@ cudaError_t prof_read(Prof* const* profs, int n, double* out) {
     out[kNumClasses + c] = cnt[c];
     out[2 * kNumClasses + c] = cm[c];
     out[3 * kNumClasses + c] = by[c];
+    out[4 * kNumClasses + c] = fm[c];
   }
   return err;
+}
+
+// Every recorded launch of n sequences (events completed) as 6 doubles: sequence index,
+// class, start and end in milliseconds after the first sequence's first event (negative
+// when earlier), complex multiply-adds, algorithmic bytes.  Writes at most cap records;
+// *count = the number of launches.
+cudaError_t prof_timeline(Prof* const* profs, int n, double* out, int64_t cap, int64_t* count) {
+  int64_t k = 0;
+  cudaEvent_t ref = nullptr;
+  for (int j = 0; j < n && !ref; ++j)
+    if (!profs[j]->ev.empty()) ref = profs[j]->ev[0].first;
+  for (int j = 0; j < n; ++j) {
+    const Prof& prof = *profs[j];
+    for (size_t i = 0; i < prof.ev.size(); ++i, ++k) {
+      if (k >= cap) continue;
+      float t0 = 0, t1 = 0;
+      cudaError_t e = cudaEventElapsedTime(&t0, ref, prof.ev[i].first);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ref, prof.ev[i].second);
+      if (e != cudaSuccess) return e;
+      double* r = out + 6 * k;
+      r[0] = j;
+      r[1] = prof.cls[i];
+      r[2] = t0;
+      r[3] = t1;
+      r[4] = prof.ev_cmacs[i];
+      r[5] = prof.ev_bytes[i];
+    }
+  }
+  *count = k;
+  return cudaSuccess;
 }
 
 cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,
