@@ -799,6 +799,8 @@ def main():
                                       "random over/under, q in {2,3,5}; 192 (knot, q) evaluations per step",
                           "order": f"auto per knot (lowest estimated cost after slicing, {args.restarts} min-fill restarts)",
                           "l2": "flushed between steps (512 MB write)",
+                          "tuning": dict(ctx.tuning(), source="compiled-in table written by "
+                                         "paper_1807_02119_gb300/autotune.py"),
                           "plan_seconds": plan_s, "complex_macs_per_step": tot_cmacs,
                           "complex_tflops": 8 * tot_cmacs / (step_ms / 1e3) / 1e12},
                "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu,

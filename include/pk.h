@@ -138,6 +138,24 @@ typedef struct {
   int32_t n_segment_steps;   /* steps inside those runs                                     */
 } pk_plan_stats;
 
+/* ---- tuning ------------------------------------------------------------------- */
+
+/* Launch-shape parameters of the executor, chosen per GPU by measurement (the package's
+ * autotune script sweeps them on the configured workloads and writes the table the
+ * library is compiled with; pk_tuning_default returns that table).  A context starts with
+ * the defaults; pk_ctx_set_tuning changes them for plans and batches created afterwards. */
+typedef struct {
+  int32_t batch_threads;     /* threads per CTA of the batch executor: 128, 256 or 512       */
+  int32_t batch_ktab;        /* batch executor: contracted-index offsets of a step kept in
+                                shared memory (steps with longer K recompute them): 256..2048 */
+  int64_t seq_outs;          /* runs of small steps launched as one sequence kernel: outputs
+                                per step at most (1..65536)                                   */
+  int64_t seq_work;          /* ... complex multiply-adds per step at most (1..2^24)          */
+  int64_t seq_k;             /* ... contracted extent per step at most (1..2048)              */
+} pk_tuning;
+
+pk_status pk_tuning_default(pk_tuning* out);
+
 /* ---- context ------------------------------------------------------------------ */
 
 /* device >= 0: a GPU context on that device; stream (a cudaStream_t, may be NULL for
@@ -145,6 +163,9 @@ typedef struct {
  * context for knot input and planning (pk_eval returns PK_ENODEVICE). */
 pk_status pk_ctx_create(int32_t device, void* stream, pk_ctx** out);
 pk_status pk_ctx_set_stream(pk_ctx* ctx, void* stream);
+/* NULL restores the defaults.  PK_EINVAL for values outside the ranges of pk_tuning. */
+pk_status pk_ctx_set_tuning(pk_ctx* ctx, const pk_tuning* t);
+pk_status pk_ctx_get_tuning(const pk_ctx* ctx, pk_tuning* out);
 const char* pk_last_error(const pk_ctx* ctx);
 void pk_ctx_destroy(pk_ctx* ctx);
 

@@ -35,6 +35,7 @@ EXPORTED = [
     "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights", "pk_eval_exact",
     "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve", "pk_decode_result",
     "pk_group_create_profiled", "pk_group_profile", "pk_group_timeline",
+    "pk_tuning_default", "pk_ctx_set_tuning", "pk_ctx_get_tuning",
 ]
 
 
@@ -55,6 +56,11 @@ class pk_plan_opts(C.Structure):
                 ("edge_weights", C.POINTER(C.c_double))]
 
 
+class pk_tuning(C.Structure):
+    _fields_ = [("batch_threads", C.c_int32), ("batch_ktab", C.c_int32), ("seq_outs", C.c_int64),
+                ("seq_work", C.c_int64), ("seq_k", C.c_int64)]
+
+
 class pk_plan_stats(C.Structure):
     _fields_ = [("log2_max_elems", C.c_double), ("cmacs", C.c_double),
                 ("bytes_c64", C.c_double), ("n_slices", C.c_int64), ("n_steps", C.c_int32),
@@ -65,6 +71,13 @@ class pk_plan_stats(C.Structure):
 
 
 _lib = None
+
+
+def default_tuning() -> dict:
+    """pk_tuning_default: the table the library was compiled with (written by autotune.py)."""
+    t = pk_tuning()
+    _check(lib().pk_tuning_default(C.byref(t)))
+    return {f: getattr(t, f) for f, _ in t._fields_}
 
 
 def lib():
@@ -124,6 +137,9 @@ def lib():
         "pk_group_create_profiled": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
         "pk_group_profile": [vp, vp, P(C.c_double)],
         "pk_group_timeline": [vp, vp, P(C.c_double), i64, P(i64)],
+        "pk_tuning_default": [P(pk_tuning)],
+        "pk_ctx_set_tuning": [vp, P(pk_tuning)],
+        "pk_ctx_get_tuning": [vp, P(pk_tuning)],
         "pk_group_destroy": [vp],
         "pk_grad_workspace_bytes": [vp, i32, P(u64)],
         "pk_grad": [vp, vp, i32, vp, u64, P(pk_scaled), P(pk_scaled), P(C.c_double),
@@ -185,6 +201,22 @@ class Context:
 
     def set_stream(self, stream: int):
         _check(lib().pk_ctx_set_stream(self.h, C.c_void_p(stream)), self)
+
+    def tuning(self) -> dict:
+        """The launch shapes plans and batches created now will use (pk_ctx_get_tuning)."""
+        t = pk_tuning()
+        _check(lib().pk_ctx_get_tuning(self.h, C.byref(t)), self)
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def set_tuning(self, **kw):
+        """pk_ctx_set_tuning: change some launch shapes (others keep their current values);
+        with no arguments, restore the compiled-in defaults."""
+        if not kw:
+            _check(lib().pk_ctx_set_tuning(self.h, None), self)
+            return
+        cur = self.tuning()
+        cur.update(kw)
+        _check(lib().pk_ctx_set_tuning(self.h, C.byref(pk_tuning(**cur))), self)
 
     def close(self):
         if self.h:

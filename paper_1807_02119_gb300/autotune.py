@@ -1,0 +1,182 @@
+"""Autotuner for the executor's launch shapes (pk_tuning), run on the target GPU.
+
+Two sweeps, each timed with CUDA events on the stream the kernels run on, L2 flushed
+before every timed launch, the fastest median kept:
+
+* batch executor (`pk_batch_*`, one persistent launch for many knots): threads per CTA
+  x contracted-index offsets kept in shared memory, on the 4096-knot batch workload
+  (q = 3, split precision);
+* sequence runs (consecutive small steps of a plan launched as one one-CTA kernel): the
+  largest step, in outputs and in complex multiply-adds, that joins a run, on the 64-knot
+  scale workload (q = 2, 3, 5; 192 plans replayed as one concurrent graph, split).
+
+Every candidate's results are checked against the first candidate's (same plans, same
+precision) before its time counts.  The winners are written to csrc/tuned_table.h (the
+defaults the library is compiled with) together with every measured time, and a copy of
+the table goes to the output directory given by --out.
+
+Usage (on a GPU): python -m paper_1807_02119_gb300.autotune [--out DIR] [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import datetime
+import os
+import statistics
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+TABLE = os.path.join(HERE, "csrc", "tuned_table.h")
+
+BATCH_THREADS = (128, 256, 512)
+BATCH_KTAB = (512, 1024, 2048)
+SEQ_OUTS = (1024, 2048, 4096, 8192)
+SEQ_WORK = (1 << 12, 1 << 14, 1 << 16)
+
+
+def _rel(a, b):
+    d = a.exp2 - b.exp2
+    ma = a.mantissa * (2.0 ** d if d > -1000 else 0.0)
+    return abs(ma - b.mantissa) / abs(b.mantissa) if b.mantissa != 0 else abs(ma)
+
+
+def _time(launch, stream, flush, reps):
+    import torch
+    for _ in range(3):
+        launch()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        launch()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def sweep_batch(pk, ctx, stream, flush, reps, log):
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    import knotgen as kg
+    knots = kg.knot_suite("batch")
+    kn = [pk.Knot.from_pd(ctx, k.pd, outer=k.outer) for k in knots]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        plans = list(ex.map(lambda k: pk.Plan(ctx, k, 3), kn))
+    rows, ref, best = [], None, None
+    for th in BATCH_THREADS:
+        for kt in BATCH_KTAB:
+            ctx.set_tuning(batch_threads=th, batch_ktab=kt)
+            b = pk.Batch(plans, "split")
+            ws = torch.empty(b.workspace_bytes()[0], dtype=torch.uint8, device="cuda")
+            b.upload(ws)
+            ms = _time(lambda: b.launch(ws), stream, flush, reps)
+            z, v = b.download(ws)
+            if ref is None:
+                ref = z
+            err = max(_rel(x, y) for x, y in zip(z, ref))
+            ok = err <= 1e-6
+            rows.append((th, kt, ms, ok))
+            log(f"batch threads={th} ktab={kt}: {ms:.3f} ms ({len(plans) / ms * 1e3:.0f} knots/s)"
+                f"{'' if ok else ' RESULTS DIFFER'}")
+            if ok and (best is None or ms < best[2]):
+                best = (th, kt, ms)
+            del b, ws
+            torch.cuda.empty_cache()
+    return best, rows
+
+
+def sweep_seq(pk, ctx, stream, flush, reps, log, quick):
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    import knotgen as kg
+    knots = kg.knot_suite("scale")
+    kn = [pk.Knot.from_pd(ctx, k.pd, outer=k.outer) for k in knots]
+    jobs = [(k, q) for k in kn for q in (2, 3, 5)]
+    rows, ref, best = [], None, None
+    outs = SEQ_OUTS if not quick else (2048, 4096)
+    works = SEQ_WORK if not quick else (1 << 12, 1 << 14)
+    for so in outs:
+        for sw in works:
+            ctx.set_tuning(seq_outs=so, seq_work=sw)
+            with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+                plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=128), jobs))
+            ws = [torch.empty(p.workspace_bytes("split") + 256, dtype=torch.uint8, device="cuda")
+                  for p in plans]
+            for p, w in zip(plans, ws):
+                pk.upload(p, "split", w)
+            g = pk.Group(plans, "split", ws)
+            ms = _time(g.launch, stream, flush, reps)
+            z = [pk.download(p, "split", w)[0] for p, w in zip(plans, ws)]
+            if ref is None:
+                ref = z
+            err = max(_rel(x, y) for x, y in zip(z, ref))
+            ok = err <= 1e-6
+            launches = sum(p.launches("split") for p in plans)
+            rows.append((so, sw, ms, ok, launches))
+            log(f"sequence runs outs<={so} work<={sw}: {ms:.2f} ms per step, {launches} launches"
+                f"{'' if ok else ' RESULTS DIFFER'}")
+            if ok and (best is None or ms < best[2]):
+                best = (so, sw, ms)
+            del g, ws, plans
+            torch.cuda.empty_cache()
+    return best, rows
+
+
+def write_table(path, tune, batch_rows, seq_rows, gpu):
+    when = datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%d %H:%M UTC")
+    lines = ["// Executor launch shapes, written by paper_1807_02119_gb300/autotune.py from",
+             f"// measurements on {gpu} ({when}); the library's defaults (pk_tuning_default).",
+             "// Batch executor, 4096 knots at q = 3, split, one launch (median ms):"]
+    for th, kt, ms, ok in batch_rows:
+        lines.append(f"//   threads {th:4d}  ktab {kt:5d}  {ms:8.3f}{'' if ok else '  (results differ)'}")
+    lines.append("// Sequence runs, 192 evaluations of the scale workload, split (median ms per step):")
+    for so, sw, ms, ok, nl in seq_rows:
+        lines.append(f"//   outs <= {so:5d}  work <= {sw:6d}  {ms:8.2f}  ({nl} launches)"
+                     f"{'' if ok else '  (results differ)'}")
+    lines += ["#pragma once", '#include "pk.h"', "",
+              "constexpr pk_tuning kTunedDefault = {" +
+              f"{tune['batch_threads']}, {tune['batch_ktab']}, {tune['seq_outs']}, "
+              f"{tune['seq_work']}, {tune['seq_k']}" + "};", ""]
+    with open(path, "w") as f:
+        f.write("\n".join(lines))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None, help="also copy the table here")
+    ap.add_argument("--reps", type=int, default=7)
+    ap.add_argument("--quick", action="store_true", help="a smaller sequence-run sweep")
+    args = ap.parse_args()
+    sys.path.insert(0, ROOT)
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1807_02119_gb300 as pk
+
+    def log(m):
+        print(f"[autotune] {m}", flush=True)
+
+    ctx = pk.Context(0)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream.cuda_stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    tune = pk.default_tuning()
+    (bt, bk, _), brows = sweep_batch(pk, ctx, stream, flush, args.reps, log)
+    ctx.set_tuning()
+    (so, sw, _), srows = sweep_seq(pk, ctx, stream, flush, args.reps, log, args.quick)
+    tune.update(batch_threads=bt, batch_ktab=bk, seq_outs=so, seq_work=sw)
+    gpu = torch.cuda.get_device_name(0)
+    write_table(TABLE, tune, brows, srows, gpu)
+    if args.out:
+        os.makedirs(args.out, exist_ok=True)
+        write_table(os.path.join(args.out, "tuned_table.h"), tune, brows, srows, gpu)
+    log(f"chosen: {tune}")
+
+
+if __name__ == "__main__":
+    main()

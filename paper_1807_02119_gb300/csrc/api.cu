@@ -170,6 +170,29 @@ pk_status pk_ctx_create(int32_t device, void* stream, pk_ctx** out) {
   return PK_OK;
 }
 
+pk_status pk_tuning_default(pk_tuning* out) {
+  if (!out) return PK_EINVAL;
+  *out = kTunedDefault;
+  return PK_OK;
+}
+
+pk_status pk_ctx_set_tuning(pk_ctx* ctx, const pk_tuning* t) {
+  if (!ctx) return PK_EINVAL;
+  if (!t) {
+    ctx->tuning = kTunedDefault;
+    return PK_OK;
+  }
+  if (!pk::valid_tuning(*t)) return fail(ctx, PK_EINVAL, "tuning value out of range");
+  ctx->tuning = *t;
+  return PK_OK;
+}
+
+pk_status pk_ctx_get_tuning(const pk_ctx* ctx, pk_tuning* out) {
+  if (!ctx || !out) return PK_EINVAL;
+  *out = ctx->tuning;
+  return PK_OK;
+}
+
 pk_status pk_ctx_set_stream(pk_ctx* ctx, void* stream) {
   if (!ctx) return PK_EINVAL;
   ctx->stream = (cudaStream_t)stream;
@@ -291,7 +314,7 @@ pk_status pk_plan_create(pk_ctx* ctx, const pk_knot* k, int32_t q, const pk_plan
   pk_plan* p = new (std::nothrow) pk_plan();
   if (!p) return fail(ctx, PK_ENOMEM, "out of host memory");
   std::string err;
-  if (!pk::make_plan(k->k, q, o, p->p, err)) {
+  if (!pk::make_plan(k->k, q, o, ctx ? ctx->tuning : kTunedDefault, p->p, err)) {
     delete p;
     if (err.find("slices") != std::string::npos || err.find("runs") != std::string::npos)
       return fail(ctx, PK_ETOOWIDE, err);

@@ -46,8 +46,6 @@ struct BatchStep {
 
 namespace {
 
-constexpr int kBatchThreads = 256;
-constexpr int kKTab = 2048;   // contracted-index offset table entries in shared memory
 
 template <typename S>
 __device__ __forceinline__ S block_max(S v, S* red) {
@@ -65,7 +63,8 @@ __device__ __forceinline__ S block_max(S v, S* red) {
 // step's runs are staged in shared memory first.
 template <typename R>
 __device__ void cta_step(const BatchStep& s, const Run* __restrict__ runs, Run* srun,
-                         Cx<R>* arena, Meta* meta, long long* tbl, typename Traits<R>::S* red) {
+                         Cx<R>* arena, Meta* meta, long long* tbl, int ktab,
+                         typename Traits<R>::S* red) {
   using S = typename Traits<R>::S;
   const int nruns = s.nrow + s.nk + s.nn;
   for (int i = threadIdx.x; i < nruns; i += blockDim.x) srun[i] = runs[s.run0 + i];
@@ -83,10 +82,10 @@ __device__ void cta_step(const BatchStep& s, const Run* __restrict__ runs, Run* 
   }
   const long long exp_c = meta[s.a].exp + xb + ea + eb;
   const S scale = (S)ldexp(1.0, -(ea + eb));
-  const bool tab = s.K <= kKTab;
+  const bool tab = s.K <= ktab;
   if (tab)
     for (long long k = threadIdx.x; k < s.K; k += blockDim.x)
-      split_runs((unsigned long long)k, kr, s.nk, tbl[k], tbl[kKTab + k]);
+      split_runs((unsigned long long)k, kr, s.nk, tbl[k], tbl[ktab + k]);
   __syncthreads();
   const Cx<R>* A = arena + s.off_a;
   const Cx<R>* B = arena + s.off_b;
@@ -103,7 +102,7 @@ __device__ void cta_step(const BatchStep& s, const Run* __restrict__ runs, Run* 
       long long ka, kb;
       if (tab) {
         ka = tbl[k];
-        kb = tbl[kKTab + k];
+        kb = tbl[ktab + k];
       } else {
         split_runs((unsigned long long)k, kr, s.nk, ka, kb);
       }
@@ -125,13 +124,13 @@ __device__ void cta_step(const BatchStep& s, const Run* __restrict__ runs, Run* 
   __syncthreads();
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchKnot* __restrict__ knots,
-                                                         int n_knots, const Recipe* recs,
-                                                         const Slot* slots, const BatchStep* steps,
-                                                         const Run* runs, Cx<R>* arena,
-                                                         Meta* meta_all, SliceResult* out,
-                                                         unsigned* next) {
+// T threads per CTA; ktab offsets of the contracted index per step in shared memory.
+template <typename R, int T>
+__global__ void __launch_bounds__(T) k_batch(const BatchKnot* __restrict__ knots, int n_knots,
+                                             const Recipe* recs, const Slot* slots,
+                                             const BatchStep* steps, const Run* runs, Cx<R>* arena,
+                                             Meta* meta_all, SliceResult* out, unsigned* next,
+                                             int ktab) {
   using S = typename Traits<R>::S;
   extern __shared__ long long tbl[];
   __shared__ S red[32];
@@ -177,7 +176,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchKnot* __rest
       }
       __syncthreads();
       for (long long i = 0; i < K.n_steps; ++i)
-        cta_step<R>(steps[K.step0 + i], runs, srun, A0, meta, tbl, red);
+        cta_step<R>(steps[K.step0 + i], runs, srun, A0, meta, tbl, ktab, red);
       if (threadIdx.x == 0) {  // add this slice's scalar at a common exponent
         const Cx<R> v = ldc(A0 + K.final_offset);
         double vr = to_double(v.re), vi = to_double(v.im);
@@ -237,6 +236,7 @@ struct pk_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int32_t device = -1;
+  int32_t threads = 256, ktab = 2048;   // launch shape (the context's tuning at creation)
 };
 
 namespace {
@@ -247,8 +247,10 @@ pk_status bfail(pk_ctx* c, pk_status s, const std::string& m) {
 }
 
 template <typename R>
-void* batch_kernel() {
-  return (void*)pk::k_batch<R>;
+void* batch_kernel(int threads) {
+  if (threads == 128) return (void*)pk::k_batch<R, 128>;
+  if (threads == 512) return (void*)pk::k_batch<R, 512>;
+  return (void*)pk::k_batch<R, 256>;
 }
 
 cudaError_t build_graph(pk_batch* b, void* ws, cudaStream_t stream) {
@@ -277,12 +279,12 @@ cudaError_t build_graph(pk_batch* b, void* ws, cudaStream_t stream) {
   if (e != cudaSuccess) return e;
   void* func;
   if (b->precision == PK_C128)
-    func = batch_kernel<double>();
+    func = batch_kernel<double>(b->threads);
   else if (b->precision == PK_C64)
-    func = batch_kernel<float>();
+    func = batch_kernel<float>(b->threads);
   else
-    func = batch_kernel<pk::ff>();
-  const size_t smem = sizeof(long long) * 2 * pk::kKTab;
+    func = batch_kernel<pk::ff>(b->threads);
+  const size_t smem = sizeof(long long) * 2 * (size_t)b->ktab;
   e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const pk::BatchKnot* knots = (const pk::BatchKnot*)(base + b->off_knots);
@@ -295,9 +297,10 @@ cudaError_t build_graph(pk_batch* b, void* ws, cudaStream_t stream) {
   pk::Meta* meta = (pk::Meta*)(base + b->off_meta);
   pk::SliceResult* res = (pk::SliceResult*)(base + b->off_results);
   unsigned* counter = (unsigned*)(base + b->off_counter);
-  void* args[] = {&knots, &n, &recs, &slots, &steps, &runs, &arena, &meta, &res, &counter};
+  int ktab = b->ktab;
+  void* args[] = {&knots, &n, &recs, &slots, &steps, &runs, &arena, &meta, &res, &counter, &ktab};
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, pk::kBatchThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, b->threads, smem);
   if (e != cudaSuccess) return e;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -306,7 +309,7 @@ cudaError_t build_graph(pk_batch* b, void* ws, cudaStream_t stream) {
   std::memset(&kp, 0, sizeof(kp));
   kp.func = func;
   kp.gridDim = dim3((unsigned)grid);
-  kp.blockDim = dim3(pk::kBatchThreads);
+  kp.blockDim = dim3((unsigned)b->threads);
   kp.sharedMemBytes = (unsigned)smem;
   kp.kernelParams = args;
   e = cudaGraphAddKernelNode(&kernel_node, b->graph, &memset_node, 1, &kp);
@@ -332,6 +335,8 @@ pk_status pk_batch_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
   b->precision = precision;
   b->n = n;
   b->device = ctx ? ctx->device : -1;
+  b->threads = ctx ? ctx->tuning.batch_threads : kTunedDefault.batch_threads;
+  b->ktab = ctx ? ctx->tuning.batch_ktab : kTunedDefault.batch_ktab;
   int64_t arena = 0, meta = 0;
   for (int32_t i = 0; i < n; ++i) {
     if (!plans[i]) {

@@ -53,7 +53,7 @@ bool holds(const std::vector<int32_t>& d, int32_t x) {
 
 }  // namespace
 
-bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err) {
+bool make_grad_program(Plan& p, int32_t stride, int32_t flags, const pk_tuning& tune, std::string& err) {
   GradProgram& G = p.grad;
   G = GradProgram();
   G.stride = stride > 1 ? stride : 1;
@@ -288,7 +288,7 @@ bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err)
   }
 
   // runs of small steps as sequence launches
-  build_segments(G.steps, G.segments, G.tiny);
+  build_segments(G.steps, tune, G.segments, G.tiny);
 
   // workspace layout
   const uint64_t nl = std::max<size_t>(1, G.leaves.size());

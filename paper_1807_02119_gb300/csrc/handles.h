@@ -8,7 +8,10 @@
 
 #include "pk_internal.h"
 
+#include "tuned_table.h"
+
 struct pk_ctx {
+  pk_tuning tuning = kTunedDefault;
   int32_t device = -1;
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;  // private stream on which launch sequences are recorded

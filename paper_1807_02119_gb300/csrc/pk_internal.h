@@ -155,9 +155,7 @@ struct Segment {
   int32_t first, count;
   int32_t tiny0;           // index of the first step's TinyStep record
 };
-constexpr int64_t kTinyOuts = 2048;       // outputs per step at most
-constexpr int64_t kTinyWork = 1 << 12;    // complex multiply-adds per step at most
-constexpr int64_t kTinyK = 2048;          // contracted extent (offset table in shared memory)
+constexpr int64_t kTinyK = 2048;          // contracted extent at most (offset table in shared memory)
 
 struct TailStep {
   int32_t step;
@@ -292,6 +290,7 @@ struct Plan {
   std::vector<Segment> segments;     // runs of small steps launched as one sequence kernel
   std::vector<TinyStep> tiny;        // their records (in the program at off_tiny)
   uint64_t off_tiny = 0;
+  pk_tuning tuning{};                // launch shapes the plan was made with
   std::vector<TailStep> tail;        // one per step >= tail_first
   int64_t tail_elems = 0;            // complex128 elements of the tail region
   int64_t final_tail_off = 0;        // final tensor's offset in the tail region
@@ -322,13 +321,15 @@ pk_status decode_total(const Plan& P, const SliceResult& r, pk_scaled* Z, pk_sca
 bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
                 bool& swapped, std::vector<int32_t>& cdims, std::string& err);
-bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std::string& err);
-// Maximal runs (>= 2) of consecutive small row-kernel steps (<= kTinyOuts outputs, K <=
-// kTinyK, <= kTinyWork complex multiply-adds), with their compact records, for the
-// sequence kernel k_seg.
-void build_segments(const std::vector<Step>& steps, std::vector<Segment>& segments,
-                    std::vector<TinyStep>& tiny);
-bool make_grad_program(Plan& p, int32_t stride, int32_t flags, std::string& err);
+bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuning& tune, Plan& p,
+               std::string& err);
+// Maximal runs (>= 2) of consecutive small row-kernel steps (at most tune.seq_outs outputs,
+// K <= tune.seq_k <= kTinyK, at most tune.seq_work complex multiply-adds), with their
+// compact records, for the sequence kernel k_seg.
+void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,
+                    std::vector<Segment>& segments, std::vector<TinyStep>& tiny);
+bool valid_tuning(const pk_tuning& t);
+bool make_grad_program(Plan& p, int32_t stride, int32_t flags, const pk_tuning& tune, std::string& err);
 // Writes the clause values of p.weights into p.slots and both program blobs.
 void apply_weights(Plan& p);
 // New per-edge weights (4 doubles per Tait edge; NULL: the standard weights of t(q)) for a

@@ -948,13 +948,20 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
 }
 
 // ------------------------------------------------------------------ plan assembly
-void build_segments(const std::vector<Step>& steps, std::vector<Segment>& segments,
-                    std::vector<TinyStep>& tiny) {
+bool valid_tuning(const pk_tuning& t) {
+  return (t.batch_threads == 128 || t.batch_threads == 256 || t.batch_threads == 512) &&
+         t.batch_ktab >= 256 && t.batch_ktab <= 2048 && t.seq_outs >= 1 && t.seq_outs <= 65536 &&
+         t.seq_work >= 1 && t.seq_work <= (1 << 24) && t.seq_k >= 1 && t.seq_k <= kTinyK;
+}
+
+void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,
+                    std::vector<Segment>& segments, std::vector<TinyStep>& tiny) {
   segments.clear();
   tiny.clear();
+  const int64_t max_k = std::min<int64_t>(tune.seq_k, kTinyK);
   auto small = [&](const Step& st) {
-    return st.kernel == KROWS && st.R * st.N <= kTinyOuts && st.K <= kTinyK &&
-           st.R * st.N * st.K <= kTinyWork;
+    return st.kernel == KROWS && st.R * st.N <= tune.seq_outs && st.K <= max_k &&
+           st.R * st.N * st.K <= tune.seq_work;
   };
   const int32_t n_steps = (int32_t)steps.size();
   int32_t s0 = 0;
@@ -1009,8 +1016,10 @@ uint64_t Plan::ws_bytes(int32_t precision) const {
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
-bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std::string& err) {
+bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuning& tune, Plan& p,
+               std::string& err) {
   p = Plan();
+  p.tuning = tune;
   if (q < 1 || q > 64) {
     err = "q out of range";
     return false;
@@ -1321,7 +1330,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
   }
 
   // ---- segments: maximal runs (>= 2) of consecutive small row-kernel steps
-  build_segments(p.steps, p.segments, p.tiny);
+  build_segments(p.steps, tune, p.segments, p.tiny);
 
   // ---- workspace layout
   uint64_t off = 0;
@@ -1352,7 +1361,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, Plan& p, std:
     std::memcpy(p.program.data() + p.off_conv, p.conv.data(), sizeof(ConvRec) * p.conv.size());
   if (!p.tiny.empty())
     std::memcpy(p.program.data() + p.off_tiny, p.tiny.data(), sizeof(TinyStep) * p.tiny.size());
-  if (grad && !make_grad_program(p, opts.checkpoint_stride, opts.flags, err)) return false;
+  if (grad && !make_grad_program(p, opts.checkpoint_stride, opts.flags, tune, err)) return false;
   return true;
 }
 

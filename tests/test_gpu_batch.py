@@ -140,3 +140,22 @@ def test_group_concurrent_replay(ctx, prec):
         for p, (z, v) in zip(plans, got):
             zs, vs = pk.evaluate(p, prec)
             assert rel_err(sc(z), sc(zs)) <= TOL[prec] and rel_err(sc(v), sc(vs)) <= TOL[prec]
+
+
+def test_batch_launch_shapes_agree(ctx):
+    """Every batch launch shape the autotuner may choose (threads per CTA, offsets kept in
+    shared memory) gives the default shape's results."""
+    knots = kg.knot_suite("batch")[:64]
+    ref = None
+    c = pk.Context(0)
+    import torch
+    c.set_stream(torch.cuda.current_stream().cuda_stream)
+    for th in (128, 256, 512):
+        for kt in (256, 2048):
+            c.set_tuning(batch_threads=th, batch_ktab=kt)
+            plans = _plans(c, knots, 3)
+            Z, V = pk.evaluate_batch(plans, "split")
+            if ref is None:
+                ref = Z
+            for z, zr in zip(Z, ref):
+                assert rel_err(sc(z), sc(zr)) <= TOL["split"], (th, kt)

@@ -209,3 +209,38 @@ def test_decode_result_status_word(ctx):
             assert st == 6          # PK_ETIMEOUT: the value is not to be used
     # the record layout the device writes: 32 bytes, status in the last 8
     assert pk.STATUS[6] == "PK_ETIMEOUT"
+
+
+def test_tuning_table_and_ranges(ctx):
+    """pk_tuning: the compiled-in table is the context's start value; set/get round-trip,
+    values outside the documented ranges are refused, NULL restores the table."""
+    d = pk.default_tuning()
+    assert ctx.tuning() == d
+    assert d["batch_threads"] in (128, 256, 512) and 256 <= d["batch_ktab"] <= 2048
+    c = pk.Context(-1)
+    c.set_tuning(seq_outs=8192, seq_work=1 << 16, batch_threads=512, batch_ktab=512)
+    assert c.tuning() == dict(d, seq_outs=8192, seq_work=1 << 16, batch_threads=512, batch_ktab=512)
+    for bad in ({"batch_threads": 100}, {"batch_ktab": 4096}, {"seq_k": 4096}, {"seq_outs": 0}):
+        with pytest.raises(pk.PkError):
+            c.set_tuning(**bad)
+    c.set_tuning()
+    assert c.tuning() == d
+
+
+@pytest.mark.parametrize("outs,work", [(1, 1), (8192, 1 << 16)])
+def test_plan_replay_under_other_sequence_thresholds(outs, work):
+    """Plans made with other sequence-run thresholds (no runs at all; long runs) replay
+    to the oracle's Z: the thresholds only group launches."""
+    c = pk.Context(-1)
+    c.set_tuning(seq_outs=outs, seq_work=work)
+    for s in range(3):
+        gk = kg.random_grid_knot(16, 300 + s, True, 20, 40)
+        k = pk.Knot.from_pd(c, gk.pd, outer=gk.outer)
+        p = pk.Plan(c, k, 3)
+        st = p.stats()
+        if outs == 1:
+            assert st["n_segments"] == 0
+        g = oracle.tait_graph(gk.pd, outer=gk.outer)
+        zo = oracle.z_complex(g.n_v, g.edges, 3)
+        z, e = replay(p)
+        assert rel_err(SC.of(z, e), zo) < 1e-10
