@@ -208,6 +208,12 @@ pk_status pk_knot_from_grid_walk(pk_ctx* ctx, int32_t L, uint64_t seed, int32_t 
 
 pk_status pk_knot_info(const pk_knot* k, int32_t* n_v, int32_t* n_c, int32_t* writhe,
                        int32_t* tau, int32_t* components);
+/* The simplified Tait graph of Sec. III.A as a new knot (signed graph, no PD code):
+ * Reidemeister I removes loops (tau -= eps, w -= eps) and spikes, i.e. degree-1 vertices
+ * (n_v -= 1, tau -= eps, w += eps); Reidemeister II removes parallel edge pairs of
+ * opposite Tait signs; repeated until none applies.  V of the result equals V of k.
+ * The caller owns *out (pk_knot_destroy). */
+pk_status pk_knot_simplify(pk_ctx* ctx, const pk_knot* k, pk_knot** out);
 /* Copies the signed Tait graph: uve[3*e..] = (u, v, eps) for each crossing (n_c edges). */
 pk_status pk_knot_edges(const pk_knot* k, int32_t* uve);
 /* Copies the PD code (4*n_c ints); PK_EINVAL for knots built from a signed graph. */
@@ -220,6 +226,15 @@ void pk_knot_destroy(pk_knot* k);
 pk_status pk_plan_create(pk_ctx* ctx, const pk_knot* k, int32_t q, const pk_plan_opts* opts,
                          pk_plan** out);
 pk_status pk_plan_info(const pk_plan* p, pk_plan_stats* out);
+/* The contraction-order search alone, without slicing or step records (for studies of
+ * order quality, Sec. III and Fig. 3): runs `order` (not PK_ORDER_AUTO; `restarts` seeds
+ * for PK_ORDER_FILL_SPIN and PK_ORDER_PARTITION, 0 -> 8) on the knot's network for q and
+ * writes 4 doubles of the best candidate (fewest indices on its largest tensor, then the
+ * least work): out[0] = that largest rank Delta_H (for PK_ORDER_GREEDY_EDGE the paper's
+ * maximal degree over the graph minors; otherwise spin indices), out[1] = log2 of the
+ * summed R K N of all pairwise steps, out[2] = initial tensors, out[3] = indices.
+ * Errors: PK_EINVAL (order, q). */
+pk_status pk_order_stats(const pk_knot* k, int32_t q, int32_t order, int32_t restarts, double* out);
 /* Device workspace needed by pk_eval / pk_upload / pk_launch at this precision. */
 pk_status pk_plan_workspace_bytes(const pk_plan* p, int32_t precision, uint64_t* bytes);
 /* Plan introspection for host-side checks: writes n_steps records of 8 int64:

@@ -35,7 +35,8 @@ EXPORTED = [
     "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights", "pk_eval_exact",
     "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve", "pk_decode_result",
     "pk_group_create_profiled", "pk_group_profile", "pk_group_timeline",
-    "pk_tuning_default", "pk_ctx_set_tuning", "pk_ctx_get_tuning",
+    "pk_tuning_default", "pk_ctx_set_tuning", "pk_ctx_get_tuning", "pk_knot_simplify",
+    "pk_order_stats",
 ]
 
 
@@ -105,6 +106,8 @@ def lib():
         "pk_knot_from_signed_graph": [vp, i32, i32, P(i32), i32, P(vp)],
         "pk_knot_from_grid_walk": [vp, i32, u64, i32, i32, i32, P(vp)],
         "pk_knot_info": [vp, P(i32), P(i32), P(i32), P(i32), P(i32)],
+        "pk_knot_simplify": [vp, vp, P(vp)],
+        "pk_order_stats": [vp, i32, i32, i32, P(C.c_double)],
         "pk_knot_edges": [vp, P(i32)],
         "pk_knot_pd": [vp, P(i32)],
         "pk_knot_destroy": [vp],
@@ -271,6 +274,28 @@ class Knot:
         _check(lib().pk_knot_from_grid_walk(ctx.h, L, seed, int(random_over_under), ncross_min,
                                             ncross_max, C.byref(h)), ctx)
         return Knot(h, ctx)
+
+    def simplified(self) -> "Knot":
+        """pk_knot_simplify: the Reidemeister-simplified signed Tait graph (same V)."""
+        h = C.c_void_p()
+        _check(lib().pk_knot_simplify(self.ctx.h, self.h, C.byref(h)), self.ctx)
+        return Knot(h, self.ctx)
+
+    def order_stats(self, q: int, order: str, restarts: int = 0) -> dict:
+        """pk_order_stats: the order search alone -- Delta_H (largest rank), log2 of the
+        unsliced work, initial tensors and indices of the best candidate."""
+        out = (C.c_double * 4)()
+        _check(lib().pk_order_stats(self.h, q, ORDERS[order], restarts, out))
+        return {"delta_h": int(out[0]), "log2_work": out[1], "tensors": int(out[2]),
+                "indices": int(out[3])}
+
+    def max_degree(self) -> int:
+        """Delta_G: the largest vertex degree of the signed Tait graph (a loop counts twice)."""
+        deg = [0] * self.info()["n_v"]
+        for u, v, _ in self.edges():
+            deg[u] += 1
+            deg[v] += 1
+        return max(deg) if deg else 0
 
     def info(self) -> dict:
         v = [C.c_int32() for _ in range(5)]

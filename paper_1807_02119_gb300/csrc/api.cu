@@ -276,6 +276,16 @@ pk_status pk_knot_from_grid_walk(pk_ctx* ctx, int32_t L, uint64_t seed, int32_t 
   return pk_knot_from_pd(ctx, flat.data(), (int32_t)pd.size(), oa, os, out);
 }
 
+pk_status pk_knot_simplify(pk_ctx* ctx, const pk_knot* k, pk_knot** out) {
+  if (!out || !k) return fail(ctx, PK_EINVAL, "null argument");
+  *out = nullptr;
+  pk_knot* r = new (std::nothrow) pk_knot();
+  if (!r) return fail(ctx, PK_ENOMEM, "out of host memory");
+  pk::simplify_knot(k->k, r->k);
+  *out = r;
+  return PK_OK;
+}
+
 pk_status pk_knot_info(const pk_knot* k, int32_t* n_v, int32_t* n_c, int32_t* writhe,
                        int32_t* tau, int32_t* components) {
   if (!k) return PK_EINVAL;
@@ -322,6 +332,11 @@ pk_status pk_plan_create(pk_ctx* ctx, const pk_knot* k, int32_t q, const pk_plan
   }
   *out = p;
   return PK_OK;
+}
+
+pk_status pk_order_stats(const pk_knot* k, int32_t q, int32_t order, int32_t restarts, double* out) {
+  if (!k || !out) return PK_EINVAL;
+  return pk::order_stats(k->k, q, order, restarts, out) ? PK_OK : PK_EINVAL;
 }
 
 pk_status pk_plan_info(const pk_plan* p, pk_plan_stats* out) {

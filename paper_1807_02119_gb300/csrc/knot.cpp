@@ -231,6 +231,85 @@ bool knot_from_graph(int32_t n_v, int32_t n_e, const int32_t* uve, int32_t writh
   return true;
 }
 
+// ------------------------------------------------------------------ simplification (Sec. III.A)
+// Reidemeister moves on the signed Tait graph, repeated until none applies:
+//  * R-I on a loop (u, u, eps): the kink's crossing goes; tau -= eps, w -= eps;
+//  * R-I on a spike (a vertex v of degree 1, edge (u, v, eps)): the crossing and the black
+//    region v go; n_v -= 1, tau -= eps, w += eps;
+//  * R-II unpoke of two parallel edges of opposite Tait signs: both crossings go (their
+//    twist signs are opposite too), w and tau are unchanged.
+// The diagram changes but not the knot, so V is unchanged: A(q) Z is evaluated with the new
+// (n_v, w, tau).
+bool simplify_knot(const Knot& in, Knot& out) {
+  std::vector<std::array<int32_t, 3>> E = in.edges;
+  int32_t w = in.writhe, tau = in.tau;
+  std::vector<char> alive_v(in.n_v, 1);
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    std::vector<std::array<int32_t, 3>> keep;
+    for (const auto& e : E) {   // loops
+      if (e[0] == e[1]) {
+        tau -= e[2];
+        w -= e[2];
+        changed = true;
+      } else {
+        keep.push_back(e);
+      }
+    }
+    E.swap(keep);
+    // opposite-sign parallel pairs
+    std::map<std::pair<int32_t, int32_t>, std::vector<int32_t>> pos, neg;
+    for (int32_t i = 0; i < (int32_t)E.size(); ++i) {
+      const auto key = std::make_pair(std::min(E[i][0], E[i][1]), std::max(E[i][0], E[i][1]));
+      (E[i][2] > 0 ? pos : neg)[key].push_back(i);
+    }
+    std::vector<char> drop(E.size(), 0);
+    for (auto& kv : pos) {
+      auto it = neg.find(kv.first);
+      if (it == neg.end()) continue;
+      const size_t m = std::min(kv.second.size(), it->second.size());
+      for (size_t j = 0; j < m; ++j) drop[kv.second[j]] = drop[it->second[j]] = 1;
+      if (m) changed = true;
+    }
+    keep.clear();
+    for (size_t i = 0; i < E.size(); ++i)
+      if (!drop[i]) keep.push_back(E[i]);
+    E.swap(keep);
+    // spikes, one at a time (a removal can make another)
+    std::vector<int32_t> deg(in.n_v, 0);
+    for (const auto& e : E) {
+      deg[e[0]]++;
+      deg[e[1]]++;
+    }
+    for (int32_t i = 0; i < (int32_t)E.size(); ++i) {
+      const int32_t u = E[i][0], v = E[i][1];
+      const int32_t leaf = deg[v] == 1 ? v : deg[u] == 1 ? u : -1;
+      if (leaf < 0) continue;
+      alive_v[leaf] = 0;
+      tau -= E[i][2];
+      w += E[i][2];
+      deg[u]--;
+      deg[v]--;
+      E.erase(E.begin() + i);
+      changed = true;
+      break;
+    }
+  }
+  std::vector<int32_t> id(in.n_v, -1);
+  int32_t n = 0;
+  for (int32_t v = 0; v < in.n_v; ++v)
+    if (alive_v[v]) id[v] = n++;
+  out = Knot();
+  out.n_v = n;
+  out.n_c = (int32_t)E.size();
+  out.writhe = w;
+  out.tau = tau;
+  out.components = in.components;
+  for (const auto& e : E) out.edges.push_back({id[e[0]], id[e[1]], e[2]});
+  return true;
+}
+
 // ------------------------------------------------------------------ grid walk (Sec. III.A)
 namespace {
 struct SplitMix64 {

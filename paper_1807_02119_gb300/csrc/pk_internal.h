@@ -26,6 +26,9 @@ bool knot_from_pd(const int32_t* pd, int32_t n, int32_t outer_arc, int32_t outer
                   std::string& err, const int32_t* signs = nullptr);
 bool knot_from_graph(int32_t n_v, int32_t n_e, const int32_t* uve, int32_t writhe, Knot& k,
                      std::string& err);
+// The signed Tait graph after repeated Reidemeister I (loops, spikes) and II (opposite-sign
+// parallel pairs) simplification, with n_v, writhe and tau updated so that V is unchanged.
+bool simplify_knot(const Knot& in, Knot& out);
 bool grid_walk_pd(int32_t L, uint64_t seed, bool random_over_under, int32_t nmin, int32_t nmax,
                   std::vector<std::array<int32_t, 4>>& pd, int32_t& outer_arc,
                   int32_t& outer_side, std::string& err);
@@ -323,6 +326,10 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 bool& swapped, std::vector<int32_t>& cdims, std::string& err);
 bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuning& tune, Plan& p,
                std::string& err);
+// Order search only (no slicing, no step records): out[0] largest tensor rank, out[1] log2
+// of the summed R K N, out[2] initial tensors, out[3] indices, for the best candidate of
+// `order` (by rank, then cost).  False for an unknown order or q.
+bool order_stats(const Knot& k, int32_t q, int32_t order, int32_t restarts, double* out);
 // Maximal runs (>= 2) of consecutive small row-kernel steps (at most tune.seq_outs outputs,
 // K <= tune.seq_k <= kTinyK, at most tune.seq_work complex multiply-adds), with their
 // compact records, for the sequence kernel k_seg.

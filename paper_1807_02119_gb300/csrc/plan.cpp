@@ -612,33 +612,64 @@ struct Bisection {
       for (int32_t x : sets[t]) c0[x] = c1[x] = 0;
     int32_t taken = best;
     for (int32_t i = 0; i < n; ++i) side[order1[i]] = i < best ? 1 : 0;
-    // refinement: move single tensors while that shrinks the number of shared indices
+    // refinement by Fiduccia-Mattheyses passes: within a pass every tensor moves at most
+    // once, always the unlocked one whose move shrinks the number of shared indices most
+    // (the gain may be negative: that is how a pass leaves a local minimum) while both
+    // sides keep at least 40% of the group; the pass is then undone back to the best
+    // state it reached.  A pass ends after 50 moves without a new best; passes repeat
+    // while they improve.
     for (int32_t t : group)
       for (int32_t x : sets[t]) (side[t] ? c1 : c0)[x]++;
     int32_t size1 = taken;
     const int32_t min_side = std::max<int32_t>(1, (n * 2) / 5);
-    std::vector<int32_t> ord(group);
-    for (int pass = 0; pass < 8; ++pass) {
-      for (int32_t i = n - 1; i > 0; --i) std::swap(ord[i], ord[next() % (i + 1)]);
-      bool moved = false;
-      for (int32_t t : ord) {
-        const int32_t sd = side[t];
-        if ((sd ? size1 : n - size1) - 1 < min_side) continue;
-        int32_t gain = 0;
-        for (int32_t x : sets[t]) {
-          const int32_t cs = sd ? c1[x] : c0[x], co = sd ? c0[x] : c1[x];
-          gain += (co > 0 ? 1 : 0) - (cs > 1 ? 1 : 0);
-        }
-        if (gain <= 0) continue;
-        for (int32_t x : sets[t]) {
-          (sd ? c1 : c0)[x]--;
-          (sd ? c0 : c1)[x]++;
-        }
-        side[t] = 1 - sd;
-        size1 += sd ? -1 : 1;
-        moved = true;
+    auto gain_of = [&](int32_t t) {
+      const int32_t sd = side[t];
+      int32_t gain = 0;
+      for (int32_t x : sets[t]) {
+        const int32_t cs = sd ? c1[x] : c0[x], co = sd ? c0[x] : c1[x];
+        gain += (co > 0 ? 1 : 0) - (cs > 1 ? 1 : 0);
       }
-      if (!moved) break;
+      return gain;
+    };
+    auto move = [&](int32_t t) {
+      const int32_t sd = side[t];
+      for (int32_t x : sets[t]) {
+        (sd ? c1 : c0)[x]--;
+        (sd ? c0 : c1)[x]++;
+      }
+      side[t] = 1 - sd;
+      size1 += sd ? -1 : 1;
+    };
+    std::vector<int32_t> locked(sets.size(), -1), moved;
+    for (int32_t pass = 0; pass < 8; ++pass) {
+      moved.clear();
+      int32_t cur = 0, best_gain = 0, best_len = 0, since_best = 0;
+      while (since_best < 50) {
+        int32_t pick = -1, pick_gain = 0;
+        for (int32_t t : group) {
+          if (locked[t] == pass) continue;
+          if ((side[t] ? size1 : n - size1) - 1 < min_side) continue;
+          const int32_t g = gain_of(t);
+          if (pick < 0 || g > pick_gain) {
+            pick = t;
+            pick_gain = g;
+          }
+        }
+        if (pick < 0) break;
+        move(pick);
+        locked[pick] = pass;
+        moved.push_back(pick);
+        cur += pick_gain;
+        if (cur > best_gain) {
+          best_gain = cur;
+          best_len = (int32_t)moved.size();
+          since_best = 0;
+        } else {
+          ++since_best;
+        }
+      }
+      for (int32_t i = (int32_t)moved.size() - 1; i >= best_len; --i) move(moved[i]);
+      if (best_gain <= 0) break;
     }
     for (int32_t t : group)
       for (int32_t x : sets[t]) (side[t] ? c1 : c0)[x] = 0;
@@ -1015,6 +1046,47 @@ uint64_t Plan::ws_bytes(int32_t precision) const {
 }
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+bool order_stats(const Knot& k, int32_t q, int32_t order, int32_t restarts, double* out) {
+  if (q < 1 || q > 64) return false;
+  std::vector<std::pair<int32_t, uint64_t>> cands;
+  const int32_t r = restarts > 0 ? restarts : 8;
+  if (order == PK_ORDER_GREEDY_EDGE || order == PK_ORDER_GREEDY_SPIN || order == PK_ORDER_ELIM_SPIN)
+    cands = {{order, 0}};
+  else if (order == PK_ORDER_FILL_SPIN || order == PK_ORDER_PARTITION)
+    for (int32_t i = 0; i < r; ++i) cands.push_back({order, (uint64_t)i});
+  else
+    return false;
+  std::vector<std::array<double, 4>> w;
+  for (const auto& e : k.edges) w.push_back(std_weight(q, e[2]));
+  bool have = false;
+  for (const auto& cand : cands) {
+    Network net;
+    if (cand.first == PK_ORDER_GREEDY_EDGE)
+      edge_network(k, q, net);
+    else
+      spin_network(k, q, false, true, w, net);
+    Greedy g;
+    run_order(net, cand.first, g, cand.second);
+    const double rank = g.seq.max_rank;
+    double macs = 0;   // complex multiply-adds: q^(indices of A and B together) per step
+    static const std::vector<int32_t> none;
+    for (size_t i = 0; i < g.seq.pairs.size(); ++i) {
+      const auto& pr = g.seq.pairs[i];
+      macs += std::pow((double)q, (double)union_size(g.seq.sets[pr.first],
+                                                     pr.second >= 0 ? g.seq.sets[pr.second] : none));
+    }
+    const double cost = std::log2(std::max(1.0, macs));
+    if (!have || rank < out[0] || (rank == out[0] && cost < out[1])) {
+      out[0] = rank;
+      out[1] = cost;
+      out[2] = (double)net.t.size();
+      out[3] = (double)net.n_idx;
+      have = true;
+    }
+  }
+  return have;
+}
 
 bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuning& tune, Plan& p,
                std::string& err) {
