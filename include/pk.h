@@ -163,6 +163,12 @@ pk_status pk_tuning_default(pk_tuning* out);
  * context for knot input and planning (pk_eval returns PK_ENODEVICE). */
 pk_status pk_ctx_create(int32_t device, void* stream, pk_ctx** out);
 pk_status pk_ctx_set_stream(pk_ctx* ctx, void* stream);
+/* Device-memory budget for the plans created afterwards (0: none, the default): a plan
+ * whose workspace at any precision (pk_plan_workspace_bytes) would exceed `bytes` is sliced
+ * further -- one index fewer on its largest tensor at a time, more slices of less memory
+ * (Sec. III.B names memory as the bottleneck) -- until it fits; PK_ETOOWIDE from
+ * pk_plan_create when the slice limit (pk_plan_opts.max_log2_slices) is reached first. */
+pk_status pk_ctx_set_hbm_budget(pk_ctx* ctx, uint64_t bytes);
 /* NULL restores the defaults.  PK_EINVAL for values outside the ranges of pk_tuning. */
 pk_status pk_ctx_set_tuning(pk_ctx* ctx, const pk_tuning* t);
 pk_status pk_ctx_get_tuning(const pk_ctx* ctx, pk_tuning* out);

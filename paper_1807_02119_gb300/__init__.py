@@ -36,7 +36,7 @@ EXPORTED = [
     "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve", "pk_decode_result",
     "pk_group_create_profiled", "pk_group_profile", "pk_group_timeline",
     "pk_tuning_default", "pk_ctx_set_tuning", "pk_ctx_get_tuning", "pk_knot_simplify",
-    "pk_order_stats",
+    "pk_order_stats", "pk_ctx_set_hbm_budget",
 ]
 
 
@@ -108,6 +108,7 @@ def lib():
         "pk_knot_info": [vp, P(i32), P(i32), P(i32), P(i32), P(i32)],
         "pk_knot_simplify": [vp, vp, P(vp)],
         "pk_order_stats": [vp, i32, i32, i32, P(C.c_double)],
+        "pk_ctx_set_hbm_budget": [vp, u64],
         "pk_knot_edges": [vp, P(i32)],
         "pk_knot_pd": [vp, P(i32)],
         "pk_knot_destroy": [vp],
@@ -204,6 +205,10 @@ class Context:
 
     def set_stream(self, stream: int):
         _check(lib().pk_ctx_set_stream(self.h, C.c_void_p(stream)), self)
+
+    def set_hbm_budget(self, nbytes: int):
+        """pk_ctx_set_hbm_budget: plans created afterwards slice until their workspace fits."""
+        _check(lib().pk_ctx_set_hbm_budget(self.h, int(nbytes)), self)
 
     def tuning(self) -> dict:
         """The launch shapes plans and batches created now will use (pk_ctx_get_tuning)."""

@@ -187,6 +187,12 @@ pk_status pk_ctx_set_tuning(pk_ctx* ctx, const pk_tuning* t) {
   return PK_OK;
 }
 
+pk_status pk_ctx_set_hbm_budget(pk_ctx* ctx, uint64_t bytes) {
+  if (!ctx) return PK_EINVAL;
+  ctx->hbm_budget = bytes;
+  return PK_OK;
+}
+
 pk_status pk_ctx_get_tuning(const pk_ctx* ctx, pk_tuning* out) {
   if (!ctx || !out) return PK_EINVAL;
   *out = ctx->tuning;
@@ -324,11 +330,24 @@ pk_status pk_plan_create(pk_ctx* ctx, const pk_knot* k, int32_t q, const pk_plan
   pk_plan* p = new (std::nothrow) pk_plan();
   if (!p) return fail(ctx, PK_ENOMEM, "out of host memory");
   std::string err;
-  if (!pk::make_plan(k->k, q, o, ctx ? ctx->tuning : kTunedDefault, p->p, err)) {
-    delete p;
-    if (err.find("slices") != std::string::npos || err.find("runs") != std::string::npos)
-      return fail(ctx, PK_ETOOWIDE, err);
-    return fail(ctx, PK_EINVAL, err);
+  const uint64_t budget = ctx ? ctx->hbm_budget : 0;
+  for (;;) {
+    if (!pk::make_plan(k->k, q, o, ctx ? ctx->tuning : kTunedDefault, p->p, err)) {
+      delete p;
+      if (err.find("slices") != std::string::npos || err.find("runs") != std::string::npos)
+        return fail(ctx, PK_ETOOWIDE, err);
+      return fail(ctx, PK_EINVAL, err);
+    }
+    const pk::Plan& P = p->p;
+    const uint64_t need = std::max(P.ws_bytes(PK_C128), std::max(P.ws_bytes(PK_SPLIT), P.ws_bytes(PK_C64)));
+    if (budget == 0 || need <= budget) break;
+    // over the device-memory budget: one index fewer on the largest tensor (more slices)
+    const double lq = std::log2((double)q);
+    if (q < 2 || P.max_rank <= 1) {
+      delete p;
+      return fail(ctx, PK_ETOOWIDE, "no slicing fits the device-memory budget");
+    }
+    o.max_log2_elems = (P.max_rank - 1) * lq + 1e-9;
   }
   *out = p;
   return PK_OK;

@@ -12,6 +12,7 @@
 
 struct pk_ctx {
   pk_tuning tuning = kTunedDefault;
+  uint64_t hbm_budget = 0;         // plans' workspaces must fit (0: no limit)
   int32_t device = -1;
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;  // private stream on which launch sequences are recorded

@@ -244,3 +244,26 @@ def test_plan_replay_under_other_sequence_thresholds(outs, work):
         zo = oracle.z_complex(g.n_v, g.edges, 3)
         z, e = replay(p)
         assert rel_err(SC.of(z, e), zo) < 1e-10
+
+
+def test_hbm_budget_slices_until_the_workspace_fits():
+    """A device-memory budget on the context: plans slice further until every precision's
+    workspace fits, still replay to the oracle's Z; a budget below any slicing is refused
+    with PK_ETOOWIDE."""
+    c = pk.Context(-1)
+    gk = kg.random_grid_knot(30, 35, True, 60, 160)        # 119 crossings, arena 263 KB
+    k = pk.Knot.from_pd(c, gk.pd, outer=gk.outer)
+    g = oracle.tait_graph(gk.pd, outer=gk.outer)
+    free = pk.Plan(c, k, 3)
+    state, arena = free.state_bytes("c128")     # the state part does not shrink with slicing
+    budget = state + (3 * arena) // 5
+    c.set_hbm_budget(budget)
+    p = pk.Plan(c, k, 3)
+    assert max(p.workspace_bytes(x) for x in ("c128", "c64", "split")) <= budget
+    assert p.stats()["n_slices"] > free.stats()["n_slices"]
+    z, e = replay(p)
+    assert rel_err(SC.of(z, e), oracle.z_complex(g.n_v, g.edges, 3)) < 1e-10
+    c.set_hbm_budget(1024)
+    with pytest.raises(pk.PkError) as ex:
+        pk.Plan(c, k, 3)
+    assert ex.value.status == 4
