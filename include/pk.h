@@ -482,6 +482,13 @@ pk_status pk_grad(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_work
 pk_status pk_grad_from_accumulators(const pk_plan* p, const double* acc, const int64_t* acc_exp,
                                     const pk_scaled* Z, double* dlogZ_dT, double* dlogV_dt);
 
+/* d log Z with respect to each Tait edge's two clause weights (the diagonal entry d_e and
+ * the off-diagonal entry o_e of pk_plan_opts.edge_weights: T_e[a,a] = d_e, T_e[a,b] = o_e
+ * for a != b), from pk_grad's dlogZ_dT (same layout): out[4e..4e+3] = re, im of
+ * sum_a dlogZ_dT[e,a,a] and of sum_{a != b} dlogZ_dT[e,a,b] (holomorphic derivatives).
+ * Host only. */
+pk_status pk_grad_weights(const pk_plan* p, const double* dlogZ_dT, double* out);
+
 /* Reverse-program statistics of a PK_FLAG_GRAD plan, 10 doubles: complex multiply-adds
  * per slice of the forward, recompute and adjoint steps; their step counts; arena
  * elements; forward intermediates kept as checkpoints; edge groups; slices. */

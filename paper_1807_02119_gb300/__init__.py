@@ -36,7 +36,7 @@ EXPORTED = [
     "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve", "pk_decode_result",
     "pk_group_create_profiled", "pk_group_profile", "pk_group_timeline",
     "pk_tuning_default", "pk_ctx_set_tuning", "pk_ctx_get_tuning", "pk_knot_simplify",
-    "pk_order_stats", "pk_ctx_set_hbm_budget",
+    "pk_order_stats", "pk_ctx_set_hbm_budget", "pk_grad_weights",
 ]
 
 
@@ -109,6 +109,7 @@ def lib():
         "pk_knot_simplify": [vp, vp, P(vp)],
         "pk_order_stats": [vp, i32, i32, i32, P(C.c_double)],
         "pk_ctx_set_hbm_budget": [vp, u64],
+        "pk_grad_weights": [vp, P(C.c_double), P(C.c_double)],
         "pk_knot_edges": [vp, P(i32)],
         "pk_knot_pd": [vp, P(i32)],
         "pk_knot_destroy": [vp],
@@ -755,6 +756,18 @@ def grad_from_accumulators(plan: Plan, acc, acc_exp, z: Scaled):
     return (arr[0::2] + 1j * arr[1::2]).reshape(n_e, q, q), complex(dv[0], dv[1])
 
 
+def grad_weights(plan: Plan, dlogz):
+    """pk_grad_weights (host only): (n_e, 2) complex array of d log Z / d(diagonal weight)
+    and d log Z / d(off-diagonal weight) per Tait edge, from pk_grad's (n_e, q, q) array."""
+    import numpy as np
+    d = np.ascontiguousarray(np.asarray(dlogz, dtype=np.complex128)).view(np.float64)
+    d = np.ascontiguousarray(d)
+    out = (C.c_double * max(1, 4 * plan.n_e))()
+    _check(lib().pk_grad_weights(plan.h, d.ctypes.data_as(C.POINTER(C.c_double)), out))
+    arr = np.frombuffer(out, dtype=np.float64)[:4 * plan.n_e]
+    return (arr[0::2] + 1j * arr[1::2]).reshape(plan.n_e, 2)
+
+
 _LOGZ_FN = None
 
 
@@ -776,12 +789,8 @@ def _logz_function():
         def forward(ctx, weights, plan, precision):
             plan.set_weights([(complex(d), complex(o)) for d, o in weights.detach().cpu().tolist()])
             z, _, dlogz, _ = grad(plan, precision)
-            q = plan.q
-            eye = torch.eye(q, dtype=torch.bool)
-            d = torch.as_tensor(dlogz, dtype=torch.complex128)
-            jd = d[:, eye].sum(dim=1)
-            jo = d[:, ~eye].sum(dim=1)
-            ctx.save_for_backward(torch.stack([jd, jo], dim=1).to(weights.device))
+            jac = torch.as_tensor(grad_weights(plan, dlogz), dtype=torch.complex128)
+            ctx.save_for_backward(jac.to(weights.device))
             logz = complex(math.log(abs(z.mantissa)) + z.exp2 * math.log(2.0),
                            math.atan2(z.im, z.re))
             return torch.tensor(logz, dtype=torch.complex128, device=weights.device)

@@ -763,6 +763,31 @@ pk_status pk_grad_from_accumulators(const pk_plan* p, const double* acc, const i
   return pk::grad_finalize(p->p, acc, acc_exp, z, dlogZ_dT, dlogV_dt) ? PK_OK : PK_EZERO;
 }
 
+pk_status pk_grad_weights(const pk_plan* p, const double* dlogZ_dT, double* out) {
+  if (!p || !dlogZ_dT || !out) return PK_EINVAL;
+  const int32_t q = p->p.q;
+  const size_t n_e = p->p.knot.edges.size();
+  for (size_t e = 0; e < n_e; ++e) {
+    double dr = 0, di = 0, orr = 0, oi = 0;
+    for (int32_t a = 0; a < q; ++a)
+      for (int32_t b = 0; b < q; ++b) {
+        const double* v = dlogZ_dT + 2 * ((e * q + a) * q + b);
+        if (a == b) {
+          dr += v[0];
+          di += v[1];
+        } else {
+          orr += v[0];
+          oi += v[1];
+        }
+      }
+    out[4 * e] = dr;
+    out[4 * e + 1] = di;
+    out[4 * e + 2] = orr;
+    out[4 * e + 3] = oi;
+  }
+  return PK_OK;
+}
+
 pk_status pk_plan_set_weights(pk_plan* p, const double* edge_weights) {
   if (!p || !p->p.general) return PK_EINVAL;
   if (!pk::set_weights(p->p, edge_weights)) return PK_EINVAL;

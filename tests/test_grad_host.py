@@ -144,3 +144,18 @@ def test_grad_errors_and_unknot(ctx):
     t = og.t_of_q(3)
     assert abs(dv - (1 / t - 2 / (t + 1))) < 1e-14         # V = 1: only A(t) and Z = q
     assert abs(z.m * 2.0 ** z.e - 3) < 1e-14
+
+
+def test_grad_weights_sums_the_diagonal_and_off_diagonal():
+    """pk_grad_weights: per Tait edge the sums of dlogZ/dT over the diagonal and over the
+    off-diagonal entries, the derivatives with respect to the two clause weights."""
+    import numpy as np
+    ctx = pk.Context(-1)
+    k = pk.Knot.from_pd(ctx, kg.braid_closure_pd([1, 1, 1], 2))
+    p = pk.Plan(ctx, k, 3, grad=True)
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(p.n_e, 3, 3)) + 1j * rng.normal(size=(p.n_e, 3, 3))
+    got = pk.grad_weights(p, d)
+    eye = np.eye(3, dtype=bool)
+    want = np.stack([d[:, eye].sum(axis=1), d[:, ~eye].sum(axis=1)], axis=1)
+    assert np.allclose(got, want, rtol=1e-14, atol=1e-14)
