@@ -468,7 +468,7 @@ pk_status pk_plan_launches(const pk_plan* p, int32_t precision, int64_t* launche
   if (!p || !launches || !valid_precision(precision)) return PK_EINVAL;
   const pk::Plan& P = p->p;
   const int64_t widen = (precision == PK_C64 && !P.conv.empty()) ? 1 : 0;
-  const int64_t digits = precision == PK_SPLIT ? 2 * (int64_t)P.n_tc : 0;  // per tensor-core step
+  const int64_t digits = precision == PK_SPLIT ? (int64_t)P.n_tc : 0;  // one conversion launch per tensor-core step
   int64_t fused = 0;  // steps saved by sequence launches (runs of small steps)
   for (const pk::Segment& g : P.segments)
     if (precision != PK_C64 || g.first + g.count <= P.tail_first) fused += g.count - 1;

@@ -293,27 +293,32 @@ __device__ __forceinline__ void convert_item(const Cx<ff>* v, int r, int kl, flo
 
 }  // namespace tc
 
-// Digits of one block of the A operand (IS_A: 128 rows) or the B operand (24 columns) of
-// a GEMM step over one flush group of K (kFlush chunks of 16 complex k): the exponent of
-// each row over the group's k, then the S digit slices of the group's chunks, stored
-// directly in the workspace.  The second read of the block hits L2.  The thread mapping
-// follows the operand's unit stride: along K (consecutive lanes read consecutive k of one
-// row) or along the rows (a warp reads 32 consecutive rows).
+// Digits of one block of the A operand (IS_A: 64 of a tile's 128 rows) or the B operand
+// (24 columns) of a GEMM step over one flush group of K (kFlush chunks of 16 complex k):
+// the exponent of each row over the group's k, then the S digit slices of the group's
+// chunks, stored directly in the workspace.  The block is read twice; the second read hits
+// L2 (a block is at most 64 x 112 complex k in flight per CTA).  The thread mapping follows
+// the operand's unit stride: along K (consecutive lanes read consecutive k of one row) or
+// along the rows (a warp reads 32 consecutive rows).
 template <int S, bool IS_A>
 __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena, unsigned char* scratch,
                                              long long blk, long long* ro, long long* kt,
                                              long long& base, int* ex, float* red) {
   using namespace tc;
-  constexpr int kRows = IS_A ? kMc : kNc;
-  constexpr int kRowsPad = IS_A ? 128 : 64;       // rows of the exponent pass's thread grid
+  constexpr int kHalves = IS_A ? 2 : 1;           // CTAs per tile block
+  constexpr int kRows = IS_A ? kMc / 2 : kNc;     // rows this CTA converts
+  constexpr int kRowsPad = 64;                    // rows of the exponent pass's thread grid
   constexpr int kPer = kConvThreads / kRowsPad;   // threads per row in the exponent pass
   constexpr int kG = Cfg<S>::kFlush * kKc;        // complex k of one flush group
   static_assert(kRows <= kRowsPad && kConvThreads % kRowsPad == 0 && kG <= kConvThreads,
                 "block geometry");
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
   const long long tiles = IS_A ? L.tiles_m : L.tiles_n;
+  const int half = (int)(blk % kHalves);
+  blk /= kHalves;
   const long long g = blk % L.groups, t = blk / L.groups;
   const long long tile = t % tiles, bb = t / tiles;
+  const int r0 = half * kRows;                    // first tile row of this CTA
   const int tid = threadIdx.x;
   const bool kin = IS_A ? s.a_kinner != 0 : s.b_kinner != 0;
   const long long k0 = g * kG;
@@ -325,7 +330,7 @@ __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena,
     base = IS_A ? a : b;
   }
   if (tid < kRowsPad) {
-    const long long r = tile * kRows + tid;
+    const long long r = tile * (IS_A ? kMc : kNc) + r0 + tid;
     long long a, b, c;
     if (tid < kRows && r < (IS_A ? s.M : s.N)) {
       if (IS_A)
@@ -362,8 +367,8 @@ __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena,
 #pragma unroll
     for (int j = 0; j < kPer; ++j) v = fmaxf(v, red[kin ? kPer * tid + j : tid + kRowsPad * j]);
     ex[tid] = bin_exp(v);
-    ((int*)(scratch + (IS_A ? L.ea_off : L.eb_off)))[((bb * tiles + tile) * L.groups + g) * kRows + tid] =
-        ex[tid];
+    ((int*)(scratch + (IS_A ? L.ea_off : L.eb_off)))[((bb * tiles + tile) * L.groups + g) *
+                                                         (IS_A ? kMc : kNc) + r0 + tid] = ex[tid];
   }
   __syncthreads();
 
@@ -385,18 +390,18 @@ __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena,
     float sc1, sc2;
     digit_scale(ex[r], sc1, sc2);
     const long long k = k0 + 4 * q;
-    convert_item<S, IS_A>(v, r, (int)(k % kKc), sc1, sc2, dst0 + (k / kKc) * (long long)kChunkBytes);
+    convert_item<S, IS_A>(v, r0 + r, (int)(k % kKc), sc1, sc2, dst0 + (k / kKc) * (long long)kChunkBytes);
   }
 }
 
-// Digits of both operands of a GEMM step in one launch: blocks [0, nA) convert A (one per
+// Digits of both operands of a GEMM step in one launch: blocks [0, nA) convert A (two per
 // batch index, 128-row block and flush group), the rest convert B.
 template <int S>
 __global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const Cx<ff>* arena,
                                                              unsigned char* scratch, long long nA) {
-  __shared__ long long ro[128], kt[tc::kConvThreads];
+  __shared__ long long ro[64], kt[tc::kConvThreads];
   __shared__ long long base;
-  __shared__ int ex[128];
+  __shared__ int ex[64];
   __shared__ float red[tc::kConvThreads];
   const long long blk = blockIdx.x;
   if (blk < nA)
