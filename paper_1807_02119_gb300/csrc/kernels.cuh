@@ -341,11 +341,14 @@ __device__ __forceinline__ S step_scale(const Step& s, Meta* meta, bool write_ex
   return (S)ldexp(1.0, -(ea + eb));
 }
 
-// Thread per output row r (batch x free-of-A): the K values A[r, :] are loaded once
-// (registers when K <= KREG), then each of the N outputs C[n, r] is formed against B
-// (read through the L1/texture path: it is small or shared across the warp).
+// Thread per (output row r, chunk of nc columns): the row's offsets are decoded once and
+// its K values A[r, :] loaded once (registers when K <= KREG), then each output C[n, r] of
+// the chunk is formed against B (read through the L1/texture path: it is small or shared
+// across the warp).  nc = N gives one thread per row; smaller chunks give steps with few
+// rows enough threads to fill the GPU while the decoding stays amortised over nc outputs.
+// Consecutive threads take consecutive rows, so the C stores of a warp are contiguous.
 template <typename R, int KREG>
-__global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* meta) {
+__global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* meta, int nc) {
   using S = typename Traits<R>::S;
   extern __shared__ long long sm[];
   long long* kA = sm;
@@ -364,8 +367,11 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
   const bool hasB = s.b >= 0;
   const int K = (int)s.K, N = (int)s.N;
   const unsigned R_ = (unsigned)s.R;
+  const unsigned chunks = (unsigned)((N + nc - 1) / nc);   // R chunks <= R N <= 2^31
   S vmax = 0;
-  for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < R_; r += gridDim.x * blockDim.x) {
+  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < R_ * chunks; w += gridDim.x * blockDim.x) {
+    const unsigned c = w / R_, r = w - c * R_;
+    const int n0 = (int)c * nc, n1 = min(N, n0 + nc);
     long long oa, ob;
     split_runs32(r, s.row, s.nrow, oa, ob);
     if (KREG > 0) {
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
 #pragma unroll
       for (int k = 0; k < KREG; ++k)
         if (k < K) a[k] = ld(A + oa + kA[k]);
-      for (int n = 0; n < N; ++n) {
+      for (int n = n0; n < n1; ++n) {
         Acc<R> acc;
         if (hasB) {
           const Cx<R>* Bn = B + ob + nB[n];
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(256) k_rows(const Step s, Cx<R>* arena, Meta* 
         vmax = fmax(vmax, mag(v));
       }
     } else {
-      for (int n = 0; n < N; ++n) {
+      for (int n = n0; n < n1; ++n) {
         Acc<R> acc;
         const Cx<R>* Bn = B + ob + (hasB ? nB[n] : 0);
         for (int k = 0; k < K; ++k) {

@@ -109,7 +109,16 @@ template <typename R>
 cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st, Marker& mk,
                         double cm, double by) {
   const size_t sm = sizeof(long long) * (size_t)(2 * s.K + s.N);
-  if (s.R < kFewRows && s.N > 1 && sizeof(long long) * 2 * (size_t)s.K <= 200 * 1024) {
+  const int kmax = sizeof(R) == 8 ? 16 : 32;   // K held in registers by the row kernel
+  // few rows, several columns: the row kernel over (row, chunk of columns) work items
+  // when A's row fits the registers, else one thread per output
+  const bool chunked = s.R < kFewRows && s.N > 1 && s.K <= kmax && sm <= 200 * 1024;
+  int nc = (int)s.N;
+  if (chunked) {
+    const long long want = std::min<long long>(s.N, (kFewRows + s.R - 1) / s.R);  // chunks
+    nc = (int)((s.N + want - 1) / want);
+  }
+  if (!chunked && s.R < kFewRows && s.N > 1 && sizeof(long long) * 2 * (size_t)s.K <= 200 * 1024) {
     const long long outs = s.R * s.N;
     const long long blocks = std::max<long long>(1, std::min<long long>((outs + 255) / 256, 152 * 16));
     mk.begin(1, cm, by, gpu_fill(blocks, 8));
@@ -117,7 +126,8 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
     mk.end();
     return cudaGetLastError();
   }
-  long long blocks = (s.R + 255) / 256;
+  const long long items = s.R * ((s.N + nc - 1) / nc);
+  long long blocks = (items + 255) / 256;
   blocks = std::max<long long>(1, std::min<long long>(blocks, 152 * 8));
   mk.begin(1, cm, by, gpu_fill(blocks, 8));
   if (sm > 200 * 1024) {
@@ -125,9 +135,8 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
     mk.end();
     return cudaGetLastError();
   }
-  const int kmax = sizeof(R) == 8 ? 16 : 32;
   const int K = (int)s.K;
-  void (*fn)(const Step, Cx<R>*, Meta*);
+  void (*fn)(const Step, Cx<R>*, Meta*, int);
   if (K <= 1)
     fn = k_rows<R, 1>;
   else if (K <= 2)
@@ -142,7 +151,7 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
     fn = k_rows<R, 32>;
   else
     fn = k_rows<R, 0>;
-  fn<<<(unsigned)blocks, 256, sm, st>>>(s, arena, meta);  // limit raised by prepare_kernels
+  fn<<<(unsigned)blocks, 256, sm, st>>>(s, arena, meta, nc);  // limit raised by prepare_kernels
   mk.end();
   return cudaGetLastError();
 }
@@ -402,14 +411,14 @@ namespace {
 template <typename R>
 cudaError_t raise_rows_smem() {
   const int lim = 200 * 1024;
-  void (*fns[])(const Step, Cx<R>*, Meta*) = {k_rows<R, 1>,  k_rows<R, 2>,  k_rows<R, 4>,
-                                              k_rows<R, 8>,  k_rows<R, 16>, k_rows<R, 32>,
-                                              k_rows<R, 0>,  k_outs<R>};
+  void (*fns[])(const Step, Cx<R>*, Meta*, int) = {k_rows<R, 1>,  k_rows<R, 2>,  k_rows<R, 4>,
+                                                   k_rows<R, 8>,  k_rows<R, 16>, k_rows<R, 32>,
+                                                   k_rows<R, 0>};
   for (auto f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  return cudaFuncSetAttribute(k_outs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 template <int S>
