@@ -10,8 +10,9 @@
 // digit product (|d_a d_b| <= 2^14) is exact, and a sum of such products stays exact in
 // FP32 while it stays below 2^24: the S digit pairs (i, j) of one level L = i + j are
 // accumulated together, and every level is flushed to float-float registers before
-// (L + 1) K' 2^14 can reach 2^24.  Levels L >= S are dropped (their weight is at most
-// 2^(-8S) of the leading term); the result is
+// (L + 1) K' 2^14 can reach 2^24 (there levels 0 and 1 are combined exactly, levels 2 and
+// up in FP32, whose rounding stays below the truncation).  Levels L >= S are dropped
+// (their weight is at most 2^(-8S) of the leading term); the result is
 //     C(m, n) = sum_groups 2^(e_g(m) + e_g(n)) sum_{L < S} acc_{g,L}(m, n) 2^(-14-8L),
 // each group's exponents applied (exactly: powers of two) when its levels are flushed.
 //
@@ -566,28 +567,35 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
         break;
       }
       fence_after();
-      // level L holds integer sums of digit products at weight 2^(-14-8L); per 8 columns the
-      // levels are summed in float-float, then scaled by the group's 2^(e(m) + e(n))
-      // (a power of two: exact) and added to the accumulators
+      // level L holds an integer sum of digit products (below 2^24 in magnitude) at weight
+      // 2^(-14-8L).  Per 8 columns: levels 0 and 1 are added exactly (TwoSum); levels 2 ..
+      // S-1, at most 2^-16 of level 0's scale, are folded into the low part with FP32 FMAs,
+      // whose rounding (below 2^-40 of level 0's scale) is under the digits' truncation.
+      // The sum is scaled by the group's 2^(e(m) + e(n) - 14) (powers of two: exact) and
+      // added to the float-float accumulators.
       const uint32_t ta0 = tmem + ((uint32_t)(quarter * 32) << 16) + half * kCw;
 #pragma unroll
       for (int c8 = 0; c8 < kCw / 8; ++c8) {
-        float th[8], tl[8];
+        float hi[8], lo[8];
+        tmem_ld8(ta0 + c8 * 8, hi);        // level 0
+        tmem_ld8(ta0 + kN + c8 * 8, lo);   // level 1
 #pragma unroll
-        for (int i = 0; i < 8; ++i) th[i] = tl[i] = 0.f;
+        for (int i = 0; i < 8; ++i) two_sum(hi[i], lo[i] * 0.00390625f, hi[i], lo[i]);   // exact
 #pragma unroll 1
-        for (int lv = 0; lv < S; ++lv) {
+        for (int lv = 2; lv < S; ++lv) {
           float v[8];
           tmem_ld8(ta0 + lv * kN + c8 * 8, v);
-          const float w = __int_as_float((127 - 14 - 8 * lv) << 23);   // 2^(-14-8L)
+          const float w = __int_as_float((127 - 8 * lv) << 23);   // 2^(-8L) relative to level 0
 #pragma unroll
-          for (int i = 0; i < 8; ++i) ff_acc(th[i], tl[i], v[i] * w, 0.f);
+          for (int i = 0; i < 8; ++i) lo[i] = fmaf(v[i], w, lo[i]);
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float f1, f2;
-          pow2_pair(eam + eb_s[ew][(c8 * 8 + i) >> 1], f1, f2);
-          ff_acc(acc_h[c8 * 8 + i], acc_l[c8 * 8 + i], (th[i] * f1) * f2, (tl[i] * f1) * f2);
+        for (int i = 0; i < 8; i += 2) {
+          float f1, f2;   // one exponent per complex column: (re, im) = columns i, i + 1
+          pow2_pair(eam - 14 + eb_s[ew][(c8 * 8 + i) >> 1], f1, f2);
+#pragma unroll
+          for (int u = i; u < i + 2; ++u)
+            ff_acc(acc_h[c8 * 8 + u], acc_l[c8 * 8 + u], (hi[u] * f1) * f2, (lo[u] * f1) * f2);
         }
       }
       fence_before();
