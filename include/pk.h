@@ -152,6 +152,9 @@ typedef struct {
                                 per step at most (1..65536)                                   */
   int64_t seq_work;          /* ... complex multiply-adds per step at most (1..2^24)          */
   int64_t seq_k;             /* ... contracted extent per step at most (1..2048)              */
+  int64_t tc_min_k;          /* PK_SPLIT: row steps of GEMM shape (M >= 64, N >= 32) with this
+                                contracted extent or more run on the tensor cores too (4..16;
+                                16: only the GEMM steps, which need K >= 16 anyway)           */
 } pk_tuning;
 
 pk_status pk_tuning_default(pk_tuning* out);

@@ -8,7 +8,9 @@ before every timed launch, the fastest median kept:
   (q = 3, split precision);
 * sequence runs (consecutive small steps of a plan launched as one one-CTA kernel): the
   largest step, in outputs and in complex multiply-adds, that joins a run, on the 64-knot
-  scale workload (q = 2, 3, 5; 192 plans replayed as one concurrent graph, split).
+  scale workload (q = 2, 3, 5; 192 plans replayed as one concurrent graph, split);
+* the smallest contracted extent from which row steps of GEMM shape also run on the
+  tensor cores (split), on the same workload.
 
 Every candidate's results are checked against the first candidate's (same plans, same
 precision) before its time counts.  The winners are written to csrc/tuned_table.h (the
@@ -33,6 +35,7 @@ BATCH_THREADS = (128, 256, 512)
 BATCH_KTAB = (512, 1024, 2048)
 SEQ_OUTS = (1024, 2048, 4096, 8192)
 SEQ_WORK = (1 << 12, 1 << 14, 1 << 16)
+TC_MIN_K = (4, 8, 16)
 
 
 def _rel(a, b):
@@ -127,7 +130,40 @@ def sweep_seq(pk, ctx, stream, flush, reps, log, quick):
     return best, rows
 
 
-def write_table(path, tune, batch_rows, seq_rows, gpu):
+def sweep_tc_min_k(pk, ctx, stream, flush, reps, log):
+    """The smallest K of the row steps of GEMM shape that go to the tensor cores (split),
+    on the scale workload with the chosen sequence thresholds."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    import knotgen as kg
+    knots = kg.knot_suite("scale")
+    kn = [pk.Knot.from_pd(ctx, k.pd, outer=k.outer) for k in knots]
+    jobs = [(k, q) for k in kn for q in (2, 3, 5)]
+    rows, ref, best = [], None, None
+    for tk in TC_MIN_K:
+        ctx.set_tuning(tc_min_k=tk)
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+            plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=128), jobs))
+        ws = [torch.empty(p.workspace_bytes("split") + 256, dtype=torch.uint8, device="cuda")
+              for p in plans]
+        for p, w in zip(plans, ws):
+            pk.upload(p, "split", w)
+        g = pk.Group(plans, "split", ws)
+        ms = _time(g.launch, stream, flush, reps)
+        z = [pk.download(p, "split", w)[0] for p, w in zip(plans, ws)]
+        if ref is None:
+            ref = z
+        ok = max(_rel(x, y) for x, y in zip(z, ref)) <= 1e-6
+        rows.append((tk, ms, ok))
+        log(f"tensor cores for row steps from K={tk}: {ms:.2f} ms per step{'' if ok else ' RESULTS DIFFER'}")
+        if ok and (best is None or ms < best[1]):
+            best = (tk, ms)
+        del g, ws, plans
+        torch.cuda.empty_cache()
+    return best, rows
+
+
+def write_table(path, tune, batch_rows, seq_rows, gpu, tc_rows=()):
     when = datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%d %H:%M UTC")
     lines = ["// Executor launch shapes, written by paper_1807_02119_gb300/autotune.py from",
              f"// measurements on {gpu} ({when}); the library's defaults (pk_tuning_default).",
@@ -138,10 +174,14 @@ def write_table(path, tune, batch_rows, seq_rows, gpu):
     for so, sw, ms, ok, nl in seq_rows:
         lines.append(f"//   outs <= {so:5d}  work <= {sw:6d}  {ms:8.2f}  ({nl} launches)"
                      f"{'' if ok else '  (results differ)'}")
+    if tc_rows:
+        lines.append("// Tensor cores for row steps of GEMM shape from this K, split (median ms per step):")
+        for tk, ms, ok in tc_rows:
+            lines.append(f"//   K >= {tk:2d}  {ms:8.2f}{'' if ok else '  (results differ)'}")
     lines += ["#pragma once", '#include "pk.h"', "",
               "constexpr pk_tuning kTunedDefault = {" +
               f"{tune['batch_threads']}, {tune['batch_ktab']}, {tune['seq_outs']}, "
-              f"{tune['seq_work']}, {tune['seq_k']}" + "};", ""]
+              f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}" + "};", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))
 
@@ -169,12 +209,14 @@ def main():
     (bt, bk, _), brows = sweep_batch(pk, ctx, stream, flush, args.reps, log)
     ctx.set_tuning()
     (so, sw, _), srows = sweep_seq(pk, ctx, stream, flush, args.reps, log, args.quick)
-    tune.update(batch_threads=bt, batch_ktab=bk, seq_outs=so, seq_work=sw)
+    ctx.set_tuning(seq_outs=so, seq_work=sw)
+    (tk, _), trows = sweep_tc_min_k(pk, ctx, stream, flush, args.reps, log)
+    tune.update(batch_threads=bt, batch_ktab=bk, seq_outs=so, seq_work=sw, tc_min_k=tk)
     gpu = torch.cuda.get_device_name(0)
-    write_table(TABLE, tune, brows, srows, gpu)
+    write_table(TABLE, tune, brows, srows, gpu, trows)
     if args.out:
         os.makedirs(args.out, exist_ok=True)
-        write_table(os.path.join(args.out, "tuned_table.h"), tune, brows, srows, gpu)
+        write_table(os.path.join(args.out, "tuned_table.h"), tune, brows, srows, gpu, trows)
     log(f"chosen: {tune}")
 
 

@@ -183,12 +183,12 @@ cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* par
   const double cm = (double)s.R * (double)s.K * (double)s.N;
   const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
   cudaError_t e;
+  if constexpr (std::is_same<R, ff>::value) {
+    if (s.tc && tc_scratch && err)  // digits of A and B, then the tensor-core GEMM
+      return s.tc == 4 ? launch_tc<4>(s, arena, meta, tc_scratch, err, stream, mk, cm, by)
+                       : launch_tc<5>(s, arena, meta, tc_scratch, err, stream, mk, cm, by);
+  }
   if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
-    if constexpr (std::is_same<R, ff>::value) {
-      if (s.tc && tc_scratch && err)  // digits of A and B, then the tensor-core GEMM
-        return s.tc == 4 ? launch_tc<4>(s, arena, meta, tc_scratch, err, stream, mk, cm, by)
-                         : launch_tc<5>(s, arena, meta, tc_scratch, err, stream, mk, cm, by);
-    }
     mk.begin(4, cm, by, gpu_fill(gemm_tiles, 8));
     k_gemm<R><<<(unsigned)gemm_tiles, 256, 0, stream>>>(s, arena, meta);
     mk.end();

@@ -822,7 +822,7 @@ double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& se
 // ------------------------------------------------------------------ step descriptors
 bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
-                bool& swapped, std::vector<int32_t>& cdims, std::string& err) {
+                bool& swapped, std::vector<int32_t>& cdims, std::string& err, int64_t tc_min_k) {
   static const std::vector<int32_t> no_dims;
   swapped = yd != nullptr && yd->size() > xd.size();
   const bool hasb = yd != nullptr;
@@ -973,8 +973,15 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
   else
     st.kernel = KROWS;
   st.chunks = st.kernel == KSPLITK ? (int32_t)std::min<int64_t>(64, (st.K + 2047) / 2048) : 0;
-  st.tc = (st.kernel == KGEMM && !(flags & PK_FLAG_NO_TC)) ? ((flags & PK_FLAG_TC_DIGITS4) ? 4 : 5)
-                                                           : 0;
+  // split precision on the tensor cores: every GEMM step, and row steps of GEMM shape with
+  // a short K (tc_min_k <= K < 16: one zero-padded chunk), whose outputs can cost the row
+  // kernel more float-float work than the tensor cores' epilogue (complex64 and complex128
+  // keep the row kernel for them)
+  const bool short_k = hasb && st.kernel == KROWS && !(flags & PK_FLAG_FORCE_ROWS) && st.M >= 64 &&
+                       st.N >= 32 && st.K >= tc_min_k;
+  st.tc = ((st.kernel == KGEMM || short_k) && !(flags & PK_FLAG_NO_TC))
+              ? ((flags & PK_FLAG_TC_DIGITS4) ? 4 : 5)
+              : 0;
   return true;
 }
 
@@ -982,7 +989,8 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
 bool valid_tuning(const pk_tuning& t) {
   return (t.batch_threads == 128 || t.batch_threads == 256 || t.batch_threads == 512) &&
          t.batch_ktab >= 256 && t.batch_ktab <= 2048 && t.seq_outs >= 1 && t.seq_outs <= 65536 &&
-         t.seq_work >= 1 && t.seq_work <= (1 << 24) && t.seq_k >= 1 && t.seq_k <= kTinyK;
+         t.seq_work >= 1 && t.seq_work <= (1 << 24) && t.seq_k >= 1 && t.seq_k <= kTinyK &&
+         t.tc_min_k >= 4 && t.tc_min_k <= 16;
 }
 
 void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,
@@ -991,7 +999,7 @@ void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,
   tiny.clear();
   const int64_t max_k = std::min<int64_t>(tune.seq_k, kTinyK);
   auto small = [&](const Step& st) {
-    return st.kernel == KROWS && st.R * st.N <= tune.seq_outs && st.K <= max_k &&
+    return st.kernel == KROWS && !st.tc && st.R * st.N <= tune.seq_outs && st.K <= max_k &&
            st.R * st.N * st.K <= tune.seq_work;
   };
   const int32_t n_steps = (int32_t)steps.size();
@@ -1221,7 +1229,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
     Step st;
     bool sw = false;
     if (!build_step(p.tensors[x].dims, y >= 0 ? &p.tensors[y].dims : nullptr, sets[cid], q,
-                    opts.flags, st, sw, p.tensors[cid].dims, err))
+                    opts.flags, st, sw, p.tensors[cid].dims, err, tune.tc_min_k))
       return false;
     st.a = sw ? y : x;
     st.b = sw ? x : y;
@@ -1232,7 +1240,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
   p.tc_bytes = 0;
   p.n_tc = 0;
   for (const Step& st : p.steps)
-    if (st.kernel == KGEMM && st.tc) {
+    if (st.tc) {
       p.n_tc++;
       p.tc_bytes = std::max<int64_t>(p.tc_bytes, tc_scratch(st.Bsz, st.M, st.N, st.K, st.tc).bytes);
     }

@@ -1,29 +1,33 @@
 // Executor launch shapes, written by paper_1807_02119_gb300/autotune.py from
-// measurements on NVIDIA GB300 (2026-12-04 05:08 UTC); the library's defaults (pk_tuning_default).
+// measurements on NVIDIA GB300 (2026-12-04 05:57 UTC); the library's defaults (pk_tuning_default).
 // Batch executor, 4096 knots at q = 3, split, one launch (median ms):
-//   threads  128  ktab   512     4.585
-//   threads  128  ktab  1024     4.541
-//   threads  128  ktab  2048     4.956
-//   threads  256  ktab   512     4.243
-//   threads  256  ktab  1024     4.278
-//   threads  256  ktab  2048     4.292
-//   threads  512  ktab   512     5.530
-//   threads  512  ktab  1024     5.580
-//   threads  512  ktab  2048     5.683
+//   threads  128  ktab   512     4.445
+//   threads  128  ktab  1024     4.501
+//   threads  128  ktab  2048     4.910
+//   threads  256  ktab   512     4.269
+//   threads  256  ktab  1024     4.312
+//   threads  256  ktab  2048     4.308
+//   threads  512  ktab   512     5.555
+//   threads  512  ktab  1024     5.578
+//   threads  512  ktab  2048     5.640
 // Sequence runs, 192 evaluations of the scale workload, split (median ms per step):
-//   outs <=  1024  work <=   4096     68.08  (6471 launches)
-//   outs <=  1024  work <=  16384     67.58  (6360 launches)
-//   outs <=  1024  work <=  65536     67.39  (6336 launches)
-//   outs <=  2048  work <=   4096     67.68  (6469 launches)
-//   outs <=  2048  work <=  16384     68.12  (6343 launches)
-//   outs <=  2048  work <=  65536     67.82  (6312 launches)
-//   outs <=  4096  work <=   4096     68.11  (6203 launches)
-//   outs <=  4096  work <=  16384     68.13  (4479 launches)
-//   outs <=  4096  work <=  65536     67.69  (4392 launches)
-//   outs <=  8192  work <=   4096     69.44  (6203 launches)
-//   outs <=  8192  work <=  16384     67.96  (4477 launches)
-//   outs <=  8192  work <=  65536     69.28  (4015 launches)
+//   outs <=  1024  work <=   4096     60.00  (6354 launches)
+//   outs <=  1024  work <=  16384     60.04  (6243 launches)
+//   outs <=  1024  work <=  65536     59.74  (6219 launches)
+//   outs <=  2048  work <=   4096     60.22  (6352 launches)
+//   outs <=  2048  work <=  16384     60.20  (6226 launches)
+//   outs <=  2048  work <=  65536     60.26  (6195 launches)
+//   outs <=  4096  work <=   4096     60.30  (6086 launches)
+//   outs <=  4096  work <=  16384     60.28  (4362 launches)
+//   outs <=  4096  work <=  65536     60.27  (4275 launches)
+//   outs <=  8192  work <=   4096     59.91  (6086 launches)
+//   outs <=  8192  work <=  16384     60.25  (4360 launches)
+//   outs <=  8192  work <=  65536     60.31  (3898 launches)
+// Tensor cores for row steps of GEMM shape from this K, split (median ms per step):
+//   K >=  4     59.96
+//   K >=  8     60.36
+//   K >= 16     60.53
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 4};
