@@ -50,7 +50,10 @@ typedef enum {
                         pk_eval_noalloc from the evaluation's own error word, which every
                         launch sequence clears again: later evaluations are unaffected     */
   PK_ENODEVICE = 7,  /* operation needs a GPU context (device >= 0)                     */
-  PK_EZERO = 8       /* Z is zero, so log-derivatives are undefined                     */
+  PK_EZERO = 8,      /* Z is zero, so log-derivatives are undefined                     */
+  PK_ENONFINITE = 9  /* the finite check (PK_DEBUG_CHECK_FINITE) found NaN or Inf in a
+                        tensor of the evaluation; pk_last_error names the slice and the
+                        step (-1: an initial tensor) that wrote it                       */
 } pk_status;
 
 typedef enum {
@@ -280,9 +283,10 @@ pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const vo
 /* Host-side last stage of pk_download, for checking it without a GPU: `record` is the
  * 32-byte total record an evaluation leaves in its workspace (double re, double im,
  * int64 exp2 of the contracted value, uint64 status word).  Writes Z (the value times the
- * plan's constant factor) and V = A(q) Z (if V is not NULL).  Errors: PK_ETIMEOUT when the
- * status word is nonzero (a bounded device wait gave up; Z is then meaningless),
- * PK_EINVAL as pk_eval for V. */
+ * plan's constant factor) and V = A(q) Z (if V is not NULL).  Errors: PK_ENONFINITE when
+ * bits 1 and up of the status word hold a finite-check code (((slice + 1) << 24 | (step +
+ * 2)) << 1), PK_ETIMEOUT when only bit 0 is set (a bounded device wait gave up); Z is then
+ * meaningless; PK_EINVAL as pk_eval for V. */
 pk_status pk_decode_result(const pk_plan* p, const void* record, pk_scaled* Z, pk_scaled* V);
 
 /* The workspace of an evaluation is a small per-plan state (initial-tensor program,
@@ -501,6 +505,51 @@ pk_status pk_grad_stats(const pk_plan* p, double* out);
  * pk_plan_opts.edge_weights; NULL restores the standard weights of t(q)).  The order,
  * slicing and arena are unchanged; the next pk_upload / pk_eval / pk_grad uses them. */
 pk_status pk_plan_set_weights(pk_plan* p, const double* edge_weights);
+
+/* ---- debugging aids and slice-level resume ---------------------------------------- */
+
+/* Debug flags of a context (0 by default).  While any is set, pk_launch and
+ * pk_launch_arena (so pk_eval) enqueue the plan's kernels directly instead of replaying a
+ * recorded graph; groups (pk_group_*), the batch executor, pk_grad, pk_eval_exact and
+ * pk_eval_noalloc ignore them. */
+#define PK_DEBUG_CHECK_FINITE 1 /* after the initial tensors and after every step (sequence
+                                   runs split into single steps) scan the tensor just
+                                   written for NaN / Inf; the first one found is reported by
+                                   pk_download as PK_ENONFINITE                            */
+#define PK_DEBUG_VERIFY 2       /* pk_plan_verify before every launch (PK_EINVAL on failure) */
+#define PK_DEBUG_NVTX 4         /* an NVTX range around every kernel launch, named
+                                   "step <i> <class>" (i = -1 for the initial tensors and the
+                                   slice results; class as pk_profile's)                    */
+pk_status pk_ctx_set_debug(pk_ctx* ctx, int32_t flags);
+
+/* Host-side check of a plan's index maps and memory layout for `precision`, without a GPU.
+ * Every gather and scatter of a step is an affine map given by stride runs, so it is
+ * checked exhaustively: A's row and contracted runs (and B's batch, contracted and column
+ * runs, and in the GEMM view C's runs) enumerate the operand's dense tensor exactly once
+ * with extents R, K, N (Bsz, M); each step reads live tensors and writes its own; every
+ * tensor lies inside the arena on a 512-byte boundary, and tensors live at the same step do
+ * not overlap; sequence-kernel records equal their steps; the complex128 tail, the split
+ * precision's digit scratch, the reverse program (PK_FLAG_GRAD) and the state records fit
+ * the workspace of pk_plan_workspace_bytes.  PK_EINVAL with the first violation in msg
+ * (NUL-terminated, at most msg_bytes; msg may be NULL). */
+pk_status pk_plan_verify(const pk_plan* p, int32_t precision, char* msg, uint64_t msg_bytes);
+
+/* Slices [first, first + count) of an evaluation (Sec. III: a sliced contraction is a sum
+ * of independent sub-contractions with the sliced indices fixed; pk_plan_stats gives
+ * n_slices): uploads the program, enqueues those slices directly (no graph; the context's
+ * debug flags apply), waits, and writes each slice's contracted value -- without the
+ * plan's constant factor -- to slices[0 .. count).  The values are plain data: a caller
+ * can store them and resume a long evaluation from the first slice not yet done.
+ * d_workspace as pk_eval.  Errors: PK_EINVAL (range), PK_ETIMEOUT / PK_ENONFINITE as
+ * pk_download for the slices run. */
+pk_status pk_eval_slices(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                         uint64_t workspace_bytes, int64_t first, int64_t count,
+                         pk_scaled* slices);
+/* Z and V (NULL: not wanted) from all n = n_slices per-slice values of pk_eval_slices, in
+ * slice order: summed at the largest exponent with compensated (Kahan) sums, times the
+ * plan's constant factor, V = A(q) Z as pk_download.  Host only. */
+pk_status pk_combine_slices(const pk_plan* p, const pk_scaled* slices, int64_t n, pk_scaled* Z,
+                            pk_scaled* V);
 
 #ifdef __cplusplus
 }

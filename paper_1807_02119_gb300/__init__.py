@@ -20,7 +20,8 @@ PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 ORDERS = {"auto": 0, "greedy_edge": 1, "greedy_spin": 2, "elim_spin": 3, "partition": 4,
           "fill_spin": 5}
 STATUS = {0: "PK_OK", 1: "PK_EINVAL", 2: "PK_ENOTKNOT", 3: "PK_ENOMEM", 4: "PK_ETOOWIDE",
-          5: "PK_ECUDA", 6: "PK_ETIMEOUT", 7: "PK_ENODEVICE", 8: "PK_EZERO"}
+          5: "PK_ECUDA", 6: "PK_ETIMEOUT", 7: "PK_ENODEVICE", 8: "PK_EZERO", 9: "PK_ENONFINITE"}
+DEBUG_CHECK_FINITE, DEBUG_VERIFY, DEBUG_NVTX = 1, 2, 4
 
 EXPORTED = [
     "pk_ctx_create", "pk_ctx_set_stream", "pk_last_error", "pk_ctx_destroy",
@@ -36,7 +37,8 @@ EXPORTED = [
     "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve", "pk_decode_result",
     "pk_group_create_profiled", "pk_group_profile", "pk_group_timeline",
     "pk_tuning_default", "pk_ctx_set_tuning", "pk_ctx_get_tuning", "pk_knot_simplify",
-    "pk_order_stats", "pk_ctx_set_hbm_budget", "pk_grad_weights",
+    "pk_order_stats", "pk_ctx_set_hbm_budget", "pk_grad_weights", "pk_ctx_set_debug",
+    "pk_plan_verify", "pk_eval_slices", "pk_combine_slices",
 ]
 
 
@@ -109,6 +111,10 @@ def lib():
         "pk_knot_simplify": [vp, vp, P(vp)],
         "pk_order_stats": [vp, i32, i32, i32, P(C.c_double)],
         "pk_ctx_set_hbm_budget": [vp, u64],
+        "pk_ctx_set_debug": [vp, i32],
+        "pk_plan_verify": [vp, i32, C.c_char_p, u64],
+        "pk_eval_slices": [vp, vp, i32, vp, u64, i64, i64, P(pk_scaled)],
+        "pk_combine_slices": [vp, P(pk_scaled), i64, P(pk_scaled), P(pk_scaled)],
         "pk_grad_weights": [vp, P(C.c_double), P(C.c_double)],
         "pk_knot_edges": [vp, P(i32)],
         "pk_knot_pd": [vp, P(i32)],
@@ -206,6 +212,10 @@ class Context:
 
     def set_stream(self, stream: int):
         _check(lib().pk_ctx_set_stream(self.h, C.c_void_p(stream)), self)
+
+    def set_debug(self, flags: int = 0):
+        """pk_ctx_set_debug: DEBUG_CHECK_FINITE | DEBUG_VERIFY | DEBUG_NVTX (0 turns them off)."""
+        _check(lib().pk_ctx_set_debug(self.h, int(flags)), self)
 
     def set_hbm_budget(self, nbytes: int):
         """pk_ctx_set_hbm_budget: plans created afterwards slice until their workspace fits."""
@@ -418,6 +428,27 @@ class Plan:
         keys = ("a", "b", "c", "R", "K", "N", "rank_c", "kernel")
         return [dict(zip(keys, arr[8 * i:8 * i + 8])) for i in range(n)]
 
+    def verify(self, precision="c128") -> str:
+        """pk_plan_verify: '' when every index map and the memory layout check out, else the
+        first violation."""
+        buf = C.create_string_buffer(512)
+        st = lib().pk_plan_verify(self.h, PRECISIONS[precision], buf, len(buf))
+        if st not in (0, 1):
+            _check(st)
+        return "" if st == 0 else buf.value.decode()
+
+    def combine_slices(self, slices):
+        """pk_combine_slices: (Z, V) from all per-slice values (Scaled, in slice order)."""
+        n = len(slices)
+        arr = (pk_scaled * max(1, n))(*[pk_scaled(x.re, x.im, x.exp2) for x in slices])
+        z, v = pk_scaled(), pk_scaled()
+        st = lib().pk_combine_slices(self.h, arr, n, C.byref(z), C.byref(v))
+        if st == 1 and n == self.stats()["n_slices"]:  # V undefined for this diagram
+            _check(lib().pk_combine_slices(self.h, arr, n, C.byref(z), None))
+            return Scaled.of(z), None
+        _check(st)
+        return Scaled.of(z), Scaled.of(v)
+
     def debug_blob(self, which: int) -> bytes:
         nb = C.c_uint64()
         _check(lib().pk_plan_debug_blob(self.h, which, None, C.byref(nb)))
@@ -462,6 +493,76 @@ def evaluate(plan: Plan, precision: str = "c128", ws=None):
         return Scaled.of(z), None
     _check(st, ctx)
     return Scaled.of(z), Scaled.of(v)
+
+
+def evaluate_slices(plan: Plan, first: int, count: int, precision: str = "c128", ws=None):
+    """pk_eval_slices: the contracted values of slices [first, first + count) as a list of
+    Scaled (without the plan's constant factor; combine with Plan.combine_slices)."""
+    ctx = plan.ctx
+    if ctx.device < 0:
+        raise PkError(7, "evaluate_slices needs a GPU context")
+    _torch_stream(ctx)
+    if ws is None:
+        ws = workspace(plan, precision)
+    out = (pk_scaled * count)()
+    _check(lib().pk_eval_slices(ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
+                                ws.numel() * ws.element_size(), int(first), int(count), out), ctx)
+    return [Scaled.of(out[i]) for i in range(count)]
+
+
+def plan_fingerprint(plan: Plan) -> str:
+    """Digest of the plan's step records and scalars: equal for the same knot, q, options
+    and library version, so a stored partial evaluation is only resumed on its own plan."""
+    import hashlib
+    h = hashlib.sha256()
+    for which in (1, 3):
+        h.update(plan.debug_blob(which))
+    return h.hexdigest()
+
+
+def evaluate_resumable(plan: Plan, path: str, precision: str = "c128", chunk: int = 64,
+                       ws=None, run_slices=None, stop_after: int | None = None):
+    """Z and V of a sliced evaluation that survives interruption: slices are run `chunk` at
+    a time and, after each chunk, every value obtained so far is written to `path` (a JSON
+    file replaced atomically, holding the plan's fingerprint and precision).  A later call
+    with the same plan and path runs only the slices not yet stored.  `stop_after` ends the
+    call (returning None) after that many chunks, for splitting a long evaluation across
+    processes; `run_slices(first, count)` replaces the GPU call (evaluate_slices)."""
+    import json
+    n = plan.stats()["n_slices"]
+    fp = plan_fingerprint(plan)
+    done: dict[int, Scaled] = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("fingerprint") != fp or rec.get("precision") != precision:
+            raise ValueError(f"{path} belongs to another plan or precision")
+        done = {int(k): Scaled(v[0], v[1], int(v[2])) for k, v in rec["slices"].items()}
+    if run_slices is None:
+        def run_slices(first, count):
+            return evaluate_slices(plan, first, count, precision, ws)
+    chunks = 0
+    first = 0
+    while first < n:
+        if first in done:
+            first += 1
+            continue
+        count = 1
+        while count < chunk and first + count < n and first + count not in done:
+            count += 1
+        for i, v in enumerate(run_slices(first, count)):
+            done[first + i] = v
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump({"fingerprint": fp, "precision": precision, "n_slices": n,
+                       "slices": {str(k): [v.re, v.im, v.exp2] for k, v in sorted(done.items())}},
+                      f)
+        os.replace(tmp, path)
+        first += count
+        chunks += 1
+        if stop_after is not None and chunks >= stop_after and len(done) < n:
+            return None
+    return plan.combine_slices([done[i] for i in range(n)])
 
 
 def evaluate_exact(plan: Plan, primes, ws=None):

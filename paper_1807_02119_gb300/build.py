@@ -23,8 +23,8 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-I", INCLUDE, "-I", CSRC,
          "--expt-relaxed-constexpr"]
-SOURCES = ["knot.cpp", "plan.cpp", "grad_plan.cpp", "jones_exact.cpp", "launch.cu", "api.cu", "noalloc.cu",
-           "batch.cu", "exact.cu"]
+SOURCES = ["knot.cpp", "plan.cpp", "grad_plan.cpp", "jones_exact.cpp", "verify.cpp", "launch.cu",
+           "api.cu", "noalloc.cu", "batch.cu", "exact.cu"]
 
 
 def nvcc() -> str:

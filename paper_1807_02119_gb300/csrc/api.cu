@@ -77,6 +77,17 @@ pk_status check_ws(pk_ctx* ctx, const pk_plan* p, int32_t precision, void*& ws, 
 // slices) are launched directly.
 pk_status launch_recorded(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* ws, void* arena) {
   const pk::Plan& P = p->p;
+  if (ctx->debug) {  // debugging aids: verified, checked launches enqueued directly
+    if (ctx->debug & PK_DEBUG_VERIFY) {
+      std::string err;
+      if (!pk::verify_plan(P, precision, err)) return fail(ctx, PK_EINVAL, "pk_plan_verify: " + err);
+    }
+    pk::LaunchOpts o;
+    o.check_finite = (ctx->debug & PK_DEBUG_CHECK_FINITE) != 0;
+    o.nvtx = (ctx->debug & PK_DEBUG_NVTX) != 0;
+    cudaError_t e = pk::launch_plan_opts(P, precision, ws, arena, ctx->stream, o);
+    return e == cudaSuccess ? PK_OK : cuda_fail(ctx, e, "launch");
+  }
   const double nodes = (double)P.n_slices * (double)(P.steps.size() + 4);
   if (nodes > 20000.0) {
     cudaError_t e = pk::launch_plan(P, precision, ws, arena, ctx->stream);
@@ -119,6 +130,21 @@ pk_status launch_recorded(pk_ctx* ctx, const pk_plan* p, int32_t precision, void
 
 namespace pk {
 
+pk_status status_error(unsigned long long status, std::string& err) {
+  if (status >> 1) {
+    err = "the finite check found NaN or Inf in the result of step " +
+          std::to_string(nonfinite_step(status)) + " of slice " +
+          std::to_string(nonfinite_slice(status)) + " (step -1: an initial tensor)";
+    return PK_ENONFINITE;
+  }
+  if (status != 0) {
+    err = "a bounded wait of the tensor-core GEMM gave up: the result is invalid (status " +
+          std::to_string(status) + ")";
+    return PK_ETIMEOUT;
+  }
+  return PK_OK;
+}
+
 pk_status decode_total(const Plan& P, const SliceResult& r, pk_scaled* Z, pk_scaled* V,
                        std::string& err) {
   Scaled z;
@@ -128,11 +154,8 @@ pk_status decode_total(const Plan& P, const SliceResult& r, pk_scaled* Z, pk_sca
   z.norm();
   z = s_mul(z, P.factor);
   *Z = to_abi(z);
-  if (r.status != 0) {
-    err = "a bounded wait of the tensor-core GEMM gave up: the result is invalid (status " +
-          std::to_string(r.status) + ")";
-    return PK_ETIMEOUT;
-  }
+  const pk_status st = status_error(r.status, err);
+  if (st != PK_OK) return st;
   if (V) {
     if (!jones_defined(P.knot)) {
       err = "3w + tau + 2 n_v + 2 not divisible by 4 (knot) or 2 (link)";
@@ -185,6 +208,26 @@ pk_status pk_ctx_set_tuning(pk_ctx* ctx, const pk_tuning* t) {
   if (!pk::valid_tuning(*t)) return fail(ctx, PK_EINVAL, "tuning value out of range");
   ctx->tuning = *t;
   return PK_OK;
+}
+
+pk_status pk_ctx_set_debug(pk_ctx* ctx, int32_t flags) {
+  if (!ctx) return PK_EINVAL;
+  if (flags & ~(PK_DEBUG_CHECK_FINITE | PK_DEBUG_VERIFY | PK_DEBUG_NVTX))
+    return fail(ctx, PK_EINVAL, "unknown debug flag");
+  ctx->debug = flags;
+  return PK_OK;
+}
+
+pk_status pk_plan_verify(const pk_plan* p, int32_t precision, char* msg, uint64_t msg_bytes) {
+  if (!p || !valid_precision(precision)) return PK_EINVAL;
+  std::string err;
+  const bool ok = pk::verify_plan(p->p, precision, err);
+  if (msg && msg_bytes > 0) {
+    const size_t n = std::min<size_t>(err.size(), (size_t)msg_bytes - 1);
+    std::memcpy(msg, err.data(), n);
+    msg[n] = 0;
+  }
+  return ok ? PK_OK : PK_EINVAL;
 }
 
 pk_status pk_ctx_set_hbm_budget(pk_ctx* ctx, uint64_t bytes) {
@@ -731,6 +774,85 @@ pk_status pk_eval(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_work
   s = pk_launch(ctx, p, precision, d_workspace, workspace_bytes);
   if (s != PK_OK) return s;
   return pk_download(ctx, p, precision, d_workspace, Z, V);
+}
+
+pk_status pk_eval_slices(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                         uint64_t workspace_bytes, int64_t first, int64_t count,
+                         pk_scaled* slices) {
+  if (!ctx || !p || !slices || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
+  const pk::Plan& P = p->p;
+  if (first < 0 || count < 1 || first > P.n_slices - count)
+    return fail(ctx, PK_EINVAL, "slice range outside [0, n_slices)");
+  pk_status s = pk_upload(ctx, p, precision, d_workspace, workspace_bytes);
+  if (s != PK_OK) return s;
+  DeviceGuard g(ctx->device);
+  void* ws = d_workspace;
+  if ((s = check_ws(ctx, p, precision, ws, workspace_bytes)) != PK_OK) return s;
+  if (ctx->debug & PK_DEBUG_VERIFY) {
+    std::string err;
+    if (!pk::verify_plan(P, precision, err)) return fail(ctx, PK_EINVAL, "pk_plan_verify: " + err);
+  }
+  pk::LaunchOpts o;
+  o.slice_first = first;
+  o.slice_count = count;
+  o.check_finite = (ctx->debug & PK_DEBUG_CHECK_FINITE) != 0;
+  o.nvtx = (ctx->debug & PK_DEBUG_NVTX) != 0;
+  cudaError_t e = pk::launch_plan_opts(P, precision, ws, (char*)ws + P.off_arena, ctx->stream, o);
+  std::vector<pk::SliceResult> rec((size_t)count + 1);
+  const char* res = (const char*)ws + P.off_result;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rec.data(), res + sizeof(pk::SliceResult) * first,
+                        sizeof(pk::SliceResult) * count, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&rec[count], res + sizeof(pk::SliceResult) * P.n_slices,
+                        sizeof(pk::SliceResult), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "slices");
+  std::string err;
+  if ((s = pk::status_error(rec[count].status, err)) != PK_OK) return fail(ctx, s, err);
+  for (int64_t i = 0; i < count; ++i) {
+    pk::Scaled z;
+    z.re = rec[i].re;
+    z.im = rec[i].im;
+    z.e = rec[i].exp;
+    z.norm();
+    slices[i] = to_abi(z);
+  }
+  return PK_OK;
+}
+
+pk_status pk_combine_slices(const pk_plan* p, const pk_scaled* slices, int64_t n, pk_scaled* Z,
+                            pk_scaled* V) {
+  if (!p || !slices || !Z || n != p->p.n_slices) return PK_EINVAL;
+  int64_t emax = INT64_MIN;
+  for (int64_t i = 0; i < n; ++i) {
+    const double m = std::max(std::fabs(slices[i].re), std::fabs(slices[i].im));
+    if (!std::isfinite(m)) return PK_EINVAL;
+    if (m > 0) {
+      int e;
+      std::frexp(m, &e);
+      emax = std::max<int64_t>(emax, slices[i].exp2 + e);
+    }
+  }
+  pk::SliceResult tot{0, 0, 0, 0};
+  if (emax != INT64_MIN) {
+    double are = 0, aim = 0, cre = 0, cim = 0;  // Kahan-compensated, as the device sum
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t d = slices[i].exp2 - emax;
+      const double f = d < -2000 ? 0.0 : std::ldexp(1.0, (int)d);
+      const double yr = slices[i].re * f - cre, tr = are + yr;
+      cre = (tr - are) - yr;
+      are = tr;
+      const double yi = slices[i].im * f - cim, ti = aim + yi;
+      cim = (ti - aim) - yi;
+      aim = ti;
+    }
+    tot.re = are;
+    tot.im = aim;
+    tot.exp = emax;
+  }
+  std::string err;
+  return pk::decode_total(p->p, tot, Z, V, err);
 }
 
 pk_status pk_grad_workspace_bytes(const pk_plan* p, int32_t precision, uint64_t* bytes) {

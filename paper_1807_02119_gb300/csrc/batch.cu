@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(T) k_batch(const BatchKnot* __restrict__ knots
         for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         if (lane == 0) {
           meta[r.meta].maxbits = max_bits(vmax);
-          meta[r.meta].exp = 0;
+          meta[r.meta].exp = r.exp2;
         }
       }
       __syncthreads();

@@ -12,6 +12,7 @@
 
 struct pk_ctx {
   pk_tuning tuning = kTunedDefault;
+  int32_t debug = 0;               // PK_DEBUG_* bits
   uint64_t hbm_budget = 0;         // plans' workspaces must fit (0: no limit)
   int32_t device = -1;
   cudaStream_t stream = nullptr;
@@ -68,6 +69,18 @@ cudaError_t launch_exact(const Plan& p, uint32_t prime, void* ws, void* arena, v
 // `ws` holds the plan state (bytes [0, off_arena)), `arena` the tensors.
 cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,
                         cudaStream_t stream);
+// Options of a launch sequence enqueued directly (not replayed from a graph).
+struct LaunchOpts {
+  int64_t slice_first = 0;   // slices [slice_first, slice_first + slice_count); the first
+  int64_t slice_count = -1;  // one clears every slice record, so records outside the range
+                             // read 0; slice_count -1: every slice
+  bool check_finite = false; // scan the initial tensors and every step's result for NaN /
+                             // Inf (steps launched one at a time); the first hit is written
+                             // into the error word (status_nonfinite)
+  bool nvtx = false;         // an NVTX range around every launch, named by step and class
+};
+cudaError_t launch_plan_opts(const Plan& p, int32_t precision, void* ws, void* arena,
+                             cudaStream_t stream, const LaunchOpts& opts);
 // Same, with CUDA-event timing per kernel class; waits for the stream (launch.cu).
 cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena,
                          cudaStream_t stream, double* out);

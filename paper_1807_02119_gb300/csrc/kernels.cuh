@@ -298,6 +298,7 @@ __global__ void __launch_bounds__(256) k_build(const Recipe* __restrict__ rec,
     vmax = fmax(vmax, mag(v));
   }
   block_max_to_meta(vmax, meta + r.meta);
+  if (blockIdx.x == 0 && threadIdx.x == 0) meta[r.meta].exp = r.exp2;
 }
 
 // ------------------------------------------------------------------ contraction step
@@ -862,7 +863,9 @@ static __global__ void k_sum_slices(SliceResult* res, long long n) {
   __shared__ long long emax_s[256];
   __shared__ double sre[256], sim[256];
   long long emax = LLONG_MIN;
+  bool bad = false;   // a non-finite slice value makes the total NaN, never a silent 0
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    if (!isfinite(res[i].re) || !isfinite(res[i].im)) bad = true;
     double m = fmax(fabs(res[i].re), fabs(res[i].im));
     if (m > 0) {
       int e;
@@ -871,7 +874,13 @@ static __global__ void k_sum_slices(SliceResult* res, long long n) {
     }
   }
   emax_s[threadIdx.x] = emax;
-  __syncthreads();
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) {
+      res[n].re = res[n].im = __longlong_as_double(0x7FF8000000000000LL);
+      res[n].exp = 0;
+    }
+    return;
+  }
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) emax_s[threadIdx.x] = max(emax_s[threadIdx.x], emax_s[threadIdx.x + o]);
     __syncthreads();

@@ -7,8 +7,10 @@
 //  split     : every kernel on float-float ("split FP32") tensors.
 //  The slice scalar and the sum over slices are always formed in FP64.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -36,6 +38,54 @@ __global__ void __launch_bounds__(256) k_widen(const ConvRec* __restrict__ conv,
     meta[c.dst_meta].maxbits = (unsigned long long)__double_as_longlong((double)m);
     meta[c.dst_meta].exp = meta[c.src_meta].exp;
   }
+}
+
+// ---- finite check (debug): NaN / Inf in a tensor just written sets the error word
+template <typename R>
+__device__ __forceinline__ bool finite_cx(const Cx<R>& v) {
+  return isfinite(v.re) && isfinite(v.im);
+}
+template <>
+__device__ __forceinline__ bool finite_cx<ff>(const Cx<ff>& v) {
+  return isfinite(v.re.hi) && isfinite(v.re.lo) && isfinite(v.im.hi) && isfinite(v.im.lo);
+}
+
+// Writes `code` into bits 1 and up of the error word unless a code is there already (the
+// checks run in stream order, so the first tensor found non-finite is the one reported);
+// bit 0 (wait expiry) is kept.  A failed exchange means another writer changed the word,
+// so the loop ends after a few rounds; it is bounded all the same.
+__device__ void set_nonfinite(unsigned long long* word, unsigned long long code) {
+  unsigned long long old = *(volatile unsigned long long*)word;
+  for (int i = 0; i < 64 && (old >> 1) == 0ull; ++i) {
+    const unsigned long long seen = atomicCAS(word, old, old | code);
+    if (seen == old) return;
+    old = seen;
+  }
+}
+
+// Entries [0, n) at x, or with `rec` the initial tensor rec[blockIdx.y].
+template <typename R>
+__global__ void __launch_bounds__(256) k_check_finite(const Cx<R>* x, long long n,
+                                                      const Recipe* rec,
+                                                      unsigned long long* word,
+                                                      unsigned long long code) {
+  if (rec) {
+    x += rec[blockIdx.y].offset;
+    n = rec[blockIdx.y].elems;
+  }
+  bool bad = false;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    bad |= !finite_cx(x[e]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) set_nonfinite(word, code);
+}
+
+template <typename R>
+cudaError_t check_tensor(const Cx<R>* x, long long n, unsigned long long* word,
+                         unsigned long long code, cudaStream_t st) {
+  const unsigned bx = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 1216));
+  k_check_finite<R><<<bx, 256, 0, st>>>(x, n, nullptr, word, code);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -68,9 +118,14 @@ double gpu_fill(long long grid, int per_sm) {
   return std::min(1.0, (double)grid / ((double)g_sms * (double)per_sm));
 }
 
+constexpr const char* kClassName[kNumClasses] = {"build", "rows", "splitk", "results",
+                                                  "gemm", "gemm_tc", "digits"};
+
 struct Marker {
   Prof* prof;
   cudaStream_t st;
+  bool nvtx = false;   // NVTX range per launch: "step <i> <class>" (i = -1: not a step)
+  int step = -1;
   // During stream capture a plain event record only marks a dependency; the external
   // flag makes it an event-record node of the graph, re-recorded by every replay.
   void record(cudaEvent_t e) {
@@ -82,6 +137,7 @@ struct Marker {
       cudaEventRecord(e, st);
   }
   void begin(int c, double cm, double by, double fill) {
+    if (nvtx) nvtxRangePushA(("step " + std::to_string(step) + " " + kClassName[c]).c_str());
     if (!prof) return;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -98,6 +154,7 @@ struct Marker {
   }
   void end() {
     if (prof) record(prof->ev.back().second);
+    if (nvtx) nvtxRangePop();
   }
 };
 
@@ -213,8 +270,7 @@ double step_bytes(const Plan& p, const Step& s, double elem_bytes) {
 // Steps [first, last) of the plan, all in storage type R.
 template <typename R>
 cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t first, int32_t last,
-                        cudaStream_t stream,
-                        Marker& mk) {
+                        cudaStream_t stream, Marker& mk, const LaunchOpts& o, long long sl) {
   Cx<R>* arena = (Cx<R>*)arena_base;
   Meta* meta = (Meta*)(base + p.off_meta);
   Cx<double>* partial = (Cx<double>*)(base + p.off_scratch);
@@ -226,7 +282,7 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
   size_t sg = 0;
   for (int32_t i = first; i < last;) {
     while (sg < p.segments.size() && p.segments[sg].first < i) ++sg;
-    if (sg < p.segments.size() && p.segments[sg].first == i &&
+    if (!o.check_finite && sg < p.segments.size() && p.segments[sg].first == i &&
         i + p.segments[sg].count <= last) {  // a run of small steps: one sequence launch
       const Segment& g = p.segments[sg];
       double cm = 0, by = 0;
@@ -234,6 +290,7 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
         cm += (double)p.steps[j].R * (double)p.steps[j].K * (double)p.steps[j].N;
         by += step_bytes(p, p.steps[j], (double)sizeof(Cx<R>));
       }
+      mk.step = i;
       mk.begin(1, cm, by, gpu_fill(1, 8));
       k_seg<R><<<1, 256, 0, stream>>>(tiny + g.tiny0, g.count, arena, meta);
       mk.end();
@@ -242,8 +299,12 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
       i += g.count;
       continue;
     }
+    mk.step = i;
     cudaError_t e = launch_step<R>(p.steps[i], arena, meta, partial, counters + i, stream, mk,
                                    step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)), tcs, err);
+    if (e == cudaSuccess && o.check_finite)
+      e = check_tensor<R>(arena + p.steps[i].off_c, p.tensors[p.steps[i].c].elems, err,
+                          status_nonfinite(sl, i), stream);
     if (e != cudaSuccess) return e;
     ++i;
   }
@@ -252,7 +313,7 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
 
 template <typename R>
 cudaError_t launch_build(const Plan& p, char* base, char* arena_base, long long sl, cudaStream_t stream,
-                         Marker& mk) {
+                         Marker& mk, const LaunchOpts& o) {
   if (p.n_init <= 0) return cudaSuccess;
   if (p.n_init > 65535) return cudaErrorInvalidValue;
   int64_t maxel = 1, initel = 0;
@@ -261,58 +322,73 @@ cudaError_t launch_build(const Plan& p, char* base, char* arena_base, long long 
     initel += r.elems;
   }
   const unsigned bx = (unsigned)std::min<int64_t>((maxel + 255) / 256, 64);
+  mk.step = -1;
   mk.begin(0, 0, (double)sizeof(Cx<R>) * (double)initel, gpu_fill((long long)bx * p.n_init, 8));
   k_build<R><<<dim3(bx, (unsigned)p.n_init), 256, 0, stream>>>(
       (const Recipe*)(base + p.off_recipe), (const Slot*)(base + p.off_slots),
       (Cx<R>*)arena_base, (Meta*)(base + p.off_meta), p.q, sl, (int)p.sliced.size());
   mk.end();
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && o.check_finite) {
+    k_check_finite<R><<<dim3(bx, (unsigned)p.n_init), 256, 0, stream>>>(
+        (const Cx<R>*)arena_base, 0, (const Recipe*)(base + p.off_recipe),
+        &((SliceResult*)(base + p.off_result))[p.n_slices].status, status_nonfinite(sl, -1));
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 // `ws` holds the plan's state (program, bookkeeping, results, scratch: the bytes before
 // off_arena); `arena` holds its tensors (and the complex128 tail region, if any).
 cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena, cudaStream_t stream,
-                        Prof* prof) {
+                        Prof* prof, const LaunchOpts& o) {
   char* base = (char*)ws;
   char* arena_base = (char*)arena;
-  Marker mk{prof, stream};
+  Marker mk{prof, stream, o.nvtx};
   SliceResult* res = (SliceResult*)(base + p.off_result);
   const int32_t n_steps = (int32_t)p.steps.size();
+  const long long first = o.slice_first;
+  const long long stop = o.slice_count < 0 ? p.n_slices : first + o.slice_count;
+  if (first < 0 || stop > p.n_slices || stop <= first) return cudaErrorInvalidValue;
+  unsigned long long* errw = &res[p.n_slices].status;
   cudaError_t e;
-  for (long long sl = 0; sl < p.n_slices; ++sl) {
+  for (long long sl = first; sl < stop; ++sl) {
     // bookkeeping and split-K tickets; the first slice also clears the slice results and
     // the total record (its status word is the evaluation's error word)
-    const uint64_t clear = sl == 0 ? p.off_result - p.off_meta + sizeof(SliceResult) * (p.n_slices + 1)
-                                   : p.off_result - p.off_meta;
+    const uint64_t clear = sl == first ? p.off_result - p.off_meta + sizeof(SliceResult) * (p.n_slices + 1)
+                                       : p.off_result - p.off_meta;
     e = cudaMemsetAsync(base + p.off_meta, 0, clear, stream);
     if (e != cudaSuccess) return e;
     if (precision == PK_C128) {
-      if ((e = launch_build<double>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
-      if ((e = launch_bulk<double>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
+      if ((e = launch_build<double>(p, base, arena_base, sl, stream, mk, o)) != cudaSuccess) return e;
+      if ((e = launch_bulk<double>(p, base, arena_base, 0, n_steps, stream, mk, o, sl)) != cudaSuccess) return e;
+      mk.step = -1;
       mk.begin(3, 0, 0, gpu_fill(1, 8));
       k_slice_result<double><<<1, 32, 0, stream>>>((Cx<double>*)arena_base,
                                                    p.tensors[p.final_tensor].offset,
                                                    (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
       mk.end();
     } else if (precision == PK_SPLIT) {
-      if ((e = launch_build<ff>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
-      if ((e = launch_bulk<ff>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
+      if ((e = launch_build<ff>(p, base, arena_base, sl, stream, mk, o)) != cudaSuccess) return e;
+      if ((e = launch_bulk<ff>(p, base, arena_base, 0, n_steps, stream, mk, o, sl)) != cudaSuccess) return e;
+      mk.step = -1;
       mk.begin(3, 0, 0, gpu_fill(1, 8));
       k_slice_result<ff><<<1, 32, 0, stream>>>((Cx<ff>*)arena_base,
                                                p.tensors[p.final_tensor].offset,
                                                (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
       mk.end();
     } else if (p.tail.empty() && p.conv.empty()) {  // complex64
-      if ((e = launch_build<float>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
-      if ((e = launch_bulk<float>(p, base, arena_base, 0, n_steps, stream, mk)) != cudaSuccess) return e;
+      if ((e = launch_build<float>(p, base, arena_base, sl, stream, mk, o)) != cudaSuccess) return e;
+      if ((e = launch_bulk<float>(p, base, arena_base, 0, n_steps, stream, mk, o, sl)) != cudaSuccess) return e;
+      mk.step = -1;
       mk.begin(3, 0, 0, gpu_fill(1, 8));
       k_slice_result<float><<<1, 32, 0, stream>>>((Cx<float>*)arena_base,
                                                   p.tensors[p.final_tensor].offset,
                                                   (Meta*)(base + p.off_meta), p.final_tensor, res, sl);
       mk.end();
     } else {  // complex64 with a complex128 tail
-      if ((e = launch_build<float>(p, base, arena_base, sl, stream, mk)) != cudaSuccess) return e;
-      if ((e = launch_bulk<float>(p, base, arena_base, 0, p.tail_first, stream, mk)) != cudaSuccess) return e;
+      if ((e = launch_build<float>(p, base, arena_base, sl, stream, mk, o)) != cudaSuccess) return e;
+      if ((e = launch_bulk<float>(p, base, arena_base, 0, p.tail_first, stream, mk, o, sl)) != cudaSuccess) return e;
       Cx<double>* tail = (Cx<double>*)(arena_base + (p.off_tail - p.off_arena));
       Meta* meta = (Meta*)(base + p.off_meta);
       if (!p.conv.empty()) {
@@ -332,11 +408,16 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
         s.off_a = ts.off_a;
         s.off_b = ts.off_b;
         s.off_c = ts.off_c;
+        mk.step = ts.step;
         e = launch_step<double>(s, tail, meta, (Cx<double>*)(base + p.off_scratch),
                                 (unsigned*)(base + p.off_counter) + ts.step, stream, mk,
                                 step_bytes(p, p.steps[ts.step], 16.0));
+        if (e == cudaSuccess && o.check_finite)
+          e = check_tensor<double>(tail + ts.off_c, p.tensors[p.steps[ts.step].c].elems, errw,
+                                   status_nonfinite(sl, ts.step), stream);
         if (e != cudaSuccess) return e;
       }
+      mk.step = -1;
       mk.begin(3, 0, 0, gpu_fill(1, 8));
       k_slice_result<double><<<1, 32, 0, stream>>>(tail, p.final_tail_off, meta, p.final_tensor,
                                                    res, sl);
@@ -344,6 +425,7 @@ cudaError_t launch_impl(const Plan& p, int32_t precision, void* ws, void* arena,
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  mk.step = -1;
   mk.begin(3, 0, 0, gpu_fill(1, 8));
   k_sum_slices<<<1, 256, 0, stream>>>(res, p.n_slices);
   mk.end();
@@ -457,7 +539,14 @@ cudaError_t launch_plan(const Plan& p, int32_t precision, void* ws, void* arena,
                         cudaStream_t stream) {
   cudaError_t e = prepare_kernels();
   if (e != cudaSuccess) return e;
-  return launch_impl(p, precision, ws, arena, stream, nullptr);
+  return launch_impl(p, precision, ws, arena, stream, nullptr, LaunchOpts{});
+}
+
+cudaError_t launch_plan_opts(const Plan& p, int32_t precision, void* ws, void* arena,
+                             cudaStream_t stream, const LaunchOpts& opts) {
+  cudaError_t e = prepare_kernels();
+  if (e != cudaSuccess) return e;
+  return launch_impl(p, precision, ws, arena, stream, nullptr, opts);
 }
 
 cudaError_t launch_grad(const Plan& p, int32_t precision, void* ws, cudaStream_t stream) {
@@ -473,7 +562,7 @@ cudaError_t launch_plan_prof(const Plan& p, int32_t precision, void* ws, void* a
                              cudaStream_t stream, Prof* prof) {
   cudaError_t e = prepare_kernels();
   if (e != cudaSuccess) return e;
-  return launch_impl(p, precision, ws, arena, stream, prof);
+  return launch_impl(p, precision, ws, arena, stream, prof, LaunchOpts{});
 }
 
 Prof* prof_new() { return new Prof(); }
@@ -545,7 +634,7 @@ cudaError_t profile_plan(const Plan& p, int32_t precision, void* ws, void* arena
   cudaError_t pe = prepare_kernels();
   if (pe != cudaSuccess) return pe;
   Prof prof;
-  cudaError_t e = launch_impl(p, precision, ws, arena, stream, &prof);
+  cudaError_t e = launch_impl(p, precision, ws, arena, stream, &prof, LaunchOpts{});
   cudaError_t e2 = cudaStreamSynchronize(stream);
   if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return e;

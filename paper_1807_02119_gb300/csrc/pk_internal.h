@@ -8,6 +8,12 @@
 
 #include "pk.h"
 
+#ifdef __CUDACC__
+#define PK_HD __host__ __device__
+#else
+#define PK_HD
+#endif
+
 namespace pk {
 
 // ------------------------------------------------------------------ knots (Sec. II)
@@ -62,6 +68,10 @@ struct Recipe {
   int64_t elems;           // q^rank
   int64_t offset;          // element offset in the tensor arena
   int32_t meta;            // meta slot (tensor id)
+  int32_t exp2;            // the entries stand for entry * 2^exp2: general clause weights
+                           // are stored scaled by a power of two (max entry in [0.5, 1)),
+                           // so that products of large or small weights neither overflow
+                           // nor underflow before the steps' own rescaling; 0 otherwise
 };
 
 struct Slot {
@@ -128,11 +138,20 @@ struct Meta {
 struct SliceResult {
   double re, im;
   long long exp;
-  // In the total record (index n_slices) only: nonzero when a bounded device wait of this
-  // evaluation gave up (the tensor-core GEMM's pipeline waits); the value is then invalid.
-  // Cleared by the first slice's bookkeeping reset of every launch sequence.
+  // In the total record (index n_slices) only, the evaluation's error word: bit 0 is set
+  // when a bounded device wait gave up (the tensor-core GEMM's pipeline waits); bits 1 and
+  // up hold status_nonfinite's code of the first tensor found non-finite by the finite
+  // check.  Nonzero: the value is invalid.  Cleared by the first slice's bookkeeping reset
+  // of every launch sequence.
   unsigned long long status;
 };
+// Error-word code of a non-finite entry in the result of `step` (-1: an initial tensor) of
+// slice `slice`; decoded by nonfinite_slice / nonfinite_step.
+PK_HD inline unsigned long long status_nonfinite(long long slice, int step) {
+  return ((unsigned long long)(slice + 1) << 24 | (unsigned long long)(step + 2)) << 1;
+}
+inline long long nonfinite_slice(unsigned long long status) { return (long long)(status >> 25) - 1; }
+inline int nonfinite_step(unsigned long long status) { return (int)((status >> 1) & 0xFFFFFF) - 2; }
 
 // Split precision: a bulk (complex64) tensor read by a complex128 tail step is copied,
 // widened, into the tail region; its copy gets its own bookkeeping slot.
@@ -167,11 +186,6 @@ struct TailStep {
   int64_t off_a, off_b, off_c;       // complex128 elements into the tail region
 };
 
-#ifdef __CUDACC__
-#define PK_HD __host__ __device__
-#else
-#define PK_HD
-#endif
 
 // GEMM steps of the split precision on the tensor cores: each operand element becomes S
 // BF16 digits (exact 8-bit pieces; S = Step::tc, 4 or 5), stored per tile block and
@@ -267,6 +281,7 @@ struct Plan {
   int32_t n_init = 0;
   std::vector<Recipe> recipes;
   std::vector<Slot> slots;
+  std::vector<int32_t> slot_exp;     // per slot: power of two its clause values are scaled by
   std::vector<Step> steps;
   std::vector<int32_t> sliced;       // sliced index ids
   int64_t n_slices = 1;
@@ -311,6 +326,14 @@ struct Plan {
   std::vector<std::vector<int32_t>> leaf_dims;  // initial tensors' dims before slicing
   GradProgram grad;
 };
+
+// Host-side check of every index map and of the memory layout of `p` for `precision`
+// (verify.cpp); false with `err` naming the first violation.
+bool verify_plan(const Plan& p, int32_t precision, std::string& err);
+
+// The error of an evaluation's error word (SliceResult::status of the total record):
+// PK_ENONFINITE for a finite-check code, PK_ETIMEOUT for an expired wait, with `err` set.
+pk_status status_error(unsigned long long status, std::string& err);
 
 // Host side of reading a result back: Z from the total record (normalised, times the
 // plan's constant factor) and V = A(q) Z when V is not null.  PK_ETIMEOUT (with `err` set)

@@ -1442,6 +1442,8 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
   if (!p.tiny.empty())
     std::memcpy(p.program.data() + p.off_tiny, p.tiny.data(), sizeof(TinyStep) * p.tiny.size());
   if (grad && !make_grad_program(p, opts.checkpoint_stride, opts.flags, tune, err)) return false;
+  // clause values of general networks, stored scaled by powers of two (Recipe::exp2)
+  if (p.general) apply_weights(p);
   return true;
 }
 
@@ -1462,22 +1464,37 @@ bool set_weights(Plan& p, const double* w) {
   return true;
 }
 
+// Binary exponent of max(|x|) over the four values (frexp convention), 0 when all are 0.
+static int32_t max_exp4(double a, double b, double c, double d) {
+  const double m = std::max(std::max(std::fabs(a), std::fabs(b)), std::max(std::fabs(c), std::fabs(d)));
+  if (!(m > 0)) return 0;
+  int e;
+  std::frexp(m, &e);
+  return e;
+}
+
 void apply_weights(Plan& p) {
+  p.slot_exp.assign(p.slots.size(), 0);
   for (const EdgeGroup& g : p.groups) {
     double dre = 1, dim = 0, ore = 1, oim = 0;
+    int64_t x = 0;   // the clause entries are (dre, dim, ore, oim) * 2^x
     if (p.std_weights) {
       int32_t ss = 0;
       for (int32_t c : g.members) ss += p.knot.edges[c][2];
       clause_diag(p.q, (int32_t)g.members.size(), ss, dre, dim);
     } else {
+      // entrywise product of the members' matrices, renormalised by exact powers of two
+      // after every factor so that no partial product overflows or underflows
       for (int32_t c : g.members) {
         const auto& w = p.weights[c];
         const double a = dre * w[0] - dim * w[1], b = dre * w[1] + dim * w[0];
         const double c2 = ore * w[2] - oim * w[3], d = ore * w[3] + oim * w[2];
-        dre = a;
-        dim = b;
-        ore = c2;
-        oim = d;
+        const int32_t e = max_exp4(a, b, c2, d);
+        dre = std::ldexp(a, -e);
+        dim = std::ldexp(b, -e);
+        ore = std::ldexp(c2, -e);
+        oim = std::ldexp(d, -e);
+        x += e;
       }
     }
     Slot& sl = p.slots[g.slot];
@@ -1485,6 +1502,25 @@ void apply_weights(Plan& p) {
     sl.dim = dim;
     sl.ore = ore;
     sl.oim = oim;
+    p.slot_exp[g.slot] = (int32_t)std::max<int64_t>(INT32_MIN / 2, std::min<int64_t>(INT32_MAX / 2, x));
+  }
+  // each initial tensor's entries carry the powers of two of its absorbed slots
+  auto set_exp = [&](std::vector<Recipe>& recs) {
+    for (Recipe& r : recs) {
+      int64_t x = 0;
+      for (int32_t j = r.slot0; j < r.slot0 + r.nslot; ++j)
+        if (p.slots[j].absorbed) x += p.slot_exp[j];
+      r.exp2 = (int32_t)std::max<int64_t>(INT32_MIN / 2, std::min<int64_t>(INT32_MAX / 2, x));
+    }
+  };
+  set_exp(p.recipes);
+  if (!p.recipes.empty())
+    std::memcpy(p.program.data() + p.off_recipe, p.recipes.data(), sizeof(Recipe) * p.recipes.size());
+  if (p.grad.built) {
+    set_exp(p.grad.recipes);
+    if (!p.grad.recipes.empty())
+      std::memcpy(p.grad.program.data() + p.grad.off_recipe, p.grad.recipes.data(),
+                  sizeof(Recipe) * p.grad.recipes.size());
   }
   if (!p.slots.empty()) {
     std::memcpy(p.program.data() + p.off_slots, p.slots.data(), sizeof(Slot) * p.slots.size());

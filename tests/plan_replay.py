@@ -14,7 +14,7 @@ MAXRUNS = 20
 class Recipe(C.Structure):
     _fields_ = [("kind", C.c_int32), ("rank", C.c_int32), ("slot0", C.c_int32),
                 ("nslot", C.c_int32), ("elems", C.c_int64), ("offset", C.c_int64),
-                ("meta", C.c_int32)]
+                ("meta", C.c_int32), ("exp2", C.c_int32)]
 
 
 class Slot(C.Structure):
@@ -209,7 +209,7 @@ def _build(recs, slots, q, sdig, arena, mx, ex):
                 val += prod
         arena[r.offset:r.offset + r.elems] = val
         mx[r.meta] = float(np.max(np.maximum(np.abs(val.real), np.abs(val.imag))))
-        ex[r.meta] = 0
+        ex[r.meta] = r.exp2
 
 
 def replay_grad(plan):

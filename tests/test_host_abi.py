@@ -204,11 +204,15 @@ def test_decode_result_status_word(ctx):
         want = SC.of(complex(0.75, -0.25), 40) * SC.of(complex(fre, fim), int(fexp))
         assert rel_err(SC.of(z.mantissa, z.exp2), want) < 1e-15
         assert v == k.jones_from_z(q, z)
-        for word in (1, 2, 1 << 40):
-            st, z2, _ = pk.decode_result(p, 0.75, -0.25, 40, word)
-            assert st == 6          # PK_ETIMEOUT: the value is not to be used
+        st, z2, _ = pk.decode_result(p, 0.75, -0.25, 40, 1)
+        assert st == 6              # PK_ETIMEOUT (bit 0): the value is not to be used
+        for sl, step in ((0, -1), (0, 0), (3, 17), (1 << 30, 5000)):
+            code = ((sl + 1) << 24 | (step + 2)) << 1      # the finite check's code
+            for word in (code, code | 1):
+                st, z2, _ = pk.decode_result(p, 0.75, -0.25, 40, word)
+                assert st == 9      # PK_ENONFINITE takes precedence over an expired wait
     # the record layout the device writes: 32 bytes, status in the last 8
-    assert pk.STATUS[6] == "PK_ETIMEOUT"
+    assert pk.STATUS[6] == "PK_ETIMEOUT" and pk.STATUS[9] == "PK_ENONFINITE"
 
 
 def test_tuning_table_and_ranges(ctx):
