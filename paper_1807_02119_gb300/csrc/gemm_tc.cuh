@@ -24,13 +24,14 @@
 // columns is one M=128, N=48 MMA per BF16 K-step of 16.
 //
 // Data movement, three kernels per step:
-//  * k_digits<S>: one CTA per (128-row block of A or 24-column block of B, flush group of
-//    kFlush chunks of K) finds the block's exponents over the group, then converts it chunk
-//    by chunk (16 complex k) into S digit slices laid out exactly as the MMA reads them from
-//    shared memory (the canonical K-major layout without swizzle: 8-row x 16-byte core
-//    matrices) and stores each chunk contiguously in the workspace.  The operands are
-//    gathered through the step's stride runs (arbitrary index permutations, which a TMA
-//    tensor map cannot express); each element is read and converted once.
+//  * k_digits<S>: one CTA per (32-row part of a 128-row block of A, or 24-column block of
+//    B; flush group of kFlush chunks of K) gathers the block into shared memory, finds its
+//    rows' exponents over the group, then converts it into S digit slices per chunk (16
+//    complex k) laid out exactly as the MMA reads them from shared memory (the canonical
+//    K-major layout without swizzle: 8-row x 16-byte core matrices) and stores each chunk
+//    contiguously in the workspace.  The operands are gathered through the step's stride
+//    runs (arbitrary index permutations, which a TMA tensor map cannot express); each
+//    element is read from memory once.
 //  * k_gemm_tc: warp 0 streams the chunks of its (batch, row block, column block) into a
 //    2-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion by
 //    mbarrier transaction count); warp 1 issues the S (S+1)/2 digit-pair products of a K
@@ -70,7 +71,8 @@ struct Cfg {
   static constexpr int kBChunk = S * kBBytes;
   static constexpr int kStage = kAChunk + kBChunk;
   static constexpr int kSmem = kStages * kStage;   // two CTAs per SM (16-byte alignment suffices)
-  static constexpr int kConvSmem = 0;   // the digit kernels use static shared memory only
+  // the digit kernel's staging tile: 32 rows x (flush group + 1) complex entries
+  static constexpr int kConvSmem = 32 * (tc_flush(S) * kKc + 1) * 16;
   // one MMA spans the stacked B digits: M = 128 allows N in multiples of 16 up to 256
   static_assert(kN % 16 == 0 && S * kN <= 256, "stacked B digits exceed one MMA");
   static_assert(kAChunk == tc_a_chunk(S) && kBChunk == tc_b_chunk(S),
@@ -194,27 +196,6 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k, int kcores) {
   return (uint32_t)((row >> 3) * kcores * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// S digits of the float-float value (h + l) 2^-e (|value| <= 1): d_i = nearest integer of
-// the running remainder times 2^(7+8i); the remainder is carried exactly as a float pair.
-// sc1 sc2 = 2^(7 - e), the row's scale as two exact powers of two (so that any exponent
-// the stored values can have is covered).  The remainder r = yh - d_i is exact and a
-// multiple of ulp(yh), while |yl| <= ulp(yh) / 2, so |r| >= |yl| unless r = 0 and the fast
-// two-sum (Dekker) is exact; it keeps (yh, yl) normalised for the next digit.
-template <int S>
-__device__ __forceinline__ void digits(float h, float l, float sc1, float sc2, __nv_bfloat16* d) {
-  float yh = (h * sc1) * sc2, yl = (l * sc1) * sc2;
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    const float di = rintf(yh);
-    d[i] = __float2bfloat16_rn(di);
-    const float r = __fsub_rn(yh, di);
-    const float sum = __fadd_rn(r, yl);
-    const float err = __fsub_rn(yl, __fsub_rn(sum, r));
-    yh = sum * 256.0f;
-    yl = err * 256.0f;
-  }
-}
-
 // 2^x as a product of two exact floats (each exponent within [-126, 127]).
 __device__ __forceinline__ void pow2_pair(int x, float& f1, float& f2) {
   const int x1 = x / 2, x2 = x - x1;
@@ -250,76 +231,86 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       : "memory");
 }
 
-// Four BF16 digits as one 8-byte group (k order within a core-matrix row).
-__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c,
-                                       __nv_bfloat16 d) {
-  uint2 u;
-  u.x = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-  u.y = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
-  return u;
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned), cached in
+// L2 only; completed by cp_async_wait.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Digit conversion of one item of an operand block: tile row r (a complex row of A, or a
-// complex column of B) x 4 consecutive complex k, written straight into the chunk's digit
-// slices as 8-byte groups of four BF16 digits.  A row r is [Re | Im] along K'; a B column
-// fills real rows 2r ([Re | -Im]) and 2r+1 ([Im | Re]).  `kl` is the item's first k within
-// its chunk (a multiple of 4).
-template <int S, bool IS_A>
-__device__ __forceinline__ void convert_item(const Cx<ff>* v, int r, int kl, float sc1, float sc2,
-                                             unsigned char* chunk) {
-  constexpr int kSlice = IS_A ? kABytes : kBBytes;
-  __nv_bfloat16 dr[4][S], di[4][S];
+// The S digit slices of one real component of 8 consecutive k of one tile row: x[u] =
+// (hi, lo) of k = 8 o + u, scaled by sc1 sc2 = 2^(7 - e) (the row's scale as two exact
+// powers of two, so that any exponent the stored values can have is covered), giving
+// float-float values y = (yh + yl) with |y| <= 2^7.  Digit i is the nearest integer d_i of
+// the running remainder times 2^(8i); the remainder r = yh - d_i is exact and a multiple
+// of ulp(yh), while |yl| <= ulp(yh) / 2, so |r| >= |yl| unless r = 0 and the fast two-sum
+// (Dekker) that renormalises (r + yl) is exact.  Digit i of the 8 values, as 8 BF16 packed
+// into 16 bytes (one core-matrix row), goes to out + i * slice and, when out2 is given,
+// also to out2 + i * slice, negated if `neg2`.
+template <int S>
+__device__ __forceinline__ void digit_rows8(const float* xh, const float* xl, float sc1, float sc2,
+                                            unsigned char* out, unsigned char* out2, bool neg2,
+                                            int slice) {
+  float yh[8], yl[8];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    digits<S>(v[u].re.hi, v[u].re.lo, sc1, sc2, dr[u]);
-    digits<S>(v[u].im.hi, v[u].im.lo, sc1, sc2, di[u]);
+  for (int u = 0; u < 8; ++u) {
+    yh[u] = (xh[u] * sc1) * sc2;
+    yl[u] = (xl[u] * sc1) * sc2;
   }
+  const uint32_t flip = neg2 ? 0x80008000u : 0u;   // negate the BF16 digits (exact)
 #pragma unroll
   for (int i = 0; i < S; ++i) {
-    unsigned char* sl = chunk + i * kSlice;
-    const uint2 re = pack4(dr[0][i], dr[1][i], dr[2][i], dr[3][i]);
-    const uint2 im = pack4(di[0][i], di[1][i], di[2][i], di[3][i]);
-    if (IS_A) {
-      *(uint2*)(sl + tile_off(r, kl, kKcores)) = re;
-      *(uint2*)(sl + tile_off(r, kKc + kl, kKcores)) = im;
-    } else {
-      const uint2 mim = pack4(__hneg(di[0][i]), __hneg(di[1][i]), __hneg(di[2][i]), __hneg(di[3][i]));
-      *(uint2*)(sl + tile_off(2 * r, kl, kKcores)) = re;
-      *(uint2*)(sl + tile_off(2 * r, kKc + kl, kKcores)) = mim;
-      *(uint2*)(sl + tile_off(2 * r + 1, kl, kKcores)) = im;
-      *(uint2*)(sl + tile_off(2 * r + 1, kKc + kl, kKcores)) = re;
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float di = rintf(yh[u]);
+      const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(di));
+      if (u & 1)
+        w[u >> 1] |= b << 16;
+      else
+        w[u >> 1] = b;
+      const float r = __fsub_rn(yh[u], di);
+      const float sum = __fadd_rn(r, yl[u]);
+      const float err = __fsub_rn(yl[u], __fsub_rn(sum, r));
+      yh[u] = sum * 256.0f;
+      yl[u] = err * 256.0f;
     }
+    *(uint4*)(out + i * slice) = make_uint4(w[0], w[1], w[2], w[3]);
+    if (out2)
+      *(uint4*)(out2 + i * slice) = make_uint4(w[0] ^ flip, w[1] ^ flip, w[2] ^ flip, w[3] ^ flip);
   }
 }
 
 }  // namespace tc
 
-// Digits of one block of the A operand (IS_A: 64 of a tile's 128 rows) or the B operand
-// (24 columns) of a GEMM step over one flush group of K (kFlush chunks of 16 complex k):
-// the exponent of each row over the group's k, then the S digit slices of the group's
-// chunks, stored directly in the workspace.  The block is read twice; the second read hits
-// L2 (a block is at most 64 x 112 complex k in flight per CTA).  The thread mapping follows
-// the operand's unit stride: along K (consecutive lanes read consecutive k of one row) or
-// along the rows (a warp reads 32 consecutive rows).
+// Digits of one block of the A operand (IS_A: 32 of a tile's 128 rows) or the B operand
+// (24 columns) of a GEMM step over one flush group of K (kFlush chunks of 16 complex k).
+// The block's entries are gathered once into shared memory (16-byte asynchronous copies;
+// consecutive threads follow the operand's unit stride: along K, or along the rows), then
+// each row's exponent over the group is taken from there, and the S digit slices of the
+// group's chunks are written in whole 16-byte core-matrix rows, consecutive threads taking
+// consecutive tile rows (full 32-byte sectors).  Row stride in shared memory kG + 1
+// entries: rows 16 bytes apart modulo 128 keep the conversion's reads free of conflicts.
 template <int S, bool IS_A>
 __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena, unsigned char* scratch,
                                              long long blk, long long* ro, long long* kt,
-                                             long long& base, int* ex, float* red) {
+                                             long long& base, int* ex, float4* tile) {
   using namespace tc;
-  constexpr int kHalves = IS_A ? 2 : 1;           // CTAs per tile block
-  constexpr int kRows = IS_A ? kMc / 2 : kNc;     // rows this CTA converts
-  constexpr int kRowsPad = 64;                    // rows of the exponent pass's thread grid
-  constexpr int kPer = kConvThreads / kRowsPad;   // threads per row in the exponent pass
+  constexpr int kParts = IS_A ? kMc / 32 : 1;     // CTAs per tile block
+  constexpr int kRows = IS_A ? 32 : kNc;          // rows this CTA converts
   constexpr int kG = Cfg<S>::kFlush * kKc;        // complex k of one flush group
-  static_assert(kRows <= kRowsPad && kConvThreads % kRowsPad == 0 && kG <= kConvThreads,
-                "block geometry");
+  constexpr int kLd = kG + 1;                     // shared-memory row stride (entries)
+  constexpr int kPer = kConvThreads / 32;         // threads per row in the exponent pass
+  static_assert(kRows <= 32 && kG <= kConvThreads && kG % 8 == 0, "block geometry");
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
   const long long tiles = IS_A ? L.tiles_m : L.tiles_n;
-  const int half = (int)(blk % kHalves);
-  blk /= kHalves;
+  const int part = (int)(blk % kParts);
+  blk /= kParts;
   const long long g = blk % L.groups, t = blk / L.groups;
-  const long long tile = t % tiles, bb = t / tiles;
-  const int r0 = half * kRows;                    // first tile row of this CTA
+  const long long tile_i = t % tiles, bb = t / tiles;
+  const int r0 = part * kRows;                    // first tile row of this CTA
   const int tid = threadIdx.x;
   const bool kin = IS_A ? s.a_kinner != 0 : s.b_kinner != 0;
   const long long k0 = g * kG;
@@ -330,10 +321,10 @@ __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena,
     runs4(bb, s.gb, s.ngb, a, b, c);
     base = IS_A ? a : b;
   }
-  if (tid < kRowsPad) {
-    const long long r = tile * (IS_A ? kMc : kNc) + r0 + tid;
+  if (tid < kRows) {
+    const long long r = tile_i * (IS_A ? kMc : kNc) + r0 + tid;
     long long a, b, c;
-    if (tid < kRows && r < (IS_A ? s.M : s.N)) {
+    if (r < (IS_A ? s.M : s.N)) {
       if (IS_A)
         runs4(r, s.gm, s.ngm, a, b, c);
       else
@@ -352,63 +343,88 @@ __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena,
   __syncthreads();
   const Cx<ff>* src = arena + (IS_A ? s.off_a : s.off_b) + base;
 
-  // ---- exponents over the group: kPer threads per row
-  const int er = kin ? (tid / kPer) : (tid % kRowsPad), es = kin ? (tid % kPer) : (tid / kRowsPad);
-  float mx = 0.f;
-  if (er < kRows && ro[er] >= 0) {
-    const long long o = ro[er];
-#pragma unroll 8
-    for (int k = es; k < kgn; k += kPer)
-      if (kt[k] >= 0) mx = fmaxf(mx, mag(ld(src + o + kt[k])));
+  // ---- gather the block: entry (r, k) -> tile[r * kLd + k]; missing entries are 0
+  for (int idx = tid; idx < kRows * kgn; idx += kConvThreads) {
+    const int r = kin ? idx / kgn : idx % kRows;
+    const int k = kin ? idx % kgn : idx / kRows;
+    float4* d = tile + r * kLd + k;
+    if (ro[r] >= 0 && kt[k] >= 0)
+      cp_async16(smem_u32(d), src + ro[r] + kt[k]);
+    else
+      *d = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  red[tid] = mx;
+  cp_async_wait();
   __syncthreads();
-  if (tid < kRows) {
-    float v = 0.f;
+
+  // ---- exponents over the group: kPer consecutive threads per row
+  {
+    const int r = tid / kPer, j = tid % kPer;
+    float mx = 0.f;
+    if (r < kRows)
+      for (int k = j; k < kgn; k += kPer) {
+        const float4 v = tile[r * kLd + k];
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
+      }
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) v = fmaxf(v, red[kin ? kPer * tid + j : tid + kRowsPad * j]);
-    ex[tid] = bin_exp(v);
-    ((int*)(scratch + (IS_A ? L.ea_off : L.eb_off)))[((bb * tiles + tile) * L.groups + g) *
-                                                         (IS_A ? kMc : kNc) + r0 + tid] = ex[tid];
+    for (int o = kPer / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (r < kRows && j == 0) {
+      ex[r] = bin_exp(mx);
+      ((int*)(scratch + (IS_A ? L.ea_off : L.eb_off)))[((bb * tiles + tile_i) * L.groups + g) *
+                                                           (IS_A ? kMc : kNc) + r0 + r] = ex[r];
+    }
   }
   __syncthreads();
 
-  // ---- digits: items (row, 4 consecutive k) of the group
+  // ---- digits: items (row, 8 consecutive k), consecutive threads on consecutive rows
   constexpr int kChunkBytes = IS_A ? Cfg<S>::kAChunk : Cfg<S>::kBChunk;
+  constexpr int kSlice = IS_A ? kABytes : kBBytes;
   unsigned char* dst0 = scratch + (IS_A ? L.a_off : L.b_off) +
-                        (bb * tiles + tile) * L.chunks * (long long)kChunkBytes;
-  const int quads = kgn / 4;
-  for (int idx = tid; idx < kRows * quads; idx += kConvThreads) {
-    const int r = kin ? idx / quads : idx % kRows;
-    const int q = kin ? idx % quads : idx / kRows;
-    Cx<ff> v[4];
-    const long long o = ro[r];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      v[u] = Cx<ff>{{0.f, 0.f}, {0.f, 0.f}};
-      if (o >= 0 && kt[4 * q + u] >= 0) v[u] = ld(src + o + kt[4 * q + u]);
-    }
+                        (bb * tiles + tile_i) * L.chunks * (long long)kChunkBytes;
+  const int octs = kgn / 8;
+  for (int idx = tid; idx < kRows * octs; idx += kConvThreads) {
+    const int r = idx % kRows, o = idx / kRows;
     float sc1, sc2;
     digit_scale(ex[r], sc1, sc2);
-    const long long k = k0 + 4 * q;
-    convert_item<S, IS_A>(v, r0 + r, (int)(k % kKc), sc1, sc2, dst0 + (k / kKc) * (long long)kChunkBytes);
+    const long long k = k0 + 8 * o;
+    const int kl = (int)(k % kKc);   // 0 or 8
+    unsigned char* ch = dst0 + (k / kKc) * (long long)kChunkBytes;
+    const float4* row = tile + r * kLd + 8 * o;
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {   // the real, then the imaginary components
+      float xh[8], xl[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 v = row[u];
+        xh[u] = part ? v.z : v.x;
+        xl[u] = part ? v.w : v.y;
+      }
+      if (IS_A)   // row [Re | Im]
+        digit_rows8<S>(xh, xl, sc1, sc2, ch + tile_off(r0 + r, part * kKc + kl, kKcores), nullptr,
+                       false, kSlice);
+      else if (part == 0)   // Re: row 2r first half, row 2r + 1 second half
+        digit_rows8<S>(xh, xl, sc1, sc2, ch + tile_off(2 * r, kl, kKcores),
+                       ch + tile_off(2 * r + 1, kKc + kl, kKcores), false, kSlice);
+      else                  // Im: row 2r + 1 first half, -Im: row 2r second half
+        digit_rows8<S>(xh, xl, sc1, sc2, ch + tile_off(2 * r + 1, kl, kKcores),
+                       ch + tile_off(2 * r, kKc + kl, kKcores), true, kSlice);
+    }
   }
 }
 
-// Digits of both operands of a GEMM step in one launch: blocks [0, nA) convert A (two per
-// batch index, 128-row block and flush group), the rest convert B.
+// Digits of both operands of a GEMM step in one launch: blocks [0, nA) convert A (four
+// per batch index, 128-row block and flush group), the rest convert B.
 template <int S>
-__global__ void __launch_bounds__(tc::kConvThreads) k_digits(const Step s, const Cx<ff>* arena,
+__global__ void __launch_bounds__(tc::kConvThreads, 4) k_digits(const Step s, const Cx<ff>* arena,
                                                              unsigned char* scratch, long long nA) {
-  __shared__ long long ro[64], kt[tc::kConvThreads];
+  __shared__ long long ro[32], kt[tc::kConvThreads];
   __shared__ long long base;
-  __shared__ int ex[64];
-  __shared__ float red[tc::kConvThreads];
+  __shared__ int ex[32];
+  extern __shared__ float4 tile[];
   const long long blk = blockIdx.x;
   if (blk < nA)
-    digits_block<S, true>(s, arena, scratch, blk, ro, kt, base, ex, red);
+    digits_block<S, true>(s, arena, scratch, blk, ro, kt, base, ex, tile);
   else
-    digits_block<S, false>(s, arena, scratch, blk - nA, ro, kt, base, ex, red);
+    digits_block<S, false>(s, arena, scratch, blk - nA, ro, kt, base, ex, tile);
 }
 
 // C tile (128 complex rows x 24 complex columns of one batch index) from the digit

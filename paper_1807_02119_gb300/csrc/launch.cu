@@ -221,7 +221,8 @@ cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* t
                       unsigned long long* err, cudaStream_t stream, Marker& mk, double cm, double by) {
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
   // class 6 (digit conversion): its bytes are the operands it reads, |A| + |B|
-  const long long nA = 2 * s.Bsz * L.tiles_m * L.groups, nB = s.Bsz * L.tiles_n * L.groups;
+  const long long nA = (tc::kMc / 32) * s.Bsz * L.tiles_m * L.groups,
+                  nB = s.Bsz * L.tiles_n * L.groups;
   mk.begin(6, 0.0, (double)sizeof(Cx<ff>) * (double)(s.R * s.K + s.Bsz * s.K * s.N),
            gpu_fill(nA + nB, 8));
   k_digits<S><<<(unsigned)(nA + nB), tc::kConvThreads, tc::Cfg<S>::kConvSmem, stream>>>(s, arena, tcs, nA);
