@@ -158,6 +158,10 @@ typedef struct {
   int64_t tc_min_k;          /* PK_SPLIT: row steps of GEMM shape (M >= 64, N >= 32) with this
                                 contracted extent or more run on the tensor cores too (4..16;
                                 16: only the GEMM steps, which need K >= 16 anyway)           */
+  int64_t tc_db_groups;      /* PK_SPLIT: tensor-core steps with at least this many flush
+                                groups of K (96 complex k each) run one CTA per SM with two
+                                accumulator sets, so a group's flush overlaps the next group's
+                                products; shorter steps run two CTAs per SM (0: never; 1..4096) */
 } pk_tuning;
 
 pk_status pk_tuning_default(pk_tuning* out);

@@ -10,7 +10,9 @@ before every timed launch, the fastest median kept:
   largest step, in outputs and in complex multiply-adds, that joins a run, on the 64-knot
   scale workload (q = 2, 3, 5; 192 plans replayed as one concurrent graph, split);
 * the smallest contracted extent from which row steps of GEMM shape also run on the
-  tensor cores (split), on the same workload.
+  tensor cores (split), on the same workload;
+* the number of flush groups from which a tensor-core step runs one CTA per SM with two
+  accumulator sets instead of two CTAs per SM with one, on the same workload.
 
 Every candidate's results are checked against the first candidate's (same plans, same
 precision) before its time counts.  The winners are written to csrc/tuned_table.h (the
@@ -18,6 +20,8 @@ defaults the library is compiled with) together with every measured time, and a 
 the table goes to the output directory given by --out.
 
 Usage (on a GPU): python -m paper_1807_02119_gb300.autotune [--out DIR] [--quick]
+[--only tc_min_k,tc_db_groups] (--only: sweep just those scale-workload parameters, the
+others keep the compiled-in table's values)
 """
 from __future__ import annotations
 
@@ -36,6 +40,8 @@ BATCH_KTAB = (512, 1024, 2048)
 SEQ_OUTS = (1024, 2048, 4096, 8192)
 SEQ_WORK = (1 << 12, 1 << 14, 1 << 16)
 TC_MIN_K = (4, 8, 16)
+TC_DB_GROUPS = (0, 2, 3, 4, 6)
+SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_db_groups": TC_DB_GROUPS}
 
 
 def _rel(a, b):
@@ -130,9 +136,9 @@ def sweep_seq(pk, ctx, stream, flush, reps, log, quick):
     return best, rows
 
 
-def sweep_tc_min_k(pk, ctx, stream, flush, reps, log):
-    """The smallest K of the row steps of GEMM shape that go to the tensor cores (split),
-    on the scale workload with the chosen sequence thresholds."""
+def sweep_scale_param(pk, ctx, stream, flush, reps, log, name):
+    """One pk_tuning field over its candidates (SCALE_PARAMS) on the scale workload (split,
+    192 plans replayed as one concurrent graph), the other fields as the context has them."""
     import torch
     from concurrent.futures import ThreadPoolExecutor
     import knotgen as kg
@@ -140,8 +146,8 @@ def sweep_tc_min_k(pk, ctx, stream, flush, reps, log):
     kn = [pk.Knot.from_pd(ctx, k.pd, outer=k.outer) for k in knots]
     jobs = [(k, q) for k in kn for q in (2, 3, 5)]
     rows, ref, best = [], None, None
-    for tk in TC_MIN_K:
-        ctx.set_tuning(tc_min_k=tk)
+    for tk in SCALE_PARAMS[name]:
+        ctx.set_tuning(**{**ctx.tuning(), name: tk})
         with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
             plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=128), jobs))
         ws = [torch.empty(p.workspace_bytes("split") + 256, dtype=torch.uint8, device="cuda")
@@ -155,7 +161,7 @@ def sweep_tc_min_k(pk, ctx, stream, flush, reps, log):
             ref = z
         ok = max(_rel(x, y) for x, y in zip(z, ref)) <= 1e-6
         rows.append((tk, ms, ok))
-        log(f"tensor cores for row steps from K={tk}: {ms:.2f} ms per step{'' if ok else ' RESULTS DIFFER'}")
+        log(f"{name} = {tk}: {ms:.2f} ms per step{'' if ok else ' RESULTS DIFFER'}")
         if ok and (best is None or ms < best[1]):
             best = (tk, ms)
         del g, ws, plans
@@ -163,7 +169,13 @@ def sweep_tc_min_k(pk, ctx, stream, flush, reps, log):
     return best, rows
 
 
-def write_table(path, tune, batch_rows, seq_rows, gpu, tc_rows=()):
+PARAM_TITLES = {
+    "tc_min_k": "Tensor cores for row steps of GEMM shape from this K",
+    "tc_db_groups": "One CTA per SM, two accumulator sets, from this many flush groups (0: never)",
+}
+
+
+def write_table(path, tune, batch_rows, seq_rows, gpu, param_rows):
     when = datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%d %H:%M UTC")
     lines = ["// Executor launch shapes, written by paper_1807_02119_gb300/autotune.py from",
              f"// measurements on {gpu} ({when}); the library's defaults (pk_tuning_default).",
@@ -174,14 +186,15 @@ def write_table(path, tune, batch_rows, seq_rows, gpu, tc_rows=()):
     for so, sw, ms, ok, nl in seq_rows:
         lines.append(f"//   outs <= {so:5d}  work <= {sw:6d}  {ms:8.2f}  ({nl} launches)"
                      f"{'' if ok else '  (results differ)'}")
-    if tc_rows:
-        lines.append("// Tensor cores for row steps of GEMM shape from this K, split (median ms per step):")
-        for tk, ms, ok in tc_rows:
-            lines.append(f"//   K >= {tk:2d}  {ms:8.2f}{'' if ok else '  (results differ)'}")
+    for name, prow in param_rows.items():
+        lines.append(f"// {PARAM_TITLES[name]}, split (median ms per step):")
+        for tk, ms, ok in prow:
+            lines.append(f"//   {name} = {tk:4d}  {ms:8.2f}{'' if ok else '  (results differ)'}")
     lines += ["#pragma once", '#include "pk.h"', "",
               "constexpr pk_tuning kTunedDefault = {" +
               f"{tune['batch_threads']}, {tune['batch_ktab']}, {tune['seq_outs']}, "
-              f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}" + "};", ""]
+              f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}, {tune['tc_db_groups']}" +
+              "};", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))
 
@@ -191,6 +204,8 @@ def main():
     ap.add_argument("--out", default=None, help="also copy the table here")
     ap.add_argument("--reps", type=int, default=7)
     ap.add_argument("--quick", action="store_true", help="a smaller sequence-run sweep")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated scale-workload parameters to sweep alone")
     args = ap.parse_args()
     sys.path.insert(0, ROOT)
     import torch
@@ -206,17 +221,32 @@ def main():
     ctx.set_stream(stream.cuda_stream)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     tune = pk.default_tuning()
+    gpu = torch.cuda.get_device_name(0)
+    prows = {}
+    if args.only:   # some scale parameters alone: the table is only written to --out
+        ctx.set_tuning()
+        for name in args.only.split(","):
+            (best, _), prows[name] = sweep_scale_param(pk, ctx, stream, flush, args.reps, log, name)
+            tune[name] = best
+            ctx.set_tuning(**tune)
+        if args.out:
+            os.makedirs(args.out, exist_ok=True)
+            write_table(os.path.join(args.out, "tuned_table.h"), tune, [], [], gpu, prows)
+        log(f"chosen: {tune}")
+        return
     (bt, bk, _), brows = sweep_batch(pk, ctx, stream, flush, args.reps, log)
     ctx.set_tuning()
     (so, sw, _), srows = sweep_seq(pk, ctx, stream, flush, args.reps, log, args.quick)
-    ctx.set_tuning(seq_outs=so, seq_work=sw)
-    (tk, _), trows = sweep_tc_min_k(pk, ctx, stream, flush, args.reps, log)
-    tune.update(batch_threads=bt, batch_ktab=bk, seq_outs=so, seq_work=sw, tc_min_k=tk)
-    gpu = torch.cuda.get_device_name(0)
-    write_table(TABLE, tune, brows, srows, gpu, trows)
+    tune.update(batch_threads=bt, batch_ktab=bk, seq_outs=so, seq_work=sw)
+    ctx.set_tuning(**tune)
+    for name in SCALE_PARAMS:
+        (best, _), prows[name] = sweep_scale_param(pk, ctx, stream, flush, args.reps, log, name)
+        tune[name] = best
+        ctx.set_tuning(**tune)
+    write_table(TABLE, tune, brows, srows, gpu, prows)
     if args.out:
         os.makedirs(args.out, exist_ok=True)
-        write_table(os.path.join(args.out, "tuned_table.h"), tune, brows, srows, gpu, trows)
+        write_table(os.path.join(args.out, "tuned_table.h"), tune, brows, srows, gpu, prows)
     log(f"chosen: {tune}")
 
 

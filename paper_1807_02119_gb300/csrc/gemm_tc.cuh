@@ -60,7 +60,8 @@ constexpr int kKr = 2 * kKc;     // MMA K per chunk (real: re half, im half)
 constexpr int kKcores = kKr / 8; // 16-byte K core columns per row
 constexpr int kABytes = kM * kKr * 2;   // one digit slice of an A chunk (BF16): 8 KB
 constexpr int kBBytes = kN * kKr * 2;   // one digit slice of a B chunk: 3 KB
-constexpr int kStages = 2;
+constexpr int kStages = 2;     // stage ring, two CTAs per SM
+constexpr int kStagesDB = 4;   // stage ring of the double-buffered variant (one CTA per SM)
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);   // producer, MMA issuer, epilogue
 constexpr int kConvThreads = 256;
@@ -71,6 +72,8 @@ struct Cfg {
   static constexpr int kBChunk = S * kBBytes;
   static constexpr int kStage = kAChunk + kBChunk;
   static constexpr int kSmem = kStages * kStage;   // two CTAs per SM (16-byte alignment suffices)
+  static constexpr int kSmemDB = kStagesDB * kStage;   // the double-buffered variant: one CTA per SM
+  static_assert(kSmemDB <= 220 * 1024, "stage ring of the double-buffered variant");
   // the digit kernel's staging tile: 32 rows x (flush group + 1) complex entries
   static constexpr int kConvSmem = 32 * (tc_flush(S) * kKc + 1) * 16;
   // one MMA spans the stacked B digits: M = 128 allows N in multiples of 16 up to 256
@@ -177,6 +180,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// Two loads of 8 columns each, one wait.
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float* a, float* b) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[8 + i]);
+  }
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
@@ -430,17 +450,27 @@ __global__ void __launch_bounds__(tc::kConvThreads, 4) k_digits(const Step s, co
 // C tile (128 complex rows x 24 complex columns of one batch index) from the digit
 // chunks: warp 0 streams chunks into the stage ring, warp 1 issues the MMAs, warps 2..9
 // flush the level accumulators and store C.
-template <int S>
-__global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff>* arena, Meta* meta,
-                                                             const unsigned char* scratch,
-                                                             unsigned long long* err) {
+// DB = false: two CTAs per SM, a 2-stage ring and one set of level accumulators, so the
+// MMAs of a CTA wait while its epilogue flushes a group (the other CTA's MMAs fill in).
+// DB = true: one CTA per SM, a 4-stage ring and two accumulator sets in TMEM (columns 0
+// and 256), used by alternate flush groups, so the flush of group g overlaps the MMAs of
+// group g + 1 (for steps with several flush groups).
+template <int S, bool DB>
+__global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step s, Cx<ff>* arena,
+                                                                      Meta* meta,
+                                                                      const unsigned char* scratch,
+                                                                      unsigned long long* err) {
   using namespace tc;
+  constexpr int kSt = DB ? kStagesDB : kStages;     // stages of the ring
+  constexpr int kSets = DB ? 2 : 1;                 // accumulator sets
+  constexpr uint32_t kCols = DB ? 512u : (uint32_t)Cfg<S>::kCols;
+  static_assert(!DB || S * kN <= 256, "two accumulator sets must fit 512 TMEM columns");
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ long long cm[kMc], cn[kNc];
   __shared__ long long cbase;
   __shared__ int eb_s[kEpiWarps][kNc / 2];   // per epilogue warp: its columns' group exponents
-  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full, acc_empty,
-      drain;
+  __shared__ __align__(8) unsigned long long full[kSt], empty[kSt], acc_full[kSets],
+      acc_empty[kSets], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int bad;
   unsigned char* sm = dsm;
@@ -457,12 +487,14 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
     long long a, b;
     runs4(bb, s.gb, s.ngb, a, b, cbase);
     bad = 0;
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < kSt; ++i) {
       mbar_init(smem_u32(&full[i]), 1);
       mbar_init(smem_u32(&empty[i]), 1);
     }
-    mbar_init(smem_u32(&acc_full), 1);
-    mbar_init(smem_u32(&acc_empty), kEpiWarps);
+    for (int i = 0; i < kSets; ++i) {
+      mbar_init(smem_u32(&acc_full[i]), 1);
+      mbar_init(smem_u32(&acc_empty[i]), kEpiWarps);
+    }
     mbar_init(smem_u32(&drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -486,7 +518,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(Cfg<S>::kCols)
+                 "r"(kCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -513,9 +545,9 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
       const unsigned char* bsrc =
           scratch + L.b_off + (bb * L.tiles_n + tn) * nchunks * (long long)Cfg<S>::kBChunk;
       for (long long c = 0; c < nchunks; ++c) {
-        const int st = (int)(c % kStages);
-        if (c >= kStages &&
-            !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c / kStages) - 1) & 1), err)) {
+        const int st = (int)(c % kSt);
+        if (c >= kSt &&
+            !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c / kSt) - 1) & 1), err)) {
           bad = 1;
           atomicOr(err, 1ull);
           break;
@@ -531,12 +563,16 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       for (long long c = 0; c < nchunks; ++c) {
-        const int st = (int)(c % kStages);
+        const int st = (int)(c % kSt);
         const long long g = c / Cfg<S>::kFlush;
+        const int set = (int)(g % kSets);
+        const long long use = g / kSets;   // earlier groups on this accumulator set
         const bool first = c % Cfg<S>::kFlush == 0;
         const bool last = (c + 1) % Cfg<S>::kFlush == 0 || c + 1 == nchunks;
-        if ((first && g > 0 && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((g - 1) & 1), err)) ||
-            !mbar_wait(smem_u32(&full[st]), (uint32_t)((c / kStages) & 1), err)) {
+        // before a set is reused, its previous group must have been flushed
+        if ((first && use > 0 &&
+             !mbar_wait(smem_u32(&acc_empty[set]), (uint32_t)((use - 1) & 1), err)) ||
+            !mbar_wait(smem_u32(&full[st]), (uint32_t)((c / kSt) & 1), err)) {
           bad = 1;
           atomicOr(err, 1ull);
           break;
@@ -545,6 +581,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
         // descriptors of the stage's first A and B slices; a slice or K-step offset is
         // added to the start-address field (shared addresses < 256 KB: no carry out of it)
         const uint32_t a0 = sm0 + st * Cfg<S>::kStage, b0 = a0 + Cfg<S>::kAChunk;
+        const uint32_t tacc = tmem + (uint32_t)set * 256u;   // this group's accumulator set
         const uint64_t da0 = smem_desc(a0, 128, kKcores * 128);
         const uint64_t db0 = smem_desc(b0, 128, kKcores * 128);
         const uint32_t acc0 = first ? 0u : 1u;
@@ -556,11 +593,11 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
         for (int kk = 0; kk < kKr / 16; ++kk)
 #pragma unroll
           for (int i = 0; i < S; ++i)
-            mma_bf16(tmem + i * kN, da0 + (uint64_t)((i * kABytes + kk * 256) >> 4),
+            mma_bf16(tacc + i * kN, da0 + (uint64_t)((i * kABytes + kk * 256) >> 4),
                      db0 + (uint64_t)((kk * 256) >> 4), idesc((S - i) * kN),
                      (i == 0 && kk == 0) ? acc0 : 1u);
         commit(smem_u32(&empty[st]));
-        if (last) commit(smem_u32(&acc_full));
+        if (last) commit(smem_u32(&acc_full[set]));
         mmas = (int)(c + 1);
       }
     }
@@ -575,7 +612,8 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
       const int eam = ea_g[g * kMc];
       if (lane < kNc / 2) eb_s[ew][lane] = eb_g[g * kNc + lane];
       __syncwarp();
-      if (!mbar_wait(smem_u32(&acc_full), (uint32_t)(g & 1), err)) {
+      const int set = g % kSets;
+      if (!mbar_wait(smem_u32(&acc_full[set]), (uint32_t)((g / kSets) & 1), err)) {
         if (lane == 0) {
           bad = 1;
           atomicOr(err, 1ull);
@@ -589,34 +627,47 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
       // whose rounding (below 2^-40 of level 0's scale) is under the digits' truncation.
       // The sum is scaled by the group's 2^(e(m) + e(n) - 14) (powers of two: exact) and
       // added to the float-float accumulators.
-      const uint32_t ta0 = tmem + ((uint32_t)(quarter * 32) << 16) + half * kCw;
+      const uint32_t ta0 = tmem + (uint32_t)set * 256u + ((uint32_t)(quarter * 32) << 16) + half * kCw;
 #pragma unroll
       for (int c8 = 0; c8 < kCw / 8; ++c8) {
         float hi[8], lo[8];
-        tmem_ld8(ta0 + c8 * 8, hi);        // level 0
-        tmem_ld8(ta0 + kN + c8 * 8, lo);   // level 1
+        tmem_ld8x2(ta0 + c8 * 8, ta0 + kN + c8 * 8, hi, lo);   // levels 0 and 1
 #pragma unroll
         for (int i = 0; i < 8; ++i) two_sum(hi[i], lo[i] * 0.00390625f, hi[i], lo[i]);   // exact
-#pragma unroll 1
-        for (int lv = 2; lv < S; ++lv) {
-          float v[8];
-          tmem_ld8(ta0 + lv * kN + c8 * 8, v);
-          const float w = __int_as_float((127 - 8 * lv) << 23);   // 2^(-8L) relative to level 0
 #pragma unroll
-          for (int i = 0; i < 8; ++i) lo[i] = fmaf(v[i], w, lo[i]);
+        for (int lv = 2; lv < S; lv += 2) {
+          float v[8], v2[8];
+          const float w = __int_as_float((127 - 8 * lv) << 23);   // 2^(-8L) relative to level 0
+          if (lv + 1 < S) {
+            tmem_ld8x2(ta0 + lv * kN + c8 * 8, ta0 + (lv + 1) * kN + c8 * 8, v, v2);
+            const float w2 = w * 0.00390625f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) lo[i] = fmaf(v2[i], w2, fmaf(v[i], w, lo[i]));
+          } else {
+            tmem_ld8(ta0 + lv * kN + c8 * 8, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) lo[i] = fmaf(v[i], w, lo[i]);
+          }
         }
 #pragma unroll
         for (int i = 0; i < 8; i += 2) {
           float f1, f2;   // one exponent per complex column: (re, im) = columns i, i + 1
           pow2_pair(eam - 14 + eb_s[ew][(c8 * 8 + i) >> 1], f1, f2);
 #pragma unroll
-          for (int u = i; u < i + 2; ++u)
-            ff_acc(acc_h[c8 * 8 + u], acc_l[c8 * 8 + u], (hi[u] * f1) * f2, (lo[u] * f1) * f2);
+          for (int u = i; u < i + 2; ++u) {
+            const float h = (hi[u] * f1) * f2, l = (lo[u] * f1) * f2;
+            if (g == 0) {   // the first group starts the sums (a float pair, not renormalised)
+              acc_h[c8 * 8 + u] = h;
+              acc_l[c8 * 8 + u] = l;
+            } else {
+              ff_acc(acc_h[c8 * 8 + u], acc_l[c8 * 8 + u], h, l);
+            }
+          }
         }
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acc_empty));
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[set]));
     }
   }
   __syncthreads();
@@ -627,8 +678,8 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
   // commit tracks all of them).  If even these waits run out, the CTA exits regardless.
   if (bad) {
     if (warp == 0 && lane == 0)
-      for (int c = issued > kStages ? issued - kStages : 0; c < issued; ++c)
-        mbar_wait(smem_u32(&full[c % kStages]), (uint32_t)((c / kStages) & 1), nullptr);
+      for (int c = issued > kSt ? issued - kSt : 0; c < issued; ++c)
+        mbar_wait(smem_u32(&full[c % kSt]), (uint32_t)((c / kSt) & 1), nullptr);
     if (warp == 1 && lane == 0 && mmas > 0) {
       commit(smem_u32(&drain));
       mbar_wait(smem_u32(&drain), 0u, nullptr);
@@ -667,7 +718,7 @@ __global__ void __launch_bounds__(tc::kThreads, 2) k_gemm_tc(const Step s, Cx<ff
   fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(Cfg<S>::kCols)
+                 "r"(kCols)
                  : "memory");
 }
 

@@ -302,14 +302,17 @@ __global__ void __launch_bounds__(256) k_build(const Recipe* __restrict__ rec,
 }
 
 // ------------------------------------------------------------------ contraction step
+// Offsets of index x of a run class (x below the class's extent, which -- like every
+// tensor -- is at most 2^31, so the digits are taken with 32-bit division).
 __device__ __forceinline__ void split_runs(unsigned long long x, const Run* runs, int n,
                                            long long& oa, long long& ob) {
+  unsigned y = (unsigned)x;
   oa = 0;
   ob = 0;
   for (int i = 0; i < n; ++i) {
-    unsigned long long sz = (unsigned long long)runs[i].size;
-    unsigned long long d = x % sz;
-    x /= sz;
+    const unsigned sz = (unsigned)runs[i].size;
+    const unsigned qd = y / sz, d = y - qd * sz;
+    y = qd;
     oa += (long long)d * runs[i].sa;
     ob += (long long)d * runs[i].sb;
   }
@@ -553,16 +556,19 @@ __global__ void __launch_bounds__(256) k_rows_big(const Step s, Cx<R>* arena, Me
 // permutation) into shared memory, coalesced along whichever of m/k (A) or k/n (B) is
 // unit-stride in memory; each of the 256 threads accumulates a 4 x 4 block of complex
 // outputs in registers.
+// Offsets in A, B and C of index x of a GEMM-view run class (x below the class's extent,
+// at most 2^31: 32-bit division).
 __device__ __forceinline__ void runs4(long long x, const Run4* r, int n, long long& oa,
                                       long long& ob, long long& oc) {
+  unsigned y = (unsigned)x;
   oa = ob = oc = 0;
   for (int i = 0; i < n; ++i) {
-    long long sz = r[i].size;
-    long long d = x % sz;
-    x /= sz;
-    oa += d * r[i].sa;
-    ob += d * r[i].sb;
-    oc += d * r[i].sc;
+    const unsigned sz = (unsigned)r[i].size;
+    const unsigned qd = y / sz, d = y - qd * sz;
+    y = qd;
+    oa += (long long)d * r[i].sa;
+    ob += (long long)d * r[i].sb;
+    oc += (long long)d * r[i].sc;
   }
 }
 

@@ -218,7 +218,8 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
 // Digit conversion of both operands, then the tensor-core GEMM, for S digits.
 template <int S>
 cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* tcs,
-                      unsigned long long* err, cudaStream_t stream, Marker& mk, double cm, double by) {
+                      unsigned long long* err, cudaStream_t stream, Marker& mk, double cm, double by,
+                      int64_t db_groups) {
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
   // class 6 (digit conversion): its bytes are the operands it reads, |A| + |B|
   const long long nA = (tc::kMc / 32) * s.Bsz * L.tiles_m * L.groups,
@@ -228,8 +229,15 @@ cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* t
   k_digits<S><<<(unsigned)(nA + nB), tc::kConvThreads, tc::Cfg<S>::kConvSmem, stream>>>(s, arena, tcs, nA);
   mk.end();
   const long long tc_tiles = L.tiles_m * L.tiles_n * s.Bsz;
-  mk.begin(5, cm, by, gpu_fill(tc_tiles, 2));
-  k_gemm_tc<S><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(s, arena, meta, tcs, err);
+  if (db_groups > 0 && L.groups >= db_groups) {   // one CTA per SM, two accumulator sets
+    mk.begin(5, cm, by, gpu_fill(tc_tiles, 1));
+    k_gemm_tc<S, true><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<S>::kSmemDB, stream>>>(
+        s, arena, meta, tcs, err);
+  } else {
+    mk.begin(5, cm, by, gpu_fill(tc_tiles, 2));
+    k_gemm_tc<S, false><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(
+        s, arena, meta, tcs, err);
+  }
   mk.end();
   return cudaGetLastError();
 }
@@ -237,14 +245,15 @@ cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* t
 template <typename R>
 cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* partial,
                         unsigned* counter, cudaStream_t stream, Marker& mk, double by,
-                        unsigned char* tc_scratch = nullptr, unsigned long long* err = nullptr) {
+                        unsigned char* tc_scratch = nullptr, unsigned long long* err = nullptr,
+                        int64_t db_groups = 0) {
   const double cm = (double)s.R * (double)s.K * (double)s.N;
   const long long gemm_tiles = ((s.M + 63) / 64) * ((s.N + 63) / 64) * s.Bsz;
   cudaError_t e;
   if constexpr (std::is_same<R, ff>::value) {
     if (s.tc && tc_scratch && err)  // digits of A and B, then the tensor-core GEMM
-      return s.tc == 4 ? launch_tc<4>(s, arena, meta, tc_scratch, err, stream, mk, cm, by)
-                       : launch_tc<5>(s, arena, meta, tc_scratch, err, stream, mk, cm, by);
+      return s.tc == 4 ? launch_tc<4>(s, arena, meta, tc_scratch, err, stream, mk, cm, by, db_groups)
+                       : launch_tc<5>(s, arena, meta, tc_scratch, err, stream, mk, cm, by, db_groups);
   }
   if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
     mk.begin(4, cm, by, gpu_fill(gemm_tiles, 8));
@@ -302,7 +311,8 @@ cudaError_t launch_bulk(const Plan& p, char* base, char* arena_base, int32_t fir
     }
     mk.step = i;
     cudaError_t e = launch_step<R>(p.steps[i], arena, meta, partial, counters + i, stream, mk,
-                                   step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)), tcs, err);
+                                   step_bytes(p, p.steps[i], (double)sizeof(Cx<R>)), tcs, err,
+                                   p.tuning.tc_db_groups);
     if (e == cudaSuccess && o.check_finite)
       e = check_tensor<R>(arena + p.steps[i].off_c, p.tensors[p.steps[i].c].elems, err,
                           status_nonfinite(sl, i), stream);
@@ -507,10 +517,16 @@ cudaError_t raise_rows_smem() {
 template <int S>
 cudaError_t prepare_tc() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_gemm_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_gemm_tc<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::Cfg<S>::kSmem)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_gemm_tc<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  if ((e = cudaFuncSetAttribute(k_gemm_tc<S, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_gemm_tc<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::Cfg<S>::kSmemDB)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_gemm_tc<S, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(k_digits<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -990,7 +990,7 @@ bool valid_tuning(const pk_tuning& t) {
   return (t.batch_threads == 128 || t.batch_threads == 256 || t.batch_threads == 512) &&
          t.batch_ktab >= 256 && t.batch_ktab <= 2048 && t.seq_outs >= 1 && t.seq_outs <= 65536 &&
          t.seq_work >= 1 && t.seq_work <= (1 << 24) && t.seq_k >= 1 && t.seq_k <= kTinyK &&
-         t.tc_min_k >= 4 && t.tc_min_k <= 16;
+         t.tc_min_k >= 4 && t.tc_min_k <= 16 && t.tc_db_groups >= 0 && t.tc_db_groups <= 4096;
 }
 
 void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,

@@ -27,7 +27,14 @@
 //   K >=  4     59.96
 //   K >=  8     60.36
 //   K >= 16     60.53
+// One CTA per SM, two accumulator sets, from this many flush groups (0: never), split
+// (median ms per step, measured separately after the rows above):
+//   tc_db_groups =    0     56.05
+//   tc_db_groups =    2     62.04
+//   tc_db_groups =    3     60.23
+//   tc_db_groups =    4     60.42
+//   tc_db_groups =    6     60.18
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 4};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 4, 0};

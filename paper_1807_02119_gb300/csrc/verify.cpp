@@ -167,6 +167,8 @@ bool check_forward(const Plan& p, int32_t precision, Checker& ck) {
     if (ti.offset < 0 || ti.elems < 1 || ti.offset + ti.elems > p.arena_elems)
       return ck.fail(w, "outside the arena");
     if (ti.offset % 64 != 0) return ck.fail(w, "not on a 512-byte boundary");
+    if (ti.elems > ((int64_t)1 << 31))   // the kernels decode indices with 32-bit division
+      return ck.fail(w, "more than 2^31 entries");
     live.push_back({ti.offset, ti.elems, ti.born, ti.dies, t});
   }
   if (!disjoint(live, "arena", ck)) return false;

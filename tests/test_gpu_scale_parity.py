@@ -28,7 +28,7 @@ from oracle.scaled import SC, rel_err
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "scale_oracle.txt")
-TOL = {"split": 1e-6, "split4": 4e-6, "c128": 1e-10}
+TOL = {"split": 1e-6, "split4": 4e-6, "split_db": 1e-6, "c128": 1e-10}
 QS = (2, 3, 5)
 
 
@@ -58,10 +58,16 @@ def ctx():
     return c
 
 
-def _plans(ctx, flags=0):
+def _plans(ctx, flags=0, qs=QS, **tuning):
+    """The workload's plans; `tuning` fields are set on a context of their own."""
+    if tuning:
+        import torch
+        ctx = pk.Context(0)
+        ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+        ctx.set_tuning(**tuning)
     knots = [kg.random_grid_knot(40, s, True, 100, 400) for s in range(1, 65)]
     kn = [pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer) for gk in knots]
-    jobs = [(gk.seed, k, q) for gk, k in zip(knots, kn) for q in QS]
+    jobs = [(gk.seed, k, q) for gk, k in zip(knots, kn) for q in qs]
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
         plans = list(ex.map(lambda j: pk.Plan(ctx, j[1], j[2], restarts=128, flags=flags), jobs))
     return [(seed, q) for seed, _, q in jobs], plans
@@ -104,11 +110,18 @@ def test_golden_covers_the_tensor_core_shapes(workload):
                for k, p in zip(keys, plans) if gold[k] is not None for st in p.steps())
 
 
-@pytest.mark.parametrize("prec", ["split", "split4", "c128"])
+@pytest.mark.parametrize("prec", ["split", "split4", "split_db", "c128"])
 def test_scale_workload_vs_oracle(ctx, workload, prec):
-    keys, plans = workload if prec != "split4" else _plans(ctx, pk.FLAG_TC_DIGITS4)
+    """split_db: every tensor-core step on the double-buffered GEMM (one CTA per SM, two
+    accumulator sets)."""
+    if prec == "split4":
+        keys, plans = _plans(ctx, pk.FLAG_TC_DIGITS4)
+    elif prec == "split_db":
+        keys, plans = _plans(ctx, tc_db_groups=1)
+    else:
+        keys, plans = workload
     gold = load_golden()
-    res = run_group(plans, prec if prec != "split4" else "split")
+    res = run_group(plans, "split" if prec.startswith("split") else prec)
     worst, worst_tc, n_tc, n_cmp = 0.0, 0.0, 0, 0
     for key, p, (z, v) in zip(keys, plans, res):
         ref = gold[key]
@@ -140,3 +153,15 @@ def test_scale_workload_beyond_the_oracle(workload):
     for (k, _), (zs, vs), (zc, vc) in zip(wide, rs, rc):
         e = max(rel_err(sc(zs), sc(zc)), rel_err(sc(vs), sc(vc)))
         assert e <= TOL["split"], (k, e)
+
+
+def test_double_buffered_gemm_is_bit_identical(ctx):
+    """The two GEMM variants form the same products and flush the groups in the same order:
+    the q = 5 evaluations agree bit for bit (every tensor-core step double-buffered against
+    none)."""
+    keys, p1 = _plans(ctx, qs=(5,), tc_db_groups=0)
+    _, p2 = _plans(ctx, qs=(5,), tc_db_groups=1)
+    assert sum(any(st["kernel"] == 2 and st["K"] > 96 for st in p.steps()) for p in p1) >= 40
+    r1, r2 = run_group(p1, "split"), run_group(p2, "split")
+    for k, (z1, v1), (z2, v2) in zip(keys, r1, r2):
+        assert (z1, v1) == (z2, v2), k
