@@ -155,13 +155,15 @@ typedef struct {
                                 per step at most (1..65536)                                   */
   int64_t seq_work;          /* ... complex multiply-adds per step at most (1..2^24)          */
   int64_t seq_k;             /* ... contracted extent per step at most (1..2048)              */
-  int64_t tc_min_k;          /* PK_SPLIT: row steps of GEMM shape (M >= 64, N >= 32) with this
-                                contracted extent or more run on the tensor cores too (4..16;
-                                16: only the GEMM steps, which need K >= 16 anyway)           */
+  int64_t tc_min_k;          /* PK_SPLIT: row steps of GEMM shape (M >= 64, N >= tc_min_n)
+                                with this contracted extent or more run on the tensor cores
+                                too (4..16; 16: only steps with K >= 16)                      */
   int64_t tc_db_groups;      /* PK_SPLIT: tensor-core steps with at least this many flush
                                 groups of K (96 complex k each) run one CTA per SM with two
                                 accumulator sets, so a group's flush overlaps the next group's
                                 products; shorter steps run two CTAs per SM (0: never; 1..4096) */
+  int64_t tc_min_n;          /* PK_SPLIT: ... and at least this many columns (8..32; a tile
+                                has 24, so narrower steps leave part of it idle)              */
 } pk_tuning;
 
 pk_status pk_tuning_default(pk_tuning* out);

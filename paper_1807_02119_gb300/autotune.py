@@ -9,8 +9,8 @@ before every timed launch, the fastest median kept:
 * sequence runs (consecutive small steps of a plan launched as one one-CTA kernel): the
   largest step, in outputs and in complex multiply-adds, that joins a run, on the 64-knot
   scale workload (q = 2, 3, 5; 192 plans replayed as one concurrent graph, split);
-* the smallest contracted extent from which row steps of GEMM shape also run on the
-  tensor cores (split), on the same workload;
+* the smallest contracted extent and column count from which row steps of GEMM shape
+  also run on the tensor cores (split), on the same workload;
 * the number of flush groups from which a tensor-core step runs one CTA per SM with two
   accumulator sets instead of two CTAs per SM with one, on the same workload.
 
@@ -41,7 +41,8 @@ SEQ_OUTS = (1024, 2048, 4096, 8192)
 SEQ_WORK = (1 << 12, 1 << 14, 1 << 16)
 TC_MIN_K = (4, 8, 16)
 TC_DB_GROUPS = (0, 2, 3, 4, 6)
-SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_db_groups": TC_DB_GROUPS}
+TC_MIN_N = (8, 12, 16, 24, 32)
+SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_min_n": TC_MIN_N, "tc_db_groups": TC_DB_GROUPS}
 
 
 def _rel(a, b):
@@ -172,6 +173,7 @@ def sweep_scale_param(pk, ctx, stream, flush, reps, log, name):
 PARAM_TITLES = {
     "tc_min_k": "Tensor cores for row steps of GEMM shape from this K",
     "tc_db_groups": "One CTA per SM, two accumulator sets, from this many flush groups (0: never)",
+    "tc_min_n": "Tensor cores for row steps of GEMM shape from this many columns",
 }
 
 
@@ -193,7 +195,8 @@ def write_table(path, tune, batch_rows, seq_rows, gpu, param_rows):
     lines += ["#pragma once", '#include "pk.h"', "",
               "constexpr pk_tuning kTunedDefault = {" +
               f"{tune['batch_threads']}, {tune['batch_ktab']}, {tune['seq_outs']}, "
-              f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}, {tune['tc_db_groups']}" +
+              f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}, {tune['tc_db_groups']}, "
+              f"{tune['tc_min_n']}" +
               "};", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))

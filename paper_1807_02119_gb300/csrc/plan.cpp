@@ -822,7 +822,8 @@ double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& se
 // ------------------------------------------------------------------ step descriptors
 bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
-                bool& swapped, std::vector<int32_t>& cdims, std::string& err, int64_t tc_min_k) {
+                bool& swapped, std::vector<int32_t>& cdims, std::string& err, int64_t tc_min_k,
+                int64_t tc_min_n) {
   static const std::vector<int32_t> no_dims;
   swapped = yd != nullptr && yd->size() > xd.size();
   const bool hasb = yd != nullptr;
@@ -978,7 +979,7 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
   // kernel more float-float work than the tensor cores' epilogue (complex64 and complex128
   // keep the row kernel for them)
   const bool short_k = hasb && st.kernel == KROWS && !(flags & PK_FLAG_FORCE_ROWS) && st.M >= 64 &&
-                       st.N >= 32 && st.K >= tc_min_k;
+                       st.N >= tc_min_n && st.K >= tc_min_k;
   st.tc = ((st.kernel == KGEMM || short_k) && !(flags & PK_FLAG_NO_TC))
               ? ((flags & PK_FLAG_TC_DIGITS4) ? 4 : 5)
               : 0;
@@ -990,7 +991,8 @@ bool valid_tuning(const pk_tuning& t) {
   return (t.batch_threads == 128 || t.batch_threads == 256 || t.batch_threads == 512) &&
          t.batch_ktab >= 256 && t.batch_ktab <= 2048 && t.seq_outs >= 1 && t.seq_outs <= 65536 &&
          t.seq_work >= 1 && t.seq_work <= (1 << 24) && t.seq_k >= 1 && t.seq_k <= kTinyK &&
-         t.tc_min_k >= 4 && t.tc_min_k <= 16 && t.tc_db_groups >= 0 && t.tc_db_groups <= 4096;
+         t.tc_min_k >= 4 && t.tc_min_k <= 16 && t.tc_db_groups >= 0 && t.tc_db_groups <= 4096 &&
+         t.tc_min_n >= 8 && t.tc_min_n <= 32;
 }
 
 void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,
@@ -1229,7 +1231,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
     Step st;
     bool sw = false;
     if (!build_step(p.tensors[x].dims, y >= 0 ? &p.tensors[y].dims : nullptr, sets[cid], q,
-                    opts.flags, st, sw, p.tensors[cid].dims, err, tune.tc_min_k))
+                    opts.flags, st, sw, p.tensors[cid].dims, err, tune.tc_min_k, tune.tc_min_n))
       return false;
     st.a = sw ? y : x;
     st.b = sw ? x : y;

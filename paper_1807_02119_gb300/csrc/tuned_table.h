@@ -34,7 +34,23 @@
 //   tc_db_groups =    3     60.23
 //   tc_db_groups =    4     60.42
 //   tc_db_groups =    6     60.18
+// Tensor cores for row steps of GEMM shape from this many columns (tc_min_k = 4), then from
+// this K (tc_min_n = 16), split (median ms per step, measured after the rows above):
+//   tc_min_n =    8     54.85
+//   tc_min_n =   12     54.88
+//   tc_min_n =   16     54.70
+//   tc_min_n =   24     54.99
+//   tc_min_n =   32     56.24
+//   tc_min_k =    4     55.21
+//   tc_min_k =    8     53.79
+//   tc_min_k =   16     53.62
+// Columns again with tc_min_k = 16 (median ms per step):
+//   tc_min_n =    8     53.79
+//   tc_min_n =   12     53.75
+//   tc_min_n =   16     54.27
+//   tc_min_n =   24     53.78
+//   tc_min_n =   32     56.28
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 4, 0};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12};

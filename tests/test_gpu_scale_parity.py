@@ -28,7 +28,7 @@ from oracle.scaled import SC, rel_err
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "scale_oracle.txt")
-TOL = {"split": 1e-6, "split4": 4e-6, "split_db": 1e-6, "c128": 1e-10}
+TOL = {"split": 1e-6, "split4": 4e-6, "split_db": 1e-6, "split_narrow": 1e-6, "c128": 1e-10}
 QS = (2, 3, 5)
 
 
@@ -110,14 +110,25 @@ def test_golden_covers_the_tensor_core_shapes(workload):
                for k, p in zip(keys, plans) if gold[k] is not None for st in p.steps())
 
 
-@pytest.mark.parametrize("prec", ["split", "split4", "split_db", "c128"])
+@pytest.mark.parametrize("prec", ["split", "split4", "split_db", "split_narrow", "c128"])
 def test_scale_workload_vs_oracle(ctx, workload, prec):
     """split_db: every tensor-core step on the double-buffered GEMM (one CTA per SM, two
-    accumulator sets)."""
+    accumulator sets); split_narrow: row steps of GEMM shape down to K = 4 and N = 8 on the
+    tensor cores too (tiles with most of their 24 columns idle)."""
     if prec == "split4":
         keys, plans = _plans(ctx, pk.FLAG_TC_DIGITS4)
     elif prec == "split_db":
         keys, plans = _plans(ctx, tc_db_groups=1)
+    elif prec == "split_narrow":
+        keys, plans = _plans(ctx, tc_min_k=4, tc_min_n=8)
+        import ctypes as C
+        from plan_replay import Step
+        narrow = 0
+        for p in plans:
+            b = p.debug_blob(1)
+            narrow += sum(st.tc > 0 and st.N < 32 for st in
+                          (Step * (len(b) // C.sizeof(Step))).from_buffer_copy(b))
+        assert narrow >= 500, narrow      # tensor-core steps with N < 32 (mostly 25 = 5^2)
     else:
         keys, plans = workload
     gold = load_golden()
