@@ -223,8 +223,6 @@ __device__ __forceinline__ void pow2_pair(int x, float& f1, float& f2) {
   f2 = __int_as_float((max(-126, min(127, x2)) + 127) << 23);
 }
 
-// 2^(7 - e), the digit scale of a row with exponent e.
-__device__ __forceinline__ void digit_scale(int e, float& sc1, float& sc2) { pow2_pair(7 - e, sc1, sc2); }
 
 }  // namespace tc
 
@@ -261,23 +259,27 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // The S digit slices of one real component of 8 consecutive k of one tile row: x[u] =
-// (hi, lo) of k = 8 o + u, scaled by sc1 sc2 = 2^(7 - e) (the row's scale as two exact
-// powers of two, so that any exponent the stored values can have is covered), giving
-// float-float values y = (yh + yl) with |y| <= 2^7.  Digit i is the nearest integer d_i of
-// the running remainder times 2^(8i); the remainder r = yh - d_i is exact and a multiple
-// of ulp(yh), while |yl| <= ulp(yh) / 2, so |r| >= |yl| unless r = 0 and the fast two-sum
-// (Dekker) that renormalises (r + yl) is exact.  Digit i of the 8 values, as 8 BF16 packed
-// into 16 bytes (one core-matrix row), goes to out + i * slice and, when out2 is given,
-// also to out2 + i * slice, negated if `neg2`.
+// (hi, lo) of k = 8 o + u, scaled by f1 f2 = 2^(7 - e) (e the row's exponent over the
+// group, |hi| < 2^e; two exact powers of two, so that any exponent the stored values can
+// have is covered), giving float-float values y = (yh + yl) with |y| < 2^7.  Digit i is
+// the nearest integer d_i of the running remainder times 2^(8i): rounding by adding and
+// subtracting 1.5 * 2^23 (exact round-to-nearest-even on the FP32 adder for |yh| < 2^22,
+// no conversion instruction); the remainder r = yh - d_i is exact and a multiple of
+// ulp(yh), while |yl| <= ulp(yh) / 2, so |r| >= |yl| unless r = 0 and the fast two-sum
+// (Dekker) that renormalises (r + yl) is exact.  An integer d_i with |d_i| <= 256 keeps
+// only the top 16 bits of its FP32 pattern, which are its BF16 pattern.  Digit i of the 8
+// values, packed into 16 bytes (one core-matrix row), goes to out + i * slice and, when
+// out2 is given, also to out2 + i * slice, negated if `neg2`.
 template <int S>
-__device__ __forceinline__ void digit_rows8(const float* xh, const float* xl, float sc1, float sc2,
+__device__ __forceinline__ void digit_rows8(const float* xh, const float* xl, float f1, float f2,
                                             unsigned char* out, unsigned char* out2, bool neg2,
                                             int slice) {
+  constexpr float kRound = 12582912.0f;   // 1.5 * 2^23
   float yh[8], yl[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
-    yh[u] = (xh[u] * sc1) * sc2;
-    yl[u] = (xl[u] * sc1) * sc2;
+    yh[u] = (xh[u] * f1) * f2;
+    yl[u] = (xl[u] * f1) * f2;
   }
   const uint32_t flip = neg2 ? 0x80008000u : 0u;   // negate the BF16 digits (exact)
 #pragma unroll
@@ -285,17 +287,18 @@ __device__ __forceinline__ void digit_rows8(const float* xh, const float* xl, fl
     uint32_t w[4];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const float di = rintf(yh[u]);
-      const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(di));
-      if (u & 1)
-        w[u >> 1] |= b << 16;
+      const float di = __fsub_rn(__fadd_rn(yh[u], kRound), kRound);
+      if (u & 1)   // BF16 of value u - 1 in the low half, of u in the high half
+        w[u >> 1] = __byte_perm(w[u >> 1], __float_as_uint(di), 0x7632);
       else
-        w[u >> 1] = b;
-      const float r = __fsub_rn(yh[u], di);
-      const float sum = __fadd_rn(r, yl[u]);
-      const float err = __fsub_rn(yl[u], __fsub_rn(sum, r));
-      yh[u] = sum * 256.0f;
-      yl[u] = err * 256.0f;
+        w[u >> 1] = __float_as_uint(di);
+      if (i + 1 < S) {
+        const float r = __fsub_rn(yh[u], di);
+        const float sum = __fadd_rn(r, yl[u]);
+        const float err = __fsub_rn(yl[u], __fsub_rn(sum, r));
+        yh[u] = sum * 256.0f;
+        yl[u] = err * 256.0f;
+      }
     }
     *(uint4*)(out + i * slice) = make_uint4(w[0], w[1], w[2], w[3]);
     if (out2)
@@ -403,8 +406,8 @@ __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena,
   const int octs = kgn / 8;
   for (int idx = tid; idx < kRows * octs; idx += kConvThreads) {
     const int r = idx % kRows, o = idx / kRows;
-    float sc1, sc2;
-    digit_scale(ex[r], sc1, sc2);
+    float sc1, sc2;   // 2^(7 - e): the row's largest entry below 2^7
+    pow2_pair(7 - ex[r], sc1, sc2);
     const long long k = k0 + 8 * o;
     const int kl = (int)(k % kKc);   // 0 or 8
     unsigned char* ch = dst0 + (k / kKc) * (long long)kChunkBytes;
