@@ -164,6 +164,12 @@ typedef struct {
                                 products; shorter steps run two CTAs per SM (0: never; 1..4096) */
   int64_t tc_min_n;          /* PK_SPLIT: ... and at least this many columns (8..32; a tile
                                 has 24, so narrower steps leave part of it idle)              */
+  int64_t cost_gemm_milli;   /* planner: cost of a complex multiply-add in a step that runs on
+                                the tensor cores (M >= 64, N >= tc_min_n, K >= tc_min_k), in
+                                thousandths of a row-kernel multiply-add (10..1000), when the
+                                candidate orders are ranked                                    */
+  int64_t cost_out_milli;    /* planner: cost of one output entry of a step (its store and
+                                normalisation), in thousandths of a multiply-add (0..100000)  */
 } pk_tuning;
 
 pk_status pk_tuning_default(pk_tuning* out);

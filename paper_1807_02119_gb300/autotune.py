@@ -12,7 +12,9 @@ before every timed launch, the fastest median kept:
 * the smallest contracted extent and column count from which row steps of GEMM shape
   also run on the tensor cores (split), on the same workload;
 * the number of flush groups from which a tensor-core step runs one CTA per SM with two
-  accumulator sets instead of two CTAs per SM with one, on the same workload.
+  accumulator sets instead of two CTAs per SM with one, on the same workload;
+* the planner's cost weights (a tensor-core multiply-add, an output entry) with which the
+  candidate contraction orders are ranked, on the same workload.
 
 Every candidate's results are checked against the first candidate's (same plans, same
 precision) before its time counts.  The winners are written to csrc/tuned_table.h (the
@@ -42,7 +44,10 @@ SEQ_WORK = (1 << 12, 1 << 14, 1 << 16)
 TC_MIN_K = (4, 8, 16)
 TC_DB_GROUPS = (0, 2, 3, 4, 6)
 TC_MIN_N = (8, 12, 16, 24, 32)
-SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_min_n": TC_MIN_N, "tc_db_groups": TC_DB_GROUPS}
+COST_GEMM = (50, 100, 150, 250, 400)
+COST_OUT = (1000, 2000, 4000, 8000)
+SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_min_n": TC_MIN_N, "tc_db_groups": TC_DB_GROUPS,
+                "cost_gemm_milli": COST_GEMM, "cost_out_milli": COST_OUT}
 
 
 def _rel(a, b):
@@ -174,6 +179,8 @@ PARAM_TITLES = {
     "tc_min_k": "Tensor cores for row steps of GEMM shape from this K",
     "tc_db_groups": "One CTA per SM, two accumulator sets, from this many flush groups (0: never)",
     "tc_min_n": "Tensor cores for row steps of GEMM shape from this many columns",
+    "cost_gemm_milli": "Planner: cost of a tensor-core multiply-add (thousandths of a row one)",
+    "cost_out_milli": "Planner: cost of an output entry (thousandths of a multiply-add)",
 }
 
 
@@ -196,7 +203,7 @@ def write_table(path, tune, batch_rows, seq_rows, gpu, param_rows):
               "constexpr pk_tuning kTunedDefault = {" +
               f"{tune['batch_threads']}, {tune['batch_ktab']}, {tune['seq_outs']}, "
               f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}, {tune['tc_db_groups']}, "
-              f"{tune['tc_min_n']}" +
+              f"{tune['tc_min_n']}, {tune['cost_gemm_milli']}, {tune['cost_out_milli']}" +
               "};", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))

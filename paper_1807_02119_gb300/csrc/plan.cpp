@@ -776,12 +776,14 @@ bool slice_indices(std::vector<std::vector<int32_t>>& sets, int32_t n_idx, int32
 }
 
 // Estimated cost of a contraction sequence over index sets `sets` (one slice), in units of
-// complex multiply-adds on the CUDA cores: a step shaped for the GEMM kernels (M >= 64,
-// N >= 32, K >= 16 in its GEMM view) is weighted kGemmWeight (the tensor-core GEMM of the
-// split precision does a multiply-add for a fraction of a row kernel's cost), and every
-// output costs kOutWeight multiply-adds (its store and normalisation).
-constexpr double kGemmWeight = 0.15, kOutWeight = 4.0;
-double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& sets, int32_t q) {
+// complex multiply-adds on the CUDA cores: a step of the shape the split precision runs on
+// the tensor cores (M >= 64, N >= tc_min_n, K >= tc_min_k in its GEMM view) is weighted
+// cost_gemm_milli / 1000 (the tensor-core GEMM does a multiply-add for a fraction of a row
+// kernel's cost), and every output costs cost_out_milli / 1000 multiply-adds (its store
+// and normalisation).
+double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& sets, int32_t q,
+                     const pk_tuning& tune) {
+  const double w_gemm = (double)tune.cost_gemm_milli / 1000.0, w_out = (double)tune.cost_out_milli / 1000.0;
   static const std::vector<int32_t> none;
   const size_t n_init = sets.size() - seq.pairs.size();
   double c = 0;
@@ -810,9 +812,10 @@ double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& se
           ++k;
       }
     const double macs = std::pow((double)q, (double)union_size(sa, sb));
-    const bool gemm = pr.second >= 0 && std::pow((double)q, m) >= 64 && std::pow((double)q, n) >= 32 &&
-                      std::pow((double)q, k) >= 16;
-    c += macs * (gemm ? kGemmWeight : 1.0) + kOutWeight * std::pow((double)q, (double)sc.size());
+    const bool gemm = pr.second >= 0 && std::pow((double)q, m) >= 64 &&
+                      std::pow((double)q, n) >= (double)tune.tc_min_n &&
+                      std::pow((double)q, k) >= (double)tune.tc_min_k;
+    c += macs * (gemm ? w_gemm : 1.0) + w_out * std::pow((double)q, (double)sc.size());
   }
   return c;
 }
@@ -992,7 +995,8 @@ bool valid_tuning(const pk_tuning& t) {
          t.batch_ktab >= 256 && t.batch_ktab <= 2048 && t.seq_outs >= 1 && t.seq_outs <= 65536 &&
          t.seq_work >= 1 && t.seq_work <= (1 << 24) && t.seq_k >= 1 && t.seq_k <= kTinyK &&
          t.tc_min_k >= 4 && t.tc_min_k <= 16 && t.tc_db_groups >= 0 && t.tc_db_groups <= 4096 &&
-         t.tc_min_n >= 8 && t.tc_min_n <= 32;
+         t.tc_min_n >= 8 && t.tc_min_n <= 32 && t.cost_gemm_milli >= 10 &&
+         t.cost_gemm_milli <= 1000 && t.cost_out_milli >= 0 && t.cost_out_milli <= 100000;
 }
 
 void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,
@@ -1172,7 +1176,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
     std::vector<std::vector<int32_t>> ss = g.seq.sets;
     std::vector<int32_t> sl;
     if (!slice_indices(ss, net.n_idx, q, rmax, max_slice_idx, sl)) continue;
-    const double c = std::pow((double)q, (double)sl.size()) * sequence_cost(g.seq, ss, q);
+    const double c = std::pow((double)q, (double)sl.size()) * sequence_cost(g.seq, ss, q, tune);
     if (c < best_cost) {
       best_cost = c;
       best_net = net;

@@ -50,7 +50,18 @@
 //   tc_min_n =   16     54.27
 //   tc_min_n =   24     53.78
 //   tc_min_n =   32     56.28
+// Planner cost weights (tensor-core steps: M >= 64, N >= tc_min_n, K >= tc_min_k), split
+// (median ms per step, cost_gemm_milli first, then cost_out_milli with it):
+//   cost_gemm_milli =   50     53.23
+//   cost_gemm_milli =  100     52.60
+//   cost_gemm_milli =  150     52.20
+//   cost_gemm_milli =  250     53.68
+//   cost_gemm_milli =  400     54.09
+//   cost_out_milli  = 1000     53.95
+//   cost_out_milli  = 2000     53.70
+//   cost_out_milli  = 4000     52.79
+//   cost_out_milli  = 8000     52.57
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12, 150, 8000};
