@@ -611,6 +611,11 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
                       quarter * 32 + lane;
     const int* eb_g = (const int*)(scratch + L.eb_off) + (bb * L.tiles_n + tn) * L.groups * kNc +
                       half * (kNc / 2);
+    // blocks of 8 real columns of this warp that hold columns of C (a narrow step's last
+    // column block has fewer than kNc; the others are neither read nor combined)
+    const long long nv = s.N - tn * kNc;
+    const int cols = (int)max(0LL, min((long long)(kCw / 2), nv - half * (kCw / 2)));
+    const int c8n = (2 * cols + 7) / 8;
     for (int g = 0; g < (int)ngroups; ++g) {
       const int eam = ea_g[g * kMc];
       if (lane < kNc / 2) eb_s[ew][lane] = eb_g[g * kNc + lane];
@@ -633,6 +638,7 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
       const uint32_t ta0 = tmem + (uint32_t)set * 256u + ((uint32_t)(quarter * 32) << 16) + half * kCw;
 #pragma unroll
       for (int c8 = 0; c8 < kCw / 8; ++c8) {
+        if (c8 >= c8n) break;   // warp-uniform
         float hi[8], lo[8];
         tmem_ld8x2(ta0 + c8 * 8, ta0 + kN + c8 * 8, hi, lo);   // levels 0 and 1
 #pragma unroll
