@@ -450,14 +450,19 @@ __global__ void __launch_bounds__(tc::kConvThreads, 4) k_digits(const Step s, co
     digits_block<S, false>(s, arena, scratch, blk - nA, ro, kt, base, ex, tile);
 }
 
-// C tile (128 complex rows x 24 complex columns of one batch index) from the digit
-// chunks: warp 0 streams chunks into the stage ring, warp 1 issues the MMAs, warps 2..9
-// flush the level accumulators and store C.
-// DB = false: two CTAs per SM, a 2-stage ring and one set of level accumulators, so the
-// MMAs of a CTA wait while its epilogue flushes a group (the other CTA's MMAs fill in).
+// C tiles (128 complex rows x 24 complex columns of one batch index) from the digit
+// chunks, persistently: CTA b takes tiles b, b + gridDim.x, ... (column blocks fastest, so
+// the CTAs busy at one time share their A row blocks in L2).  Warp 0 streams the chunks of
+// its tiles into the stage ring, warp 1 issues the MMAs, warps 2..9 flush the level
+// accumulators and store C.  The ring's and the accumulators' barrier phases run on across
+// tiles: the producer loads the next tile's chunks while the current one is multiplied and
+// flushed, and the epilogue stores a tile from its registers after releasing the
+// accumulators, while the next tile's MMAs run; barriers and tensor memory are set up once.
+// DB = false: two CTAs per SM, a 2-stage ring and one set of level accumulators (the other
+// CTA's MMAs fill in while one CTA flushes).
 // DB = true: one CTA per SM, a 4-stage ring and two accumulator sets in TMEM (columns 0
 // and 256), used by alternate flush groups, so the flush of group g overlaps the MMAs of
-// group g + 1 (for steps with several flush groups).
+// group g + 1.
 template <int S, bool DB>
 __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step s, Cx<ff>* arena,
                                                                       Meta* meta,
@@ -467,28 +472,20 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
   constexpr int kSt = DB ? kStagesDB : kStages;     // stages of the ring
   constexpr int kSets = DB ? 2 : 1;                 // accumulator sets
   constexpr uint32_t kCols = DB ? 512u : (uint32_t)Cfg<S>::kCols;
+  constexpr int kFlush = Cfg<S>::kFlush;
   static_assert(!DB || S * kN <= 256, "two accumulator sets must fit 512 TMEM columns");
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ long long cm[kMc], cn[kNc];
-  __shared__ long long cbase;
-  __shared__ int eb_s[kEpiWarps][kNc / 2];   // per epilogue warp: its columns' group exponents
+  __shared__ long long cn_s[kEpiWarps][kNc / 2];   // per epilogue warp: its columns' C offsets
+  __shared__ int eb_s[kEpiWarps][kNc / 2];         // ... and their group exponents
   __shared__ __align__(8) unsigned long long full[kSt], empty[kSt], acc_full[kSets],
       acc_empty[kSets], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int bad;
-  unsigned char* sm = dsm;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
-  // column blocks fastest: the CTAs resident at one time share their A row blocks in L2
-  long long t = blockIdx.x;
-  const long long tn = t % L.tiles_n;
-  t /= L.tiles_n;
-  const long long tm = t % L.tiles_m;
-  const long long bb = t / L.tiles_m;
+  const long long ntiles = L.tiles_m * L.tiles_n * s.Bsz;
 
   if (tid == 0) {
-    long long a, b;
-    runs4(bb, s.gb, s.ngb, a, b, cbase);
     bad = 0;
     for (int i = 0; i < kSt; ++i) {
       mbar_init(smem_u32(&full[i]), 1);
@@ -500,23 +497,6 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
     }
     mbar_init(smem_u32(&drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (tid >= 64 && tid < 64 + kMc) {
-    const int i = tid - 64;
-    const long long m = tm * kMc + i;
-    long long a, b;
-    if (m < s.M)
-      runs4(m, s.gm, s.ngm, a, b, cm[i]);
-    else
-      cm[i] = -1;
-  } else if (tid >= 64 + kMc && tid < 64 + kMc + kNc) {
-    const int j = tid - 64 - kMc;
-    const long long n = tn * kNc + j;
-    long long a, b;
-    if (n < s.N)
-      runs4(n, s.gn, s.ngn, a, b, cn[j]);
-    else
-      cn[j] = -1;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -531,160 +511,226 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
   fence_after();
   const uint32_t tmem = tmem_slot;
   const long long nchunks = L.chunks;
-  const long long ngroups = (nchunks + Cfg<S>::kFlush - 1) / Cfg<S>::kFlush;
-  const uint32_t sm0 = smem_u32(sm);
+  const int ngroups = (int)((nchunks + kFlush - 1) / kFlush);
+  const uint32_t sm0 = smem_u32(dsm);
+  // (batch, row block, column block) of a tile, column blocks fastest
+  auto tile_coords = [&](long long t, long long& bb, long long& tm, long long& tn) {
+    tn = t % L.tiles_n;
+    t /= L.tiles_n;
+    tm = t % L.tiles_m;
+    bb = t / L.tiles_m;
+  };
 
   constexpr int kCw = kN / 2;  // columns per epilogue thread (two warps per lane quarter)
-  float acc_h[kCw], acc_l[kCw];
-#pragma unroll
-  for (int j = 0; j < kCw; ++j) acc_h[j] = acc_l[j] = 0.f;
-  int issued = 0;   // producer: chunks whose bulk copies were started (chunks < 2^31)
-  int mmas = 0;     // MMA issuer: chunks whose MMAs were issued
+  int issued = 0;   // producer: chunks of this CTA whose bulk copies were started
+  int mmas = 0;     // MMA issuer: chunks of this CTA whose MMAs were issued
+  float vmax = 0;
 
   if (warp == 0) {
     if (lane == 0) {  // producer
-      const unsigned char* asrc =
-          scratch + L.a_off + (bb * L.tiles_m + tm) * nchunks * (long long)Cfg<S>::kAChunk;
-      const unsigned char* bsrc =
-          scratch + L.b_off + (bb * L.tiles_n + tn) * nchunks * (long long)Cfg<S>::kBChunk;
-      for (long long c = 0; c < nchunks; ++c) {
-        const int st = (int)(c % kSt);
-        if (c >= kSt &&
-            !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c / kSt) - 1) & 1), err)) {
-          bad = 1;
-          atomicOr(err, 1ull);
-          break;
+      long long gc = 0;   // chunks of this CTA so far (all its tiles)
+      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        long long bb, tm, tn;
+        tile_coords(t, bb, tm, tn);
+        const unsigned char* asrc =
+            scratch + L.a_off + (bb * L.tiles_m + tm) * nchunks * (long long)Cfg<S>::kAChunk;
+        const unsigned char* bsrc =
+            scratch + L.b_off + (bb * L.tiles_n + tn) * nchunks * (long long)Cfg<S>::kBChunk;
+        for (long long c = 0; c < nchunks; ++c, ++gc) {
+          const int st = (int)(gc % kSt);
+          if (gc >= kSt &&
+              !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((gc / kSt) - 1) & 1), err)) {
+            bad = 1;
+            atomicOr(err, 1ull);
+            goto producer_done;
+          }
+          const uint32_t dst = sm0 + st * Cfg<S>::kStage;
+          mbar_expect_tx(smem_u32(&full[st]), Cfg<S>::kStage);
+          bulk_g2s(dst, asrc + c * Cfg<S>::kAChunk, Cfg<S>::kAChunk, smem_u32(&full[st]));
+          bulk_g2s(dst + Cfg<S>::kAChunk, bsrc + c * Cfg<S>::kBChunk, Cfg<S>::kBChunk,
+                   smem_u32(&full[st]));
+          issued = (int)(gc + 1);
         }
-        const uint32_t dst = sm0 + st * Cfg<S>::kStage;
-        mbar_expect_tx(smem_u32(&full[st]), Cfg<S>::kStage);
-        bulk_g2s(dst, asrc + c * Cfg<S>::kAChunk, Cfg<S>::kAChunk, smem_u32(&full[st]));
-        bulk_g2s(dst + Cfg<S>::kAChunk, bsrc + c * Cfg<S>::kBChunk, Cfg<S>::kBChunk,
-                 smem_u32(&full[st]));
-        issued = (int)(c + 1);
       }
+    producer_done:;
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      for (long long c = 0; c < nchunks; ++c) {
-        const int st = (int)(c % kSt);
-        const long long g = c / Cfg<S>::kFlush;
-        const int set = (int)(g % kSets);
-        const long long use = g / kSets;   // earlier groups on this accumulator set
-        const bool first = c % Cfg<S>::kFlush == 0;
-        const bool last = (c + 1) % Cfg<S>::kFlush == 0 || c + 1 == nchunks;
-        // before a set is reused, its previous group must have been flushed
-        if ((first && use > 0 &&
-             !mbar_wait(smem_u32(&acc_empty[set]), (uint32_t)((use - 1) & 1), err)) ||
-            !mbar_wait(smem_u32(&full[st]), (uint32_t)((c / kSt) & 1), err)) {
-          bad = 1;
-          atomicOr(err, 1ull);
+      long long gc = 0, gg = 0;   // chunks and flush groups of this CTA so far
+      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (long long c = 0; c < nchunks; ++c, ++gc) {
+          const int st = (int)(gc % kSt);
+          const int set = (int)(gg % kSets);
+          const long long use = gg / kSets;   // earlier groups on this accumulator set
+          const bool first = c % kFlush == 0;
+          const bool last = (c + 1) % kFlush == 0 || c + 1 == nchunks;
+          // before a set is reused, its previous group must have been flushed
+          if ((first && use > 0 &&
+               !mbar_wait(smem_u32(&acc_empty[set]), (uint32_t)((use - 1) & 1), err)) ||
+              !mbar_wait(smem_u32(&full[st]), (uint32_t)((gc / kSt) & 1), err)) {
+            bad = 1;
+            atomicOr(err, 1ull);
+            goto mma_done;
+          }
+          fence_after();
+          // descriptors of the stage's first A and B slices; a slice or K-step offset is
+          // added to the start-address field (shared addresses < 256 KB: no carry out of it)
+          const uint32_t a0 = sm0 + st * Cfg<S>::kStage, b0 = a0 + Cfg<S>::kAChunk;
+          const uint32_t tacc = tmem + (uint32_t)set * 256u;   // this group's accumulator set
+          const uint64_t da0 = smem_desc(a0, 128, kKcores * 128);
+          const uint64_t db0 = smem_desc(b0, 128, kKcores * 128);
+          const uint32_t acc0 = first ? 0u : 1u;
+          // A digit i meets B digits 0 .. S-1-i in ONE MMA: the B digit slices lie one after
+          // another in shared memory (the same 8-row-group stride), so together they are a
+          // (S - i) N column operand, and its products land on the level accumulators
+          // i .. S-1, which lie one after another in TMEM from column i N.
+#pragma unroll
+          for (int kk = 0; kk < kKr / 16; ++kk)
+#pragma unroll
+            for (int i = 0; i < S; ++i)
+              mma_bf16(tacc + i * kN, da0 + (uint64_t)((i * kABytes + kk * 256) >> 4),
+                       db0 + (uint64_t)((kk * 256) >> 4), idesc((S - i) * kN),
+                       (i == 0 && kk == 0) ? acc0 : 1u);
+          commit(smem_u32(&empty[st]));
+          if (last) {
+            commit(smem_u32(&acc_full[set]));
+            ++gg;
+          }
+          mmas = (int)(gc + 1);
+        }
+      }
+    mma_done:;
+    }
+  } else {  // epilogue warps: flush the levels every kFlush chunks, store each tile
+    const int quarter = warp & 3, half = (warp - 2) / 4, ew = warp - 2;
+    int gg = 0;   // flush groups of this CTA so far (tiles and chunks per step < 2^31)
+    bool failed = false;
+    for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+      long long bb, tm, tn;
+      tile_coords(t, bb, tm, tn);
+      // this thread's row of C (lane = row within the lane quarter) and, per lane j < 12,
+      // its warp's column j
+      const long long m = tm * kMc + quarter * 32 + lane;
+      long long crow = -1;
+      {
+        long long a, b, cb, cr;
+        runs4(bb, s.gb, s.ngb, a, b, cb);
+        if (m < s.M) {
+          runs4(m, s.gm, s.ngm, a, b, cr);
+          crow = cb + cr;
+        }
+      }
+      if (lane < kNc / 2) {
+        const long long n = tn * kNc + half * (kNc / 2) + lane;
+        long long a, b, cc = -1;
+        if (n < s.N) runs4(n, s.gn, s.ngn, a, b, cc);
+        cn_s[ew][lane] = cc;
+      }
+      // this thread's row exponent and its warp's column exponents, per flush group
+      const int* ea_g = (const int*)(scratch + L.ea_off) + (bb * L.tiles_m + tm) * L.groups * kMc +
+                        quarter * 32 + lane;
+      const int* eb_g = (const int*)(scratch + L.eb_off) + (bb * L.tiles_n + tn) * L.groups * kNc +
+                        half * (kNc / 2);
+      // blocks of 8 real columns of this warp that hold columns of C (a narrow step's last
+      // column block has fewer than kNc; the others are neither read nor combined)
+      const long long nv = s.N - tn * kNc;
+      const int cols = (int)max(0LL, min((long long)(kCw / 2), nv - half * (kCw / 2)));
+      const int c8n = (2 * cols + 7) / 8;
+      float acc_h[kCw], acc_l[kCw];
+#pragma unroll
+      for (int j = 0; j < kCw; ++j) acc_h[j] = acc_l[j] = 0.f;
+      for (int g = 0; g < ngroups; ++g, ++gg) {
+        const int set = gg % kSets;
+        const int eam = ea_g[g * kMc];
+        if (lane < kNc / 2) eb_s[ew][lane] = eb_g[g * kNc + lane];
+        __syncwarp();
+        if (!mbar_wait(smem_u32(&acc_full[set]), (uint32_t)((gg / kSets) & 1), err)) {
+          if (lane == 0) {
+            bad = 1;
+            atomicOr(err, 1ull);
+          }
+          failed = true;
           break;
         }
         fence_after();
-        // descriptors of the stage's first A and B slices; a slice or K-step offset is
-        // added to the start-address field (shared addresses < 256 KB: no carry out of it)
-        const uint32_t a0 = sm0 + st * Cfg<S>::kStage, b0 = a0 + Cfg<S>::kAChunk;
-        const uint32_t tacc = tmem + (uint32_t)set * 256u;   // this group's accumulator set
-        const uint64_t da0 = smem_desc(a0, 128, kKcores * 128);
-        const uint64_t db0 = smem_desc(b0, 128, kKcores * 128);
-        const uint32_t acc0 = first ? 0u : 1u;
-        // A digit i meets B digits 0 .. S-1-i in ONE MMA: the B digit slices lie one after
-        // another in shared memory (the same 8-row-group stride), so together they are a
-        // (S - i) N column operand, and its products land on the level accumulators
-        // i .. S-1, which lie one after another in TMEM from column i N.
+        // level L holds an integer sum of digit products (below 2^24 in magnitude) at weight
+        // 2^(-14-8L).  Per 8 columns: levels 0 and 1 are added exactly (TwoSum); levels 2 ..
+        // S-1, at most 2^-16 of level 0's scale, are folded into the low part with FP32 FMAs,
+        // whose rounding (below 2^-40 of level 0's scale) is under the digits' truncation.
+        // The sum is scaled by the group's 2^(e(m) + e(n) - 14) (powers of two: exact) and
+        // added to the float-float accumulators.
+        const uint32_t ta0 =
+            tmem + (uint32_t)set * 256u + ((uint32_t)(quarter * 32) << 16) + half * kCw;
 #pragma unroll
-        for (int kk = 0; kk < kKr / 16; ++kk)
+        for (int c8 = 0; c8 < kCw / 8; ++c8) {
+          if (c8 >= c8n) break;   // warp-uniform
+          float hi[8], lo[8];
+          tmem_ld8x2(ta0 + c8 * 8, ta0 + kN + c8 * 8, hi, lo);   // levels 0 and 1
 #pragma unroll
-          for (int i = 0; i < S; ++i)
-            mma_bf16(tacc + i * kN, da0 + (uint64_t)((i * kABytes + kk * 256) >> 4),
-                     db0 + (uint64_t)((kk * 256) >> 4), idesc((S - i) * kN),
-                     (i == 0 && kk == 0) ? acc0 : 1u);
-        commit(smem_u32(&empty[st]));
-        if (last) commit(smem_u32(&acc_full[set]));
-        mmas = (int)(c + 1);
-      }
-    }
-  } else {  // epilogue warps: flush the levels every kFlush chunks
-    const int quarter = warp & 3, half = (warp - 2) / 4, ew = warp - 2;
-    // this thread's row exponent and its warp's column exponents, per flush group
-    const int* ea_g = (const int*)(scratch + L.ea_off) + (bb * L.tiles_m + tm) * L.groups * kMc +
-                      quarter * 32 + lane;
-    const int* eb_g = (const int*)(scratch + L.eb_off) + (bb * L.tiles_n + tn) * L.groups * kNc +
-                      half * (kNc / 2);
-    // blocks of 8 real columns of this warp that hold columns of C (a narrow step's last
-    // column block has fewer than kNc; the others are neither read nor combined)
-    const long long nv = s.N - tn * kNc;
-    const int cols = (int)max(0LL, min((long long)(kCw / 2), nv - half * (kCw / 2)));
-    const int c8n = (2 * cols + 7) / 8;
-    for (int g = 0; g < (int)ngroups; ++g) {
-      const int eam = ea_g[g * kMc];
-      if (lane < kNc / 2) eb_s[ew][lane] = eb_g[g * kNc + lane];
-      __syncwarp();
-      const int set = g % kSets;
-      if (!mbar_wait(smem_u32(&acc_full[set]), (uint32_t)((g / kSets) & 1), err)) {
-        if (lane == 0) {
-          bad = 1;
-          atomicOr(err, 1ull);
-        }
-        break;
-      }
-      fence_after();
-      // level L holds an integer sum of digit products (below 2^24 in magnitude) at weight
-      // 2^(-14-8L).  Per 8 columns: levels 0 and 1 are added exactly (TwoSum); levels 2 ..
-      // S-1, at most 2^-16 of level 0's scale, are folded into the low part with FP32 FMAs,
-      // whose rounding (below 2^-40 of level 0's scale) is under the digits' truncation.
-      // The sum is scaled by the group's 2^(e(m) + e(n) - 14) (powers of two: exact) and
-      // added to the float-float accumulators.
-      const uint32_t ta0 = tmem + (uint32_t)set * 256u + ((uint32_t)(quarter * 32) << 16) + half * kCw;
+          for (int i = 0; i < 8; ++i) two_sum(hi[i], lo[i] * 0.00390625f, hi[i], lo[i]);   // exact
 #pragma unroll
-      for (int c8 = 0; c8 < kCw / 8; ++c8) {
-        if (c8 >= c8n) break;   // warp-uniform
-        float hi[8], lo[8];
-        tmem_ld8x2(ta0 + c8 * 8, ta0 + kN + c8 * 8, hi, lo);   // levels 0 and 1
+          for (int lv = 2; lv < S; lv += 2) {
+            float v[8], v2[8];
+            const float w = __int_as_float((127 - 8 * lv) << 23);   // 2^(-8L) relative to level 0
+            if (lv + 1 < S) {
+              tmem_ld8x2(ta0 + lv * kN + c8 * 8, ta0 + (lv + 1) * kN + c8 * 8, v, v2);
+              const float w2 = w * 0.00390625f;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) two_sum(hi[i], lo[i] * 0.00390625f, hi[i], lo[i]);   // exact
-#pragma unroll
-        for (int lv = 2; lv < S; lv += 2) {
-          float v[8], v2[8];
-          const float w = __int_as_float((127 - 8 * lv) << 23);   // 2^(-8L) relative to level 0
-          if (lv + 1 < S) {
-            tmem_ld8x2(ta0 + lv * kN + c8 * 8, ta0 + (lv + 1) * kN + c8 * 8, v, v2);
-            const float w2 = w * 0.00390625f;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) lo[i] = fmaf(v2[i], w2, fmaf(v[i], w, lo[i]));
-          } else {
-            tmem_ld8(ta0 + lv * kN + c8 * 8, v);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) lo[i] = fmaf(v[i], w, lo[i]);
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 8; i += 2) {
-          float f1, f2;   // one exponent per complex column: (re, im) = columns i, i + 1
-          pow2_pair(eam - 14 + eb_s[ew][(c8 * 8 + i) >> 1], f1, f2);
-#pragma unroll
-          for (int u = i; u < i + 2; ++u) {
-            const float h = (hi[u] * f1) * f2, l = (lo[u] * f1) * f2;
-            if (g == 0) {   // the first group starts the sums (a float pair, not renormalised)
-              acc_h[c8 * 8 + u] = h;
-              acc_l[c8 * 8 + u] = l;
+              for (int i = 0; i < 8; ++i) lo[i] = fmaf(v2[i], w2, fmaf(v[i], w, lo[i]));
             } else {
-              ff_acc(acc_h[c8 * 8 + u], acc_l[c8 * 8 + u], h, l);
+              tmem_ld8(ta0 + lv * kN + c8 * 8, v);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) lo[i] = fmaf(v[i], w, lo[i]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            float f1, f2;   // one exponent per complex column: (re, im) = columns i, i + 1
+            pow2_pair(eam - 14 + eb_s[ew][(c8 * 8 + i) >> 1], f1, f2);
+#pragma unroll
+            for (int u = i; u < i + 2; ++u) {
+              const float h = (hi[u] * f1) * f2, l = (lo[u] * f1) * f2;
+              if (g == 0) {   // the first group starts the sums (a float pair, not renormalised)
+                acc_h[c8 * 8 + u] = h;
+                acc_l[c8 * 8 + u] = l;
+              } else {
+                ff_acc(acc_h[c8 * 8 + u], acc_l[c8 * 8 + u], h, l);
+              }
             }
           }
         }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[set]));
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[set]));
+      // ---- store the tile (the accumulators are released: the next tile's MMAs run):
+      // scaled by the step's normalisation; this thread's columns hold the (re, im) pairs
+      // of kCw / 2 complex columns of its row.  A tile whose wait gave up is written as NaN.
+      Cx<ff>* C = arena + s.off_c;
+#pragma unroll
+      for (int j = 0; j < kCw / 2; ++j) {
+        ff re = ff_norm(acc_h[2 * j], acc_l[2 * j]), im = ff_norm(acc_h[2 * j + 1], acc_l[2 * j + 1]);
+        re.hi *= scale;
+        re.lo *= scale;
+        im.hi *= scale;
+        im.lo *= scale;
+        if (failed) re.hi = re.lo = im.hi = im.lo = __int_as_float(0x7fc00000);
+        const long long cc = cn_s[ew][j];
+        if (crow >= 0 && cc >= 0) {
+          const Cx<ff> out{re, im};
+          st(C + crow + cc, out);
+          vmax = fmaxf(vmax, mag(out));
+        }
+      }
+      __syncwarp();   // cn_s of this tile read before the next tile's offsets replace it
     }
   }
   __syncthreads();
 
-  // ---- give-up path: before the tile is written and the tensor memory freed, wait (with
-  // the same bound, ignoring the error word) for this CTA's asynchronous work in flight:
-  // the bulk copies of the last chunk issued on each stage, and every MMA issued (one more
-  // commit tracks all of them).  If even these waits run out, the CTA exits regardless.
+  // ---- give-up path: before the tensor memory is freed, wait (with the same bound,
+  // ignoring the error word) for this CTA's asynchronous work in flight: the bulk copies of
+  // the last chunk issued on each stage, and every MMA issued (one more commit tracks all
+  // of them).  If even these waits run out, the CTA exits regardless.
   if (bad) {
     if (warp == 0 && lane == 0)
       for (int c = issued > kSt ? issued - kSt : 0; c < issued; ++c)
@@ -696,30 +742,6 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
     fence_before();
     __syncthreads();
     fence_after();
-  }
-
-  // ---- store: scale by 2^(e(m) + e(n)) and the step's normalisation; this thread's TMEM
-  // lane is complex row m, its columns hold (re, im) of kCw / 2 complex columns
-  float vmax = 0;
-  if (warp >= 2) {
-    const int quarter = warp & 3, half = (warp - 2) / 4;
-    const int m = quarter * 32 + lane;
-    Cx<ff>* C = arena + s.off_c + cbase;
-#pragma unroll
-    for (int j = 0; j < kCw / 2; ++j) {
-      const int n = half * (kCw / 2) + j;
-      ff re = ff_norm(acc_h[2 * j], acc_l[2 * j]), im = ff_norm(acc_h[2 * j + 1], acc_l[2 * j + 1]);
-      re.hi *= scale;
-      re.lo *= scale;
-      im.hi *= scale;
-      im.lo *= scale;
-      if (bad) re.hi = re.lo = im.hi = im.lo = __int_as_float(0x7fc00000);
-      if (cm[m] >= 0 && cn[n] >= 0) {
-        const Cx<ff> out{re, im};
-        st(C + cm[m] + cn[n], out);
-        vmax = fmaxf(vmax, mag(out));
-      }
-    }
   }
   block_max_to_meta(vmax, meta + s.c);
   fence_before();

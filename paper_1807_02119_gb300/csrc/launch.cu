@@ -228,14 +228,17 @@ cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* t
            gpu_fill(nA + nB, 8));
   k_digits<S><<<(unsigned)(nA + nB), tc::kConvThreads, tc::Cfg<S>::kConvSmem, stream>>>(s, arena, tcs, nA);
   mk.end();
+  // persistent: at most one CTA per tile slot of the GPU, each looping over its tiles
   const long long tc_tiles = L.tiles_m * L.tiles_n * s.Bsz;
   if (db_groups > 0 && L.groups >= db_groups) {   // one CTA per SM, two accumulator sets
-    mk.begin(5, cm, by, gpu_fill(tc_tiles, 1));
-    k_gemm_tc<S, true><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<S>::kSmemDB, stream>>>(
+    const long long grid = std::min<long long>(tc_tiles, (long long)g_sms);
+    mk.begin(5, cm, by, gpu_fill(grid, 1));
+    k_gemm_tc<S, true><<<(unsigned)grid, tc::kThreads, tc::Cfg<S>::kSmemDB, stream>>>(
         s, arena, meta, tcs, err);
   } else {
-    mk.begin(5, cm, by, gpu_fill(tc_tiles, 2));
-    k_gemm_tc<S, false><<<(unsigned)tc_tiles, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(
+    const long long grid = std::min<long long>(tc_tiles, 2LL * g_sms);
+    mk.begin(5, cm, by, gpu_fill(grid, 2));
+    k_gemm_tc<S, false><<<(unsigned)grid, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(
         s, arena, meta, tcs, err);
   }
   mk.end();
