@@ -170,6 +170,9 @@ typedef struct {
                                 candidate orders are ranked                                    */
   int64_t cost_out_milli;    /* planner: cost of one output entry of a step (its store and
                                 normalisation), in thousandths of a multiply-add (0..100000)  */
+  int64_t tc_wide_n;         /* PK_SPLIT: row steps of GEMM shape with K >= 4 (below tc_min_k)
+                                also run on the tensor cores when they have at least this many
+                                columns (16..2^30; 2^30: never)                               */
 } pk_tuning;
 
 pk_status pk_tuning_default(pk_tuning* out);

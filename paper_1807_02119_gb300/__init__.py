@@ -63,7 +63,8 @@ class pk_tuning(C.Structure):
     _fields_ = [("batch_threads", C.c_int32), ("batch_ktab", C.c_int32), ("seq_outs", C.c_int64),
                 ("seq_work", C.c_int64), ("seq_k", C.c_int64), ("tc_min_k", C.c_int64),
                 ("tc_db_groups", C.c_int64), ("tc_min_n", C.c_int64),
-                ("cost_gemm_milli", C.c_int64), ("cost_out_milli", C.c_int64)]
+                ("cost_gemm_milli", C.c_int64), ("cost_out_milli", C.c_int64),
+                ("tc_wide_n", C.c_int64)]
 
 
 class pk_plan_stats(C.Structure):

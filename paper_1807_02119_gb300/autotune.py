@@ -46,8 +46,10 @@ TC_DB_GROUPS = (0, 2, 3, 4, 6)
 TC_MIN_N = (8, 12, 16, 24, 32)
 COST_GEMM = (50, 100, 150, 250, 400)
 COST_OUT = (1000, 2000, 4000, 8000)
-SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_min_n": TC_MIN_N, "tc_db_groups": TC_DB_GROUPS,
-                "cost_gemm_milli": COST_GEMM, "cost_out_milli": COST_OUT}
+TC_WIDE_N = (100, 500, 1 << 30)
+SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_min_n": TC_MIN_N, "tc_wide_n": TC_WIDE_N,
+                "tc_db_groups": TC_DB_GROUPS, "cost_gemm_milli": COST_GEMM,
+                "cost_out_milli": COST_OUT}
 
 
 def _rel(a, b):
@@ -181,6 +183,7 @@ PARAM_TITLES = {
     "tc_min_n": "Tensor cores for row steps of GEMM shape from this many columns",
     "cost_gemm_milli": "Planner: cost of a tensor-core multiply-add (thousandths of a row one)",
     "cost_out_milli": "Planner: cost of an output entry (thousandths of a multiply-add)",
+    "tc_wide_n": "Tensor cores for short-K (4 <= K < tc_min_k) row steps from this many columns",
 }
 
 
@@ -203,7 +206,8 @@ def write_table(path, tune, batch_rows, seq_rows, gpu, param_rows):
               "constexpr pk_tuning kTunedDefault = {" +
               f"{tune['batch_threads']}, {tune['batch_ktab']}, {tune['seq_outs']}, "
               f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}, {tune['tc_db_groups']}, "
-              f"{tune['tc_min_n']}, {tune['cost_gemm_milli']}, {tune['cost_out_milli']}" +
+              f"{tune['tc_min_n']}, {tune['cost_gemm_milli']}, {tune['cost_out_milli']}, "
+              f"{tune['tc_wide_n']}" +
               "};", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))

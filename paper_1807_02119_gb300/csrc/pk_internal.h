@@ -344,13 +344,13 @@ pk_status decode_total(const Plan& P, const SliceResult& r, pk_scaled* Z, pk_sca
 // Step descriptor for C = sum over the indices of X and Y that are not in `out` of X Y
 // (Y absent: the constant 1).  `a` is the operand with more indices (ties: X); the
 // result's layout is written to `cdims`.
-// tc_min_k, tc_min_n: split precision, row steps of GEMM shape (M >= 64) with K >= tc_min_k
-// and N >= tc_min_n also go to
+// tc_min_k, tc_min_n, tc_wide_n: split precision, row steps of GEMM shape (M >= 64) with
+// N >= tc_min_n and either K >= tc_min_k or (K >= 4 and N >= tc_wide_n) also go to
 // the tensor cores (Step::tc).
 bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
                 bool& swapped, std::vector<int32_t>& cdims, std::string& err, int64_t tc_min_k = 16,
-                int64_t tc_min_n = 32);
+                int64_t tc_min_n = 32, int64_t tc_wide_n = (int64_t)1 << 30);
 bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuning& tune, Plan& p,
                std::string& err);
 // Order search only (no slicing, no step records): out[0] largest tensor rank, out[1] log2

@@ -812,9 +812,9 @@ double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& se
           ++k;
       }
     const double macs = std::pow((double)q, (double)union_size(sa, sb));
-    const bool gemm = pr.second >= 0 && std::pow((double)q, m) >= 64 &&
-                      std::pow((double)q, n) >= (double)tune.tc_min_n &&
-                      std::pow((double)q, k) >= (double)tune.tc_min_k;
+    const double nq = std::pow((double)q, n), kq = std::pow((double)q, k);
+    const bool gemm = pr.second >= 0 && std::pow((double)q, m) >= 64 && nq >= (double)tune.tc_min_n &&
+                      (kq >= (double)tune.tc_min_k || (kq >= 4 && nq >= (double)tune.tc_wide_n));
     c += macs * (gemm ? w_gemm : 1.0) + w_out * std::pow((double)q, (double)sc.size());
   }
   return c;
@@ -826,7 +826,7 @@ double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& se
 bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
                 bool& swapped, std::vector<int32_t>& cdims, std::string& err, int64_t tc_min_k,
-                int64_t tc_min_n) {
+                int64_t tc_min_n, int64_t tc_wide_n) {
   static const std::vector<int32_t> no_dims;
   swapped = yd != nullptr && yd->size() > xd.size();
   const bool hasb = yd != nullptr;
@@ -982,7 +982,7 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
   // kernel more float-float work than the tensor cores' epilogue (complex64 and complex128
   // keep the row kernel for them)
   const bool short_k = hasb && st.kernel == KROWS && !(flags & PK_FLAG_FORCE_ROWS) && st.M >= 64 &&
-                       st.N >= tc_min_n && st.K >= tc_min_k;
+                       st.N >= tc_min_n && (st.K >= tc_min_k || (st.K >= 4 && st.N >= tc_wide_n));
   st.tc = ((st.kernel == KGEMM || short_k) && !(flags & PK_FLAG_NO_TC))
               ? ((flags & PK_FLAG_TC_DIGITS4) ? 4 : 5)
               : 0;
@@ -996,7 +996,8 @@ bool valid_tuning(const pk_tuning& t) {
          t.seq_work >= 1 && t.seq_work <= (1 << 24) && t.seq_k >= 1 && t.seq_k <= kTinyK &&
          t.tc_min_k >= 4 && t.tc_min_k <= 16 && t.tc_db_groups >= 0 && t.tc_db_groups <= 4096 &&
          t.tc_min_n >= 8 && t.tc_min_n <= 32 && t.cost_gemm_milli >= 10 &&
-         t.cost_gemm_milli <= 1000 && t.cost_out_milli >= 0 && t.cost_out_milli <= 100000;
+         t.cost_gemm_milli <= 1000 && t.cost_out_milli >= 0 && t.cost_out_milli <= 100000 &&
+         t.tc_wide_n >= 16 && t.tc_wide_n <= ((int64_t)1 << 30);
 }
 
 void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,
@@ -1235,7 +1236,8 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
     Step st;
     bool sw = false;
     if (!build_step(p.tensors[x].dims, y >= 0 ? &p.tensors[y].dims : nullptr, sets[cid], q,
-                    opts.flags, st, sw, p.tensors[cid].dims, err, tune.tc_min_k, tune.tc_min_n))
+                    opts.flags, st, sw, p.tensors[cid].dims, err, tune.tc_min_k, tune.tc_min_n,
+                    tune.tc_wide_n))
       return false;
     st.a = sw ? y : x;
     st.b = sw ? x : y;

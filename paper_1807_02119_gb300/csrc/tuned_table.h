@@ -61,7 +61,14 @@
 //   cost_out_milli  = 2000     53.70
 //   cost_out_milli  = 4000     52.79
 //   cost_out_milli  = 8000     52.57
+// After the persistent tensor-core GEMM (median ms per step, 9 replays):
+//   tc_min_k = 4 / 8 / 16:            49.40 / 50.21 / 48.28
+//   tc_db_groups = 0 / 2 / 3 / 4 / 6: 49.63 / 54.46 / 55.23 / 53.26 / 56.95
+// Tensor cores for short-K (4 <= K < tc_min_k) row steps from this many columns:
+//   tc_wide_n =  100     48.04
+//   tc_wide_n =  500     48.26
+//   tc_wide_n = never    50.07
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12, 150, 8000};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12, 150, 8000, 100};
