@@ -68,6 +68,8 @@
 //   tc_wide_n =  100     48.04
 //   tc_wide_n =  500     48.26
 //   tc_wide_n = never    50.07
+//   again: 16 / 25 / 50 / 100 / never: 48.96 / 49.26 / 47.72 / 48.45 / 50.73 (50 and 100
+//   differ only by a few q = 3 steps with N = 81: within run-to-run noise; 100 kept)
 #pragma once
 #include "pk.h"
 
