@@ -451,10 +451,14 @@ __global__ void __launch_bounds__(tc::kConvThreads, 4) k_digits(const Step s, co
 }
 
 // C tiles (128 complex rows x 24 complex columns of one batch index) from the digit
-// chunks, persistently: CTA b takes tiles b, b + gridDim.x, ... (column blocks fastest, so
-// the CTAs busy at one time share their A row blocks in L2).  Warp 0 streams the chunks of
-// its tiles into the stage ring, warp 1 issues the MMAs, warps 2..9 flush the level
-// accumulators and store C.  The ring's and the accumulators' barrier phases run on across
+// chunks, persistently (column blocks fastest: tiles in flight together share their A row
+// blocks in L2).  Q = true: the producer of each CTA takes its next tile from the step's
+// tile counter (`ticket`, zero at launch) and passes it to the MMA issuer and the epilogue
+// through a small queue in shared memory, so the tiles in flight on the GPU stay a window
+// of consecutive tiles however unevenly the CTAs progress (best for short tiles).
+// Q = false: CTA b takes tiles b, b + gridDim.x, ..., each role computing them itself (no
+// hand-over between the roles; measured faster for tiles with many flush groups).  Warp 0 streams the chunks of its tiles into the stage ring, warp 1 issues the MMAs,
+// warps 2..9 flush the level accumulators and store C.  The ring's and the accumulators' barrier phases run on across
 // tiles: the producer loads the next tile's chunks while the current one is multiplied and
 // flushed, and the epilogue stores a tile from its registers after releasing the
 // accumulators, while the next tile's MMAs run; barriers and tensor memory are set up once.
@@ -463,13 +467,15 @@ __global__ void __launch_bounds__(tc::kConvThreads, 4) k_digits(const Step s, co
 // DB = true: one CTA per SM, a 4-stage ring and two accumulator sets in TMEM (columns 0
 // and 256), used by alternate flush groups, so the flush of group g overlaps the MMAs of
 // group g + 1.
-template <int S, bool DB>
+template <int S, bool DB, bool Q>
 __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step s, Cx<ff>* arena,
                                                                       Meta* meta,
                                                                       const unsigned char* scratch,
+                                                                      unsigned* ticket,
                                                                       unsigned long long* err) {
   using namespace tc;
   constexpr int kSt = DB ? kStagesDB : kStages;     // stages of the ring
+  constexpr int kTq = 4;                            // tile queue: tiles handed out ahead
   constexpr int kSets = DB ? 2 : 1;                 // accumulator sets
   constexpr uint32_t kCols = DB ? 512u : (uint32_t)Cfg<S>::kCols;
   constexpr int kFlush = Cfg<S>::kFlush;
@@ -478,7 +484,8 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
   __shared__ long long cn_s[kEpiWarps][kNc / 2];   // per epilogue warp: its columns' C offsets
   __shared__ int eb_s[kEpiWarps][kNc / 2];         // ... and their group exponents
   __shared__ __align__(8) unsigned long long full[kSt], empty[kSt], acc_full[kSets],
-      acc_empty[kSets], drain;
+      acc_empty[kSets], drain, tq_full[kTq], tq_empty[kTq];
+  __shared__ int tq[kTq];   // tile indices handed out (-1: no tiles left)
   __shared__ uint32_t tmem_slot;
   __shared__ int bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -496,6 +503,10 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
       mbar_init(smem_u32(&acc_empty[i]), kEpiWarps);
     }
     mbar_init(smem_u32(&drain), 1);
+    for (int i = 0; i < kTq; ++i) {
+      mbar_init(smem_u32(&tq_full[i]), 1);
+      mbar_init(smem_u32(&tq_empty[i]), 1 + kEpiWarps);   // the MMA issuer and 8 epilogue warps
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -529,7 +540,23 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
   if (warp == 0) {
     if (lane == 0) {  // producer
       long long gc = 0;   // chunks of this CTA so far (all its tiles)
-      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      for (int i = 0;; ++i) {
+        long long t;
+        if constexpr (Q) {   // hand out the next tile (or the end) through queue slot i mod kTq
+          const int slot = i % kTq;
+          if (i >= kTq &&
+              !mbar_wait(smem_u32(&tq_empty[slot]), (uint32_t)(((i / kTq) - 1) & 1), err)) {
+            bad = 1;
+            atomicOr(err, 1ull);
+            goto producer_done;
+          }
+          t = (long long)atomicAdd(ticket, 1u);
+          tq[slot] = t < ntiles ? (int)t : -1;
+          mbar_arrive(smem_u32(&tq_full[slot]));
+        } else {
+          t = (long long)blockIdx.x + (long long)i * gridDim.x;
+        }
+        if (t >= ntiles) break;
         long long bb, tm, tn;
         tile_coords(t, bb, tm, tn);
         const unsigned char* asrc =
@@ -557,7 +584,20 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       long long gc = 0, gg = 0;   // chunks and flush groups of this CTA so far
-      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      for (int i = 0;; ++i) {
+        if constexpr (Q) {
+          const int slot = i % kTq;
+          if (!mbar_wait(smem_u32(&tq_full[slot]), (uint32_t)((i / kTq) & 1), err)) {
+            bad = 1;
+            atomicOr(err, 1ull);
+            goto mma_done;
+          }
+          const int t = tq[slot];
+          mbar_arrive(smem_u32(&tq_empty[slot]));
+          if (t < 0) break;
+        } else {
+          if ((long long)blockIdx.x + (long long)i * gridDim.x >= ntiles) break;
+        }
         for (long long c = 0; c < nchunks; ++c, ++gc) {
           const int st = (int)(gc % kSt);
           const int set = (int)(gg % kSets);
@@ -605,7 +645,24 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
     const int quarter = warp & 3, half = (warp - 2) / 4, ew = warp - 2;
     int gg = 0;   // flush groups of this CTA so far (tiles and chunks per step < 2^31)
     bool failed = false;
-    for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    // i: tiles of this CTA so far; t: the tile (tiles per step < 2^31)
+    for (int i = 0, t = (int)blockIdx.x; !failed; ++i, t += (int)gridDim.x) {
+      if constexpr (Q) {
+        const int slot = i % kTq;
+        if (!mbar_wait(smem_u32(&tq_full[slot]), (uint32_t)((i / kTq) & 1), err)) {
+          if (lane == 0) {
+            bad = 1;
+            atomicOr(err, 1ull);
+          }
+          break;
+        }
+        t = tq[slot];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tq_empty[slot]));
+        if (t < 0) break;
+      } else {
+        if (t >= ntiles) break;
+      }
       long long bb, tm, tn;
       tile_coords(t, bb, tm, tn);
       // this thread's row of C (lane = row within the lane quarter) and, per lane j < 12,

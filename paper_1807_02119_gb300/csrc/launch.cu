@@ -213,13 +213,14 @@ cudaError_t launch_rows(const Step& s, Cx<R>* arena, Meta* meta, cudaStream_t st
   return cudaGetLastError();
 }
 
-// One contraction step; `counter` is its split-K ticket, `by` its algorithmic bytes
+// One contraction step; `counter` is its split-K ticket or its tensor-core tile counter
+// (zeroed with the bookkeeping before every slice), `by` its algorithmic bytes
 // (for the optional timing only).
 // Digit conversion of both operands, then the tensor-core GEMM, for S digits.
 template <int S>
 cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* tcs,
-                      unsigned long long* err, cudaStream_t stream, Marker& mk, double cm, double by,
-                      int64_t db_groups) {
+                      unsigned* ticket, unsigned long long* err, cudaStream_t stream, Marker& mk,
+                      double cm, double by, int64_t db_groups) {
   const TcScratch L = tc_scratch(s.Bsz, s.M, s.N, s.K, S);
   // class 6 (digit conversion): its bytes are the operands it reads, |A| + |B|
   const long long nA = (tc::kMc / 32) * s.Bsz * L.tiles_m * L.groups,
@@ -228,18 +229,28 @@ cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* t
            gpu_fill(nA + nB, 8));
   k_digits<S><<<(unsigned)(nA + nB), tc::kConvThreads, tc::Cfg<S>::kConvSmem, stream>>>(s, arena, tcs, nA);
   mk.end();
-  // persistent: at most one CTA per tile slot of the GPU, each looping over its tiles
+  // persistent: at most one CTA per tile slot of the GPU, each looping over its tiles;
+  // tiles of steps with at most two flush groups come from the tile counter
   const long long tc_tiles = L.tiles_m * L.tiles_n * s.Bsz;
+  const bool q = L.groups <= 2;
   if (db_groups > 0 && L.groups >= db_groups) {   // one CTA per SM, two accumulator sets
     const long long grid = std::min<long long>(tc_tiles, (long long)g_sms);
     mk.begin(5, cm, by, gpu_fill(grid, 1));
-    k_gemm_tc<S, true><<<(unsigned)grid, tc::kThreads, tc::Cfg<S>::kSmemDB, stream>>>(
-        s, arena, meta, tcs, err);
+    if (q)
+      k_gemm_tc<S, true, true><<<(unsigned)grid, tc::kThreads, tc::Cfg<S>::kSmemDB, stream>>>(
+          s, arena, meta, tcs, ticket, err);
+    else
+      k_gemm_tc<S, true, false><<<(unsigned)grid, tc::kThreads, tc::Cfg<S>::kSmemDB, stream>>>(
+          s, arena, meta, tcs, ticket, err);
   } else {
     const long long grid = std::min<long long>(tc_tiles, 2LL * g_sms);
     mk.begin(5, cm, by, gpu_fill(grid, 2));
-    k_gemm_tc<S, false><<<(unsigned)grid, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(
-        s, arena, meta, tcs, err);
+    if (q)
+      k_gemm_tc<S, false, true><<<(unsigned)grid, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(
+          s, arena, meta, tcs, ticket, err);
+    else
+      k_gemm_tc<S, false, false><<<(unsigned)grid, tc::kThreads, tc::Cfg<S>::kSmem, stream>>>(
+          s, arena, meta, tcs, ticket, err);
   }
   mk.end();
   return cudaGetLastError();
@@ -255,8 +266,9 @@ cudaError_t launch_step(const Step& s, Cx<R>* arena, Meta* meta, Cx<double>* par
   cudaError_t e;
   if constexpr (std::is_same<R, ff>::value) {
     if (s.tc && tc_scratch && err)  // digits of A and B, then the tensor-core GEMM
-      return s.tc == 4 ? launch_tc<4>(s, arena, meta, tc_scratch, err, stream, mk, cm, by, db_groups)
-                       : launch_tc<5>(s, arena, meta, tc_scratch, err, stream, mk, cm, by, db_groups);
+      return s.tc == 4
+                 ? launch_tc<4>(s, arena, meta, tc_scratch, counter, err, stream, mk, cm, by, db_groups)
+                 : launch_tc<5>(s, arena, meta, tc_scratch, counter, err, stream, mk, cm, by, db_groups);
   }
   if (s.kernel == KGEMM && gemm_tiles < (1LL << 31)) {
     mk.begin(4, cm, by, gpu_fill(gemm_tiles, 8));
@@ -517,21 +529,22 @@ cudaError_t raise_rows_smem() {
   return cudaFuncSetAttribute(k_outs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
+template <int S, bool DB, bool Q>
+cudaError_t prepare_gemm_tc() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<S, DB, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       DB ? tc::Cfg<S>::kSmemDB : tc::Cfg<S>::kSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm_tc<S, DB, Q>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
+}
+
 template <int S>
 cudaError_t prepare_tc() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_gemm_tc<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::Cfg<S>::kSmem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_gemm_tc<S, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_gemm_tc<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::Cfg<S>::kSmemDB)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_gemm_tc<S, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
-    return e;
+  if ((e = prepare_gemm_tc<S, false, false>()) != cudaSuccess) return e;
+  if ((e = prepare_gemm_tc<S, false, true>()) != cudaSuccess) return e;
+  if ((e = prepare_gemm_tc<S, true, false>()) != cudaSuccess) return e;
+  if ((e = prepare_gemm_tc<S, true, true>()) != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_digits<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               tc::Cfg<S>::kConvSmem);
 }
