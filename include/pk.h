@@ -169,7 +169,7 @@ typedef struct {
                                 thousandths of a row-kernel multiply-add (10..1000), when the
                                 candidate orders are ranked                                    */
   int64_t cost_out_milli;    /* planner: cost of one output entry of a step (its store and
-                                normalisation), in thousandths of a multiply-add (0..100000)  */
+                                normalisation), in thousandths of a multiply-add (0..10^6)    */
   int64_t tc_wide_n;         /* PK_SPLIT: row steps of GEMM shape with K >= 4 (below tc_min_k)
                                 also run on the tensor cores when they have at least this many
                                 columns (16..2^30; 2^30: never)                               */

@@ -45,7 +45,7 @@ TC_MIN_K = (4, 8, 16)
 TC_DB_GROUPS = (0, 2, 3, 4, 6)
 TC_MIN_N = (8, 12, 16, 24, 32)
 COST_GEMM = (50, 100, 150, 250, 400)
-COST_OUT = (1000, 2000, 4000, 8000)
+COST_OUT = (1000, 2000, 4000, 8000, 16000, 32000, 64000, 128000, 256000)
 TC_WIDE_N = (16, 25, 50, 100, 1 << 30)
 SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_min_n": TC_MIN_N, "tc_wide_n": TC_WIDE_N,
                 "tc_db_groups": TC_DB_GROUPS, "cost_gemm_milli": COST_GEMM,

@@ -996,7 +996,7 @@ bool valid_tuning(const pk_tuning& t) {
          t.seq_work >= 1 && t.seq_work <= (1 << 24) && t.seq_k >= 1 && t.seq_k <= kTinyK &&
          t.tc_min_k >= 4 && t.tc_min_k <= 16 && t.tc_db_groups >= 0 && t.tc_db_groups <= 4096 &&
          t.tc_min_n >= 8 && t.tc_min_n <= 32 && t.cost_gemm_milli >= 10 &&
-         t.cost_gemm_milli <= 1000 && t.cost_out_milli >= 0 && t.cost_out_milli <= 100000 &&
+         t.cost_gemm_milli <= 1000 && t.cost_out_milli >= 0 && t.cost_out_milli <= 1000000 &&
          t.tc_wide_n >= 16 && t.tc_wide_n <= ((int64_t)1 << 30);
 }
 

@@ -70,7 +70,13 @@
 //   tc_wide_n = never    50.07
 //   again: 16 / 25 / 50 / 100 / never: 48.96 / 49.26 / 47.72 / 48.45 / 50.73 (50 and 100
 //   differ only by a few q = 3 steps with N = 81: within run-to-run noise; 100 kept)
+// Planner weights again after the persistent GEMM (median ms per step, 9 replays):
+//   cost_gemm_milli = 50 / 100 / 150 / 250 / 400:  48.40 / 48.91 / 48.02 / 48.62 / 49.50
+//   cost_out_milli = 1000 / 2000 / 4000 / 8000 / 16000 / 32000:
+//                    49.83 / 49.91 / 48.35 / 48.64 / 48.26 / 47.74
+//   cost_out_milli = 16000 / 32000 / 64000 / 128000 / 256000:
+//                    49.33 / 47.89 / 48.28 / 48.97 / 48.81
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12, 150, 8000, 100};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12, 150, 32000, 100};
