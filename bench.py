@@ -278,12 +278,12 @@ CLASS_KERNEL = {"build": "k_build", "rows": "k_rows / k_outs / k_seg (fused perm
 # divided by that launch's algorithmic bytes as the library counts them (its storage type,
 # 16 bytes per complex entry in split): the multiple applied to a class's average launch.
 # Sources (the heaviest launch of each class in the workload): tensor-core GEMM
-# profiles/k_gemm_tc_split_q5_seed53.md (2.774 GB against (48.8 M + 9.8 M + 48.8 M) x 16 B),
+# profiles/k_gemm_tc_split_q5_seed53.md (3.532 GB against (48.8 M + 9.8 M + 48.8 M) x 16 B),
 # digits profiles/k_digits_split_q5_seed53.md (2.432 GB against the operands it reads,
-# (48.8 M + 9.8 M) x 16 B), rows profiles/k_rows_split_q5_seed53.md (0.739 GB against
-# (0.39 M + 0.08 M + 48.8 M) x 16 B).
-NCU_TRAFFIC_RATIO = {"gemm_tc": 2.774273 / 1.71875, "digits": 2.431523 / 0.9375,
-                     "rows": 0.738859 / 0.78875}
+# (48.8 M + 9.8 M) x 16 B), rows profiles/k_rows_split_q5_seed53.md (1.520 GB against
+# (48.8 M + 25 + 48.8 M) x 16 B).
+NCU_TRAFFIC_RATIO = {"gemm_tc": 3.531654 / 1.71875, "digits": 2.431405 / 0.9375,
+                     "rows": 1.519674 / 1.5625}
 
 
 def roofline_blocks(classes, prec, pk_, instep=None):
