@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle baseline")
     ap.add_argument("--skip-extra", action="store_true",
                     help="omit the batch and grad workloads of the default line")
-    ap.add_argument("--restarts", type=int, default=128,
+    ap.add_argument("--restarts", type=int, default=256,
                     help="min-fill restarts per plan (planning effort; plans are built once, "
                          "before the timed region, on all host cores)")
     ap.add_argument("--workload", default="scale", choices=["scale", "batch", "large"],

@@ -36,6 +36,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 TABLE = os.path.join(HERE, "csrc", "tuned_table.h")
+RESTARTS = 256   # min-fill restarts per plan of the scale workload, as bench.py builds them
 
 BATCH_THREADS = (128, 256, 512)
 BATCH_KTAB = (512, 1024, 2048)
@@ -121,7 +122,7 @@ def sweep_seq(pk, ctx, stream, flush, reps, log, quick):
         for sw in works:
             ctx.set_tuning(seq_outs=so, seq_work=sw)
             with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-                plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=128), jobs))
+                plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=RESTARTS), jobs))
             ws = [torch.empty(p.workspace_bytes("split") + 256, dtype=torch.uint8, device="cuda")
                   for p in plans]
             for p, w in zip(plans, ws):
@@ -157,7 +158,7 @@ def sweep_scale_param(pk, ctx, stream, flush, reps, log, name):
     for tk in SCALE_PARAMS[name]:
         ctx.set_tuning(**{**ctx.tuning(), name: tk})
         with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-            plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=128), jobs))
+            plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=RESTARTS), jobs))
         ws = [torch.empty(p.workspace_bytes("split") + 256, dtype=torch.uint8, device="cuda")
               for p in plans]
         for p, w in zip(plans, ws):
