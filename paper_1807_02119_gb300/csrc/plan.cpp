@@ -854,6 +854,41 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
     int32_t pp = pos_in(bd, v);
     return pp < 0 ? 0 : qpow(rb - 1 - pp);
   };
+  // The kernel class follows from the shape alone (extents of the batch, m, n and
+  // contracted indices), so it is decided before the layout: steps that run as GEMMs (the
+  // tensor cores in split precision, the tiled CUDA-core GEMM otherwise) put the m indices
+  // (free of B) innermost in C and the batch indices outside them, so that a tile's
+  // consecutive rows are consecutive in memory and its stores coalesce; other steps keep
+  // A's order.
+  int32_t n_m = 0, n_n = 0, n_k = 0;
+  for (int32_t v : ad) {
+    if (!in_c(v))
+      ++n_k;
+    else if (pos_in(bd, v) < 0)
+      ++n_m;
+  }
+  for (int32_t v : bd)
+    if (pos_in(ad, v) < 0) {
+      if (in_c(v))
+        ++n_n;
+      else
+        ++n_k;
+    }
+  const int64_t M0 = qpow(n_m), N0 = qpow(n_n), K0 = qpow(n_k);
+  const bool gemm_shape = hasb && !(flags & PK_FLAG_FORCE_ROWS) &&
+                          ((flags & PK_FLAG_FORCE_GEMM) || (M0 >= 64 && N0 >= 32 && K0 >= 16) ||
+                           (M0 >= 64 && N0 >= tc_min_n &&
+                            (K0 >= tc_min_k || (K0 >= 4 && N0 >= tc_wide_n))));
+  // row indices of A in C order, inner -> outer: A's order, or its m indices then its
+  // batch indices
+  std::vector<int32_t> row_order;
+  for (int pass = 0; pass < (gemm_shape ? 2 : 1); ++pass)
+    for (int32_t i = ra - 1; i >= 0; --i) {
+      const int32_t v = ad[i];
+      if (!in_c(v)) continue;
+      const bool batch = pos_in(bd, v) >= 0;
+      if (!gemm_shape || (pass == 0) != batch) row_order.push_back(v);
+    }
   std::vector<Run> rows, ks, ns;
   std::vector<int32_t> row_dims, n_dims;
   auto push = [&](std::vector<Run>& v, int64_t sa, int64_t sb) {
@@ -866,14 +901,13 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
     }
     v.push_back({(int64_t)q, sa, sb});
   };
+  for (int32_t v : row_order) {  // inner -> outer in C
+    push(rows, stride_a(v), stride_b(v));
+    row_dims.push_back(v);
+  }
   for (int32_t i = ra - 1; i >= 0; --i) {  // inner -> outer
-    int32_t v = ad[i];
-    if (in_c(v)) {
-      push(rows, stride_a(v), stride_b(v));
-      row_dims.push_back(v);
-    } else {
-      push(ks, stride_a(v), stride_b(v));
-    }
+    const int32_t v = ad[i];
+    if (!in_c(v)) push(ks, stride_a(v), stride_b(v));
   }
   for (int32_t i = rb - 1; i >= 0; --i) {
     int32_t v = bd[i];
@@ -910,7 +944,7 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
     st.nr[i] = ns[i];
     st.N *= ns[i].size;
   }
-  // C layout (outermost first): N dims (B order), then row dims (A order)
+  // C layout (outermost first): N dims (B order), then the row dims (row_order reversed)
   cdims.clear();
   for (int32_t i = (int32_t)n_dims.size() - 1; i >= 0; --i) cdims.push_back(n_dims[i]);
   for (int32_t i = (int32_t)row_dims.size() - 1; i >= 0; --i) cdims.push_back(row_dims[i]);
@@ -928,10 +962,8 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
       }
       v.push_back({(int64_t)q, sa, sb, sc});
     };
-    int64_t csr = 1;  // C stride of the next row dim (inner -> outer, A order)
-    for (int32_t i = ra - 1; i >= 0; --i) {
-      int32_t v = ad[i];
-      if (!in_c(v)) continue;
+    int64_t csr = 1;  // C stride of the next row dim (inner -> outer in C)
+    for (int32_t v : row_order) {
       if (pos_in(bd, v) >= 0)
         push4(gbv, stride_a(v), stride_b(v), csr);
       else
