@@ -346,15 +346,27 @@ __device__ __forceinline__ void digits_block(const Step& s, const Cx<ff>* arena,
   }
   if (tid < kRows) {
     const long long r = tile_i * (IS_A ? kMc : kNc) + r0 + tid;
-    long long a, b, c;
+    long long a, b, c, cc = -1;
     if (r < (IS_A ? s.M : s.N)) {
       if (IS_A)
         runs4(r, s.gm, s.ngm, a, b, c);
       else
         runs4(r, s.gn, s.ngn, a, b, c);
       ro[tid] = IS_A ? a : b;
+      cc = c;
     } else {
       ro[tid] = -1;
+    }
+    // the row's (column's) C offset for the GEMM's epilogue: once per row, by the first
+    // flush group (columns: by batch index 0, their offsets do not depend on it)
+    if (g == 0 && (IS_A || bb == 0)) {
+      if (IS_A && cc >= 0) {
+        long long a2, b2, cb;
+        runs4(bb, s.gb, s.ngb, a2, b2, cb);
+        cc += cb;
+      }
+      ((long long*)(scratch + (IS_A ? L.cr_off : L.cc_off)))
+          [IS_A ? (bb * tiles + tile_i) * kMc + r0 + tid : tile_i * kNc + tid] = cc;
     }
   }
   if (tid < kG) {
@@ -666,23 +678,11 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
       long long bb, tm, tn;
       tile_coords(t, bb, tm, tn);
       // this thread's row of C (lane = row within the lane quarter) and, per lane j < 12,
-      // its warp's column j
-      const long long m = tm * kMc + quarter * 32 + lane;
-      long long crow = -1;
-      {
-        long long a, b, cb, cr;
-        runs4(bb, s.gb, s.ngb, a, b, cb);
-        if (m < s.M) {
-          runs4(m, s.gm, s.ngm, a, b, cr);
-          crow = cb + cr;
-        }
-      }
-      if (lane < kNc / 2) {
-        const long long n = tn * kNc + half * (kNc / 2) + lane;
-        long long a, b, cc = -1;
-        if (n < s.N) runs4(n, s.gn, s.ngn, a, b, cc);
-        cn_s[ew][lane] = cc;
-      }
+      // its warp's column j: offsets from the digit kernel's tables (-1 past the edge)
+      const long long crow =
+          ((const long long*)(scratch + L.cr_off))[(bb * L.tiles_m + tm) * kMc + quarter * 32 + lane];
+      if (lane < kNc / 2)
+        cn_s[ew][lane] = ((const long long*)(scratch + L.cc_off))[tn * kNc + half * (kNc / 2) + lane];
       // this thread's row exponent and its warp's column exponents, per flush group
       const int* ea_g = (const int*)(scratch + L.ea_off) + (bb * L.tiles_m + tm) * L.groups * kMc +
                         quarter * 32 + lane;

@@ -200,9 +200,12 @@ PK_HD constexpr long long tc_b_chunk(int S) { return (long long)S * (2 * kTcNc) 
 // Chunks per flush group: the S digit pairs of a level, 2 kTcKc real terms per chunk and
 // digit products below 2^14 keep a level's FP32 sum exact (below 2^24) for this many chunks.
 PK_HD constexpr int tc_flush(int S) { return ((1 << 10) - 1) / (S * 2 * kTcKc); }
+// After the digits and exponents: the C offsets of every tile row (batch base included,
+// Bsz x tiles_m x kTcMc) and tile column (tiles_n x kTcNc), -1 past the edge, written by
+// the digit kernel for the GEMM's epilogue.
 struct TcScratch {
   long long tiles_m, tiles_n, chunks, groups;
-  long long a_off, b_off, ea_off, eb_off, bytes;
+  long long a_off, b_off, ea_off, eb_off, cr_off, cc_off, bytes;
 };
 PK_HD inline TcScratch tc_scratch(long long Bsz, long long M, long long N, long long K, int S) {
   TcScratch x;
@@ -214,7 +217,9 @@ PK_HD inline TcScratch tc_scratch(long long Bsz, long long M, long long N, long 
   x.b_off = x.a_off + Bsz * x.tiles_m * x.chunks * tc_a_chunk(S);
   x.ea_off = x.b_off + Bsz * x.tiles_n * x.chunks * tc_b_chunk(S);
   x.eb_off = x.ea_off + ((Bsz * x.tiles_m * x.groups * kTcMc * 4 + 255) & ~255LL);
-  x.bytes = x.eb_off + ((Bsz * x.tiles_n * x.groups * kTcNc * 4 + 255) & ~255LL);
+  x.cr_off = x.eb_off + ((Bsz * x.tiles_n * x.groups * kTcNc * 4 + 255) & ~255LL);
+  x.cc_off = x.cr_off + ((Bsz * x.tiles_m * kTcMc * 8 + 255) & ~255LL);
+  x.bytes = x.cc_off + ((x.tiles_n * kTcNc * 8 + 255) & ~255LL);
   return x;
 }
 
