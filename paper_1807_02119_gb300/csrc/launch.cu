@@ -226,7 +226,7 @@ cudaError_t launch_tc(const Step& s, Cx<ff>* arena, Meta* meta, unsigned char* t
   const long long nA = (tc::kMc / 32) * s.Bsz * L.tiles_m * L.groups,
                   nB = s.Bsz * L.tiles_n * L.groups;
   mk.begin(6, 0.0, (double)sizeof(Cx<ff>) * (double)(s.R * s.K + s.Bsz * s.K * s.N),
-           gpu_fill(nA + nB, 8));
+           gpu_fill(nA + nB, 4));   // 4 CTAs per SM (64 registers x 256 threads)
   k_digits<S><<<(unsigned)(nA + nB), tc::kConvThreads, tc::Cfg<S>::kConvSmem, stream>>>(s, arena, tcs, nA);
   mk.end();
   // persistent: at most one CTA per tile slot of the GPU, each looping over its tiles;
