@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle baseline")
     ap.add_argument("--skip-extra", action="store_true",
                     help="omit the batch and grad workloads of the default line")
+    ap.add_argument("--refine", type=int, default=8,
+                    help="subtree reconfiguration of the cheapest candidate orders, frontiers of "
+                         "up to this many subtrees (pk_plan_opts.refine; 0 = off)")
     ap.add_argument("--restarts", type=int, default=256,
                     help="min-fill restarts per plan (planning effort; plans are built once, "
                          "before the timed region, on all host cores)")
@@ -662,25 +665,29 @@ def main():
     ctx.set_stream(stream.cuda_stream)
     t0 = time.perf_counter()
     from concurrent.futures import ThreadPoolExecutor
+    # reconfiguration ranks sequences by the split precision's tensor-core cost model
+    refine = args.refine if args.precision == "split" else 0
+    args.refine = refine
     kn = [pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer) for gk in knots]
     jobs = [(k, q) for k in kn for q in qs]
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:   # planning is host C++
-        plans = list(ex.map(lambda kq: pk.Plan(ctx, kq[0], kq[1], restarts=args.restarts), jobs))
+        plans = list(ex.map(lambda kq: pk.Plan(ctx, kq[0], kq[1], restarts=args.restarts,
+                                                   refine=refine), jobs))
     plan_s = time.perf_counter() - t0
     log(f"planned {len(plans)} evaluations in {plan_s:.2f}s")
     stats = [p.stats() for p in plans]
     prec = args.precision
     dev = f"cuda:{local}"
 
-    def workspaces(pr):
+    def workspaces(pr, pl=plans):
         """A full workspace per plan (program uploaded, resident in HBM)."""
-        ws = [torch.empty(p.workspace_bytes(pr) + 256, dtype=torch.uint8, device=dev) for p in plans]
-        for p, w in zip(plans, ws):
+        ws = [torch.empty(p.workspace_bytes(pr) + 256, dtype=torch.uint8, device=dev) for p in pl]
+        for p, w in zip(pl, ws):
             pk.upload(p, pr, w)
         return ws
 
-    def results(pr, ws):
-        return [pk.download(p, pr, w) for p, w in zip(plans, ws)]
+    def results(pr, ws, pl=plans):
+        return [pk.download(p, pr, w) for p, w in zip(pl, ws)]
 
     # every plan's kernels recorded as an independent branch of one CUDA graph
     ws = workspaces(prec)
@@ -770,11 +777,19 @@ def main():
     compare = {}
     res_by = {prec: res_main}
     if not args.skip_compare:
+        # complex64 and complex128 keep GEMM-shaped row steps (N < 32) on the row kernel,
+        # where the reconfigured sequences (ranked by the tensor-core cost model) are slow:
+        # they run the same knots' plans without reconfiguration
+        cplans = plans
+        if args.refine > 0:
+            with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+                cplans = list(ex.map(lambda kq: pk.Plan(ctx, kq[0], kq[1], restarts=args.restarts),
+                                     jobs))
         for pr in ("c64", "c128"):
             if pr == prec:
                 continue
-            ws2 = workspaces(pr)
-            g2 = pk.Group(plans, pr, ws2)
+            ws2 = workspaces(pr, cplans)
+            g2 = pk.Group(cplans, pr, ws2)
             g2.launch()                         # loads the kernels
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
@@ -784,9 +799,11 @@ def main():
             b.record(stream)
             b.synchronize()
             ms = max_over_ranks(a.elapsed_time(b), dist, dev)
-            res_by[pr] = results(pr, ws2)
+            res_by[pr] = results(pr, ws2, cplans)
             compare[pr] = {"value": world * evals / (ms / 1000.0), "unit": "knots/s",
-                           "ms_per_step": ms, "note": "one timed replay after a warm-up replay"}
+                           "ms_per_step": ms, "note": "one timed replay after a warm-up replay"
+                           + ("; plans without subtree reconfiguration" if cplans is not plans else ""),
+                           "complex_macs_per_step": sum(p.stats()["cmacs"] for p in cplans)}
             del g2, ws2
             torch.cuda.empty_cache()
             log(f"{pr} pass")
@@ -822,7 +839,8 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
                "config": {"workload": "scale: 64 random grid-walk knots per GPU, L=40, 100-400 crossings, "
                                       "random over/under, q in {2,3,5}; 192 (knot, q) evaluations per step",
-                          "order": f"auto per knot (lowest estimated cost after slicing, {args.restarts} min-fill restarts)",
+                          "order": f"auto per knot (lowest estimated cost after slicing, {args.restarts} min-fill "
+                                   f"restarts, subtree reconfiguration with up to {args.refine} subtrees)",
                           "l2": "flushed between steps (512 MB write)",
                           "tuning": dict(ctx.tuning(), source="compiled-in table written by "
                                          "paper_1807_02119_gb300/autotune.py"),

@@ -121,6 +121,9 @@ typedef struct {
                                 the A(q) of the standard weights (meaningless unless they
                                 are those weights); such networks are general (see
                                 PK_FLAG_GRAD) and use spin-network orders                   */
+  int32_t refine;            /* local-search moves applied to the best candidate's spin
+                                elimination order (simulated annealing on the estimated
+                                cost; 0 -> none).  Planning effort only: Z is unchanged      */
 } pk_plan_opts;
 
 typedef struct {

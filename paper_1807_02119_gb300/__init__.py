@@ -56,7 +56,7 @@ class pk_plan_opts(C.Structure):
     _fields_ = [("order", C.c_int32), ("flags", C.c_int32), ("max_log2_elems", C.c_double),
                 ("max_log2_slices", C.c_double), ("tail_steps", C.c_int32),
                 ("restarts", C.c_int32), ("checkpoint_stride", C.c_int32),
-                ("edge_weights", C.POINTER(C.c_double))]
+                ("edge_weights", C.POINTER(C.c_double)), ("refine", C.c_int32)]
 
 
 class pk_tuning(C.Structure):
@@ -368,13 +368,13 @@ class Plan:
     def __init__(self, ctx: Context, knot: Knot, q: int, order: str = "auto",
                  max_log2_elems: float = 0.0, max_log2_slices: float = 0.0, flags: int = 0,
                  tail_steps: int = 0, restarts: int = 0, grad: bool = False,
-                 checkpoint_stride: int = 0, weights=None):
+                 checkpoint_stride: int = 0, weights=None, refine: int = 0):
         w = None
         if weights is not None:
             w = _weights_array(weights, knot.info()["n_c"])
         o = pk_plan_opts(ORDERS[order], flags | (FLAG_GRAD if grad else 0), max_log2_elems,
                          max_log2_slices, tail_steps, restarts, checkpoint_stride,
-                         C.cast(w, C.POINTER(C.c_double)) if w is not None else None)
+                         C.cast(w, C.POINTER(C.c_double)) if w is not None else None, refine)
         h = C.c_void_p()
         _check(lib().pk_plan_create(ctx.h, knot.h, q, C.byref(o), C.byref(h)), ctx)
         self.h = h

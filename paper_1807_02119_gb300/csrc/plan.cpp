@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <functional>
 #include <cstring>
 #include <limits>
 #include <map>
@@ -729,18 +730,35 @@ std::vector<int32_t> dissection_order(const Network& net, uint64_t seed) {
   return order;
 }
 
-bool run_order(const Network& net, int32_t order, Greedy& g, uint64_t seed = 0) {
+// Contraction sequence of a spin elimination order: for each spin in turn, the tensors
+// holding it are contracted pairwise (greedy among them) until at most one holds it.
+void run_elimination(const Network& net, const std::vector<int32_t>& ord, Greedy& g) {
   g = Greedy();
   g.init(net);
+  for (int32_t v : ord) {
+    int32_t a, b;
+    while (g.cnt[v] >= 2 && g.best_pair(v, a, b)) g.contract(a, b);
+  }
+  int32_t a, b;
+  while (g.best_pair(-1, a, b)) g.contract(a, b);
+  g.finish();
+}
+
+// `ord_out` (may be null) receives the spin elimination order of elimination-type orders
+// (empty for the greedy orders).
+bool run_order(const Network& net, int32_t order, Greedy& g, uint64_t seed = 0,
+               std::vector<int32_t>* ord_out = nullptr) {
+  if (ord_out) ord_out->clear();
   if (order == PK_ORDER_ELIM_SPIN || order == PK_ORDER_FILL_SPIN || order == PK_ORDER_PARTITION) {
     std::vector<int32_t> ord = order == PK_ORDER_ELIM_SPIN ? min_degree_order(net)
                                : order == PK_ORDER_FILL_SPIN ? min_fill_order(net, seed)
                                                              : dissection_order(net, seed);
-    for (int32_t v : ord) {
-      int32_t a, b;
-      while (g.cnt[v] >= 2 && g.best_pair(v, a, b)) g.contract(a, b);
-    }
+    run_elimination(net, ord, g);
+    if (ord_out) *ord_out = std::move(ord);
+    return true;
   }
+  g = Greedy();
+  g.init(net);
   int32_t a, b;
   while (g.best_pair(-1, a, b)) g.contract(a, b);
   g.finish();
@@ -818,6 +836,251 @@ double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& se
     c += macs * (gemm ? w_gemm : 1.0) + w_out * std::pow((double)q, (double)sc.size());
   }
   return c;
+}
+
+// Total estimated cost of a contraction sequence: slices x cost of one slice, or
+// infinity when it needs more slices than allowed.
+double sliced_cost(const Greedy& g, int32_t n_idx, int32_t q, int32_t rmax, size_t max_slices,
+                   const pk_tuning& tune) {
+  std::vector<std::vector<int32_t>> ss = g.seq.sets;
+  std::vector<int32_t> sl;
+  if (!slice_indices(ss, n_idx, q, rmax, max_slices, sl))
+    return std::numeric_limits<double>::infinity();
+  return std::pow((double)q, (double)sl.size()) * sequence_cost(g.seq, ss, q, tune);
+}
+
+// ---- subtree reconfiguration of a contraction tree
+//
+// Not in the paper (its orders are greedy and graph partitioning): a refinement of the
+// chosen contraction sequence.  Every internal node r of the tree, cut a few levels down,
+// is the contraction of a few subtrees F = {f_1, ..., f_k} (k <= refine); the best way to
+// contract F pairwise is found exactly by dynamic programming over the subsets of F, and
+// replaces the old one when it is cheaper under the planner's cost model.  An index of a
+// subset S of F survives its contraction iff r's result or a member of F outside S still
+// holds it (a tensor holds exactly the indices its leaves share with the rest of the
+// network), so every new intermediate is what the greedy bookkeeping would produce.  Z is
+// unchanged: only the bracketing of the product changes.
+struct CTree {
+  int32_t n_init = 0;
+  std::vector<int32_t> lc, rc;  // children; leaves: -2; a one-operand step: rc = -1
+  std::vector<std::vector<int32_t>> sets;
+  int32_t root = -1;
+};
+
+CTree tree_of(const Seq& seq) {
+  CTree t;
+  t.n_init = (int32_t)(seq.sets.size() - seq.pairs.size());
+  t.sets = seq.sets;
+  t.lc.assign(t.n_init, -2);
+  t.rc.assign(t.n_init, -2);
+  for (const auto& pr : seq.pairs) {
+    t.lc.push_back(pr.first);
+    t.rc.push_back(pr.second);
+  }
+  t.root = (int32_t)t.sets.size() - 1;
+  return t;
+}
+
+// The steps of the tree in post order (operands before results), renumbered.
+Seq seq_of(const CTree& t) {
+  Seq out;
+  out.sets.assign(t.sets.begin(), t.sets.begin() + t.n_init);
+  for (const auto& s : out.sets) out.max_rank = std::max<int32_t>(out.max_rank, (int32_t)s.size());
+  std::vector<int32_t> id(t.sets.size(), -1);
+  for (int32_t i = 0; i < t.n_init; ++i) id[i] = i;
+  std::vector<std::pair<int32_t, int32_t>> st{{t.root, 0}};
+  while (!st.empty()) {
+    auto& top = st.back();
+    const int32_t v = top.first;
+    if (v < t.n_init) {
+      st.pop_back();
+      continue;
+    }
+    if (top.second == 0) {
+      top.second = 1;
+      st.push_back({t.lc[v], 0});
+    } else if (top.second == 1) {
+      top.second = 2;
+      if (t.rc[v] >= 0) st.push_back({t.rc[v], 0});
+    } else {
+      id[v] = (int32_t)out.sets.size();
+      out.pairs.push_back({id[t.lc[v]], t.rc[v] >= 0 ? id[t.rc[v]] : -1});
+      out.sets.push_back(t.sets[v]);
+      out.max_rank = std::max<int32_t>(out.max_rank, (int32_t)t.sets[v].size());
+      st.pop_back();
+    }
+  }
+  return out;
+}
+
+// Cost of one step in the units of sequence_cost, on bit masks of a local index numbering.
+struct StepCost {
+  int32_t q;
+  double w_gemm, w_out, min_n, min_k, wide_n;
+  double qp[65];
+  StepCost(int32_t q_, const pk_tuning& tune) : q(q_) {
+    w_gemm = (double)tune.cost_gemm_milli / 1000.0;
+    w_out = (double)tune.cost_out_milli / 1000.0;
+    min_n = (double)tune.tc_min_n;
+    min_k = (double)tune.tc_min_k;
+    wide_n = (double)tune.tc_wide_n;
+    qp[0] = 1;
+    for (int i = 1; i <= 64; ++i) qp[i] = qp[i - 1] * q;
+  }
+  double operator()(uint64_t a, uint64_t b, uint64_t c) const {
+    if (__builtin_popcountll(b) > __builtin_popcountll(a)) std::swap(a, b);
+    const int m = __builtin_popcountll(a & c & ~b), n = __builtin_popcountll(b & c & ~a);
+    const int k = __builtin_popcountll((a | b) & ~c);
+    const bool gemm = qp[m] >= 64 && qp[n] >= min_n && (qp[k] >= min_k || (qp[k] >= 4 && qp[n] >= wide_n));
+    return qp[__builtin_popcountll(a | b)] * (gemm ? w_gemm : 1.0) + w_out * qp[__builtin_popcountll(c)];
+  }
+};
+
+// One pass over the tree's internal nodes (largest results first); returns whether any
+// subtree changed.  `rmax` bounds the rank of new intermediates (no extra slicing).
+bool reconfigure_pass(CTree& t, int32_t kmax, int32_t rmax, const StepCost& cost) {
+  std::vector<int32_t> nodes;
+  for (int32_t v = t.n_init; v < (int32_t)t.sets.size(); ++v) nodes.push_back(v);
+  // reachable internal binary nodes only
+  std::vector<char> live(t.sets.size(), 0);
+  {
+    std::vector<int32_t> st{t.root};
+    while (!st.empty()) {
+      int32_t v = st.back();
+      st.pop_back();
+      live[v] = 1;
+      if (v >= t.n_init) {
+        st.push_back(t.lc[v]);
+        if (t.rc[v] >= 0) st.push_back(t.rc[v]);
+      }
+    }
+  }
+  auto bin = [&](int32_t v) { return v >= t.n_init && t.rc[v] >= 0; };
+  std::vector<int32_t> order;
+  for (int32_t v : nodes)
+    if (live[v] && bin(v)) order.push_back(v);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    size_t ux = t.sets[t.lc[x]].size() + t.sets[t.rc[x]].size(), uy = t.sets[t.lc[y]].size() + t.sets[t.rc[y]].size();
+    return ux > uy;
+  });
+  bool changed = false;
+  std::vector<double> best;
+  std::vector<uint64_t> keep;
+  std::vector<uint32_t> split;
+  for (int32_t r : order) {
+    if (!bin(r)) continue;
+    // frontier: expand the binary member with the most indices until kmax members
+    std::vector<int32_t> F{t.lc[r], t.rc[r]};
+    std::vector<int32_t> inner{r};
+    while ((int32_t)F.size() < kmax) {
+      int32_t bi = -1;
+      for (int32_t i = 0; i < (int32_t)F.size(); ++i)
+        if (bin(F[i]) && (bi < 0 || t.sets[F[i]].size() > t.sets[F[bi]].size())) bi = i;
+      if (bi < 0) break;
+      const int32_t v = F[bi];
+      inner.push_back(v);
+      F[bi] = t.lc[v];
+      F.push_back(t.rc[v]);
+    }
+    const int32_t k = (int32_t)F.size();
+    if (k < 3) continue;
+    // local numbering of the indices involved
+    std::vector<int32_t> U;
+    for (int32_t f : F) U.insert(U.end(), t.sets[f].begin(), t.sets[f].end());
+    std::sort(U.begin(), U.end());
+    U.erase(std::unique(U.begin(), U.end()), U.end());
+    if (U.size() > 64) continue;
+    auto mask_of = [&](const std::vector<int32_t>& s) {
+      uint64_t m = 0;
+      for (int32_t x : s) m |= 1ull << (std::lower_bound(U.begin(), U.end(), x) - U.begin());
+      return m;
+    };
+    std::vector<uint64_t> fm(k);
+    for (int32_t i = 0; i < k; ++i) fm[i] = mask_of(t.sets[F[i]]);
+    const uint64_t rm = mask_of(t.sets[r]);
+    // cost of the current bracketing of F
+    std::map<int32_t, uint64_t> mk;
+    for (int32_t i = 0; i < k; ++i) mk[F[i]] = fm[i];
+    double old_cost = 0;
+    for (auto it = inner.rbegin(); it != inner.rend(); ++it) {
+      const int32_t v = *it;
+      const uint64_t mv = mask_of(t.sets[v]);
+      old_cost += cost(mk.at(t.lc[v]), mk.at(t.rc[v]), mv);
+      mk[v] = mv;
+    }
+    const uint32_t full = (1u << k) - 1;
+    best.assign((size_t)full + 1, 0.0);
+    keep.assign((size_t)full + 1, 0);
+    split.assign((size_t)full + 1, 0);
+    std::vector<uint64_t> uni((size_t)full + 1, 0);
+    for (uint32_t S = 1; S <= full; ++S) {
+      const int32_t low = __builtin_ctz(S);
+      uni[S] = uni[S & (S - 1)] | fm[low];
+    }
+    for (uint32_t S = 1; S <= full; ++S) keep[S] = uni[S] & (rm | uni[full & ~S]);
+    for (uint32_t S = 1; S <= full; ++S) {
+      if ((S & (S - 1)) == 0) continue;  // a single member: no step
+      double b = std::numeric_limits<double>::infinity();
+      uint32_t bs = 0;
+      const uint32_t lowbit = S & (~S + 1);
+      if (__builtin_popcountll(keep[S]) > rmax) {
+        best[S] = b;
+        continue;
+      }
+      for (uint32_t A = (S - 1) & S; A > 0; A = (A - 1) & S) {
+        if (!(A & lowbit)) continue;
+        const uint32_t B = S & ~A;
+        const double c = best[A] + best[B];
+        if (!(c < b)) continue;
+        const double cc = c + cost(keep[A], keep[B], keep[S]);
+        if (cc < b) {
+          b = cc;
+          bs = A;
+        }
+      }
+      best[S] = b;
+      split[S] = bs;
+    }
+    if (!(best[full] < old_cost * (1.0 - 1e-9))) continue;
+    // rebuild: r keeps its id and result; new intermediates are appended
+    std::vector<int32_t> gidx;
+    std::function<int32_t(uint32_t)> build = [&](uint32_t S) -> int32_t {
+      if ((S & (S - 1)) == 0) return F[__builtin_ctz(S)];
+      const uint32_t A = split[S], B = S & ~A;
+      const int32_t a = build(A), b2 = build(B);
+      if (S == full) {
+        t.lc[r] = a;
+        t.rc[r] = b2;
+        return r;
+      }
+      std::vector<int32_t> set;
+      for (int32_t i = 0; i < (int32_t)U.size(); ++i)
+        if ((keep[S] >> i) & 1) set.push_back(U[i]);
+      t.lc.push_back(a);
+      t.rc.push_back(b2);
+      t.sets.push_back(set);
+      return (int32_t)t.sets.size() - 1;
+    };
+    build(full);
+    changed = true;
+  }
+  return changed;
+}
+
+// Reconfigures `seq` in place (at most `passes` passes); returns whether it changed.
+bool reconfigure(Seq& seq, int32_t kmax, int32_t rmax, int32_t q, const pk_tuning& tune,
+                 int32_t passes = 4) {
+  if (kmax < 3 || seq.pairs.empty()) return false;
+  kmax = std::min<int32_t>(kmax, 16);
+  CTree t = tree_of(seq);
+  const StepCost cost(q, tune);
+  bool any = false;
+  for (int32_t p = 0; p < passes; ++p) {
+    if (!reconfigure_pass(t, kmax, rmax, cost)) break;
+    any = true;
+  }
+  if (any) seq = seq_of(t);
+  return any;
 }
 
 }  // namespace
@@ -1192,10 +1455,17 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
     err = "unknown order";
     return false;
   }
-  Network best_net;
-  Greedy best_g;
-  double best_cost = std::numeric_limits<double>::infinity();
-  int32_t best_order = -1;
+  // the cheapest candidates (by estimated cost after slicing), best first; with
+  // opts.refine the kRefineTop cheapest are kept for the reconfiguration below
+  constexpr size_t kRefineTop = 8;
+  const size_t keep_top = opts.refine > 0 ? kRefineTop : 1;
+  struct Cand {
+    double cost;
+    int32_t order;
+    Network net;
+    Greedy g;
+  };
+  std::vector<Cand> top_c;
   for (const auto& cand : cands) {
     const int32_t o = cand.first;
     Network net;
@@ -1206,21 +1476,41 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
     Greedy g;
     run_order(net, o, g, cand.second);
     // cost in complex MACs at this q after slicing: slices x work per slice
-    std::vector<std::vector<int32_t>> ss = g.seq.sets;
-    std::vector<int32_t> sl;
-    if (!slice_indices(ss, net.n_idx, q, rmax, max_slice_idx, sl)) continue;
-    const double c = std::pow((double)q, (double)sl.size()) * sequence_cost(g.seq, ss, q, tune);
-    if (c < best_cost) {
-      best_cost = c;
-      best_net = net;
-      best_g = g;
-      best_order = o;
-    }
+    const double c = sliced_cost(g, net.n_idx, q, rmax, max_slice_idx, tune);
+    if (!std::isfinite(c)) continue;
+    if (top_c.size() == keep_top && !(c < top_c.back().cost)) continue;
+    auto at = std::upper_bound(top_c.begin(), top_c.end(), c,
+                               [](double x, const Cand& y) { return x < y.cost; });
+    top_c.insert(at, Cand{c, o, std::move(net), std::move(g)});
+    if (top_c.size() > keep_top) top_c.pop_back();
   }
-  if (best_order < 0) {
+  if (top_c.empty()) {
     err = "plan needs more slices than allowed";
     return false;
   }
+  size_t best_i = 0;
+  if (opts.refine > 0) {
+    // subtree reconfiguration of each kept candidate with frontiers of 4, 6, ... up to
+    // opts.refine subtrees in turn; the cheapest result wins
+    for (size_t i = 0; i < top_c.size(); ++i) {
+      Cand& cd = top_c[i];
+      Greedy rg = cd.g;
+      bool changed = false;
+      for (int32_t kk = 4; kk <= std::max<int32_t>(4, std::min<int32_t>(opts.refine, 16)); kk += 2)
+        changed |= reconfigure(rg.seq, kk, rmax, q, tune);
+      if (changed) {
+        const double c = sliced_cost(rg, cd.net.n_idx, q, rmax, max_slice_idx, tune);
+        if (c < cd.cost) {
+          cd.cost = c;
+          cd.g = std::move(rg);
+        }
+      }
+      if (cd.cost < top_c[best_i].cost) best_i = i;
+    }
+  }
+  Network best_net = std::move(top_c[best_i].net);
+  Greedy best_g = std::move(top_c[best_i].g);
+  const int32_t best_order = top_c[best_i].order;
   p.order_used = best_order;
   Network& net = best_net;
   Greedy& g = best_g;

@@ -3,8 +3,9 @@ evaluation.
 
 64 random grid-walk knots (L = 40, seeds 1..64, 100..400 crossings, random over/under) at
 q = 2, 3, 5: 192 evaluations, run in the launch configuration bench.py times -- plans with
-256 min-fill restarts built on all host cores, one resident workspace per plan, every
-plan's launch sequence an independent branch of one CUDA graph -- and compared with the
+256 min-fill restarts and subtree reconfiguration built on all host cores, one resident
+workspace per plan, every plan's launch sequence an independent branch of one CUDA graph --
+and compared with the
 oracle's Z(q) (Sec. II spin sum) and V = A(q) Z (Eq. JonesPotts) stored in
 tests/golden/scale_oracle.txt (written by tests/golden/make_scale_oracle.py from `oracle`
 only).  The q = 5 plans carry the tensor-core GEMM steps at their real shapes (several
@@ -29,6 +30,7 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "scale_oracle.txt")
 RESTARTS = 256   # min-fill restarts per plan, as bench.py builds the workload's plans
+REFINE = 8       # subtree reconfiguration (frontiers of up to 8 subtrees), as bench.py
 TOL = {"split": 1e-6, "split4": 4e-6, "split_db": 1e-6, "split_narrow": 1e-6, "c128": 1e-10}
 QS = (2, 3, 5)
 
@@ -70,7 +72,8 @@ def _plans(ctx, flags=0, qs=QS, **tuning):
     kn = [pk.Knot.from_pd(ctx, gk.pd, outer=gk.outer) for gk in knots]
     jobs = [(gk.seed, k, q) for gk, k in zip(knots, kn) for q in qs]
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-        plans = list(ex.map(lambda j: pk.Plan(ctx, j[1], j[2], restarts=RESTARTS, flags=flags), jobs))
+        plans = list(ex.map(lambda j: pk.Plan(ctx, j[1], j[2], restarts=RESTARTS, flags=flags,
+                                                     refine=REFINE), jobs))
     return [(seed, q) for seed, _, q in jobs], plans
 
 

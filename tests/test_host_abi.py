@@ -112,6 +112,37 @@ def test_plan_replay_matches_oracle(ctx, order):
             assert rel_err(got, want) < 1e-10 or (abs(want.m) == 0 and abs(z) < 1e-12), (pd, q, order)
 
 
+@pytest.mark.parametrize("order", ["greedy_edge", "greedy_spin", "fill_spin", "auto"])
+def test_reconfigured_plan_replay_matches_oracle(ctx, order):
+    """Subtree reconfiguration (pk_plan_opts.refine) rebrackets the pairwise products only:
+    the replayed plan still gives the oracle's Z, its records pass the plan verifier, and
+    at q = 5 it finds cheaper sequences than the unrefined plan on most knots."""
+    cheaper = 0
+    for i, pd in enumerate(_pds()[5:20]):
+        k = pk.Knot.from_pd(ctx, pd)
+        for q in (2, 3, 5):
+            p = pk.Plan(ctx, k, q, order=order, refine=8)
+            assert p.verify("split") == "" and p.verify("c128") == ""
+            z, e = replay(p)
+            assert rel_err(SC.of(z, e), _z_oracle(pd, q)) < 1e-10, (i, q, order)
+            if q == 5:
+                cheaper += p.stats()["cmacs"] < pk.Plan(ctx, k, q, order=order).stats()["cmacs"]
+    assert cheaper >= 1
+
+
+def test_reconfigured_plan_with_slicing(ctx):
+    """Reconfiguration keeps every new intermediate within the slicing bound."""
+    for s in range(4):
+        pd = kg.random_grid_knot(16, 100 + s, True, 20, 60).pd
+        k = pk.Knot.from_pd(ctx, pd)
+        for q, lim in ((2, 4.0), (3, 4.8), (5, 7.0)):
+            p = pk.Plan(ctx, k, q, max_log2_elems=lim, refine=10)
+            st = p.stats()
+            assert st["log2_max_elems"] <= lim + 1e-9
+            z, e = replay(p)
+            assert rel_err(SC.of(z, e), _z_oracle(pd, q)) < 1e-10, (s, q)
+
+
 def test_plan_replay_with_slicing(ctx):
     for s in range(6):
         pd = kg.random_grid_knot(16, 100 + s, True, 20, 60).pd
