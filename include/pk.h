@@ -176,6 +176,10 @@ typedef struct {
   int64_t tc_wide_n;         /* PK_SPLIT: row steps of GEMM shape with K >= 4 (below tc_min_k)
                                 also run on the tensor cores when they have at least this many
                                 columns (16..2^30; 2^30: never)                               */
+  int64_t cost_tcin_milli;   /* planner: cost of one operand entry (of A and of B) of a step
+                                that runs on the tensor cores (its BF16 digits are written by a
+                                conversion pass and read back by the GEMM), in thousandths of a
+                                multiply-add (0..10^6)                                         */
 } pk_tuning;
 
 pk_status pk_tuning_default(pk_tuning* out);

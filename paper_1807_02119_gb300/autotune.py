@@ -37,6 +37,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 TABLE = os.path.join(HERE, "csrc", "tuned_table.h")
 RESTARTS = 256   # min-fill restarts per plan of the scale workload, as bench.py builds them
+REFINE = 8       # subtree reconfiguration of the scale workload's plans, as bench.py
 
 BATCH_THREADS = (128, 256, 512)
 BATCH_KTAB = (512, 1024, 2048)
@@ -48,9 +49,10 @@ TC_MIN_N = (8, 12, 16, 24, 32)
 COST_GEMM = (50, 100, 150, 250, 400)
 COST_OUT = (1000, 2000, 4000, 8000, 16000, 32000, 64000, 128000, 256000)
 TC_WIDE_N = (16, 25, 50, 100, 1 << 30)
+COST_TCIN = (0, 500, 1000, 2000, 4000, 8000, 16000)
 SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_min_n": TC_MIN_N, "tc_wide_n": TC_WIDE_N,
                 "tc_db_groups": TC_DB_GROUPS, "cost_gemm_milli": COST_GEMM,
-                "cost_out_milli": COST_OUT}
+                "cost_out_milli": COST_OUT, "cost_tcin_milli": COST_TCIN}
 
 
 def _rel(a, b):
@@ -122,7 +124,8 @@ def sweep_seq(pk, ctx, stream, flush, reps, log, quick):
         for sw in works:
             ctx.set_tuning(seq_outs=so, seq_work=sw)
             with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-                plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=RESTARTS), jobs))
+                plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=RESTARTS,
+                                                          refine=REFINE), jobs))
             ws = [torch.empty(p.workspace_bytes("split") + 256, dtype=torch.uint8, device="cuda")
                   for p in plans]
             for p, w in zip(plans, ws):
@@ -158,7 +161,8 @@ def sweep_scale_param(pk, ctx, stream, flush, reps, log, name):
     for tk in SCALE_PARAMS[name]:
         ctx.set_tuning(**{**ctx.tuning(), name: tk})
         with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-            plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=RESTARTS), jobs))
+            plans = list(ex.map(lambda j: pk.Plan(ctx, j[0], j[1], restarts=RESTARTS,
+                                                          refine=REFINE), jobs))
         ws = [torch.empty(p.workspace_bytes("split") + 256, dtype=torch.uint8, device="cuda")
               for p in plans]
         for p, w in zip(plans, ws):
@@ -185,6 +189,7 @@ PARAM_TITLES = {
     "cost_gemm_milli": "Planner: cost of a tensor-core multiply-add (thousandths of a row one)",
     "cost_out_milli": "Planner: cost of an output entry (thousandths of a multiply-add)",
     "tc_wide_n": "Tensor cores for short-K (4 <= K < tc_min_k) row steps from this many columns",
+    "cost_tcin_milli": "Planner: cost of a tensor-core step's operand entry (thousandths of a multiply-add)",
 }
 
 
@@ -208,7 +213,7 @@ def write_table(path, tune, batch_rows, seq_rows, gpu, param_rows):
               f"{tune['batch_threads']}, {tune['batch_ktab']}, {tune['seq_outs']}, "
               f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}, {tune['tc_db_groups']}, "
               f"{tune['tc_min_n']}, {tune['cost_gemm_milli']}, {tune['cost_out_milli']}, "
-              f"{tune['tc_wide_n']}" +
+              f"{tune['tc_wide_n']}, {tune['cost_tcin_milli']}" +
               "};", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))

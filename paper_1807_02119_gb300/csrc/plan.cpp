@@ -802,6 +802,7 @@ bool slice_indices(std::vector<std::vector<int32_t>>& sets, int32_t n_idx, int32
 double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& sets, int32_t q,
                      const pk_tuning& tune) {
   const double w_gemm = (double)tune.cost_gemm_milli / 1000.0, w_out = (double)tune.cost_out_milli / 1000.0;
+  const double w_in = (double)tune.cost_tcin_milli / 1000.0;
   static const std::vector<int32_t> none;
   const size_t n_init = sets.size() - seq.pairs.size();
   double c = 0;
@@ -834,6 +835,7 @@ double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& se
     const bool gemm = pr.second >= 0 && std::pow((double)q, m) >= 64 && nq >= (double)tune.tc_min_n &&
                       (kq >= (double)tune.tc_min_k || (kq >= 4 && nq >= (double)tune.tc_wide_n));
     c += macs * (gemm ? w_gemm : 1.0) + w_out * std::pow((double)q, (double)sc.size());
+    if (gemm) c += w_in * (std::pow((double)q, (double)sa.size()) + std::pow((double)q, (double)sb.size()));
   }
   return c;
 }
@@ -916,11 +918,12 @@ Seq seq_of(const CTree& t) {
 // Cost of one step in the units of sequence_cost, on bit masks of a local index numbering.
 struct StepCost {
   int32_t q;
-  double w_gemm, w_out, min_n, min_k, wide_n;
+  double w_gemm, w_out, w_in, min_n, min_k, wide_n;
   double qp[65];
   StepCost(int32_t q_, const pk_tuning& tune) : q(q_) {
     w_gemm = (double)tune.cost_gemm_milli / 1000.0;
     w_out = (double)tune.cost_out_milli / 1000.0;
+    w_in = (double)tune.cost_tcin_milli / 1000.0;
     min_n = (double)tune.tc_min_n;
     min_k = (double)tune.tc_min_k;
     wide_n = (double)tune.tc_wide_n;
@@ -932,7 +935,8 @@ struct StepCost {
     const int m = __builtin_popcountll(a & c & ~b), n = __builtin_popcountll(b & c & ~a);
     const int k = __builtin_popcountll((a | b) & ~c);
     const bool gemm = qp[m] >= 64 && qp[n] >= min_n && (qp[k] >= min_k || (qp[k] >= 4 && qp[n] >= wide_n));
-    return qp[__builtin_popcountll(a | b)] * (gemm ? w_gemm : 1.0) + w_out * qp[__builtin_popcountll(c)];
+    return qp[__builtin_popcountll(a | b)] * (gemm ? w_gemm : 1.0) + w_out * qp[__builtin_popcountll(c)] +
+           (gemm ? w_in * (qp[__builtin_popcountll(a)] + qp[__builtin_popcountll(b)]) : 0.0);
   }
 };
 
@@ -1292,7 +1296,8 @@ bool valid_tuning(const pk_tuning& t) {
          t.tc_min_k >= 4 && t.tc_min_k <= 16 && t.tc_db_groups >= 0 && t.tc_db_groups <= 4096 &&
          t.tc_min_n >= 8 && t.tc_min_n <= 32 && t.cost_gemm_milli >= 10 &&
          t.cost_gemm_milli <= 1000 && t.cost_out_milli >= 0 && t.cost_out_milli <= 1000000 &&
-         t.tc_wide_n >= 16 && t.tc_wide_n <= ((int64_t)1 << 30);
+         t.tc_wide_n >= 16 && t.tc_wide_n <= ((int64_t)1 << 30) && t.cost_tcin_milli >= 0 &&
+         t.cost_tcin_milli <= 1000000;
 }
 
 void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,

@@ -76,7 +76,34 @@
 //                    49.83 / 49.91 / 48.35 / 48.64 / 48.26 / 47.74
 //   cost_out_milli = 16000 / 32000 / 64000 / 128000 / 256000:
 //                    49.33 / 47.89 / 48.28 / 48.97 / 48.81
+// Planner cost weights again, on plans with subtree reconfiguration (frontiers of up to
+// 8 subtrees), in turn: operand entry of a tensor-core step, tensor-core multiply-add,
+// output entry (measured 2026-12-04 10:14 UTC; run-to-run spread about 1 ms):
+// Planner: cost of a tensor-core step's operand entry (thousandths of a multiply-add), split (median ms per step):
+//   cost_tcin_milli =    0     31.54
+//   cost_tcin_milli =  500     31.73
+//   cost_tcin_milli = 1000     32.02
+//   cost_tcin_milli = 2000     32.92
+//   cost_tcin_milli = 4000     29.72
+//   cost_tcin_milli = 8000     36.94
+//   cost_tcin_milli = 16000    412.03
+// Planner: cost of a tensor-core multiply-add (thousandths of a row one), split (median ms per step):
+//   cost_gemm_milli =   50     30.34
+//   cost_gemm_milli =  100     29.28
+//   cost_gemm_milli =  150     29.63
+//   cost_gemm_milli =  250     31.96
+//   cost_gemm_milli =  400     33.17
+// Planner: cost of an output entry (thousandths of a multiply-add), split (median ms per step):
+//   cost_out_milli = 1000     49.18
+//   cost_out_milli = 2000     48.90
+//   cost_out_milli = 4000     33.82
+//   cost_out_milli = 8000     33.62
+//   cost_out_milli = 16000     32.19
+//   cost_out_milli = 32000     29.28
+//   cost_out_milli = 64000     30.65
+//   cost_out_milli = 128000     31.22
+//   cost_out_milli = 256000     30.65
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12, 150, 32000, 100};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12, 100, 32000, 100, 4000};

@@ -259,7 +259,7 @@ def test_tuning_table_and_ranges(ctx):
                 {"tc_min_k": 3}, {"tc_min_k": 17}, {"tc_db_groups": -1}, {"tc_db_groups": 5000},
                 {"tc_min_n": 7}, {"tc_min_n": 33}, {"cost_gemm_milli": 5},
                 {"cost_gemm_milli": 1001}, {"cost_out_milli": -1}, {"cost_out_milli": 1000001}, {"tc_wide_n": 15},
-                {"tc_wide_n": (1 << 30) + 1}):
+                {"tc_wide_n": (1 << 30) + 1}, {"cost_tcin_milli": -1}, {"cost_tcin_milli": 1000001}):
         with pytest.raises(pk.PkError):
             c.set_tuning(**bad)
     c.set_tuning()
