@@ -65,6 +65,8 @@ constexpr int kStagesDB = 4;   // stage ring of the double-buffered variant (one
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);   // producer, MMA issuer, epilogue
 constexpr int kConvThreads = 256;
+// the GEMM's tile order takes row blocks in groups whose A digits fill about this much of L2
+constexpr long long kRowGroupBytes = 48ll << 20;
 
 template <int S>
 struct Cfg {
@@ -463,8 +465,8 @@ __global__ void __launch_bounds__(tc::kConvThreads, 4) k_digits(const Step s, co
 }
 
 // C tiles (128 complex rows x 24 complex columns of one batch index) from the digit
-// chunks, persistently (column blocks fastest: tiles in flight together share their A row
-// blocks in L2).  Q = true: the producer of each CTA takes its next tile from the step's
+// chunks, persistently (grouped tile order: tiles in flight together share the A row
+// blocks of a group and a run of B column blocks in L2).  Q = true: the producer of each CTA takes its next tile from the step's
 // tile counter (`ticket`, zero at launch) and passes it to the MMA issuer and the epilogue
 // through a small queue in shared memory, so the tiles in flight on the GPU stay a window
 // of consecutive tiles however unevenly the CTAs progress (best for short tiles).
@@ -536,12 +538,26 @@ __global__ void __launch_bounds__(tc::kThreads, DB ? 1 : 2) k_gemm_tc(const Step
   const long long nchunks = L.chunks;
   const int ngroups = (int)((nchunks + kFlush - 1) / kFlush);
   const uint32_t sm0 = smem_u32(dsm);
-  // (batch, row block, column block) of a tile, column blocks fastest
+  // (batch, row block, column block) of a tile.  Within a batch index the row blocks go
+  // in groups of rg; inside a group the tiles run down the group's row blocks of one
+  // column block, then on to the next column block.  With rg = 1 (column blocks fastest)
+  // the tiles in flight together (one per CTA) cover gridDim.x / tiles_n row blocks and
+  // every column block, so B's digits are read from memory once per such wave.  A group of
+  // rg row blocks (as many as hold about kRowGroupBytes of A digits) whose A digits stay in
+  // L2 while its column blocks are swept reads B once per group instead, fewer times when
+  // rg exceeds the rows of a wave (wide N and long K).  Steps of at most two flush groups
+  // keep column blocks fastest (measured faster).
+  long long rg = max(1ll, min(L.tiles_m, kRowGroupBytes / (L.chunks * (long long)Cfg<S>::kAChunk)));
+  if (Q || rg * L.tiles_n <= (long long)gridDim.x) rg = 1;
   auto tile_coords = [&](long long t, long long& bb, long long& tm, long long& tn) {
-    tn = t % L.tiles_n;
-    t /= L.tiles_n;
-    tm = t % L.tiles_m;
-    bb = t / L.tiles_m;
+    const long long per_b = L.tiles_m * L.tiles_n;
+    bb = t / per_b;
+    const long long u = t - bb * per_b;
+    const long long r0 = (u / (rg * L.tiles_n)) * rg;
+    const long long gm = min(rg, L.tiles_m - r0);
+    const long long v = u - r0 * L.tiles_n;
+    tn = v / gm;
+    tm = r0 + v % gm;
   };
 
   constexpr int kCw = kN / 2;  // columns per epilogue thread (two warps per lane quarter)
