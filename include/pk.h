@@ -142,6 +142,8 @@ typedef struct {
   int32_t n_segments;        /* runs of consecutive small steps launched as one sequence
                                 kernel (one CTA, a block barrier between steps)              */
   int32_t n_segment_steps;   /* steps inside those runs                                     */
+  double est_cost;           /* the planner's estimated cost of the chosen sequence, all
+                                slices (the ranking's units: row-kernel multiply-adds)        */
 } pk_plan_stats;
 
 /* ---- tuning ------------------------------------------------------------------- */
@@ -271,9 +273,11 @@ pk_status pk_plan_info(const pk_plan* p, pk_plan_stats* out);
 pk_status pk_order_stats(const pk_knot* k, int32_t q, int32_t order, int32_t restarts, double* out);
 /* Device workspace needed by pk_eval / pk_upload / pk_launch at this precision. */
 pk_status pk_plan_workspace_bytes(const pk_plan* p, int32_t precision, uint64_t* bytes);
-/* Plan introspection for host-side checks: writes n_steps records of 8 int64:
- * (a, b, c, R, K, N, rank_c, kernel) with a/b/c tensor ids and the GEMM extents
- * R (batch x free-of-A rows), K, N of one slice. */
+/* Plan introspection for host-side checks: writes n_steps records of 10 int64:
+ * (a, b, c, R, K, N, rank_c, kernel, tc, Bsz) with a/b/c tensor ids, the GEMM extents
+ * R (batch x free-of-A rows), K, N of one slice, the kernel kind (0 row, 1 split-K,
+ * 2 GEMM), the digits per operand when the split precision runs the step on the tensor
+ * cores (0 otherwise) and the batch extent (R = Bsz x M). */
 pk_status pk_plan_steps(const pk_plan* p, int64_t* rec);
 void pk_plan_destroy(pk_plan* p);
 
@@ -401,6 +405,14 @@ pk_status pk_batch_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
  * copies host->device (knot headers, recipes and steps). */
 pk_status pk_batch_workspace_bytes(const pk_batch* b, uint64_t* bytes, uint64_t* upload_bytes);
 pk_status pk_batch_upload(pk_ctx* ctx, pk_batch* b, void* d_workspace, uint64_t workspace_bytes);
+/* Copies only the knot-derived part of the image (knot headers, initial-tensor recipes and
+ * their slots) host->device on the context's stream; the step records and index runs (the
+ * plans' structure) stay as an earlier pk_batch_upload of this batch left them in the same
+ * workspace, which the caller must have done (they are not checked).  For repeated
+ * evaluations of the same planned knots.  *copied (may be NULL): the bytes copied.
+ * Errors as pk_batch_upload. */
+pk_status pk_batch_upload_inputs(pk_ctx* ctx, pk_batch* b, void* d_workspace,
+                                 uint64_t workspace_bytes, uint64_t* copied);
 pk_status pk_batch_launch(pk_ctx* ctx, pk_batch* b, void* d_workspace, uint64_t workspace_bytes);
 /* Waits for the stream; Z[i], V[i] for knot or link i (V[i] = 0 and PK_EINVAL where the
  * A(q) exponent condition fails). */

@@ -30,7 +30,8 @@ EXPORTED = [
     "pk_plan_workspace_bytes", "pk_plan_steps", "pk_plan_destroy", "pk_eval", "pk_upload",
     "pk_launch", "pk_download", "pk_plan_launches", "pk_jones_from_z", "pk_plan_debug_blob",
     "pk_profile", "pk_eval_noalloc", "pk_plan_state_bytes", "pk_launch_arena",
-    "pk_batch_create", "pk_batch_workspace_bytes", "pk_batch_upload", "pk_batch_launch",
+    "pk_batch_create", "pk_batch_workspace_bytes", "pk_batch_upload", "pk_batch_upload_inputs",
+    "pk_batch_launch",
     "pk_batch_download", "pk_eval_batch", "pk_batch_destroy", "pk_group_create",
     "pk_group_launch", "pk_group_destroy", "pk_grad_workspace_bytes", "pk_grad",
     "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights", "pk_eval_exact",
@@ -73,7 +74,7 @@ class pk_plan_stats(C.Structure):
                 ("max_rank", C.c_int32), ("order_used", C.c_int32), ("n_tensors", C.c_int32),
                 ("workspace_c128", C.c_uint64), ("workspace_c64", C.c_uint64),
                 ("workspace_split", C.c_uint64), ("n_segments", C.c_int32),
-                ("n_segment_steps", C.c_int32)]
+                ("n_segment_steps", C.c_int32), ("est_cost", C.c_double)]
 
 
 _lib = None
@@ -142,6 +143,7 @@ def lib():
         "pk_batch_create": [vp, P(vp), i32, i32, P(vp)],
         "pk_batch_workspace_bytes": [vp, P(u64), P(u64)],
         "pk_batch_upload": [vp, vp, vp, u64],
+        "pk_batch_upload_inputs": [vp, vp, vp, u64, P(u64)],
         "pk_batch_launch": [vp, vp, vp, u64],
         "pk_batch_download": [vp, vp, vp, P(pk_scaled), P(pk_scaled)],
         "pk_eval_batch": [vp, P(vp), i32, i32, vp, u64, P(pk_scaled), P(pk_scaled)],
@@ -426,10 +428,10 @@ class Plan:
 
     def steps(self):
         n = self.stats()["n_steps"]
-        arr = (C.c_int64 * max(1, 8 * n))()
+        arr = (C.c_int64 * max(1, 10 * n))()
         _check(lib().pk_plan_steps(self.h, arr))
-        keys = ("a", "b", "c", "R", "K", "N", "rank_c", "kernel")
-        return [dict(zip(keys, arr[8 * i:8 * i + 8])) for i in range(n)]
+        keys = ("a", "b", "c", "R", "K", "N", "rank_c", "kernel", "tc", "Bsz")
+        return [dict(zip(keys, arr[10 * i:10 * i + 10])) for i in range(n)]
 
     def verify(self, precision="c128") -> str:
         """pk_plan_verify: '' when every index map and the memory layout check out, else the
@@ -728,6 +730,13 @@ class Batch:
     def upload(self, ws):
         _check(lib().pk_batch_upload(self.ctx.h, self.h, C.c_void_p(ws.data_ptr()), ws.numel()),
                self.ctx)
+
+    def upload_inputs(self, ws) -> int:
+        """pk_batch_upload_inputs: the knot-derived part only (after one upload); bytes copied."""
+        n = C.c_uint64()
+        _check(lib().pk_batch_upload_inputs(self.ctx.h, self.h, C.c_void_p(ws.data_ptr()),
+                                            ws.numel(), C.byref(n)), self.ctx)
+        return n.value
 
     def launch(self, ws):
         _check(lib().pk_batch_launch(self.ctx.h, self.h, C.c_void_p(ws.data_ptr()), ws.numel()),

@@ -419,6 +419,7 @@ pk_status pk_plan_info(const pk_plan* p, pk_plan_stats* out) {
   for (const pk::Segment& g : P.segments) seg_steps += g.count;
   out->n_segments = (int32_t)P.segments.size();
   out->n_segment_steps = seg_steps;
+  out->est_cost = P.est_cost;
   return PK_OK;
 }
 
@@ -432,7 +433,7 @@ pk_status pk_plan_steps(const pk_plan* p, int64_t* rec) {
   if (!p || (!rec && !p->p.steps.empty())) return PK_EINVAL;
   for (size_t i = 0; i < p->p.steps.size(); ++i) {
     const pk::Step& s = p->p.steps[i];
-    int64_t* r = rec + 8 * i;
+    int64_t* r = rec + 10 * i;
     r[0] = s.a;
     r[1] = s.b;
     r[2] = s.c;
@@ -441,6 +442,8 @@ pk_status pk_plan_steps(const pk_plan* p, int64_t* rec) {
     r[5] = s.N;
     r[6] = s.rank_c;
     r[7] = s.kernel;
+    r[8] = s.tc;
+    r[9] = s.Bsz;
   }
   return PK_OK;
 }

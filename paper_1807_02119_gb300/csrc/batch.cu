@@ -447,6 +447,26 @@ pk_status pk_batch_upload(pk_ctx* ctx, pk_batch* b, void* d_ws, uint64_t bytes) 
   return PK_OK;
 }
 
+pk_status pk_batch_upload_inputs(pk_ctx* ctx, pk_batch* b, void* d_ws, uint64_t bytes,
+                                 uint64_t* copied) {
+  if (!ctx || !b || !d_ws) return bfail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return bfail(ctx, PK_ENODEVICE, "host-only context");
+  if (bytes < b->total) return bfail(ctx, PK_ENOMEM, "workspace smaller than pk_batch_workspace_bytes");
+  if ((uintptr_t)d_ws & 255u) return bfail(ctx, PK_EINVAL, "workspace must be 256-byte aligned");
+  if (!b->pinned) {
+    if (cudaMallocHost((void**)&b->pinned, std::max<uint64_t>(1, b->image_bytes)) != cudaSuccess)
+      return bfail(ctx, PK_ENOMEM, "pinned host allocation failed");
+    std::memcpy(b->pinned, b->image.data(), b->image_bytes);
+  }
+  // knots, recipes and slots lie first in the image, the steps and runs after them
+  const uint64_t n = b->off_steps - b->off_knots;
+  cudaError_t e = cudaMemcpyAsync((char*)d_ws + b->off_knots, b->pinned + b->off_knots, n,
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return bfail(ctx, PK_ECUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+  if (copied) *copied = n;
+  return PK_OK;
+}
+
 pk_status pk_batch_launch(pk_ctx* ctx, pk_batch* b, void* d_ws, uint64_t bytes) {
   if (!ctx || !b || !d_ws) return bfail(ctx, PK_EINVAL, "bad argument");
   if (ctx->device < 0) return bfail(ctx, PK_ENODEVICE, "host-only context");

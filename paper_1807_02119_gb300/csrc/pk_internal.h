@@ -297,6 +297,7 @@ struct Plan {
   int32_t max_rank = 0;
   double log2_max_elems = 0;
   double cmacs = 0, bytes_c64 = 0;
+  double est_cost = 0;   // the planner's estimated cost of the chosen sequence (all slices)
   int64_t arena_elems = 0;
   int64_t splitk_partials = 0;      // complex scratch entries for split-K steps
   // device program layout (byte offsets inside the workspace)

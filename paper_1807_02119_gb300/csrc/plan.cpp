@@ -1517,6 +1517,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
   Greedy best_g = std::move(top_c[best_i].g);
   const int32_t best_order = top_c[best_i].order;
   p.order_used = best_order;
+  p.est_cost = top_c[best_i].cost;
   Network& net = best_net;
   Greedy& g = best_g;
   p.factor = net.factor;

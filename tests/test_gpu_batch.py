@@ -159,3 +159,27 @@ def test_batch_launch_shapes_agree(ctx):
                 ref = Z
             for z, zr in zip(Z, ref):
                 assert rel_err(sc(z), sc(zr)) <= TOL["split"], (th, kt)
+
+
+def test_batch_upload_inputs_restores_the_knot_part(ctx):
+    """pk_batch_upload_inputs copies only the knot-derived part of the image (the first
+    `copied` bytes of the workspace: knot headers, recipes, slots); with that part wiped on
+    the device, it alone must bring back the same Z and V, bit for bit."""
+    import torch
+    knots = kg.knot_suite("batch")[:64]
+    plans = _plans(ctx, knots, 3)
+    b = pk.Batch(plans, "split")
+    nbytes, upbytes = b.workspace_bytes()
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    b.upload(ws)
+    b.launch(ws)
+    z0, v0 = b.download(ws)
+    n = b.upload_inputs(ws)
+    assert 0 < n < upbytes
+    for rnd in range(2):
+        ws[:n].zero_()
+        assert b.upload_inputs(ws) == n
+        b.launch(ws)
+        z1, v1 = b.download(ws)
+        for a, c in zip(z0 + v0, z1 + v1):
+            assert a.mantissa == c.mantissa and a.exp2 == c.exp2, rnd
