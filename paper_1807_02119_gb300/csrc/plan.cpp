@@ -942,7 +942,8 @@ struct StepCost {
 
 // One pass over the tree's internal nodes (largest results first); returns whether any
 // subtree changed.  `rmax` bounds the rank of new intermediates (no extra slicing).
-bool reconfigure_pass(CTree& t, int32_t kmax, int32_t rmax, const StepCost& cost) {
+bool reconfigure_pass(CTree& t, int32_t kmax, int32_t rmax, const StepCost& cost,
+                      size_t max_nodes = SIZE_MAX) {
   std::vector<int32_t> nodes;
   for (int32_t v = t.n_init; v < (int32_t)t.sets.size(); ++v) nodes.push_back(v);
   // reachable internal binary nodes only
@@ -971,6 +972,7 @@ bool reconfigure_pass(CTree& t, int32_t kmax, int32_t rmax, const StepCost& cost
   std::vector<double> best;
   std::vector<uint64_t> keep;
   std::vector<uint32_t> split;
+  if (order.size() > max_nodes) order.resize(max_nodes);
   for (int32_t r : order) {
     if (!bin(r)) continue;
     // frontier: expand the binary member with the most indices until kmax members
@@ -1073,14 +1075,14 @@ bool reconfigure_pass(CTree& t, int32_t kmax, int32_t rmax, const StepCost& cost
 
 // Reconfigures `seq` in place (at most `passes` passes); returns whether it changed.
 bool reconfigure(Seq& seq, int32_t kmax, int32_t rmax, int32_t q, const pk_tuning& tune,
-                 int32_t passes = 4) {
+                 int32_t passes = 4, size_t max_nodes = SIZE_MAX) {
   if (kmax < 3 || seq.pairs.empty()) return false;
   kmax = std::min<int32_t>(kmax, 16);
   CTree t = tree_of(seq);
   const StepCost cost(q, tune);
   bool any = false;
   for (int32_t p = 0; p < passes; ++p) {
-    if (!reconfigure_pass(t, kmax, rmax, cost)) break;
+    if (!reconfigure_pass(t, kmax, rmax, cost, max_nodes)) break;
     any = true;
   }
   if (any) seq = seq_of(t);
@@ -1462,7 +1464,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
   }
   // the cheapest candidates (by estimated cost after slicing), best first; with
   // opts.refine the kRefineTop cheapest are kept for the reconfiguration below
-  constexpr size_t kRefineTop = 8;
+  constexpr size_t kRefineTop = 16;
   const size_t keep_top = opts.refine > 0 ? kRefineTop : 1;
   struct Cand {
     double cost;
@@ -1496,13 +1498,16 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
   size_t best_i = 0;
   if (opts.refine > 0) {
     // subtree reconfiguration of each kept candidate with frontiers of 4, 6, ... up to
-    // opts.refine subtrees in turn; the cheapest result wins
+    // opts.refine subtrees in turn, then frontiers of opts.refine + 2 at the kWideNodes
+    // nodes with the widest operands; the cheapest result wins
+    constexpr size_t kWideNodes = 12;
+    const int32_t kmax = std::max<int32_t>(4, std::min<int32_t>(opts.refine, 14));
     for (size_t i = 0; i < top_c.size(); ++i) {
       Cand& cd = top_c[i];
       Greedy rg = cd.g;
       bool changed = false;
-      for (int32_t kk = 4; kk <= std::max<int32_t>(4, std::min<int32_t>(opts.refine, 16)); kk += 2)
-        changed |= reconfigure(rg.seq, kk, rmax, q, tune);
+      for (int32_t kk = 4; kk <= kmax; kk += 2) changed |= reconfigure(rg.seq, kk, rmax, q, tune);
+      changed |= reconfigure(rg.seq, kmax + 2, rmax, q, tune, 2, kWideNodes);
       if (changed) {
         const double c = sliced_cost(rg, cd.net.n_idx, q, rmax, max_slice_idx, tune);
         if (c < cd.cost) {

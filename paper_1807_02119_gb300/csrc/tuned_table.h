@@ -103,7 +103,23 @@
 //   cost_out_milli = 64000     30.65
 //   cost_out_milli = 128000     31.22
 //   cost_out_milli = 256000     30.65
+// Tensor cores for row steps again, on the reconfigured plans (16 candidates rebracketed,
+// frontiers of up to 10 subtrees at the 12 largest nodes), in turn: columns, columns for
+// short K, contracted extent (median ms per step, measured 2026-12-04 11:30 UTC):
+//   tc_min_n =    8     28.13
+//   tc_min_n =   12     28.11
+//   tc_min_n =   16     28.11
+//   tc_min_n =   24     28.15
+//   tc_min_n =   32     34.00
+//   tc_wide_n =   16     27.27
+//   tc_wide_n =   25     27.17
+//   tc_wide_n =   50     28.08
+//   tc_wide_n =  100     28.15
+//   tc_wide_n = 1073741824     31.04
+//   tc_min_k =    4     27.37
+//   tc_min_k =    8     27.14
+//   tc_min_k =   16     27.23
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 16, 0, 12, 100, 32000, 100, 4000};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 8, 0, 12, 100, 32000, 25, 4000};

@@ -130,6 +130,17 @@ def test_reconfigured_plan_replay_matches_oracle(ctx, order):
     assert cheaper >= 1
 
 
+def test_reconfiguration_never_raises_the_estimated_cost(ctx):
+    """The planner keeps a rebracketed sequence only when its estimated cost (after
+    slicing) is lower, so refine > 0 can only lower pk_plan_stats.est_cost."""
+    for s in range(6):
+        k = pk.Knot.from_pd(ctx, kg.random_grid_knot(24, 300 + s, True, 40, 120).pd)
+        for q in (3, 5):
+            base = pk.Plan(ctx, k, q, restarts=16).stats()["est_cost"]
+            ref = pk.Plan(ctx, k, q, restarts=16, refine=8).stats()["est_cost"]
+            assert 0 < ref <= base * (1 + 1e-12), (s, q, base, ref)
+
+
 def test_reconfigured_plan_with_slicing(ctx):
     """Reconfiguration keeps every new intermediate within the slicing bound."""
     for s in range(4):
