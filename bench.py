@@ -748,7 +748,8 @@ def main():
     value = job_rate(world, evals, step_ms)
 
     # end to end through the public API, every step: every program host->device (pinned),
-    # the kernels, every scaled result device->host; the mean over the same number of steps
+    # the kernels, every scaled result device->host (one wait for all); the mean over the
+    # same number of steps
     h2d = sum(len(p.debug_blob(0)) for p in plans)
     d2h = 32 * len(plans)
     torch.cuda.synchronize()
@@ -756,10 +757,9 @@ def main():
         dist.barrier()
     t1 = time.perf_counter()
     for _ in range(args.steps):
-        for p, w in zip(plans, ws):
-            pk.upload(p, prec, w)
+        group.upload()
         group.launch()
-        results(prec, ws)
+        group.download()
     e2e_s = max_over_ranks((time.perf_counter() - t1) / args.steps, dist, dev)
     e2e_val = job_rate(world, evals, 1000.0 * e2e_s)
     log("end-to-end pass")

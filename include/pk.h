@@ -368,6 +368,16 @@ pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
                           void* const* d_workspaces, const uint64_t* workspace_bytes,
                           pk_group** out);
 pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp);
+/* pk_upload of every plan of the group into its workspace (asynchronous, the context's
+ * stream). */
+pk_status pk_group_upload(pk_ctx* ctx, pk_group* grp);
+/* The results of every plan of the group after a pk_group_launch: one device->host copy
+ * per plan of its 32-byte result record into pinned memory, one wait for the stream, then
+ * Z[i] and V[i] (V may be NULL) as pk_download gives them.  status (may be NULL): every
+ * plan's pk_download status.  Returns PK_OK, or the first plan's failing status (with the
+ * plan index in pk_last_error). */
+pk_status pk_group_download(pk_ctx* ctx, pk_group* grp, pk_scaled* Z, pk_scaled* V,
+                            int32_t* status);
 void pk_group_destroy(pk_group* grp);
 /* As pk_group_create, but inside the graph every kernel launch of every plan is
  * bracketed by two CUDA event-record nodes, so one pk_group_launch measures the duration

@@ -33,7 +33,8 @@ EXPORTED = [
     "pk_batch_create", "pk_batch_workspace_bytes", "pk_batch_upload", "pk_batch_upload_inputs",
     "pk_batch_launch",
     "pk_batch_download", "pk_eval_batch", "pk_batch_destroy", "pk_group_create",
-    "pk_group_launch", "pk_group_destroy", "pk_grad_workspace_bytes", "pk_grad",
+    "pk_group_launch", "pk_group_upload", "pk_group_download", "pk_group_destroy",
+    "pk_grad_workspace_bytes", "pk_grad",
     "pk_grad_from_accumulators", "pk_grad_stats", "pk_plan_set_weights", "pk_eval_exact",
     "pk_jones_coefficients", "pk_jones_plan", "pk_jones_solve", "pk_decode_result",
     "pk_group_create_profiled", "pk_group_profile", "pk_group_timeline",
@@ -150,6 +151,8 @@ def lib():
         "pk_batch_destroy": [vp],
         "pk_group_create": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
         "pk_group_launch": [vp, vp],
+        "pk_group_upload": [vp, vp],
+        "pk_group_download": [vp, vp, P(pk_scaled), P(pk_scaled), P(i32)],
         "pk_group_create_profiled": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
         "pk_group_profile": [vp, vp, P(C.c_double)],
         "pk_group_timeline": [vp, vp, P(C.c_double), i64, P(i64)],
@@ -793,6 +796,17 @@ class Group:
 
     def launch(self):
         _check(lib().pk_group_launch(self.ctx.h, self.h), self.ctx)
+
+    def upload(self):
+        """pk_group_upload: every plan's program into its workspace."""
+        _check(lib().pk_group_upload(self.ctx.h, self.h), self.ctx)
+
+    def download(self):
+        """pk_group_download: [(Z, V)] of every plan, one wait for the stream."""
+        n = len(self.plans)
+        z, v, st = (pk_scaled * n)(), (pk_scaled * n)(), (C.c_int32 * n)()
+        _check(lib().pk_group_download(self.ctx.h, self.h, z, v, st), self.ctx)
+        return [(Scaled.of(a), Scaled.of(b)) for a, b in zip(z, v)]
 
     def profile(self):
         """Per kernel class: summed in-replay launch durations (ms), launches, complex

@@ -622,6 +622,11 @@ struct pk_group {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int32_t n = 0;
+  int32_t precision = 0;
+  std::vector<const pk_plan*> plans;
+  std::vector<void*> ws;
+  std::vector<uint64_t> ws_bytes;
+  pk::SliceResult* pinned = nullptr;   // every plan's total result record (pk_group_download)
   std::vector<pk::Prof*> profs;   // profiled groups: the per-launch events of every branch
 };
 
@@ -639,6 +644,10 @@ pk_status group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, int3
   pk_group* grp = new (std::nothrow) pk_group();
   if (!grp) return fail(ctx, PK_ENOMEM, "out of host memory");
   grp->n = n;
+  grp->precision = precision;
+  grp->plans.assign(plans, plans + n);
+  grp->ws.assign(d_workspaces, d_workspaces + n);
+  grp->ws_bytes.assign(workspace_bytes, workspace_bytes + n);
   cudaError_t e = pk::prepare_kernels();
   if (e == cudaSuccess && !ctx->capture) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaGraphCreate(&grp->graph, 0);
@@ -724,8 +733,49 @@ pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp) {
   return e == cudaSuccess ? PK_OK : cuda_fail(ctx, e, "group launch");
 }
 
+pk_status pk_group_upload(pk_ctx* ctx, pk_group* grp) {
+  if (!ctx || !grp) return fail(ctx, PK_EINVAL, "bad argument");
+  for (int32_t i = 0; i < grp->n; ++i) {
+    const pk_status s = pk_upload(ctx, grp->plans[i], grp->precision, grp->ws[i], grp->ws_bytes[i]);
+    if (s != PK_OK) return s;
+  }
+  return PK_OK;
+}
+
+pk_status pk_group_download(pk_ctx* ctx, pk_group* grp, pk_scaled* Z, pk_scaled* V,
+                            int32_t* status) {
+  if (!ctx || !grp || (grp->n > 0 && !Z)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (grp->n == 0) return PK_OK;
+  DeviceGuard g(ctx->device);
+  if (!grp->pinned &&
+      cudaMallocHost((void**)&grp->pinned, sizeof(pk::SliceResult) * (size_t)grp->n) != cudaSuccess)
+    return fail(ctx, PK_ENOMEM, "pinned host allocation failed");
+  cudaError_t e = cudaSuccess;
+  for (int32_t i = 0; e == cudaSuccess && i < grp->n; ++i) {
+    const pk::Plan& P = grp->plans[i]->p;
+    const char* src = (const char*)grp->ws[i] + P.off_result + sizeof(pk::SliceResult) * P.n_slices;
+    e = cudaMemcpyAsync(grp->pinned + i, src, sizeof(pk::SliceResult), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "group download");
+  pk_status first = PK_OK;
+  std::string err;
+  for (int32_t i = 0; i < grp->n; ++i) {
+    pk_scaled vv;
+    const pk_status s = pk::decode_total(grp->plans[i]->p, grp->pinned[i], Z + i, V ? V + i : &vv, err);
+    if (status) status[i] = s;
+    if (s != PK_OK && first == PK_OK) {
+      first = s;
+      fail(ctx, s, "plan " + std::to_string(i) + ": " + err);
+    }
+  }
+  return first;
+}
+
 void pk_group_destroy(pk_group* grp) {
   if (!grp) return;
+  if (grp->pinned) cudaFreeHost(grp->pinned);
   if (grp->exec) cudaGraphExecDestroy(grp->exec);
   if (grp->graph) cudaGraphDestroy(grp->graph);
   for (pk::Prof* p : grp->profs) pk::prof_free(p);

@@ -134,10 +134,16 @@ def test_group_concurrent_replay(ctx, prec):
     for p, w in zip(plans, ws):
         pk.upload(p, prec, w)
     g = pk.Group(plans, prec, ws)
-    for _ in range(2):
+    for rnd in range(2):
+        if rnd:   # the group's own upload and one-wait download
+            for w in ws:
+                w.zero_()
+            g.upload()
         g.launch()
         got = [pk.download(p, prec, w) for p, w in zip(plans, ws)]
-        for p, (z, v) in zip(plans, got):
+        together = g.download()
+        for p, (z, v), (z2, v2) in zip(plans, got, together):
+            assert (z.mantissa, z.exp2, v.mantissa, v.exp2) == (z2.mantissa, z2.exp2, v2.mantissa, v2.exp2)
             zs, vs = pk.evaluate(p, prec)
             assert rel_err(sc(z), sc(zs)) <= TOL[prec] and rel_err(sc(v), sc(vs)) <= TOL[prec]
 
