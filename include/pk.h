@@ -182,6 +182,9 @@ typedef struct {
                                 that runs on the tensor cores (its BF16 digits are written by a
                                 conversion pass and read back by the GEMM), in thousandths of a
                                 multiply-add (0..10^6)                                         */
+  int64_t tc_min_work;       /* PK_SPLIT: row steps of GEMM shape (above) run on the tensor
+                                cores only from this many complex multiply-adds per slice
+                                (0..2^40; smaller ones stay on the row kernels)               */
 } pk_tuning;
 
 pk_status pk_tuning_default(pk_tuning* out);

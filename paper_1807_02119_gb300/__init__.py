@@ -66,7 +66,8 @@ class pk_tuning(C.Structure):
                 ("seq_work", C.c_int64), ("seq_k", C.c_int64), ("tc_min_k", C.c_int64),
                 ("tc_db_groups", C.c_int64), ("tc_min_n", C.c_int64),
                 ("cost_gemm_milli", C.c_int64), ("cost_out_milli", C.c_int64),
-                ("tc_wide_n", C.c_int64), ("cost_tcin_milli", C.c_int64)]
+                ("tc_wide_n", C.c_int64), ("cost_tcin_milli", C.c_int64),
+                ("tc_min_work", C.c_int64)]
 
 
 class pk_plan_stats(C.Structure):

@@ -50,9 +50,11 @@ COST_GEMM = (50, 100, 150, 250, 400)
 COST_OUT = (1000, 2000, 4000, 8000, 16000, 32000, 64000, 128000, 256000)
 TC_WIDE_N = (16, 25, 50, 100, 1 << 30)
 COST_TCIN = (0, 500, 1000, 2000, 4000, 8000, 16000)
+TC_MIN_WORK = (0, 1 << 16, 1 << 18, 1 << 20, 1 << 22)
 SCALE_PARAMS = {"tc_min_k": TC_MIN_K, "tc_min_n": TC_MIN_N, "tc_wide_n": TC_WIDE_N,
                 "tc_db_groups": TC_DB_GROUPS, "cost_gemm_milli": COST_GEMM,
-                "cost_out_milli": COST_OUT, "cost_tcin_milli": COST_TCIN}
+                "cost_out_milli": COST_OUT, "cost_tcin_milli": COST_TCIN,
+                "tc_min_work": TC_MIN_WORK}
 
 
 def _rel(a, b):
@@ -190,6 +192,7 @@ PARAM_TITLES = {
     "cost_out_milli": "Planner: cost of an output entry (thousandths of a multiply-add)",
     "tc_wide_n": "Tensor cores for short-K (4 <= K < tc_min_k) row steps from this many columns",
     "cost_tcin_milli": "Planner: cost of a tensor-core step's operand entry (thousandths of a multiply-add)",
+    "tc_min_work": "Tensor cores for row steps of GEMM shape from this many multiply-adds",
 }
 
 
@@ -213,7 +216,7 @@ def write_table(path, tune, batch_rows, seq_rows, gpu, param_rows):
               f"{tune['batch_threads']}, {tune['batch_ktab']}, {tune['seq_outs']}, "
               f"{tune['seq_work']}, {tune['seq_k']}, {tune['tc_min_k']}, {tune['tc_db_groups']}, "
               f"{tune['tc_min_n']}, {tune['cost_gemm_milli']}, {tune['cost_out_milli']}, "
-              f"{tune['tc_wide_n']}, {tune['cost_tcin_milli']}" +
+              f"{tune['tc_wide_n']}, {tune['cost_tcin_milli']}, {tune['tc_min_work']}" +
               "};", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))

@@ -356,7 +356,7 @@ pk_status decode_total(const Plan& P, const SliceResult& r, pk_scaled* Z, pk_sca
 bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
                 bool& swapped, std::vector<int32_t>& cdims, std::string& err, int64_t tc_min_k = 16,
-                int64_t tc_min_n = 32, int64_t tc_wide_n = (int64_t)1 << 30);
+                int64_t tc_min_n = 32, int64_t tc_wide_n = (int64_t)1 << 30, int64_t tc_min_work = 0);
 bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuning& tune, Plan& p,
                std::string& err);
 // Order search only (no slicing, no step records): out[0] largest tensor rank, out[1] log2

@@ -833,7 +833,8 @@ double sequence_cost(const Seq& seq, const std::vector<std::vector<int32_t>>& se
     const double macs = std::pow((double)q, (double)union_size(sa, sb));
     const double nq = std::pow((double)q, n), kq = std::pow((double)q, k);
     const bool gemm = pr.second >= 0 && std::pow((double)q, m) >= 64 && nq >= (double)tune.tc_min_n &&
-                      (kq >= (double)tune.tc_min_k || (kq >= 4 && nq >= (double)tune.tc_wide_n));
+                      (kq >= (double)tune.tc_min_k || (kq >= 4 && nq >= (double)tune.tc_wide_n)) &&
+                      ((nq >= 32 && kq >= 16) || macs >= (double)tune.tc_min_work);
     c += macs * (gemm ? w_gemm : 1.0) + w_out * std::pow((double)q, (double)sc.size());
     if (gemm) c += w_in * (std::pow((double)q, (double)sa.size()) + std::pow((double)q, (double)sb.size()));
   }
@@ -918,7 +919,7 @@ Seq seq_of(const CTree& t) {
 // Cost of one step in the units of sequence_cost, on bit masks of a local index numbering.
 struct StepCost {
   int32_t q;
-  double w_gemm, w_out, w_in, min_n, min_k, wide_n;
+  double w_gemm, w_out, w_in, min_n, min_k, wide_n, min_work;
   double qp[65];
   StepCost(int32_t q_, const pk_tuning& tune) : q(q_) {
     w_gemm = (double)tune.cost_gemm_milli / 1000.0;
@@ -927,6 +928,7 @@ struct StepCost {
     min_n = (double)tune.tc_min_n;
     min_k = (double)tune.tc_min_k;
     wide_n = (double)tune.tc_wide_n;
+    min_work = (double)tune.tc_min_work;
     qp[0] = 1;
     for (int i = 1; i <= 64; ++i) qp[i] = qp[i - 1] * q;
   }
@@ -934,7 +936,8 @@ struct StepCost {
     if (__builtin_popcountll(b) > __builtin_popcountll(a)) std::swap(a, b);
     const int m = __builtin_popcountll(a & c & ~b), n = __builtin_popcountll(b & c & ~a);
     const int k = __builtin_popcountll((a | b) & ~c);
-    const bool gemm = qp[m] >= 64 && qp[n] >= min_n && (qp[k] >= min_k || (qp[k] >= 4 && qp[n] >= wide_n));
+    const bool gemm = qp[m] >= 64 && qp[n] >= min_n && (qp[k] >= min_k || (qp[k] >= 4 && qp[n] >= wide_n)) &&
+                      ((qp[n] >= 32 && qp[k] >= 16) || qp[__builtin_popcountll(a | b)] >= min_work);
     return qp[__builtin_popcountll(a | b)] * (gemm ? w_gemm : 1.0) + w_out * qp[__builtin_popcountll(c)] +
            (gemm ? w_in * (qp[__builtin_popcountll(a)] + qp[__builtin_popcountll(b)]) : 0.0);
   }
@@ -1095,7 +1098,7 @@ bool reconfigure(Seq& seq, int32_t kmax, int32_t rmax, int32_t q, const pk_tunin
 bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
                 const std::vector<int32_t>& out, int32_t q, int32_t flags, Step& st,
                 bool& swapped, std::vector<int32_t>& cdims, std::string& err, int64_t tc_min_k,
-                int64_t tc_min_n, int64_t tc_wide_n) {
+                int64_t tc_min_n, int64_t tc_wide_n, int64_t tc_min_work) {
   static const std::vector<int32_t> no_dims;
   swapped = yd != nullptr && yd->size() > xd.size();
   const bool hasb = yd != nullptr;
@@ -1143,11 +1146,15 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
       else
         ++n_k;
     }
+  int32_t n_bat = 0;
+  for (int32_t v : ad)
+    if (in_c(v) && pos_in(bd, v) >= 0) ++n_bat;
   const int64_t M0 = qpow(n_m), N0 = qpow(n_n), K0 = qpow(n_k);
   const bool gemm_shape = hasb && !(flags & PK_FLAG_FORCE_ROWS) &&
                           ((flags & PK_FLAG_FORCE_GEMM) || (M0 >= 64 && N0 >= 32 && K0 >= 16) ||
                            (M0 >= 64 && N0 >= tc_min_n &&
-                            (K0 >= tc_min_k || (K0 >= 4 && N0 >= tc_wide_n))));
+                            (K0 >= tc_min_k || (K0 >= 4 && N0 >= tc_wide_n)) &&
+                            qpow(n_m + n_n + n_k + n_bat) >= tc_min_work));
   // row indices of A in C order, inner -> outer: A's order, or its m indices then its
   // batch indices
   std::vector<int32_t> row_order;
@@ -1283,7 +1290,8 @@ bool build_step(const std::vector<int32_t>& xd, const std::vector<int32_t>* yd,
   // kernel more float-float work than the tensor cores' epilogue (complex64 and complex128
   // keep the row kernel for them)
   const bool short_k = hasb && st.kernel == KROWS && !(flags & PK_FLAG_FORCE_ROWS) && st.M >= 64 &&
-                       st.N >= tc_min_n && (st.K >= tc_min_k || (st.K >= 4 && st.N >= tc_wide_n));
+                       st.N >= tc_min_n && (st.K >= tc_min_k || (st.K >= 4 && st.N >= tc_wide_n)) &&
+                       st.R * st.K * st.N >= tc_min_work;
   st.tc = ((st.kernel == KGEMM || short_k) && !(flags & PK_FLAG_NO_TC))
               ? ((flags & PK_FLAG_TC_DIGITS4) ? 4 : 5)
               : 0;
@@ -1299,7 +1307,7 @@ bool valid_tuning(const pk_tuning& t) {
          t.tc_min_n >= 8 && t.tc_min_n <= 32 && t.cost_gemm_milli >= 10 &&
          t.cost_gemm_milli <= 1000 && t.cost_out_milli >= 0 && t.cost_out_milli <= 1000000 &&
          t.tc_wide_n >= 16 && t.tc_wide_n <= ((int64_t)1 << 30) && t.cost_tcin_milli >= 0 &&
-         t.cost_tcin_milli <= 1000000;
+         t.cost_tcin_milli <= 1000000 && t.tc_min_work >= 0 && t.tc_min_work <= ((int64_t)1 << 40);
 }
 
 void build_segments(const std::vector<Step>& steps, const pk_tuning& tune,
@@ -1570,7 +1578,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
     bool sw = false;
     if (!build_step(p.tensors[x].dims, y >= 0 ? &p.tensors[y].dims : nullptr, sets[cid], q,
                     opts.flags, st, sw, p.tensors[cid].dims, err, tune.tc_min_k, tune.tc_min_n,
-                    tune.tc_wide_n))
+                    tune.tc_wide_n, tune.tc_min_work))
       return false;
     st.a = sw ? y : x;
     st.b = sw ? x : y;

@@ -119,7 +119,14 @@
 //   tc_min_k =    4     27.37
 //   tc_min_k =    8     27.14
 //   tc_min_k =   16     27.23
+// Tensor cores for row steps of GEMM shape from this many multiply-adds (median ms per
+// step, 2026-12-04 11:55 UTC; 0 and 65536 tie, 65536 kept: fewer launches):
+//   tc_min_work =    0     27.19
+//   tc_min_work = 65536     27.19
+//   tc_min_work = 262144     27.39
+//   tc_min_work = 1048576     28.12
+//   tc_min_work = 4194304     28.99
 #pragma once
 #include "pk.h"
 
-constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 8, 0, 12, 100, 32000, 25, 4000};
+constexpr pk_tuning kTunedDefault = {256, 512, 1024, 65536, 2048, 8, 0, 12, 100, 32000, 25, 4000, 65536};

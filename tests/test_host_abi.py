@@ -270,7 +270,8 @@ def test_tuning_table_and_ranges(ctx):
                 {"tc_min_k": 3}, {"tc_min_k": 17}, {"tc_db_groups": -1}, {"tc_db_groups": 5000},
                 {"tc_min_n": 7}, {"tc_min_n": 33}, {"cost_gemm_milli": 5},
                 {"cost_gemm_milli": 1001}, {"cost_out_milli": -1}, {"cost_out_milli": 1000001}, {"tc_wide_n": 15},
-                {"tc_wide_n": (1 << 30) + 1}, {"cost_tcin_milli": -1}, {"cost_tcin_milli": 1000001}):
+                {"tc_wide_n": (1 << 30) + 1}, {"cost_tcin_milli": -1}, {"cost_tcin_milli": 1000001},
+                {"tc_min_work": -1}, {"tc_min_work": (1 << 40) + 1}):
         with pytest.raises(pk.PkError):
             c.set_tuning(**bad)
     c.set_tuning()
@@ -317,3 +318,20 @@ def test_hbm_budget_slices_until_the_workspace_fits():
     with pytest.raises(pk.PkError) as ex:
         pk.Plan(c, k, 3)
     assert ex.value.status == 4
+
+
+@pytest.mark.parametrize("work", [1 << 12, 1 << 20])
+def test_plan_replay_with_tensor_core_work_floor(work):
+    """tc_min_work keeps small GEMM-shaped row steps off the tensor cores (and their C in
+    the row kernels' layout); the plans still replay to the oracle's Z."""
+    c = pk.Context(-1)
+    c.set_tuning(tc_min_work=work)
+    for s in range(3):
+        pd = kg.random_grid_knot(20, 400 + s, True, 40, 80).pd
+        for q in (3, 5):
+            p = pk.Plan(c, pk.Knot.from_pd(c, pd), q, refine=6)
+            z, e = replay(p)
+            assert rel_err(SC.of(z, e), _z_oracle(pd, q)) < 1e-10, (s, q)
+            small = [st for st in p.steps() if st["tc"] and st["kernel"] == 0 and
+                     st["R"] * st["K"] * st["N"] < work]
+            assert not small
