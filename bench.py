@@ -281,11 +281,11 @@ CLASS_KERNEL = {"build": "k_build", "rows": "k_rows / k_outs / k_seg (fused perm
 # divided by that launch's algorithmic bytes as the library counts them (its storage type,
 # 16 bytes per complex entry in split): the multiple applied to a class's average launch.
 # Sources (the heaviest launch of each class in the workload, knot seed 11 at q = 5):
-# tensor-core GEMM profiles/k_gemm_tc_split_q5_seed11.md (2.009 GB against (9.77 M + 9.77 M
-# + 48.8 M) x 16 B), digits profiles/k_digits_split_q5_seed11.md (2.380 GB against the
+# tensor-core GEMM profiles/k_gemm_tc_split_q5_seed11.md (2.008 GB against (9.77 M + 9.77 M
+# + 48.8 M) x 16 B), digits profiles/k_digits_split_q5_seed11.md (2.599 GB against the
 # operands it reads, (48.8 M + 9.77 M) x 16 B).  The row kernels (2% of the step) have no
 # capture of a launch large enough to leave its output in DRAM.
-NCU_TRAFFIC_RATIO = {"gemm_tc": 2.008668 / 1.09375, "digits": 2.379908 / 0.9375}
+NCU_TRAFFIC_RATIO = {"gemm_tc": 2.008012 / 1.09375, "digits": 2.599281 / 0.9375}
 
 
 def roofline_blocks(classes, prec, pk_, instep=None):
