@@ -85,6 +85,18 @@ def test_grad_matches_oracle(ctx, prec):
     print(f"[grad {prec}] worst relative error of dlogZ/dT vs the oracle {worst:.2e}")
 
 
+@pytest.mark.parametrize("prec", ["c128", "split"])
+def test_grad_reconfigured_plans_match_oracle(ctx, prec):
+    """Gradient plans with subtree reconfiguration (pk_plan_opts.refine) on the GPU: the
+    reverse pass over the rebracketed tree against the oracle's adjoints."""
+    for pd, outer in _knots()[2:]:
+        k = pk.Knot.from_pd(ctx, pd, outer=outer)
+        for q in (3, 5):
+            p = pk.Plan(ctx, k, q, grad=True, checkpoint_stride=4, refine=8)
+            z, v, d, dv = pk.grad(p, prec)
+            _compare(k, q, z, d, dv, prec)
+
+
 def test_grad_sliced_and_forced_kernels(ctx):
     for s in range(3):
         gk = kg.random_grid_knot(16, 400 + s, True, 25, 50)

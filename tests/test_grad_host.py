@@ -159,3 +159,14 @@ def test_grad_weights_sums_the_diagonal_and_off_diagonal():
     eye = np.eye(3, dtype=bool)
     want = np.stack([d[:, eye].sum(axis=1), d[:, ~eye].sum(axis=1)], axis=1)
     assert np.allclose(got, want, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("q", [3, 5])
+def test_grad_reconfigured_plan_matches_oracle(ctx, q):
+    """A gradient plan whose contraction tree was rebracketed (pk_plan_opts.refine): the
+    reverse program follows the new tree and the adjoints still match the oracle's."""
+    for pd in _knots()[4:]:
+        k = pk.Knot.from_pd(ctx, pd)
+        for stride in (0, 2):
+            p = pk.Plan(ctx, k, q, grad=True, checkpoint_stride=stride, refine=8)
+            _check(p, k, q)
