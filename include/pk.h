@@ -121,9 +121,12 @@ typedef struct {
                                 the A(q) of the standard weights (meaningless unless they
                                 are those weights); such networks are general (see
                                 PK_FLAG_GRAD) and use spin-network orders                   */
-  int32_t refine;            /* local-search moves applied to the best candidate's spin
-                                elimination order (simulated annealing on the estimated
-                                cost; 0 -> none).  Planning effort only: Z is unchanged      */
+  int32_t refine;            /* subtree reconfiguration of the 16 cheapest candidate
+                                sequences: pairwise bracketings of frontiers of up to
+                                `refine` subtrees (4..10; larger values act as 10), and of
+                                refine + 2 at the 12 widest nodes, chosen exactly by dynamic
+                                programming under the ranking's cost model (0 -> none).
+                                Planning effort only: Z is unchanged                          */
 } pk_plan_opts;
 
 typedef struct {

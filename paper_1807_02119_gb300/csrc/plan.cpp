@@ -1509,7 +1509,7 @@ bool make_plan(const Knot& k, int32_t q, const pk_plan_opts& opts, const pk_tuni
     // opts.refine subtrees in turn, then frontiers of opts.refine + 2 at the kWideNodes
     // nodes with the widest operands; the cheapest result wins
     constexpr size_t kWideNodes = 12;
-    const int32_t kmax = std::max<int32_t>(4, std::min<int32_t>(opts.refine, 14));
+    const int32_t kmax = std::max<int32_t>(4, std::min<int32_t>(opts.refine, 10));
     for (size_t i = 0; i < top_c.size(); ++i) {
       Cand& cd = top_c[i];
       Greedy rg = cd.g;
