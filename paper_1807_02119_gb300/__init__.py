@@ -369,7 +369,8 @@ def _weights_array(weights, n_e):
 class Plan:
     """A contraction plan.  grad=True also builds the reverse-pass program (pk_grad);
     weights: None (the Jones weights of Eq. clause) or one (diagonal, off-diagonal) complex
-    pair per Tait edge."""
+    pair per Tait edge; refine > 0: subtree reconfiguration of the cheapest candidate
+    sequences with frontiers of up to `refine` subtrees (pk_plan_opts.refine)."""
 
     def __init__(self, ctx: Context, knot: Knot, q: int, order: str = "auto",
                  max_log2_elems: float = 0.0, max_log2_slices: float = 0.0, flags: int = 0,
