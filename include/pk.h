@@ -307,6 +307,13 @@ pk_status pk_eval(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_work
  * pk_download waits for the stream, copies the scaled result back and applies A(q). */
 pk_status pk_upload(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                     uint64_t workspace_bytes);
+/* As pk_upload, but only the knot-derived part of the program: the initial-tensor recipes
+ * and their slots (the program's first bytes).  The plan's other records (conversion and
+ * sequence-kernel step records) stay as an earlier pk_upload of this plan and precision
+ * left them in the same workspace, which the caller must have done (not checked).  For
+ * repeated evaluations of the same plan.  *copied (may be NULL): the bytes copied. */
+pk_status pk_upload_inputs(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                           uint64_t workspace_bytes, uint64_t* copied);
 pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                     uint64_t workspace_bytes);
 pk_status pk_download(pk_ctx* ctx, const pk_plan* p, int32_t precision, const void* d_workspace,
@@ -374,9 +381,10 @@ pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
                           void* const* d_workspaces, const uint64_t* workspace_bytes,
                           pk_group** out);
 pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp);
-/* pk_upload of every plan of the group into its workspace (asynchronous, the context's
- * stream). */
-pk_status pk_group_upload(pk_ctx* ctx, pk_group* grp);
+/* pk_upload (inputs_only = 0) or pk_upload_inputs (inputs_only != 0) of every plan of the
+ * group into its workspace (asynchronous, the context's stream).  *copied (may be NULL):
+ * the bytes copied over all plans. */
+pk_status pk_group_upload(pk_ctx* ctx, pk_group* grp, int32_t inputs_only, uint64_t* copied);
 /* The results of every plan of the group after a pk_group_launch: one device->host copy
  * per plan of its 32-byte result record into pinned memory, one wait for the stream, then
  * Z[i] and V[i] (V may be NULL) as pk_download gives them.  status (may be NULL): every

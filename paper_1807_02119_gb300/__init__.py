@@ -28,6 +28,7 @@ EXPORTED = [
     "pk_knot_from_pd", "pk_link_from_pd", "pk_knot_from_signed_graph", "pk_knot_from_grid_walk", "pk_knot_info",
     "pk_knot_edges", "pk_knot_pd", "pk_knot_destroy", "pk_plan_create", "pk_plan_info",
     "pk_plan_workspace_bytes", "pk_plan_steps", "pk_plan_destroy", "pk_eval", "pk_upload",
+    "pk_upload_inputs",
     "pk_launch", "pk_download", "pk_plan_launches", "pk_jones_from_z", "pk_plan_debug_blob",
     "pk_profile", "pk_eval_noalloc", "pk_plan_state_bytes", "pk_launch_arena",
     "pk_batch_create", "pk_batch_workspace_bytes", "pk_batch_upload", "pk_batch_upload_inputs",
@@ -152,7 +153,8 @@ def lib():
         "pk_batch_destroy": [vp],
         "pk_group_create": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
         "pk_group_launch": [vp, vp],
-        "pk_group_upload": [vp, vp],
+        "pk_group_upload": [vp, vp, i32, P(u64)],
+        "pk_upload_inputs": [vp, vp, i32, vp, u64, P(u64)],
         "pk_group_download": [vp, vp, P(pk_scaled), P(pk_scaled), P(i32)],
         "pk_group_create_profiled": [vp, P(vp), i32, i32, P(vp), P(u64), P(vp)],
         "pk_group_profile": [vp, vp, P(C.c_double)],
@@ -661,6 +663,14 @@ def upload(plan: Plan, precision: str, ws):
                            ws.numel()), plan.ctx)
 
 
+def upload_inputs(plan: Plan, precision: str, ws) -> int:
+    """pk_upload_inputs: the knot-derived part of the program only (after one upload)."""
+    n = C.c_uint64()
+    _check(lib().pk_upload_inputs(plan.ctx.h, plan.h, PRECISIONS[precision],
+                                  C.c_void_p(ws.data_ptr()), ws.numel(), C.byref(n)), plan.ctx)
+    return n.value
+
+
 def launch(plan: Plan, precision: str, ws):
     _check(lib().pk_launch(plan.ctx.h, plan.h, PRECISIONS[precision], C.c_void_p(ws.data_ptr()),
                            ws.numel()), plan.ctx)
@@ -799,9 +809,12 @@ class Group:
     def launch(self):
         _check(lib().pk_group_launch(self.ctx.h, self.h), self.ctx)
 
-    def upload(self):
-        """pk_group_upload: every plan's program into its workspace."""
-        _check(lib().pk_group_upload(self.ctx.h, self.h), self.ctx)
+    def upload(self, inputs_only=False) -> int:
+        """pk_group_upload: every plan's program (or with inputs_only its knot-derived part,
+        after one full upload) into its workspace; the bytes copied."""
+        n = C.c_uint64()
+        _check(lib().pk_group_upload(self.ctx.h, self.h, int(inputs_only), C.byref(n)), self.ctx)
+        return n.value
 
     def download(self):
         """pk_group_download: [(Z, V)] of every plan, one wait for the stream."""

@@ -557,6 +557,34 @@ pk_status pk_upload(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_wo
   return PK_OK;
 }
 
+pk_status pk_upload_inputs(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
+                           uint64_t workspace_bytes, uint64_t* copied) {
+  if (!ctx || !p || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
+  if (ctx->device < 0) return fail(ctx, PK_ENODEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  pk_status s = PK_OK;
+  if (d_workspace == nullptr)
+    s = check_ws(ctx, p, precision, d_workspace, workspace_bytes);
+  else if (workspace_bytes < p->p.off_arena)
+    s = fail(ctx, PK_ENOMEM, "buffer smaller than the plan state (pk_plan_state_bytes)");
+  if (s != PK_OK) return s;
+  const pk::Plan& P = p->p;
+  // recipes and slots lie first in the program, the conversion and sequence records after
+  const uint64_t n = std::min<uint64_t>(P.off_conv, P.program.size());
+  if (copied) *copied = n;
+  if (n == 0) return PK_OK;
+  pk_plan* mp = const_cast<pk_plan*>(p);
+  if (!mp->pinned_program) {
+    if (cudaMallocHost((void**)&mp->pinned_program, P.program.size()) != cudaSuccess)
+      return fail(ctx, PK_ENOMEM, "pinned host allocation failed");
+    std::memcpy(mp->pinned_program, P.program.data(), P.program.size());
+  }
+  cudaError_t e = cudaMemcpyAsync(d_workspace, mp->pinned_program, n, cudaMemcpyHostToDevice,
+                                  ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+  return PK_OK;
+}
+
 pk_status pk_launch(pk_ctx* ctx, const pk_plan* p, int32_t precision, void* d_workspace,
                     uint64_t workspace_bytes) {
   if (!ctx || !p || !valid_precision(precision)) return fail(ctx, PK_EINVAL, "bad argument");
@@ -733,12 +761,18 @@ pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp) {
   return e == cudaSuccess ? PK_OK : cuda_fail(ctx, e, "group launch");
 }
 
-pk_status pk_group_upload(pk_ctx* ctx, pk_group* grp) {
+pk_status pk_group_upload(pk_ctx* ctx, pk_group* grp, int32_t inputs_only, uint64_t* copied) {
   if (!ctx || !grp) return fail(ctx, PK_EINVAL, "bad argument");
+  uint64_t total = 0;
   for (int32_t i = 0; i < grp->n; ++i) {
-    const pk_status s = pk_upload(ctx, grp->plans[i], grp->precision, grp->ws[i], grp->ws_bytes[i]);
+    uint64_t n = grp->plans[i]->p.program.size();
+    const pk_status s =
+        inputs_only ? pk_upload_inputs(ctx, grp->plans[i], grp->precision, grp->ws[i], grp->ws_bytes[i], &n)
+                    : pk_upload(ctx, grp->plans[i], grp->precision, grp->ws[i], grp->ws_bytes[i]);
     if (s != PK_OK) return s;
+    total += n;
   }
+  if (copied) *copied = total;
   return PK_OK;
 }
 

@@ -189,3 +189,41 @@ def test_batch_upload_inputs_restores_the_knot_part(ctx):
         z1, v1 = b.download(ws)
         for a, c in zip(z0 + v0, z1 + v1):
             assert a.mantissa == c.mantissa and a.exp2 == c.exp2, rnd
+
+
+def test_plan_and_group_upload_inputs(ctx):
+    """pk_upload_inputs / pk_group_upload(inputs_only) copy only the knot-derived part of a
+    program (its first `copied` bytes); with that part wiped on the device, it alone brings
+    back the same Z and V, bit for bit, for a single plan and for a group."""
+    import torch
+    knots = kg.knot_suite("scale")[:4]
+    plans = []
+    for k in knots:
+        kn = pk.Knot.from_pd(ctx, k.pd, outer=k.outer)
+        plans += [pk.Plan(ctx, kn, q) for q in (3, 5)]
+    prec = "split"
+    ws = [torch.empty(p.workspace_bytes(prec) + 256, dtype=torch.uint8, device="cuda")
+          for p in plans]
+    ref = []
+    for p, w in zip(plans, ws):
+        pk.upload(p, prec, w)
+        pk.launch(p, prec, w)
+        ref.append(pk.download(p, prec, w))
+    n0 = pk.upload_inputs(plans[0], prec, ws[0])
+    assert 0 < n0 <= len(plans[0].debug_blob(0))
+    ws[0][:n0].zero_()
+    assert pk.upload_inputs(plans[0], prec, ws[0]) == n0
+    pk.launch(plans[0], prec, ws[0])
+    z, v = pk.download(plans[0], prec, ws[0])
+    assert (z.mantissa, z.exp2, v.mantissa, v.exp2) == (ref[0][0].mantissa, ref[0][0].exp2,
+                                                        ref[0][1].mantissa, ref[0][1].exp2)
+    g = pk.Group(plans, prec, ws)
+    total = g.upload(inputs_only=True)
+    assert 0 < total < sum(len(p.debug_blob(0)) for p in plans) + 1
+    for p, w in zip(plans, ws):
+        w[:pk.upload_inputs(p, prec, w)].zero_()
+    torch.cuda.synchronize()
+    assert g.upload(inputs_only=True) == total
+    g.launch()
+    for (z, v), (zr, vr) in zip(g.download(), ref):
+        assert (z.mantissa, z.exp2, v.mantissa, v.exp2) == (zr.mantissa, zr.exp2, vr.mantissa, vr.exp2)
