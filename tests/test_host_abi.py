@@ -335,3 +335,19 @@ def test_plan_replay_with_tensor_core_work_floor(work):
             small = [st for st in p.steps() if st["tc"] and st["kernel"] == 0 and
                      st["R"] * st["K"] * st["N"] < work]
             assert not small
+
+
+def test_device_calls_refuse_a_host_only_context(ctx):
+    """Upload, launch and download entry points need a GPU context: on a host-only context
+    they return PK_ENODEVICE (7) before touching any pointer."""
+    import ctypes as C
+    k = pk.Knot.from_pd(ctx, kg.braid_closure_pd([1, 1, 1], 2))
+    p = pk.Plan(ctx, k, 3)
+    L = pk.lib()
+    n = C.c_uint64()
+    buf = C.c_void_p(1 << 20)   # never dereferenced: the context check comes first
+    assert L.pk_upload(ctx.h, p.h, 0, buf, 1 << 30) == 7
+    assert L.pk_upload_inputs(ctx.h, p.h, 0, buf, 1 << 30, C.byref(n)) == 7
+    assert L.pk_launch(ctx.h, p.h, 0, buf, 1 << 30) == 7
+    z, v = pk.pk_scaled(), pk.pk_scaled()
+    assert L.pk_download(ctx.h, p.h, 0, buf, C.byref(z), C.byref(v)) == 7
