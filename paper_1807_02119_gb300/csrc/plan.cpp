@@ -976,8 +976,10 @@ bool reconfigure_pass(CTree& t, int32_t kmax, int32_t rmax, const StepCost& cost
   std::vector<uint64_t> keep;
   std::vector<uint32_t> split;
   if (order.size() > max_nodes) order.resize(max_nodes);
+  // nodes a rebracketing of this pass has replaced (no longer in the tree)
+  std::vector<char> gone(t.sets.size(), 0);
   for (int32_t r : order) {
-    if (!bin(r)) continue;
+    if (!bin(r) || gone[r]) continue;
     // frontier: expand the binary member with the most indices until kmax members
     std::vector<int32_t> F{t.lc[r], t.rc[r]};
     std::vector<int32_t> inner{r};
@@ -1071,6 +1073,8 @@ bool reconfigure_pass(CTree& t, int32_t kmax, int32_t rmax, const StepCost& cost
       return (int32_t)t.sets.size() - 1;
     };
     build(full);
+    for (int32_t v : inner)   // nodes appended by this pass are never visited by it
+      if (v != r && v < (int32_t)gone.size()) gone[v] = 1;
     changed = true;
   }
   return changed;
