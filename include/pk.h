@@ -383,7 +383,8 @@ pk_status pk_group_create(pk_ctx* ctx, const pk_plan* const* plans, int32_t n, i
 pk_status pk_group_launch(pk_ctx* ctx, pk_group* grp);
 /* pk_upload (inputs_only = 0) or pk_upload_inputs (inputs_only != 0) of every plan of the
  * group into its workspace (asynchronous, the context's stream).  *copied (may be NULL):
- * the bytes copied over all plans. */
+ * the bytes copied over all plans.  This call and pk_group_download read the group's
+ * plans: they must not be destroyed before the group. */
 pk_status pk_group_upload(pk_ctx* ctx, pk_group* grp, int32_t inputs_only, uint64_t* copied);
 /* The results of every plan of the group after a pk_group_launch: one device->host copy
  * per plan of its 32-byte result record into pinned memory, one wait for the stream, then
